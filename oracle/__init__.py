@@ -1,0 +1,340 @@
+"""CPU FP64 oracle of the Z4c hot path -- test infrastructure only.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline arm
+may import this package; the product library never does.  The arithmetic is in
+``z4c_oracle.c`` (plain C, compiled with -O2 -ffp-contract=off -fno-fast-math,
+OpenMP over z-planes); this file loads it and adds the Berger-Oliger driver
+(Sec. 2.2.1), which only sequences the C operators.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle_z4c.so")
+_lock = threading.Lock()
+_lib = None
+
+NF = 25
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no GPU involved)."""
+    src = os.path.join(_HERE, "z4c_oracle.c")
+    hdr = os.path.join(_HERE, "z4c_oracle.h")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-std=c11", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _OrcPatch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("g", ctypes.c_int), ("dx", ctypes.c_double),
+                ("origin", ctypes.c_double * 3)]
+
+
+class _OrcParams(ctypes.Structure):
+    _fields_ = [("kappa1", ctypes.c_double), ("kappa2", ctypes.c_double), ("eta", ctypes.c_double),
+                ("sigma_ko", ctypes.c_double), ("w_floor", ctypes.c_double),
+                ("lapse", ctypes.c_int), ("shift", ctypes.c_int), ("lapse_uses_khat", ctypes.c_int)]
+
+
+BC_SOMMERFELD, BC_PERIODIC, BC_FROZEN = 0, 1, 2
+
+
+@dataclasses.dataclass
+class Params:
+    """Run parameters; defaults are the paper's (Sec. 2.2 and Sec. 3)."""
+    kappa1: float = 0.005
+    kappa2: float = 0.0
+    eta: float = 0.36
+    sigma_ko: float = 0.5
+    w_floor: float = 1e-10
+    lapse: int = 0          # 0: 1+log, 1: harmonic
+    shift: int = 0          # 0: Gamma driver, 1: frozen
+    lapse_uses_khat: int = 0
+
+    def c(self) -> _OrcParams:
+        return _OrcParams(self.kappa1, self.kappa2, self.eta, self.sigma_ko, self.w_floor,
+                          self.lapse, self.shift, self.lapse_uses_khat)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.POINTER
+            dp = P(ctypes.c_double)
+            L.orc_z4c_rhs.argtypes = [P(_OrcPatch), P(_OrcParams), dp, dp]
+            L.orc_z4c_rhs_terms.argtypes = [P(_OrcPatch), P(_OrcParams), dp, dp, ctypes.c_int]
+            L.orc_sommerfeld_rhs.argtypes = [P(_OrcPatch), dp, dp]
+            L.orc_fill_periodic.argtypes = [P(_OrcPatch), dp]
+            L.orc_enforce.argtypes = [P(_OrcPatch), ctypes.c_double, ctypes.c_int, dp]
+            L.orc_rk4_step.argtypes = [P(_OrcPatch), P(_OrcParams), ctypes.c_int, ctypes.c_double, dp]
+            L.orc_rk4_stage.argtypes = [P(_OrcPatch), P(_OrcParams), ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_int, dp, dp, dp, dp]
+            L.orc_constraints.argtypes = [P(_OrcPatch), dp, ctypes.c_double, dp, dp]
+            L.orc_pi_symmetry.argtypes = [P(_OrcPatch), dp, ctypes.c_int]
+            L.orc_pi_symmetry.restype = ctypes.c_double
+            L.orc_prolong_ghosts.argtypes = [P(_OrcPatch), dp, P(_OrcPatch), dp]
+            L.orc_restrict.argtypes = [P(_OrcPatch), dp, P(_OrcPatch), dp]
+            L.orc_exchange.argtypes = [P(_OrcPatch), dp, P(_OrcPatch), dp]
+            L.orc_exchange.restype = ctypes.c_long
+            L.orc_lagrange_weights.argtypes = [ctypes.c_int, P(ctypes.c_int), ctypes.c_double, dp]
+            L.orc_num_threads.restype = ctypes.c_int
+            L.orc_stencils.argtypes = [P(_OrcPatch), dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, dp, dp]
+            _lib = L
+    return _lib
+
+
+def _cp(p) -> _OrcPatch:
+    return _OrcPatch((ctypes.c_int * 3)(*[int(v) for v in p.n]), int(p.g), float(p.dx),
+                     (ctypes.c_double * 3)(*[float(v) for v in p.origin]))
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def rhs(p, u: np.ndarray, prm: Params = Params(), terms: int = 7) -> np.ndarray:
+    """Z4c right-hand side at active points (ghost entries 0).
+    terms: bit0 sources, bit1 advection, bit2 Kreiss-Oliger."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty_like(u)
+    lib().orc_z4c_rhs_terms(ctypes.byref(_cp(p)), ctypes.byref(prm.c()), _ptr(u), _ptr(out), terms)
+    return out
+
+
+def sommerfeld_rhs(p, u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros_like(u)
+    lib().orc_sommerfeld_rhs(ctypes.byref(_cp(p)), _ptr(u), _ptr(out))
+    return out
+
+
+def fill_periodic(p, u: np.ndarray) -> np.ndarray:
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    lib().orc_fill_periodic(ctypes.byref(_cp(p)), _ptr(u))
+    return u
+
+
+def enforce(p, u: np.ndarray, w_floor: float = 1e-10, all_points: bool = False) -> np.ndarray:
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    lib().orc_enforce(ctypes.byref(_cp(p)), w_floor, int(all_points), _ptr(u))
+    return u
+
+
+def rk4_step(p, u: np.ndarray, dt: float, prm: Params = Params(), bc: int = BC_SOMMERFELD) -> np.ndarray:
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    lib().orc_rk4_step(ctypes.byref(_cp(p)), ctypes.byref(prm.c()), bc, dt, _ptr(u))
+    return u
+
+
+def rk4_stage(p, prm: Params, s: int, dt: float, evolve_ghosts: bool, us, un, y, out):
+    lib().orc_rk4_stage(ctypes.byref(_cp(p)), ctypes.byref(prm.c()), s, dt, int(evolve_ghosts),
+                        _ptr(us), _ptr(un), _ptr(y), _ptr(out))
+
+
+def constraints(p, u: np.ndarray, w_excise: float = 0.0):
+    """Returns (c[4, ...] pointwise H, M^x, M^y, M^z; norms[4])."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    c = np.empty((4,) + u.shape[1:])
+    norms = np.empty(4)
+    lib().orc_constraints(ctypes.byref(_cp(p)), _ptr(u), w_excise, _ptr(c), _ptr(norms))
+    return c, norms
+
+
+def pi_symmetry(p, u: np.ndarray, include_ghosts: bool = True) -> float:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().orc_pi_symmetry(ctypes.byref(_cp(p)), _ptr(u), int(include_ghosts))
+
+
+def prolong_ghosts(parent, up: np.ndarray, child, uc: np.ndarray) -> np.ndarray:
+    up = np.ascontiguousarray(up, dtype=np.float64)
+    uc = np.array(uc, dtype=np.float64, order="C", copy=True)
+    rc = lib().orc_prolong_ghosts(ctypes.byref(_cp(parent)), _ptr(up), ctypes.byref(_cp(child)), _ptr(uc))
+    if rc != 0:
+        raise ValueError("prolongation stencil leaves the parent patch or patches misaligned")
+    return uc
+
+
+def restrict(parent, up: np.ndarray, child, uc: np.ndarray) -> np.ndarray:
+    up = np.array(up, dtype=np.float64, order="C", copy=True)
+    uc = np.ascontiguousarray(uc, dtype=np.float64)
+    rc = lib().orc_restrict(ctypes.byref(_cp(parent)), _ptr(up), ctypes.byref(_cp(child)), _ptr(uc))
+    if rc != 0:
+        raise ValueError("child not aligned with / not inside the parent")
+    return up
+
+
+def exchange(a, ua: np.ndarray, b, ub: np.ndarray) -> int:
+    """In-place same-level exchange between two patches; returns points touched."""
+    n = lib().orc_exchange(ctypes.byref(_cp(a)), _ptr(ua), ctypes.byref(_cp(b)), _ptr(ub))
+    if n < 0:
+        raise ValueError("patches not aligned")
+    return int(n)
+
+
+def stencils(p, u: np.ndarray, field: int, i: int, j: int, k: int, b=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """The RHS's finite-difference operators at one point (array indices incl.
+    ghosts): [D_x, D_y, D_z, D_xx, D_yy, D_zz, D_xD_y, D_xD_z, D_yD_z,
+    upwind D_x, D_y, D_z for shift b, 6th differences x, y, z]."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    bb = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.empty(15)
+    lib().orc_stencils(ctypes.byref(_cp(p)), _ptr(u), field, i, j, k, _ptr(bb), _ptr(out))
+    return out
+
+
+def lagrange_weights(nodes: Sequence[int], x: float) -> np.ndarray:
+    arr = (ctypes.c_int * len(nodes))(*nodes)
+    w = np.empty(len(nodes))
+    lib().orc_lagrange_weights(len(nodes), arr, x, _ptr(w))
+    return w
+
+
+def time_weights(nlevels: int, s: float) -> np.ndarray:
+    """Weights of the parent time levels (oldest first) at fraction s of the
+    parent step measured from the middle level (Sec. 2.2.1: quadratic through
+    t-DT, t, t+DT once three levels exist; linear through t, t+DT before)."""
+    if nlevels >= 3:
+        return lagrange_weights([-1, 0, 1], s)
+    return np.concatenate([[0.0], lagrange_weights([0, 1], s)])
+
+
+# ------------------------------------------------------------------ Berger-Oliger driver
+
+class BOHierarchy:
+    """Berger-Oliger subcycling over a static box-in-box hierarchy (Sec. 2.2.1).
+
+    level_step(l): one RK4 step of level l (dt_l = courant * dx_l) with child
+    ghosts prolonged (space: 6th-order Lagrange; time: quadratic through the
+    parent's three time levels, linear while only two exist) at every stage;
+    then two steps of level l+1; then restriction of l+1 onto l.  Level 0's
+    ghosts follow the Sommerfeld condition and are evolved with the stage.
+    """
+
+    def __init__(self, hierarchy, states: List[np.ndarray], prm: Params, courant: float = 0.5,
+                 bc0: int = BC_SOMMERFELD, previous: Optional[List[np.ndarray]] = None):
+        self.h = hierarchy
+        self.prm = prm
+        self.courant = courant
+        self.bc0 = bc0
+        self.patches = [p for lv in hierarchy.levels for p in lv]
+        idx = 0
+        self.level_ids = []
+        for lv in hierarchy.levels:
+            self.level_ids.append(list(range(idx, idx + len(lv))))
+            idx += len(lv)
+        self.parent = [None] * len(self.patches)
+        for l in range(1, len(hierarchy.levels)):
+            for pid in self.level_ids[l]:
+                self.parent[pid] = self._find_parent(pid, l)
+        # time levels per patch: list of arrays, oldest first (at most 3)
+        self.tl = [[np.array(s, dtype=np.float64, copy=True)] for s in states]
+        if previous is not None:  # states one step dt_l earlier: quadratic interpolation from the start
+            for pid, s in enumerate(previous):
+                self.tl[pid].insert(0, np.array(s, dtype=np.float64, copy=True))
+        self.nsteps = [0] * len(hierarchy.levels)
+
+    def _find_parent(self, pid, l):
+        c = self.patches[pid]
+        for qid in self.level_ids[l - 1]:
+            q = self.patches[qid]
+            inside = all(q.origin[d] <= c.origin[d] and
+                         c.origin[d] + c.n[d] * c.dx <= q.origin[d] + q.n[d] * q.dx for d in range(3))
+            if inside:
+                return qid
+        raise ValueError("patch %d has no parent" % pid)
+
+    def dt(self, l):
+        return self.courant * self.h.dx0 / (2 ** l)
+
+    def current(self, pid) -> np.ndarray:
+        return self.tl[pid][-1]
+
+    def _fill_child_ghosts(self, pid, u, frac):
+        """Prolong parent data at fraction frac of the parent's last step."""
+        ppid = self.parent[pid]
+        levels = self.tl[ppid]
+        # the parent's last step went from levels[-2] to levels[-1]
+        w = time_weights(len(levels), frac)
+        src = levels[-3:] if len(levels) >= 3 else [levels[-2], levels[-1]]
+        ws = w if len(levels) >= 3 else w[1:]
+        up = np.zeros_like(src[0])
+        for wi, si in zip(ws, src):
+            up = up + wi * si
+        return prolong_ghosts(self.patches[ppid], up, self.patches[pid], u)
+
+    def _exchange_level(self, l, arrays):
+        ids = self.level_ids[l]
+        for a in range(len(ids)):
+            for b in range(a + 1, len(ids)):
+                exchange(self.patches[ids[a]], arrays[a], self.patches[ids[b]], arrays[b])
+
+    def _rk4_level(self, l, frac0, dfrac):
+        """One RK4 step of every patch of level l; frac0/dfrac locate the step
+        inside the parent's last step (unused on level 0)."""
+        ids = self.level_ids[l]
+        dt = self.dt(l)
+        un = [self.tl[pid][-1] for pid in ids]
+        y = [np.zeros_like(a) for a in un]
+        cur = [a.copy() for a in un]
+        stage_frac = [0.0, 0.5, 0.5, 1.0]
+        evolve_ghosts = (l == 0 and self.bc0 == BC_SOMMERFELD)
+        for s in range(1, 5):
+            if l == 0 and self.bc0 == BC_PERIODIC:
+                cur = [fill_periodic(self.patches[pid], c) for pid, c in zip(ids, cur)]
+            if l > 0:
+                for a, pid in enumerate(ids):
+                    cur[a] = self._fill_child_ghosts(pid, cur[a], frac0 + stage_frac[s - 1] * dfrac)
+                if s == 1:
+                    un = [c.copy() for c in cur]
+                if len(ids) > 1:
+                    self._exchange_level(l, cur)
+            out = [np.empty_like(a) for a in un]
+            for a, pid in enumerate(ids):
+                rk4_stage(self.patches[pid], self.prm, s, dt, evolve_ghosts, cur[a], un[a], y[a], out[a])
+            cur = out
+        for a, pid in enumerate(ids):
+            if l == 0 and self.bc0 == BC_PERIODIC:
+                cur[a] = fill_periodic(self.patches[pid], cur[a])
+            self.tl[pid].append(cur[a])
+            if len(self.tl[pid]) > 3:
+                self.tl[pid].pop(0)
+        self.nsteps[l] += 1
+
+    def level_step(self, l=0, frac0=0.0, dfrac=1.0):
+        self._rk4_level(l, frac0, dfrac)
+        if l + 1 < len(self.h.levels):
+            self.level_step(l + 1, 0.0, 0.5)
+            self.level_step(l + 1, 0.5, 0.5)
+            # child ghosts at the parent's new time, then restriction
+            for pid in self.level_ids[l + 1]:
+                ppid = self.parent[pid]
+                uc = self._fill_child_ghosts(pid, self.tl[pid][-1], 1.0)
+                self.tl[pid][-1] = uc
+                self.tl[ppid][-1] = restrict(self.patches[ppid], self.tl[ppid][-1],
+                                             self.patches[pid], uc)

@@ -1,0 +1,147 @@
+/*
+ * Z4c oracle: a plain, slow, FP64 CPU statement of the hot path (test
+ * infrastructure only -- only the tests, the smoke check and the benchmark's
+ * CPU-baseline arm may load it; the product library never does).
+ *
+ * What pins each function (tests/test_oracle_*.py), i.e. checks it against
+ * something other than itself:
+ *   orc_stencils        exact on polynomials to each stencil's order; upwind
+ *                       bias closed form on x^6; 6th difference = 720 h^6 x^6
+ *   orc_z4c_rhs(_terms) every field converges at 4th order to the continuum
+ *                       ADM time derivative on generic smooth data (physical
+ *                       Christoffels/Ricci by definition, autograd
+ *                       derivatives); Minkowski exactly 0; Brill-Lindquist
+ *                       closed forms (W, alpha, gt, Gamt RHS exactly 0;
+ *                       d_t Khat -> -2 psi^-8 |grad psi|^2); gauge-wave RHS ->
+ *                       d/dt of the closed form; KO and advection closed forms
+ *   orc_constraints     H, M^i converge at 4th order to the ADM constraints
+ *   orc_sommerfeld_rhs  2nd-order convergence on an exact outgoing wave
+ *   orc_rk4_step/stage  gauge wave (closed form in time) at 4th order
+ *   orc_fill_periodic   brute force
+ *   orc_enforce         det gt = 1 and gt^ij At_ij = 0 to rounding
+ *   orc_pi_symmetry     symmetrised data 0, noisy data > 0; RHS and RK4 keep 0
+ *   orc_prolong_ghosts  exact on degree <= 5, not on degree 6
+ *   orc_restrict        exact on degree <= 3, not on degree 4
+ *   orc_exchange        brute force of the three overlap rules
+ *   orc_lagrange_weights exact fractions (Fraction arithmetic)
+ *   Berger-Oliger driver (oracle/__init__.py) gauge wave on 3 nested levels,
+ *                       2nd-order convergence with quadratic time interpolation
+ * No function is left "parity unpinned".
+ *
+ * Field order (25 evolved fields of the Z4c/BSSN puncture system, Sec. 2.1.1):
+ *   0 W; 1-6 gt_xx,xy,xz,yy,yz,zz; 7 Khat; 8 Theta; 9-14 At_xx..zz;
+ *   15-17 Gamt^x,y,z; 18 alpha; 19-21 beta^x,y,z; 22-24 B^x,y,z.
+ * Storage of one patch: double u[25][n2+2g][n1+2g][n0+2g], x fastest, no
+ * padding.  Active cell i (0 <= i < n) has its centre at
+ * origin + (i + 1/2) dx; ghost cells are i = -g..-1 and n..n+g-1.
+ */
+#ifndef Z4C_ORACLE_H
+#define Z4C_ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_NF 25
+
+typedef struct {
+  int n[3];          /* active cells per axis */
+  int g;             /* ghost width (3) */
+  double dx;         /* grid spacing, same on all axes */
+  double origin[3];  /* lower face of active cell 0 */
+} orc_patch;
+
+typedef struct {
+  double kappa1, kappa2;  /* Z4c damping (Sec. 3: 0.005/M, 0) */
+  double eta;             /* Gamma-driver damping (Sec. 3: 0.36/M) */
+  double sigma_ko;        /* Kreiss-Oliger coefficient (Sec. 2.2: 0.5) */
+  double w_floor;         /* floor applied to W after each stage write */
+  int lapse;              /* 0: 1+log slicing, 1: harmonic slicing */
+  int shift;              /* 0: hyperbolic Gamma driver, 1: frozen (beta=B=0) */
+  int lapse_uses_khat;    /* 0: lapse source uses K = Khat + 2 Theta; 1: Khat */
+} orc_params;
+
+/* ghost treatment of a uniform patch */
+enum { ORC_BC_SOMMERFELD = 0, ORC_BC_PERIODIC = 1, ORC_BC_FROZEN = 2, ORC_BC_NONE = 3 };
+
+size_t orc_patch_points(const orc_patch* p);
+
+/* Z4c right-hand side at every active point (ghost entries of rhs set to 0). */
+void orc_z4c_rhs(const orc_patch* p, const orc_params* prm, const double* u, double* rhs);
+
+/* Same, with only the selected terms: bit0 = sources, bit1 = advection,
+ * bit2 = Kreiss-Oliger.  orc_z4c_rhs == mask 7. */
+void orc_z4c_rhs_terms(const orc_patch* p, const orc_params* prm, const double* u,
+                       double* rhs, int mask);
+
+/* Sommerfeld outgoing-wave right-hand side at every ghost point. */
+void orc_sommerfeld_rhs(const orc_patch* p, const double* u, double* rhs);
+
+/* periodic ghost fill */
+void orc_fill_periodic(const orc_patch* p, double* u);
+
+/* algebraic constraints: det gt = 1, At trace-free, W >= w_floor; at active
+ * points (all points when all_points != 0) */
+void orc_enforce(const orc_patch* p, double w_floor, int all_points, double* u);
+
+/* one classical RK4 step of a uniform patch in place.  For ORC_BC_NONE the
+ * caller must fill ghosts itself, so this variant is not offered here; the
+ * AMR driver uses orc_rk4_stage. */
+void orc_rk4_step(const orc_patch* p, const orc_params* prm, int bc, double dt, double* u);
+
+/* one RK4 stage s (1..4), as used by the Berger-Oliger driver:
+ *   k = F(us) at active points (+ Sommerfeld at ghost points if evolve_ghosts)
+ *   s==1: y = un + dt/6 k ; s==2,3: y += dt/3 k ; s==4: out = y + dt/6 k
+ *   s<4: out = un + c_s dt k (c = 1/2, 1/2, 1)
+ * then enforcement on the written points.  Points that are not updated keep
+ * the values of un in out. */
+void orc_rk4_stage(const orc_patch* p, const orc_params* prm, int s, double dt,
+                   int evolve_ghosts, const double* us, const double* un, double* y,
+                   double* out);
+
+/* Hamiltonian and momentum constraints (index up) at active points:
+ * c[4][points] (ghost entries 0) and volume-normalised L2 norms over active
+ * points with W >= w_excise. */
+void orc_constraints(const orc_patch* p, const double* u, double w_excise, double* c,
+                     double norms[4]);
+
+/* Rotation-by-pi (x,y -> -x,-y) symmetry monitor: max over points and fields
+ * of |f(x,y,z) - s_f f(-x,-y,z)|.  Patch must be centred on x=y=0. */
+double orc_pi_symmetry(const orc_patch* p, const double* u, int include_ghosts);
+
+/* 6th-order Lagrange prolongation from a parent state into every ghost point
+ * of a child patch (2:1, cell centred). Returns 0, or -1 if the stencil leaves
+ * the parent array or the patches are not aligned. */
+int orc_prolong_ghosts(const orc_patch* parent, const double* up, const orc_patch* child,
+                       double* uc);
+
+/* 4th-order Lagrange restriction of the child onto every parent cell covered
+ * by the child's active region (child ghosts must be valid). */
+int orc_restrict(const orc_patch* parent, double* up, const orc_patch* child,
+                 const double* uc);
+
+/* Same-level exchange between two aligned patches: ghosts of each that lie in
+ * the other's active region are overwritten; active points present in both are
+ * replaced by the average. Returns the number of points touched. */
+long orc_exchange(const orc_patch* a, double* ua, const orc_patch* b, double* ub);
+
+/* The finite-difference operators of the RHS at one point (i,j,k are array
+ * indices incl. ghosts) of one field: out[0..2] = D_x, D_y, D_z (centred);
+ * out[3..5] = D_xx, D_yy, D_zz; out[6..8] = D_x(D_y), D_x(D_z), D_y(D_z);
+ * out[9..11] = upwind D_x, D_y, D_z for shift components b[0..2];
+ * out[12..14] = 6th differences along x, y, z. */
+void orc_stencils(const orc_patch* p, const double* u, int field, int i, int j, int k,
+                  const double b[3], double out[15]);
+
+/* Lagrange basis weights of a set of integer nodes at position x. */
+void orc_lagrange_weights(int nnodes, const int* nodes, double x, double* w);
+
+/* number of threads the OpenMP loops use (1 without OpenMP) */
+int orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,267 @@
+"""Continuum reference for the oracle pins, computed by a route that shares
+nothing with the oracle: the ADM (3+1) vacuum equations written with the
+physical metric, its Christoffel symbols and Ricci tensor by definition, and
+exact derivatives from torch autograd (float64, CPU).
+
+For data with Theta = 0 and Gamt^i = -d_j gt^ij (the Gamma constraint
+satisfied), the Z4c right-hand side reduces to the ADM time derivatives of the
+conformal variables plus constraint additions that the Z4c/BSSN derivation
+fixes:
+  d_t Khat  = d_t K|ADM - alpha H            (Theta absorbs alpha H / 2)
+  d_t Theta = alpha H / 2
+  d_t Gamt^i = d_t(-d_j gt^ij)|ADM + 2 alpha gt^ij M_j
+with H = R + K^2 - K_ij K^ij and M_j = D_i (K^i_j - delta^i_j K) the vacuum
+Hamiltonian and momentum constraints (Sec. 2.3).
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+from torch.func import jacfwd, vmap
+
+torch.set_default_dtype(torch.float64)
+
+EPS = 0.15
+
+
+def _sym(c):
+    """6 components (xx,xy,xz,yy,yz,zz) -> 3x3 symmetric tensor."""
+    return torch.stack([torch.stack([c[0], c[1], c[2]]), torch.stack([c[1], c[3], c[4]]),
+                        torch.stack([c[2], c[4], c[5]])])
+
+
+def det3(m):
+    """3x3 determinant by cofactors (explicit arithmetic: vmap/jacfwd safe)."""
+    return (m[0, 0] * (m[1, 1] * m[2, 2] - m[1, 2] * m[2, 1])
+            - m[0, 1] * (m[1, 0] * m[2, 2] - m[1, 2] * m[2, 0])
+            + m[0, 2] * (m[1, 0] * m[2, 1] - m[1, 1] * m[2, 0]))
+
+
+def inv3(m):
+    """3x3 inverse by the adjugate."""
+    c = [[m[(j + 1) % 3, (i + 1) % 3] * m[(j + 2) % 3, (i + 2) % 3]
+          - m[(j + 1) % 3, (i + 2) % 3] * m[(j + 2) % 3, (i + 1) % 3] for j in range(3)] for i in range(3)]
+    adj = torch.stack([torch.stack(row) for row in c])
+    return adj / det3(m)
+
+
+def _six(m):
+    return torch.stack([m[0, 0], m[0, 1], m[0, 2], m[1, 1], m[1, 2], m[2, 2]])
+
+
+# ------------------------------------------------------------- smooth generic data
+PI = math.pi
+
+
+def gamma(x):
+    X, Y, Z = x[0], x[1], x[2]
+    c = [1.0 + EPS * torch.sin(PI * X + 0.3) * torch.cos(0.5 * PI * Y),
+         0.5 * EPS * torch.sin(PI * (X + Y) + 0.1),
+         0.4 * EPS * torch.cos(PI * Z - 0.2) * torch.sin(0.5 * PI * X + 0.4),
+         1.0 + EPS * torch.cos(PI * Y - 0.5) * torch.sin(0.7 * PI * Z + 0.2),
+         0.3 * EPS * torch.sin(PI * (Y - Z) + 0.7),
+         1.0 + EPS * torch.sin(PI * Z + 0.9) * torch.cos(0.6 * PI * X)]
+    return _sym(c)
+
+
+def Kij(x):
+    X, Y, Z = x[0], x[1], x[2]
+    c = [0.3 * torch.cos(PI * X + 0.2) * torch.sin(0.5 * PI * Z + 0.1),
+         0.2 * torch.sin(PI * Y - 0.4),
+         0.25 * torch.cos(PI * (X - Z)),
+         -0.2 * torch.sin(PI * X + 0.6) * torch.cos(PI * Y),
+         0.15 * torch.cos(PI * Y + 0.3),
+         0.1 * torch.sin(PI * (X + Z) + 0.5)]
+    return _sym(c)
+
+
+def alpha(x):
+    return 0.8 + 0.1 * torch.sin(PI * x[0] + 0.2) * torch.cos(0.5 * PI * x[1] - 0.3) + 0.05 * torch.cos(PI * x[2])
+
+
+def beta(x):
+    X, Y, Z = x[0], x[1], x[2]
+    return torch.stack([0.2 * torch.sin(PI * Y + 0.4) + 0.1 * torch.cos(PI * Z),
+                        -0.15 * torch.cos(PI * X - 0.2) * torch.sin(0.5 * PI * Z + 0.6),
+                        0.1 * torch.sin(PI * (X + Y) - 0.5)])
+
+
+def Bvec(x):
+    X, Y, Z = x[0], x[1], x[2]
+    return torch.stack([0.1 * torch.cos(PI * Z + 0.2), 0.05 * torch.sin(PI * X),
+                        -0.08 * torch.cos(PI * Y - 0.1)])
+
+
+# ------------------------------------------------------------- conformal variables
+
+def W_of(x):
+    return det3(gamma(x)) ** (-1.0 / 6.0)
+
+
+def gt_of(x):
+    return W_of(x) ** 2 * gamma(x)
+
+
+def gtu_of(x):
+    return inv3(gt_of(x))
+
+
+def Ktr_of(x):
+    return torch.einsum("ij,ij->", inv3(gamma(x)), Kij(x))
+
+
+def At_of(x):
+    return W_of(x) ** 2 * (Kij(x) - gamma(x) * Ktr_of(x) / 3.0)
+
+
+def Gamt_of(x):
+    dgtu = jacfwd(gtu_of)(x)  # [i, j, k] = d_k gt^ij
+    return -torch.einsum("ijj->i", dgtu)
+
+
+def z4c_state(x):
+    """All 25 evolved fields at one point."""
+    return torch.cat([W_of(x)[None], _six(gt_of(x)), Ktr_of(x)[None], torch.zeros(1), _six(At_of(x)),
+                      Gamt_of(x), alpha(x)[None], beta(x), Bvec(x)])
+
+
+# ------------------------------------------------------------- ADM by definition
+
+def christoffel(x):
+    """Gamma^k_ij of the physical metric: [k, i, j]."""
+    g = gamma(x)
+    gu = inv3(g)
+    dg = jacfwd(gamma)(x)  # [i, j, k] = d_k g_ij
+    # Gamma_lij = 1/2 (d_i g_lj + d_j g_il - d_l g_ij)
+    low = 0.5 * (torch.einsum("lji->lij", dg) + torch.einsum("ilj->lij", dg)
+                 - torch.einsum("ijl->lij", dg))
+    return torch.einsum("kl,lij->kij", gu, low)
+
+
+def ricci(x):
+    G = christoffel(x)
+    dG = jacfwd(christoffel)(x)  # [k, i, j, m] = d_m Gamma^k_ij
+    t1 = torch.einsum("kijk->ij", dG)
+    t2 = torch.einsum("kikj->ij", dG)
+    t3 = torch.einsum("kkl,lij->ij", G, G)
+    t4 = torch.einsum("kjl,lik->ij", G, G)
+    return t1 - t2 + t3 - t4
+
+
+def lie_cov(T_fn, x):
+    """Lie derivative of a covariant 2-tensor along beta."""
+    T = T_fn(x)
+    dT = jacfwd(T_fn)(x)  # [i, j, k] = d_k T_ij
+    b = beta(x)
+    db = jacfwd(beta)(x)  # [k, i] = d_i beta^k
+    return (torch.einsum("k,ijk->ij", b, dT) + torch.einsum("kj,ki->ij", T, db)
+            + torch.einsum("ik,kj->ij", T, db))
+
+
+def dt_gamma(x):
+    return -2.0 * alpha(x) * Kij(x) + lie_cov(gamma, x)
+
+
+def dt_K(x):
+    """d_t K_ij (vacuum ADM)."""
+    G = christoffel(x)
+    da = jacfwd(alpha)(x)
+    dda = jacfwd(jacfwd(alpha))(x)
+    DDa = dda - torch.einsum("kij,k->ij", G, da)
+    K = Kij(x)
+    gu = inv3(gamma(x))
+    Kmix = torch.einsum("kl,lj->kj", gu, K)  # K^k_j
+    trK = torch.einsum("kk->", Kmix)
+    return (-DDa + alpha(x) * (ricci(x) - 2.0 * torch.einsum("ik,kj->ij", K, Kmix) + trK * K)
+            + lie_cov(Kij, x))
+
+
+def constraints_adm(x):
+    """Hamiltonian H and covariant momentum constraint M_j."""
+    g = gamma(x)
+    gu = inv3(g)
+    K = Kij(x)
+    trK = torch.einsum("ij,ij->", gu, K)
+    KK = torch.einsum("ia,jb,ij,ab->", gu, gu, K, K)
+    R = torch.einsum("ij,ij->", gu, ricci(x))
+    H = R + trK ** 2 - KK
+    G = christoffel(x)
+    dK = jacfwd(Kij)(x)  # [k, j, i] = d_i K_kj
+    # D_i K_kj = d_i K_kj - Gamma^l_ik K_lj - Gamma^l_ij K_kl
+    DK = (torch.einsum("kji->ikj", dK) - torch.einsum("lik,lj->ikj", G, K)
+          - torch.einsum("lij,kl->ikj", G, K))
+    dtrK = jacfwd(Ktr_of)(x)
+    M = torch.einsum("ik,ikj->j", gu, DK) - dtrK
+    return H, M
+
+
+def dt_W(x):
+    gu = inv3(gamma(x))
+    return -W_of(x) / 6.0 * torch.einsum("ij,ij->", gu, dt_gamma(x))
+
+
+def dt_gt(x):
+    return 2.0 * W_of(x) * dt_W(x) * gamma(x) + W_of(x) ** 2 * dt_gamma(x)
+
+
+def dt_Ktr(x):
+    gu = inv3(gamma(x))
+    dgu = -gu @ dt_gamma(x) @ gu
+    return torch.einsum("ij,ij->", dgu, Kij(x)) + torch.einsum("ij,ij->", gu, dt_K(x))
+
+
+def dt_At(x):
+    W = W_of(x)
+    K = Ktr_of(x)
+    return (2.0 * W * dt_W(x) * (Kij(x) - gamma(x) * K / 3.0)
+            + W ** 2 * (dt_K(x) - dt_gamma(x) * K / 3.0 - gamma(x) * dt_Ktr(x) / 3.0))
+
+
+def dt_gtu(x):
+    gu = gtu_of(x)
+    return -gu @ dt_gt(x) @ gu
+
+
+def dt_Gamt_kinematic(x):
+    d = jacfwd(dt_gtu)(x)  # [i, j, k] = d_k (d_t gt^ij)
+    return -torch.einsum("ijj->i", d)
+
+
+def z4c_rhs_continuum(x, eta=0.36):
+    """Expected Z4c RHS (no dissipation) for this data, 25 fields."""
+    H, M = constraints_adm(x)
+    a = alpha(x)
+    b = beta(x)
+    gtu = gtu_of(x)
+    rW = dt_W(x)
+    rgt = _six(dt_gt(x))
+    rTh = 0.5 * a * H
+    rKh = dt_Ktr(x) - a * H
+    rAt = _six(dt_At(x))
+    rG = dt_Gamt_kinematic(x) + 2.0 * a * (gtu @ M)
+    K = Ktr_of(x)
+    ra = -2.0 * a * K + b @ jacfwd(alpha)(x)
+    db = jacfwd(beta)(x)
+    rb = 0.75 * Bvec(x) + db @ b
+    dG = jacfwd(Gamt_of)(x)
+    dB = jacfwd(Bvec)(x)
+    rB = rG - dG @ b + dB @ b - eta * Bvec(x)
+    return torch.cat([rW[None], rgt, rKh[None], rTh[None], rAt, rG, ra[None], rb, rB])
+
+
+def constraints_continuum(x):
+    """H and M^i (index raised with the physical metric)."""
+    H, M = constraints_adm(x)
+    gu = inv3(gamma(x))
+    return torch.cat([H[None], gu @ M])
+
+
+def on_points(fn, pts):
+    """Evaluate fn at an (N, 3) float64 array of points, in chunks."""
+    import numpy as np
+    out = []
+    P = torch.as_tensor(pts)
+    for s in range(0, P.shape[0], 2048):
+        out.append(vmap(fn)(P[s:s + 2048]).detach().numpy())
+    return np.concatenate(out, axis=0)
