@@ -114,9 +114,17 @@ static double D1(const double* f, ptrdiff_t q, ptrdiff_t s, double h) {
   return (8.0 * (f[q + s] - f[q - s]) - (f[q + 2 * s] - f[q - 2 * s])) / (12.0 * h);
 }
 
-/* 4th-order centred second derivative along stride s */
+/* Every stencil below is a linear combination whose coefficients sum to
+ * zero, so it is evaluated on differences from the centre value f_k - f_0:
+ * the same combination, rounded relative to the result instead of to the
+ * field value (this matters where the RHS is many orders of magnitude below
+ * the field, e.g. dissipation of 1e-10 noise on gt_xx = 1). */
+
+/* 4th-order centred second derivative along stride s:
+ * (16 (f1 + f-1) - (f2 + f-2) - 30 f0) / (12 h^2) */
 static double D2(const double* f, ptrdiff_t q, ptrdiff_t s, double h) {
-  return (16.0 * (f[q + s] + f[q - s]) - (f[q + 2 * s] + f[q - 2 * s]) - 30.0 * f[q]) /
+  double f0 = f[q];
+  return (16.0 * ((f[q + s] - f0) + (f[q - s] - f0)) - ((f[q + 2 * s] - f0) + (f[q - 2 * s] - f0))) /
          (12.0 * h * h);
 }
 
@@ -130,7 +138,7 @@ static double D11(const double* f, ptrdiff_t q, ptrdiff_t sa, ptrdiff_t sb, doub
 /* lopsided stencil with one point behind and three ahead:
  * (-3 f_{-1} - 10 f_0 + 18 f_{+1} - 6 f_{+2} + f_{+3}) / 12  (times 1/h) */
 static double lop(double am1, double a0, double ap1, double ap2, double ap3) {
-  return (-3.0 * am1 - 10.0 * a0 + 18.0 * ap1 - 6.0 * ap2 + ap3) / 12.0;
+  return (-3.0 * (am1 - a0) + 18.0 * (ap1 - a0) - 6.0 * (ap2 - a0) + (ap3 - a0)) / 12.0;
 }
 
 /* 4th-order upwind derivative along stride s, biased toward the side the
@@ -144,8 +152,9 @@ static double Dup(const double* f, ptrdiff_t q, ptrdiff_t s, double h, double b)
 
 /* 6th difference along stride s (the Kreiss-Oliger operator's stencil) */
 static double Delta6(const double* f, ptrdiff_t q, ptrdiff_t s) {
-  return (f[q - 3 * s] + f[q + 3 * s]) - 6.0 * (f[q - 2 * s] + f[q + 2 * s]) +
-         15.0 * (f[q - s] + f[q + s]) - 20.0 * f[q];
+  double f0 = f[q];
+  return ((f[q - 3 * s] - f0) + (f[q + 3 * s] - f0)) - 6.0 * ((f[q - 2 * s] - f0) + (f[q + 2 * s] - f0)) +
+         15.0 * ((f[q - s] - f0) + (f[q + s] - f0));
 }
 
 void orc_stencils(const orc_patch* p, const double* u, int field, int i, int j, int k,
