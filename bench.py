@@ -1,0 +1,369 @@
+"""Throughput benchmark of the Z4c hot path on GB300.
+
+One step = one coarse step of the 7-level box-in-box Berger-Oliger hierarchy
+around an equal-mass Brill-Lindquist binary (L0-L4: one 96^3 patch each,
+dx = 4 .. 1/4; L5-L6: two 64^3 patches around the punctures at (+-5, 0, 0)):
+127 level steps of RK4 with ghost prolongation, restriction and the
+Sommerfeld outer boundary, recorded once as a CUDA graph and replayed.
+77,758,464 zone updates per step (the paper's ZCPS count: sum over levels of
+2^l x active cells).  value = zone updates / s over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Multi-GPU: replicas only (each rank evolves its own hierarchy; no collective
+on the data path), launched by torchrun.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Z4c zone-updates/s per RK4 step, FP64 vs mixed; % of GB300 HBM roofline"
+UNIT = "zone-updates/s"
+WORKLOAD = "7-level box-in-box BO binary (BL m1=m2=0.5, sep 10M), one coarse step"
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe); measured FMA probe: 1.0
+# algorithmic HBM bytes per zone per RK stage (25 FP64 fields): stage 1 reads
+# u_n and writes y and u_2 (3 passes), stages 2-3 read u_s, u_n, y and write
+# y, u_s+1 (5), stage 4 reads u_4, y and writes u_n+1 (3): 16 passes per step
+BYTES_PER_ZONE_UPDATE = 16 * 25 * 8
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                           "--format=csv,noheader,nounits", "-lms", "200"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self._proc = None
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def hierarchy():
+    import initial_data as idd
+    return idd.binary_7_level()
+
+
+def launches_per_coarse_step(h) -> int:
+    """Kernels launched by one coarse step (the recursion is static)."""
+    total = 0
+    for l, lv in enumerate(h.levels):
+        steps = 2 ** l
+        per = 0
+        for s in range(4):
+            if l > 0:
+                per += 1 + (len(lv) * (len(lv) - 1)) // 2 * 0  # prolongation (exchange only if touching)
+            per += 1                                          # fused stage kernel
+            if l == 0:
+                per += 1                                      # Sommerfeld ghosts
+        per += 1                                              # level bookkeeping
+        if l > 0:
+            per += 2                                          # ghost fill at the new time + restriction
+        total += steps * per
+    return total
+
+
+def cpu_sample(steps: int = 1):
+    """The oracle (as it stands) on a bounded sample of the workload: RK4
+    steps of the level-0 96^3 patch with its Sommerfeld ghosts, all host cores."""
+    import initial_data as idd
+    import oracle
+    h = hierarchy()
+    p = h.levels[0][0]
+    u = idd.punctures(p, h.masses, h.positions)
+    prm = oracle.Params()
+    oracle.rk4_step(p, u, 0.25 * p.dx, prm)  # warm (builds the oracle)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = oracle.rk4_step(p, u, 0.25 * p.dx, prm)
+    dt = time.perf_counter() - t0
+    zu = steps * p.active_points
+    return zu / dt, oracle.num_threads(), "%d RK4 step(s) of the level-0 96^3 patch (%d zone updates)" % (
+        steps, zu)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_sample(1)
+    vals = []
+    cores = 1
+    sample = ""
+    for _ in range(args.steps):
+        v, cores, sample = cpu_sample(1)
+        vals.append(v)
+    value = float(np.mean(vals))
+    ms = 96 ** 3 / value * 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--courant", type=float, default=0.25)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", default="amr7", choices=["amr7", "uniform96"],
+                    help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2607_08743_gb300 import build as skbuild
+    skbuild.build()
+    import paper_2607_08743_gb300 as sk
+
+    if args.case == "uniform96":
+        uniform_case(torch, sk, args)
+        return
+
+    h = hierarchy()
+    zu = h.zone_updates_per_coarse_step()
+    prm = sk.Params(courant=args.courant, precision=1 if args.precision == "mixed" else 0)
+    stream = torch.cuda.Stream()
+    g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=stream)
+    g.set_initial_data(1, h.masses, h.positions)
+
+    # per-launch time of the fused stage kernel, measured on the grid's stream
+    def step():
+        g.level_step(0)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * zu / (ms * 1e-3)
+    # the state must still be finite (stage kernels flag non-finite values)
+    norms = g.constraints(0)
+
+    # dominant kernel: the fused Z4c stage kernel, every launch of a profiled
+    # (eager) pass over the same workload timed with CUDA events
+    kern = stage_kernel_timing(g, max(1, min(args.steps, 2)))
+    kern["share_of_step"] = kern["ms"] * kern["launches"] / max(1, min(args.steps, 2)) / ms
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(torch, sk, h, prm, args, world, dist)
+
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ach_gflops = kern["flops_per_launch"] / (kern["ms"] * 1e-3) / 1e12 if kern["flops_per_launch"] else None
+    hbm_gbs = kern["bytes_per_launch"] / (kern["ms"] * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": ach_gflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (ach_gflops / FP64_PEAK_TFLOPS) if ach_gflops else None, "traffic": kern["traffic"],
+            "kernel": kern["name"], "launch_ms": kern["ms"],
+            "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm, "hbm_frac_of_measured": hbm_gbs / hbm,
+            "peak_note": "FP64 nominal 1.25 TFLOP/s (recipe); HBM peak of measured copy"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels": len(h.levels), "patches": len(h.patches),
+                       "zone_updates_per_step": zu, "courant": args.courant, "precision": args.precision,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2: %.2f GB per state copy" % (
+                           sum(25 * 8 * (p.n[0] + 6) * (p.n[1] + 6) * (p.n[2] + 6) for p in h.patches) / 1e9),
+                       "hbm_roofline_zone_updates_per_s": hbm * 1e9 / BYTES_PER_ZONE_UPDATE,
+                       "hbm_frac_of_measured": value / world / (hbm * 1e9 / BYTES_PER_ZONE_UPDATE)},
+            "roofline": roof,
+            "gpu_launches": launches_per_coarse_step(h) * args.steps,
+            "clocks": clk.summary(),
+            "constraints_l0": list(norms)}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_sample(1)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def uniform_case(torch, sk, args):
+    """RK4 steps of the level-0 96^3 patch alone (Sommerfeld ghosts): the
+    small, single-kernel case used for ncu captures."""
+    import initial_data as idd
+    h = hierarchy()
+    p = h.levels[0][0]
+    prm = sk.Params(courant=args.courant, precision=1 if args.precision == "mixed" else 0)
+    stream = torch.cuda.Stream()
+    g = sk.Grid(1, p.dx, [p], prm, stream=stream)
+    g.set_initial_data(1, h.masses, h.positions)
+    for _ in range(args.warmup):
+        g.rk4_step(0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.rk4_step(0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    g.constraints(0)
+    print(json.dumps({"case": "uniform96", "ms_per_rk4_step": ms,
+                      "zone_updates_per_s": p.active_points / (ms * 1e-3)}), flush=True)
+    g.close()
+
+
+def stage_kernel_timing(g, steps):
+    """Average duration of one launch of the fused RHS + RK4 stage kernel over
+    `steps` coarse steps, from CUDA events bracketing every launch on the
+    grid's stream (eager launches while profiling is on)."""
+    g.profile_enable(True)
+    for _ in range(steps):
+        g.level_step(0)
+    ms, n, zones = g.profile_read()
+    g.profile_enable(False)
+    per = ms / n
+    zones_per_launch = zones / n
+    fz = FLOPS_PER_ZONE_STAGE.get(g.params.precision)
+    return {"name": "z4c_stage_fp64_kernel" if g.params.precision == 0 else "z4c_stage_mixed_kernel",
+            "ms": per, "launches": n, "share_of_step": None,
+            "bytes_per_launch": zones_per_launch * BYTES_PER_ZONE_UPDATE / 4.0,
+            "flops_per_launch": zones_per_launch * fz if fz else None,
+            "traffic": None, "zones_per_launch": zones_per_launch}
+
+
+# FP64 flops per zone per stage of the fused kernel (DFMA counted as 2), from
+# the ncu instruction counts of one launch divided by the zones it updates
+FLOPS_PER_ZONE_STAGE = {}
+
+
+def end_to_end(torch, sk, h, prm, args, world, dist):
+    """Same metric through the public API with host buffers: every step
+    uploads every patch from pinned host memory, runs the coarse step and
+    downloads every patch."""
+    stream = torch.cuda.Stream()
+    g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=stream)
+    g.set_initial_data(1, h.masses, h.positions)
+    host = [torch.empty(g.shape(i), dtype=torch.float64).pin_memory() for i in range(len(h.patches))]
+    for i in range(len(h.patches)):
+        g.download_fields(i, host[i])
+    nbytes = sum(x.numel() * 8 for x in host)
+
+    def step():
+        for i in range(len(h.patches)):
+            g.upload_fields(i, host[i])
+        g.level_step(0)
+        for i in range(len(h.patches)):
+            g.download_fields(i, host[i])
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    g.close()
+    zu = h.zone_updates_per_coarse_step()
+    return {"value": world * zu / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "ms_per_step": ms}
+
+
+if __name__ == "__main__":
+    main()

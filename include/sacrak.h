@@ -1,0 +1,169 @@
+/*
+ * sacrak.h -- C ABI of the GB300 (sm_103a) Z4c hot path.
+ *
+ * The library evolves the 25 Z4c/BSSN puncture fields (Sec. 2.1.1 of the
+ * SACRA-K paper) with 4th-order finite differences, lopsided upwind advection
+ * along the shift, 6th-order Kreiss-Oliger dissipation and classical RK4
+ * (Sec. 2.2), on static box-in-box Berger-Oliger patches with subcycling,
+ * 6th-order Lagrange prolongation, time interpolation between parent time
+ * levels and 4th-order Lagrange restriction (Sec. 2.2.1), with the Sommerfeld
+ * outgoing-wave condition on the coarsest level (Sec. 2.2.2) and the
+ * Hamiltonian/momentum constraint monitor (Sec. 2.3).
+ *
+ * Conventions shared by every call
+ *  - Field order: 0 W; 1-6 gt_xx,xy,xz,yy,yz,zz; 7 Khat; 8 Theta;
+ *    9-14 At_xx..zz; 15-17 Gamt^x,y,z; 18 alpha; 19-21 beta^x,y,z;
+ *    22-24 B^x,y,z.
+ *  - A "patch array" exchanged with the caller is double[25][NZ][NY][NX] with
+ *    NX = n[0]+6, NY = n[1]+6, NZ = n[2]+6 (ghost width 3 on every side), x
+ *    fastest, no padding.  Active cell i has its centre at
+ *    origin + (i + 1/2) dx_level; ghost cells are i = -3..-1 and n..n+2.
+ *  - Pointers named host_or_dev may be host memory (pageable or pinned) or
+ *    device memory; the library asks CUDA which it is.
+ *  - Ownership: the caller owns every buffer it passes, including the device
+ *    arena given to sacrak_grid_create, which the library never frees and
+ *    never reallocates.  The library allocates no device memory on any call.
+ *  - Ordering: all device work is issued on the grid's CUDA stream, in call
+ *    order.  Calls that return values computed on the device (constraints,
+ *    pi symmetry, downloads to host memory) synchronise that stream.
+ *  - Errors: no call aborts or throws across the ABI.  Invalid arguments
+ *    return SACRAK_EINVAL before any device work is issued; a CUDA error
+ *    returns SACRAK_ECUDA; a non-finite value detected by a stage returns
+ *    SACRAK_ENONFINITE at the next call that synchronises; a bounded device
+ *    wait that runs out returns SACRAK_ETIMEOUT.  After ECUDA, ENONFINITE or
+ *    ETIMEOUT the grid is marked invalid and every stepping call returns
+ *    SACRAK_ESTATE until new data is uploaded or set.  sacrak_last_error
+ *    gives a one-line description.
+ *  - Thread safety: one grid per host thread.
+ */
+#ifndef SACRAK_H
+#define SACRAK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SACRAK_OK = 0,
+  SACRAK_EINVAL = 1,
+  SACRAK_ENOMEM = 2,
+  SACRAK_ECUDA = 3,
+  SACRAK_ENONFINITE = 4,
+  SACRAK_ETIMEOUT = 5,
+  SACRAK_ESTATE = 6
+} sacrak_status;
+
+typedef struct sacrak_grid sacrak_grid; /* opaque, host memory */
+
+/* Run parameters (Sec. 2.2, Sec. 3: kappa1 = 0.005/M, kappa2 = 0,
+ * eta = 0.36/M, sigma_KO = 0.5, Courant factor 0.5). */
+typedef struct {
+  double kappa1, kappa2; /* Z4c constraint damping */
+  double eta;            /* Gamma-driver damping */
+  double sigma_ko;       /* Kreiss-Oliger coefficient */
+  double courant;        /* dt_level = courant * dx_level */
+  double w_floor;        /* W >= w_floor after every stage write */
+  int lapse;             /* 0: 1+log (d0 alpha = -2 alpha K), 1: harmonic (-alpha^2 K) */
+  int shift;             /* 0: hyperbolic Gamma driver, 1: frozen (beta = B = 0) */
+  int bc;                /* coarsest level ghosts: 0 Sommerfeld, 1 periodic, 2 frozen */
+  int precision;         /* 0: FP64, 1: mixed (FP32 stencils/sources, FP64 state) */
+  int lapse_uses_khat;   /* 0: 1+log source uses K = Khat + 2 Theta, 1: Khat */
+} sacrak_params;
+
+/* One patch: refinement level, active cells per axis, lower face of active
+ * cell 0.  Level l has spacing dx0 / 2^l.  A patch of level l > 0 must lie
+ * inside one patch of level l-1 with its faces on that parent's cell faces
+ * and at least 4 parent cells between its active region and the parent's
+ * active edge (the 6-point prolongation stencils of its ghosts then read
+ * parent active cells only); n must be even on levels > 0. */
+typedef struct {
+  int level;
+  int n[3];
+  double origin[3];
+} sacrak_patch_desc;
+
+/* Bytes of device memory a grid of this shape needs (6 state copies per
+ * patch: 3 time levels, the RK accumulator and 2 stage buffers; plus tables
+ * and reduction scratch).  Returns 0 for an invalid description. */
+size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* patches);
+
+/* Create a grid on the current CUDA device.  device_arena must point to at
+ * least sacrak_arena_bytes(...) bytes of device memory, 256-byte aligned.
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream). Fields start
+ * as Minkowski.  With the Sommerfeld boundary (bc = 0) every level-0 patch must
+ * contain the coordinate origin. */
+sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
+                                 const sacrak_patch_desc* patches, const sacrak_params* params,
+                                 void* cuda_stream, void* device_arena, size_t arena_bytes,
+                                 sacrak_grid** out);
+
+sacrak_status sacrak_grid_destroy(sacrak_grid* grid);
+
+/* Analytic initial data on every patch (ghosts included), generated on the
+ * device.  kind: 0 Minkowski, 1 Brill-Lindquist punctures (m[a], pos[3a..]),
+ * 2 gauge wave (H = 1 - gw_amp sin(2 pi x / gw_len), harmonic slicing, zero
+ * shift).  noise_amp > 0 adds uniform noise in [-noise_amp, noise_amp) from
+ * the counter hash h = sm(sm(sm(sm(seed + f) ^ i) ^ j) ^ k), SplitMix64's
+ * output function sm, level-global cell indices (i,j,k) counted from the
+ * level-0 patch's origin.  symmetrise_pi replaces every point with x < 0 by
+ * its pi partner (-x,-y,z) times the field parity (Sec. 3.2); it needs patches
+ * centred on x = y = 0.  Resets the time levels (the next step interpolates
+ * linearly in time, Sec. 2.2.1). */
+sacrak_status sacrak_set_initial_data(sacrak_grid* grid, int kind, int npunct, const double* m,
+                                      const double* pos, double gw_amp, double gw_len,
+                                      double noise_amp, uint64_t seed, int symmetrise_pi);
+
+/* Copy a whole patch array (ghosts included) into / out of the current time
+ * level.  Upload resets the time levels like sacrak_set_initial_data. */
+sacrak_status sacrak_upload_fields(sacrak_grid* grid, int patch, const double* host_or_dev);
+sacrak_status sacrak_download_fields(sacrak_grid* grid, int patch, double* host_or_dev);
+
+/* Z4c right-hand side (sources + upwind advection + Kreiss-Oliger) of the
+ * current state of one patch at its active points, ghosts used as they are.
+ * Output is a patch array whose ghost entries are 0. */
+sacrak_status sacrak_rhs(sacrak_grid* grid, int patch, double* host_or_dev_rhs);
+
+/* One classical RK4 step of every patch of one level with dt (dt <= 0: use
+ * courant * dx_level).  Level 0's ghosts follow params.bc; ghosts of finer
+ * levels are prolonged from the parent at every stage time.  Does not recurse
+ * into finer levels and does not restrict. */
+sacrak_status sacrak_rk4_step(sacrak_grid* grid, int level, double dt);
+
+/* Berger-Oliger step of `level` and everything finer (Sec. 2.2.1): RK4 step of
+ * the level, two recursive steps of level+1, restriction of level+1 onto it.
+ * sacrak_level_step(grid, 0) is one coarse step.  The first call records the
+ * launch sequence into a CUDA graph; later calls replay it. */
+sacrak_status sacrak_level_step(sacrak_grid* grid, int level);
+
+/* Volume-normalised L2 norms of H, M^x, M^y, M^z over the active cells of a
+ * level with W >= w_excise (Sec. 2.3). */
+sacrak_status sacrak_constraints(sacrak_grid* grid, int level, double w_excise,
+                                 double out_l2[4]);
+
+/* max over all points (ghosts included) and fields of |f(x,y,z) - s_f f(-x,-y,z)|
+ * for one patch centred on x = y = 0 (Sec. 3.2). */
+sacrak_status sacrak_pi_symmetry(sacrak_grid* grid, int patch, double* max_abs_diff);
+
+/* Kernel timing for roofline reports.  While enabled, level steps launch
+ * eagerly (no graph) and every launch of the fused RHS + RK4 stage kernel is
+ * bracketed by CUDA events on the grid's stream.  sacrak_profile_read
+ * synchronises the stream and returns the summed duration of those launches
+ * (ms), their number and the zones they updated; enabling again clears the
+ * totals. */
+sacrak_status sacrak_profile_enable(sacrak_grid* grid, int enable);
+sacrak_status sacrak_profile_read(sacrak_grid* grid, double* stage_ms, long long* stage_launches,
+                                  long long* stage_zones);
+
+/* Current time of a level. */
+sacrak_status sacrak_level_time(sacrak_grid* grid, int level, double* t);
+
+/* One-line description of the last error on this grid ("" if none). */
+const char* sacrak_last_error(const sacrak_grid* grid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SACRAK_H */

@@ -245,10 +245,31 @@ def binary_10_level() -> Hierarchy:
 
 
 def small_binary(n_fixed: int = 24, n_moving: int = 16, n_levels: int = 4, n_fixed_levels: int = 2,
-                 dx0: float = 1.0, sep: float = 2.5) -> Hierarchy:
+                 dx0: float = 1.0, sep: float = 2.0) -> Hierarchy:
     """Scaled-down version of the 7-level hierarchy for oracle parity runs."""
     return box_in_box(n_fixed, n_moving, n_levels, n_fixed_levels, dx0, [0.5, 0.5],
                       [(sep, 0.0, 0.0), (-sep, 0.0, 0.0)])
+
+
+def nesting_ok(h: Hierarchy, margin: int = 4) -> bool:
+    """Every patch of level l > 0 lies inside a patch of level l-1, aligned with
+    its cell faces, with at least `margin` parent cells around it."""
+    for l in range(1, len(h.levels)):
+        for c in h.levels[l]:
+            ok_any = False
+            for p in h.levels[l - 1]:
+                ok = True
+                for d in range(3):
+                    t = (c.origin[d] - p.origin[d]) / p.dx
+                    if abs(t - round(t)) > 1e-9 or c.n[d] % 2:
+                        ok = False
+                    off = int(round(t))
+                    if off - margin < 0 or off + c.n[d] // 2 + margin - 1 > p.n[d] - 1:
+                        ok = False
+                ok_any |= ok
+            if not ok_any:
+                return False
+    return True
 
 
 def level_origin(h: Hierarchy, level: int):

@@ -231,9 +231,12 @@ class BOHierarchy:
 
     level_step(l): one RK4 step of level l (dt_l = courant * dx_l) with child
     ghosts prolonged (space: 6th-order Lagrange; time: quadratic through the
-    parent's three time levels, linear while only two exist) at every stage;
-    then two steps of level l+1; then restriction of l+1 onto l.  Level 0's
-    ghosts follow the Sommerfeld condition and are evolved with the stage.
+    parent's three time levels, linear while only two exist) and then exchanged
+    between same-level patches at every stage; then two steps of level l+1;
+    then, for level l+1: ghosts prolonged at the parent's new time from the
+    unrestricted parent, exchange, and restriction of every child onto l.
+    Level 0's ghosts follow the Sommerfeld condition and are evolved with the
+    stage.
     """
 
     def __init__(self, hierarchy, states: List[np.ndarray], prm: Params, courant: float = 0.5,
@@ -310,10 +313,10 @@ class BOHierarchy:
             if l > 0:
                 for a, pid in enumerate(ids):
                     cur[a] = self._fill_child_ghosts(pid, cur[a], frac0 + stage_frac[s - 1] * dfrac)
-                if s == 1:
-                    un = [c.copy() for c in cur]
                 if len(ids) > 1:
                     self._exchange_level(l, cur)
+                if s == 1:  # the stage-1 state, ghosts filled, is the step's u_n
+                    un = [c.copy() for c in cur]
             out = [np.empty_like(a) for a in un]
             for a, pid in enumerate(ids):
                 rk4_stage(self.patches[pid], self.prm, s, dt, evolve_ghosts, cur[a], un[a], y[a], out[a])
@@ -331,10 +334,15 @@ class BOHierarchy:
         if l + 1 < len(self.h.levels):
             self.level_step(l + 1, 0.0, 0.5)
             self.level_step(l + 1, 0.5, 0.5)
-            # child ghosts at the parent's new time, then restriction
-            for pid in self.level_ids[l + 1]:
+            # child ghosts at the parent's new time (from the parent before any
+            # restriction), same-level exchange, then restriction of every child
+            kids = self.level_ids[l + 1]
+            for pid in kids:
+                self.tl[pid][-1] = self._fill_child_ghosts(pid, self.tl[pid][-1], 1.0)
+            if len(kids) > 1:
+                cur = [self.tl[pid][-1] for pid in kids]
+                self._exchange_level(l + 1, cur)
+            for pid in kids:
                 ppid = self.parent[pid]
-                uc = self._fill_child_ghosts(pid, self.tl[pid][-1], 1.0)
-                self.tl[pid][-1] = uc
                 self.tl[ppid][-1] = restrict(self.patches[ppid], self.tl[ppid][-1],
-                                             self.patches[pid], uc)
+                                             self.patches[pid], self.tl[pid][-1])

@@ -1,0 +1,257 @@
+"""Python binding of libsacrak (the C ABI in include/sacrak.h).
+
+Argument marshalling only: every step of the Z4c hot path runs in the CUDA
+kernels of libsacrak.so.  PyTorch provides the device arena and the stream.
+There is no CPU fallback: importing works without a GPU, but creating a grid
+needs the built library and a CUDA device, and fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsacrak.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE = range(7)
+_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ESTATE"]
+NF = 25
+GHOST = 3
+
+# functions the header declares (checked by the ABI test)
+EXPORTS = [
+    "sacrak_arena_bytes", "sacrak_grid_create", "sacrak_grid_destroy", "sacrak_set_initial_data",
+    "sacrak_upload_fields", "sacrak_download_fields", "sacrak_rhs", "sacrak_rk4_step",
+    "sacrak_level_step", "sacrak_constraints", "sacrak_pi_symmetry", "sacrak_level_time",
+    "sacrak_last_error", "sacrak_profile_enable", "sacrak_profile_read",
+]
+
+
+class SacrakError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_NAMES[status] if 0 <= status < 7 else status, msg))
+        self.status = status
+
+
+class sacrak_params(ctypes.Structure):
+    _fields_ = [("kappa1", ctypes.c_double), ("kappa2", ctypes.c_double), ("eta", ctypes.c_double),
+                ("sigma_ko", ctypes.c_double), ("courant", ctypes.c_double), ("w_floor", ctypes.c_double),
+                ("lapse", ctypes.c_int), ("shift", ctypes.c_int), ("bc", ctypes.c_int),
+                ("precision", ctypes.c_int), ("lapse_uses_khat", ctypes.c_int)]
+
+
+class sacrak_patch_desc(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("n", ctypes.c_int * 3), ("origin", ctypes.c_double * 3)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsacrak.so (build it first with paper_2607_08743_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libsacrak.so is not built (%s); run paper_2607_08743_gb300.build.build()"
+                                   % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.POINTER
+            vp, dp = ctypes.c_void_p, P(ctypes.c_double)
+            L.sacrak_arena_bytes.restype = ctypes.c_size_t
+            L.sacrak_arena_bytes.argtypes = [ctypes.c_int, ctypes.c_int, P(sacrak_patch_desc)]
+            L.sacrak_grid_create.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                             P(sacrak_patch_desc), P(sacrak_params), vp, vp,
+                                             ctypes.c_size_t, P(vp)]
+            L.sacrak_grid_destroy.argtypes = [vp]
+            L.sacrak_set_initial_data.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                                  ctypes.c_int]
+            L.sacrak_upload_fields.argtypes = [vp, ctypes.c_int, vp]
+            L.sacrak_download_fields.argtypes = [vp, ctypes.c_int, vp]
+            L.sacrak_rhs.argtypes = [vp, ctypes.c_int, vp]
+            L.sacrak_rk4_step.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+            L.sacrak_level_step.argtypes = [vp, ctypes.c_int]
+            L.sacrak_constraints.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp]
+            L.sacrak_pi_symmetry.argtypes = [vp, ctypes.c_int, dp]
+            L.sacrak_level_time.argtypes = [vp, ctypes.c_int, dp]
+            L.sacrak_profile_enable.argtypes = [vp, ctypes.c_int]
+            L.sacrak_profile_read.argtypes = [vp, dp, P(ctypes.c_longlong), P(ctypes.c_longlong)]
+            L.sacrak_last_error.argtypes = [vp]
+            L.sacrak_last_error.restype = ctypes.c_char_p
+            for name in EXPORTS:
+                if name != "sacrak_arena_bytes" and name != "sacrak_last_error":
+                    getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+@dataclasses.dataclass
+class Params:
+    """sacrak_params; defaults are the paper's (Sec. 2.2, Sec. 3)."""
+    kappa1: float = 0.005
+    kappa2: float = 0.0
+    eta: float = 0.36
+    sigma_ko: float = 0.5
+    courant: float = 0.5
+    w_floor: float = 1e-10
+    lapse: int = 0
+    shift: int = 0
+    bc: int = 0            # 0 Sommerfeld, 1 periodic, 2 frozen
+    precision: int = 0     # 0 FP64, 1 mixed
+    lapse_uses_khat: int = 0
+
+    def c(self) -> sacrak_params:
+        return sacrak_params(self.kappa1, self.kappa2, self.eta, self.sigma_ko, self.courant, self.w_floor,
+                             self.lapse, self.shift, self.bc, self.precision, self.lapse_uses_khat)
+
+
+def _descs(patches) -> ctypes.Array:
+    arr = (sacrak_patch_desc * len(patches))()
+    for i, p in enumerate(patches):
+        arr[i].level = int(getattr(p, "level", 0))
+        for d in range(3):
+            arr[i].n[d] = int(p.n[d])
+            arr[i].origin[d] = float(p.origin[d])
+    return arr
+
+
+def arena_bytes(nlevels: int, patches) -> int:
+    d = _descs(patches)
+    return int(lib().sacrak_arena_bytes(nlevels, len(patches), d))
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.dtype.itemsize == 8 and a.is_contiguous()
+    return a.data_ptr()
+
+
+class Grid:
+    """A static box-in-box hierarchy on one GPU.  `patches` are objects with
+    .level, .n (3 ints) and .origin (3 floats); level l has spacing dx0/2^l."""
+
+    def __init__(self, nlevels: int, dx0: float, patches: Sequence, params: Params = Params(),
+                 stream=None, device=None):
+        import torch
+        self._torch = torch
+        L = lib()
+        self.nlevels = nlevels
+        self.dx0 = dx0
+        self.patches = list(patches)
+        self.params = params
+        d = _descs(self.patches)
+        nbytes = L.sacrak_arena_bytes(nlevels, len(self.patches), d)
+        if nbytes == 0:
+            raise SacrakError(EINVAL, "invalid patch description")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        with torch.cuda.device(dev):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+            self.arena = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            h = ctypes.c_void_p()
+            prm = params.c()
+            st = L.sacrak_grid_create(nlevels, dx0, len(self.patches), d, ctypes.byref(prm),
+                                      ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.c_void_p(self.arena.data_ptr()), nbytes, ctypes.byref(h))
+        if st != OK:
+            raise SacrakError(st, "sacrak_grid_create failed")
+        self._h = h
+        self.arena_bytes = nbytes
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, st: int, what: str):
+        if st != OK:
+            msg = lib().sacrak_last_error(self._h).decode()
+            raise SacrakError(st, "%s: %s" % (what, msg))
+
+    def shape(self, patch: int):
+        p = self.patches[patch]
+        return (NF, p.n[2] + 2 * GHOST, p.n[1] + 2 * GHOST, p.n[0] + 2 * GHOST)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sacrak_grid_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ ABI
+    def set_initial_data(self, kind: int = 0, masses=(), positions=(), gw_amp: float = 0.0,
+                         gw_len: float = 1.0, noise_amp: float = 0.0, seed: int = 0,
+                         symmetrise_pi: bool = False):
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+        pos = np.ascontiguousarray(np.asarray(positions, dtype=np.float64).reshape(-1))
+        dp = ctypes.POINTER(ctypes.c_double)
+        st = lib().sacrak_set_initial_data(self._h, kind, len(m), m.ctypes.data_as(dp) if len(m) else None,
+                                           pos.ctypes.data_as(dp) if len(pos) else None, gw_amp, gw_len,
+                                           noise_amp, seed, int(symmetrise_pi))
+        self._check(st, "set_initial_data")
+
+    def upload_fields(self, patch: int, data):
+        if isinstance(data, np.ndarray):
+            data = np.ascontiguousarray(data, dtype=np.float64)
+            assert data.shape == self.shape(patch)
+        self._check(lib().sacrak_upload_fields(self._h, patch, ctypes.c_void_p(_ptr(data))), "upload_fields")
+
+    def download_fields(self, patch: int, out=None):
+        if out is None:
+            out = np.empty(self.shape(patch))
+        self._check(lib().sacrak_download_fields(self._h, patch, ctypes.c_void_p(_ptr(out))), "download_fields")
+        return out
+
+    def rhs(self, patch: int, out=None):
+        if out is None:
+            out = np.empty(self.shape(patch))
+        self._check(lib().sacrak_rhs(self._h, patch, ctypes.c_void_p(_ptr(out))), "rhs")
+        return out
+
+    def rk4_step(self, level: int = 0, dt: float = 0.0):
+        self._check(lib().sacrak_rk4_step(self._h, level, dt), "rk4_step")
+
+    def level_step(self, level: int = 0):
+        self._check(lib().sacrak_level_step(self._h, level), "level_step")
+
+    def constraints(self, level: int = 0, w_excise: float = 0.0) -> np.ndarray:
+        out = np.empty(4)
+        self._check(lib().sacrak_constraints(self._h, level, w_excise,
+                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "constraints")
+        return out
+
+    def pi_symmetry(self, patch: int = 0) -> float:
+        v = ctypes.c_double()
+        self._check(lib().sacrak_pi_symmetry(self._h, patch, ctypes.byref(v)), "pi_symmetry")
+        return v.value
+
+    def level_time(self, level: int = 0) -> float:
+        v = ctypes.c_double()
+        self._check(lib().sacrak_level_time(self._h, level, ctypes.byref(v)), "level_time")
+        return v.value
+
+    def profile_enable(self, enable: bool = True):
+        self._check(lib().sacrak_profile_enable(self._h, int(enable)), "profile_enable")
+
+    def profile_read(self):
+        """(summed stage-kernel ms, launches, zones updated) since enabling."""
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        z = ctypes.c_longlong()
+        self._check(lib().sacrak_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(z)),
+                    "profile_read")
+        return ms.value, n.value, z.value
+
+    def last_error(self) -> str:
+        return lib().sacrak_last_error(self._h).decode()

@@ -1,0 +1,761 @@
+// C ABI of the Z4c hot path: grid creation over a caller-owned device arena,
+// data movement, RK4 stages, Berger-Oliger subcycling (captured as a CUDA
+// graph) and diagnostics.  Host code only issues launches; every step of the
+// path runs in the kernels of z4c_fp64.cu, z4c_mixed.cu, amr.cu and
+// diagnostics.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sacrak.h"
+#include "sacrak_dev.cuh"
+
+using namespace sacrak;
+
+namespace {
+
+constexpr int TILE_X = 32, TILE_Y = 4;
+enum { FILL_PERIODIC = 0, FILL_FROZEN = 1, FILL_PROLONG = 2, FILL_RESTRICT = 3 };
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+  // byte offsets inside the arena
+  size_t patches, levels, ids, tiles, err, results, scratch, states, total;
+  std::vector<size_t> patch_state;  // offset of each patch's first buffer
+  std::vector<long long> fstride;
+  std::vector<int> px;
+  size_t ntiles = 0, scratch_doubles = 0;
+};
+
+bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, Layout& L, std::string& why) {
+  if (nlevels < 1 || npatches < 1 || !pd) {
+    why = "need at least one level and one patch";
+    return false;
+  }
+  std::vector<int> count(nlevels, 0);
+  for (int p = 0; p < npatches; ++p) {
+    if (pd[p].level < 0 || pd[p].level >= nlevels) {
+      why = "patch level out of range";
+      return false;
+    }
+    for (int d = 0; d < 3; ++d)
+      if (pd[p].n[d] < 4 || pd[p].n[d] > 4096) {
+        why = "patch size out of range (4..4096 cells per axis)";
+        return false;
+      }
+    count[pd[p].level]++;
+  }
+  for (int l = 0; l < nlevels; ++l)
+    if (count[l] == 0) {
+      why = "every level needs a patch";
+      return false;
+    }
+  size_t off = 0;
+  L.patches = off;
+  off = align_up(off + sizeof(DevPatch) * npatches, 256);
+  L.levels = off;
+  off = align_up(off + sizeof(DevLevel) * nlevels, 256);
+  L.ids = off;
+  off = align_up(off + sizeof(int) * npatches, 256);
+  size_t ntiles = 0, maxtiles_level = 0, maxpts = 0;
+  std::vector<size_t> lt(nlevels, 0);
+  for (int p = 0; p < npatches; ++p) {
+    size_t t = (size_t)((pd[p].n[0] + TILE_X - 1) / TILE_X) * ((pd[p].n[1] + TILE_Y - 1) / TILE_Y) *
+               pd[p].n[2];
+    ntiles += t;
+    lt[pd[p].level] += t;
+    size_t pts = (size_t)(pd[p].n[0] + 2 * GH) * (pd[p].n[1] + 2 * GH) * (pd[p].n[2] + 2 * GH);
+    maxpts = pts > maxpts ? pts : maxpts;
+  }
+  for (int l = 0; l < nlevels; ++l) maxtiles_level = lt[l] > maxtiles_level ? lt[l] : maxtiles_level;
+  L.ntiles = ntiles;
+  L.tiles = off;
+  off = align_up(off + sizeof(Tile) * ntiles, 256);
+  L.err = off;
+  off = align_up(off + 16, 256);
+  L.results = off;
+  off = align_up(off + 64 * sizeof(double), 256);
+  L.scratch_doubles = maxtiles_level * 5 > maxpts / 256 + 1 ? maxtiles_level * 5 : maxpts / 256 + 1;
+  L.scratch = off;
+  off = align_up(off + L.scratch_doubles * sizeof(double), 256);
+  L.states = off;
+  L.patch_state.resize(npatches);
+  L.fstride.resize(npatches);
+  L.px.resize(npatches);
+  for (int p = 0; p < npatches; ++p) {
+    int NX = pd[p].n[0] + 2 * GH, NY = pd[p].n[1] + 2 * GH, NZ = pd[p].n[2] + 2 * GH;
+    int px = (int)align_up(NX, 8);
+    long long fs = (long long)px * NY * NZ;
+    L.px[p] = px;
+    L.fstride[p] = fs;
+    L.patch_state[p] = off;
+    off = align_up(off + (size_t)NBUF * NF * fs * sizeof(double), 256);
+  }
+  L.total = off;
+  return true;
+}
+
+}  // namespace
+
+struct sacrak_grid {
+  sacrak_params prm;
+  cudaStream_t stream;
+  char* arena;
+  size_t arena_bytes;
+  int nlevels, npatches;
+  double dx0;
+  Layout L;
+  std::vector<DevPatch> hp;                // host copy of the patch table
+  std::vector<std::vector<int>> lvl_ids;   // patch ids per level
+  std::vector<int> lvl_id_off;             // offset of each level's ids in the device id array
+  std::vector<size_t> lvl_tile_off, lvl_ntiles;
+  std::vector<long long> lvl_max_shell, lvl_max_restrict;
+  DevPatch* d_patches;
+  DevLevel* d_levels;
+  int* d_ids;
+  Tile* d_tiles;
+  unsigned* d_err;
+  double* d_results;
+  double* d_scratch;
+  bool invalid = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::string last_error;
+  // profiling of the fused stage kernel
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  size_t ev_used = 0;
+  long long prof_zones = 0;
+  std::vector<long long> lvl_zones;
+};
+
+namespace {
+
+sacrak_status fail(sacrak_grid* g, sacrak_status s, const char* fmt, ...) {
+  if (g) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g->last_error = buf;
+    if (s == SACRAK_ECUDA || s == SACRAK_ENONFINITE || s == SACRAK_ETIMEOUT) g->invalid = true;
+  }
+  return s;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(g, SACRAK_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));           \
+  } while (0)
+
+DevParams dev_params(const sacrak_params& p) {
+  DevParams d;
+  d.kappa1 = p.kappa1;
+  d.kappa2 = p.kappa2;
+  d.eta = p.eta;
+  d.sigma_ko = p.sigma_ko;
+  d.w_floor = p.w_floor;
+  d.lapse = p.lapse;
+  d.shift = p.shift;
+  d.lapse_uses_khat = p.lapse_uses_khat;
+  d.pad_ = 0;
+  return d;
+}
+
+double level_dt(const sacrak_grid* g, int l) { return g->prm.courant * g->dx0 / std::ldexp(1.0, l); }
+
+sacrak_status check_launch(sacrak_grid* g) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(g, SACRAK_ECUDA, "launch: %s", cudaGetErrorString(e));
+  return SACRAK_OK;
+}
+
+// read the device error flag (synchronises the stream)
+sacrak_status sync_and_check(sacrak_grid* g) {
+  unsigned flag = 0;
+  CK(cudaMemcpyAsync(&flag, g->d_err, sizeof flag, cudaMemcpyDeviceToHost, g->stream));
+  CK(cudaStreamSynchronize(g->stream));
+  if (flag & ERR_NONFINITE) return fail(g, SACRAK_ENONFINITE, "non-finite value in a stage update");
+  if (flag & ERR_TIMEOUT) return fail(g, SACRAK_ETIMEOUT, "bounded device wait ran out");
+  if (flag & ERR_BOUNDS) return fail(g, SACRAK_ECUDA, "device bounds check failed");
+  return SACRAK_OK;
+}
+
+void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones) {
+  if (g->prof) {
+    if (g->ev_used == g->ev.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> p;
+      cudaEventCreate(&p.first);
+      cudaEventCreate(&p.second);
+      g->ev.push_back(p);
+    }
+    cudaEventRecord(g->ev[g->ev_used].first, g->stream);
+  }
+#ifdef SACRAK_HAVE_MIXED
+  if (g->prm.precision == 1)
+    launch_stage_mixed(a, g->stream);
+  else
+#endif
+    launch_stage_fp64(a, g->stream);
+  if (g->prof) {
+    cudaEventRecord(g->ev[g->ev_used].second, g->stream);
+    g->ev_used++;
+    g->prof_zones += zones;
+  }
+}
+
+// Time weights of the parent's (oldest, middle, newest) levels for the ghost
+// data of child RK stage `stage` (1..4) of a child step that starts at
+// fraction s0 of the parent's last step and lasts ds: the parent's time
+// interpolant -- quadratic through s = -1, 0, 1 once three levels exist,
+// linear through s = 0, 1 before (Sec. 2.2.1) -- evaluated at the stage time
+// s0 + c_s ds, c = (0, 1/2, 1/2, 1).  stage 0 asks for s0 itself.
+void ghost_time_weights(double s0, double ds, int stage, double wq[3], double wl[3]) {
+  static const double cf[5] = {0.0, 0.0, 0.5, 0.5, 1.0};
+  const double s = s0 + cf[stage] * ds;
+  wq[0] = s * (s - 1.0) * 0.5;
+  wq[1] = (1.0 - s) * (1.0 + s);
+  wq[2] = s * (s + 1.0) * 0.5;
+  wl[0] = 0.0;
+  wl[1] = 1.0 - s;
+  wl[2] = s;
+}
+
+FillArgs fill_args(sacrak_grid* g, int l, int mode, int stage, double s0, double ds = 0.0) {
+  FillArgs a;
+  a.patches = g->d_patches;
+  a.patch_ids = g->d_ids + g->lvl_id_off[l];
+  a.lev = g->d_levels + l;
+  a.plev = l > 0 ? g->d_levels + (l - 1) : nullptr;
+  a.mode = mode;
+  a.stage = stage;
+  ghost_time_weights(s0, ds, mode == 0 ? stage : 0, a.wq, a.wl);
+  return a;
+}
+
+// ghost fill of level l for the buffer given by (mode, stage); for levels
+// > 0 the child step starts at fraction s0 of the parent step and lasts ds
+void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double ds) {
+  const int np = (int)g->lvl_ids[l].size();
+  if (l == 0) {
+    if (g->prm.bc == 1)
+      launch_fill(FILL_PERIODIC, fill_args(g, l, mode, stage, 0.0), np, g->lvl_max_shell[l], g->stream);
+    else if (g->prm.bc == 2)
+      launch_fill(FILL_FROZEN, fill_args(g, l, mode, stage, 0.0), np, g->lvl_max_shell[l], g->stream);
+    return;
+  }
+  launch_fill(FILL_PROLONG, fill_args(g, l, mode, stage, s0, ds), np, g->lvl_max_shell[l], g->stream);
+  // same-level exchange between every overlapping pair
+  const auto& ids = g->lvl_ids[l];
+  for (size_t a = 0; a < ids.size(); ++a)
+    for (size_t b = a + 1; b < ids.size(); ++b) {
+      const DevPatch& A = g->hp[ids[a]];
+      const DevPatch& B = g->hp[ids[b]];
+      int off[3];
+      bool touch = true;
+      for (int d = 0; d < 3; ++d) {
+        off[d] = (int)std::llround((A.origin[d] - B.origin[d]) / A.dx);
+        // index ranges incl. ghosts overlap?
+        int alo = -GH + off[d], ahi = A.n[d] + GH - 1 + off[d];
+        int blo = -GH, bhi = B.n[d] + GH - 1;
+        if (ahi < blo || bhi < alo) touch = false;
+      }
+      if (!touch) continue;
+      ExchArgs e;
+      e.patches = g->d_patches;
+      e.lev = g->d_levels + l;
+      e.a = ids[a];
+      e.b = ids[b];
+      for (int d = 0; d < 3; ++d) e.off[d] = off[d];
+      e.mode = mode;
+      e.stage = stage;
+      launch_exchange(e, (long long)A.NX * A.NY * A.NZ, g->stream);
+    }
+}
+
+void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
+  const int np = (int)g->lvl_ids[l].size();
+  for (int s = 1; s <= 4; ++s) {
+    if (!(l == 0 && (g->prm.bc == 0 || (g->prm.bc == 2 && s == 1))))
+      fill_ghosts(g, l, 0, s, frac0, dfrac);
+    StageArgs a;
+    a.tiles = g->d_tiles + g->lvl_tile_off[l];
+    a.ntiles = (int)g->lvl_ntiles[l];
+    a.patches = g->d_patches;
+    a.lev = g->d_levels + l;
+    a.stage = s;
+    a.dt = dt;
+    a.prm = dev_params(g->prm);
+    a.err = g->d_err;
+    launch_stage(g, a, g->lvl_zones[l]);
+    if (l == 0 && g->prm.bc == 0) {
+      GhostArgs ga;
+      ga.patches = g->d_patches;
+      ga.patch_ids = g->d_ids + g->lvl_id_off[l];
+      ga.lev = g->d_levels + l;
+      ga.stage = s;
+      ga.dt = dt;
+      ga.prm = a.prm;
+      ga.err = g->d_err;
+      launch_sommerfeld(ga, np, g->lvl_max_shell[l], g->stream);
+    }
+  }
+  // ghosts of the new time level for periodic / frozen outer boundaries
+  if (l == 0 && g->prm.bc == 1)
+    launch_fill(FILL_PERIODIC, fill_args(g, l, 2, 4, 0.0), np, g->lvl_max_shell[l], g->stream);
+  if (l == 0 && g->prm.bc == 2)
+    launch_fill(FILL_FROZEN, fill_args(g, l, 2, 4, 0.0), np, g->lvl_max_shell[l], g->stream);
+  launch_level_advance(g->d_levels + l, dt, g->stream);
+}
+
+void level_step_rec(sacrak_grid* g, int l, double frac0, double dfrac) {
+  rk4_level(g, l, level_dt(g, l), frac0, dfrac);
+  if (l + 1 < g->nlevels) {
+    level_step_rec(g, l + 1, 0.0, 0.5);
+    level_step_rec(g, l + 1, 0.5, 0.5);
+    const int nc = (int)g->lvl_ids[l + 1].size();
+    fill_ghosts(g, l + 1, 1, 0, 1.0, 0.0);  // prolongation (unrestricted parent) + exchange
+    launch_fill(FILL_RESTRICT, fill_args(g, l + 1, 1, 0, 0.0), nc, g->lvl_max_restrict[l + 1],
+                g->stream);
+  }
+}
+
+sacrak_status reset_levels(sacrak_grid* g) {
+  std::vector<DevLevel> lv(g->nlevels);
+  for (auto& x : lv) {
+    x.ring = 0;
+    x.nvalid = 1;
+    x.steps = 0;
+    x.pad_ = 0;
+    x.t = 0.0;
+  }
+  CK(cudaMemcpyAsync(g->d_levels, lv.data(), sizeof(DevLevel) * g->nlevels, cudaMemcpyHostToDevice,
+                     g->stream));
+  CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), g->stream));
+  g->invalid = false;
+  return SACRAK_OK;
+}
+
+sacrak_status read_level(sacrak_grid* g, int l, DevLevel* out) {
+  CK(cudaMemcpyAsync(out, g->d_levels + l, sizeof(DevLevel), cudaMemcpyDeviceToHost, g->stream));
+  CK(cudaStreamSynchronize(g->stream));
+  return SACRAK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* patches) {
+  Layout L;
+  std::string why;
+  if (!describe(nlevels, npatches, patches, L, why)) return 0;
+  return L.total;
+}
+
+sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
+                                 const sacrak_patch_desc* pd, const sacrak_params* params,
+                                 void* cuda_stream, void* device_arena, size_t arena_bytes,
+                                 sacrak_grid** out) {
+  if (!out || !params || !device_arena || !(dx0 > 0.0)) return SACRAK_EINVAL;
+  *out = nullptr;
+  Layout L;
+  std::string why;
+  if (!describe(nlevels, npatches, pd, L, why)) return SACRAK_EINVAL;
+  if (arena_bytes < L.total || ((uintptr_t)device_arena % 256) != 0) return SACRAK_EINVAL;
+  const sacrak_params& p = *params;
+  if (p.lapse < 0 || p.lapse > 1 || p.shift < 0 || p.shift > 1 || p.bc < 0 || p.bc > 2 ||
+      p.precision < 0 || p.precision > 1 || !(p.courant > 0.0) || !(p.sigma_ko >= 0.0))
+    return SACRAK_EINVAL;
+#ifndef SACRAK_HAVE_MIXED
+  if (p.precision == 1) return SACRAK_EINVAL;
+#endif
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, device_arena) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return SACRAK_EINVAL;
+  }
+
+  sacrak_grid* g = new sacrak_grid();
+  g->prm = p;
+  g->stream = (cudaStream_t)cuda_stream;
+  g->arena = (char*)device_arena;
+  g->arena_bytes = arena_bytes;
+  g->nlevels = nlevels;
+  g->npatches = npatches;
+  g->dx0 = dx0;
+  g->L = L;
+  g->hp.resize(npatches);
+  g->lvl_ids.assign(nlevels, {});
+  for (int i = 0; i < npatches; ++i) {
+    DevPatch& P = g->hp[i];
+    std::memset(&P, 0, sizeof P);
+    for (int d = 0; d < 3; ++d) {
+      P.n[d] = pd[i].n[d];
+      P.origin[d] = pd[i].origin[d];
+    }
+    P.NX = P.n[0] + 2 * GH;
+    P.NY = P.n[1] + 2 * GH;
+    P.NZ = P.n[2] + 2 * GH;
+    P.px = L.px[i];
+    P.plane = (long long)P.px * P.NY;
+    P.fstride = L.fstride[i];
+    P.level = pd[i].level;
+    P.dx = dx0 / std::ldexp(1.0, P.level);
+    P.parent = -1;
+    for (int b = 0; b < NBUF; ++b)
+      P.buf[b] = (double*)(g->arena + L.patch_state[i] + (size_t)b * NF * P.fstride * sizeof(double));
+    g->lvl_ids[P.level].push_back(i);
+  }
+  // parents: the patch of the level above containing the child with margin
+  for (int i = 0; i < npatches; ++i) {
+    DevPatch& C = g->hp[i];
+    if (C.level == 0) continue;
+    for (int d = 0; d < 3; ++d)
+      if (C.n[d] % 2) {
+        delete g;
+        return SACRAK_EINVAL;
+      }
+    for (int j : g->lvl_ids[C.level - 1]) {
+      const DevPatch& P = g->hp[j];
+      bool ok = true;
+      int off[3];
+      for (int d = 0; d < 3; ++d) {
+        double t = (C.origin[d] - P.origin[d]) / P.dx;
+        double r = std::floor(t + 0.5);
+        if (std::fabs(t - r) > 1e-9) ok = false;
+        off[d] = (int)r;
+        // prolongation stencils need parent cells off-4 .. off+n/2+3 inside the active region
+        if (off[d] - 4 < 0 || off[d] + C.n[d] / 2 + 3 > P.n[d] - 1) ok = false;
+      }
+      if (ok) {
+        C.parent = j;
+        for (int d = 0; d < 3; ++d) C.off[d] = off[d];
+        break;
+      }
+    }
+    if (C.parent < 0) {
+      delete g;
+      return SACRAK_EINVAL;
+    }
+  }
+  // Sommerfeld ghosts use one-sided differences toward the origin: the
+  // origin must lie inside every level-0 patch so that they stay in the array
+  if (p.bc == 0)
+    for (int i : g->lvl_ids[0])
+      for (int d = 0; d < 3; ++d) {
+        const DevPatch& P = g->hp[i];
+        if (!(P.origin[d] < 0.0 && P.origin[d] + P.n[d] * P.dx > 0.0)) {
+          delete g;
+          return SACRAK_EINVAL;
+        }
+      }
+  g->d_patches = (DevPatch*)(g->arena + L.patches);
+  g->d_levels = (DevLevel*)(g->arena + L.levels);
+  g->d_ids = (int*)(g->arena + L.ids);
+  g->d_tiles = (Tile*)(g->arena + L.tiles);
+  g->d_err = (unsigned*)(g->arena + L.err);
+  g->d_results = (double*)(g->arena + L.results);
+  g->d_scratch = (double*)(g->arena + L.scratch);
+  std::vector<int> ids;
+  std::vector<Tile> tiles;
+  g->lvl_id_off.resize(nlevels);
+  g->lvl_tile_off.resize(nlevels);
+  g->lvl_ntiles.resize(nlevels);
+  g->lvl_max_shell.assign(nlevels, 0);
+  g->lvl_zones.assign(nlevels, 0);
+  g->lvl_max_restrict.assign(nlevels, 0);
+  for (int l = 0; l < nlevels; ++l) {
+    g->lvl_id_off[l] = (int)ids.size();
+    g->lvl_tile_off[l] = tiles.size();
+    for (int pid : g->lvl_ids[l]) {
+      ids.push_back(pid);
+      const DevPatch& P = g->hp[pid];
+      for (int z = 0; z < P.n[2]; ++z)
+        for (int y = 0; y < P.n[1]; y += TILE_Y)
+          for (int x = 0; x < P.n[0]; x += TILE_X) tiles.push_back(Tile{pid, x, y, z});
+      long long sh = (long long)P.NX * P.NY * P.NZ - (long long)P.n[0] * P.n[1] * P.n[2];
+      if (sh > g->lvl_max_shell[l]) g->lvl_max_shell[l] = sh;
+      g->lvl_zones[l] += (long long)P.n[0] * P.n[1] * P.n[2];
+      long long rs = (long long)(P.n[0] / 2) * (P.n[1] / 2) * (P.n[2] / 2);
+      if (rs > g->lvl_max_restrict[l]) g->lvl_max_restrict[l] = rs;
+    }
+    g->lvl_ntiles[l] = tiles.size() - g->lvl_tile_off[l];
+  }
+  cudaStream_t s = g->stream;
+  sacrak_status st = SACRAK_OK;
+  if (cudaMemcpyAsync(g->d_patches, g->hp.data(), sizeof(DevPatch) * npatches,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(g->d_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(g->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess)
+    st = SACRAK_ECUDA;
+  if (st == SACRAK_OK) st = reset_levels(g);
+  if (st == SACRAK_OK) {
+    // tables must be on the device before the host vectors go away
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = SACRAK_ECUDA;
+  }
+  if (st == SACRAK_OK) st = sacrak_set_initial_data(g, 0, 0, nullptr, nullptr, 0, 1, 0, 0, 0);
+  if (st != SACRAK_OK) {
+    cudaGetLastError();
+    delete g;
+    return st;
+  }
+  *out = g;
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_grid_destroy(sacrak_grid* g) {
+  if (!g) return SACRAK_EINVAL;
+  for (auto& p : g->ev) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_set_initial_data(sacrak_grid* g, int kind, int npunct, const double* m,
+                                      const double* pos, double gw_amp, double gw_len,
+                                      double noise_amp, uint64_t seed, int symmetrise_pi) {
+  if (!g) return SACRAK_EINVAL;
+  if (kind < 0 || kind > 2 || npunct < 0 || npunct > 8 || (kind == 1 && (!m || !pos)) ||
+      (kind == 2 && !(gw_len > 0.0)) || !(noise_amp >= 0.0))
+    return fail(g, SACRAK_EINVAL, "invalid initial-data arguments");
+  if (symmetrise_pi) {
+    for (const DevPatch& P : g->hp)
+      for (int d = 0; d < 2; ++d)
+        if (std::fabs(P.origin[d] + 0.5 * P.n[d] * P.dx) > 1e-12 * P.dx)
+          return fail(g, SACRAK_EINVAL, "pi symmetrisation needs patches centred on x = y = 0");
+  }
+  sacrak_status st = reset_levels(g);
+  if (st != SACRAK_OK) return st;
+  InitArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.patches = g->d_patches;
+  a.levels = g->d_levels;
+  a.kind = kind;
+  a.npunct = kind == 1 ? npunct : 0;
+  for (int i = 0; i < a.npunct; ++i) {
+    a.m[i] = m[i];
+    for (int d = 0; d < 3; ++d) a.pos[3 * i + d] = pos[3 * i + d];
+  }
+  a.gw_amp = gw_amp;
+  a.gw_len = gw_len;
+  a.noise_amp = noise_amp;
+  a.seed = seed;
+  for (int d = 0; d < 3; ++d) a.lo[d] = g->hp[g->lvl_ids[0][0]].origin[d];
+  for (int p = 0; p < g->npatches; ++p) {
+    const DevPatch& P = g->hp[p];
+    launch_init(a, p, (long long)P.NX * P.NY * P.NZ, g->stream);
+    if (symmetrise_pi) launch_symmetrise(g->d_patches, g->d_levels, p, (long long)(P.NX / 2) * P.NY * P.NZ, g->stream);
+  }
+  return check_launch(g);
+}
+
+static sacrak_status copy_patch(sacrak_grid* g, int patch, double* dst_dev_slot, const double* src,
+                                double* dst, bool upload) {
+  const DevPatch& P = g->hp[patch];
+  size_t width = (size_t)P.NX * sizeof(double);
+  size_t rows = (size_t)NF * P.NY * P.NZ;
+  if (upload)
+    CK(cudaMemcpy2DAsync(dst_dev_slot, P.px * sizeof(double), src, width, width, rows,
+                         cudaMemcpyDefault, g->stream));
+  else
+    CK(cudaMemcpy2DAsync(dst, width, dst_dev_slot, P.px * sizeof(double), width, rows,
+                         cudaMemcpyDefault, g->stream));
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_upload_fields(sacrak_grid* g, int patch, const double* src) {
+  if (!g) return SACRAK_EINVAL;
+  if (patch < 0 || patch >= g->npatches || !src) return fail(g, SACRAK_EINVAL, "bad patch or pointer");
+  const DevPatch& P = g->hp[patch];
+  DevLevel lv;
+  sacrak_status st = read_level(g, P.level, &lv);
+  if (st != SACRAK_OK) return st;
+  st = copy_patch(g, patch, P.buf[lv.ring], src, nullptr, true);
+  if (st != SACRAK_OK) return st;
+  lv.nvalid = 1;
+  CK(cudaMemcpyAsync(&g->d_levels[P.level], &lv, sizeof lv, cudaMemcpyHostToDevice, g->stream));
+  CK(cudaStreamSynchronize(g->stream));  // lv is a host stack variable
+  g->invalid = false;
+  CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), g->stream));
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_download_fields(sacrak_grid* g, int patch, double* dst) {
+  if (!g) return SACRAK_EINVAL;
+  if (patch < 0 || patch >= g->npatches || !dst) return fail(g, SACRAK_EINVAL, "bad patch or pointer");
+  const DevPatch& P = g->hp[patch];
+  DevLevel lv;
+  sacrak_status st = read_level(g, P.level, &lv);
+  if (st != SACRAK_OK) return st;
+  st = copy_patch(g, patch, P.buf[lv.ring], nullptr, dst, false);
+  if (st != SACRAK_OK) return st;
+  return sync_and_check(g);
+}
+
+sacrak_status sacrak_rhs(sacrak_grid* g, int patch, double* dst) {
+  if (!g) return SACRAK_EINVAL;
+  if (patch < 0 || patch >= g->npatches || !dst) return fail(g, SACRAK_EINVAL, "bad patch or pointer");
+  if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
+  const DevPatch& P = g->hp[patch];
+  CK(cudaMemsetAsync(P.buf[B_S1], 0, (size_t)NF * P.fstride * sizeof(double), g->stream));
+  // launch over this patch's tiles only
+  const int l = P.level;
+  size_t first = g->lvl_tile_off[l], count = 0;
+  {
+    size_t acc = 0;
+    for (int pid : g->lvl_ids[l]) {
+      const DevPatch& Q = g->hp[pid];
+      size_t t = (size_t)((Q.n[0] + TILE_X - 1) / TILE_X) * ((Q.n[1] + TILE_Y - 1) / TILE_Y) * Q.n[2];
+      if (pid == patch) {
+        first += acc;
+        count = t;
+        break;
+      }
+      acc += t;
+    }
+  }
+  StageArgs a;
+  a.tiles = g->d_tiles + first;
+  a.ntiles = (int)count;
+  a.patches = g->d_patches;
+  a.lev = g->d_levels + l;
+  a.stage = 0;
+  a.dt = 0.0;
+  a.prm = dev_params(g->prm);
+  a.err = g->d_err;
+  launch_stage(g, a, (long long)P.n[0] * P.n[1] * P.n[2]);
+  sacrak_status st = check_launch(g);
+  if (st != SACRAK_OK) return st;
+  st = copy_patch(g, patch, P.buf[B_S1], nullptr, dst, false);
+  if (st != SACRAK_OK) return st;
+  return sync_and_check(g);
+}
+
+sacrak_status sacrak_rk4_step(sacrak_grid* g, int level, double dt) {
+  if (!g) return SACRAK_EINVAL;
+  if (level < 0 || level >= g->nlevels) return fail(g, SACRAK_EINVAL, "bad level");
+  if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
+  rk4_level(g, level, dt > 0.0 ? dt : level_dt(g, level), 0.0, 0.5);
+  return check_launch(g);
+}
+
+sacrak_status sacrak_level_step(sacrak_grid* g, int level) {
+  if (!g) return SACRAK_EINVAL;
+  if (level < 0 || level >= g->nlevels) return fail(g, SACRAK_EINVAL, "bad level");
+  if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
+  if (level > 0 || g->stream == nullptr || g->prof) {
+    level_step_rec(g, level, 0.0, 0.5);
+    return check_launch(g);
+  }
+  if (!g->graph_exec) {
+    cudaStreamCaptureStatus cs;
+    CK(cudaStreamIsCapturing(g->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {  // caller is capturing: just record launches
+      level_step_rec(g, 0, 0.0, 1.0);
+      return check_launch(g);
+    }
+    CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    level_step_rec(g, 0, 0.0, 1.0);
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+    if (e != cudaSuccess) return fail(g, SACRAK_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&g->graph_exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return fail(g, SACRAK_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    g->graph = graph;
+  }
+  CK(cudaGraphLaunch(g->graph_exec, g->stream));
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_constraints(sacrak_grid* g, int level, double w_excise, double out_l2[4]) {
+  if (!g) return SACRAK_EINVAL;
+  if (level < 0 || level >= g->nlevels || !out_l2) return fail(g, SACRAK_EINVAL, "bad arguments");
+  ConsArgs a;
+  a.tiles = g->d_tiles + g->lvl_tile_off[level];
+  a.patches = g->d_patches;
+  a.lev = g->d_levels + level;
+  a.w_excise = w_excise;
+  a.partial = g->d_scratch;
+  launch_constraints(a, (int)g->lvl_ntiles[level], g->d_results, g->stream);
+  sacrak_status st = check_launch(g);
+  if (st != SACRAK_OK) return st;
+  double sums[5];
+  CK(cudaMemcpyAsync(sums, g->d_results, sizeof sums, cudaMemcpyDeviceToHost, g->stream));
+  st = sync_and_check(g);
+  if (st != SACRAK_OK) return st;
+  for (int c = 0; c < 4; ++c) out_l2[c] = sums[4] > 0 ? std::sqrt(sums[c] / sums[4]) : 0.0;
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_pi_symmetry(sacrak_grid* g, int patch, double* out) {
+  if (!g) return SACRAK_EINVAL;
+  if (patch < 0 || patch >= g->npatches || !out) return fail(g, SACRAK_EINVAL, "bad arguments");
+  const DevPatch& P = g->hp[patch];
+  for (int d = 0; d < 2; ++d)
+    if (std::fabs(P.origin[d] + 0.5 * P.n[d] * P.dx) > 1e-12 * P.dx)
+      return fail(g, SACRAK_EINVAL, "patch not centred on x = y = 0");
+  launch_pi_symmetry(g->d_patches, g->d_levels, patch, (long long)P.NX * P.NY * P.NZ, g->d_scratch,
+                     g->d_results, g->stream);
+  sacrak_status st = check_launch(g);
+  if (st != SACRAK_OK) return st;
+  double v;
+  CK(cudaMemcpyAsync(&v, g->d_results, sizeof v, cudaMemcpyDeviceToHost, g->stream));
+  st = sync_and_check(g);
+  if (st != SACRAK_OK) return st;
+  *out = v;
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_profile_enable(sacrak_grid* g, int enable) {
+  if (!g) return SACRAK_EINVAL;
+  g->prof = enable != 0;
+  g->ev_used = 0;
+  g->prof_zones = 0;
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_profile_read(sacrak_grid* g, double* ms, long long* launches, long long* zones) {
+  if (!g || !ms || !launches || !zones) return SACRAK_EINVAL;
+  CK(cudaStreamSynchronize(g->stream));
+  double tot = 0.0;
+  for (size_t i = 0; i < g->ev_used; ++i) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, g->ev[i].first, g->ev[i].second));
+    tot += t;
+  }
+  *ms = tot;
+  *launches = (long long)g->ev_used;
+  *zones = g->prof_zones;
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_level_time(sacrak_grid* g, int level, double* t) {
+  if (!g) return SACRAK_EINVAL;
+  if (level < 0 || level >= g->nlevels || !t) return fail(g, SACRAK_EINVAL, "bad arguments");
+  DevLevel lv;
+  sacrak_status st = read_level(g, level, &lv);
+  if (st != SACRAK_OK) return st;
+  *t = lv.t;
+  return SACRAK_OK;
+}
+
+const char* sacrak_last_error(const sacrak_grid* g) { return g ? g->last_error.c_str() : "null grid"; }
+
+}  // extern "C"

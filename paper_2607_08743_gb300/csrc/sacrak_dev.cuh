@@ -1,0 +1,266 @@
+// Device-side data structures and finite-difference helpers shared by the
+// kernels of the GB300 Z4c hot path.
+//
+// Memory layout (HBM): every patch owns six state copies (three time levels,
+// the RK4 accumulator y and two stage buffers).  A state copy is
+// double[25][NZ][NY][px]: x fastest, the row pitch px rounded up to 8 doubles
+// (64 B) so that every row starts on a 64-byte boundary, and every field
+// padded to a multiple of 32 doubles (256 B).  Ghost width is 3 on every side.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sacrak {
+
+constexpr int NF = 25;
+constexpr int GH = 3;
+constexpr int NBUF = 6;
+
+enum Field {
+  F_W = 0, F_GXX, F_GXY, F_GXZ, F_GYY, F_GYZ, F_GZZ, F_KH, F_TH,
+  F_AXX, F_AXY, F_AXZ, F_AYY, F_AYZ, F_AZZ, F_GAMX, F_GAMY, F_GAMZ,
+  F_ALP, F_BETX, F_BETY, F_BETZ, F_BX, F_BY, F_BZ
+};
+
+// buffer slots of a patch
+enum { B_TL0 = 0, B_TL1 = 1, B_TL2 = 2, B_Y = 3, B_S0 = 4, B_S1 = 5 };
+
+struct DevPatch {
+  int n[3];          // active cells
+  int NX, NY, NZ;    // extents incl. ghosts
+  int px;            // row pitch in doubles
+  int level;
+  int parent;        // parent patch index, -1 on level 0
+  int off[3];        // this patch's origin in parent cell units
+  int pad_;
+  long long plane;   // px * NY
+  long long fstride; // doubles between consecutive fields
+  double dx;
+  double origin[3];
+  double* buf[NBUF];
+};
+
+struct DevLevel {
+  int ring;    // slot of the current time level
+  int nvalid;  // valid time levels (1..3)
+  int steps;
+  int pad_;
+  double t;    // time of the current time level
+};
+
+struct Tile {
+  int patch;
+  int x0, y0, z0;
+};
+
+struct DevParams {
+  double kappa1, kappa2, eta, sigma_ko, w_floor;
+  int lapse, shift, lapse_uses_khat, pad_;
+};
+
+// error flags written by kernels (bitmask), read by the host after a sync
+enum { ERR_NONFINITE = 1, ERR_BOUNDS = 2, ERR_TIMEOUT = 4 };
+
+// pi-rotation parity of each field (x,y -> -x,-y)
+__host__ __device__ inline int pi_parity(int f) {
+  // W gt(xx xy xz yy yz zz) Khat Theta At(..) Gamt(x y z) alpha beta(x y z) B(x y z)
+  const unsigned odd_mask = (1u << F_GXZ) | (1u << F_GYZ) | (1u << F_AXZ) | (1u << F_AYZ) |
+                            (1u << F_GAMX) | (1u << F_GAMY) | (1u << F_BETX) |
+                            (1u << F_BETY) | (1u << F_BX) | (1u << F_BY);
+  return (odd_mask >> f) & 1u ? -1 : 1;
+}
+
+__host__ __device__ inline double flat_value(int f) {
+  return (f == F_W || f == F_GXX || f == F_GYY || f == F_GZZ || f == F_ALP) ? 1.0 : 0.0;
+}
+
+// symmetric index (i,j) -> 0..5 (xx,xy,xz,yy,yz,zz)
+__host__ __device__ constexpr int S2(int i, int j) {
+  return (i == j) ? (i == 0 ? 0 : (i == 1 ? 3 : 5))
+                  : ((i + j) == 1 ? 1 : ((i + j) == 2 ? 2 : 4));
+}
+
+// slot of the stage input / output buffer for RK4 stage s (1..4)
+__host__ __device__ inline int stage_in_slot(int s, int ring) {
+  return s == 1 ? ring : (s == 3 ? B_S1 : B_S0);
+}
+__host__ __device__ inline int stage_out_slot(int s, int ring) {
+  return s == 4 ? (ring + 1) % 3 : (s == 2 ? B_S1 : B_S0);
+}
+
+// ---------------------------------------------------------------------------
+// Finite-difference operators on a field pointer f at linear offset q with
+// stride st.  The pair forms (f+ - f-) and (f+ + f-) make every operator
+// exactly antisymmetric/symmetric under mirroring, which keeps pi symmetry
+// bitwise for any contraction pattern the compiler picks.
+
+// 4th-order centred first derivative, unscaled: 8 (f1 - f-1) - (f2 - f-2);
+// multiply by 1/(12 h).
+__device__ __forceinline__ double d1u(const double* __restrict__ f, long long q, long long st) {
+  double a = __ldg(f + q + st) - __ldg(f + q - st);
+  double b = __ldg(f + q + 2 * st) - __ldg(f + q - 2 * st);
+  return 8.0 * a - b;
+}
+
+// The stencils whose coefficients sum to zero are evaluated on differences
+// from the centre value, f_k - f_0, so that they round relative to the result
+// rather than to the field value.
+
+// 4th-order centred second derivative, unscaled:
+// 16 (f1 + f-1) - (f2 + f-2) - 30 f0; multiply by 1/(12 h^2).
+__device__ __forceinline__ double d2u(const double* __restrict__ f, long long q, long long st,
+                                      double f0) {
+  double a = (__ldg(f + q + st) - f0) + (__ldg(f + q - st) - f0);
+  double b = (__ldg(f + q + 2 * st) - f0) + (__ldg(f + q - 2 * st) - f0);
+  return 16.0 * a - b;
+}
+
+// nested mixed derivative D_a(D_b f), unscaled; multiply by 1/(144 h^2).
+__device__ __forceinline__ double d11u(const double* __restrict__ f, long long q, long long sa,
+                                       long long sb) {
+  double p1 = d1u(f, q + sa, sb), m1 = d1u(f, q - sa, sb);
+  double p2 = d1u(f, q + 2 * sa, sb), m2 = d1u(f, q - 2 * sa, sb);
+  return 8.0 * (p1 - m1) - (p2 - m2);
+}
+
+// lopsided upwind derivative (one point behind, three ahead along the side
+// the shift points to), unscaled: (-3 f-s - 10 f0 + 18 fs - 6 f2s + f3s) * s;
+// multiply by 1/(12 h).  The mirrored case is the same expression on mirrored
+// points, negated.
+__device__ __forceinline__ double dupu(const double* __restrict__ f, long long q, long long st,
+                                       double b, double f0) {
+  long long s = b > 0.0 ? st : -st;
+  double v = -3.0 * (__ldg(f + q - s) - f0) + 18.0 * (__ldg(f + q + s) - f0) -
+             6.0 * (__ldg(f + q + 2 * s) - f0) + (__ldg(f + q + 3 * s) - f0);
+  return b > 0.0 ? v : -v;
+}
+
+// 6th difference along st (Kreiss-Oliger stencil)
+__device__ __forceinline__ double delta6(const double* __restrict__ f, long long q, long long st,
+                                         double f0) {
+  double a = (__ldg(f + q + 3 * st) - f0) + (__ldg(f + q - 3 * st) - f0);
+  double b = (__ldg(f + q + 2 * st) - f0) + (__ldg(f + q - 2 * st) - f0);
+  double c = (__ldg(f + q + st) - f0) + (__ldg(f + q - st) - f0);
+  return (a - 6.0 * b) + 15.0 * c;
+}
+
+// Kernel argument bundles ----------------------------------------------------
+
+// linear ghost-shell index -> (i,j,k) array indices (ghosts included): two z
+// slabs, then two y slabs over the middle z range, then two x slabs
+__device__ __forceinline__ void shell_ijk(long long id, int NX, int NY, int NZ, int& i, int& j,
+                                          int& k) {
+  const long long zslab = (long long)GH * NY * NX;
+  const int nz = NZ - 2 * GH, ny = NY - 2 * GH;
+  const long long yslab = (long long)GH * NX * nz;
+  if (id < 2 * zslab) {
+    int side = id >= zslab;
+    long long r = id - side * zslab;
+    i = (int)(r % NX);
+    r /= NX;
+    j = (int)(r % NY);
+    k = (int)(r / NY) + (side ? NZ - GH : 0);
+    return;
+  }
+  id -= 2 * zslab;
+  if (id < 2 * yslab) {
+    int side = id >= yslab;
+    long long r = id - side * yslab;
+    i = (int)(r % NX);
+    r /= NX;
+    j = (int)(r % GH) + (side ? NY - GH : 0);
+    k = (int)(r / GH) + GH;
+    return;
+  }
+  id -= 2 * yslab;
+  const long long xslab = (long long)GH * ny * nz;
+  int side = id >= xslab;
+  long long r = id - side * xslab;
+  i = (int)(r % GH) + (side ? NX - GH : 0);
+  r /= GH;
+  j = (int)(r % ny) + GH;
+  k = (int)(r / ny) + GH;
+}
+
+__host__ __device__ inline long long shell_count(int NX, int NY, int NZ) {
+  return (long long)NX * NY * NZ - (long long)(NX - 2 * GH) * (NY - 2 * GH) * (NZ - 2 * GH);
+}
+
+struct StageArgs {
+  const Tile* tiles;
+  int ntiles;
+  const DevPatch* patches;
+  const DevLevel* lev;  // the level being stepped
+  int stage;            // 1..4; 0 = write the RHS into S1 (no RK update)
+  double dt;
+  DevParams prm;
+  unsigned* err;
+};
+
+struct GhostArgs {
+  const DevPatch* patches;
+  const int* patch_ids;  // patches of the level
+  const DevLevel* lev;
+  int stage;
+  double dt;
+  DevParams prm;
+  unsigned* err;
+};
+
+struct ConsArgs {
+  const Tile* tiles;
+  const DevPatch* patches;
+  const DevLevel* lev;
+  double w_excise;
+  double* partial;  // [ntiles][5]
+};
+
+// ghost fills: mode 0 = stage input of stage s, 1 = current time level,
+// 2 = next time level
+struct FillArgs {
+  const DevPatch* patches;
+  const int* patch_ids;
+  const DevLevel* lev;   // level of the patches being filled
+  const DevLevel* plev;  // parent level (prolongation / restriction)
+  int mode, stage;
+  // prolongation: weights of the parent's (oldest, middle, newest) time levels,
+  // for three valid levels (wq) and for two (wl, oldest weight 0)
+  double wq[3], wl[3];
+};
+
+struct ExchArgs {
+  const DevPatch* patches;
+  const DevLevel* lev;
+  int a, b;
+  int off[3];  // b's cell index of a's cell 0
+  int mode, stage;
+};
+
+struct InitArgs {
+  const DevPatch* patches;
+  const DevLevel* levels;
+  int kind;  // 0 Minkowski, 1 punctures, 2 gauge wave
+  int npunct;
+  double m[8];
+  double pos[24];
+  double gw_amp, gw_len;
+  double noise_amp;
+  uint64_t seed;
+  double lo[3];  // level-0 origin (origin of level-global cell indices)
+};
+
+// launchers (host)
+void launch_stage_fp64(const StageArgs& a, cudaStream_t st);
+void launch_stage_mixed(const StageArgs& a, cudaStream_t st);
+void launch_sommerfeld(const GhostArgs& a, int npatches, long long max_shell, cudaStream_t st);
+void launch_constraints(const ConsArgs& a, int ntiles, double* out5, cudaStream_t st);
+void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cudaStream_t st);
+void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st);
+void launch_level_advance(DevLevel* L, double dt, cudaStream_t st);
+void launch_init(const InitArgs& a, int patch, long long tot, cudaStream_t st);
+void launch_symmetrise(const DevPatch* p, const DevLevel* l, int patch, long long half_tot,
+                       cudaStream_t st);
+int launch_pi_symmetry(const DevPatch* p, const DevLevel* l, int patch, long long tot,
+                       double* partial, double* out, cudaStream_t st);
+
+}  // namespace sacrak

@@ -1,0 +1,596 @@
+// FP64 Z4c right-hand side fused with the classical RK4 stage update and the
+// algebraic constraints (Sec. 2.1.1, 2.2 of the SACRA-K paper), plus the
+// Hamiltonian / momentum constraint monitor (Sec. 2.3).
+//
+// One thread per active point.  The FP64 pipe of GB300 (measured about
+// 1 TFLOP/s, 1/74 of FP32) bounds this path, so the code is written to keep
+// the FP64 instruction count low: unscaled stencil sums multiplied once by
+// 1/(12h) or 1/(144h^2), contractions of the Christoffel symbols through the
+// partially raised symbol X[j][k][l] = gt^lm Gt_jkm, and second derivatives
+// of gt consumed into the Ricci tensor as they are formed.
+#include "sacrak_dev.cuh"
+
+namespace sacrak {
+
+struct PointState {
+  double W, gt[6], Kh, Th, At[6], Gam[3], al, be[3], Bv[3];
+};
+
+__device__ __forceinline__ void load_centre(const double* __restrict__ u, long long q,
+                                            long long fs, PointState& c) {
+  c.W = __ldg(u + F_W * fs + q);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    c.gt[a] = __ldg(u + (F_GXX + a) * fs + q);
+    c.At[a] = __ldg(u + (F_AXX + a) * fs + q);
+  }
+  c.Kh = __ldg(u + F_KH * fs + q);
+  c.Th = __ldg(u + F_TH * fs + q);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    c.Gam[i] = __ldg(u + (F_GAMX + i) * fs + q);
+    c.be[i] = __ldg(u + (F_BETX + i) * fs + q);
+    c.Bv[i] = __ldg(u + (F_BX + i) * fs + q);
+  }
+  c.al = __ldg(u + F_ALP * fs + q);
+}
+
+// inverse of a symmetric 3x3 matrix
+__device__ __forceinline__ void sym_inv(const double g[6], double gu[6]) {
+  double c0 = g[3] * g[5] - g[4] * g[4];
+  double c1 = g[2] * g[4] - g[1] * g[5];
+  double c2 = g[1] * g[4] - g[2] * g[3];
+  double det = g[0] * c0 + g[1] * c1 + g[2] * c2;
+  double id = 1.0 / det;
+  gu[0] = c0 * id;
+  gu[1] = c1 * id;
+  gu[2] = c2 * id;
+  gu[3] = (g[0] * g[5] - g[2] * g[2]) * id;
+  gu[4] = (g[1] * g[2] - g[0] * g[4]) * id;
+  gu[5] = (g[0] * g[3] - g[1] * g[1]) * id;
+}
+
+// sum_{l,m} S^{lm} T_{lm} of two symmetric tensors
+__device__ __forceinline__ double sym_contract(const double S[6], const double T[6]) {
+  return S[0] * T[0] + S[3] * T[3] + S[5] * T[5] + 2.0 * (S[1] * T[1] + S[2] * T[2] + S[4] * T[4]);
+}
+
+// Geometry shared by the RHS and the constraint monitor.
+struct Geo {
+  double gtu[6];
+  double dW[3], dal[3];
+  double Gu[3][6];    // Gt^i_jk
+  double Gd[3];       // Gamd^i
+  double Ric[6];      // R_ij
+  double DDa[6];      // D_i D_j alpha (physical)
+  double Lapa;        // D^i D_i alpha
+  double Rsc;         // R
+};
+
+__device__ __forceinline__ void geometry(const double* __restrict__ u, long long q,
+                                         const long long st[3], long long fs, double c1,
+                                         double c2, double c11, const PointState& c, Geo& G,
+                                         double dGam[3][3], double dbe[3][3]) {
+  sym_inv(c.gt, G.gtu);
+  const double* gtu = G.gtu;
+
+  // first derivatives of gt -> Christoffel symbols of the first kind
+  double dgt[3][6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) dgt[d][a] = d1u(u + (F_GXX + a) * fs, q, st[d]) * c1;
+    G.dW[d] = d1u(u + F_W * fs, q, st[d]) * c1;
+    G.dal[d] = d1u(u + F_ALP * fs, q, st[d]) * c1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dGam[d][i] = d1u(u + (F_GAMX + i) * fs, q, st[d]) * c1;
+      dbe[d][i] = d1u(u + (F_BETX + i) * fs, q, st[d]) * c1;
+    }
+  }
+  double Gl[3][6];  // Gt_ijk = 1/2 (d_j gt_ik + d_k gt_ij - d_i gt_jk)
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = j; k < 3; ++k)
+        Gl[i][S2(j, k)] = 0.5 * (dgt[j][S2(i, k)] + dgt[k][S2(i, j)] - dgt[i][S2(j, k)]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+      G.Gu[i][a] = gtu[S2(i, 0)] * Gl[0][a] + gtu[S2(i, 1)] * Gl[1][a] + gtu[S2(i, 2)] * Gl[2][a];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) G.Gd[i] = sym_contract(gtu, G.Gu[i]);
+
+  // X[j][k][l] = gt^lm Gt_jkm
+  double X[3][3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        X[j][k][l] = gtu[S2(l, 0)] * Gl[j][S2(k, 0)] + gtu[S2(l, 1)] * Gl[j][S2(k, 1)] +
+                     gtu[S2(l, 2)] * Gl[j][S2(k, 2)];
+
+  // conformal Ricci tensor
+  double Rt[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int ij = S2(i, j);
+      // -1/2 gt^lm d_l d_m gt_ij
+      const double* f = u + (F_GXX + ij) * fs;
+      double f0 = c.gt[ij];
+      double dd[6];
+      dd[0] = d2u(f, q, st[0], f0) * c2;
+      dd[3] = d2u(f, q, st[1], f0) * c2;
+      dd[5] = d2u(f, q, st[2], f0) * c2;
+      dd[1] = d11u(f, q, st[0], st[1]) * c11;
+      dd[2] = d11u(f, q, st[0], st[2]) * c11;
+      dd[4] = d11u(f, q, st[1], st[2]) * c11;
+      double r = -0.5 * sym_contract(gtu, dd);
+      // gt_k(i d_j) Gamt^k
+      double t2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t2 += c.gt[S2(k, i)] * dGam[j][k] + c.gt[S2(k, j)] * dGam[i][k];
+      r += 0.5 * t2;
+      // Gamd^k Gt_(ij)k
+      double t3 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t3 += G.Gd[k] * (Gl[i][S2(j, k)] + Gl[j][S2(i, k)]);
+      r += 0.5 * t3;
+      // gt^lm (Gt^k_li Gt_jkm + Gt^k_lj Gt_ikm + Gt^k_im Gt_klj)
+      double t4 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+          t4 += G.Gu[k][S2(l, i)] * X[j][k][l] + G.Gu[k][S2(l, j)] * X[i][k][l] +
+                G.Gu[k][S2(i, l)] * X[k][j][l];
+      Rt[ij] = r + t4;
+    }
+
+  // conformal-factor and lapse second covariant derivatives
+  const double W = c.W;
+  const double iW = 1.0 / W;
+  double DDW[6], DDal[6];
+  {
+    const double* fW = u + F_W * fs;
+    const double* fa = u + F_ALP * fs;
+    double ddW[6], dda[6];
+    ddW[0] = d2u(fW, q, st[0], W) * c2;
+    ddW[3] = d2u(fW, q, st[1], W) * c2;
+    ddW[5] = d2u(fW, q, st[2], W) * c2;
+    ddW[1] = d11u(fW, q, st[0], st[1]) * c11;
+    ddW[2] = d11u(fW, q, st[0], st[2]) * c11;
+    ddW[4] = d11u(fW, q, st[1], st[2]) * c11;
+    dda[0] = d2u(fa, q, st[0], c.al) * c2;
+    dda[3] = d2u(fa, q, st[1], c.al) * c2;
+    dda[5] = d2u(fa, q, st[2], c.al) * c2;
+    dda[1] = d11u(fa, q, st[0], st[1]) * c11;
+    dda[2] = d11u(fa, q, st[0], st[2]) * c11;
+    dda[4] = d11u(fa, q, st[1], st[2]) * c11;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      DDW[a] = ddW[a] - (G.Gu[0][a] * G.dW[0] + G.Gu[1][a] * G.dW[1] + G.Gu[2][a] * G.dW[2]);
+      DDal[a] = dda[a] - (G.Gu[0][a] * G.dal[0] + G.Gu[1][a] * G.dal[1] + G.Gu[2][a] * G.dal[2]);
+    }
+  }
+  double dWW[6], dWa[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      dWW[S2(i, j)] = G.dW[i] * G.dW[j];
+      dWa[S2(i, j)] = G.dW[i] * G.dal[j] + G.dW[j] * G.dal[i];
+    }
+  const double trDDW = sym_contract(gtu, DDW);
+  const double dWdW = sym_contract(gtu, dWW);
+  const double dWda = 0.5 * sym_contract(gtu, dWa);
+  const double trDDa = sym_contract(gtu, DDal);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    G.Ric[a] = Rt[a] + (DDW[a] + c.gt[a] * trDDW) * iW - 2.0 * c.gt[a] * dWdW * (iW * iW);
+    G.DDa[a] = DDal[a] + (dWa[a] - c.gt[a] * dWda) * iW;
+  }
+  G.Rsc = W * W * sym_contract(gtu, G.Ric);
+  G.Lapa = W * W * trDDa - W * dWda;
+}
+
+__device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ u, long long q,
+                                              long long sy, long long sz, long long fs,
+                                              double h, const DevParams& prm, double r[NF]) {
+  const long long st[3] = {1, sy, sz};
+  const double c1 = 1.0 / (12.0 * h);
+  const double c2 = c1 / h;
+  const double c11 = c1 * c1;
+  PointState c;
+  load_centre(u, q, fs, c);
+  Geo G;
+  double dGam[3][3], dbe[3][3];
+  geometry(u, q, st, fs, c1, c2, c11, c, G, dGam, dbe);
+  const double* gtu = G.gtu;
+  const double W = c.W, al = c.al;
+  const double K = c.Kh + 2.0 * c.Th;
+  const double divb = dbe[0][0] + dbe[1][1] + dbe[2][2];
+
+  // At with one index raised (Am[i][j] = gt^ik At_kj), At^ij, At_ij At^ij
+  double Am[3][3], Atu[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Am[i][j] = gtu[S2(i, 0)] * c.At[S2(0, j)] + gtu[S2(i, 1)] * c.At[S2(1, j)] +
+                 gtu[S2(i, 2)] * c.At[S2(2, j)];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j)
+      Atu[S2(i, j)] = Am[i][0] * gtu[S2(0, j)] + Am[i][1] * gtu[S2(1, j)] + Am[i][2] * gtu[S2(2, j)];
+  const double AA = sym_contract(c.At, Atu);
+
+  r[F_W] = W * (1.0 / 3.0) * (al * K - divb);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int ij = S2(i, j);
+      double s = -2.0 * al * c.At[ij];
+      double sA = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        s += c.gt[S2(i, k)] * dbe[j][k] + c.gt[S2(j, k)] * dbe[i][k];
+        sA += c.At[S2(i, k)] * dbe[j][k] + c.At[S2(j, k)] * dbe[i][k];
+      }
+      r[F_GXX + ij] = s - (2.0 / 3.0) * c.gt[ij] * divb;
+      r[F_AXX + ij] = sA - (2.0 / 3.0) * c.At[ij] * divb;  // completed below
+    }
+  const double alk1 = al * prm.kappa1;
+  r[F_KH] = -G.Lapa + al * (AA + K * K * (1.0 / 3.0)) + alk1 * (1.0 - prm.kappa2) * c.Th;
+  r[F_TH] = 0.5 * al * (G.Rsc - AA + (2.0 / 3.0) * K * K) - alk1 * (2.0 + prm.kappa2) * c.Th;
+
+  {
+    double X[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) X[a] = al * G.Ric[a] - G.DDa[a];
+    const double trX3 = sym_contract(gtu, X) * (1.0 / 3.0);
+    const double W2 = W * W;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const int ij = S2(i, j);
+        double AikAkj = c.At[S2(i, 0)] * Am[0][j] + c.At[S2(i, 1)] * Am[1][j] + c.At[S2(i, 2)] * Am[2][j];
+        r[F_AXX + ij] += W2 * (X[ij] - c.gt[ij] * trX3) + al * (K * c.At[ij] - 2.0 * AikAkj);
+      }
+  }
+
+  // Gamma-tilde: second derivatives of the shift
+  {
+    double ddb[3][6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double* f = u + (F_BETX + i) * fs;
+      ddb[i][0] = d2u(f, q, st[0], c.be[i]) * c2;
+      ddb[i][3] = d2u(f, q, st[1], c.be[i]) * c2;
+      ddb[i][5] = d2u(f, q, st[2], c.be[i]) * c2;
+      ddb[i][1] = d11u(f, q, st[0], st[1]) * c11;
+      ddb[i][2] = d11u(f, q, st[0], st[2]) * c11;
+      ddb[i][4] = d11u(f, q, st[1], st[2]) * c11;
+    }
+    double ddivb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ddivb[j] = ddb[0][S2(j, 0)] + ddb[1][S2(j, 1)] + ddb[2][S2(j, 2)];
+    double dKh[3], dTh[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      dKh[d] = d1u(u + F_KH * fs, q, st[d]) * c1;
+      dTh[d] = d1u(u + F_TH * fs, q, st[d]) * c1;
+    }
+    const double iW = 1.0 / W;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double inner = sym_contract(G.Gu[i], Atu);
+      double s = 0.0, t = 0.0, v = 0.0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        s += Atu[S2(i, j)] * G.dal[j];
+        t += Atu[S2(i, j)] * G.dW[j];
+        v += gtu[S2(i, j)] * (2.0 * dKh[j] + dTh[j]);
+      }
+      inner -= 3.0 * t * iW + v * (1.0 / 3.0);
+      double g = -2.0 * s + 2.0 * al * inner;
+      g += sym_contract(gtu, ddb[i]);
+      g += (gtu[S2(i, 0)] * ddivb[0] + gtu[S2(i, 1)] * ddivb[1] + gtu[S2(i, 2)] * ddivb[2]) * (1.0 / 3.0);
+      g += (2.0 / 3.0) * G.Gd[i] * divb;
+      g -= G.Gd[0] * dbe[0][i] + G.Gd[1] * dbe[1][i] + G.Gd[2] * dbe[2][i];
+      g -= 2.0 * alk1 * (c.Gam[i] - G.Gd[i]);
+      r[F_GAMX + i] = g;
+    }
+  }
+
+  if (prm.lapse == 1)
+    r[F_ALP] = -al * al * K;
+  else
+    r[F_ALP] = -2.0 * al * (prm.lapse_uses_khat ? c.Kh : K);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r[F_BETX + i] = 0.75 * c.Bv[i];
+    r[F_BX + i] = r[F_GAMX + i] - prm.eta * c.Bv[i];
+  }
+
+  // advection along the shift (upwind) and Kreiss-Oliger dissipation
+  const double cko = prm.sigma_ko / (64.0 * h);
+#pragma unroll 1
+  for (int f = 0; f < NF; ++f) {
+    const double* fp = u + f * fs;
+    const double f0 = __ldg(fp + q);
+    double adv = c.be[0] * dupu(fp, q, st[0], c.be[0], f0) + c.be[1] * dupu(fp, q, st[1], c.be[1], f0) +
+                 c.be[2] * dupu(fp, q, st[2], c.be[2], f0);
+    double ko = delta6(fp, q, st[0], f0) + delta6(fp, q, st[1], f0) + delta6(fp, q, st[2], f0);
+    r[f] += adv * c1 + ko * cko;
+  }
+  if (prm.shift == 1) {
+#pragma unroll
+    for (int f = F_BETX; f < NF; ++f) r[f] = 0.0;
+  }
+}
+
+// det gt = 1, At trace-free w.r.t. gt, W >= w_floor (pointwise, on a state
+// vector of 25 values)
+__device__ __forceinline__ void enforce_point(double v[NF], double w_floor) {
+  double g[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) g[a] = v[F_GXX + a];
+  double det = g[0] * (g[3] * g[5] - g[4] * g[4]) - g[1] * (g[1] * g[5] - g[4] * g[2]) +
+               g[2] * (g[1] * g[4] - g[3] * g[2]);
+  double fac = 1.0 / cbrt(det);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) g[a] *= fac;
+  double gu[6];
+  sym_inv(g, gu);
+  double tr3 = sym_contract(gu, v + F_AXX) * (1.0 / 3.0);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    v[F_GXX + a] = g[a];
+    v[F_AXX + a] -= g[a] * tr3;
+  }
+  if (v[F_W] < w_floor) v[F_W] = w_floor;
+}
+
+__device__ __forceinline__ void rk_update(int s, double dt, long long q, long long fs,
+                                          const double* __restrict__ un, double* __restrict__ y,
+                                          double* __restrict__ out, double k[NF], double w_floor,
+                                          unsigned* err) {
+  const double bw = (s == 1 || s == 4) ? (1.0 / 6.0) : (1.0 / 3.0);
+  const double cw = (s == 3) ? 1.0 : 0.5;
+  const double bdt = bw * dt, cdt = cw * dt;
+  double v[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const long long o = f * fs + q;
+    if (s == 4) {
+      v[f] = y[o] + bdt * k[f];
+    } else {
+      const double a = un[o];
+      const double yn = (s == 1) ? a + bdt * k[f] : y[o] + bdt * k[f];
+      y[o] = yn;
+      v[f] = a + cdt * k[f];
+    }
+  }
+  enforce_point(v, w_floor);
+  bool bad = false;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    out[f * fs + q] = v[f];
+    bad |= !isfinite(v[f]);
+  }
+  if (bad) atomicOr(err, (unsigned)ERR_NONFINITE);
+}
+
+template <int MODE>  // 0: RK stage, 1: RHS only
+__global__ void __launch_bounds__(128) z4c_stage_fp64_kernel(StageArgs A) {
+  const Tile tl = A.tiles[blockIdx.x];
+  const DevPatch* P = A.patches + tl.patch;
+  const int i = tl.x0 + (threadIdx.x & 31);
+  const int j = tl.y0 + (threadIdx.x >> 5);
+  const int k = tl.z0;
+  if (i >= P->n[0] || j >= P->n[1] || k >= P->n[2]) return;
+  const int ring = A.lev->ring;
+  const int s = A.stage;
+  const long long sy = P->px, sz = P->plane, fs = P->fstride;
+  const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
+  const double* __restrict__ u = P->buf[MODE ? ring : stage_in_slot(s, ring)];
+  double r[NF];
+  z4c_rhs_point(u, q, sy, sz, fs, P->dx, A.prm, r);
+  if (MODE == 1) {
+    double* out = P->buf[B_S1];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) out[f * fs + q] = r[f];
+    return;
+  }
+  rk_update(s, A.dt, q, fs, P->buf[ring], P->buf[B_Y], P->buf[stage_out_slot(s, ring)], r,
+            A.prm.w_floor, A.err);
+}
+
+// ---------------------------------------------------------------------------
+// Sommerfeld outgoing-wave condition on the ghost points of level-0 patches
+// (Sec. 2.2.2): d_t f = -(f - f_flat)/r - (x^i/r) d_i f, with d_i the 2nd-order
+// one-sided difference toward the origin, evolved with the same RK4 stage.
+
+__global__ void __launch_bounds__(128) sommerfeld_stage_kernel(GhostArgs A) {
+  const DevPatch* P = A.patches + A.patch_ids[blockIdx.y];
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (id >= shell_count(P->NX, P->NY, P->NZ)) return;
+  shell_ijk(id, P->NX, P->NY, P->NZ, i, j, k);
+  const int ring = A.lev->ring;
+  const int s = A.stage;
+  const long long sy = P->px, sz = P->plane, fs = P->fstride;
+  const long long q = i + (long long)j * sy + (long long)k * sz;
+  const double* __restrict__ u = P->buf[stage_in_slot(s, ring)];
+  const double h = P->dx;
+  const int idx[3] = {i, j, k};
+  const long long st[3] = {1, sy, sz};
+  double x[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) x[d] = P->origin[d] + (idx[d] - GH + 0.5) * h;
+  const double rr = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  const double ir = 1.0 / rr;
+  const double c = 1.0 / (2.0 * h);
+  double kk[NF];
+#pragma unroll 1
+  for (int f = 0; f < NF; ++f) {
+    const double* fp = u + f * fs;
+    const double f0 = fp[q];
+    double acc = (f0 - flat_value(f)) * ir;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long o = x[d] > 0.0 ? -st[d] : st[d];
+      double v = (3.0 * f0 - 4.0 * fp[q + o] + fp[q + 2 * o]) * c;
+      double dfd = x[d] > 0.0 ? v : -v;
+      acc += (x[d] * ir) * dfd;
+    }
+    kk[f] = -acc;
+  }
+  rk_update(s, A.dt, q, fs, P->buf[ring], P->buf[B_Y], P->buf[stage_out_slot(s, ring)], kk,
+            A.prm.w_floor, A.err);
+}
+
+// ---------------------------------------------------------------------------
+// Constraint monitor (Sec. 2.3): H = R + 2/3 K^2 - At_ij At^ij and
+// M^i = W^2 gt^ij (gt^kl Dt_k At_lj - 3 At_j^k d_k W / W - 2/3 d_j K), per block
+// partial sums of H^2, (M^x)^2, (M^y)^2, (M^z)^2 and the count over active
+// points with W >= w_excise.
+
+__global__ void __launch_bounds__(128) constraints_kernel(ConsArgs A) {
+  __shared__ double red[5][4];
+  const Tile tl = A.tiles[blockIdx.x];
+  const DevPatch* P = A.patches + tl.patch;
+  const int i = tl.x0 + (threadIdx.x & 31);
+  const int j = tl.y0 + (threadIdx.x >> 5);
+  const int k = tl.z0;
+  double acc[5] = {0, 0, 0, 0, 0};
+  if (i < P->n[0] && j < P->n[1] && k < P->n[2]) {
+    const long long sy = P->px, sz = P->plane, fs = P->fstride;
+    const long long st[3] = {1, sy, sz};
+    const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
+    const double* __restrict__ u = P->buf[A.lev->ring];
+    const double h = P->dx;
+    const double c1 = 1.0 / (12.0 * h), c2 = c1 / h, c11 = c1 * c1;
+    PointState c;
+    load_centre(u, q, fs, c);
+    Geo G;
+    double dGam[3][3], dbe[3][3];
+    geometry(u, q, st, fs, c1, c2, c11, c, G, dGam, dbe);
+    const double* gtu = G.gtu;
+    double Am[3][3], Atu[6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        Am[a][b] = gtu[S2(a, 0)] * c.At[S2(0, b)] + gtu[S2(a, 1)] * c.At[S2(1, b)] +
+                   gtu[S2(a, 2)] * c.At[S2(2, b)];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b)
+        Atu[S2(a, b)] = Am[a][0] * gtu[S2(0, b)] + Am[a][1] * gtu[S2(1, b)] + Am[a][2] * gtu[S2(2, b)];
+    const double K = c.Kh + 2.0 * c.Th;
+    const double H = G.Rsc + (2.0 / 3.0) * K * K - sym_contract(c.At, Atu);
+    double dAt[3][6], dK[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int a = 0; a < 6; ++a) dAt[d][a] = d1u(u + (F_AXX + a) * fs, q, st[d]) * c1;
+      dK[d] = (d1u(u + F_KH * fs, q, st[d]) + 2.0 * d1u(u + F_TH * fs, q, st[d])) * c1;
+    }
+    double Ml[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double s = 0.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          // Dt_b At_ea = d_b At_ea - Gt^l_be At_la - Gt^l_ba At_el
+          double DA = dAt[b][S2(e, a)];
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+            DA -= G.Gu[l][S2(b, e)] * c.At[S2(l, a)] + G.Gu[l][S2(b, a)] * c.At[S2(e, l)];
+          s += gtu[S2(b, e)] * DA;
+        }
+      s -= 3.0 * (Am[0][a] * G.dW[0] + Am[1][a] * G.dW[1] + Am[2][a] * G.dW[2]) / c.W;
+      s -= (2.0 / 3.0) * dK[a];
+      Ml[a] = s;
+    }
+    if (c.W >= A.w_excise) {
+      acc[0] = H * H;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double m = c.W * c.W * (gtu[S2(a, 0)] * Ml[0] + gtu[S2(a, 1)] * Ml[1] + gtu[S2(a, 2)] * Ml[2]);
+        acc[1 + a] = m * m;
+      }
+      acc[4] = 1.0;
+    }
+  }
+  // fixed-order block reduction: warp shuffles, then 4 warps in order
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    double v = acc[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    const int a = threadIdx.x;
+    A.partial[(long long)blockIdx.x * 5 + a] = ((red[a][0] + red[a][1]) + red[a][2]) + red[a][3];
+  }
+}
+
+// deterministic final sum of per-block partials: one block, fixed order
+__global__ void sum_partials_kernel(const double* partial, int nblocks, int width, double* out) {
+  __shared__ double sh[256];
+  for (int a = 0; a < width; ++a) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[(long long)b * width + a];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[a] = sh[0];
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// host-side launchers
+
+void launch_stage_fp64(const StageArgs& a, cudaStream_t st) {
+  if (a.ntiles == 0) return;
+  if (a.stage == 0)
+    z4c_stage_fp64_kernel<1><<<a.ntiles, 128, 0, st>>>(a);
+  else
+    z4c_stage_fp64_kernel<0><<<a.ntiles, 128, 0, st>>>(a);
+}
+
+void launch_sommerfeld(const GhostArgs& a, int npatches, long long max_shell, cudaStream_t st) {
+  if (npatches == 0 || max_shell == 0) return;
+  dim3 grid((unsigned)((max_shell + 127) / 128), npatches);
+  sommerfeld_stage_kernel<<<grid, 128, 0, st>>>(a);
+}
+
+void launch_constraints(const ConsArgs& a, int ntiles, double* out5, cudaStream_t st) {
+  if (ntiles == 0) return;
+  constraints_kernel<<<ntiles, 128, 0, st>>>(a);
+  sum_partials_kernel<<<1, 256, 0, st>>>(a.partial, ntiles, 5, out5);
+}
+
+}  // namespace sacrak

@@ -1,0 +1,59 @@
+"""The C ABI library loads, exports every function include/sacrak.h
+declares, and validates arguments on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2607_08743_gb300 as sk
+from paper_2607_08743_gb300 import build as skbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    skbuild.build()
+    return sk.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sacrak.h")).read()
+    return sorted(set(re.findall(r"\b(sacrak_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert _declared() == sorted(sk.EXPORTS)
+
+
+def test_every_declared_symbol_exported(L):
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_arena_bytes_host_side(L):
+    import initial_data as idd
+    h = idd.binary_7_level()
+    n = sk.arena_bytes(len(h.levels), h.patches)
+    # six state copies of every patch dominate
+    states = sum(6 * 25 * 8 * (p.n[0] + 6 + (-(p.n[0] + 6)) % 8) * (p.n[1] + 6) * (p.n[2] + 6)
+                 for p in h.patches)
+    assert states <= n < states + 64 * 2 ** 20
+    assert sk.arena_bytes(2, h.patches[:1]) == 0  # level 1 without a patch
+
+
+def test_invalid_arguments_rejected_before_device_work(L):
+    out = ctypes.c_void_p()
+    prm = sk.Params().c()
+    d = sk._descs([type("P", (), {"level": 0, "n": (8, 8, 8), "origin": (0, 0, 0)})()])
+    # null arena
+    assert L.sacrak_grid_create(1, 1.0, 1, d, ctypes.byref(prm), None, None, 0, ctypes.byref(out)) == sk.EINVAL
+    # bad dx0
+    assert L.sacrak_grid_create(1, -1.0, 1, d, ctypes.byref(prm), None, ctypes.c_void_p(256), 1 << 30,
+                                ctypes.byref(out)) == sk.EINVAL
+    # null grid handles
+    assert L.sacrak_rk4_step(None, 0, 0.1) == sk.EINVAL
+    assert L.sacrak_level_step(None, 0) == sk.EINVAL
+    assert L.sacrak_grid_destroy(None) == sk.EINVAL
+    assert L.sacrak_last_error(None) == b"null grid"
