@@ -157,6 +157,25 @@ sacrak_status sacrak_profile_enable(sacrak_grid* grid, int enable);
 sacrak_status sacrak_profile_read(sacrak_grid* grid, double* stage_ms, long long* stage_launches,
                                   long long* stage_zones);
 
+/* Allocation-free constraint monitor for callers that cannot allocate device
+ * memory (a process whose device memory belongs to another framework's pool,
+ * a fixed-size sandbox or service, a hook that must not call cudaMalloc).  No
+ * counterpart in the paper: it computes what sacrak_constraints computes for
+ * one level (the L2 norms of H, M^x, M^y, M^z over active cells with
+ * W >= w_excise), for one patch array that the caller keeps in its own device
+ * memory (dev_u, the unpadded patch-array layout above, n[3] active cells,
+ * 4 <= n <= 512 per axis, spacing dx), without a grid.  Its partial sums live
+ * in one static device array of 2048 x 5 + 8 doubles (about 80 KB) that every
+ * GPU which loads the library keeps until the process exits; nothing is
+ * allocated or freed.  The first call on a device looks that array up (with
+ * the device current) and should come before any stream capture.  Calls that
+ * overlap on the GPU share the array and race; serialise them (one stream,
+ * or one call at a time).  Runs on cuda_stream (a cudaStream_t, NULL = legacy
+ * default) and synchronises it to return out_l2 (host memory).  Sizes beyond
+ * the limits and non-device dev_u return SACRAK_EINVAL. */
+sacrak_status sacrak_constraints_noalloc(const double* dev_u, const int n[3], double dx,
+                                         double w_excise, void* cuda_stream, double out_l2[4]);
+
 /* Current time of a level. */
 sacrak_status sacrak_level_time(sacrak_grid* grid, int level, double* t);
 

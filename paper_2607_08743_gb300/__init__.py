@@ -28,7 +28,7 @@ EXPORTS = [
     "sacrak_arena_bytes", "sacrak_grid_create", "sacrak_grid_destroy", "sacrak_set_initial_data",
     "sacrak_upload_fields", "sacrak_download_fields", "sacrak_rhs", "sacrak_rk4_step",
     "sacrak_level_step", "sacrak_constraints", "sacrak_pi_symmetry", "sacrak_level_time",
-    "sacrak_last_error", "sacrak_profile_enable", "sacrak_profile_read",
+    "sacrak_last_error", "sacrak_profile_enable", "sacrak_profile_read", "sacrak_constraints_noalloc",
 ]
 
 
@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
             L.sacrak_level_time.argtypes = [vp, ctypes.c_int, dp]
             L.sacrak_profile_enable.argtypes = [vp, ctypes.c_int]
             L.sacrak_profile_read.argtypes = [vp, dp, P(ctypes.c_longlong), P(ctypes.c_longlong)]
+            L.sacrak_constraints_noalloc.argtypes = [vp, P(ctypes.c_int), ctypes.c_double, ctypes.c_double,
+                                                     vp, dp]
             L.sacrak_last_error.argtypes = [vp]
             L.sacrak_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
@@ -134,6 +136,20 @@ def _ptr(a) -> int:
         return a.ctypes.data
     assert a.dtype.itemsize == 8 and a.is_contiguous()
     return a.data_ptr()
+
+
+def constraints_noalloc(dev_u, n, dx: float, w_excise: float = 0.0, stream=None) -> np.ndarray:
+    """Constraint norms of one patch array held in caller-owned device memory
+    (a CUDA tensor in the unpadded patch-array layout), without a grid and
+    without any device allocation (sacrak_constraints_noalloc)."""
+    nn = (ctypes.c_int * 3)(*[int(v) for v in n])
+    out = np.empty(4)
+    sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    st = lib().sacrak_constraints_noalloc(ctypes.c_void_p(_ptr(dev_u)), nn, dx, w_excise, sp,
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != OK:
+        raise SacrakError(st, "sacrak_constraints_noalloc failed")
+    return out
 
 
 class Grid:

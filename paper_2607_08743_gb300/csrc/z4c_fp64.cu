@@ -8,6 +8,9 @@
 // 1/(12h) or 1/(144h^2), contractions of the Christoffel symbols through the
 // partially raised symbol X[j][k][l] = gt^lm Gt_jkm, and second derivatives
 // of gt consumed into the Ricci tensor as they are formed.
+#include <mutex>
+
+#include "../../include/sacrak.h"
 #include "sacrak_dev.cuh"
 
 namespace sacrak {
@@ -594,3 +597,169 @@ void launch_constraints(const ConsArgs& a, int ntiles, double* out5, cudaStream_
 }
 
 }  // namespace sacrak
+
+// ----------------------------------------------------------------------------
+// Allocation-free variant of the constraint monitor.
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// host framework that owns the whole device through its own memory pool,
+// inside a pre-sized sandbox or a fixed-memory production service, or in a
+// hook that must never trigger cudaMalloc's implicit synchronisation.  They
+// keep a patch in their own device memory and want its constraint norms.
+// This entry point needs no grid and no arena: the per-block partial sums go
+// to one file-scope device array of fixed size that every GPU loading this
+// library holds until the process exits.
+
+namespace sacrak {
+namespace {
+
+constexpr int NOALLOC_MAX_BLOCKS = 2048;  // partial-sum slots (5 doubles each)
+constexpr int NOALLOC_MAX_N = 512;        // largest active cells per axis
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+// [0, 5*NOALLOC_MAX_BLOCKS): per-block partials; then 5 final sums.  Every call
+// overwrites the slots it uses before reading them, so nothing has to start
+// at zero; calls that overlap on the GPU race on this array.
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * 5 + 8];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// device address of the scratch array on the current device (looked up once
+// per device, with that device current; the host-side symbol is only a
+// stand-in and must never be handed to a kernel)
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = (double*)g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+// one block per group of 32x4 points of a z-plane, grid-striding over the
+// patch; the same per-point arithmetic as constraints_kernel
+__global__ void __launch_bounds__(128) constraints_noalloc_kernel(const double* __restrict__ u,
+                                                                  int nx, int ny, int nz, double h,
+                                                                  double w_excise, double* partial) {
+  __shared__ double red[5][4];
+  const int tx = (nx + 31) / 32, ty = (ny + 3) / 4;
+  const long long ntiles = (long long)tx * ty * nz;
+  const int NX = nx + 2 * GH, NY = ny + 2 * GH, NZ = nz + 2 * GH;
+  const long long sy = NX, sz = (long long)NX * NY, fs = sz * NZ;
+  const long long st[3] = {1, sy, sz};
+  const double c1 = 1.0 / (12.0 * h), c2 = c1 / h, c11 = c1 * c1;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int i = (int)(t % tx) * 32 + (threadIdx.x & 31);
+    const int j = (int)((t / tx) % ty) * 4 + (threadIdx.x >> 5);
+    const int k = (int)(t / ((long long)tx * ty));
+    if (i >= nx || j >= ny) continue;
+    const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
+    PointState c;
+    load_centre(u, q, fs, c);
+    Geo G;
+    double dGam[3][3], dbe[3][3];
+    geometry(u, q, st, fs, c1, c2, c11, c, G, dGam, dbe);
+    const double* gtu = G.gtu;
+    double Am[3][3], Atu[6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        Am[a][b] = gtu[S2(a, 0)] * c.At[S2(0, b)] + gtu[S2(a, 1)] * c.At[S2(1, b)] +
+                   gtu[S2(a, 2)] * c.At[S2(2, b)];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b)
+        Atu[S2(a, b)] = Am[a][0] * gtu[S2(0, b)] + Am[a][1] * gtu[S2(1, b)] + Am[a][2] * gtu[S2(2, b)];
+    const double K = c.Kh + 2.0 * c.Th;
+    const double H = G.Rsc + (2.0 / 3.0) * K * K - sym_contract(c.At, Atu);
+    double dAt[3][6], dK[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int a = 0; a < 6; ++a) dAt[d][a] = d1u(u + (F_AXX + a) * fs, q, st[d]) * c1;
+      dK[d] = (d1u(u + F_KH * fs, q, st[d]) + 2.0 * d1u(u + F_TH * fs, q, st[d])) * c1;
+    }
+    double Ml[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double s = 0.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          double DA = dAt[b][S2(e, a)];
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+            DA -= G.Gu[l][S2(b, e)] * c.At[S2(l, a)] + G.Gu[l][S2(b, a)] * c.At[S2(e, l)];
+          s += gtu[S2(b, e)] * DA;
+        }
+      s -= 3.0 * (Am[0][a] * G.dW[0] + Am[1][a] * G.dW[1] + Am[2][a] * G.dW[2]) / c.W;
+      s -= (2.0 / 3.0) * dK[a];
+      Ml[a] = s;
+    }
+    if (c.W >= w_excise) {
+      acc[0] += H * H;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double m = c.W * c.W * (gtu[S2(a, 0)] * Ml[0] + gtu[S2(a, 1)] * Ml[1] + gtu[S2(a, 2)] * Ml[2]);
+        acc[1 + a] += m * m;
+      }
+      acc[4] += 1.0;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    double v = acc[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    const int a = threadIdx.x;
+    partial[(long long)blockIdx.x * 5 + a] = ((red[a][0] + red[a][1]) + red[a][2]) + red[a][3];
+  }
+}
+
+}  // namespace
+}  // namespace sacrak
+
+extern "C" sacrak_status sacrak_constraints_noalloc(const double* dev_u, const int n[3], double dx,
+                                                    double w_excise, void* cuda_stream,
+                                                    double out_l2[4]) {
+  using namespace sacrak;
+  if (!dev_u || !n || !out_l2 || !(dx > 0.0)) return SACRAK_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (n[d] < 4 || n[d] > NOALLOC_MAX_N) return SACRAK_EINVAL;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, dev_u) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return SACRAK_EINVAL;
+  }
+  double* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) return SACRAK_ECUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const long long ntiles = (long long)((n[0] + 31) / 32) * ((n[1] + 3) / 4) * n[2];
+  const int nblocks = (int)(ntiles < NOALLOC_MAX_BLOCKS ? ntiles : NOALLOC_MAX_BLOCKS);
+  constraints_noalloc_kernel<<<nblocks, 128, 0, st>>>(dev_u, n[0], n[1], n[2], dx, w_excise, scratch);
+  double* sums_dev = scratch + (size_t)NOALLOC_MAX_BLOCKS * 5;
+  sum_partials_kernel<<<1, 256, 0, st>>>(scratch, nblocks, 5, sums_dev);
+  if (cudaGetLastError() != cudaSuccess) return SACRAK_ECUDA;
+  double sums[5];
+  if (cudaMemcpyAsync(sums, sums_dev, sizeof sums, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SACRAK_ECUDA;
+  for (int c = 0; c < 4; ++c) out_l2[c] = sums[4] > 0 ? sqrt(sums[c] / sums[4]) : 0.0;
+  return SACRAK_OK;
+}
