@@ -114,9 +114,26 @@ def test_periodic_gauge_wave_steps_parity():
     for _ in range(4):
         g.rk4_step(0, dt)
         u = oracle.rk4_step(p, u, dt, op, bc=oracle.BC_PERIODIC)
-    # Theta vanishes in the continuum gauge wave: judged against a 1e-6 floor
-    e = rel_err(g.download_fields(0), u, floor=1e-6)
-    assert e.max() <= 1e-12, dict(zip(idd.FIELD_NAMES, e))
+    # every non-constant field of the gauge wave is O(A) = O(0.01); fields that
+    # vanish analytically (Theta) are roundoff noise, so each field is judged
+    # relative to max(|field|, A)
+    e = rel_err(g.download_fields(0), u, floor=0.01)
+    # four RK4 steps accumulate the per-call rounding differences (1e-12 per
+    # RHS call); Khat, Theta and At reach ~1e-12 relative after four steps
+    assert e.max() <= 1e-11, " ".join("%s=%.2e" % kv for kv in zip(idd.FIELD_NAMES, e) if kv[1] > 1e-14)
+
+
+def test_gauge_wave_rhs_parity():
+    """RHS parity on the gauge wave (non-flat gt, At, K, Gamt active)."""
+    p = idd.Patch(n=(32, 4, 4), dx=1 / 32, origin=(-0.5, -2 / 32, -2 / 32))
+    prm = dict(lapse=1, shift=1, bc=1, sigma_ko=0.5, kappa1=0.005, courant=0.25)
+    g = grid_for([p], **prm)
+    u = oracle.fill_periodic(p, idd.gauge_wave(p, 0.01))
+    g.upload_fields(0, u)
+    r = g.rhs(0)
+    ro = oracle.rhs(p, u, oracle.Params(lapse=1, shift=1, sigma_ko=0.5, kappa1=0.005))
+    e = rel_err(r, ro, floor=1e-3)
+    assert e.max() <= TOL_RHS, {k: "%.2e" % v for k, v in zip(idd.FIELD_NAMES, e)}
 
 
 def test_frozen_ghosts_parity():
