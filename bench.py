@@ -101,21 +101,18 @@ def hierarchy():
 
 
 def launches_per_coarse_step(h) -> int:
-    """Kernels launched by one coarse step (the recursion is static)."""
+    """Kernels launched by one coarse step (the recursion is static): per level
+    step 4 x (ghost fill on levels > 0, fused stage kernel, Sommerfeld ghosts
+    on level 0), the level bookkeeping, the spatial prolongation of the new
+    slot for the children; per child level step pair: ghost fill at the new
+    time, restriction and the prolongation of the restricted slot."""
     total = 0
+    nlev = len(h.levels)
     for l, lv in enumerate(h.levels):
-        steps = 2 ** l
-        per = 0
-        for s in range(4):
-            if l > 0:
-                per += 1 + (len(lv) * (len(lv) - 1)) // 2 * 0  # prolongation (exchange only if touching)
-            per += 1                                          # fused stage kernel
-            if l == 0:
-                per += 1                                      # Sommerfeld ghosts
-        per += 1                                              # level bookkeeping
-        if l > 0:
-            per += 2                                          # ghost fill at the new time + restriction
-        total += steps * per
+        per = 4 * (1 + (1 if l > 0 else 0) + (1 if l == 0 else 0)) + 1
+        if l + 1 < nlev:
+            per += 1 + 3  # prolong new slot; after the two child steps: fill, restrict, prolong
+        total += (2 ** l) * per
     return total
 
 

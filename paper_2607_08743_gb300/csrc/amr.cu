@@ -55,62 +55,158 @@ __constant__ double c_wm[6] = {63.0 / 8192, -495.0 / 8192, 2310.0 / 8192,
 
 __device__ __forceinline__ int floor_half(int i) { return i >= 0 ? i / 2 : -((-i + 1) / 2); }
 
-// Child ghosts from the parent: a combination of the parent's time levels
-// (oldest, middle, newest; the host computes the weights: quadratic once three
-// levels exist, linear before) interpolated in space with the tensor-product
-// 6-point Lagrange interpolant.
-__global__ void __launch_bounds__(128) prolong_kernel(FillArgs A) {
+// Spatial prolongation of one parent time level onto the ghost shell of each
+// child (Sec. 2.2.1, 6th-order Lagrange, tensor product).  The result is
+// cached per parent ring slot in the child's gsh[slot]; the per-stage ghost
+// fill then only combines the cached slots in time (ghost_time_fill_kernel),
+// so the 6^3 stencils run twice per parent step instead of at every child
+// stage.  One thread computes one field of the 2x2x2 children of one parent
+// cell from its 7^3 neighbourhood with separable x, y, z passes (the even
+// child sits at -1/4 of the parent cell, nodes -3..2; the odd one at +1/4,
+// nodes -2..3).
+struct ProlongArgs {
+  const DevPatch* patches;
+  const int* patch_ids;   // children (one level)
+  const DevLevel* plev;   // parent level: slot = its current ring slot
+};
+
+__device__ __forceinline__ void box_shell_ijk(long long id, int m0, int m1, int m2, int w, int& a,
+                                              int& b, int& c) {
+  // shell of width w of an m0 x m1 x m2 box: two z slabs, two y slabs, two x slabs
+  const long long zs = (long long)w * m1 * m0;
+  const int n2 = m2 - 2 * w, n1 = m1 - 2 * w;
+  const long long ys = (long long)w * m0 * n2;
+  if (id < 2 * zs) {
+    int side = id >= zs;
+    long long r = id - side * zs;
+    a = (int)(r % m0);
+    r /= m0;
+    b = (int)(r % m1);
+    c = (int)(r / m1) + (side ? m2 - w : 0);
+    return;
+  }
+  id -= 2 * zs;
+  if (id < 2 * ys) {
+    int side = id >= ys;
+    long long r = id - side * ys;
+    a = (int)(r % m0);
+    r /= m0;
+    b = (int)(r % w) + (side ? m1 - w : 0);
+    c = (int)(r / w) + w;
+    return;
+  }
+  id -= 2 * ys;
+  const long long xs = (long long)w * n1 * n2;
+  int side = id >= xs;
+  long long r = id - side * xs;
+  a = (int)(r % w) + (side ? m0 - w : 0);
+  r /= w;
+  b = (int)(r % n1) + w;
+  c = (int)(r / n1) + w;
+}
+
+__global__ void __launch_bounds__(128) prolong_space_kernel(ProlongArgs A, long long max_work) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= max_work) return;
+  const DevPatch* C = A.patches + A.patch_ids[blockIdx.y];
+  // parent cells whose children touch the ghost shell: the box
+  // [off-2, off+n/2+1] minus its interior [off, off+n/2-1] (a shell of width 2)
+  const int m0 = C->n[0] / 2 + 4, m1 = C->n[1] / 2 + 4, m2 = C->n[2] / 2 + 4;
+  const long long ncl = (long long)m0 * m1 * m2 - (long long)(m0 - 4) * (m1 - 4) * (m2 - 4);
+  const int f = (int)(tid % NF);
+  const long long cl = tid / NF;
+  if (cl >= ncl) return;
+  int a, b, c;
+  box_shell_ijk(cl, m0, m1, m2, 2, a, b, c);
+  const DevPatch* P = A.patches + C->parent;
+  const int slot = A.plev->ring;
+  const double* __restrict__ up = P->buf[slot] + (long long)f * P->fstride;
+  // parent array index of the cell and of its 7^3 neighbourhood origin
+  const int pi = C->off[0] - 2 + a + GH, pj = C->off[1] - 2 + b + GH, pk = C->off[2] - 2 + c + GH;
+  const long long q0 = (pi - 3) + (long long)(pj - 3) * P->px + (long long)(pk - 3) * P->plane;
+  // weights over offsets -3..3 for the even (-1/4) and odd (+1/4) child
+  double we[7], wo[7];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    we[t] = c_wm[t];
+    wo[t + 1] = c_wp[t];
+  }
+  we[6] = 0.0;
+  wo[0] = 0.0;
+  // Only parent cells off-4 .. off+n/2+3 (parent active cells, by the nesting
+  // margin) are read: the children that are kept need no others, and cells
+  // outside that range (possibly never written) would turn a zero weight into
+  // NaN.  Valid stencil offsets t along each axis: [t_lo, t_hi].
+  const int xlo = max(0, 1 - a), xhi = min(6, C->n[0] / 2 + 8 - a);
+  const int ylo = max(0, 1 - b), yhi = min(6, C->n[1] / 2 + 8 - b);
+  const int zlo = max(0, 1 - c), zhi = min(6, C->n[2] / 2 + 8 - c);
+  double acc[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};  // [z][y][x] parity
+#pragma unroll 1
+  for (int kz = zlo; kz <= zhi; ++kz) {
+    double vy[2][2] = {{0, 0}, {0, 0}};
+#pragma unroll
+    for (int jy = 0; jy < 7; ++jy) {
+      if (jy < ylo || jy > yhi) continue;
+      const double* row = up + q0 + (long long)kz * P->plane + (long long)jy * P->px;
+      double xe = 0.0, xo = 0.0;
+#pragma unroll
+      for (int ix = 0; ix < 7; ++ix) {
+        const double v = (ix >= xlo && ix <= xhi) ? __ldg(row + ix) : 0.0;
+        xe += we[ix] * v;
+        xo += wo[ix] * v;
+      }
+      vy[0][0] += we[jy] * xe;
+      vy[0][1] += we[jy] * xo;
+      vy[1][0] += wo[jy] * xe;
+      vy[1][1] += wo[jy] * xo;
+    }
+#pragma unroll
+    for (int y = 0; y < 2; ++y)
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {
+        acc[0][y][x] += we[kz] * vy[y][x];
+        acc[1][y][x] += wo[kz] * vy[y][x];
+      }
+  }
+  // child indices of the even child along each axis
+  const int c0 = 2 * (a - 2), c1 = 2 * (b - 2), c2 = 2 * (c - 2);
+  double* __restrict__ g = C->gsh[slot] + (long long)f * C->fstride;
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+#pragma unroll
+    for (int y = 0; y < 2; ++y)
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {
+        const int i = c0 + x, j = c1 + y, k = c2 + z;
+        if (i < -GH || j < -GH || k < -GH || i >= C->n[0] + GH || j >= C->n[1] + GH || k >= C->n[2] + GH)
+          continue;
+        const bool active = i >= 0 && j >= 0 && k >= 0 && i < C->n[0] && j < C->n[1] && k < C->n[2];
+        if (active) continue;
+        g[(i + GH) + (long long)(j + GH) * C->px + (long long)(k + GH) * C->plane] = acc[z][y][x];
+      }
+}
+
+// Ghosts of the child's target buffer = time combination of the cached
+// spatial prolongations of the parent's (oldest, middle, newest) slots.
+__global__ void ghost_time_fill_kernel(FillArgs A) {
   const DevPatch* C = A.patches + A.patch_ids[blockIdx.y];
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= nshell(C)) return;
   int i, j, k;
   shell_ijk(id, C->NX, C->NY, C->NZ, i, j, k);
-  const DevPatch* P = A.patches + C->parent;
   const int pr = A.plev->ring;
-  const int nv = A.plev->nvalid;
-  const bool q3 = nv >= 3;
-  const double wt[3] = {q3 ? A.wq[0] : 0.0, q3 ? A.wq[1] : A.wl[1], q3 ? A.wq[2] : A.wl[2]};
-  const double* __restrict__ t0 = P->buf[(pr + 1) % 3];  // oldest
-  const double* __restrict__ t1 = P->buf[(pr + 2) % 3];  // middle
-  const double* __restrict__ t2 = P->buf[pr];            // newest
-  const int ci[3] = {i - GH, j - GH, k - GH};
-  int base[3];
-  const double* w[3];
-  int lo[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int odd = ci[d] & 1;
-    base[d] = C->off[d] + floor_half(ci[d]) + GH;
-    w[d] = odd ? c_wp : c_wm;
-    lo[d] = odd ? -2 : -3;
-  }
+  const bool q3 = A.plev->nvalid >= 3;
+  const double w0 = q3 ? A.wq[0] : 0.0, w1 = q3 ? A.wq[1] : A.wl[1], w2 = q3 ? A.wq[2] : A.wl[2];
+  const double* __restrict__ g0 = C->gsh[(pr + 1) % 3];
+  const double* __restrict__ g1 = C->gsh[(pr + 2) % 3];
+  const double* __restrict__ g2 = C->gsh[pr];
   double* __restrict__ dst = C->buf[fill_slot(A.mode, A.stage, A.lev->ring)];
-  const long long qc = i + (long long)j * C->px + (long long)k * C->plane;
-  const long long q0 = (base[0] + lo[0]) + (long long)(base[1] + lo[1]) * P->px +
-                       (long long)(base[2] + lo[2]) * P->plane;
-  const bool quad = nv >= 3;
-#pragma unroll 1
+  const long long q = i + (long long)j * C->px + (long long)k * C->plane;
   for (int f = 0; f < NF; ++f) {
-    const long long fo = f * P->fstride + q0;
-    double v = 0.0;
-#pragma unroll 1
-    for (int c = 0; c < 6; ++c) {
-      double vy = 0.0;
-#pragma unroll 1
-      for (int b = 0; b < 6; ++b) {
-        const long long o = fo + (long long)c * P->plane + (long long)b * P->px;
-        double vx = 0.0;
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-          double val = wt[1] * __ldg(t1 + o + a) + wt[2] * __ldg(t2 + o + a);
-          if (quad) val += wt[0] * __ldg(t0 + o + a);
-          vx += w[0][a] * val;
-        }
-        vy += w[1][b] * vx;
-      }
-      v += w[2][c] * vy;
-    }
-    dst[f * C->fstride + qc] = v;
+    const long long o = f * C->fstride + q;
+    double v = w1 * g1[o] + w2 * g2[o];
+    if (q3) v += w0 * g0[o];
+    dst[o] = v;
   }
 }
 
@@ -209,9 +305,21 @@ void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cu
   switch (kind) {
     case 0: periodic_fill_kernel<<<grid, 128, 0, st>>>(a); break;
     case 1: frozen_fill_kernel<<<grid, 128, 0, st>>>(a); break;
-    case 2: prolong_kernel<<<grid, 128, 0, st>>>(a); break;
+    case 2: ghost_time_fill_kernel<<<grid, 128, 0, st>>>(a); break;
     case 3: restrict_kernel<<<grid, 128, 0, st>>>(a); break;
   }
+}
+
+void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,
+                          long long max_clusters, cudaStream_t st) {
+  if (nchildren == 0 || max_clusters == 0) return;
+  ProlongArgs a;
+  a.patches = patches;
+  a.patch_ids = ids;
+  a.plev = plev;
+  const long long work = max_clusters * NF;
+  dim3 grid((unsigned)((work + 127) / 128), nchildren);
+  prolong_space_kernel<<<grid, 128, 0, st>>>(a, work);
 }
 
 void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st) {

@@ -93,7 +93,8 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, Layout& L,
     L.px[p] = px;
     L.fstride[p] = fs;
     L.patch_state[p] = off;
-    off = align_up(off + (size_t)NBUF * NF * fs * sizeof(double), 256);
+    const int nbuf = NBUF + (pd[p].level > 0 ? 3 : 0);  // + cached prolongation slots
+    off = align_up(off + (size_t)nbuf * NF * fs * sizeof(double), 256);
   }
   L.total = off;
   return true;
@@ -113,7 +114,8 @@ struct sacrak_grid {
   std::vector<std::vector<int>> lvl_ids;   // patch ids per level
   std::vector<int> lvl_id_off;             // offset of each level's ids in the device id array
   std::vector<size_t> lvl_tile_off, lvl_ntiles;
-  std::vector<long long> lvl_max_shell, lvl_max_restrict;
+  std::vector<long long> lvl_max_shell, lvl_max_restrict, lvl_max_clusters;
+  bool shells_dirty = true;
   DevPatch* d_patches;
   DevLevel* d_levels;
   int* d_ids;
@@ -280,6 +282,20 @@ void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double d
     }
 }
 
+// spatial prolongation of level l-1's current slot onto level l's shells
+void refresh_shells(sacrak_grid* g, int l) {
+  if (l <= 0 || l >= g->nlevels) return;
+  launch_prolong_space(g->d_patches, g->d_ids + g->lvl_id_off[l], g->d_levels + (l - 1),
+                       (int)g->lvl_ids[l].size(), g->lvl_max_clusters[l], g->stream);
+}
+
+// after new data: every child level's cache for its parent's current slot
+void refresh_all_shells(sacrak_grid* g) {
+  if (!g->shells_dirty) return;
+  for (int l = 1; l < g->nlevels; ++l) refresh_shells(g, l);
+  g->shells_dirty = false;
+}
+
 void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
   const int np = (int)g->lvl_ids[l].size();
   for (int s = 1; s <= 4; ++s) {
@@ -313,6 +329,7 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
   if (l == 0 && g->prm.bc == 2)
     launch_fill(FILL_FROZEN, fill_args(g, l, 2, 4, 0.0), np, g->lvl_max_shell[l], g->stream);
   launch_level_advance(g->d_levels + l, dt, g->stream);
+  refresh_shells(g, l + 1);  // the children's cache of this level's new slot
 }
 
 void level_step_rec(sacrak_grid* g, int l, double frac0, double dfrac) {
@@ -324,6 +341,7 @@ void level_step_rec(sacrak_grid* g, int l, double frac0, double dfrac) {
     fill_ghosts(g, l + 1, 1, 0, 1.0, 0.0);  // prolongation (unrestricted parent) + exchange
     launch_fill(FILL_RESTRICT, fill_args(g, l + 1, 1, 0, 0.0), nc, g->lvl_max_restrict[l + 1],
                 g->stream);
+    refresh_shells(g, l + 1);  // the restricted slot, for the next parent step
   }
 }
 
@@ -412,6 +430,10 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
     P.parent = -1;
     for (int b = 0; b < NBUF; ++b)
       P.buf[b] = (double*)(g->arena + L.patch_state[i] + (size_t)b * NF * P.fstride * sizeof(double));
+    for (int b = 0; b < 3; ++b)
+      P.gsh[b] = P.level > 0 ? (double*)(g->arena + L.patch_state[i] +
+                                        (size_t)(NBUF + b) * NF * P.fstride * sizeof(double))
+                             : nullptr;
     g->lvl_ids[P.level].push_back(i);
   }
   // parents: the patch of the level above containing the child with margin
@@ -471,6 +493,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   g->lvl_ntiles.resize(nlevels);
   g->lvl_max_shell.assign(nlevels, 0);
   g->lvl_zones.assign(nlevels, 0);
+  g->lvl_max_clusters.assign(nlevels, 0);
   g->lvl_max_restrict.assign(nlevels, 0);
   for (int l = 0; l < nlevels; ++l) {
     g->lvl_id_off[l] = (int)ids.size();
@@ -484,6 +507,11 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
       long long sh = (long long)P.NX * P.NY * P.NZ - (long long)P.n[0] * P.n[1] * P.n[2];
       if (sh > g->lvl_max_shell[l]) g->lvl_max_shell[l] = sh;
       g->lvl_zones[l] += (long long)P.n[0] * P.n[1] * P.n[2];
+      {
+        long long m0 = P.n[0] / 2 + 4, m1 = P.n[1] / 2 + 4, m2 = P.n[2] / 2 + 4;
+        long long cl = m0 * m1 * m2 - (m0 - 4) * (m1 - 4) * (m2 - 4);
+        if (cl > g->lvl_max_clusters[l]) g->lvl_max_clusters[l] = cl;
+      }
       long long rs = (long long)(P.n[0] / 2) * (P.n[1] / 2) * (P.n[2] / 2);
       if (rs > g->lvl_max_restrict[l]) g->lvl_max_restrict[l] = rs;
     }
@@ -540,6 +568,7 @@ sacrak_status sacrak_set_initial_data(sacrak_grid* g, int kind, int npunct, cons
   }
   sacrak_status st = reset_levels(g);
   if (st != SACRAK_OK) return st;
+  g->shells_dirty = true;
   InitArgs a;
   std::memset(&a, 0, sizeof a);
   a.patches = g->d_patches;
@@ -587,6 +616,7 @@ sacrak_status sacrak_upload_fields(sacrak_grid* g, int patch, const double* src)
   st = copy_patch(g, patch, P.buf[lv.ring], src, nullptr, true);
   if (st != SACRAK_OK) return st;
   lv.nvalid = 1;
+  g->shells_dirty = true;
   CK(cudaMemcpyAsync(&g->d_levels[P.level], &lv, sizeof lv, cudaMemcpyHostToDevice, g->stream));
   CK(cudaStreamSynchronize(g->stream));  // lv is a host stack variable
   g->invalid = false;
@@ -649,6 +679,7 @@ sacrak_status sacrak_rk4_step(sacrak_grid* g, int level, double dt) {
   if (!g) return SACRAK_EINVAL;
   if (level < 0 || level >= g->nlevels) return fail(g, SACRAK_EINVAL, "bad level");
   if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
+  refresh_all_shells(g);
   rk4_level(g, level, dt > 0.0 ? dt : level_dt(g, level), 0.0, 0.5);
   return check_launch(g);
 }
@@ -657,6 +688,7 @@ sacrak_status sacrak_level_step(sacrak_grid* g, int level) {
   if (!g) return SACRAK_EINVAL;
   if (level < 0 || level >= g->nlevels) return fail(g, SACRAK_EINVAL, "bad level");
   if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
+  refresh_all_shells(g);  // eager, outside any graph
   if (level > 0 || g->stream == nullptr || g->prof) {
     level_step_rec(g, level, 0.0, 0.5);
     return check_launch(g);

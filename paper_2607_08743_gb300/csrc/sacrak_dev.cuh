@@ -38,6 +38,9 @@ struct DevPatch {
   double dx;
   double origin[3];
   double* buf[NBUF];
+  // levels > 0: the parent's time level in each ring slot, prolonged in space
+  // onto this patch (full patch layout; only the ghost shell is written)
+  double* gsh[3];
 };
 
 struct DevLevel {
@@ -256,6 +259,8 @@ void launch_sommerfeld(const GhostArgs& a, int npatches, long long max_shell, cu
 void launch_constraints(const ConsArgs& a, int ntiles, double* out5, cudaStream_t st);
 void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cudaStream_t st);
 void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st);
+void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,
+                          long long max_clusters, cudaStream_t st);
 void launch_level_advance(DevLevel* L, double dt, cudaStream_t st);
 void launch_init(const InitArgs& a, int patch, long long tot, cudaStream_t st);
 void launch_symmetrise(const DevPatch* p, const DevLevel* l, int patch, long long half_tot,
