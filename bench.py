@@ -167,8 +167,10 @@ def main():
     ap.add_argument("--courant", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--case", default="amr7", choices=["amr7", "uniform96"],
-                    help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures)")
+    ap.add_argument("--case", default="amr7", choices=["amr7", "uniform96", "mixed-error"],
+                    help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
+                         "mixed-error: the 7-level hierarchy in FP64 and mixed precision side by side")
+    ap.add_argument("--coarse-steps", type=int, default=64, help="mixed-error: coarse steps")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -191,6 +193,9 @@ def main():
 
     if args.case == "uniform96":
         uniform_case(torch, sk, args)
+        return
+    if args.case == "mixed-error":
+        mixed_error_case(torch, sk, args)
         return
 
     h = hierarchy()
@@ -297,6 +302,51 @@ def uniform_case(torch, sk, args):
     print(json.dumps({"case": "uniform96", "ms_per_rk4_step": ms,
                       "zone_updates_per_s": p.active_points / (ms * 1e-3)}), flush=True)
     g.close()
+
+
+def mixed_error_case(torch, sk, args):
+    """Evolve the 7-level binary in FP64 and in mixed precision from the same
+    data for --coarse-steps coarse steps; report per level and field the
+    max |mixed - FP64| (absolute and over the field's max |FP64|) and both
+    runs' constraint norms."""
+    import initial_data as idd
+    h = hierarchy()
+    grids = {}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(courant=args.courant, precision=prec),
+                    stream=torch.cuda.Stream())
+        g.set_initial_data(1, h.masses, h.positions)
+        grids[name] = g
+    times = {}
+    for name, g in grids.items():
+        t0 = time.perf_counter()
+        for _ in range(args.coarse_steps):
+            g.level_step(0)
+        torch.cuda.synchronize()
+        times[name] = (time.perf_counter() - t0) / args.coarse_steps
+    report = {"case": "mixed-error", "coarse_steps": args.coarse_steps, "courant": args.courant,
+              "t_final": grids["fp64"].level_time(0),
+              "s_per_coarse_step": times, "levels": []}
+    for l in range(len(h.levels)):
+        ids = [i for i, p in enumerate(h.patches) if p.level == l]
+        err = np.zeros(25)
+        rel = np.zeros(25)
+        for i in ids:
+            a = grids["fp64"].download_fields(i)[:, 3:-3, 3:-3, 3:-3]
+            m = grids["mixed"].download_fields(i)[:, 3:-3, 3:-3, 3:-3]
+            d = np.abs(m - a).max(axis=(1, 2, 3))
+            s = np.abs(a).max(axis=(1, 2, 3))
+            err = np.maximum(err, d)
+            rel = np.maximum(rel, np.where(s > 0, d / np.where(s > 0, s, 1), d))
+        report["levels"].append({
+            "level": l,
+            "max_abs_err": {n: float(v) for n, v in zip(idd.FIELD_NAMES, err)},
+            "max_rel_err": {n: float(v) for n, v in zip(idd.FIELD_NAMES, rel)},
+            "constraints_fp64": list(map(float, grids["fp64"].constraints(l))),
+            "constraints_mixed": list(map(float, grids["mixed"].constraints(l)))})
+    print(json.dumps(report), flush=True)
+    for g in grids.values():
+        g.close()
 
 
 def stage_kernel_timing(g, steps):

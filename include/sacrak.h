@@ -85,10 +85,14 @@ typedef struct {
   double origin[3];
 } sacrak_patch_desc;
 
-/* Bytes of device memory a grid of this shape needs (6 state copies per
- * patch: 3 time levels, the RK accumulator and 2 stage buffers; plus tables
- * and reduction scratch).  Returns 0 for an invalid description. */
-size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* patches);
+/* Bytes of device memory a grid of this shape needs: per patch 6 FP64 state
+ * copies (3 time levels, the RK accumulator, 2 stage buffers), 3 more on
+ * levels > 0 (the parent's time levels prolonged onto the ghost shell), and
+ * with params->precision == 1 eight FP32 copies (hi/lo split of the time
+ * levels, 2 stage buffers); plus tables and reduction scratch.  params may be
+ * NULL (FP64).  Returns 0 for an invalid description. */
+size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* patches,
+                          const sacrak_params* params);
 
 /* Create a grid on the current CUDA device.  device_arena must point to at
  * least sacrak_arena_bytes(...) bytes of device memory, 256-byte aligned.

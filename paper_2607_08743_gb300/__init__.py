@@ -65,7 +65,7 @@ def lib() -> ctypes.CDLL:
             P = ctypes.POINTER
             vp, dp = ctypes.c_void_p, P(ctypes.c_double)
             L.sacrak_arena_bytes.restype = ctypes.c_size_t
-            L.sacrak_arena_bytes.argtypes = [ctypes.c_int, ctypes.c_int, P(sacrak_patch_desc)]
+            L.sacrak_arena_bytes.argtypes = [ctypes.c_int, ctypes.c_int, P(sacrak_patch_desc), P(sacrak_params)]
             L.sacrak_grid_create.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                              P(sacrak_patch_desc), P(sacrak_params), vp, vp,
                                              ctypes.c_size_t, P(vp)]
@@ -124,9 +124,10 @@ def _descs(patches) -> ctypes.Array:
     return arr
 
 
-def arena_bytes(nlevels: int, patches) -> int:
+def arena_bytes(nlevels: int, patches, params: Optional["Params"] = None) -> int:
     d = _descs(patches)
-    return int(lib().sacrak_arena_bytes(nlevels, len(patches), d))
+    prm = params.c() if params is not None else None
+    return int(lib().sacrak_arena_bytes(nlevels, len(patches), d, ctypes.byref(prm) if prm else None))
 
 
 def _ptr(a) -> int:
@@ -166,7 +167,8 @@ class Grid:
         self.patches = list(patches)
         self.params = params
         d = _descs(self.patches)
-        nbytes = L.sacrak_arena_bytes(nlevels, len(self.patches), d)
+        prm0 = params.c()
+        nbytes = L.sacrak_arena_bytes(nlevels, len(self.patches), d, ctypes.byref(prm0))
         if nbytes == 0:
             raise SacrakError(EINVAL, "invalid patch description")
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())

@@ -17,7 +17,14 @@ __device__ __forceinline__ int fill_slot(int mode, int s, int ring) {
   return mode == 0 ? stage_in_slot(s, ring) : (mode == 1 ? ring : (ring + 1) % 3);
 }
 
+__device__ __forceinline__ void split_to(double v, float* h, float* l, long long o) {
+  const float hi = __double2float_rn(v);
+  h[o] = hi;
+  l[o] = __double2float_rn(v - (double)hi);
+}
+
 // periodic: every ghost takes the value of the active point congruent modulo n
+// (mixed precision: the split buffers the stage reads are copied as well)
 __global__ void periodic_fill_kernel(FillArgs A) {
   const DevPatch* P = A.patches + A.patch_ids[blockIdx.y];
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -27,10 +34,29 @@ __global__ void periodic_fill_kernel(FillArgs A) {
   const int si = GH + ((i - GH) % P->n[0] + P->n[0]) % P->n[0];
   const int sj = GH + ((j - GH) % P->n[1] + P->n[1]) % P->n[1];
   const int sk = GH + ((k - GH) % P->n[2] + P->n[2]) % P->n[2];
-  double* u = P->buf[fill_slot(A.mode, A.stage, A.lev->ring)];
+  const int ring = A.lev->ring;
   const long long q = i + (long long)j * P->px + (long long)k * P->plane;
   const long long qs = si + (long long)sj * P->px + (long long)sk * P->plane;
-  for (int f = 0; f < NF; ++f) u[f * P->fstride + q] = u[f * P->fstride + qs];
+  const long long fs = P->fstride;
+  if (!A.mixed) {
+    double* u = P->buf[fill_slot(A.mode, A.stage, ring)];
+    for (int f = 0; f < NF; ++f) u[f * fs + q] = u[f * fs + qs];
+    return;
+  }
+  if (A.mode == 0 && A.stage > 1) {
+    float* lo = mixed_lo_in(P, A.stage, ring);
+    for (int f = 0; f < NF; ++f) lo[f * fs + q] = lo[f * fs + qs];
+    return;
+  }
+  const int slot = A.mode == 2 ? (ring + 1) % 3 : ring;
+  double* u = P->buf[slot];
+  float* h = P->hs[slot];
+  float* l = P->ls[slot];
+  for (int f = 0; f < NF; ++f) {
+    u[f * fs + q] = u[f * fs + qs];
+    h[f * fs + q] = h[f * fs + qs];
+    l[f * fs + q] = l[f * fs + qs];
+  }
 }
 
 // frozen: ghosts of the target buffer take the ghosts of the current level
@@ -41,10 +67,27 @@ __global__ void frozen_fill_kernel(FillArgs A) {
   int i, j, k;
   shell_ijk(id, P->NX, P->NY, P->NZ, i, j, k);
   const int ring = A.lev->ring;
-  const int dst = fill_slot(A.mode, A.stage, ring);
-  if (dst == ring) return;
   const long long q = i + (long long)j * P->px + (long long)k * P->plane;
-  for (int f = 0; f < NF; ++f) P->buf[dst][f * P->fstride + q] = P->buf[ring][f * P->fstride + q];
+  const long long fs = P->fstride;
+  if (!A.mixed) {
+    const int dst = fill_slot(A.mode, A.stage, ring);
+    if (dst == ring) return;
+    for (int f = 0; f < NF; ++f) P->buf[dst][f * fs + q] = P->buf[ring][f * fs + q];
+    return;
+  }
+  if (A.mode == 0) {
+    if (A.stage == 1) return;
+    float* lo = mixed_lo_in(P, A.stage, ring);
+    for (int f = 0; f < NF; ++f) lo[f * fs + q] = P->ls[ring][f * fs + q];
+    return;
+  }
+  if (A.mode != 2) return;
+  const int nx = (ring + 1) % 3;
+  for (int f = 0; f < NF; ++f) {
+    P->buf[nx][f * fs + q] = P->buf[ring][f * fs + q];
+    P->hs[nx][f * fs + q] = P->hs[ring][f * fs + q];
+    P->ls[nx][f * fs + q] = P->ls[ring][f * fs + q];
+  }
 }
 
 // 6-point Lagrange weights at +1/4 (nodes -2..3) and -1/4 (nodes -3..2), /8192
@@ -200,13 +243,32 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
   const double* __restrict__ g0 = C->gsh[(pr + 1) % 3];
   const double* __restrict__ g1 = C->gsh[(pr + 2) % 3];
   const double* __restrict__ g2 = C->gsh[pr];
-  double* __restrict__ dst = C->buf[fill_slot(A.mode, A.stage, A.lev->ring)];
+  const int ring = A.lev->ring;
   const long long q = i + (long long)j * C->px + (long long)k * C->plane;
+  if (!A.mixed) {
+    double* __restrict__ dst = C->buf[fill_slot(A.mode, A.stage, ring)];
+    for (int f = 0; f < NF; ++f) {
+      const long long o = f * C->fstride + q;
+      double v = w1 * g1[o] + w2 * g2[o];
+      if (q3) v += w0 * g0[o];
+      dst[o] = v;
+    }
+    return;
+  }
+  // mixed precision: stage 1 (and the fill of the current level) sets the
+  // FP64 ghost and its hi/lo split; later stages set lo_s = v - hi_n
+  const bool later = (A.mode == 0 && A.stage > 1);
+  float* __restrict__ lo_s = later ? mixed_lo_in(C, A.stage, ring) : nullptr;
   for (int f = 0; f < NF; ++f) {
     const long long o = f * C->fstride + q;
     double v = w1 * g1[o] + w2 * g2[o];
     if (q3) v += w0 * g0[o];
-    dst[o] = v;
+    if (later) {
+      lo_s[o] = __double2float_rn(v - (double)C->hs[ring][o]);
+    } else {
+      C->buf[ring][o] = v;
+      split_to(v, C->hs[ring], C->ls[ring], o);
+    }
   }
 }
 
@@ -246,6 +308,7 @@ __global__ void __launch_bounds__(128) restrict_kernel(FillArgs A) {
       v += w[c] * vy;
     }
     up[f * P->fstride + qp] = v;
+    if (A.mixed) split_to(v, P->hs[A.plev->ring], P->ls[A.plev->ring], f * P->fstride + qp);
   }
 }
 
@@ -268,14 +331,33 @@ __global__ void exchange_kernel(ExchArgs E) {
   const bool b_act = ib >= 0 && ib < Pb->n[0] && jb >= 0 && jb < Pb->n[1] && kb >= 0 && kb < Pb->n[2];
   if (!a_act && !b_act) return;
   const int ring = E.lev->ring;
-  const int slot = fill_slot(E.mode, E.stage, ring);
-  double* ua = Pa->buf[slot];
-  double* ub = Pb->buf[slot];
   const long long qa = I + (long long)J * Pa->px + (long long)K * Pa->plane;
   const long long qb = (ib + GH) + (long long)(jb + GH) * Pb->px + (long long)(kb + GH) * Pb->plane;
+  if (E.mixed && E.mode == 0 && E.stage > 1) {
+    // stage state hi_n + lo_s: move lo_s (and average the stage values)
+    float* la = mixed_lo_in(Pa, E.stage, ring);
+    float* lb = mixed_lo_in(Pb, E.stage, ring);
+    for (int f = 0; f < NF; ++f) {
+      const long long oa = f * Pa->fstride + qa, ob = f * Pb->fstride + qb;
+      if (a_act && b_act) {
+        const float m = 0.5f * ((Pa->hs[ring][oa] + la[oa]) + (Pb->hs[ring][ob] + lb[ob]));
+        la[oa] = m - Pa->hs[ring][oa];
+        lb[ob] = m - Pb->hs[ring][ob];
+      } else if (b_act) {
+        la[oa] = (Pb->hs[ring][ob] - Pa->hs[ring][oa]) + lb[ob];
+      } else {
+        lb[ob] = (Pa->hs[ring][oa] - Pb->hs[ring][ob]) + la[oa];
+      }
+    }
+    return;
+  }
+  const int slot = E.mixed ? ring : fill_slot(E.mode, E.stage, ring);
+  double* ua = Pa->buf[slot];
+  double* ub = Pb->buf[slot];
   for (int f = 0; f < NF; ++f) {
-    double* pa = ua + f * Pa->fstride + qa;
-    double* pb = ub + f * Pb->fstride + qb;
+    const long long oa = f * Pa->fstride + qa, ob = f * Pb->fstride + qb;
+    double* pa = ua + oa;
+    double* pb = ub + ob;
     if (a_act && b_act) {
       double m = 0.5 * (*pa + *pb);
       *pa = m;
@@ -284,6 +366,10 @@ __global__ void exchange_kernel(ExchArgs E) {
       *pa = *pb;
     } else {
       *pb = *pa;
+    }
+    if (E.mixed) {
+      split_to(*pa, Pa->hs[slot], Pa->ls[slot], oa);
+      split_to(*pb, Pb->hs[slot], Pb->ls[slot], ob);
     }
   }
 }

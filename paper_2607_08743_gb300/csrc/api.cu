@@ -31,7 +31,8 @@ struct Layout {
   size_t ntiles = 0, scratch_doubles = 0;
 };
 
-bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, Layout& L, std::string& why) {
+bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed, Layout& L,
+              std::string& why) {
   if (nlevels < 1 || npatches < 1 || !pd) {
     why = "need at least one level and one patch";
     return false;
@@ -95,6 +96,7 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, Layout& L,
     L.patch_state[p] = off;
     const int nbuf = NBUF + (pd[p].level > 0 ? 3 : 0);  // + cached prolongation slots
     off = align_up(off + (size_t)nbuf * NF * fs * sizeof(double), 256);
+    if (mixed) off = align_up(off + (size_t)8 * NF * fs * sizeof(float), 256);  // hs[3] ls[3] la lb
   }
   L.total = off;
   return true;
@@ -116,6 +118,7 @@ struct sacrak_grid {
   std::vector<size_t> lvl_tile_off, lvl_ntiles;
   std::vector<long long> lvl_max_shell, lvl_max_restrict, lvl_max_clusters;
   bool shells_dirty = true;
+  bool split_dirty = true;  // mixed precision: hi/lo of the current levels stale
   DevPatch* d_patches;
   DevLevel* d_levels;
   int* d_ids;
@@ -200,11 +203,9 @@ void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones) {
     }
     cudaEventRecord(g->ev[g->ev_used].first, g->stream);
   }
-#ifdef SACRAK_HAVE_MIXED
   if (g->prm.precision == 1)
     launch_stage_mixed(a, g->stream);
   else
-#endif
     launch_stage_fp64(a, g->stream);
   if (g->prof) {
     cudaEventRecord(g->ev[g->ev_used].second, g->stream);
@@ -239,6 +240,7 @@ FillArgs fill_args(sacrak_grid* g, int l, int mode, int stage, double s0, double
   a.mode = mode;
   a.stage = stage;
   ghost_time_weights(s0, ds, mode == 0 ? stage : 0, a.wq, a.wl);
+  a.mixed = g->prm.precision == 1;
   return a;
 }
 
@@ -278,6 +280,7 @@ void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double d
       for (int d = 0; d < 3; ++d) e.off[d] = off[d];
       e.mode = mode;
       e.stage = stage;
+      e.mixed = g->prm.precision == 1;
       launch_exchange(e, (long long)A.NX * A.NY * A.NZ, g->stream);
     }
 }
@@ -289,8 +292,16 @@ void refresh_shells(sacrak_grid* g, int l) {
                        (int)g->lvl_ids[l].size(), g->lvl_max_clusters[l], g->stream);
 }
 
-// after new data: every child level's cache for its parent's current slot
+// after new data: every child level's cache for its parent's current slot,
+// and (mixed precision) the hi/lo split of every current level
 void refresh_all_shells(sacrak_grid* g) {
+  if (g->prm.precision == 1 && g->split_dirty) {
+    for (int p = 0; p < g->npatches; ++p) {
+      const DevPatch& P = g->hp[p];
+      launch_split(g->d_patches, g->d_levels, p, (long long)P.NX * P.NY * P.NZ, g->stream);
+    }
+    g->split_dirty = false;
+  }
   if (!g->shells_dirty) return;
   for (int l = 1; l < g->nlevels; ++l) refresh_shells(g, l);
   g->shells_dirty = false;
@@ -320,7 +331,10 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
       ga.dt = dt;
       ga.prm = a.prm;
       ga.err = g->d_err;
-      launch_sommerfeld(ga, np, g->lvl_max_shell[l], g->stream);
+      if (g->prm.precision == 1)
+        launch_sommerfeld_mixed(ga, np, g->lvl_max_shell[l], g->stream);
+      else
+        launch_sommerfeld(ga, np, g->lvl_max_shell[l], g->stream);
     }
   }
   // ghosts of the new time level for periodic / frozen outer boundaries
@@ -371,10 +385,12 @@ sacrak_status read_level(sacrak_grid* g, int l, DevLevel* out) {
 
 extern "C" {
 
-size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* patches) {
+size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* patches,
+                          const sacrak_params* params) {
   Layout L;
   std::string why;
-  if (!describe(nlevels, npatches, patches, L, why)) return 0;
+  const int mixed = params ? (params->precision == 1) : 0;
+  if (!describe(nlevels, npatches, patches, mixed, L, why)) return 0;
   return L.total;
 }
 
@@ -386,15 +402,13 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   *out = nullptr;
   Layout L;
   std::string why;
-  if (!describe(nlevels, npatches, pd, L, why)) return SACRAK_EINVAL;
+  if (!describe(nlevels, npatches, pd, params->precision == 1, L, why)) return SACRAK_EINVAL;
   if (arena_bytes < L.total || ((uintptr_t)device_arena % 256) != 0) return SACRAK_EINVAL;
   const sacrak_params& p = *params;
   if (p.lapse < 0 || p.lapse > 1 || p.shift < 0 || p.shift > 1 || p.bc < 0 || p.bc > 2 ||
       p.precision < 0 || p.precision > 1 || !(p.courant > 0.0) || !(p.sigma_ko >= 0.0))
     return SACRAK_EINVAL;
-#ifndef SACRAK_HAVE_MIXED
-  if (p.precision == 1) return SACRAK_EINVAL;
-#endif
+
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, device_arena) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
     cudaGetLastError();
@@ -434,6 +448,17 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
       P.gsh[b] = P.level > 0 ? (double*)(g->arena + L.patch_state[i] +
                                         (size_t)(NBUF + b) * NF * P.fstride * sizeof(double))
                              : nullptr;
+    if (p.precision == 1) {
+      const size_t nb = (size_t)(NBUF + (P.level > 0 ? 3 : 0)) * NF * P.fstride * sizeof(double);
+      float* m0 = (float*)(g->arena + align_up(L.patch_state[i] + nb, 256));
+      const size_t fl = (size_t)NF * P.fstride;
+      for (int b = 0; b < 3; ++b) {
+        P.hs[b] = m0 + (size_t)b * fl;
+        P.ls[b] = m0 + (size_t)(3 + b) * fl;
+      }
+      P.la = m0 + 6 * fl;
+      P.lb = m0 + 7 * fl;
+    }
     g->lvl_ids[P.level].push_back(i);
   }
   // parents: the patch of the level above containing the child with margin
@@ -569,6 +594,7 @@ sacrak_status sacrak_set_initial_data(sacrak_grid* g, int kind, int npunct, cons
   sacrak_status st = reset_levels(g);
   if (st != SACRAK_OK) return st;
   g->shells_dirty = true;
+  g->split_dirty = true;
   InitArgs a;
   std::memset(&a, 0, sizeof a);
   a.patches = g->d_patches;
@@ -617,6 +643,7 @@ sacrak_status sacrak_upload_fields(sacrak_grid* g, int patch, const double* src)
   if (st != SACRAK_OK) return st;
   lv.nvalid = 1;
   g->shells_dirty = true;
+  g->split_dirty = true;
   CK(cudaMemcpyAsync(&g->d_levels[P.level], &lv, sizeof lv, cudaMemcpyHostToDevice, g->stream));
   CK(cudaStreamSynchronize(g->stream));  // lv is a host stack variable
   g->invalid = false;
@@ -641,6 +668,7 @@ sacrak_status sacrak_rhs(sacrak_grid* g, int patch, double* dst) {
   if (patch < 0 || patch >= g->npatches || !dst) return fail(g, SACRAK_EINVAL, "bad patch or pointer");
   if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
   const DevPatch& P = g->hp[patch];
+  refresh_all_shells(g);
   CK(cudaMemsetAsync(P.buf[B_S1], 0, (size_t)NF * P.fstride * sizeof(double), g->stream));
   // launch over this patch's tiles only
   const int l = P.level;

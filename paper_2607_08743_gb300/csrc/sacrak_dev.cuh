@@ -41,6 +41,13 @@ struct DevPatch {
   // levels > 0: the parent's time level in each ring slot, prolonged in space
   // onto this patch (full patch layout; only the ghost shell is written)
   double* gsh[3];
+  // mixed precision only (null otherwise): each time level split into FP32
+  // hi + lo (hs, ls, same ring slots as buf), and the FP32 low parts of the
+  // stage states u_s = hi_n + lo_s (la, lb; stage s reads ls[ring], la, lb, la)
+  float* hs[3];
+  float* ls[3];
+  float* la;
+  float* lb;
 };
 
 struct DevLevel {
@@ -81,6 +88,14 @@ __host__ __device__ inline double flat_value(int f) {
 __host__ __device__ constexpr int S2(int i, int j) {
   return (i == j) ? (i == 0 ? 0 : (i == 1 ? 3 : 5))
                   : ((i + j) == 1 ? 1 : ((i + j) == 2 ? 2 : 4));
+}
+
+// mixed precision: FP32 low-part buffer read (in) / written (out) by stage s
+__host__ __device__ inline float* mixed_lo_in(const DevPatch* P, int s, int ring) {
+  return s == 1 ? P->ls[ring] : (s == 3 ? P->lb : P->la);
+}
+__host__ __device__ inline float* mixed_lo_out(const DevPatch* P, int s) {
+  return s == 2 ? P->lb : P->la;  // stage 4 writes the split of the new level instead
 }
 
 // slot of the stage input / output buffer for RK4 stage s (1..4)
@@ -229,6 +244,7 @@ struct FillArgs {
   // prolongation: weights of the parent's (oldest, middle, newest) time levels,
   // for three valid levels (wq) and for two (wl, oldest weight 0)
   double wq[3], wl[3];
+  int mixed;  // also maintain the FP32 split buffers
 };
 
 struct ExchArgs {
@@ -237,6 +253,7 @@ struct ExchArgs {
   int a, b;
   int off[3];  // b's cell index of a's cell 0
   int mode, stage;
+  int mixed;
 };
 
 struct InitArgs {
@@ -261,6 +278,9 @@ void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cu
 void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st);
 void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,
                           long long max_clusters, cudaStream_t st);
+void launch_sommerfeld_mixed(const GhostArgs& a, int npatches, long long max_shell, cudaStream_t st);
+void launch_split(const DevPatch* patches, const DevLevel* levels, int patch, long long tot,
+                  cudaStream_t st);
 void launch_level_advance(DevLevel* L, double dt, cudaStream_t st);
 void launch_init(const InitArgs& a, int patch, long long tot, cudaStream_t st);
 void launch_symmetrise(const DevPatch* p, const DevLevel* l, int patch, long long half_tot,

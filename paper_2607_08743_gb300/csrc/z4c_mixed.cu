@@ -1,0 +1,571 @@
+// Mixed-precision Z4c RHS fused with the RK4 stage update.
+//
+// Every time level is kept in FP64 and, beside it, split into two FP32 arrays
+// hi + lo (hi = the FP32 rounding of the value, lo = the FP32 rounding of the
+// rest): hi + lo carries ~48 bits.  A stage state is represented as
+// u_s = hi_n + lo_s with lo_s = lo_n + c_s dt k (FP32), so no stage ever
+// converts from FP64.  Derivatives, advection, dissipation and the Z4c
+// sources run in FP32 on differences against the centre value,
+// (hi_k - hi_0) + (lo_k - lo_0): exact in hi for nearby values and accurate to
+// FP32 relative to the difference itself, so 1e-10 perturbations of O(1)
+// fields survive.  FP64 is kept for the RK4 accumulator y, the new time level
+// u_{n+1} = y + dt/6 k4 and its algebraic constraints (det gt = 1, trace-free
+// At, W floor); the intermediate stage states are enforced in FP32 on the
+// deviations from the flat metric.
+//
+// The same equations as z4c_fp64.cu (Sec. 2.1.1, 2.2 of the SACRA-K paper).
+#include <math.h>
+
+#include "sacrak_dev.cuh"
+
+namespace sacrak {
+namespace {
+
+// ------------------------------------------------------------------ stencils
+
+__device__ __forceinline__ float pdiff(const float* __restrict__ H, const float* __restrict__ L,
+                                       long long a, long long b) {
+  return (__ldg(H + a) - __ldg(H + b)) + (__ldg(L + a) - __ldg(L + b));
+}
+__device__ __forceinline__ float cdiff(const float* __restrict__ H, const float* __restrict__ L,
+                                       long long a, float h0, float l0) {
+  return (__ldg(H + a) - h0) + (__ldg(L + a) - l0);
+}
+// 8 (f1 - f-1) - (f2 - f-2); times 1/(12 h)
+__device__ __forceinline__ float d1f(const float* H, const float* L, long long q, long long s) {
+  return 8.0f * pdiff(H, L, q + s, q - s) - pdiff(H, L, q + 2 * s, q - 2 * s);
+}
+// 16 (f1 + f-1) - (f2 + f-2) - 30 f0 on centre differences; times 1/(12 h^2)
+__device__ __forceinline__ float d2f(const float* H, const float* L, long long q, long long s,
+                                     float h0, float l0) {
+  float a = cdiff(H, L, q + s, h0, l0) + cdiff(H, L, q - s, h0, l0);
+  float b = cdiff(H, L, q + 2 * s, h0, l0) + cdiff(H, L, q - 2 * s, h0, l0);
+  return 16.0f * a - b;
+}
+// nested D_a(D_b f); times 1/(144 h^2)
+__device__ __forceinline__ float d11f(const float* H, const float* L, long long q, long long sa,
+                                      long long sb) {
+  float p1 = d1f(H, L, q + sa, sb), m1 = d1f(H, L, q - sa, sb);
+  float p2 = d1f(H, L, q + 2 * sa, sb), m2 = d1f(H, L, q - 2 * sa, sb);
+  return 8.0f * (p1 - m1) - (p2 - m2);
+}
+// lopsided upwind on centre differences; times 1/(12 h)
+__device__ __forceinline__ float dupf(const float* H, const float* L, long long q, long long st,
+                                      float b, float h0, float l0) {
+  long long s = b > 0.0f ? st : -st;
+  float v = -3.0f * cdiff(H, L, q - s, h0, l0) + 18.0f * cdiff(H, L, q + s, h0, l0) -
+            6.0f * cdiff(H, L, q + 2 * s, h0, l0) + cdiff(H, L, q + 3 * s, h0, l0);
+  return b > 0.0f ? v : -v;
+}
+__device__ __forceinline__ float delta6f(const float* H, const float* L, long long q, long long st,
+                                         float h0, float l0) {
+  float a = cdiff(H, L, q + 3 * st, h0, l0) + cdiff(H, L, q - 3 * st, h0, l0);
+  float b = cdiff(H, L, q + 2 * st, h0, l0) + cdiff(H, L, q - 2 * st, h0, l0);
+  float c = cdiff(H, L, q + st, h0, l0) + cdiff(H, L, q - st, h0, l0);
+  return (a - 6.0f * b) + 15.0f * c;
+}
+
+__device__ __forceinline__ void sym_inv_f(const float g[6], float gu[6]) {
+  float c0 = g[3] * g[5] - g[4] * g[4];
+  float c1 = g[2] * g[4] - g[1] * g[5];
+  float c2 = g[1] * g[4] - g[2] * g[3];
+  float id = 1.0f / (g[0] * c0 + g[1] * c1 + g[2] * c2);
+  gu[0] = c0 * id;
+  gu[1] = c1 * id;
+  gu[2] = c2 * id;
+  gu[3] = (g[0] * g[5] - g[2] * g[2]) * id;
+  gu[4] = (g[1] * g[2] - g[0] * g[4]) * id;
+  gu[5] = (g[0] * g[3] - g[1] * g[1]) * id;
+}
+__device__ __forceinline__ float symc(const float S[6], const float T[6]) {
+  return S[0] * T[0] + S[3] * T[3] + S[5] * T[5] + 2.0f * (S[1] * T[1] + S[2] * T[2] + S[4] * T[4]);
+}
+
+// ------------------------------------------------------------------ the RHS
+
+// Z4c RHS of one point in FP32 from the split state (H, L); r[f] gets the
+// full RHS (sources + advection + dissipation).
+__device__ __forceinline__ void z4c_rhs_point_mixed(const float* __restrict__ H,
+                                                    const float* __restrict__ L, long long q,
+                                                    long long sy, long long sz, long long fs,
+                                                    float h, const DevParams& prm, float r[NF]) {
+  const long long st[3] = {1, sy, sz};
+  const float c1 = 1.0f / (12.0f * h);
+  const float c2 = c1 / h;
+  const float c11 = c1 * c1;
+#define HF(f) (H + (long long)(f) * fs)
+#define LF(f) (L + (long long)(f) * fs)
+#define CV(f) (__ldg(HF(f) + q) + __ldg(LF(f) + q))
+  const float W = CV(F_W), al = CV(F_ALP);
+  const float Kh = CV(F_KH), Th = CV(F_TH);
+  float gt[6], At[6], Gam[3], be[3], Bv[3];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    gt[a] = CV(F_GXX + a);
+    At[a] = CV(F_AXX + a);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Gam[i] = CV(F_GAMX + i);
+    be[i] = CV(F_BETX + i);
+    Bv[i] = CV(F_BX + i);
+  }
+  float gtu[6];
+  sym_inv_f(gt, gtu);
+
+  // first derivatives
+  float dgt[3][6], dW[3], dal[3], dGam[3][3], dbe[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) dgt[d][a] = d1f(HF(F_GXX + a), LF(F_GXX + a), q, st[d]) * c1;
+    dW[d] = d1f(HF(F_W), LF(F_W), q, st[d]) * c1;
+    dal[d] = d1f(HF(F_ALP), LF(F_ALP), q, st[d]) * c1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dGam[d][i] = d1f(HF(F_GAMX + i), LF(F_GAMX + i), q, st[d]) * c1;
+      dbe[d][i] = d1f(HF(F_BETX + i), LF(F_BETX + i), q, st[d]) * c1;
+    }
+  }
+  float Gl[3][6], Gu[3][6], Gd[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = j; k < 3; ++k)
+        Gl[i][S2(j, k)] = 0.5f * (dgt[j][S2(i, k)] + dgt[k][S2(i, j)] - dgt[i][S2(j, k)]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+      Gu[i][a] = gtu[S2(i, 0)] * Gl[0][a] + gtu[S2(i, 1)] * Gl[1][a] + gtu[S2(i, 2)] * Gl[2][a];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Gd[i] = symc(gtu, Gu[i]);
+  float X[3][3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        X[j][k][l] = gtu[S2(l, 0)] * Gl[j][S2(k, 0)] + gtu[S2(l, 1)] * Gl[j][S2(k, 1)] +
+                     gtu[S2(l, 2)] * Gl[j][S2(k, 2)];
+  float Ric[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int ij = S2(i, j);
+      const float* fH = HF(F_GXX + ij);
+      const float* fL = LF(F_GXX + ij);
+      const float h0 = __ldg(fH + q), l0 = __ldg(fL + q);
+      float dd[6];
+      dd[0] = d2f(fH, fL, q, st[0], h0, l0) * c2;
+      dd[3] = d2f(fH, fL, q, st[1], h0, l0) * c2;
+      dd[5] = d2f(fH, fL, q, st[2], h0, l0) * c2;
+      dd[1] = d11f(fH, fL, q, st[0], st[1]) * c11;
+      dd[2] = d11f(fH, fL, q, st[0], st[2]) * c11;
+      dd[4] = d11f(fH, fL, q, st[1], st[2]) * c11;
+      float rr = -0.5f * symc(gtu, dd);
+      float t2 = 0.0f, t3 = 0.0f, t4 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        t2 += gt[S2(k, i)] * dGam[j][k] + gt[S2(k, j)] * dGam[i][k];
+        t3 += Gd[k] * (Gl[i][S2(j, k)] + Gl[j][S2(i, k)]);
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+          t4 += Gu[k][S2(l, i)] * X[j][k][l] + Gu[k][S2(l, j)] * X[i][k][l] +
+                Gu[k][S2(i, l)] * X[k][j][l];
+      Ric[ij] = rr + 0.5f * t2 + 0.5f * t3 + t4;
+    }
+  const float iW = 1.0f / W;
+  float DDW[6], DDal[6];
+  {
+    const float* WH = HF(F_W);
+    const float* WL = LF(F_W);
+    const float* aH = HF(F_ALP);
+    const float* aL = LF(F_ALP);
+    const float wh = __ldg(WH + q), wl = __ldg(WL + q), ah = __ldg(aH + q), alo = __ldg(aL + q);
+    float ddW[6], dda[6];
+    ddW[0] = d2f(WH, WL, q, st[0], wh, wl) * c2;
+    ddW[3] = d2f(WH, WL, q, st[1], wh, wl) * c2;
+    ddW[5] = d2f(WH, WL, q, st[2], wh, wl) * c2;
+    ddW[1] = d11f(WH, WL, q, st[0], st[1]) * c11;
+    ddW[2] = d11f(WH, WL, q, st[0], st[2]) * c11;
+    ddW[4] = d11f(WH, WL, q, st[1], st[2]) * c11;
+    dda[0] = d2f(aH, aL, q, st[0], ah, alo) * c2;
+    dda[3] = d2f(aH, aL, q, st[1], ah, alo) * c2;
+    dda[5] = d2f(aH, aL, q, st[2], ah, alo) * c2;
+    dda[1] = d11f(aH, aL, q, st[0], st[1]) * c11;
+    dda[2] = d11f(aH, aL, q, st[0], st[2]) * c11;
+    dda[4] = d11f(aH, aL, q, st[1], st[2]) * c11;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      DDW[a] = ddW[a] - (Gu[0][a] * dW[0] + Gu[1][a] * dW[1] + Gu[2][a] * dW[2]);
+      DDal[a] = dda[a] - (Gu[0][a] * dal[0] + Gu[1][a] * dal[1] + Gu[2][a] * dal[2]);
+    }
+  }
+  float dWW[6], dWa[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      dWW[S2(i, j)] = dW[i] * dW[j];
+      dWa[S2(i, j)] = dW[i] * dal[j] + dW[j] * dal[i];
+    }
+  const float trDDW = symc(gtu, DDW);
+  const float dWdW = symc(gtu, dWW);
+  const float dWda = 0.5f * symc(gtu, dWa);
+  const float trDDa = symc(gtu, DDal);
+  float DDa[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    Ric[a] += (DDW[a] + gt[a] * trDDW) * iW - 2.0f * gt[a] * dWdW * (iW * iW);
+    DDa[a] = DDal[a] + (dWa[a] - gt[a] * dWda) * iW;
+  }
+  const float Rsc = W * W * symc(gtu, Ric);
+  const float Lapa = W * W * trDDa - W * dWda;
+
+  const float K = Kh + 2.0f * Th;
+  const float divb = dbe[0][0] + dbe[1][1] + dbe[2][2];
+  float Am[3][3], Atu[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Am[i][j] = gtu[S2(i, 0)] * At[S2(0, j)] + gtu[S2(i, 1)] * At[S2(1, j)] + gtu[S2(i, 2)] * At[S2(2, j)];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j)
+      Atu[S2(i, j)] = Am[i][0] * gtu[S2(0, j)] + Am[i][1] * gtu[S2(1, j)] + Am[i][2] * gtu[S2(2, j)];
+  const float AA = symc(At, Atu);
+
+  r[F_W] = W * (1.0f / 3.0f) * (al * K - divb);
+  {
+    float X2[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) X2[a] = al * Ric[a] - DDa[a];
+    const float trX3 = symc(gtu, X2) * (1.0f / 3.0f);
+    const float W2 = W * W;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const int ij = S2(i, j);
+        float s = -2.0f * al * At[ij];
+        float sA = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          s += gt[S2(i, k)] * dbe[j][k] + gt[S2(j, k)] * dbe[i][k];
+          sA += At[S2(i, k)] * dbe[j][k] + At[S2(j, k)] * dbe[i][k];
+        }
+        r[F_GXX + ij] = s - (2.0f / 3.0f) * gt[ij] * divb;
+        float AikAkj = At[S2(i, 0)] * Am[0][j] + At[S2(i, 1)] * Am[1][j] + At[S2(i, 2)] * Am[2][j];
+        r[F_AXX + ij] = sA - (2.0f / 3.0f) * At[ij] * divb + W2 * (X2[ij] - gt[ij] * trX3) +
+                        al * (K * At[ij] - 2.0f * AikAkj);
+      }
+  }
+  const float k1 = (float)prm.kappa1, k2 = (float)prm.kappa2;
+  const float alk1 = al * k1;
+  r[F_KH] = -Lapa + al * (AA + K * K * (1.0f / 3.0f)) + alk1 * (1.0f - k2) * Th;
+  r[F_TH] = 0.5f * al * (Rsc - AA + (2.0f / 3.0f) * K * K) - alk1 * (2.0f + k2) * Th;
+  {
+    float ddb[3][6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float* fH = HF(F_BETX + i);
+      const float* fL = LF(F_BETX + i);
+      const float h0 = __ldg(fH + q), l0 = __ldg(fL + q);
+      ddb[i][0] = d2f(fH, fL, q, st[0], h0, l0) * c2;
+      ddb[i][3] = d2f(fH, fL, q, st[1], h0, l0) * c2;
+      ddb[i][5] = d2f(fH, fL, q, st[2], h0, l0) * c2;
+      ddb[i][1] = d11f(fH, fL, q, st[0], st[1]) * c11;
+      ddb[i][2] = d11f(fH, fL, q, st[0], st[2]) * c11;
+      ddb[i][4] = d11f(fH, fL, q, st[1], st[2]) * c11;
+    }
+    float ddivb[3], dKh[3], dTh[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      ddivb[j] = ddb[0][S2(j, 0)] + ddb[1][S2(j, 1)] + ddb[2][S2(j, 2)];
+      dKh[j] = d1f(HF(F_KH), LF(F_KH), q, st[j]) * c1;
+      dTh[j] = d1f(HF(F_TH), LF(F_TH), q, st[j]) * c1;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float inner = symc(Gu[i], Atu);
+      float s = 0.0f, t = 0.0f, v = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        s += Atu[S2(i, j)] * dal[j];
+        t += Atu[S2(i, j)] * dW[j];
+        v += gtu[S2(i, j)] * (2.0f * dKh[j] + dTh[j]);
+      }
+      inner -= 3.0f * t * iW + v * (1.0f / 3.0f);
+      float g = -2.0f * s + 2.0f * al * inner;
+      g += symc(gtu, ddb[i]);
+      g += (gtu[S2(i, 0)] * ddivb[0] + gtu[S2(i, 1)] * ddivb[1] + gtu[S2(i, 2)] * ddivb[2]) * (1.0f / 3.0f);
+      g += (2.0f / 3.0f) * Gd[i] * divb;
+      g -= Gd[0] * dbe[0][i] + Gd[1] * dbe[1][i] + Gd[2] * dbe[2][i];
+      g -= 2.0f * alk1 * (Gam[i] - Gd[i]);
+      r[F_GAMX + i] = g;
+    }
+  }
+  if (prm.lapse == 1)
+    r[F_ALP] = -al * al * K;
+  else
+    r[F_ALP] = -2.0f * al * (prm.lapse_uses_khat ? Kh : K);
+  const float eta = (float)prm.eta;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r[F_BETX + i] = 0.75f * Bv[i];
+    r[F_BX + i] = r[F_GAMX + i] - eta * Bv[i];
+  }
+  const float cko = (float)(prm.sigma_ko / (64.0 * (double)h));
+#pragma unroll 1
+  for (int f = 0; f < NF; ++f) {
+    const float* fH = HF(f);
+    const float* fL = LF(f);
+    const float h0 = __ldg(fH + q), l0 = __ldg(fL + q);
+    float adv = be[0] * dupf(fH, fL, q, st[0], be[0], h0, l0) + be[1] * dupf(fH, fL, q, st[1], be[1], h0, l0) +
+                be[2] * dupf(fH, fL, q, st[2], be[2], h0, l0);
+    float ko = delta6f(fH, fL, q, st[0], h0, l0) + delta6f(fH, fL, q, st[1], h0, l0) +
+               delta6f(fH, fL, q, st[2], h0, l0);
+    r[f] += adv * c1 + ko * cko;
+  }
+  if (prm.shift == 1) {
+#pragma unroll
+    for (int f = F_BETX; f < NF; ++f) r[f] = 0.0f;
+  }
+#undef HF
+#undef LF
+#undef CV
+}
+
+// ------------------------------------------------------------------ epilogue
+
+__device__ __forceinline__ void split_store(double v, float* __restrict__ h, float* __restrict__ l,
+                                            long long o) {
+  const float hi = __double2float_rn(v);
+  h[o] = hi;
+  l[o] = __double2float_rn(v - (double)hi);
+}
+
+// FP64 algebraic constraints of the new time level (same as the FP64 path)
+__device__ __forceinline__ void enforce_point_d(double v[NF], double w_floor) {
+  double g[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) g[a] = v[F_GXX + a];
+  double det = g[0] * (g[3] * g[5] - g[4] * g[4]) - g[1] * (g[1] * g[5] - g[4] * g[2]) +
+               g[2] * (g[1] * g[4] - g[3] * g[2]);
+  double fac = 1.0 / cbrt(det);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) g[a] *= fac;
+  double c0 = g[3] * g[5] - g[4] * g[4], c1 = g[2] * g[4] - g[1] * g[5], c2 = g[1] * g[4] - g[2] * g[3];
+  double id = 1.0 / (g[0] * c0 + g[1] * c1 + g[2] * c2);
+  double gu[6] = {c0 * id, c1 * id, c2 * id, (g[0] * g[5] - g[2] * g[2]) * id,
+                  (g[1] * g[2] - g[0] * g[4]) * id, (g[0] * g[3] - g[1] * g[1]) * id};
+  const double* A = v + F_AXX;
+  double tr3 = (gu[0] * A[0] + gu[3] * A[3] + gu[5] * A[5] + 2.0 * (gu[1] * A[1] + gu[2] * A[2] + gu[4] * A[4])) *
+               (1.0 / 3.0);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    v[F_GXX + a] = g[a];
+    v[F_AXX + a] -= g[a] * tr3;
+  }
+  if (v[F_W] < w_floor) v[F_W] = w_floor;
+}
+
+// FP32 algebraic constraints of a stage state u = hi + lo, applied to lo:
+// det gt = 1 through the deviation h = gt - 1 (det - 1 = tr h + second and
+// third invariants, so small deviations keep their precision), trace-free At,
+// W floor.
+__device__ __forceinline__ void enforce_stage_f(const float hi[NF], float lo[NF], float w_floor) {
+  float hd[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const bool diag = (a == 0 || a == 3 || a == 5);
+    hd[a] = (diag ? hi[F_GXX + a] - 1.0f : hi[F_GXX + a]) + lo[F_GXX + a];
+  }
+  const float tr = hd[0] + hd[3] + hd[5];
+  const float q2 = hd[0] * hd[3] + hd[0] * hd[5] + hd[3] * hd[5] - hd[1] * hd[1] - hd[2] * hd[2] -
+                   hd[4] * hd[4];
+  const float q3 = hd[0] * (hd[3] * hd[5] - hd[4] * hd[4]) - hd[1] * (hd[1] * hd[5] - hd[4] * hd[2]) +
+                   hd[2] * (hd[1] * hd[4] - hd[3] * hd[2]);
+  const float fm1 = expm1f(-log1pf(tr + q2 + q3) * (1.0f / 3.0f));  // det^(-1/3) - 1
+  float g[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float gv = hi[F_GXX + a] + lo[F_GXX + a];
+    lo[F_GXX + a] += gv * fm1;
+    g[a] = gv * (1.0f + fm1);
+  }
+  float gu[6], A[6];
+  sym_inv_f(g, gu);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) A[a] = hi[F_AXX + a] + lo[F_AXX + a];
+  const float tr3 = symc(gu, A) * (1.0f / 3.0f);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) lo[F_AXX + a] -= g[a] * tr3;
+  if (hi[F_W] + lo[F_W] < w_floor) lo[F_W] = w_floor - hi[F_W];
+}
+
+__device__ __forceinline__ void rk_update_mixed(const DevPatch* P, int s, int ring, double dt,
+                                                long long q, const float k[NF], double w_floor,
+                                                unsigned* err) {
+  const long long fs = P->fstride;
+  const float* __restrict__ Hn = P->hs[ring];
+  const float* __restrict__ Ln = P->ls[ring];
+  double* __restrict__ y = P->buf[B_Y];
+  bool bad = false;
+  if (s < 4) {
+    const double bw = (s == 1) ? (1.0 / 6.0) : (1.0 / 3.0);
+    const double bdt = bw * dt;
+    const float cdt = (float)((s == 3 ? 1.0 : 0.5) * dt);
+    const double* __restrict__ Un = P->buf[ring];
+    float* __restrict__ Lo = mixed_lo_out(P, s);
+    float hi[NF], lo[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const long long o = f * fs + q;
+      const double yn = (s == 1 ? Un[o] : y[o]) + bdt * (double)k[f];
+      y[o] = yn;
+      hi[f] = Hn[o];
+      lo[f] = Ln[o] + cdt * k[f];
+      bad |= !isfinite(yn);
+    }
+    enforce_stage_f(hi, lo, (float)w_floor);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      Lo[f * fs + q] = lo[f];
+      bad |= !isfinite(lo[f]);
+    }
+  } else {
+    const double bdt = dt / 6.0;
+    const int nx = (ring + 1) % 3;
+    double* __restrict__ Un1 = P->buf[nx];
+    float* __restrict__ Hx = P->hs[nx];
+    float* __restrict__ Lx = P->ls[nx];
+    double v[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) v[f] = y[f * fs + q] + bdt * (double)k[f];
+    enforce_point_d(v, w_floor);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const long long o = f * fs + q;
+      Un1[o] = v[f];
+      split_store(v[f], Hx, Lx, o);
+      bad |= !isfinite(v[f]);
+    }
+  }
+  if (bad) atomicOr(err, (unsigned)ERR_NONFINITE);
+}
+
+template <int MODE>  // 0: RK stage, 1: RHS only (FP64 output in S1)
+__global__ void __launch_bounds__(128) z4c_stage_mixed_kernel(StageArgs A) {
+  const Tile tl = A.tiles[blockIdx.x];
+  const DevPatch* P = A.patches + tl.patch;
+  const int i = tl.x0 + (threadIdx.x & 31);
+  const int j = tl.y0 + (threadIdx.x >> 5);
+  const int k = tl.z0;
+  if (i >= P->n[0] || j >= P->n[1] || k >= P->n[2]) return;
+  const int ring = A.lev->ring;
+  const int s = A.stage;
+  const long long sy = P->px, sz = P->plane, fs = P->fstride;
+  const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
+  const float* __restrict__ H = P->hs[ring];
+  const float* __restrict__ L = MODE ? P->ls[ring] : mixed_lo_in(P, s, ring);
+  float r[NF];
+  z4c_rhs_point_mixed(H, L, q, sy, sz, fs, (float)P->dx, A.prm, r);
+  if (MODE == 1) {
+    double* out = P->buf[B_S1];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) out[f * fs + q] = (double)r[f];
+    return;
+  }
+  rk_update_mixed(P, s, ring, A.dt, q, r, A.prm.w_floor, A.err);
+}
+
+// Sommerfeld ghosts of level-0 patches in the split representation
+__global__ void __launch_bounds__(128) sommerfeld_mixed_kernel(GhostArgs A) {
+  const DevPatch* P = A.patches + A.patch_ids[blockIdx.y];
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= shell_count(P->NX, P->NY, P->NZ)) return;
+  int i, j, k;
+  shell_ijk(id, P->NX, P->NY, P->NZ, i, j, k);
+  const int ring = A.lev->ring;
+  const int s = A.stage;
+  const long long sy = P->px, sz = P->plane, fs = P->fstride;
+  const long long q = i + (long long)j * sy + (long long)k * sz;
+  const float* __restrict__ H = P->hs[ring];
+  const float* __restrict__ L = mixed_lo_in(P, s, ring);
+  const double h = P->dx;
+  const int idx[3] = {i, j, k};
+  const long long st[3] = {1, sy, sz};
+  float x[3];
+  double xd[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    xd[d] = P->origin[d] + (idx[d] - GH + 0.5) * h;
+    x[d] = (float)xd[d];
+  }
+  const float ir = (float)(1.0 / sqrt(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]));
+  const float c = (float)(1.0 / (2.0 * h));
+  float kk[NF];
+#pragma unroll 1
+  for (int f = 0; f < NF; ++f) {
+    const float* fH = H + (long long)f * fs;
+    const float* fL = L + (long long)f * fs;
+    const float h0 = fH[q], l0 = fL[q];
+    float acc = ((h0 - (float)flat_value(f)) + l0) * ir;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long o = xd[d] > 0.0 ? -st[d] : st[d];
+      // (3 f0 - 4 f1 + f2) on centre differences
+      float v = (-4.0f * ((fH[q + o] - h0) + (fL[q + o] - l0)) + ((fH[q + 2 * o] - h0) + (fL[q + 2 * o] - l0))) * c;
+      float dfd = xd[d] > 0.0 ? v : -v;
+      acc += (x[d] * ir) * dfd;
+    }
+    kk[f] = -acc;
+  }
+  rk_update_mixed(P, s, ring, A.dt, q, kk, A.prm.w_floor, A.err);
+}
+
+// split the current time level of one patch (all points) into hi + lo
+__global__ void split_kernel(const DevPatch* patches, const DevLevel* levels, int patch) {
+  const DevPatch* P = patches + patch;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long pts = (long long)P->NX * P->NY * P->NZ;
+  if (id >= pts) return;
+  const int I = id % P->NX, J = (id / P->NX) % P->NY, K = id / ((long long)P->NX * P->NY);
+  const long long q = I + (long long)J * P->px + (long long)K * P->plane;
+  const int ring = levels[P->level].ring;
+  for (int f = 0; f < NF; ++f) split_store(P->buf[ring][f * P->fstride + q], P->hs[ring], P->ls[ring], f * P->fstride + q);
+}
+
+}  // namespace
+
+void launch_stage_mixed(const StageArgs& a, cudaStream_t st) {
+  if (a.ntiles == 0) return;
+  if (a.stage == 0)
+    z4c_stage_mixed_kernel<1><<<a.ntiles, 128, 0, st>>>(a);
+  else
+    z4c_stage_mixed_kernel<0><<<a.ntiles, 128, 0, st>>>(a);
+}
+
+void launch_sommerfeld_mixed(const GhostArgs& a, int npatches, long long max_shell, cudaStream_t st) {
+  if (npatches == 0 || max_shell == 0) return;
+  dim3 grid((unsigned)((max_shell + 127) / 128), npatches);
+  sommerfeld_mixed_kernel<<<grid, 128, 0, st>>>(a);
+}
+
+void launch_split(const DevPatch* patches, const DevLevel* levels, int patch, long long tot,
+                  cudaStream_t st) {
+  split_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(patches, levels, patch);
+}
+
+}  // namespace sacrak

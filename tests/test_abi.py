@@ -35,11 +35,15 @@ def test_every_declared_symbol_exported(L):
 def test_arena_bytes_host_side(L):
     import initial_data as idd
     h = idd.binary_7_level()
+    def copies(mixed):
+        # 6 FP64 state copies per patch, 3 prolongation caches on levels > 0,
+        # mixed precision: 8 FP32 copies (= 4 FP64 copies)
+        return sum((6 + (3 if p.level > 0 else 0) + (4 if mixed else 0)) * 25 * 8 *
+                   (p.n[0] + 6 + (-(p.n[0] + 6)) % 8) * (p.n[1] + 6) * (p.n[2] + 6) for p in h.patches)
     n = sk.arena_bytes(len(h.levels), h.patches)
-    # six state copies of every patch dominate
-    states = sum(6 * 25 * 8 * (p.n[0] + 6 + (-(p.n[0] + 6)) % 8) * (p.n[1] + 6) * (p.n[2] + 6)
-                 for p in h.patches)
-    assert states <= n < states + 64 * 2 ** 20
+    assert copies(False) <= n < copies(False) + 64 * 2 ** 20
+    nm = sk.arena_bytes(len(h.levels), h.patches, sk.Params(precision=1))
+    assert copies(True) <= nm < copies(True) + 64 * 2 ** 20
     assert sk.arena_bytes(2, h.patches[:1]) == 0  # level 1 without a patch
 
 
