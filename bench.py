@@ -38,6 +38,11 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe); measured FMA 
 # u_n and writes y and u_2 (3 passes), stages 2-3 read u_s, u_n, y and write
 # y, u_s+1 (5), stage 4 reads u_4, y and writes u_n+1 (3): 16 passes per step
 BYTES_PER_ZONE_UPDATE = 16 * 25 * 8
+# mixed precision: stage 1 reads hi_n, lo_n (FP32) and u_n (FP64), writes y
+# (FP64) and lo_2 (FP32): 700 B; stages 2-3 read hi_n, lo_s, y and write y,
+# lo_s+1: 700 B; stage 4 reads hi_n, lo_4, y and writes u_n+1 and its split:
+# 800 B.  2900 B per zone update.
+BYTES_PER_ZONE_UPDATE_MIXED = 2900
 
 
 def _peaks():
@@ -163,7 +168,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
+                    help="both: value = mixed precision, with the FP64 run beside it")
     ap.add_argument("--courant", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -200,81 +206,108 @@ def main():
 
     h = hierarchy()
     zu = h.zone_updates_per_coarse_step()
-    prm = sk.Params(courant=args.courant, precision=1 if args.precision == "mixed" else 0)
-    stream = torch.cuda.Stream()
-    g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=stream)
-    g.set_initial_data(1, h.masses, h.positions)
-
-    # per-launch time of the fused stage kernel, measured on the grid's stream
-    def step():
-        g.level_step(0)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    precisions = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    runs = {}
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * zu / (ms * 1e-3)
-    # the state must still be finite (stage kernels flag non-finite values)
-    norms = g.constraints(0)
-
-    # dominant kernel: the fused Z4c stage kernel, every launch of a profiled
-    # (eager) pass over the same workload timed with CUDA events
-    kern = stage_kernel_timing(g, max(1, min(args.steps, 2)))
-    kern["share_of_step"] = kern["ms"] * kern["launches"] / max(1, min(args.steps, 2)) / ms
-
-    e2e = None
-    if not args.no_e2e:
-        e2e = end_to_end(torch, sk, h, prm, args, world, dist)
-
+        for p in precisions:
+            runs[p] = measure(torch, sk, h, p, args, world, dist)
+    head = runs[precisions[0]]
     peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    ach_gflops = kern["flops_per_launch"] / (kern["ms"] * 1e-3) / 1e12 if kern["flops_per_launch"] else None
-    hbm_gbs = kern["bytes_per_launch"] / (kern["ms"] * 1e-3) / 1e9
-    roof = {"bound": "alu", "achieved": ach_gflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": (ach_gflops / FP64_PEAK_TFLOPS) if ach_gflops else None, "traffic": kern["traffic"],
-            "kernel": kern["name"], "launch_ms": kern["ms"],
-            "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm, "hbm_frac_of_measured": hbm_gbs / hbm,
-            "peak_note": "FP64 nominal 1.25 TFLOP/s (recipe); HBM peak of measured copy"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if precisions[0] == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "levels": len(h.levels), "patches": len(h.patches),
-                       "zone_updates_per_step": zu, "courant": args.courant, "precision": args.precision,
+                       "zone_updates_per_step": zu, "courant": args.courant, "precision": precisions[0],
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2: %.2f GB per state copy" % (
                            sum(25 * 8 * (p.n[0] + 6) * (p.n[1] + 6) * (p.n[2] + 6) for p in h.patches) / 1e9),
-                       "hbm_roofline_zone_updates_per_s": hbm * 1e9 / BYTES_PER_ZONE_UPDATE,
-                       "hbm_frac_of_measured": value / world / (hbm * 1e9 / BYTES_PER_ZONE_UPDATE)},
-            "roofline": roof,
-            "gpu_launches": launches_per_coarse_step(h) * args.steps,
+                       "hbm_roofline_zone_updates_per_s": hbm * 1e9 / head["bytes_per_zone_update"],
+                       "hbm_frac_of_measured": head["value"] / world / (hbm * 1e9 / head["bytes_per_zone_update"])},
+            "roofline": roofline(head, hbm),
+            "gpu_launches": launches_per_coarse_step(h) * args.steps * len(precisions),
             "clocks": clk.summary(),
-            "constraints_l0": list(norms)}
-    if e2e:
-        line["e2e"] = e2e
+            "constraints_l0": head["constraints_l0"]}
+    if head.get("e2e"):
+        line["e2e"] = head["e2e"]
+    for p in precisions[1:]:
+        r = runs[p]
+        line[p] = {"value": r["value"], "ms_per_step": r["ms"], "dtype": "f64" if p == "fp64" else "f32+f64",
+                   "roofline": roofline(r, hbm), "constraints_l0": r["constraints_l0"]}
+        if r.get("e2e"):
+            line[p]["e2e"] = r["e2e"]
+    if len(precisions) > 1:
+        line["speedup_mixed_over_fp64"] = runs["mixed"]["value"] / runs["fp64"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, sample = cpu_sample(1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    g.close()
     if dist:
         dist.destroy_process_group()
+
+
+# per-zone DRAM traffic of one stage-kernel launch from the ncu captures of the
+# 96^3 case (profiles/): FP64 1.53-1.98 GB, mixed 0.877 GB per 884,736 zones
+NCU_TRAFFIC_PER_ZONE = {0: 1.98e9 / 884736, 1: 0.877e9 / 884736}
+
+
+def roofline(r, hbm):
+    k = r["kern"]
+    if r["precision"] == "fp64":
+        ach = k["flops_per_launch"] / (k["ms"] * 1e-3) / 1e12 if k["flops_per_launch"] else None
+        out = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": ach / FP64_PEAK_TFLOPS if ach else None,
+               "peak_note": "FP64 pipe, nominal 1.25 TFLOP/s (the recipe's unit rate); a DFMA probe "
+                            "measured 1.0 TFLOP/s on this GPU"}
+    else:
+        ach = k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+               "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+    out.update({"traffic": NCU_TRAFFIC_PER_ZONE[0 if r["precision"] == "fp64" else 1] * k["zones_per_launch"],
+                "kernel": k["name"], "launch_ms": k["ms"], "launches_per_step": k["launches"] / k["steps"],
+                "share_of_step": k["ms"] * k["launches"] / k["steps"] / r["ms"],
+                "algorithmic_bytes_per_launch": k["bytes_per_launch"],
+                "hbm_frac_of_measured": k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9 / hbm})
+    return out
+
+
+def measure(torch, sk, h, precision, args, world, dist):
+    zu = h.zone_updates_per_coarse_step()
+    prm = sk.Params(courant=args.courant, precision=1 if precision == "mixed" else 0)
+    stream = torch.cuda.Stream()
+    g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=stream)
+    g.set_initial_data(1, h.masses, h.positions)
+    for _ in range(args.warmup):
+        g.level_step(0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.level_step(0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    norms = list(map(float, g.constraints(0)))  # also checks the state stayed finite
+    nprof = max(1, min(args.steps, 2))
+    kern = stage_kernel_timing(g, nprof)
+    kern["steps"] = nprof
+    g.close()
+    out = {"precision": precision, "value": world * zu / (ms * 1e-3), "ms": ms, "kern": kern,
+           "constraints_l0": norms,
+           "bytes_per_zone_update": BYTES_PER_ZONE_UPDATE_MIXED if precision == "mixed" else BYTES_PER_ZONE_UPDATE}
+    if not args.no_e2e:
+        out["e2e"] = end_to_end(torch, sk, h, prm, args, world, dist)
+    return out
 
 
 def uniform_case(torch, sk, args):
@@ -285,7 +318,7 @@ def uniform_case(torch, sk, args):
     p = h.levels[0][0]
     prm = sk.Params(courant=args.courant, precision=1 if args.precision == "mixed" else 0)
     stream = torch.cuda.Stream()
-    g = sk.Grid(1, p.dx, [p], prm, stream=stream)
+    g = sk.Grid(1, p.dx, [p], prm, stream=stream)  # (--precision both runs FP64 here)
     g.set_initial_data(1, h.masses, h.positions)
     for _ in range(args.warmup):
         g.rk4_step(0)
@@ -363,14 +396,15 @@ def stage_kernel_timing(g, steps):
     fz = FLOPS_PER_ZONE_STAGE.get(g.params.precision)
     return {"name": "z4c_stage_fp64_kernel" if g.params.precision == 0 else "z4c_stage_mixed_kernel",
             "ms": per, "launches": n, "share_of_step": None,
-            "bytes_per_launch": zones_per_launch * BYTES_PER_ZONE_UPDATE / 4.0,
+            "bytes_per_launch": zones_per_launch * (BYTES_PER_ZONE_UPDATE_MIXED if g.params.precision == 1
+                                                    else BYTES_PER_ZONE_UPDATE) / 4.0,
             "flops_per_launch": zones_per_launch * fz if fz else None,
             "traffic": None, "zones_per_launch": zones_per_launch}
 
 
 # FP64 flops per zone per stage of the fused kernel (DFMA counted as 2), from
 # the ncu instruction counts of one launch divided by the zones it updates
-FLOPS_PER_ZONE_STAGE = {}
+FLOPS_PER_ZONE_STAGE = {0: 5355}
 
 
 def end_to_end(torch, sk, h, prm, args, world, dist):

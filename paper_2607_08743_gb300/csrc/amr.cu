@@ -229,6 +229,93 @@ __global__ void __launch_bounds__(128) prolong_space_kernel(ProlongArgs A, long 
       }
 }
 
+// Mixed precision: the same interpolant in FP32 on differences against the
+// parent cell's value, from the parent's hi/lo split, added to that value in
+// FP64 (the weights sum to one along every axis, so subtracting the reference
+// changes nothing but the rounding).
+__global__ void __launch_bounds__(128) prolong_space_mixed_kernel(ProlongArgs A, long long max_work) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= max_work) return;
+  const DevPatch* C = A.patches + A.patch_ids[blockIdx.y];
+  const int m0 = C->n[0] / 2 + 4, m1 = C->n[1] / 2 + 4, m2 = C->n[2] / 2 + 4;
+  const long long ncl = (long long)m0 * m1 * m2 - (long long)(m0 - 4) * (m1 - 4) * (m2 - 4);
+  const int f = (int)(tid % NF);
+  const long long cl = tid / NF;
+  if (cl >= ncl) return;
+  int a, b, c;
+  box_shell_ijk(cl, m0, m1, m2, 2, a, b, c);
+  const DevPatch* P = A.patches + C->parent;
+  const int slot = A.plev->ring;
+  const long long fo = (long long)f * P->fstride;
+  const float* __restrict__ hp = P->hs[slot] + fo;
+  const float* __restrict__ lp = P->ls[slot] + fo;
+  const int pi = C->off[0] - 2 + a + GH, pj = C->off[1] - 2 + b + GH, pk = C->off[2] - 2 + c + GH;
+  // reference: the parent cell itself when it is readable, else the nearest
+  // readable cell along each axis
+  const int xlo = max(0, 1 - a), xhi = min(6, C->n[0] / 2 + 8 - a);
+  const int ylo = max(0, 1 - b), yhi = min(6, C->n[1] / 2 + 8 - b);
+  const int zlo = max(0, 1 - c), zhi = min(6, C->n[2] / 2 + 8 - c);
+  const int ri = pi - 3 + min(max(3, xlo), xhi), rj = pj - 3 + min(max(3, ylo), yhi),
+            rk = pk - 3 + min(max(3, zlo), zhi);
+  const long long qr = ri + (long long)rj * P->px + (long long)rk * P->plane;
+  const float h0 = hp[qr], l0 = lp[qr];
+  const double u0 = P->buf[slot][fo + qr];
+  const long long q0 = (pi - 3) + (long long)(pj - 3) * P->px + (long long)(pk - 3) * P->plane;
+  float we[7], wo[7];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    we[t] = (float)c_wm[t];
+    wo[t + 1] = (float)c_wp[t];
+  }
+  we[6] = 0.0f;
+  wo[0] = 0.0f;
+  float acc[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
+#pragma unroll 1
+  for (int kz = zlo; kz <= zhi; ++kz) {
+    float vy[2][2] = {{0, 0}, {0, 0}};
+#pragma unroll
+    for (int jy = 0; jy < 7; ++jy) {
+      if (jy < ylo || jy > yhi) continue;
+      const long long row = q0 + (long long)kz * P->plane + (long long)jy * P->px;
+      float xe = 0.0f, xo = 0.0f;
+#pragma unroll
+      for (int ix = 0; ix < 7; ++ix) {
+        const float v = (ix >= xlo && ix <= xhi)
+                            ? (__ldg(hp + row + ix) - h0) + (__ldg(lp + row + ix) - l0)
+                            : 0.0f;
+        xe += we[ix] * v;
+        xo += wo[ix] * v;
+      }
+      vy[0][0] += we[jy] * xe;
+      vy[0][1] += we[jy] * xo;
+      vy[1][0] += wo[jy] * xe;
+      vy[1][1] += wo[jy] * xo;
+    }
+#pragma unroll
+    for (int y = 0; y < 2; ++y)
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {
+        acc[0][y][x] += we[kz] * vy[y][x];
+        acc[1][y][x] += wo[kz] * vy[y][x];
+      }
+  }
+  const int c0 = 2 * (a - 2), c1 = 2 * (b - 2), c2 = 2 * (c - 2);
+  double* __restrict__ g = C->gsh[slot] + (long long)f * C->fstride;
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+#pragma unroll
+    for (int y = 0; y < 2; ++y)
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {
+        const int i = c0 + x, j = c1 + y, k = c2 + z;
+        if (i < -GH || j < -GH || k < -GH || i >= C->n[0] + GH || j >= C->n[1] + GH || k >= C->n[2] + GH)
+          continue;
+        const bool active = i >= 0 && j >= 0 && k >= 0 && i < C->n[0] && j < C->n[1] && k < C->n[2];
+        if (active) continue;
+        g[(i + GH) + (long long)(j + GH) * C->px + (long long)(k + GH) * C->plane] = u0 + (double)acc[z][y][x];
+      }
+}
+
 // Ghosts of the child's target buffer = time combination of the cached
 // spatial prolongations of the parent's (oldest, middle, newest) slots.
 __global__ void ghost_time_fill_kernel(FillArgs A) {
@@ -397,7 +484,7 @@ void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cu
 }
 
 void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,
-                          long long max_clusters, cudaStream_t st) {
+                          long long max_clusters, int mixed, cudaStream_t st) {
   if (nchildren == 0 || max_clusters == 0) return;
   ProlongArgs a;
   a.patches = patches;
@@ -405,7 +492,10 @@ void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLeve
   a.plev = plev;
   const long long work = max_clusters * NF;
   dim3 grid((unsigned)((work + 127) / 128), nchildren);
-  prolong_space_kernel<<<grid, 128, 0, st>>>(a, work);
+  if (mixed)
+    prolong_space_mixed_kernel<<<grid, 128, 0, st>>>(a, work);
+  else
+    prolong_space_kernel<<<grid, 128, 0, st>>>(a, work);
 }
 
 void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st) {

@@ -289,7 +289,8 @@ void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double d
 void refresh_shells(sacrak_grid* g, int l) {
   if (l <= 0 || l >= g->nlevels) return;
   launch_prolong_space(g->d_patches, g->d_ids + g->lvl_id_off[l], g->d_levels + (l - 1),
-                       (int)g->lvl_ids[l].size(), g->lvl_max_clusters[l], g->stream);
+                       (int)g->lvl_ids[l].size(), g->lvl_max_clusters[l], g->prm.precision == 1,
+                       g->stream);
 }
 
 // after new data: every child level's cache for its parent's current slot,

@@ -277,7 +277,7 @@ void launch_constraints(const ConsArgs& a, int ntiles, double* out5, cudaStream_
 void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cudaStream_t st);
 void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st);
 void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,
-                          long long max_clusters, cudaStream_t st);
+                          long long max_clusters, int mixed, cudaStream_t st);
 void launch_sommerfeld_mixed(const GhostArgs& a, int npatches, long long max_shell, cudaStream_t st);
 void launch_split(const DevPatch* patches, const DevLevel* levels, int patch, long long tot,
                   cudaStream_t st);
