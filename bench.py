@@ -38,11 +38,12 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe); measured FMA 
 # u_n and writes y and u_2 (3 passes), stages 2-3 read u_s, u_n, y and write
 # y, u_s+1 (5), stage 4 reads u_4, y and writes u_n+1 (3): 16 passes per step
 BYTES_PER_ZONE_UPDATE = 16 * 25 * 8
-# mixed precision: stage 1 reads hi_n, lo_n (FP32) and u_n (FP64), writes y
-# (FP64) and lo_2 (FP32): 700 B; stages 2-3 read hi_n, lo_s, y and write y,
-# lo_s+1: 700 B; stage 4 reads hi_n, lo_4, y and writes u_n+1 and its split:
-# 800 B.  2900 B per zone update.
-BYTES_PER_ZONE_UPDATE_MIXED = 2900
+# mixed precision (FP32 hi/lo pairs, 8 B per value): stage 1 reads the split
+# (hi_n, lo_n) and u_n (FP64), writes y (FP64) and the stage-2 pairs: 800 B;
+# stages 2-3 read the stage pairs, (hi_n, lo_n) and y, write y and the next
+# pairs: 1000 B; stage 4 reads the stage pairs and y, writes u_n+1 and its
+# split: 800 B.  3600 B per zone update.
+BYTES_PER_ZONE_UPDATE_MIXED = 3600
 
 
 def _peaks():

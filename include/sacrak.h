@@ -88,8 +88,8 @@ typedef struct {
 /* Bytes of device memory a grid of this shape needs: per patch 6 FP64 state
  * copies (3 time levels, the RK accumulator, 2 stage buffers), 3 more on
  * levels > 0 (the parent's time levels prolonged onto the ghost shell), and
- * with params->precision == 1 eight FP32 copies (hi/lo split of the time
- * levels, 2 stage buffers); plus tables and reduction scratch.  params may be
+ * with params->precision == 1 five copies of FP32 hi/lo pairs (the split of
+ * the 3 time levels, 2 stage states); plus tables and reduction scratch.  params may be
  * NULL (FP64).  Returns 0 for an invalid description. */
 size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* patches,
                           const sacrak_params* params);

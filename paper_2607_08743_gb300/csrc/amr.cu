@@ -17,10 +17,9 @@ __device__ __forceinline__ int fill_slot(int mode, int s, int ring) {
   return mode == 0 ? stage_in_slot(s, ring) : (mode == 1 ? ring : (ring + 1) % 3);
 }
 
-__device__ __forceinline__ void split_to(double v, float* h, float* l, long long o) {
+__device__ __forceinline__ void split_to(double v, float2* hl, long long o) {
   const float hi = __double2float_rn(v);
-  h[o] = hi;
-  l[o] = __double2float_rn(v - (double)hi);
+  hl[o] = make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
 // periodic: every ghost takes the value of the active point congruent modulo n
@@ -44,18 +43,16 @@ __global__ void periodic_fill_kernel(FillArgs A) {
     return;
   }
   if (A.mode == 0 && A.stage > 1) {
-    float* lo = mixed_lo_in(P, A.stage, ring);
-    for (int f = 0; f < NF; ++f) lo[f * fs + q] = lo[f * fs + qs];
+    float2* in = mixed_in(P, A.stage, ring);
+    for (int f = 0; f < NF; ++f) in[f * fs + q] = in[f * fs + qs];
     return;
   }
   const int slot = A.mode == 2 ? (ring + 1) % 3 : ring;
   double* u = P->buf[slot];
-  float* h = P->hs[slot];
-  float* l = P->ls[slot];
+  float2* hl = P->hl[slot];
   for (int f = 0; f < NF; ++f) {
     u[f * fs + q] = u[f * fs + qs];
-    h[f * fs + q] = h[f * fs + qs];
-    l[f * fs + q] = l[f * fs + qs];
+    hl[f * fs + q] = hl[f * fs + qs];
   }
 }
 
@@ -77,16 +74,15 @@ __global__ void frozen_fill_kernel(FillArgs A) {
   }
   if (A.mode == 0) {
     if (A.stage == 1) return;
-    float* lo = mixed_lo_in(P, A.stage, ring);
-    for (int f = 0; f < NF; ++f) lo[f * fs + q] = P->ls[ring][f * fs + q];
+    float2* in = mixed_in(P, A.stage, ring);
+    for (int f = 0; f < NF; ++f) in[f * fs + q] = P->hl[ring][f * fs + q];
     return;
   }
   if (A.mode != 2) return;
   const int nx = (ring + 1) % 3;
   for (int f = 0; f < NF; ++f) {
     P->buf[nx][f * fs + q] = P->buf[ring][f * fs + q];
-    P->hs[nx][f * fs + q] = P->hs[ring][f * fs + q];
-    P->ls[nx][f * fs + q] = P->ls[ring][f * fs + q];
+    P->hl[nx][f * fs + q] = P->hl[ring][f * fs + q];
   }
 }
 
@@ -247,8 +243,7 @@ __global__ void __launch_bounds__(128) prolong_space_mixed_kernel(ProlongArgs A,
   const DevPatch* P = A.patches + C->parent;
   const int slot = A.plev->ring;
   const long long fo = (long long)f * P->fstride;
-  const float* __restrict__ hp = P->hs[slot] + fo;
-  const float* __restrict__ lp = P->ls[slot] + fo;
+  const float2* __restrict__ hp = P->hl[slot] + fo;
   const int pi = C->off[0] - 2 + a + GH, pj = C->off[1] - 2 + b + GH, pk = C->off[2] - 2 + c + GH;
   // reference: the parent cell itself when it is readable, else the nearest
   // readable cell along each axis
@@ -258,7 +253,8 @@ __global__ void __launch_bounds__(128) prolong_space_mixed_kernel(ProlongArgs A,
   const int ri = pi - 3 + min(max(3, xlo), xhi), rj = pj - 3 + min(max(3, ylo), yhi),
             rk = pk - 3 + min(max(3, zlo), zhi);
   const long long qr = ri + (long long)rj * P->px + (long long)rk * P->plane;
-  const float h0 = hp[qr], l0 = lp[qr];
+  const float2 ref = hp[qr];
+  const float h0 = ref.x, l0 = ref.y;
   const double u0 = P->buf[slot][fo + qr];
   const long long q0 = (pi - 3) + (long long)(pj - 3) * P->px + (long long)(pk - 3) * P->plane;
   float we[7], wo[7];
@@ -280,9 +276,11 @@ __global__ void __launch_bounds__(128) prolong_space_mixed_kernel(ProlongArgs A,
       float xe = 0.0f, xo = 0.0f;
 #pragma unroll
       for (int ix = 0; ix < 7; ++ix) {
-        const float v = (ix >= xlo && ix <= xhi)
-                            ? (__ldg(hp + row + ix) - h0) + (__ldg(lp + row + ix) - l0)
-                            : 0.0f;
+        float v = 0.0f;
+        if (ix >= xlo && ix <= xhi) {
+          const float2 w = __ldg(hp + row + ix);
+          v = (w.x - h0) + (w.y - l0);
+        }
         xe += we[ix] * v;
         xo += wo[ix] * v;
       }
@@ -345,16 +343,17 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
   // mixed precision: stage 1 (and the fill of the current level) sets the
   // FP64 ghost and its hi/lo split; later stages set lo_s = v - hi_n
   const bool later = (A.mode == 0 && A.stage > 1);
-  float* __restrict__ lo_s = later ? mixed_lo_in(C, A.stage, ring) : nullptr;
+  float2* __restrict__ in = later ? mixed_in(C, A.stage, ring) : nullptr;
   for (int f = 0; f < NF; ++f) {
     const long long o = f * C->fstride + q;
     double v = w1 * g1[o] + w2 * g2[o];
     if (q3) v += w0 * g0[o];
     if (later) {
-      lo_s[o] = __double2float_rn(v - (double)C->hs[ring][o]);
+      const float hi = C->hl[ring][o].x;
+      in[o] = make_float2(hi, __double2float_rn(v - (double)hi));
     } else {
       C->buf[ring][o] = v;
-      split_to(v, C->hs[ring], C->ls[ring], o);
+      split_to(v, C->hl[ring], o);
     }
   }
 }
@@ -395,7 +394,7 @@ __global__ void __launch_bounds__(128) restrict_kernel(FillArgs A) {
       v += w[c] * vy;
     }
     up[f * P->fstride + qp] = v;
-    if (A.mixed) split_to(v, P->hs[A.plev->ring], P->ls[A.plev->ring], f * P->fstride + qp);
+    if (A.mixed) split_to(v, P->hl[A.plev->ring], f * P->fstride + qp);
   }
 }
 
@@ -422,18 +421,19 @@ __global__ void exchange_kernel(ExchArgs E) {
   const long long qb = (ib + GH) + (long long)(jb + GH) * Pb->px + (long long)(kb + GH) * Pb->plane;
   if (E.mixed && E.mode == 0 && E.stage > 1) {
     // stage state hi_n + lo_s: move lo_s (and average the stage values)
-    float* la = mixed_lo_in(Pa, E.stage, ring);
-    float* lb = mixed_lo_in(Pb, E.stage, ring);
+    float2* ia = mixed_in(Pa, E.stage, ring);
+    float2* ib = mixed_in(Pb, E.stage, ring);
     for (int f = 0; f < NF; ++f) {
       const long long oa = f * Pa->fstride + qa, ob = f * Pb->fstride + qb;
+      const float2 a = ia[oa], b = ib[ob];
       if (a_act && b_act) {
-        const float m = 0.5f * ((Pa->hs[ring][oa] + la[oa]) + (Pb->hs[ring][ob] + lb[ob]));
-        la[oa] = m - Pa->hs[ring][oa];
-        lb[ob] = m - Pb->hs[ring][ob];
+        const float m = 0.5f * ((a.x + a.y) + (b.x + b.y));
+        ia[oa] = make_float2(a.x, m - a.x);
+        ib[ob] = make_float2(b.x, m - b.x);
       } else if (b_act) {
-        la[oa] = (Pb->hs[ring][ob] - Pa->hs[ring][oa]) + lb[ob];
+        ia[oa] = make_float2(a.x, (b.x - a.x) + b.y);
       } else {
-        lb[ob] = (Pa->hs[ring][oa] - Pb->hs[ring][ob]) + la[oa];
+        ib[ob] = make_float2(b.x, (a.x - b.x) + a.y);
       }
     }
     return;
@@ -455,8 +455,8 @@ __global__ void exchange_kernel(ExchArgs E) {
       *pb = *pa;
     }
     if (E.mixed) {
-      split_to(*pa, Pa->hs[slot], Pa->ls[slot], oa);
-      split_to(*pb, Pb->hs[slot], Pb->ls[slot], ob);
+      split_to(*pa, Pa->hl[slot], oa);
+      split_to(*pb, Pb->hl[slot], ob);
     }
   }
 }

@@ -96,7 +96,7 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed,
     L.patch_state[p] = off;
     const int nbuf = NBUF + (pd[p].level > 0 ? 3 : 0);  // + cached prolongation slots
     off = align_up(off + (size_t)nbuf * NF * fs * sizeof(double), 256);
-    if (mixed) off = align_up(off + (size_t)8 * NF * fs * sizeof(float), 256);  // hs[3] ls[3] la lb
+    if (mixed) off = align_up(off + (size_t)5 * NF * fs * sizeof(float2), 256);  // hl[3] sa sb
   }
   L.total = off;
   return true;
@@ -451,14 +451,11 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
                              : nullptr;
     if (p.precision == 1) {
       const size_t nb = (size_t)(NBUF + (P.level > 0 ? 3 : 0)) * NF * P.fstride * sizeof(double);
-      float* m0 = (float*)(g->arena + align_up(L.patch_state[i] + nb, 256));
+      float2* m0 = (float2*)(g->arena + align_up(L.patch_state[i] + nb, 256));
       const size_t fl = (size_t)NF * P.fstride;
-      for (int b = 0; b < 3; ++b) {
-        P.hs[b] = m0 + (size_t)b * fl;
-        P.ls[b] = m0 + (size_t)(3 + b) * fl;
-      }
-      P.la = m0 + 6 * fl;
-      P.lb = m0 + 7 * fl;
+      for (int b = 0; b < 3; ++b) P.hl[b] = m0 + (size_t)b * fl;
+      P.sa = m0 + 3 * fl;
+      P.sb = m0 + 4 * fl;
     }
     g->lvl_ids[P.level].push_back(i);
   }

@@ -42,12 +42,12 @@ struct DevPatch {
   // onto this patch (full patch layout; only the ghost shell is written)
   double* gsh[3];
   // mixed precision only (null otherwise): each time level split into FP32
-  // hi + lo (hs, ls, same ring slots as buf), and the FP32 low parts of the
-  // stage states u_s = hi_n + lo_s (la, lb; stage s reads ls[ring], la, lb, la)
-  float* hs[3];
-  float* ls[3];
-  float* la;
-  float* lb;
+  // hi + lo, interleaved (hl, same ring slots as buf), and the stage states
+  // u_s = hi_n + lo_s stored the same way (sa, sb): stage s reads hl[ring],
+  // sa, sb, sa; stages 1-3 write sa, sb, sa; stage 4 writes hl[ring + 1]
+  float2* hl[3];
+  float2* sa;
+  float2* sb;
 };
 
 struct DevLevel {
@@ -90,12 +90,12 @@ __host__ __device__ constexpr int S2(int i, int j) {
                   : ((i + j) == 1 ? 1 : ((i + j) == 2 ? 2 : 4));
 }
 
-// mixed precision: FP32 low-part buffer read (in) / written (out) by stage s
-__host__ __device__ inline float* mixed_lo_in(const DevPatch* P, int s, int ring) {
-  return s == 1 ? P->ls[ring] : (s == 3 ? P->lb : P->la);
+// mixed precision: split stage state read (in) / written (out) by stage s
+__host__ __device__ inline float2* mixed_in(const DevPatch* P, int s, int ring) {
+  return s == 1 ? P->hl[ring] : (s == 3 ? P->sb : P->sa);
 }
-__host__ __device__ inline float* mixed_lo_out(const DevPatch* P, int s) {
-  return s == 2 ? P->lb : P->la;  // stage 4 writes the split of the new level instead
+__host__ __device__ inline float2* mixed_out(const DevPatch* P, int s) {
+  return s == 2 ? P->sb : P->sa;  // stage 4 writes the split of the new level instead
 }
 
 // slot of the stage input / output buffer for RK4 stage s (1..4)

@@ -23,45 +23,42 @@ namespace {
 
 // ------------------------------------------------------------------ stencils
 
-__device__ __forceinline__ float pdiff(const float* __restrict__ H, const float* __restrict__ L,
-                                       long long a, long long b) {
-  return (__ldg(H + a) - __ldg(H + b)) + (__ldg(L + a) - __ldg(L + b));
+__device__ __forceinline__ float pdiff(const float2* __restrict__ F, long long a, long long b) {
+  const float2 x = __ldg(F + a), y = __ldg(F + b);
+  return (x.x - y.x) + (x.y - y.y);
 }
-__device__ __forceinline__ float cdiff(const float* __restrict__ H, const float* __restrict__ L,
-                                       long long a, float h0, float l0) {
-  return (__ldg(H + a) - h0) + (__ldg(L + a) - l0);
+__device__ __forceinline__ float cdiff(const float2* __restrict__ F, long long a, float h0, float l0) {
+  const float2 x = __ldg(F + a);
+  return (x.x - h0) + (x.y - l0);
 }
 // 8 (f1 - f-1) - (f2 - f-2); times 1/(12 h)
-__device__ __forceinline__ float d1f(const float* H, const float* L, long long q, long long s) {
-  return 8.0f * pdiff(H, L, q + s, q - s) - pdiff(H, L, q + 2 * s, q - 2 * s);
+__device__ __forceinline__ float d1f(const float2* F, long long q, long long s) {
+  return 8.0f * pdiff(F, q + s, q - s) - pdiff(F, q + 2 * s, q - 2 * s);
 }
 // 16 (f1 + f-1) - (f2 + f-2) - 30 f0 on centre differences; times 1/(12 h^2)
-__device__ __forceinline__ float d2f(const float* H, const float* L, long long q, long long s,
-                                     float h0, float l0) {
-  float a = cdiff(H, L, q + s, h0, l0) + cdiff(H, L, q - s, h0, l0);
-  float b = cdiff(H, L, q + 2 * s, h0, l0) + cdiff(H, L, q - 2 * s, h0, l0);
+__device__ __forceinline__ float d2f(const float2* F, long long q, long long s, float h0, float l0) {
+  float a = cdiff(F, q + s, h0, l0) + cdiff(F, q - s, h0, l0);
+  float b = cdiff(F, q + 2 * s, h0, l0) + cdiff(F, q - 2 * s, h0, l0);
   return 16.0f * a - b;
 }
 // nested D_a(D_b f); times 1/(144 h^2)
-__device__ __forceinline__ float d11f(const float* H, const float* L, long long q, long long sa,
-                                      long long sb) {
-  float p1 = d1f(H, L, q + sa, sb), m1 = d1f(H, L, q - sa, sb);
-  float p2 = d1f(H, L, q + 2 * sa, sb), m2 = d1f(H, L, q - 2 * sa, sb);
+__device__ __forceinline__ float d11f(const float2* F, long long q, long long sa, long long sb) {
+  float p1 = d1f(F, q + sa, sb), m1 = d1f(F, q - sa, sb);
+  float p2 = d1f(F, q + 2 * sa, sb), m2 = d1f(F, q - 2 * sa, sb);
   return 8.0f * (p1 - m1) - (p2 - m2);
 }
 // lopsided upwind on centre differences; times 1/(12 h)
-__device__ __forceinline__ float dupf(const float* H, const float* L, long long q, long long st,
-                                      float b, float h0, float l0) {
+__device__ __forceinline__ float dupf(const float2* F, long long q, long long st, float b, float h0,
+                                      float l0) {
   long long s = b > 0.0f ? st : -st;
-  float v = -3.0f * cdiff(H, L, q - s, h0, l0) + 18.0f * cdiff(H, L, q + s, h0, l0) -
-            6.0f * cdiff(H, L, q + 2 * s, h0, l0) + cdiff(H, L, q + 3 * s, h0, l0);
+  float v = -3.0f * cdiff(F, q - s, h0, l0) + 18.0f * cdiff(F, q + s, h0, l0) -
+            6.0f * cdiff(F, q + 2 * s, h0, l0) + cdiff(F, q + 3 * s, h0, l0);
   return b > 0.0f ? v : -v;
 }
-__device__ __forceinline__ float delta6f(const float* H, const float* L, long long q, long long st,
-                                         float h0, float l0) {
-  float a = cdiff(H, L, q + 3 * st, h0, l0) + cdiff(H, L, q - 3 * st, h0, l0);
-  float b = cdiff(H, L, q + 2 * st, h0, l0) + cdiff(H, L, q - 2 * st, h0, l0);
-  float c = cdiff(H, L, q + st, h0, l0) + cdiff(H, L, q - st, h0, l0);
+__device__ __forceinline__ float delta6f(const float2* F, long long q, long long st, float h0, float l0) {
+  float a = cdiff(F, q + 3 * st, h0, l0) + cdiff(F, q - 3 * st, h0, l0);
+  float b = cdiff(F, q + 2 * st, h0, l0) + cdiff(F, q - 2 * st, h0, l0);
+  float c = cdiff(F, q + st, h0, l0) + cdiff(F, q - st, h0, l0);
   return (a - 6.0f * b) + 15.0f * c;
 }
 
@@ -83,50 +80,87 @@ __device__ __forceinline__ float symc(const float S[6], const float T[6]) {
 
 // ------------------------------------------------------------------ the RHS
 
-// Z4c RHS of one point in FP32 from the split state (H, L); r[f] gets the
-// full RHS (sources + advection + dissipation).
-__device__ __forceinline__ void z4c_rhs_point_mixed(const float* __restrict__ H,
-                                                    const float* __restrict__ L, long long q,
+// The 114 first and second derivatives a point needs are formed first and
+// parked in shared memory (one column per thread, no sharing, so no barrier);
+// the curvature algebra then reads them back as it goes.  Splitting the two
+// phases this way keeps the algebra's register demand well below what holding
+// every derivative in registers needed (255 registers with spills, 8 warps per
+// SM), so more warps hide the latency of the stencil loads.
+constexpr int MIX_THREADS = 128;
+constexpr int ND = 114;  // derivatives kept per point
+// slots: dgt[d][a] 0..17, dW 18..20, dal 21..23, dGam[d][i] 24..32,
+// dbe[d][i] 33..41, dKh 42..44, dTh 45..47, ddgt[a][lm] 48..83, ddW 84..89,
+// ddal 90..95, ddbe[i][lm] 96..113
+enum {
+  K_DGT = 0, K_DW = 18, K_DAL = 21, K_DGAM = 24, K_DBE = 33, K_DKH = 42, K_DTH = 45,
+  K_DDGT = 48, K_DDW = 84, K_DDAL = 90, K_DDBE = 96
+};
+
+// all six second derivatives of one field into slots k0..k0+5 (xx xy xz yy yz zz)
+__device__ __forceinline__ void second_derivs(float* sd, int k0, const float2* F, long long q,
+                                              const long long st[3], float c2, float c11) {
+  const int t = threadIdx.x;
+  const float2 c = __ldg(F + q);
+  sd[(k0 + 0) * MIX_THREADS + t] = d2f(F, q, st[0], c.x, c.y) * c2;
+  sd[(k0 + 3) * MIX_THREADS + t] = d2f(F, q, st[1], c.x, c.y) * c2;
+  sd[(k0 + 5) * MIX_THREADS + t] = d2f(F, q, st[2], c.x, c.y) * c2;
+  sd[(k0 + 1) * MIX_THREADS + t] = d11f(F, q, st[0], st[1]) * c11;
+  sd[(k0 + 2) * MIX_THREADS + t] = d11f(F, q, st[0], st[2]) * c11;
+  sd[(k0 + 4) * MIX_THREADS + t] = d11f(F, q, st[1], st[2]) * c11;
+}
+
+// Z4c RHS of one point in FP32 from the split state U (hi, lo interleaved);
+// r[f] gets the full RHS (sources + advection + dissipation).  sd: this CTA's
+// ND x MIX_THREADS shared-memory derivative slots.
+__device__ __forceinline__ void z4c_rhs_point_mixed(const float2* __restrict__ U, long long q,
                                                     long long sy, long long sz, long long fs,
-                                                    float h, const DevParams& prm, float r[NF]) {
+                                                    float h, const DevParams& prm, float* sd,
+                                                    float r[NF]) {
   const long long st[3] = {1, sy, sz};
   const float c1 = 1.0f / (12.0f * h);
   const float c2 = c1 / h;
   const float c11 = c1 * c1;
-#define HF(f) (H + (long long)(f) * fs)
-#define LF(f) (L + (long long)(f) * fs)
-#define CV(f) (__ldg(HF(f) + q) + __ldg(LF(f) + q))
+  const int t = threadIdx.x;
+#define HF(f) (U + (long long)(f) * fs)
+#define SD(k) sd[(k) * MIX_THREADS + t]
+  auto CV = [&](int f) {
+    const float2 v = __ldg(HF(f) + q);
+    return v.x + v.y;
+  };
+
+  // ---- phase 1: derivatives into shared memory
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) SD(K_DGT + 6 * d + a) = d1f(HF(F_GXX + a), q, st[d]) * c1;
+    SD(K_DW + d) = d1f(HF(F_W), q, st[d]) * c1;
+    SD(K_DAL + d) = d1f(HF(F_ALP), q, st[d]) * c1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      SD(K_DGAM + 3 * d + i) = d1f(HF(F_GAMX + i), q, st[d]) * c1;
+      SD(K_DBE + 3 * d + i) = d1f(HF(F_BETX + i), q, st[d]) * c1;
+    }
+    SD(K_DKH + d) = d1f(HF(F_KH), q, st[d]) * c1;
+    SD(K_DTH + d) = d1f(HF(F_TH), q, st[d]) * c1;
+  }
+#pragma unroll 1
+  for (int a = 0; a < 6; ++a) second_derivs(sd, K_DDGT + 6 * a, HF(F_GXX + a), q, st, c2, c11);
+  second_derivs(sd, K_DDW, HF(F_W), q, st, c2, c11);
+  second_derivs(sd, K_DDAL, HF(F_ALP), q, st, c2, c11);
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) second_derivs(sd, K_DDBE + 6 * i, HF(F_BETX + i), q, st, c2, c11);
+
+  // ---- phase 2: curvature and sources
   const float W = CV(F_W), al = CV(F_ALP);
   const float Kh = CV(F_KH), Th = CV(F_TH);
-  float gt[6], At[6], Gam[3], be[3], Bv[3];
+  float gt[6], At[6];
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
     gt[a] = CV(F_GXX + a);
     At[a] = CV(F_AXX + a);
   }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    Gam[i] = CV(F_GAMX + i);
-    be[i] = CV(F_BETX + i);
-    Bv[i] = CV(F_BX + i);
-  }
   float gtu[6];
   sym_inv_f(gt, gtu);
-
-  // first derivatives
-  float dgt[3][6], dW[3], dal[3], dGam[3][3], dbe[3][3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-#pragma unroll
-    for (int a = 0; a < 6; ++a) dgt[d][a] = d1f(HF(F_GXX + a), LF(F_GXX + a), q, st[d]) * c1;
-    dW[d] = d1f(HF(F_W), LF(F_W), q, st[d]) * c1;
-    dal[d] = d1f(HF(F_ALP), LF(F_ALP), q, st[d]) * c1;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      dGam[d][i] = d1f(HF(F_GAMX + i), LF(F_GAMX + i), q, st[d]) * c1;
-      dbe[d][i] = d1f(HF(F_BETX + i), LF(F_BETX + i), q, st[d]) * c1;
-    }
-  }
   float Gl[3][6], Gu[3][6], Gd[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -134,7 +168,8 @@ __device__ __forceinline__ void z4c_rhs_point_mixed(const float* __restrict__ H,
     for (int j = 0; j < 3; ++j)
 #pragma unroll
       for (int k = j; k < 3; ++k)
-        Gl[i][S2(j, k)] = 0.5f * (dgt[j][S2(i, k)] + dgt[k][S2(i, j)] - dgt[i][S2(j, k)]);
+        Gl[i][S2(j, k)] = 0.5f * (SD(K_DGT + 6 * j + S2(i, k)) + SD(K_DGT + 6 * k + S2(i, j)) -
+                                  SD(K_DGT + 6 * i + S2(j, k)));
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -142,95 +177,83 @@ __device__ __forceinline__ void z4c_rhs_point_mixed(const float* __restrict__ H,
       Gu[i][a] = gtu[S2(i, 0)] * Gl[0][a] + gtu[S2(i, 1)] * Gl[1][a] + gtu[S2(i, 2)] * Gl[2][a];
 #pragma unroll
   for (int i = 0; i < 3; ++i) Gd[i] = symc(gtu, Gu[i]);
-  float X[3][3][3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int l = 0; l < 3; ++l)
-        X[j][k][l] = gtu[S2(l, 0)] * Gl[j][S2(k, 0)] + gtu[S2(l, 1)] * Gl[j][S2(k, 1)] +
-                     gtu[S2(l, 2)] * Gl[j][S2(k, 2)];
+
   float Ric[6];
+  {
+    float X[3][3][3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = i; j < 3; ++j) {
-      const int ij = S2(i, j);
-      const float* fH = HF(F_GXX + ij);
-      const float* fL = LF(F_GXX + ij);
-      const float h0 = __ldg(fH + q), l0 = __ldg(fL + q);
-      float dd[6];
-      dd[0] = d2f(fH, fL, q, st[0], h0, l0) * c2;
-      dd[3] = d2f(fH, fL, q, st[1], h0, l0) * c2;
-      dd[5] = d2f(fH, fL, q, st[2], h0, l0) * c2;
-      dd[1] = d11f(fH, fL, q, st[0], st[1]) * c11;
-      dd[2] = d11f(fH, fL, q, st[0], st[2]) * c11;
-      dd[4] = d11f(fH, fL, q, st[1], st[2]) * c11;
-      float rr = -0.5f * symc(gtu, dd);
-      float t2 = 0.0f, t3 = 0.0f, t4 = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        t2 += gt[S2(k, i)] * dGam[j][k] + gt[S2(k, j)] * dGam[i][k];
-        t3 += Gd[k] * (Gl[i][S2(j, k)] + Gl[j][S2(i, k)]);
-      }
+    for (int j = 0; j < 3; ++j)
 #pragma unroll
       for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int l = 0; l < 3; ++l)
-          t4 += Gu[k][S2(l, i)] * X[j][k][l] + Gu[k][S2(l, j)] * X[i][k][l] +
-                Gu[k][S2(i, l)] * X[k][j][l];
-      Ric[ij] = rr + 0.5f * t2 + 0.5f * t3 + t4;
-    }
+          X[j][k][l] = gtu[S2(l, 0)] * Gl[j][S2(k, 0)] + gtu[S2(l, 1)] * Gl[j][S2(k, 1)] +
+                       gtu[S2(l, 2)] * Gl[j][S2(k, 2)];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const int ij = S2(i, j);
+        float dd[6];
+#pragma unroll
+        for (int b = 0; b < 6; ++b) dd[b] = SD(K_DDGT + 6 * ij + b);
+        float rr = -0.5f * symc(gtu, dd);
+        float t2 = 0.0f, t3 = 0.0f, t4 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          t2 += gt[S2(k, i)] * SD(K_DGAM + 3 * j + k) + gt[S2(k, j)] * SD(K_DGAM + 3 * i + k);
+          t3 += Gd[k] * (Gl[i][S2(j, k)] + Gl[j][S2(i, k)]);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+            t4 += Gu[k][S2(l, i)] * X[j][k][l] + Gu[k][S2(l, j)] * X[i][k][l] +
+                  Gu[k][S2(i, l)] * X[k][j][l];
+        Ric[ij] = rr + 0.5f * t2 + 0.5f * t3 + t4;
+      }
+  }
+  float dW[3], dal[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dW[d] = SD(K_DW + d);
+    dal[d] = SD(K_DAL + d);
+  }
   const float iW = 1.0f / W;
-  float DDW[6], DDal[6];
+  float DDa[6], trDDa, dWda;
   {
-    const float* WH = HF(F_W);
-    const float* WL = LF(F_W);
-    const float* aH = HF(F_ALP);
-    const float* aL = LF(F_ALP);
-    const float wh = __ldg(WH + q), wl = __ldg(WL + q), ah = __ldg(aH + q), alo = __ldg(aL + q);
-    float ddW[6], dda[6];
-    ddW[0] = d2f(WH, WL, q, st[0], wh, wl) * c2;
-    ddW[3] = d2f(WH, WL, q, st[1], wh, wl) * c2;
-    ddW[5] = d2f(WH, WL, q, st[2], wh, wl) * c2;
-    ddW[1] = d11f(WH, WL, q, st[0], st[1]) * c11;
-    ddW[2] = d11f(WH, WL, q, st[0], st[2]) * c11;
-    ddW[4] = d11f(WH, WL, q, st[1], st[2]) * c11;
-    dda[0] = d2f(aH, aL, q, st[0], ah, alo) * c2;
-    dda[3] = d2f(aH, aL, q, st[1], ah, alo) * c2;
-    dda[5] = d2f(aH, aL, q, st[2], ah, alo) * c2;
-    dda[1] = d11f(aH, aL, q, st[0], st[1]) * c11;
-    dda[2] = d11f(aH, aL, q, st[0], st[2]) * c11;
-    dda[4] = d11f(aH, aL, q, st[1], st[2]) * c11;
+    float DDW[6], DDal[6], dWW[6], dWa[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-      DDW[a] = ddW[a] - (Gu[0][a] * dW[0] + Gu[1][a] * dW[1] + Gu[2][a] * dW[2]);
-      DDal[a] = dda[a] - (Gu[0][a] * dal[0] + Gu[1][a] * dal[1] + Gu[2][a] * dal[2]);
+      DDW[a] = SD(K_DDW + a) - (Gu[0][a] * dW[0] + Gu[1][a] * dW[1] + Gu[2][a] * dW[2]);
+      DDal[a] = SD(K_DDAL + a) - (Gu[0][a] * dal[0] + Gu[1][a] * dal[1] + Gu[2][a] * dal[2]);
     }
-  }
-  float dWW[6], dWa[6];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = i; j < 3; ++j) {
-      dWW[S2(i, j)] = dW[i] * dW[j];
-      dWa[S2(i, j)] = dW[i] * dal[j] + dW[j] * dal[i];
+      for (int j = i; j < 3; ++j) {
+        dWW[S2(i, j)] = dW[i] * dW[j];
+        dWa[S2(i, j)] = dW[i] * dal[j] + dW[j] * dal[i];
+      }
+    const float trDDW = symc(gtu, DDW);
+    const float dWdW = symc(gtu, dWW);
+    dWda = 0.5f * symc(gtu, dWa);
+    trDDa = symc(gtu, DDal);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      Ric[a] += (DDW[a] + gt[a] * trDDW) * iW - 2.0f * gt[a] * dWdW * (iW * iW);
+      DDa[a] = DDal[a] + (dWa[a] - gt[a] * dWda) * iW;
     }
-  const float trDDW = symc(gtu, DDW);
-  const float dWdW = symc(gtu, dWW);
-  const float dWda = 0.5f * symc(gtu, dWa);
-  const float trDDa = symc(gtu, DDal);
-  float DDa[6];
-#pragma unroll
-  for (int a = 0; a < 6; ++a) {
-    Ric[a] += (DDW[a] + gt[a] * trDDW) * iW - 2.0f * gt[a] * dWdW * (iW * iW);
-    DDa[a] = DDal[a] + (dWa[a] - gt[a] * dWda) * iW;
   }
   const float Rsc = W * W * symc(gtu, Ric);
   const float Lapa = W * W * trDDa - W * dWda;
 
   const float K = Kh + 2.0f * Th;
+  float dbe[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dbe[d][i] = SD(K_DBE + 3 * d + i);
   const float divb = dbe[0][0] + dbe[1][1] + dbe[2][2];
   float Am[3][3], Atu[6];
 #pragma unroll
@@ -275,43 +298,30 @@ __device__ __forceinline__ void z4c_rhs_point_mixed(const float* __restrict__ H,
   r[F_KH] = -Lapa + al * (AA + K * K * (1.0f / 3.0f)) + alk1 * (1.0f - k2) * Th;
   r[F_TH] = 0.5f * al * (Rsc - AA + (2.0f / 3.0f) * K * K) - alk1 * (2.0f + k2) * Th;
   {
-    float ddb[3][6];
+    float ddivb[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float* fH = HF(F_BETX + i);
-      const float* fL = LF(F_BETX + i);
-      const float h0 = __ldg(fH + q), l0 = __ldg(fL + q);
-      ddb[i][0] = d2f(fH, fL, q, st[0], h0, l0) * c2;
-      ddb[i][3] = d2f(fH, fL, q, st[1], h0, l0) * c2;
-      ddb[i][5] = d2f(fH, fL, q, st[2], h0, l0) * c2;
-      ddb[i][1] = d11f(fH, fL, q, st[0], st[1]) * c11;
-      ddb[i][2] = d11f(fH, fL, q, st[0], st[2]) * c11;
-      ddb[i][4] = d11f(fH, fL, q, st[1], st[2]) * c11;
-    }
-    float ddivb[3], dKh[3], dTh[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      ddivb[j] = ddb[0][S2(j, 0)] + ddb[1][S2(j, 1)] + ddb[2][S2(j, 2)];
-      dKh[j] = d1f(HF(F_KH), LF(F_KH), q, st[j]) * c1;
-      dTh[j] = d1f(HF(F_TH), LF(F_TH), q, st[j]) * c1;
-    }
+    for (int j = 0; j < 3; ++j)
+      ddivb[j] = SD(K_DDBE + 0 + S2(j, 0)) + SD(K_DDBE + 6 + S2(j, 1)) + SD(K_DDBE + 12 + S2(j, 2));
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       float inner = symc(Gu[i], Atu);
-      float s = 0.0f, t = 0.0f, v = 0.0f;
+      float s = 0.0f, tt = 0.0f, v = 0.0f;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         s += Atu[S2(i, j)] * dal[j];
-        t += Atu[S2(i, j)] * dW[j];
-        v += gtu[S2(i, j)] * (2.0f * dKh[j] + dTh[j]);
+        tt += Atu[S2(i, j)] * dW[j];
+        v += gtu[S2(i, j)] * (2.0f * SD(K_DKH + j) + SD(K_DTH + j));
       }
-      inner -= 3.0f * t * iW + v * (1.0f / 3.0f);
+      inner -= 3.0f * tt * iW + v * (1.0f / 3.0f);
       float g = -2.0f * s + 2.0f * al * inner;
-      g += symc(gtu, ddb[i]);
+      float ddb[6];
+#pragma unroll
+      for (int b = 0; b < 6; ++b) ddb[b] = SD(K_DDBE + 6 * i + b);
+      g += symc(gtu, ddb);
       g += (gtu[S2(i, 0)] * ddivb[0] + gtu[S2(i, 1)] * ddivb[1] + gtu[S2(i, 2)] * ddivb[2]) * (1.0f / 3.0f);
       g += (2.0f / 3.0f) * Gd[i] * divb;
       g -= Gd[0] * dbe[0][i] + Gd[1] * dbe[1][i] + Gd[2] * dbe[2][i];
-      g -= 2.0f * alk1 * (Gam[i] - Gd[i]);
+      g -= 2.0f * alk1 * (CV(F_GAMX + i) - Gd[i]);
       r[F_GAMX + i] = g;
     }
   }
@@ -322,19 +332,23 @@ __device__ __forceinline__ void z4c_rhs_point_mixed(const float* __restrict__ H,
   const float eta = (float)prm.eta;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    r[F_BETX + i] = 0.75f * Bv[i];
-    r[F_BX + i] = r[F_GAMX + i] - eta * Bv[i];
+    const float Bv = CV(F_BX + i);
+    r[F_BETX + i] = 0.75f * Bv;
+    r[F_BX + i] = r[F_GAMX + i] - eta * Bv;
   }
+
+  // ---- phase 3: advection along the shift and dissipation, field by field
+  float be[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) be[i] = CV(F_BETX + i);
   const float cko = (float)(prm.sigma_ko / (64.0 * (double)h));
 #pragma unroll 1
   for (int f = 0; f < NF; ++f) {
-    const float* fH = HF(f);
-    const float* fL = LF(f);
-    const float h0 = __ldg(fH + q), l0 = __ldg(fL + q);
-    float adv = be[0] * dupf(fH, fL, q, st[0], be[0], h0, l0) + be[1] * dupf(fH, fL, q, st[1], be[1], h0, l0) +
-                be[2] * dupf(fH, fL, q, st[2], be[2], h0, l0);
-    float ko = delta6f(fH, fL, q, st[0], h0, l0) + delta6f(fH, fL, q, st[1], h0, l0) +
-               delta6f(fH, fL, q, st[2], h0, l0);
+    const float2* F = HF(f);
+    const float2 c = __ldg(F + q);
+    float adv = be[0] * dupf(F, q, st[0], be[0], c.x, c.y) + be[1] * dupf(F, q, st[1], be[1], c.x, c.y) +
+                be[2] * dupf(F, q, st[2], be[2], c.x, c.y);
+    float ko = delta6f(F, q, st[0], c.x, c.y) + delta6f(F, q, st[1], c.x, c.y) + delta6f(F, q, st[2], c.x, c.y);
     r[f] += adv * c1 + ko * cko;
   }
   if (prm.shift == 1) {
@@ -342,17 +356,14 @@ __device__ __forceinline__ void z4c_rhs_point_mixed(const float* __restrict__ H,
     for (int f = F_BETX; f < NF; ++f) r[f] = 0.0f;
   }
 #undef HF
-#undef LF
-#undef CV
+#undef SD
 }
 
 // ------------------------------------------------------------------ epilogue
 
-__device__ __forceinline__ void split_store(double v, float* __restrict__ h, float* __restrict__ l,
-                                            long long o) {
+__device__ __forceinline__ float2 split2(double v) {
   const float hi = __double2float_rn(v);
-  h[o] = hi;
-  l[o] = __double2float_rn(v - (double)hi);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
 // FP64 algebraic constraints of the new time level (same as the FP64 path)
@@ -418,8 +429,7 @@ __device__ __forceinline__ void rk_update_mixed(const DevPatch* P, int s, int ri
                                                 long long q, const float k[NF], double w_floor,
                                                 unsigned* err) {
   const long long fs = P->fstride;
-  const float* __restrict__ Hn = P->hs[ring];
-  const float* __restrict__ Ln = P->ls[ring];
+  const float2* __restrict__ Hn = P->hl[ring];
   double* __restrict__ y = P->buf[B_Y];
   bool bad = false;
   if (s < 4) {
@@ -427,29 +437,29 @@ __device__ __forceinline__ void rk_update_mixed(const DevPatch* P, int s, int ri
     const double bdt = bw * dt;
     const float cdt = (float)((s == 3 ? 1.0 : 0.5) * dt);
     const double* __restrict__ Un = P->buf[ring];
-    float* __restrict__ Lo = mixed_lo_out(P, s);
+    float2* __restrict__ out = mixed_out(P, s);
     float hi[NF], lo[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const long long o = f * fs + q;
       const double yn = (s == 1 ? Un[o] : y[o]) + bdt * (double)k[f];
       y[o] = yn;
-      hi[f] = Hn[o];
-      lo[f] = Ln[o] + cdt * k[f];
+      const float2 n = Hn[o];
+      hi[f] = n.x;
+      lo[f] = n.y + cdt * k[f];
       bad |= !isfinite(yn);
     }
     enforce_stage_f(hi, lo, (float)w_floor);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      Lo[f * fs + q] = lo[f];
+      out[f * fs + q] = make_float2(hi[f], lo[f]);
       bad |= !isfinite(lo[f]);
     }
   } else {
     const double bdt = dt / 6.0;
     const int nx = (ring + 1) % 3;
     double* __restrict__ Un1 = P->buf[nx];
-    float* __restrict__ Hx = P->hs[nx];
-    float* __restrict__ Lx = P->ls[nx];
+    float2* __restrict__ Hx = P->hl[nx];
     double v[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) v[f] = y[f * fs + q] + bdt * (double)k[f];
@@ -458,7 +468,7 @@ __device__ __forceinline__ void rk_update_mixed(const DevPatch* P, int s, int ri
     for (int f = 0; f < NF; ++f) {
       const long long o = f * fs + q;
       Un1[o] = v[f];
-      split_store(v[f], Hx, Lx, o);
+      Hx[o] = split2(v[f]);
       bad |= !isfinite(v[f]);
     }
   }
@@ -466,7 +476,8 @@ __device__ __forceinline__ void rk_update_mixed(const DevPatch* P, int s, int ri
 }
 
 template <int MODE>  // 0: RK stage, 1: RHS only (FP64 output in S1)
-__global__ void __launch_bounds__(128) z4c_stage_mixed_kernel(StageArgs A) {
+__global__ void __launch_bounds__(MIX_THREADS, 3) z4c_stage_mixed_kernel(StageArgs A) {
+  extern __shared__ float sd[];  // ND x MIX_THREADS derivative slots
   const Tile tl = A.tiles[blockIdx.x];
   const DevPatch* P = A.patches + tl.patch;
   const int i = tl.x0 + (threadIdx.x & 31);
@@ -477,10 +488,9 @@ __global__ void __launch_bounds__(128) z4c_stage_mixed_kernel(StageArgs A) {
   const int s = A.stage;
   const long long sy = P->px, sz = P->plane, fs = P->fstride;
   const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
-  const float* __restrict__ H = P->hs[ring];
-  const float* __restrict__ L = MODE ? P->ls[ring] : mixed_lo_in(P, s, ring);
+  const float2* __restrict__ U = MODE ? P->hl[ring] : mixed_in(P, s, ring);
   float r[NF];
-  z4c_rhs_point_mixed(H, L, q, sy, sz, fs, (float)P->dx, A.prm, r);
+  z4c_rhs_point_mixed(U, q, sy, sz, fs, (float)P->dx, A.prm, sd, r);
   if (MODE == 1) {
     double* out = P->buf[B_S1];
 #pragma unroll
@@ -501,8 +511,7 @@ __global__ void __launch_bounds__(128) sommerfeld_mixed_kernel(GhostArgs A) {
   const int s = A.stage;
   const long long sy = P->px, sz = P->plane, fs = P->fstride;
   const long long q = i + (long long)j * sy + (long long)k * sz;
-  const float* __restrict__ H = P->hs[ring];
-  const float* __restrict__ L = mixed_lo_in(P, s, ring);
+  const float2* __restrict__ U = mixed_in(P, s, ring);
   const double h = P->dx;
   const int idx[3] = {i, j, k};
   const long long st[3] = {1, sy, sz};
@@ -518,15 +527,16 @@ __global__ void __launch_bounds__(128) sommerfeld_mixed_kernel(GhostArgs A) {
   float kk[NF];
 #pragma unroll 1
   for (int f = 0; f < NF; ++f) {
-    const float* fH = H + (long long)f * fs;
-    const float* fL = L + (long long)f * fs;
-    const float h0 = fH[q], l0 = fL[q];
+    const float2* F = U + (long long)f * fs;
+    const float2 c0 = F[q];
+    const float h0 = c0.x, l0 = c0.y;
     float acc = ((h0 - (float)flat_value(f)) + l0) * ir;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const long long o = xd[d] > 0.0 ? -st[d] : st[d];
       // (3 f0 - 4 f1 + f2) on centre differences
-      float v = (-4.0f * ((fH[q + o] - h0) + (fL[q + o] - l0)) + ((fH[q + 2 * o] - h0) + (fL[q + 2 * o] - l0))) * c;
+      const float2 a1 = F[q + o], a2 = F[q + 2 * o];
+      float v = (-4.0f * ((a1.x - h0) + (a1.y - l0)) + ((a2.x - h0) + (a2.y - l0))) * c;
       float dfd = xd[d] > 0.0 ? v : -v;
       acc += (x[d] * ir) * dfd;
     }
@@ -544,17 +554,27 @@ __global__ void split_kernel(const DevPatch* patches, const DevLevel* levels, in
   const int I = id % P->NX, J = (id / P->NX) % P->NY, K = id / ((long long)P->NX * P->NY);
   const long long q = I + (long long)J * P->px + (long long)K * P->plane;
   const int ring = levels[P->level].ring;
-  for (int f = 0; f < NF; ++f) split_store(P->buf[ring][f * P->fstride + q], P->hs[ring], P->ls[ring], f * P->fstride + q);
+  for (int f = 0; f < NF; ++f) P->hl[ring][f * P->fstride + q] = split2(P->buf[ring][f * P->fstride + q]);
 }
 
 }  // namespace
 
 void launch_stage_mixed(const StageArgs& a, cudaStream_t st) {
   if (a.ntiles == 0) return;
+  const size_t smem = sizeof(float) * ND * MIX_THREADS;
+  // opt in to more than 48 KB of dynamic shared memory, once per device
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaFuncSetAttribute(z4c_stage_mixed_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(z4c_stage_mixed_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set[dev] = true;
+  }
   if (a.stage == 0)
-    z4c_stage_mixed_kernel<1><<<a.ntiles, 128, 0, st>>>(a);
+    z4c_stage_mixed_kernel<1><<<a.ntiles, MIX_THREADS, smem, st>>>(a);
   else
-    z4c_stage_mixed_kernel<0><<<a.ntiles, 128, 0, st>>>(a);
+    z4c_stage_mixed_kernel<0><<<a.ntiles, MIX_THREADS, smem, st>>>(a);
 }
 
 void launch_sommerfeld_mixed(const GhostArgs& a, int npatches, long long max_shell, cudaStream_t st) {

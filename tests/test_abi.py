@@ -37,8 +37,8 @@ def test_arena_bytes_host_side(L):
     h = idd.binary_7_level()
     def copies(mixed):
         # 6 FP64 state copies per patch, 3 prolongation caches on levels > 0,
-        # mixed precision: 8 FP32 copies (= 4 FP64 copies)
-        return sum((6 + (3 if p.level > 0 else 0) + (4 if mixed else 0)) * 25 * 8 *
+        # mixed precision: 5 copies of FP32 hi/lo pairs (= 5 FP64 copies)
+        return sum((6 + (3 if p.level > 0 else 0) + (5 if mixed else 0)) * 25 * 8 *
                    (p.n[0] + 6 + (-(p.n[0] + 6)) % 8) * (p.n[1] + 6) * (p.n[2] + 6) for p in h.patches)
     n = sk.arena_bytes(len(h.levels), h.patches)
     assert copies(False) <= n < copies(False) + 64 * 2 ** 20
