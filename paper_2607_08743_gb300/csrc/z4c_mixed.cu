@@ -87,27 +87,23 @@ __device__ __forceinline__ float symc(const float S[6], const float T[6]) {
 // every derivative in registers needed (255 registers with spills, 8 warps per
 // SM), so more warps hide the latency of the stencil loads.
 constexpr int MIX_THREADS = 128;
-constexpr int ND = 114;  // derivatives kept per point
+constexpr int ND = 139;  // values kept per point
 // slots: dgt[d][a] 0..17, dW 18..20, dal 21..23, dGam[d][i] 24..32,
 // dbe[d][i] 33..41, dKh 42..44, dTh 45..47, ddgt[a][lm] 48..83, ddW 84..89,
-// ddal 90..95, ddbe[i][lm] 96..113
+// ddal 90..95, ddbe[i][lm] 96..113, advection + dissipation of field f 114 + f
 enum {
   K_DGT = 0, K_DW = 18, K_DAL = 21, K_DGAM = 24, K_DBE = 33, K_DKH = 42, K_DTH = 45,
-  K_DDGT = 48, K_DDW = 84, K_DDAL = 90, K_DDBE = 96
+  K_DDGT = 48, K_DDW = 84, K_DDAL = 90, K_DDBE = 96, K_AK = 114
 };
-
-// all six second derivatives of one field into slots k0..k0+5 (xx xy xz yy yz zz)
-__device__ __forceinline__ void second_derivs(float* sd, int k0, const float2* F, long long q,
-                                              const long long st[3], float c2, float c11) {
-  const int t = threadIdx.x;
-  const float2 c = __ldg(F + q);
-  sd[(k0 + 0) * MIX_THREADS + t] = d2f(F, q, st[0], c.x, c.y) * c2;
-  sd[(k0 + 3) * MIX_THREADS + t] = d2f(F, q, st[1], c.x, c.y) * c2;
-  sd[(k0 + 5) * MIX_THREADS + t] = d2f(F, q, st[2], c.x, c.y) * c2;
-  sd[(k0 + 1) * MIX_THREADS + t] = d11f(F, q, st[0], st[1]) * c11;
-  sd[(k0 + 2) * MIX_THREADS + t] = d11f(F, q, st[0], st[2]) * c11;
-  sd[(k0 + 4) * MIX_THREADS + t] = d11f(F, q, st[1], st[2]) * c11;
-}
+// per field: slot of its x first derivative and the stride to y, z (-1: not
+// needed), and the first of its six second-derivative slots (-1: not needed)
+__constant__ int c_d1base[NF] = {K_DW, K_DGT + 0, K_DGT + 1, K_DGT + 2, K_DGT + 3, K_DGT + 4, K_DGT + 5,
+                                 K_DKH, K_DTH, -1, -1, -1, -1, -1, -1, K_DGAM + 0, K_DGAM + 1, K_DGAM + 2,
+                                 K_DAL, K_DBE + 0, K_DBE + 1, K_DBE + 2, -1, -1, -1};
+__constant__ int c_d1stride[NF] = {1, 6, 6, 6, 6, 6, 6, 1, 1, 0, 0, 0, 0, 0, 0, 3, 3, 3, 1, 3, 3, 3, 0, 0, 0};
+__constant__ int c_d2base[NF] = {K_DDW, K_DDGT + 0, K_DDGT + 6, K_DDGT + 12, K_DDGT + 18, K_DDGT + 24,
+                                 K_DDGT + 30, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
+                                 K_DDAL, K_DDBE + 0, K_DDBE + 6, K_DDBE + 12, -1, -1, -1};
 
 // Z4c RHS of one point in FP32 from the split state U (hi, lo interleaved);
 // r[f] gets the full RHS (sources + advection + dissipation).  sd: this CTA's
@@ -128,27 +124,44 @@ __device__ __forceinline__ void z4c_rhs_point_mixed(const float2* __restrict__ U
     return v.x + v.y;
   };
 
-  // ---- phase 1: derivatives into shared memory
+  // ---- phase 1: one pass over the fields: the 7-point star along each axis
+  // gives the first and second derivatives, the lopsided advection and the
+  // Kreiss-Oliger term from the same six differences; the mixed second
+  // derivatives add the off-axis points.  Everything goes to shared memory.
+  float be[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) be[i] = CV(F_BETX + i);
+  const float cko = (float)(prm.sigma_ko / (64.0 * (double)h));
 #pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
+  for (int f = 0; f < NF; ++f) {
+    const float2* F = HF(f);
+    const float2 c0 = __ldg(F + q);
+    const float h0 = c0.x, l0 = c0.y;
+    const int s1 = c_d1base[f], s1d = c_d1stride[f], s2 = c_d2base[f];
+    float ko = 0.0f, adv = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 6; ++a) SD(K_DGT + 6 * d + a) = d1f(HF(F_GXX + a), q, st[d]) * c1;
-    SD(K_DW + d) = d1f(HF(F_W), q, st[d]) * c1;
-    SD(K_DAL + d) = d1f(HF(F_ALP), q, st[d]) * c1;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      SD(K_DGAM + 3 * d + i) = d1f(HF(F_GAMX + i), q, st[d]) * c1;
-      SD(K_DBE + 3 * d + i) = d1f(HF(F_BETX + i), q, st[d]) * c1;
+    for (int d = 0; d < 3; ++d) {
+      const long long o = st[d];
+      const float cm3 = cdiff(F, q - 3 * o, h0, l0), cm2 = cdiff(F, q - 2 * o, h0, l0);
+      const float cm1 = cdiff(F, q - o, h0, l0), cp1 = cdiff(F, q + o, h0, l0);
+      const float cp2 = cdiff(F, q + 2 * o, h0, l0), cp3 = cdiff(F, q + 3 * o, h0, l0);
+      ko += (cm3 + cp3) - 6.0f * (cm2 + cp2) + 15.0f * (cm1 + cp1);
+      // lopsided: one point behind and three ahead along the shift; the
+      // mirrored branch is the same expression on mirrored points, negated
+      const bool pos = be[d] > 0.0f;
+      const float ua = pos ? cm1 : cp1, ub = pos ? cp1 : cm1, uc = pos ? cp2 : cm2, ud = pos ? cp3 : cm3;
+      const float v = -3.0f * ua + 18.0f * ub - 6.0f * uc + ud;
+      adv += be[d] * (pos ? v : -v);
+      if (s1 >= 0) SD(s1 + s1d * d) = (8.0f * (cp1 - cm1) - (cp2 - cm2)) * c1;
+      if (s2 >= 0) SD(s2 + (d == 0 ? 0 : (d == 1 ? 3 : 5))) = (16.0f * (cp1 + cm1) - (cp2 + cm2)) * c2;
     }
-    SD(K_DKH + d) = d1f(HF(F_KH), q, st[d]) * c1;
-    SD(K_DTH + d) = d1f(HF(F_TH), q, st[d]) * c1;
+    if (s2 >= 0) {
+      SD(s2 + 1) = d11f(F, q, st[0], st[1]) * c11;
+      SD(s2 + 2) = d11f(F, q, st[0], st[2]) * c11;
+      SD(s2 + 4) = d11f(F, q, st[1], st[2]) * c11;
+    }
+    SD(K_AK + f) = adv * c1 + ko * cko;
   }
-#pragma unroll 1
-  for (int a = 0; a < 6; ++a) second_derivs(sd, K_DDGT + 6 * a, HF(F_GXX + a), q, st, c2, c11);
-  second_derivs(sd, K_DDW, HF(F_W), q, st, c2, c11);
-  second_derivs(sd, K_DDAL, HF(F_ALP), q, st, c2, c11);
-#pragma unroll 1
-  for (int i = 0; i < 3; ++i) second_derivs(sd, K_DDBE + 6 * i, HF(F_BETX + i), q, st, c2, c11);
 
   // ---- phase 2: curvature and sources
   const float W = CV(F_W), al = CV(F_ALP);
@@ -337,20 +350,9 @@ __device__ __forceinline__ void z4c_rhs_point_mixed(const float2* __restrict__ U
     r[F_BX + i] = r[F_GAMX + i] - eta * Bv;
   }
 
-  // ---- phase 3: advection along the shift and dissipation, field by field
-  float be[3];
+  // advection and dissipation from phase 1
 #pragma unroll
-  for (int i = 0; i < 3; ++i) be[i] = CV(F_BETX + i);
-  const float cko = (float)(prm.sigma_ko / (64.0 * (double)h));
-#pragma unroll 1
-  for (int f = 0; f < NF; ++f) {
-    const float2* F = HF(f);
-    const float2 c = __ldg(F + q);
-    float adv = be[0] * dupf(F, q, st[0], be[0], c.x, c.y) + be[1] * dupf(F, q, st[1], be[1], c.x, c.y) +
-                be[2] * dupf(F, q, st[2], be[2], c.x, c.y);
-    float ko = delta6f(F, q, st[0], c.x, c.y) + delta6f(F, q, st[1], c.x, c.y) + delta6f(F, q, st[2], c.x, c.y);
-    r[f] += adv * c1 + ko * cko;
-  }
+  for (int f = 0; f < NF; ++f) r[f] += SD(K_AK + f);
   if (prm.shift == 1) {
 #pragma unroll
     for (int f = F_BETX; f < NF; ++f) r[f] = 0.0f;
