@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -174,7 +175,17 @@ def main():
     ap.add_argument("--courant", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--case", default="amr7", choices=["amr7", "uniform96", "mixed-error"],
+    ap.add_argument("--kernel", type=int, default=None,
+                    help="uniform96: force this stage kernel (0 direct, 1-4 TMA tiles) after autotuning")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default stage kernels instead of timing them first")
+    ap.add_argument("--sizes", default="32,64,128", help="gauge-wave / robust-stability grid sizes")
+    ap.add_argument("--sweep-sizes", default="48,64,96,128,160,192", help="sweep: single-patch sizes")
+    ap.add_argument("--no-coarse", action="store_true", help="sweep: skip the full 10-level coarse step")
+    ap.add_argument("--gw-steps", type=int, default=1000,
+                    help="gauge-wave: RK4 steps on the coarsest grid; robust-stability: steps per grid")
+    ap.add_argument("--case", default="amr7",
+                    choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep"],
                     help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
                          "mixed-error: the 7-level hierarchy in FP64 and mixed precision side by side")
     ap.add_argument("--coarse-steps", type=int, default=64, help="mixed-error: coarse steps")
@@ -203,6 +214,15 @@ def main():
         return
     if args.case == "mixed-error":
         mixed_error_case(torch, sk, args)
+        return
+    if args.case == "sweep":
+        sweep_case(torch, sk, args)
+        return
+    if args.case == "gauge-wave":
+        gauge_wave_case(torch, sk, args)
+        return
+    if args.case == "robust-stability":
+        robust_stability_case(torch, sk, args)
         return
 
     h = hierarchy()
@@ -266,6 +286,9 @@ def roofline(r, hbm):
         ach = k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9
         out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+    out["stage_kernels"] = k.get("stage_kernels")
+    if k.get("autotune"):
+        out["autotune"] = k["autotune"]
     out.update({"traffic": NCU_TRAFFIC_PER_ZONE[0 if r["precision"] == "fp64" else 1] * k["zones_per_launch"],
                 "kernel": k["name"], "launch_ms": k["ms"], "launches_per_step": k["launches"] / k["steps"],
                 "share_of_step": k["ms"] * k["launches"] / k["steps"] / r["ms"],
@@ -280,6 +303,11 @@ def measure(torch, sk, h, precision, args, world, dist):
     stream = torch.cuda.Stream()
     g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=stream)
     g.set_initial_data(1, h.masses, h.positions)
+    tune = None
+    if precision == "mixed" and not args.no_autotune:
+        us = g.autotune(reps=3)
+        tune = {"kernels": [sk.STAGE_KERNELS[g.stage_kernel(l)] for l in range(len(h.levels))],
+                "us_per_launch": [[round(float(x), 1) for x in row] for row in us]}
     for _ in range(args.warmup):
         g.level_step(0)
     torch.cuda.synchronize()
@@ -303,12 +331,194 @@ def measure(torch, sk, h, precision, args, world, dist):
     kern = stage_kernel_timing(g, nprof)
     kern["steps"] = nprof
     g.close()
+    kern["stage_kernels"] = [sk.STAGE_KERNELS[k] for k in kern.pop("kernel_ids")]
+    if tune:
+        kern["autotune"] = tune
     out = {"precision": precision, "value": world * zu / (ms * 1e-3), "ms": ms, "kern": kern,
            "constraints_l0": norms,
            "bytes_per_zone_update": BYTES_PER_ZONE_UPDATE_MIXED if precision == "mixed" else BYTES_PER_ZONE_UPDATE}
     if not args.no_e2e:
         out["e2e"] = end_to_end(torch, sk, h, prm, args, world, dist)
     return out
+
+
+def _gw_grid(torch, sk, n, precision, **prm):
+    """Periodic unit box [-1/2, 1/2]^3 with n^3 cells, harmonic slicing,
+    frozen shift, Courant 0.25 (the gauge-wave / robust-stability setup)."""
+    import initial_data as idd
+    p = idd.centred_patch(n, 1.0 / n)
+    g = sk.Grid(1, p.dx, [p], sk.Params(lapse=1, shift=1, bc=1, courant=0.25, precision=precision),
+                stream=torch.cuda.Stream())
+    return p, g
+
+
+def gauge_wave_case(torch, sk, args):
+    """Gauge wave A = 0.01, wavelength = box size 1, on periodic 3D grids of
+    32^3, 64^3 and 128^3 cells: 1000 RK4 steps at 32^3 and the same final time
+    t = 1000 * 0.25 / 32 on the finer grids (2000 and 4000 steps).  Reports
+    the max-norm error against the closed form per resolution, the
+    convergence rates, the constraint norms and the wall time."""
+    import initial_data as idd
+    sizes = [int(x) for x in args.sizes.split(",")]
+    steps0 = args.gw_steps
+    t_final = steps0 * 0.25 / sizes[0]
+    out = {"case": "gauge-wave", "amp": 0.01, "wavelength": 1.0, "courant": 0.25, "t_final": t_final,
+           "precision": args.precision if args.precision != "both" else "fp64", "runs": []}
+    prec = 1 if out["precision"] == "mixed" else 0
+    errs = []
+    for n in sizes:
+        p, g = _gw_grid(torch, sk, n, prec)
+        g.set_initial_data(2, gw_amp=0.01, gw_len=1.0)
+        nsteps = steps0 * n // sizes[0]
+        h0 = g.constraints(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = []
+        for s in range(nsteps):
+            g.rk4_step(0)
+            if (s + 1) % (nsteps // 4) == 0:
+                hist.append([s + 1] + list(map(float, g.constraints(0))))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        u = g.download_fields(0)[:, 3:-3, 3:-3, 3:-3]
+        ex = idd.gauge_wave(p, 0.01, t=g.level_time(0))[:, 3:-3, 3:-3, 3:-3]
+        e = np.abs(u - ex).max(axis=(1, 2, 3))
+        errs.append(float(e.max()))
+        out["runs"].append({"n": n, "steps": nsteps, "t": g.level_time(0), "max_err": float(e.max()),
+                            "max_err_per_field": {k: float(v) for k, v in zip(idd.FIELD_NAMES, e) if v > 0},
+                            "constraints_t0": list(map(float, h0)), "constraints_history": hist,
+                            "wall_s": wall, "zone_updates_per_s": n ** 3 * nsteps / wall})
+        g.close()
+    out["rates"] = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    print(json.dumps(out), flush=True)
+
+
+def robust_stability_case(torch, sk, args):
+    """Minkowski plus uniform noise of amplitude 1e-10 (dx/dx0)^2, dx0 = 1/32,
+    on periodic 32^3, 64^3, 128^3 grids, 1000 RK4 steps each (Courant 0.25,
+    harmonic slicing, frozen shift); the Hamiltonian and momentum constraint
+    norms every 100 steps."""
+    import initial_data as idd
+    sizes = [int(x) for x in args.sizes.split(",")]
+    out = {"case": "robust-stability", "courant": 0.25, "steps": args.gw_steps,
+           "precision": args.precision if args.precision != "both" else "fp64", "runs": []}
+    prec = 1 if out["precision"] == "mixed" else 0
+    for n in sizes:
+        p, g = _gw_grid(torch, sk, n, prec)
+        amp = 1e-10 * (32.0 / n) ** 2
+        g.set_initial_data(0, noise_amp=amp, seed=idd.STABILITY_SEED)
+        flat = idd.minkowski(p)[:, 3:-3, 3:-3, 3:-3]
+
+        def dev():
+            d = np.abs(g.download_fields(0)[:, 3:-3, 3:-3, 3:-3] - flat)
+            return [float(x) for x in d.max(axis=(1, 2, 3))]
+
+        hist = [[0] + list(map(float, g.constraints(0)))]
+        devs = [[0] + dev()]
+        for s in range(args.gw_steps):
+            g.rk4_step(0)
+            if (s + 1) % 100 == 0:
+                hist.append([s + 1] + list(map(float, g.constraints(0))))
+                devs.append([s + 1] + dev())
+        out["runs"].append({"n": n, "noise_amp": amp, "t": g.level_time(0), "constraints_history": hist,
+                            "field_names": idd.FIELD_NAMES, "max_dev_from_flat_history": devs,
+                            "growth_H": hist[-1][1] / hist[0][1] if hist[0][1] > 0 else None})
+        g.close()
+    print(json.dumps(out), flush=True)
+
+
+def _time_rk4(torch, g, level, steps, warm=1):
+    for _ in range(warm):
+        g.rk4_step(level)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(g.stream)
+    for _ in range(steps):
+        g.rk4_step(level)
+    e1.record(g.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def sweep_case(torch, sk, args):
+    """Large-AMR throughput sweep.  (a) Single patches of 48^3 .. 192^3
+    (Brill-Lindquist m = 1 at the centre, Sommerfeld ghosts): the autotuned
+    mixed-precision stage kernel and the FP64 kernel, zone updates/s of RK4
+    steps and the HBM fraction.  (b) The 10-level hierarchy (L0-L5 one 192^3
+    patch, L6-L9 two 160^3 patches around m = 0.6 / 0.4 punctures): per level,
+    the zone updates/s of one RK4 step of that level (its ghost fills
+    included) in both precisions, and one full coarse step (1023 level steps,
+    one CUDA graph) in mixed precision."""
+    import initial_data as idd
+    hbm = float(_peaks().get("hbm_gbs", 6800.0))
+    out = {"case": "amr10-sweep", "hbm_gbs": hbm, "courant": args.courant, "patches": [], "levels": []}
+    for n in [int(x) for x in args.sweep_sizes.split(",")]:
+        p = idd.centred_patch(n, 16.0 / n)
+        row = {"n": n}
+        for prec in (1, 0):
+            g = sk.Grid(1, p.dx, [p], sk.Params(courant=args.courant, precision=prec), stream=torch.cuda.Stream())
+            g.set_initial_data(1, [1.0], [(0.0, 0.0, 0.0)])
+            key = "mixed" if prec else "fp64"
+            if prec:
+                us = g.autotune(reps=3, use_cache=False)[0]
+                row["autotune_us_per_stage1"] = [round(float(x), 1) for x in us]
+                row["kernel"] = sk.STAGE_KERNELS[g.stage_kernel(0)]
+            ms = _time_rk4(torch, g, 0, 5 if prec else 2)
+            zu = p.active_points / (ms * 1e-3)
+            bpz = BYTES_PER_ZONE_UPDATE_MIXED if prec else BYTES_PER_ZONE_UPDATE
+            row[key] = {"ms_per_rk4_step": ms, "zone_updates_per_s": zu, "hbm_frac": zu * bpz / (hbm * 1e9)}
+            g.close()
+            del g
+            torch.cuda.empty_cache()
+        out["patches"].append(row)
+        print(json.dumps(row), flush=True)
+    h = idd.binary_10_level()
+    for prec in (1, 0):
+        prm = sk.Params(courant=args.courant, precision=prec)
+        need = sk.arena_bytes(len(h.levels), h.patches, prm)
+        free, total = torch.cuda.mem_get_info()
+        key = "mixed" if prec else "fp64"
+        if need > free - (8 << 30):
+            out["levels"].append({key: "skipped: arena %.1f GB, free %.1f GB" % (need / 1e9, free / 1e9)})
+            continue
+        g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=torch.cuda.Stream())
+        g.set_initial_data(1, h.masses, h.positions)
+        res = {"precision": key, "arena_gb": need / 1e9, "per_level": []}
+        if prec:
+            g.autotune(reps=2)
+        for l, lv in enumerate(h.levels):
+            act = sum(p.active_points for p in lv)
+            ms = _time_rk4(torch, g, l, 2)
+            zu = act / (ms * 1e-3)
+            bpz = BYTES_PER_ZONE_UPDATE_MIXED if prec else BYTES_PER_ZONE_UPDATE
+            res["per_level"].append({"level": l, "patches": [list(p.n) for p in lv],
+                                     "kernel": sk.STAGE_KERNELS[g.stage_kernel(l)],
+                                     "ms_per_rk4_step": ms, "zone_updates_per_s": zu,
+                                     "hbm_frac": zu * bpz / (hbm * 1e9)})
+        if prec and not args.no_coarse:
+            # the RK4 steps above advanced the levels independently: start the
+            # coarse step from fresh data
+            g.set_initial_data(1, h.masses, h.positions)
+            g.level_step(0)  # records the graph
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(g.stream)
+            g.level_step(0)
+            e1.record(g.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            zu = h.zone_updates_per_coarse_step()
+            res["coarse_step"] = {"ms": ms, "zone_updates": zu, "zone_updates_per_s": zu / (ms * 1e-3),
+                                  "hbm_frac": zu / (ms * 1e-3) * BYTES_PER_ZONE_UPDATE_MIXED / (hbm * 1e9),
+                                  "constraints_l0": list(map(float, g.constraints(0)))}
+        out["levels"].append(res)
+        print(json.dumps(res), flush=True)
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
 
 
 def uniform_case(torch, sk, args):
@@ -321,6 +531,11 @@ def uniform_case(torch, sk, args):
     stream = torch.cuda.Stream()
     g = sk.Grid(1, p.dx, [p], prm, stream=stream)  # (--precision both runs FP64 here)
     g.set_initial_data(1, h.masses, h.positions)
+    tune = None
+    if prm.precision == 1:
+        tune = [round(float(x), 1) for x in g.autotune(reps=3, use_cache=False)[0]]
+        if args.kernel is not None:
+            g.set_stage_kernel(0, args.kernel)
     for _ in range(args.warmup):
         g.rk4_step(0)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -334,7 +549,9 @@ def uniform_case(torch, sk, args):
     ms = e0.elapsed_time(e1) / args.steps
     g.constraints(0)
     print(json.dumps({"case": "uniform96", "ms_per_rk4_step": ms,
-                      "zone_updates_per_s": p.active_points / (ms * 1e-3)}), flush=True)
+                      "zone_updates_per_s": p.active_points / (ms * 1e-3),
+                      "stage_kernel": sk.STAGE_KERNELS[g.stage_kernel(0)],
+                      "autotune_us_per_stage1_launch": tune}), flush=True)
     g.close()
 
 
@@ -387,6 +604,7 @@ def stage_kernel_timing(g, steps):
     """Average duration of one launch of the fused RHS + RK4 stage kernel over
     `steps` coarse steps, from CUDA events bracketing every launch on the
     grid's stream (eager launches while profiling is on)."""
+    ids = [g.stage_kernel(l) for l in range(g.nlevels)]
     g.profile_enable(True)
     for _ in range(steps):
         g.level_step(0)
@@ -395,7 +613,13 @@ def stage_kernel_timing(g, steps):
     per = ms / n
     zones_per_launch = zones / n
     fz = FLOPS_PER_ZONE_STAGE.get(g.params.precision)
-    return {"name": "z4c_stage_fp64_kernel" if g.params.precision == 0 else "z4c_stage_mixed_kernel",
+    if g.params.precision == 0:
+        name = "z4c_stage_fp64_kernel"
+    else:
+        names = sorted({"z4c_stage_mixed_kernel" if k == 0 else "z4c_stage_tma_kernel (%s)" % sk.STAGE_KERNELS[k]
+                        for k in ids})
+        name = " + ".join(names)
+    return {"name": name, "kernel_ids": ids,
             "ms": per, "launches": n, "share_of_step": None,
             "bytes_per_launch": zones_per_launch * (BYTES_PER_ZONE_UPDATE_MIXED if g.params.precision == 1
                                                     else BYTES_PER_ZONE_UPDATE) / 4.0,

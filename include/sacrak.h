@@ -180,6 +180,32 @@ sacrak_status sacrak_profile_read(sacrak_grid* grid, double* stage_ms, long long
 sacrak_status sacrak_constraints_noalloc(const double* dev_u, const int n[3], double dx,
                                          double w_excise, void* cuda_stream, double out_l2[4]);
 
+/* Stage kernel of a level.  kernel 0: the direct kernel (every stencil value
+ * read through the L1 cache); kernel 1..4 (mixed precision only): the
+ * TMA-staged kernel with tiles of 32 x 4 x 1, 32 x 2 x 2, 32 x 4 x 2 and
+ * 32 x 8 x 1 points, which copies each field's tile plus its 3-cell halo into
+ * shared memory with tensor-memory-accelerator loads and walks all tiles of
+ * the level in one persistent launch.  All kernels compute the same RHS up to
+ * FP32 rounding order.  A TMA kernel needs at most 8 patches on the level and
+ * at least 32 x TY x TZ active cells per patch, else SACRAK_EINVAL.  New grids
+ * use kernel 1 where it fits and 0 elsewhere.  Changing the kernel of a level
+ * drops the recorded CUDA graph of the coarse step (it is recorded again at
+ * the next sacrak_level_step). */
+sacrak_status sacrak_set_stage_kernel(sacrak_grid* grid, int level, int kernel);
+sacrak_status sacrak_get_stage_kernel(sacrak_grid* grid, int level, int* kernel);
+
+/* Autotuner of the stage kernel: for every level, times RK4 stage 1 (which
+ * reads the current time level and writes only the RK accumulator and the
+ * first stage buffer, so the state is unchanged) with every kernel usable on
+ * that level, `reps` launches each after one warm-up launch (CUDA events on
+ * the grid's stream), and selects the fastest.  Results are cached for the
+ * process, keyed by device, precision and the level's patch shapes; with
+ * use_cache != 0 a cached level is not timed again.  us_per_launch, if not
+ * NULL, receives nlevels x 5 timings in microseconds (kernel 0..4 of each
+ * level; -1 where not timed).  Synchronises the stream; must not be called
+ * while the stream is being captured (SACRAK_ESTATE). */
+sacrak_status sacrak_autotune(sacrak_grid* grid, int reps, int use_cache, double* us_per_launch);
+
 /* Current time of a level. */
 sacrak_status sacrak_level_time(sacrak_grid* grid, int level, double* t);
 

@@ -29,7 +29,11 @@ EXPORTS = [
     "sacrak_upload_fields", "sacrak_download_fields", "sacrak_rhs", "sacrak_rk4_step",
     "sacrak_level_step", "sacrak_constraints", "sacrak_pi_symmetry", "sacrak_level_time",
     "sacrak_last_error", "sacrak_profile_enable", "sacrak_profile_read", "sacrak_constraints_noalloc",
+    "sacrak_set_stage_kernel", "sacrak_get_stage_kernel", "sacrak_autotune",
 ]
+
+# stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles
+STAGE_KERNELS = {0: "direct", 1: "tma 32x4x1", 2: "tma 32x2x2", 3: "tma 32x4x2", 4: "tma 32x8x1"}
 
 
 class SacrakError(RuntimeError):
@@ -85,6 +89,9 @@ def lib() -> ctypes.CDLL:
             L.sacrak_profile_read.argtypes = [vp, dp, P(ctypes.c_longlong), P(ctypes.c_longlong)]
             L.sacrak_constraints_noalloc.argtypes = [vp, P(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                                      vp, dp]
+            L.sacrak_set_stage_kernel.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            L.sacrak_get_stage_kernel.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+            L.sacrak_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
             L.sacrak_last_error.argtypes = [vp]
             L.sacrak_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
@@ -270,6 +277,24 @@ class Grid:
         self._check(lib().sacrak_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(z)),
                     "profile_read")
         return ms.value, n.value, z.value
+
+    def set_stage_kernel(self, level: int, kernel: int):
+        """Stage kernel of a level: 0 direct, 1..4 TMA-staged (see STAGE_KERNELS)."""
+        self._check(lib().sacrak_set_stage_kernel(self._h, level, kernel), "set_stage_kernel")
+
+    def stage_kernel(self, level: int) -> int:
+        v = ctypes.c_int()
+        self._check(lib().sacrak_get_stage_kernel(self._h, level, ctypes.byref(v)), "get_stage_kernel")
+        return v.value
+
+    def autotune(self, reps: int = 3, use_cache: bool = True) -> np.ndarray:
+        """Time every usable stage kernel on every level and keep the fastest;
+        returns the timings (nlevels x 5, microseconds per launch, -1 = not
+        timed) and leaves the choice in place."""
+        out = np.full((self.nlevels, len(STAGE_KERNELS)), -1.0)
+        self._check(lib().sacrak_autotune(self._h, reps, int(use_cache),
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "autotune")
+        return out
 
     def last_error(self) -> str:
         return lib().sacrak_last_error(self._h).decode()

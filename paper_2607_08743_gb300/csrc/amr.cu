@@ -2,6 +2,8 @@
 // periodic and frozen ghost fills, 6th-order Lagrange prolongation of child
 // ghosts with quadratic (linear on the first step) time interpolation between
 // parent time levels, 4th-order Lagrange restriction, same-level exchange.
+#include <type_traits>
+
 #include "sacrak_dev.cuh"
 
 namespace sacrak {
@@ -98,220 +100,174 @@ __device__ __forceinline__ int floor_half(int i) { return i >= 0 ? i / 2 : -((-i
 // child (Sec. 2.2.1, 6th-order Lagrange, tensor product).  The result is
 // cached per parent ring slot in the child's gsh[slot]; the per-stage ghost
 // fill then only combines the cached slots in time (ghost_time_fill_kernel),
-// so the 6^3 stencils run twice per parent step instead of at every child
-// stage.  One thread computes one field of the 2x2x2 children of one parent
-// cell from its 7^3 neighbourhood with separable x, y, z passes (the even
-// child sits at -1/4 of the parent cell, nodes -3..2; the odd one at +1/4,
-// nodes -2..3).
+// so the spatial stencils run twice per parent step instead of at every child
+// stage.
+//
+// The parent cells whose children reach the child's ghost shell form a shell
+// of width 2 around the parent cells under the child's active region: the
+// box of m = n/2 + 4 cells per axis (parent cells off-2 .. off+n/2+1) minus
+// its interior.  That shell is cut into six slabs (two per axis, 2 cells
+// thick) and each slab into bricks of at most 8 x 8 cells in its two long
+// directions.  One CTA takes one field of one brick: it stages the brick's
+// parent cells plus a 3-cell halo in shared memory and applies the 6-point
+// interpolant as three separable passes (x, then y, then z), each child at
+// -1/4 (nodes -3..2) or +1/4 (nodes -2..3) of its parent cell.
 struct ProlongArgs {
   const DevPatch* patches;
   const int* patch_ids;   // children (one level)
   const DevLevel* plev;   // parent level: slot = its current ring slot
 };
 
-__device__ __forceinline__ void box_shell_ijk(long long id, int m0, int m1, int m2, int w, int& a,
-                                              int& b, int& c) {
-  // shell of width w of an m0 x m1 x m2 box: two z slabs, two y slabs, two x slabs
-  const long long zs = (long long)w * m1 * m0;
-  const int n2 = m2 - 2 * w, n1 = m1 - 2 * w;
-  const long long ys = (long long)w * m0 * n2;
-  if (id < 2 * zs) {
-    int side = id >= zs;
-    long long r = id - side * zs;
-    a = (int)(r % m0);
-    r /= m0;
-    b = (int)(r % m1);
-    c = (int)(r / m1) + (side ? m2 - w : 0);
-    return;
-  }
-  id -= 2 * zs;
-  if (id < 2 * ys) {
-    int side = id >= ys;
-    long long r = id - side * ys;
-    a = (int)(r % m0);
-    r /= m0;
-    b = (int)(r % w) + (side ? m1 - w : 0);
-    c = (int)(r / w) + w;
-    return;
-  }
-  id -= 2 * ys;
-  const long long xs = (long long)w * n1 * n2;
-  int side = id >= xs;
-  long long r = id - side * xs;
-  a = (int)(r % w) + (side ? m0 - w : 0);
-  r /= w;
-  b = (int)(r % n1) + w;
-  c = (int)(r / n1) + w;
-}
+constexpr int PB = 8;          // brick edge along a slab's long directions
+constexpr int PB_THREADS = 256;
+constexpr int PB_S = 14 * 14 * 8;   // staged parent cells: (8+6) x (8+6) x (2+6)
+constexpr int PB_X1 = 16 * 14 * 8;  // after the x pass, largest orientation
+constexpr int PB_X2 = 16 * 16 * 8;  // after the y pass
 
-__global__ void __launch_bounds__(128) prolong_space_kernel(ProlongArgs A, long long max_work) {
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= max_work) return;
-  const DevPatch* C = A.patches + A.patch_ids[blockIdx.y];
-  // parent cells whose children touch the ghost shell: the box
-  // [off-2, off+n/2+1] minus its interior [off, off+n/2-1] (a shell of width 2)
-  const int m0 = C->n[0] / 2 + 4, m1 = C->n[1] / 2 + 4, m2 = C->n[2] / 2 + 4;
-  const long long ncl = (long long)m0 * m1 * m2 - (long long)(m0 - 4) * (m1 - 4) * (m2 - 4);
-  const int f = (int)(tid % NF);
-  const long long cl = tid / NF;
-  if (cl >= ncl) return;
-  int a, b, c;
-  box_shell_ijk(cl, m0, m1, m2, 2, a, b, c);
-  const DevPatch* P = A.patches + C->parent;
-  const int slot = A.plev->ring;
-  const double* __restrict__ up = P->buf[slot] + (long long)f * P->fstride;
-  // parent array index of the cell and of its 7^3 neighbourhood origin
-  const int pi = C->off[0] - 2 + a + GH, pj = C->off[1] - 2 + b + GH, pk = C->off[2] - 2 + c + GH;
-  const long long q0 = (pi - 3) + (long long)(pj - 3) * P->px + (long long)(pk - 3) * P->plane;
-  // weights over offsets -3..3 for the even (-1/4) and odd (+1/4) child
-  double we[7], wo[7];
-#pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    we[t] = c_wm[t];
-    wo[t + 1] = c_wp[t];
-  }
-  we[6] = 0.0;
-  wo[0] = 0.0;
-  // Only parent cells off-4 .. off+n/2+3 (parent active cells, by the nesting
-  // margin) are read: the children that are kept need no others, and cells
-  // outside that range (possibly never written) would turn a zero weight into
-  // NaN.  Valid stencil offsets t along each axis: [t_lo, t_hi].
-  const int xlo = max(0, 1 - a), xhi = min(6, C->n[0] / 2 + 8 - a);
-  const int ylo = max(0, 1 - b), yhi = min(6, C->n[1] / 2 + 8 - b);
-  const int zlo = max(0, 1 - c), zhi = min(6, C->n[2] / 2 + 8 - c);
-  double acc[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};  // [z][y][x] parity
-#pragma unroll 1
-  for (int kz = zlo; kz <= zhi; ++kz) {
-    double vy[2][2] = {{0, 0}, {0, 0}};
-#pragma unroll
-    for (int jy = 0; jy < 7; ++jy) {
-      if (jy < ylo || jy > yhi) continue;
-      const double* row = up + q0 + (long long)kz * P->plane + (long long)jy * P->px;
-      double xe = 0.0, xo = 0.0;
-#pragma unroll
-      for (int ix = 0; ix < 7; ++ix) {
-        const double v = (ix >= xlo && ix <= xhi) ? __ldg(row + ix) : 0.0;
-        xe += we[ix] * v;
-        xo += wo[ix] * v;
-      }
-      vy[0][0] += we[jy] * xe;
-      vy[0][1] += we[jy] * xo;
-      vy[1][0] += wo[jy] * xe;
-      vy[1][1] += wo[jy] * xo;
+__host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// bricks of one slab: s = 0,1 z slabs, 2,3 y slabs, 4,5 x slabs
+__host__ __device__ inline void slab_bricks(int s, int m0, int m1, int m2, int nb[3]) {
+  const int ax = 2 - s / 2;  // thin axis: z, y, x
+  const int len[3] = {m0, m1, m2};
+  for (int d = 0; d < 3; ++d) {
+    int l = len[d];
+    if (d == ax) {
+      nb[d] = 1;
+      continue;
     }
-#pragma unroll
-    for (int y = 0; y < 2; ++y)
-#pragma unroll
-      for (int x = 0; x < 2; ++x) {
-        acc[0][y][x] += we[kz] * vy[y][x];
-        acc[1][y][x] += wo[kz] * vy[y][x];
-      }
+    // z slabs cover everything in x and y; y slabs the middle (2 .. m-3) in
+    // z; x slabs the middle in y and z
+    if (d > ax) l -= 4;
+    nb[d] = cdiv(l, PB);
   }
-  // child indices of the even child along each axis
-  const int c0 = 2 * (a - 2), c1 = 2 * (b - 2), c2 = 2 * (c - 2);
-  double* __restrict__ g = C->gsh[slot] + (long long)f * C->fstride;
-#pragma unroll
-  for (int z = 0; z < 2; ++z)
-#pragma unroll
-    for (int y = 0; y < 2; ++y)
-#pragma unroll
-      for (int x = 0; x < 2; ++x) {
-        const int i = c0 + x, j = c1 + y, k = c2 + z;
-        if (i < -GH || j < -GH || k < -GH || i >= C->n[0] + GH || j >= C->n[1] + GH || k >= C->n[2] + GH)
-          continue;
-        const bool active = i >= 0 && j >= 0 && k >= 0 && i < C->n[0] && j < C->n[1] && k < C->n[2];
-        if (active) continue;
-        g[(i + GH) + (long long)(j + GH) * C->px + (long long)(k + GH) * C->plane] = acc[z][y][x];
-      }
 }
 
-// Mixed precision: the same interpolant in FP32 on differences against the
-// parent cell's value, from the parent's hi/lo split, added to that value in
-// FP64 (the weights sum to one along every axis, so subtracting the reference
-// changes nothing but the rounding).
-__global__ void __launch_bounds__(128) prolong_space_mixed_kernel(ProlongArgs A, long long max_work) {
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= max_work) return;
-  const DevPatch* C = A.patches + A.patch_ids[blockIdx.y];
-  const int m0 = C->n[0] / 2 + 4, m1 = C->n[1] / 2 + 4, m2 = C->n[2] / 2 + 4;
-  const long long ncl = (long long)m0 * m1 * m2 - (long long)(m0 - 4) * (m1 - 4) * (m2 - 4);
-  const int f = (int)(tid % NF);
-  const long long cl = tid / NF;
-  if (cl >= ncl) return;
-  int a, b, c;
-  box_shell_ijk(cl, m0, m1, m2, 2, a, b, c);
+__host__ __device__ inline int slab_count(int s, int m0, int m1, int m2) {
+  int nb[3];
+  slab_bricks(s, m0, m1, m2, nb);
+  return nb[0] * nb[1] * nb[2];
+}
+
+int prolong_bricks(int n0, int n1, int n2) {
+  const int m0 = n0 / 2 + 4, m1 = n1 / 2 + 4, m2 = n2 / 2 + 4;
+  int tot = 0;
+  for (int s = 0; s < 6; ++s) tot += slab_count(s, m0, m1, m2);
+  return tot;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A) {
+  typedef typename std::conditional<MIXED, float, double>::type T;
+  __shared__ T S[PB_S];
+  __shared__ T X1[PB_X1];
+  __shared__ T X2[PB_X2];
+  const DevPatch* C = A.patches + A.patch_ids[blockIdx.z];
+  const int f = blockIdx.y;
+  const int m[3] = {C->n[0] / 2 + 4, C->n[1] / 2 + 4, C->n[2] / 2 + 4};
+  // which slab and which brick of it
+  int b = blockIdx.x, s = 0;
+  for (; s < 6; ++s) {
+    const int c = slab_count(s, m[0], m[1], m[2]);
+    if (b < c) break;
+    b -= c;
+  }
+  if (s == 6) return;
+  int nb[3];
+  slab_bricks(s, m[0], m[1], m[2], nb);
+  const int ax = 2 - s / 2;
+  const int bi[3] = {b % nb[0], (b / nb[0]) % nb[1], b / (nb[0] * nb[1])};
+  int lo[3], B[3];
+  for (int d = 0; d < 3; ++d) {
+    if (d == ax) {
+      lo[d] = (s & 1) ? m[d] - 2 : 0;
+      B[d] = 2;
+      continue;
+    }
+    const int base = d > ax ? 2 : 0;  // slab range along d starts here
+    const int len = d > ax ? m[d] - 4 : m[d];
+    lo[d] = base + bi[d] * PB;
+    B[d] = min(PB, base + len - lo[d]);
+  }
+  const int Sx = B[0] + 6, Sy = B[1] + 6, Sz = B[2] + 6;
+  const int Cx = 2 * B[0], Cy = 2 * B[1], Cz = 2 * B[2];
   const DevPatch* P = A.patches + C->parent;
   const int slot = A.plev->ring;
   const long long fo = (long long)f * P->fstride;
-  const float2* __restrict__ hp = P->hl[slot] + fo;
-  const int pi = C->off[0] - 2 + a + GH, pj = C->off[1] - 2 + b + GH, pk = C->off[2] - 2 + c + GH;
-  // reference: the parent cell itself when it is readable, else the nearest
-  // readable cell along each axis
-  const int xlo = max(0, 1 - a), xhi = min(6, C->n[0] / 2 + 8 - a);
-  const int ylo = max(0, 1 - b), yhi = min(6, C->n[1] / 2 + 8 - b);
-  const int zlo = max(0, 1 - c), zhi = min(6, C->n[2] / 2 + 8 - c);
-  const int ri = pi - 3 + min(max(3, xlo), xhi), rj = pj - 3 + min(max(3, ylo), yhi),
-            rk = pk - 3 + min(max(3, zlo), zhi);
-  const long long qr = ri + (long long)rj * P->px + (long long)rk * P->plane;
-  const float2 ref = hp[qr];
-  const float h0 = ref.x, l0 = ref.y;
-  const double u0 = P->buf[slot][fo + qr];
-  const long long q0 = (pi - 3) + (long long)(pj - 3) * P->px + (long long)(pk - 3) * P->plane;
-  float we[7], wo[7];
-#pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    we[t] = (float)c_wm[t];
-    wo[t + 1] = (float)c_wp[t];
+  // parent array index of shell cell a along d: off[d] - 2 + a + GH
+  auto pq = [&](int a, int bb, int c) {
+    return (long long)(C->off[0] - 2 + a + GH) + (long long)(C->off[1] - 2 + bb + GH) * P->px +
+           (long long)(C->off[2] - 2 + c + GH) * P->plane;
+  };
+  // Only parent cells -2 .. m+1 (parent active cells off-4 .. off+n/2+3, by
+  // the nesting margin) are read: the children that are kept need no others,
+  // and cells outside that range (possibly never written) would turn a zero
+  // weight into NaN.  They are staged as 0.
+  float h0 = 0.0f, l0 = 0.0f;
+  double u0 = 0.0;
+  if (MIXED) {
+    // reference: the brick's first parent cell; the weights sum to one along
+    // every axis, so interpolating differences from it and adding it back in
+    // FP64 changes only the rounding
+    const long long qr = pq(lo[0], lo[1], lo[2]);
+    const float2 r = P->hl[slot][fo + qr];
+    h0 = r.x;
+    l0 = r.y;
+    u0 = P->buf[slot][fo + qr];
   }
-  we[6] = 0.0f;
-  wo[0] = 0.0f;
-  float acc[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
-#pragma unroll 1
-  for (int kz = zlo; kz <= zhi; ++kz) {
-    float vy[2][2] = {{0, 0}, {0, 0}};
-#pragma unroll
-    for (int jy = 0; jy < 7; ++jy) {
-      if (jy < ylo || jy > yhi) continue;
-      const long long row = q0 + (long long)kz * P->plane + (long long)jy * P->px;
-      float xe = 0.0f, xo = 0.0f;
-#pragma unroll
-      for (int ix = 0; ix < 7; ++ix) {
-        float v = 0.0f;
-        if (ix >= xlo && ix <= xhi) {
-          const float2 w = __ldg(hp + row + ix);
-          v = (w.x - h0) + (w.y - l0);
-        }
-        xe += we[ix] * v;
-        xo += wo[ix] * v;
+  for (int e = threadIdx.x; e < Sx * Sy * Sz; e += PB_THREADS) {
+    const int x = e % Sx, y = (e / Sx) % Sy, z = e / (Sx * Sy);
+    const int a = lo[0] - 3 + x, bb = lo[1] - 3 + y, c = lo[2] - 3 + z;
+    T v = T(0);
+    if (a >= -2 && a <= m[0] + 1 && bb >= -2 && bb <= m[1] + 1 && c >= -2 && c <= m[2] + 1) {
+      const long long q = fo + pq(a, bb, c);
+      if (MIXED) {
+        const float2 w = __ldg(P->hl[slot] + q);
+        v = (T)((w.x - h0) + (w.y - l0));
+      } else {
+        v = (T)__ldg(P->buf[slot] + q);
       }
-      vy[0][0] += we[jy] * xe;
-      vy[0][1] += we[jy] * xo;
-      vy[1][0] += wo[jy] * xe;
-      vy[1][1] += wo[jy] * xo;
     }
-#pragma unroll
-    for (int y = 0; y < 2; ++y)
-#pragma unroll
-      for (int x = 0; x < 2; ++x) {
-        acc[0][y][x] += we[kz] * vy[y][x];
-        acc[1][y][x] += wo[kz] * vy[y][x];
-      }
+    S[e] = v;
   }
-  const int c0 = 2 * (a - 2), c1 = 2 * (b - 2), c2 = 2 * (c - 2);
+  __syncthreads();
+  // x pass: X1[z][y][cx]
+  for (int e = threadIdx.x; e < Cx * Sy * Sz; e += PB_THREADS) {
+    const int cx = e % Cx, r = e / Cx;
+    const int p = cx >> 1, od = cx & 1;
+    const T* row = S + r * Sx + p + od;
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * row[t];
+    X1[e] = acc;
+  }
+  __syncthreads();
+  // y pass: X2[z][cy][cx]
+  for (int e = threadIdx.x; e < Cx * Cy * Sz; e += PB_THREADS) {
+    const int cx = e % Cx, cy = (e / Cx) % Cy, z = e / (Cx * Cy);
+    const int p = cy >> 1, od = cy & 1;
+    const T* col = X1 + (z * Sy + p + od) * Cx + cx;
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * col[t * Cx];
+    X2[e] = acc;
+  }
+  __syncthreads();
+  // z pass and store of the children in the ghost shell
   double* __restrict__ g = C->gsh[slot] + (long long)f * C->fstride;
+  for (int e = threadIdx.x; e < Cx * Cy * Cz; e += PB_THREADS) {
+    const int cx = e % Cx, cy = (e / Cx) % Cy, cz = e / (Cx * Cy);
+    const int i = 2 * lo[0] - 4 + cx, j = 2 * lo[1] - 4 + cy, k = 2 * lo[2] - 4 + cz;
+    if (i < -GH || j < -GH || k < -GH || i >= C->n[0] + GH || j >= C->n[1] + GH || k >= C->n[2] + GH) continue;
+    if (i >= 0 && j >= 0 && k >= 0 && i < C->n[0] && j < C->n[1] && k < C->n[2]) continue;
+    const int p = cz >> 1, od = cz & 1;
+    const T* col = X2 + ((p + od) * Cy + cy) * Cx + cx;
+    T acc = T(0);
 #pragma unroll
-  for (int z = 0; z < 2; ++z)
-#pragma unroll
-    for (int y = 0; y < 2; ++y)
-#pragma unroll
-      for (int x = 0; x < 2; ++x) {
-        const int i = c0 + x, j = c1 + y, k = c2 + z;
-        if (i < -GH || j < -GH || k < -GH || i >= C->n[0] + GH || j >= C->n[1] + GH || k >= C->n[2] + GH)
-          continue;
-        const bool active = i >= 0 && j >= 0 && k >= 0 && i < C->n[0] && j < C->n[1] && k < C->n[2];
-        if (active) continue;
-        g[(i + GH) + (long long)(j + GH) * C->px + (long long)(k + GH) * C->plane] = u0 + (double)acc[z][y][x];
-      }
+    for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * col[t * Cx * Cy];
+    g[(i + GH) + (long long)(j + GH) * C->px + (long long)(k + GH) * C->plane] =
+        MIXED ? u0 + (double)acc : (double)acc;
+  }
 }
 
 // Ghosts of the child's target buffer = time combination of the cached
@@ -378,6 +334,40 @@ __global__ void __launch_bounds__(128) restrict_kernel(FillArgs A) {
                        (long long)(2 * K - 1 + GH) * C->plane;
   const long long qp = (I + C->off[0] + GH) + (long long)(J + C->off[1] + GH) * P->px +
                        (long long)(K + C->off[2] + GH) * P->plane;
+  if (A.mixed) {
+    // mixed precision: the interpolant in FP32 on the child's hi/lo split,
+    // as differences from the fine cell (2I, 2J, 2K), added back to that
+    // cell's FP64 value (the weights sum to one along every axis)
+    const float2* __restrict__ hc = C->hl[A.lev->ring];
+    const long long qr = q0 + 1 + C->px + C->plane;
+    const float wf[4] = {-1.0f / 16, 9.0f / 16, 9.0f / 16, -1.0f / 16};
+    for (int f = 0; f < NF; ++f) {
+      const long long o = f * C->fstride;
+      const float2 r = hc[o + qr];
+      const float2* src = hc + o + q0;
+      float v = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float vy = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float2* row = src + (long long)c * C->plane + (long long)b * C->px;
+          float vx = 0.0f;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const float2 x = __ldg(row + a);
+            vx += wf[a] * ((x.x - r.x) + (x.y - r.y));
+          }
+          vy += wf[b] * vx;
+        }
+        v += wf[c] * vy;
+      }
+      const double res = uc[o + qr] + (double)v;
+      up[f * P->fstride + qp] = res;
+      split_to(res, P->hl[A.plev->ring], f * P->fstride + qp);
+    }
+    return;
+  }
   for (int f = 0; f < NF; ++f) {
     const double* src = uc + f * C->fstride + q0;
     double v = 0.0;
@@ -394,7 +384,6 @@ __global__ void __launch_bounds__(128) restrict_kernel(FillArgs A) {
       v += w[c] * vy;
     }
     up[f * P->fstride + qp] = v;
-    if (A.mixed) split_to(v, P->hl[A.plev->ring], f * P->fstride + qp);
   }
 }
 
@@ -484,18 +473,17 @@ void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cu
 }
 
 void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,
-                          long long max_clusters, int mixed, cudaStream_t st) {
-  if (nchildren == 0 || max_clusters == 0) return;
+                          long long max_bricks, int mixed, cudaStream_t st) {
+  if (nchildren == 0 || max_bricks == 0) return;
   ProlongArgs a;
   a.patches = patches;
   a.patch_ids = ids;
   a.plev = plev;
-  const long long work = max_clusters * NF;
-  dim3 grid((unsigned)((work + 127) / 128), nchildren);
+  dim3 grid((unsigned)max_bricks, NF, nchildren);
   if (mixed)
-    prolong_space_mixed_kernel<<<grid, 128, 0, st>>>(a, work);
+    prolong_brick_kernel<true><<<grid, PB_THREADS, 0, st>>>(a);
   else
-    prolong_space_kernel<<<grid, 128, 0, st>>>(a, work);
+    prolong_brick_kernel<false><<<grid, PB_THREADS, 0, st>>>(a);
 }
 
 void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st) {

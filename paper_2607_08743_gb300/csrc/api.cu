@@ -3,15 +3,19 @@
 // graph) and diagnostics.  Host code only issues launches; every step of the
 // path runs in the kernels of z4c_fp64.cu, z4c_mixed.cu, amr.cu and
 // diagnostics.cu.
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/sacrak.h"
 #include "sacrak_dev.cuh"
+#include "stage_tma.h"
 
 using namespace sacrak;
 
@@ -116,7 +120,7 @@ struct sacrak_grid {
   std::vector<std::vector<int>> lvl_ids;   // patch ids per level
   std::vector<int> lvl_id_off;             // offset of each level's ids in the device id array
   std::vector<size_t> lvl_tile_off, lvl_ntiles;
-  std::vector<long long> lvl_max_shell, lvl_max_restrict, lvl_max_clusters;
+  std::vector<long long> lvl_max_shell, lvl_max_restrict, lvl_max_clusters;  // clusters: prolongation bricks
   bool shells_dirty = true;
   bool split_dirty = true;  // mixed precision: hi/lo of the current levels stale
   DevPatch* d_patches;
@@ -136,6 +140,14 @@ struct sacrak_grid {
   size_t ev_used = 0;
   long long prof_zones = 0;
   std::vector<long long> lvl_zones;
+  // stage kernel per level: 0 the direct kernel, 1..TMA_NVARIANTS the TMA
+  // variant (id - 1); chosen by default, by sacrak_set_stage_kernel or by
+  // sacrak_autotune
+  std::vector<int> lvl_kernel;
+  // TMA descriptors per variant and patch (built on first use of a variant)
+  std::vector<std::array<CUtensorMap, 5>> maps[TMA_NVARIANTS];
+  int tma_blocks[TMA_NVARIANTS] = {};  // resident CTAs per SM, 0 = not set up
+  int nsm = 0;
 };
 
 namespace {
@@ -193,7 +205,84 @@ sacrak_status sync_and_check(sacrak_grid* g) {
   return SACRAK_OK;
 }
 
-void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones) {
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Can TMA variant v run the patches `pids` in one launch?  Every box must fit
+// in its patch array (32 x TY x TZ active cells at least) and the launch
+// arguments hold TMA_MAXP patches.
+bool tma_eligible(const sacrak_grid* g, int v, const std::vector<int>& pids) {
+  if (g->prm.precision != 1 || v < 0 || v >= TMA_NVARIANTS || pids.empty() || (int)pids.size() > TMA_MAXP)
+    return false;
+  int ty, tz;
+  tma_variant_shape(v, &ty, &tz);
+  for (int pid : pids) {
+    const DevPatch& P = g->hp[pid];
+    if (P.n[0] < 32 || P.n[1] < ty || P.n[2] < tz) return false;
+  }
+  return true;
+}
+
+// tensor maps of variant v for every patch: the five split buffers viewed as
+// 3D arrays of floats [NF*NZ][NY][2*NX] (row pitch px pairs), box
+// 76 x (TY+6) x (TZ+6) floats
+sacrak_status ensure_maps(sacrak_grid* g, int v) {
+  if (!g->maps[v].empty() && g->tma_blocks[v] > 0) return SACRAK_OK;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return fail(g, SACRAK_ECUDA, "cuTensorMapEncodeTiled is not available");
+  int ty, tz;
+  tma_variant_shape(v, &ty, &tz);
+  std::vector<std::array<CUtensorMap, 5>> maps(g->npatches);
+  for (int p = 0; p < g->npatches; ++p) {
+    const DevPatch& P = g->hp[p];
+    float2* bufs[5] = {P.hl[0], P.hl[1], P.hl[2], P.sa, P.sb};
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * P.NX, (cuuint64_t)P.NY, (cuuint64_t)NF * P.NZ};
+    const cuuint64_t strides[2] = {(cuuint64_t)P.px * 8, (cuuint64_t)P.plane * 8};
+    const cuuint32_t box[3] = {76, (cuuint32_t)(ty + 6), (cuuint32_t)(tz + 6)};
+    const cuuint32_t es[3] = {1, 1, 1};
+    for (int b = 0; b < 5; ++b) {
+      CUresult r = enc(&maps[p][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)bufs[b], dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(g, SACRAK_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+  }
+  const int nb = tma_setup_variant(v);
+  if (nb <= 0) {
+    cudaGetLastError();
+    return fail(g, SACRAK_ECUDA, "TMA stage kernel %d cannot be resident", v + 1);
+  }
+  if (g->nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g->nsm <= 0)
+      return fail(g, SACRAK_ECUDA, "cannot read the SM count");
+  }
+  g->maps[v] = std::move(maps);
+  g->tma_blocks[v] = nb;
+  return SACRAK_OK;
+}
+
+void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones, const std::vector<int>& pids,
+                  int kernel) {
   if (g->prof) {
     if (g->ev_used == g->ev.size()) {
       std::pair<cudaEvent_t, cudaEvent_t> p;
@@ -203,15 +292,57 @@ void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones) {
     }
     cudaEventRecord(g->ev[g->ev_used].first, g->stream);
   }
-  if (g->prm.precision == 1)
+  if (g->prm.precision == 1 && kernel > 0) {
+    const int v = kernel - 1;
+    int ty, tz;
+    tma_variant_shape(v, &ty, &tz);
+    TmaStageArgs t;
+    std::memset(&t, 0, sizeof t);
+    t.st = a;
+    t.np = (int)pids.size();
+    int acc = 0;
+    for (int i = 0; i < t.np; ++i) {
+      const DevPatch& P = g->hp[pids[i]];
+      t.pid[i] = pids[i];
+      t.tstart[i] = acc;
+      t.ntx[i] = (P.n[0] + 31) / 32;
+      t.nty[i] = (P.n[1] + ty - 1) / ty;
+      t.nz[i] = P.NZ;
+      acc += t.ntx[i] * t.nty[i] * ((P.n[2] + tz - 1) / tz);
+      for (int b = 0; b < 5; ++b) t.map[i][b] = g->maps[v][pids[i]][b];
+    }
+    t.tstart[t.np] = acc;
+    t.ntiles = acc;
+    const long long res = (long long)g->nsm * g->tma_blocks[v];
+    const int grid = (int)(acc < res ? acc : res);
+    if (grid > 0) launch_stage_tma(v, t, grid, g->stream);
+  } else if (g->prm.precision == 1) {
     launch_stage_mixed(a, g->stream);
-  else
+  } else {
     launch_stage_fp64(a, g->stream);
+  }
   if (g->prof) {
     cudaEventRecord(g->ev[g->ev_used].second, g->stream);
     g->ev_used++;
     g->prof_zones += zones;
   }
+}
+
+// select the stage kernel of a level (0 direct, 1.. TMA variant + 1)
+sacrak_status select_kernel(sacrak_grid* g, int l, int kernel) {
+  if (kernel > 0) {
+    if (!tma_eligible(g, kernel - 1, g->lvl_ids[l])) return fail(g, SACRAK_EINVAL, "kernel %d not usable on level %d", kernel, l);
+    sacrak_status st = ensure_maps(g, kernel - 1);
+    if (st != SACRAK_OK) return st;
+  }
+  if (g->lvl_kernel[l] != kernel && g->graph_exec) {  // the captured coarse step used the old kernel
+    cudaGraphExecDestroy(g->graph_exec);
+    cudaGraphDestroy(g->graph);
+    g->graph_exec = nullptr;
+    g->graph = nullptr;
+  }
+  g->lvl_kernel[l] = kernel;
+  return SACRAK_OK;
 }
 
 // Time weights of the parent's (oldest, middle, newest) levels for the ghost
@@ -322,7 +453,7 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
     a.dt = dt;
     a.prm = dev_params(g->prm);
     a.err = g->d_err;
-    launch_stage(g, a, g->lvl_zones[l]);
+    launch_stage(g, a, g->lvl_zones[l], g->lvl_ids[l], g->lvl_kernel[l]);
     if (l == 0 && g->prm.bc == 0) {
       GhostArgs ga;
       ga.patches = g->d_patches;
@@ -530,10 +661,9 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
       long long sh = (long long)P.NX * P.NY * P.NZ - (long long)P.n[0] * P.n[1] * P.n[2];
       if (sh > g->lvl_max_shell[l]) g->lvl_max_shell[l] = sh;
       g->lvl_zones[l] += (long long)P.n[0] * P.n[1] * P.n[2];
-      {
-        long long m0 = P.n[0] / 2 + 4, m1 = P.n[1] / 2 + 4, m2 = P.n[2] / 2 + 4;
-        long long cl = m0 * m1 * m2 - (m0 - 4) * (m1 - 4) * (m2 - 4);
-        if (cl > g->lvl_max_clusters[l]) g->lvl_max_clusters[l] = cl;
+      if (P.level > 0) {
+        const long long nb = prolong_bricks(P.n[0], P.n[1], P.n[2]);
+        if (nb > g->lvl_max_clusters[l]) g->lvl_max_clusters[l] = nb;
       }
       long long rs = (long long)(P.n[0] / 2) * (P.n[1] / 2) * (P.n[2] / 2);
       if (rs > g->lvl_max_restrict[l]) g->lvl_max_restrict[l] = rs;
@@ -555,6 +685,10 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
     if (cudaStreamSynchronize(s) != cudaSuccess) st = SACRAK_ECUDA;
   }
   if (st == SACRAK_OK) st = sacrak_set_initial_data(g, 0, 0, nullptr, nullptr, 0, 1, 0, 0, 0);
+  // default stage kernel: the TMA-staged 32 x 4 x 1 tiles where they fit
+  g->lvl_kernel.assign(nlevels, 0);
+  for (int l = 0; st == SACRAK_OK && l < nlevels; ++l)
+    if (tma_eligible(g, 0, g->lvl_ids[l])) st = select_kernel(g, l, 1);
   if (st != SACRAK_OK) {
     cudaGetLastError();
     delete g;
@@ -693,7 +827,7 @@ sacrak_status sacrak_rhs(sacrak_grid* g, int patch, double* dst) {
   a.dt = 0.0;
   a.prm = dev_params(g->prm);
   a.err = g->d_err;
-  launch_stage(g, a, (long long)P.n[0] * P.n[1] * P.n[2]);
+  launch_stage(g, a, (long long)P.n[0] * P.n[1] * P.n[2], std::vector<int>{patch}, g->lvl_kernel[l]);
   sacrak_status st = check_launch(g);
   if (st != SACRAK_OK) return st;
   st = copy_patch(g, patch, P.buf[B_S1], nullptr, dst, false);
@@ -802,6 +936,99 @@ sacrak_status sacrak_profile_read(sacrak_grid* g, double* ms, long long* launche
   *launches = (long long)g->ev_used;
   *zones = g->prof_zones;
   return SACRAK_OK;
+}
+
+sacrak_status sacrak_set_stage_kernel(sacrak_grid* g, int level, int kernel) {
+  if (!g) return SACRAK_EINVAL;
+  if (level < 0 || level >= g->nlevels || kernel < 0 || kernel > TMA_NVARIANTS ||
+      (kernel > 0 && !tma_eligible(g, kernel - 1, g->lvl_ids[level])))
+    return fail(g, SACRAK_EINVAL, "stage kernel %d not usable on level %d", kernel, level);
+  return select_kernel(g, level, kernel);
+}
+
+sacrak_status sacrak_get_stage_kernel(sacrak_grid* g, int level, int* kernel) {
+  if (!g) return SACRAK_EINVAL;
+  if (level < 0 || level >= g->nlevels || !kernel) return fail(g, SACRAK_EINVAL, "bad arguments");
+  *kernel = g->lvl_kernel[level];
+  return SACRAK_OK;
+}
+
+// Process-wide cache of autotuning results: the fastest stage kernel for a
+// level, keyed by device, precision and the level's patch shapes.
+static std::mutex g_tune_mu;
+static std::map<std::vector<int>, int> g_tune_cache;
+
+sacrak_status sacrak_autotune(sacrak_grid* g, int reps, int use_cache, double* us_out) {
+  if (!g) return SACRAK_EINVAL;
+  if (reps < 1 || reps > 1000) return fail(g, SACRAK_EINVAL, "reps must be 1..1000");
+  if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
+  cudaStreamCaptureStatus cs;
+  CK(cudaStreamIsCapturing(g->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(g, SACRAK_ESTATE, "autotuning needs a stream that is not capturing");
+  if (us_out)
+    for (int i = 0; i < g->nlevels * (1 + TMA_NVARIANTS); ++i) us_out[i] = -1.0;
+  refresh_all_shells(g);  // the split of the current levels must be valid
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  sacrak_status st = SACRAK_OK;
+  for (int l = 0; l < g->nlevels && st == SACRAK_OK; ++l) {
+    std::vector<int> key = {dev, g->prm.precision};
+    for (int pid : g->lvl_ids[l]) key.insert(key.end(), g->hp[pid].n, g->hp[pid].n + 3);
+    if (use_cache) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        st = select_kernel(g, l, it->second);
+        continue;
+      }
+    }
+    // time stage 1 of the level with every usable kernel: it reads the
+    // current time level and writes only the RK accumulator and the first
+    // stage buffer, so repeating it leaves the state as it was
+    StageArgs a;
+    a.tiles = g->d_tiles + g->lvl_tile_off[l];
+    a.ntiles = (int)g->lvl_ntiles[l];
+    a.patches = g->d_patches;
+    a.lev = g->d_levels + l;
+    a.stage = 1;
+    a.dt = level_dt(g, l);
+    a.prm = dev_params(g->prm);
+    a.err = g->d_err;
+    int best = g->lvl_kernel[l];
+    float best_ms = 0.0f;
+    const int nk = g->prm.precision == 1 ? 1 + TMA_NVARIANTS : 1;
+    for (int k = 0; k < nk && st == SACRAK_OK; ++k) {
+      if (k > 0 && !tma_eligible(g, k - 1, g->lvl_ids[l])) continue;
+      if (k > 0 && (st = ensure_maps(g, k - 1)) != SACRAK_OK) break;
+      const bool prof = g->prof;
+      g->prof = false;
+      launch_stage(g, a, 0, g->lvl_ids[l], k);  // warm-up
+      cudaEventRecord(e0, g->stream);
+      for (int r = 0; r < reps; ++r) launch_stage(g, a, 0, g->lvl_ids[l], k);
+      cudaEventRecord(e1, g->stream);
+      g->prof = prof;
+      if ((st = check_launch(g)) != SACRAK_OK) break;
+      if ((st = sync_and_check(g)) != SACRAK_OK) break;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (us_out) us_out[l * (1 + TMA_NVARIANTS) + k] = 1e3 * ms;
+      if (k == 0 || ms < best_ms) {
+        best = k;
+        best_ms = ms;
+      }
+    }
+    if (st != SACRAK_OK) break;
+    st = select_kernel(g, l, best);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 sacrak_status sacrak_level_time(sacrak_grid* g, int level, double* t) {

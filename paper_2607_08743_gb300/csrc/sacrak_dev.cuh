@@ -276,8 +276,10 @@ void launch_sommerfeld(const GhostArgs& a, int npatches, long long max_shell, cu
 void launch_constraints(const ConsArgs& a, int ntiles, double* out5, cudaStream_t st);
 void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cudaStream_t st);
 void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st);
+// bricks of the spatial prolongation of one child patch (n active cells)
+int prolong_bricks(int n0, int n1, int n2);
 void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,
-                          long long max_clusters, int mixed, cudaStream_t st);
+                          long long max_bricks, int mixed, cudaStream_t st);
 void launch_sommerfeld_mixed(const GhostArgs& a, int npatches, long long max_shell, cudaStream_t st);
 void launch_split(const DevPatch* patches, const DevLevel* levels, int patch, long long tot,
                   cudaStream_t st);

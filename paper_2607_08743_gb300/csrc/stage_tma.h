@@ -1,0 +1,36 @@
+// Launch interface of the TMA-staged mixed-precision stage kernels
+// (z4c_mixed_tma.cu).  Host code builds one CUtensorMap per patch and split
+// buffer (hl[0..2], sa, sb) for the tile shape of the chosen variant and
+// passes them by value (__grid_constant__), so that the kernel can pick the
+// stage input from the ring slot it reads on the device.
+#pragma once
+#include <cuda.h>
+
+#include "sacrak_dev.cuh"
+
+namespace sacrak {
+
+constexpr int TMA_MAXP = 8;       // patches of one level in one launch
+constexpr int TMA_NVARIANTS = 4;  // tile shapes 32x4x1, 32x2x2, 32x4x2, 32x8x1
+
+struct TmaStageArgs {
+  CUtensorMap map[TMA_MAXP][5];  // per patch slot: hl[0], hl[1], hl[2], sa, sb
+  StageArgs st;                  // tiles / ntiles of st are not used
+  int np;                        // patches in this launch
+  int ntiles;                    // tiles over all of them
+  int pid[TMA_MAXP];             // patch index of each slot
+  int tstart[TMA_MAXP + 1];      // first tile of each slot
+  int ntx[TMA_MAXP], nty[TMA_MAXP];  // tiles along x and y of each slot
+  int nz[TMA_MAXP];              // NZ (z extent incl. ghosts) of each slot
+};
+
+// tile shape (TY, TZ) of variant v; tiles are 32 x TY x TZ points
+void tma_variant_shape(int v, int* ty, int* tz);
+// bytes of one field box (38 x (TY+6) x (TZ+6) hi/lo pairs)
+int tma_box_bytes(int v);
+// opt the kernels of variant v in to their shared memory; returns the
+// resident CTAs per SM (0 on failure)
+int tma_setup_variant(int v);
+void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st);
+
+}  // namespace sacrak
