@@ -616,8 +616,11 @@ def stage_kernel_timing(g, steps):
     if g.params.precision == 0:
         name = "z4c_stage_fp64_kernel"
     else:
-        names = sorted({"z4c_stage_mixed_kernel" if k == 0 else "z4c_stage_tma_kernel (%s)" % sk.STAGE_KERNELS[k]
-                        for k in ids})
+        import paper_2607_08743_gb300 as sk
+        kn = {0: "z4c_stage_mixed_kernel"}
+        kn.update({k: "z4c_stage_tma_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (1, 2, 3, 4)})
+        kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6)})
+        names = sorted({kn[k] for k in ids})
         name = " + ".join(names)
     return {"name": name, "kernel_ids": ids,
             "ms": per, "launches": n, "share_of_step": None,

@@ -89,8 +89,10 @@ typedef struct {
  * copies (3 time levels, the RK accumulator, 2 stage buffers), 3 more on
  * levels > 0 (the parent's time levels prolonged onto the ghost shell), and
  * with params->precision == 1 five copies of FP32 hi/lo pairs (the split of
- * the 3 time levels, 2 stage states); plus tables and reduction scratch.  params may be
- * NULL (FP64).  Returns 0 for an invalid description. */
+ * the 3 time levels, 2 stage states) and 103 FP32 derivative planes over the
+ * 32 x 4 x 1 tiles of the level with the most tiles (stage kernel 7); plus
+ * tables and reduction scratch.  params may be NULL (FP64).  Returns 0 for
+ * an invalid description. */
 size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* patches,
                           const sacrak_params* params);
 
@@ -181,16 +183,23 @@ sacrak_status sacrak_constraints_noalloc(const double* dev_u, const int n[3], do
                                          double w_excise, void* cuda_stream, double out_l2[4]);
 
 /* Stage kernel of a level.  kernel 0: the direct kernel (every stencil value
- * read through the L1 cache); kernel 1..4 (mixed precision only): the
- * TMA-staged kernel with tiles of 32 x 4 x 1, 32 x 2 x 2, 32 x 4 x 2 and
- * 32 x 8 x 1 points, which copies each field's tile plus its 3-cell halo into
- * shared memory with tensor-memory-accelerator loads and walks all tiles of
- * the level in one persistent launch.  All kernels compute the same RHS up to
- * FP32 rounding order.  A TMA kernel needs at most 8 patches on the level and
- * at least 32 x TY x TZ active cells per patch, else SACRAK_EINVAL.  New grids
- * use kernel 1 where it fits and 0 elsewhere.  Changing the kernel of a level
- * drops the recorded CUDA graph of the coarse step (it is recorded again at
- * the next sacrak_level_step). */
+ * read through the L1 cache, second derivatives kept in full).  Mixed
+ * precision only: kernels 1..4, the TMA-staged kernel with tiles of
+ * 32 x 4 x 1, 32 x 2 x 2, 32 x 4 x 2 and 32 x 8 x 1 points, which copies each
+ * field's tile plus its 3-cell halo into shared memory with
+ * tensor-memory-accelerator loads and walks all tiles of the level in one
+ * persistent launch; kernels 5 and 6, the same arithmetic as 1..4 (hi/lo
+ * pairs in packed FP32x2 instructions, branch-free upwinding, second
+ * derivatives contracted as they are formed) reading through the L1 cache,
+ * 3 CTAs per SM; kernel 6 also prefetches the next field's stencil rows
+ * into L1 and the RK update's streaming reads into L2; kernel 7 splits the
+ * stage into two launches, the derivatives (five fields per thread) into FP32
+ * planes in the arena and then the algebra and RK4 update.  All kernels compute the same RHS up to FP32
+ * rounding order.  A TMA kernel needs at most 8 patches on the level and at
+ * least 32 x TY x TZ active cells per patch, else SACRAK_EINVAL.  New grids
+ * use kernel 6 in mixed precision and 0 in FP64.  Changing the kernel of a
+ * level drops the recorded CUDA graph of the coarse step (it is recorded
+ * again at the next sacrak_level_step). */
 sacrak_status sacrak_set_stage_kernel(sacrak_grid* grid, int level, int kernel);
 sacrak_status sacrak_get_stage_kernel(sacrak_grid* grid, int level, int* kernel);
 
@@ -201,7 +210,7 @@ sacrak_status sacrak_get_stage_kernel(sacrak_grid* grid, int level, int* kernel)
  * the grid's stream), and selects the fastest.  Results are cached for the
  * process, keyed by device, precision and the level's patch shapes; with
  * use_cache != 0 a cached level is not timed again.  us_per_launch, if not
- * NULL, receives nlevels x 5 timings in microseconds (kernel 0..4 of each
+ * NULL, receives nlevels x 8 timings in microseconds (kernel 0..7 of each
  * level; -1 where not timed).  Synchronises the stream; must not be called
  * while the stream is being captured (SACRAK_ESTATE). */
 sacrak_status sacrak_autotune(sacrak_grid* grid, int reps, int use_cache, double* us_per_launch);

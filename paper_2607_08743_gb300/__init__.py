@@ -32,8 +32,11 @@ EXPORTS = [
     "sacrak_set_stage_kernel", "sacrak_get_stage_kernel", "sacrak_autotune",
 ]
 
-# stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles
-STAGE_KERNELS = {0: "direct", 1: "tma 32x4x1", 2: "tma 32x2x2", 3: "tma 32x4x2", 4: "tma 32x8x1"}
+# stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
+# 5..6 L1 path with packed pair arithmetic (without / with prefetching),
+# 7 split into a derivative and an algebra launch
+STAGE_KERNELS = {0: "direct", 1: "tma 32x4x1", 2: "tma 32x2x2", 3: "tma 32x4x2", 4: "tma 32x8x1",
+                 5: "l1 pairs", 6: "l1 pairs + prefetch", 7: "split deriv + algebra"}
 
 
 class SacrakError(RuntimeError):
@@ -279,7 +282,7 @@ class Grid:
         return ms.value, n.value, z.value
 
     def set_stage_kernel(self, level: int, kernel: int):
-        """Stage kernel of a level: 0 direct, 1..4 TMA-staged (see STAGE_KERNELS)."""
+        """Stage kernel of a level (see STAGE_KERNELS)."""
         self._check(lib().sacrak_set_stage_kernel(self._h, level, kernel), "set_stage_kernel")
 
     def stage_kernel(self, level: int) -> int:
@@ -289,7 +292,7 @@ class Grid:
 
     def autotune(self, reps: int = 3, use_cache: bool = True) -> np.ndarray:
         """Time every usable stage kernel on every level and keep the fastest;
-        returns the timings (nlevels x 5, microseconds per launch, -1 = not
+        returns the timings (nlevels x 8, microseconds per launch, -1 = not
         timed) and leaves the choice in place."""
         out = np.full((self.nlevels, len(STAGE_KERNELS)), -1.0)
         self._check(lib().sacrak_autotune(self._h, reps, int(use_cache),

@@ -215,58 +215,75 @@ __global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A
     l0 = r.y;
     u0 = P->buf[slot][fo + qr];
   }
-  for (int e = threadIdx.x; e < Sx * Sy * Sz; e += PB_THREADS) {
-    const int x = e % Sx, y = (e / Sx) % Sy, z = e / (Sx * Sy);
-    const int a = lo[0] - 3 + x, bb = lo[1] - 3 + y, c = lo[2] - 3 + z;
-    T v = T(0);
-    if (a >= -2 && a <= m[0] + 1 && bb >= -2 && bb <= m[1] + 1 && c >= -2 && c <= m[2] + 1) {
-      const long long q = fo + pq(a, bb, c);
-      if (MIXED) {
-        const float2 w = __ldg(P->hl[slot] + q);
-        v = (T)((w.x - h0) + (w.y - l0));
-      } else {
-        v = (T)__ldg(P->buf[slot] + q);
+  // threads as a 16 x 16 sheet (x, y); every pass loops over its third axis
+  // (every extent is at most 16)
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (tx < Sx && ty < Sy) {
+    const int a = lo[0] - 3 + tx, bb = lo[1] - 3 + ty;
+    const bool inxy = a >= -2 && a <= m[0] + 1 && bb >= -2 && bb <= m[1] + 1;
+    for (int z = 0; z < Sz; ++z) {
+      const int c = lo[2] - 3 + z;
+      T v = T(0);
+      if (inxy && c >= -2 && c <= m[2] + 1) {
+        const long long q = fo + pq(a, bb, c);
+        if (MIXED) {
+          const float2 w = __ldg(P->hl[slot] + q);
+          v = (T)((w.x - h0) + (w.y - l0));
+        } else {
+          v = (T)__ldg(P->buf[slot] + q);
+        }
       }
+      S[(z * Sy + ty) * Sx + tx] = v;
     }
-    S[e] = v;
   }
   __syncthreads();
   // x pass: X1[z][y][cx]
-  for (int e = threadIdx.x; e < Cx * Sy * Sz; e += PB_THREADS) {
-    const int cx = e % Cx, r = e / Cx;
-    const int p = cx >> 1, od = cx & 1;
-    const T* row = S + r * Sx + p + od;
-    T acc = T(0);
+  if (tx < Cx && ty < Sy) {
+    const int p = tx >> 1, od = tx & 1;
+    for (int z = 0; z < Sz; ++z) {
+      const T* row = S + (z * Sy + ty) * Sx + p + od;
+      T acc = T(0);
 #pragma unroll
-    for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * row[t];
-    X1[e] = acc;
+      for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * row[t];
+      X1[(z * Sy + ty) * Cx + tx] = acc;
+    }
   }
   __syncthreads();
   // y pass: X2[z][cy][cx]
-  for (int e = threadIdx.x; e < Cx * Cy * Sz; e += PB_THREADS) {
-    const int cx = e % Cx, cy = (e / Cx) % Cy, z = e / (Cx * Cy);
-    const int p = cy >> 1, od = cy & 1;
-    const T* col = X1 + (z * Sy + p + od) * Cx + cx;
-    T acc = T(0);
+  if (tx < Cx && ty < Cy) {
+    const int p = ty >> 1, od = ty & 1;
+    for (int z = 0; z < Sz; ++z) {
+      const T* col = X1 + (z * Sy + p + od) * Cx + tx;
+      T acc = T(0);
 #pragma unroll
-    for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * col[t * Cx];
-    X2[e] = acc;
+      for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * col[t * Cx];
+      X2[(z * Cy + ty) * Cx + tx] = acc;
+    }
   }
   __syncthreads();
-  // z pass and store of the children in the ghost shell
+  // z pass and store of the children in the ghost shell (mixed precision:
+  // stored as hi/lo pairs in the same 8-byte entries)
   double* __restrict__ g = C->gsh[slot] + (long long)f * C->fstride;
-  for (int e = threadIdx.x; e < Cx * Cy * Cz; e += PB_THREADS) {
-    const int cx = e % Cx, cy = (e / Cx) % Cy, cz = e / (Cx * Cy);
-    const int i = 2 * lo[0] - 4 + cx, j = 2 * lo[1] - 4 + cy, k = 2 * lo[2] - 4 + cz;
-    if (i < -GH || j < -GH || k < -GH || i >= C->n[0] + GH || j >= C->n[1] + GH || k >= C->n[2] + GH) continue;
-    if (i >= 0 && j >= 0 && k >= 0 && i < C->n[0] && j < C->n[1] && k < C->n[2]) continue;
-    const int p = cz >> 1, od = cz & 1;
-    const T* col = X2 + ((p + od) * Cy + cy) * Cx + cx;
-    T acc = T(0);
+  float2* __restrict__ g2 = reinterpret_cast<float2*>(g);
+  if (tx < Cx && ty < Cy) {
+    const int i = 2 * lo[0] - 4 + tx, j = 2 * lo[1] - 4 + ty;
+    if (i < -GH || j < -GH || i >= C->n[0] + GH || j >= C->n[1] + GH) return;
+    const bool actxy = i >= 0 && j >= 0 && i < C->n[0] && j < C->n[1];
+    for (int cz = 0; cz < Cz; ++cz) {
+      const int k = 2 * lo[2] - 4 + cz;
+      if (k < -GH || k >= C->n[2] + GH) continue;
+      if (actxy && k >= 0 && k < C->n[2]) continue;
+      const int p = cz >> 1, od = cz & 1;
+      const T* col = X2 + ((p + od) * Cy + ty) * Cx + tx;
+      T acc = T(0);
 #pragma unroll
-    for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * col[t * Cx * Cy];
-    g[(i + GH) + (long long)(j + GH) * C->px + (long long)(k + GH) * C->plane] =
-        MIXED ? u0 + (double)acc : (double)acc;
+      for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * col[t * Cx * Cy];
+      const long long o = (i + GH) + (long long)(j + GH) * C->px + (long long)(k + GH) * C->plane;
+      if (MIXED)
+        split_to(u0 + (double)acc, g2, o);
+      else
+        g[o] = (double)acc;
+    }
   }
 }
 
@@ -286,9 +303,12 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
   const double* __restrict__ g2 = C->gsh[pr];
   const int ring = A.lev->ring;
   const long long q = i + (long long)j * C->px + (long long)k * C->plane;
+  // this block's five fields (gridDim.z = 5 groups)
+  const int f0 = blockIdx.z * (NF / 5);
   if (!A.mixed) {
     double* __restrict__ dst = C->buf[fill_slot(A.mode, A.stage, ring)];
-    for (int f = 0; f < NF; ++f) {
+#pragma unroll
+    for (int f = f0; f < f0 + NF / 5; ++f) {
       const long long o = f * C->fstride + q;
       double v = w1 * g1[o] + w2 * g2[o];
       if (q3) v += w0 * g0[o];
@@ -296,18 +316,31 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
     }
     return;
   }
-  // mixed precision: stage 1 (and the fill of the current level) sets the
-  // FP64 ghost and its hi/lo split; later stages set lo_s = v - hi_n
+  // mixed precision: the cached slots hold hi/lo pairs.  Stage 1 (and the
+  // fill of the current level) sets the FP64 ghost and its split; later
+  // stages set lo_s = v - hi_n.  The time weights sum to one and are exact
+  // in FP32, so both are formed in FP32 on differences from a nearby hi.
   const bool later = (A.mode == 0 && A.stage > 1);
   float2* __restrict__ in = later ? mixed_in(C, A.stage, ring) : nullptr;
-  for (int f = 0; f < NF; ++f) {
+  const float2* __restrict__ h0 = reinterpret_cast<const float2*>(g0);
+  const float2* __restrict__ h1 = reinterpret_cast<const float2*>(g1);
+  const float2* __restrict__ h2 = reinterpret_cast<const float2*>(g2);
+  const float w0f = (float)w0, w1f = (float)w1, w2f = (float)w2;
+#pragma unroll
+  for (int f = f0; f < f0 + NF / 5; ++f) {
     const long long o = f * C->fstride + q;
-    double v = w1 * g1[o] + w2 * g2[o];
-    if (q3) v += w0 * g0[o];
+    const float2 a1 = h1[o], a2 = h2[o];
+    const float2 a0 = q3 ? h0[o] : make_float2(0.0f, 0.0f);
     if (later) {
       const float hi = C->hl[ring][o].x;
-      in[o] = make_float2(hi, __double2float_rn(v - (double)hi));
+      float lo = w1f * ((a1.x - hi) + a1.y) + w2f * ((a2.x - hi) + a2.y);
+      if (q3) lo += w0f * ((a0.x - hi) + a0.y);
+      in[o] = make_float2(hi, lo);
     } else {
+      const float r = a1.x;
+      float d = w1f * a1.y + w2f * ((a2.x - r) + a2.y);
+      if (q3) d += w0f * ((a0.x - r) + a0.y);
+      const double v = (double)r + (double)d;
       C->buf[ring][o] = v;
       split_to(v, C->hl[ring], o);
     }
@@ -467,7 +500,7 @@ void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cu
   switch (kind) {
     case 0: periodic_fill_kernel<<<grid, 128, 0, st>>>(a); break;
     case 1: frozen_fill_kernel<<<grid, 128, 0, st>>>(a); break;
-    case 2: ghost_time_fill_kernel<<<grid, 128, 0, st>>>(a); break;
+    case 2: ghost_time_fill_kernel<<<dim3(grid.x, grid.y, 5), 128, 0, st>>>(a); break;
     case 3: restrict_kernel<<<grid, 128, 0, st>>>(a); break;
   }
 }

@@ -28,7 +28,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
   // byte offsets inside the arena
-  size_t patches, levels, ids, tiles, err, results, scratch, states, total;
+  size_t patches, levels, ids, tiles, err, results, scratch, dslot, states, total;
   std::vector<size_t> patch_state;  // offset of each patch's first buffer
   std::vector<long long> fstride;
   std::vector<int> px;
@@ -87,6 +87,10 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed,
   L.scratch_doubles = maxtiles_level * 5 > maxpts / 256 + 1 ? maxtiles_level * 5 : maxpts / 256 + 1;
   L.scratch = off;
   off = align_up(off + L.scratch_doubles * sizeof(double), 256);
+  // mixed precision: FP32 derivative planes of the split stage kernel, for
+  // the level with the most tiles
+  L.dslot = off;
+  if (mixed) off = align_up(off + (size_t)split_slot_floats((long long)maxtiles_level) * sizeof(float), 256);
   L.states = off;
   L.patch_state.resize(npatches);
   L.fstride.resize(npatches);
@@ -130,6 +134,7 @@ struct sacrak_grid {
   unsigned* d_err;
   double* d_results;
   double* d_scratch;
+  float* d_dslot;  // mixed precision: derivative planes of the split stage kernel
   bool invalid = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -241,6 +246,17 @@ bool tma_eligible(const sacrak_grid* g, int v, const std::vector<int>& pids) {
   return true;
 }
 
+// kernel ids: 0 direct, 1..TMA_NVARIANTS TMA variant id-1, then the two
+// L1-path kernels with packed pair arithmetic (without and with prefetching)
+constexpr int K_LDG3 = TMA_NVARIANTS + 1, K_LDG4 = TMA_NVARIANTS + 2, K_SPLIT = TMA_NVARIANTS + 3,
+              K_COUNT = TMA_NVARIANTS + 4;
+
+bool kernel_eligible(const sacrak_grid* g, int k, const std::vector<int>& pids) {
+  if (k == 0) return true;
+  if (k >= 1 && k <= TMA_NVARIANTS) return tma_eligible(g, k - 1, pids);
+  return (k == K_LDG3 || k == K_LDG4 || k == K_SPLIT) && g->prm.precision == 1;
+}
+
 // tensor maps of variant v for every patch: the five split buffers viewed as
 // 3D arrays of floats [NF*NZ][NY][2*NX] (row pitch px pairs), box
 // 76 x (TY+6) x (TZ+6) floats
@@ -292,7 +308,7 @@ void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones, const std
     }
     cudaEventRecord(g->ev[g->ev_used].first, g->stream);
   }
-  if (g->prm.precision == 1 && kernel > 0) {
+  if (g->prm.precision == 1 && kernel >= 1 && kernel <= TMA_NVARIANTS) {
     const int v = kernel - 1;
     int ty, tz;
     tma_variant_shape(v, &ty, &tz);
@@ -316,6 +332,10 @@ void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones, const std
     const long long res = (long long)g->nsm * g->tma_blocks[v];
     const int grid = (int)(acc < res ? acc : res);
     if (grid > 0) launch_stage_tma(v, t, grid, g->stream);
+  } else if (g->prm.precision == 1 && (kernel == K_LDG3 || kernel == K_LDG4)) {
+    launch_stage_ldg(kernel == K_LDG4 ? 1 : 0, a, g->stream);
+  } else if (g->prm.precision == 1 && kernel == K_SPLIT) {
+    launch_stage_split(a, g->d_dslot, g->stream);
   } else if (g->prm.precision == 1) {
     launch_stage_mixed(a, g->stream);
   } else {
@@ -330,10 +350,20 @@ void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones, const std
 
 // select the stage kernel of a level (0 direct, 1.. TMA variant + 1)
 sacrak_status select_kernel(sacrak_grid* g, int l, int kernel) {
-  if (kernel > 0) {
-    if (!tma_eligible(g, kernel - 1, g->lvl_ids[l])) return fail(g, SACRAK_EINVAL, "kernel %d not usable on level %d", kernel, l);
+  if (!kernel_eligible(g, kernel, g->lvl_ids[l]))
+    return fail(g, SACRAK_EINVAL, "kernel %d not usable on level %d", kernel, l);
+  if (kernel >= 1 && kernel <= TMA_NVARIANTS) {
     sacrak_status st = ensure_maps(g, kernel - 1);
     if (st != SACRAK_OK) return st;
+  }
+  if (kernel == K_LDG3 || kernel == K_LDG4) {
+    static bool done[64][2] = {};  // shared-memory opt-in, once per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done[dev][kernel - K_LDG3]) {
+      if (!ldg_setup(kernel == K_LDG4 ? 1 : 0)) return fail(g, SACRAK_ECUDA, "stage kernel %d setup failed", kernel);
+      if (dev >= 0 && dev < 64) done[dev][kernel - K_LDG3] = true;
+    }
   }
   if (g->lvl_kernel[l] != kernel && g->graph_exec) {  // the captured coarse step used the old kernel
     cudaGraphExecDestroy(g->graph_exec);
@@ -640,6 +670,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   g->d_err = (unsigned*)(g->arena + L.err);
   g->d_results = (double*)(g->arena + L.results);
   g->d_scratch = (double*)(g->arena + L.scratch);
+  g->d_dslot = (float*)(g->arena + L.dslot);
   std::vector<int> ids;
   std::vector<Tile> tiles;
   g->lvl_id_off.resize(nlevels);
@@ -685,10 +716,11 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
     if (cudaStreamSynchronize(s) != cudaSuccess) st = SACRAK_ECUDA;
   }
   if (st == SACRAK_OK) st = sacrak_set_initial_data(g, 0, 0, nullptr, nullptr, 0, 1, 0, 0, 0);
-  // default stage kernel: the TMA-staged 32 x 4 x 1 tiles where they fit
+  // default stage kernel (mixed precision): the L1-path kernel with packed
+  // pair arithmetic and prefetching (the fastest on 64^3 and 96^3 patches)
   g->lvl_kernel.assign(nlevels, 0);
   for (int l = 0; st == SACRAK_OK && l < nlevels; ++l)
-    if (tma_eligible(g, 0, g->lvl_ids[l])) st = select_kernel(g, l, 1);
+    if (p.precision == 1) st = select_kernel(g, l, K_LDG4);
   if (st != SACRAK_OK) {
     cudaGetLastError();
     delete g;
@@ -940,8 +972,8 @@ sacrak_status sacrak_profile_read(sacrak_grid* g, double* ms, long long* launche
 
 sacrak_status sacrak_set_stage_kernel(sacrak_grid* g, int level, int kernel) {
   if (!g) return SACRAK_EINVAL;
-  if (level < 0 || level >= g->nlevels || kernel < 0 || kernel > TMA_NVARIANTS ||
-      (kernel > 0 && !tma_eligible(g, kernel - 1, g->lvl_ids[level])))
+  if (level < 0 || level >= g->nlevels || kernel < 0 || kernel >= K_COUNT ||
+      !kernel_eligible(g, kernel, g->lvl_ids[level]))
     return fail(g, SACRAK_EINVAL, "stage kernel %d not usable on level %d", kernel, level);
   return select_kernel(g, level, kernel);
 }
@@ -966,7 +998,7 @@ sacrak_status sacrak_autotune(sacrak_grid* g, int reps, int use_cache, double* u
   CK(cudaStreamIsCapturing(g->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return fail(g, SACRAK_ESTATE, "autotuning needs a stream that is not capturing");
   if (us_out)
-    for (int i = 0; i < g->nlevels * (1 + TMA_NVARIANTS); ++i) us_out[i] = -1.0;
+    for (int i = 0; i < g->nlevels * K_COUNT; ++i) us_out[i] = -1.0;
   refresh_all_shells(g);  // the split of the current levels must be valid
   int dev = 0;
   CK(cudaGetDevice(&dev));
@@ -999,10 +1031,11 @@ sacrak_status sacrak_autotune(sacrak_grid* g, int reps, int use_cache, double* u
     a.err = g->d_err;
     int best = g->lvl_kernel[l];
     float best_ms = 0.0f;
-    const int nk = g->prm.precision == 1 ? 1 + TMA_NVARIANTS : 1;
+    const int nk = g->prm.precision == 1 ? K_COUNT : 1;
+    const int keep = g->lvl_kernel[l];
     for (int k = 0; k < nk && st == SACRAK_OK; ++k) {
-      if (k > 0 && !tma_eligible(g, k - 1, g->lvl_ids[l])) continue;
-      if (k > 0 && (st = ensure_maps(g, k - 1)) != SACRAK_OK) break;
+      if (!kernel_eligible(g, k, g->lvl_ids[l])) continue;
+      if ((st = select_kernel(g, l, k)) != SACRAK_OK) break;  // one-time set-up of kernel k
       const bool prof = g->prof;
       g->prof = false;
       launch_stage(g, a, 0, g->lvl_ids[l], k);  // warm-up
@@ -1015,13 +1048,16 @@ sacrak_status sacrak_autotune(sacrak_grid* g, int reps, int use_cache, double* u
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= reps;
-      if (us_out) us_out[l * (1 + TMA_NVARIANTS) + k] = 1e3 * ms;
+      if (us_out) us_out[l * K_COUNT + k] = 1e3 * ms;
       if (k == 0 || ms < best_ms) {
         best = k;
         best_ms = ms;
       }
     }
-    if (st != SACRAK_OK) break;
+    if (st != SACRAK_OK) {
+      select_kernel(g, l, keep);
+      break;
+    }
     st = select_kernel(g, l, best);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;

@@ -39,7 +39,8 @@ struct DevPatch {
   double origin[3];
   double* buf[NBUF];
   // levels > 0: the parent's time level in each ring slot, prolonged in space
-  // onto this patch (full patch layout; only the ghost shell is written)
+  // onto this patch (full patch layout; only the ghost shell is written; in
+  // mixed precision each 8-byte entry holds the hi/lo float2 split instead)
   double* gsh[3];
   // mixed precision only (null otherwise): each time level split into FP32
   // hi + lo, interleaved (hl, same ring slots as buf), and the stage states

@@ -33,4 +33,18 @@ int tma_box_bytes(int v);
 int tma_setup_variant(int v);
 void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st);
 
+// The same arithmetic reading every stencil value through the L1 cache, over
+// the 32 x 4 x 1 tile list of StageArgs, 3 CTAs per SM; with prefetch != 0
+// the next field's stencil rows are prefetched into L1 and the epilogue's
+// streaming reads into L2.  ldg_setup opts the kernels in to their shared
+// memory (false on failure).
+int ldg_setup(int prefetch);
+void launch_stage_ldg(int prefetch, const StageArgs& a, cudaStream_t st);
+
+// The stage split in two launches: derivatives of five fields per thread into
+// FP32 slot planes in global memory (dslot, split_slot_floats(ntiles) floats
+// for a launch over ntiles tiles), then the algebra and the RK4 update.
+long long split_slot_floats(long long ntiles);
+void launch_stage_split(const StageArgs& a, float* dslot, cudaStream_t st);
+
 }  // namespace sacrak

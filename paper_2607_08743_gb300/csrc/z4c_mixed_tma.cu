@@ -125,6 +125,29 @@ enum {
   S_AK = 72,    // advection + dissipation of field f
   NSLOT = 97
 };
+// The split kernels (derivatives to global memory, then the algebra) keep
+// the three contributions d_j d_i beta^i of the three beta fields apart
+// (they are formed by different threads): S_DVB + 3 i + j, then S_AK.
+enum { S_AK_SPLIT = 78, NSLOT_SPLIT = 103 };
+
+// slot storage: one column per thread in shared memory, or one plane per
+// slot in global memory (point index p of n points)
+template <int NT>
+struct SmemSlots {
+  float* sd;
+  int t;
+  __device__ __forceinline__ float& operator()(int k) const { return sd[k * NT + t]; }
+};
+struct GlobalSlots {
+  float* d;
+  long long n, p;
+  __device__ __forceinline__ float& operator()(int k) const { return d[k * n + p]; }
+};
+struct GlobalSlotsIn {
+  const float* __restrict__ d;
+  long long n, p;
+  __device__ __forceinline__ float operator()(int k) const { return __ldg(d + k * n + p); }
+};
 
 // what phase 1 forms for each field
 struct FieldPlan {
@@ -180,26 +203,40 @@ __device__ __forceinline__ TileLoc locate(const TmaStageArgs& A, int tile) {
 
 // ------------------------------------------------------------------ phase 1
 
-// One field: its box is in shared memory (T, pairs), c is this thread's point
-// in the box.  Forms the plan's derivatives into the slots, the advection +
-// dissipation sum into S_AK + F, and returns the centre value.
-template <int TY, int TZ, int F>
-__device__ __forceinline__ float field_pass(const float2* __restrict__ T, int c, float* __restrict__ sd,
-                                            int t, const float wko[3], const float wup[3], float c1,
-                                            float c2, float c11, const float gtu[6]) {
-  using C = Cfg<TY, TZ>;
-  constexpr FieldPlan P = plan(F);
-  constexpr int NT = C::NT;
-  constexpr int OFF[3] = {1, C::SY, C::SZ};
-#define SD(k) sd[(k) * NT + t]
-  const float2 c0 = T[c];
+// Where a stencil value comes from: the staged box in shared memory (offsets
+// are compile-time constants) or the stage state in global memory through
+// the L1 cache.
+template <int SY, int SZ>
+struct SmemAcc {
+  const float2* __restrict__ T;
+  int c;  // this thread's point in the box
+  __device__ __forceinline__ float2 operator()(int dx, int dy, int dz) const {
+    return T[c + dx + dy * SY + dz * SZ];
+  }
+};
+struct GlobalAcc {
+  const float2* __restrict__ F;  // the field at this thread's point
+  long long sy, sz;
+  __device__ __forceinline__ float2 operator()(int dx, int dy, int dz) const {
+    return __ldg(F + dx + dy * sy + dz * sz);
+  }
+};
+
+// One field, values from `at`: forms the plan's derivatives into the slots
+// (NT columns), the advection + dissipation sum into S_AK + F, and returns
+// the centre value.
+template <bool SPLIT, class Acc, class Slots>
+__device__ __forceinline__ float field_pass_p(const Acc& at, const FieldPlan P, const int F, const Slots& SD,
+                                              const float wko[3], const float wup[3], float c1, float c2,
+                                              float c11, const float gtu[6]) {
+#define AT(d, k) at((d) == 0 ? (k) : 0, (d) == 1 ? (k) : 0, (d) == 2 ? (k) : 0)
+  const float2 c0 = at(0, 0, 0);
   float2 acc = make_float2(0.0f, 0.0f);
   float dd[6];  // second derivatives, symmetric index
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const int o = OFF[d];
-    const float2 m3 = T[c - 3 * o], m2 = T[c - 2 * o], m1 = T[c - o];
-    const float2 p1 = T[c + o], p2 = T[c + 2 * o], p3 = T[c + 3 * o];
+    const float2 m3 = AT(d, -3), m2 = AT(d, -2), m1 = AT(d, -1);
+    const float2 p1 = AT(d, 1), p2 = AT(d, 2), p3 = AT(d, 3);
     // centre-referenced sums (symmetric stencils) ...
     const float2 a = add2(sub2(m3, c0), sub2(p3, c0));
     const float2 b = add2(sub2(m2, c0), sub2(p2, c0));
@@ -218,13 +255,17 @@ __device__ __forceinline__ float field_pass(const float2* __restrict__ T, int c,
     constexpr int PA[3] = {0, 0, 1}, PB[3] = {1, 2, 2}, PS[3] = {1, 2, 4};
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      const int oa = OFF[PA[m]], ob = OFF[PB[m]];
+      const int A = PA[m], B = PB[m];
       float2 inner[4];
       constexpr int KA[4] = {1, -1, 2, -2};
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int q = c + KA[u] * oa;
-        inner[u] = fma2s(sub2(T[q + ob], T[q - ob]), 8.0f, sub2(T[q - 2 * ob], T[q + 2 * ob]));
+        const int ka = KA[u];
+        auto pt = [&](int kb) {
+          return at((A == 0 ? ka : 0) + (B == 0 ? kb : 0), (A == 1 ? ka : 0) + (B == 1 ? kb : 0),
+                    (A == 2 ? ka : 0) + (B == 2 ? kb : 0));
+        };
+        inner[u] = fma2s(sub2(pt(1), pt(-1)), 8.0f, sub2(pt(-2), pt(2)));
       }
       dd[PS[m]] = hsum(fma2s(sub2(inner[0], inner[1]), 8.0f, sub2(inner[3], inner[2]))) * c11;
     }
@@ -234,11 +275,13 @@ __device__ __forceinline__ float field_pass(const float2* __restrict__ T, int c,
     } else {
       SD(P.d2slot) = symc(gtu, dd);
       if (P.d2 == 3) {
-        constexpr int I = F - F_BETX;
+        const int I = F - F_BETX;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
           const float v = dd[S2(j, I)];
-          if (I == 0)
+          if (SPLIT)
+            SD(S_DVB + 3 * I + j) = v;
+          else if (I == 0)
             SD(S_DVB + j) = v;
           else
             SD(S_DVB + j) += v;
@@ -246,20 +289,19 @@ __device__ __forceinline__ float field_pass(const float2* __restrict__ T, int c,
       }
     }
   }
-  SD(S_AK + F) = hsum(acc);
-#undef SD
+  SD((SPLIT ? S_AK_SPLIT : S_AK) + F) = hsum(acc);
+#undef AT
   return c0.x + c0.y;
 }
+
 
 // ------------------------------------------------------------------ phase 2
 
 // Curvature, gauge and Z4c sources from the slots and the centre values;
 // r[f] = sources + advection + dissipation.
-template <int NT>
-__device__ __forceinline__ void sources(const float* __restrict__ sd, int t, const float cen[NF],
-                                        const float gt[6], const float gtu[6], const DevParams& prm,
-                                        float r[NF]) {
-#define SD(k) sd[(k) * NT + t]
+template <bool SPLIT, class Slots>
+__device__ __forceinline__ void sources(const Slots& SD, const float cen[NF], const float gt[6],
+                                        const float gtu[6], const DevParams& prm, float r[NF]) {
   const float W = cen[F_W], al = cen[F_ALP], Kh = cen[F_KH], Th = cen[F_TH];
   float At[6];
 #pragma unroll
@@ -410,8 +452,11 @@ __device__ __forceinline__ void sources(const float* __restrict__ sd, int t, con
       inner -= 3.0f * tt * iW + v * (1.0f / 3.0f);
       float g = -2.0f * s + 2.0f * al * inner;
       g += SD(S_LBE + i);
-      g += (gtu[S2(i, 0)] * SD(S_DVB + 0) + gtu[S2(i, 1)] * SD(S_DVB + 1) + gtu[S2(i, 2)] * SD(S_DVB + 2)) *
-           (1.0f / 3.0f);
+      float dvb[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        dvb[j] = SPLIT ? SD(S_DVB + j) + SD(S_DVB + 3 + j) + SD(S_DVB + 6 + j) : SD(S_DVB + j);
+      g += (gtu[S2(i, 0)] * dvb[0] + gtu[S2(i, 1)] * dvb[1] + gtu[S2(i, 2)] * dvb[2]) * (1.0f / 3.0f);
       g += (2.0f / 3.0f) * Gd[i] * divb;
       g -= Gd[0] * dbe[0][i] + Gd[1] * dbe[1][i] + Gd[2] * dbe[2][i];
       g -= 2.0f * alk1 * (cen[F_GAMX + i] - Gd[i]);
@@ -430,12 +475,47 @@ __device__ __forceinline__ void sources(const float* __restrict__ sd, int t, con
     r[F_BX + i] = r[F_GAMX + i] - eta * Bv;
   }
 #pragma unroll
-  for (int f = 0; f < NF; ++f) r[f] += SD(S_AK + f);
+  for (int f = 0; f < NF; ++f) r[f] += SD((SPLIT ? S_AK_SPLIT : S_AK) + f);
   if (prm.shift == 1) {
 #pragma unroll
     for (int f = F_BETX; f < NF; ++f) r[f] = 0.0f;
   }
-#undef SD
+}
+
+// Centre values needed before phase 1 -- gt (for the contractions) and beta
+// (for the advection weights) -- the inverse metric, the stencil scales and
+// the per-direction weights of Delta^6 and of the antisymmetric upwind part.
+__device__ __forceinline__ void point_setup(const float2* __restrict__ U, long long q, long long fs, bool valid,
+                                            double dx, double sigma_ko, float gt[6], float be[3], float gtu[6],
+                                            float wko[3], float wup[3], float& c1, float& c2, float& c11) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float2 v = valid ? __ldg(U + (F_GXX + a) * fs + q) : make_float2((a == 0 || a == 3 || a == 5), 0.f);
+    gt[a] = v.x + v.y;
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float2 v = valid ? __ldg(U + (F_BETX + d) * fs + q) : make_float2(0.f, 0.f);
+    be[d] = v.x + v.y;
+  }
+  sym_inv_f(gt, gtu);
+  const float h = (float)dx;
+  c1 = 1.0f / (12.0f * h);
+  c2 = c1 / h;
+  c11 = c1 * c1;
+  const float cko = (float)(sigma_ko / (64.0 * dx));
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    wko[d] = 0.5f * fabsf(be[d]) * c1 + cko;
+    wup[d] = 0.5f * be[d] * c1;
+  }
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // ------------------------------------------------------------------ kernel
@@ -461,28 +541,6 @@ __device__ __forceinline__ void wait_copy(const Pipe& p, unsigned g, unsigned* e
     *p.abort = 1;
     atomicOr(err, (unsigned)ERR_TIMEOUT);
   }
-}
-
-template <int TY, int TZ, int F>
-__device__ __forceinline__ void field_step(const TmaStageArgs& A, const Pipe& p, unsigned& g, int tile, int c,
-                                           float* sd, int t, const float wko[3], const float wup[3], float c1,
-                                           float c2, float c11, const float gtu[6], float cen[NF], int which,
-                                           bool& stop) {
-  if (stop) return;
-  // the copy after this one: next field of this tile, or the first field of
-  // the CTA's next tile; its buffer was released by the barrier ending g - 1
-  if (t == 0) {
-    if (F + 1 < NF)
-      issue_load<TY, TZ>(A, p, g + 1, tile, F + 1, which);
-    else if (tile + (int)gridDim.x < A.ntiles)
-      issue_load<TY, TZ>(A, p, g + 1, tile + gridDim.x, 0, which);
-  }
-  wait_copy(p, g, A.st.err);
-  const float v = field_pass<TY, TZ, F>(p.buf[g & 1], c, sd, t, wko, wup, c1, c2, c11, gtu);
-  if (plan(F).cen) cen[F] = v;
-  __syncthreads();
-  ++g;
-  if (*p.abort) stop = true;
 }
 
 template <int TY, int TZ, int MODE>
@@ -526,45 +584,49 @@ __global__ void __launch_bounds__(32 * TY * TZ, (TY * TZ <= 4) ? 2 : 1)
     const long long sy = P->px, sz = P->plane, fs = P->fstride;
     const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
     const float2* __restrict__ U = (MODE == 1) ? P->hl[ring] : mixed_in(P, s, ring);
-    // centre values needed before phase 1: gt (for the contractions) and
-    // beta (for the advection weights)
-    float gt[6], be[3];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-      const float2 v = valid ? __ldg(U + (F_GXX + a) * fs + q) : make_float2((a == 0 || a == 3 || a == 5), 0.f);
-      gt[a] = v.x + v.y;
+    float gt[6], be[3], gtu[6], wko[3], wup[3], c1, c2, c11;
+    point_setup(U, q, fs, valid, P->dx, S.prm.sigma_ko, gt, be, gtu, wko, wup, c1, c2, c11);
+    if (valid && MODE == 0) {
+      // the epilogue's streaming reads start their way from HBM into L2
+      const double* ya = (s == 1) ? P->buf[ring] : P->buf[B_Y];
+#pragma unroll 5
+      for (int f = 0; f < NF; ++f) {
+        prefetch_l2(ya + f * fs + q);
+        if (s < 4) prefetch_l2(P->hl[ring] + f * fs + q);
+      }
     }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const float2 v = valid ? __ldg(U + (F_BETX + d) * fs + q) : make_float2(0.f, 0.f);
-      be[d] = v.x + v.y;
+    // the fields one after another (a loop: unrolled, the 25 passes overflow
+    // the instruction cache)
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) {
+      // the copy after this one: next field of this tile, or the first field
+      // of the CTA's next tile; its buffer was released by the barrier that
+      // ended copy g - 1
+      if (t == 0) {
+        if (f + 1 < NF)
+          issue_load<TY, TZ>(A, p, g + 1, tile, f + 1, which);
+        else if (tile + (int)gridDim.x < A.ntiles)
+          issue_load<TY, TZ>(A, p, g + 1, tile + gridDim.x, 0, which);
+      }
+      wait_copy(p, g, S.err);
+      const SmemAcc<C::SY, C::SZ> at{p.buf[g & 1], c};
+      field_pass_p<false>(at, plan(f), f, SmemSlots<C::NT>{sd, t}, wko, wup, c1, c2, c11, gtu);
+      __syncthreads();
+      ++g;
+      if (*p.abort) {
+        stop = true;
+        break;
+      }
     }
-    float gtu[6];
-    sym_inv_f(gt, gtu);
-    const float h = (float)P->dx;
-    const float c1 = 1.0f / (12.0f * h);
-    const float c2 = c1 / h;
-    const float c11 = c1 * c1;
-    const float cko = (float)(S.prm.sigma_ko / (64.0 * P->dx));
-    float wko[3], wup[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      wko[d] = 0.5f * fabsf(be[d]) * c1 + cko;
-      wup[d] = 0.5f * be[d] * c1;
-    }
-    float cen[NF];
-#define FS(F) field_step<TY, TZ, F>(A, p, g, tile, c, sd, t, wko, wup, c1, c2, c11, gtu, cen, which, stop)
-    FS(0); FS(1); FS(2); FS(3); FS(4); FS(5); FS(6); FS(7); FS(8); FS(9); FS(10); FS(11); FS(12);
-    FS(13); FS(14); FS(15); FS(16); FS(17); FS(18); FS(19); FS(20); FS(21); FS(22); FS(23); FS(24);
-#undef FS
     if (stop) break;
-#pragma unroll
-    for (int a = 0; a < 6; ++a) cen[F_GXX + a] = gt[a];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) cen[F_BETX + d] = be[d];
     if (!valid) continue;
-    float r[NF];
-    sources<C::NT>(sd, t, cen, gt, gtu, S.prm, r);
+    float cen[NF], r[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const float2 v = __ldg(U + (long long)f * fs + q);
+      cen[f] = v.x + v.y;
+    }
+    sources<false>(SmemSlots<C::NT>{sd, t}, cen, gt, gtu, S.prm, r);
     if (MODE == 1) {
       double* out = P->buf[B_S1];
 #pragma unroll
@@ -604,17 +666,192 @@ int setup_variant() {
   return nb;
 }
 
+// ------------------------------------------------------------------ L1 path
+
+// Prefetch into L1 the rows of the next field that its stencils read: the
+// centre row, the y and z arms of the star, and (for fields with second
+// derivatives) the 16 rows of the y-z mixed stencil.  x neighbours share the
+// rows.  A warp's 32 points cover two 128-byte lines per row.
+__device__ __forceinline__ void prefetch_field(const float2* F, long long sy, long long sz, bool mixed) {
+  prefetch_l1(F);
+#pragma unroll
+  for (int k = 1; k <= 3; ++k) {
+    prefetch_l1(F + k * sy);
+    prefetch_l1(F - k * sy);
+    prefetch_l1(F + k * sz);
+    prefetch_l1(F - k * sz);
+  }
+  if (mixed) {
+#pragma unroll
+    for (int a = -2; a <= 2; ++a)
+#pragma unroll
+      for (int b = -2; b <= 2; ++b)
+        if (a != 0 && b != 0) prefetch_l1(F + a * sy + b * sz);
+  }
+}
+
+// The same arithmetic with every stencil value read from global memory
+// through the L1 cache (no staging and no barriers, so threads beyond the
+// patch leave at once): one thread per point of the level's 32 x 4 x 1 tile
+// list, MINB CTAs per SM (NSLOT x 128 shared-memory slots each).
+template <int MINB, int MODE, bool PF>
+__global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
+  extern __shared__ float sd[];
+  const Tile tl = S.tiles[blockIdx.x];
+  const DevPatch* P = S.patches + tl.patch;
+  const int t = threadIdx.x;
+  const int i = tl.x0 + (t & 31), j = tl.y0 + (t >> 5), k = tl.z0;
+  if (i >= P->n[0] || j >= P->n[1] || k >= P->n[2]) return;
+  const int ring = S.lev->ring, s = S.stage;
+  const long long sy = P->px, sz = P->plane, fs = P->fstride;
+  const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
+  const float2* __restrict__ U = (MODE == 1) ? P->hl[ring] : mixed_in(P, s, ring);
+  if (PF && MODE == 0) {
+    // the epilogue's streaming reads (RK accumulator or time level, and the
+    // split of the time level) start their way from HBM into L2 now
+    const double* ya = (s == 1) ? P->buf[ring] : P->buf[B_Y];
+    const float2* hn = P->hl[ring];
+#pragma unroll 5
+    for (int f = 0; f < NF; ++f) {
+      prefetch_l2(ya + f * fs + q);
+      if (s < 4) prefetch_l2(hn + f * fs + q);
+    }
+  }
+  float gt[6], be[3], gtu[6], wko[3], wup[3], c1, c2, c11;
+  point_setup(U, q, fs, true, P->dx, S.prm.sigma_ko, gt, be, gtu, wko, wup, c1, c2, c11);
+  // one field at a time (a loop, not unrolled: the register budget of 3 or 4
+  // CTAs per SM has no room for hoisting loads across fields); with PF the
+  // next field's rows are prefetched into L1 while this one is formed
+#pragma unroll 1
+  for (int f = 0; f < NF; ++f) {
+    if (PF && f + 1 < NF) prefetch_field(U + (long long)(f + 1) * fs + q, sy, sz, plan(f + 1).d2 != 0);
+    const GlobalAcc at{U + (long long)f * fs + q, sy, sz};
+    field_pass_p<false>(at, plan(f), f, SmemSlots<128>{sd, t}, wko, wup, c1, c2, c11, gtu);
+  }
+  float cen[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const float2 v = __ldg(U + (long long)f * fs + q);
+    cen[f] = v.x + v.y;
+  }
+  float r[NF];
+  sources<false>(SmemSlots<128>{sd, t}, cen, gt, gtu, S.prm, r);
+  if (MODE == 1) {
+    double* out = P->buf[B_S1];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) out[f * fs + q] = (double)r[f];
+  } else {
+    rk_update_mixed(P, s, ring, S.dt, q, r, S.prm.w_floor, S.err);
+  }
+}
+
+template <bool PF>
+bool setup_ldg() {
+  const int smem = NSLOT * 128 * 4;
+  return cudaFuncSetAttribute(z4c_stage_ldg_kernel<3, 0, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(z4c_stage_ldg_kernel<3, 1, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+             cudaSuccess;
+}
+
+template <bool PF>
+void launch_ldg(const StageArgs& a, cudaStream_t st) {
+  const int smem = NSLOT * 128 * 4;
+  if (a.stage == 0)
+    z4c_stage_ldg_kernel<3, 1, PF><<<a.ntiles, 128, smem, st>>>(a);
+  else
+    z4c_stage_ldg_kernel<3, 0, PF><<<a.ntiles, 128, smem, st>>>(a);
+}
+
+// ------------------------------------------------------------------ split path
+
+// The stage in two launches.  The derivative kernel forms, for FG fields per
+// thread and one point, the same slot values as phase 1 and stores them as
+// planes of FP32 in global memory; with no curvature algebra it needs few
+// registers and no shared memory, so many warps hide the stencil latency.
+// The algebra kernel then reads a point's slots (coalesced, one plane per
+// slot), forms the sources and applies the RK4 update.  Point p of a launch
+// is thread t of tile b: p = 128 b + t.
+constexpr int FG = 5;  // fields per derivative thread
+
+template <int MODE>
+__global__ void __launch_bounds__(128) z4c_deriv_kernel(StageArgs S, float* __restrict__ dslot, long long npts) {
+  const Tile tl = S.tiles[blockIdx.x];
+  const DevPatch* P = S.patches + tl.patch;
+  const int t = threadIdx.x;
+  const int i = tl.x0 + (t & 31), j = tl.y0 + (t >> 5), k = tl.z0;
+  if (i >= P->n[0] || j >= P->n[1] || k >= P->n[2]) return;
+  const int ring = S.lev->ring, s = S.stage;
+  const long long sy = P->px, sz = P->plane, fs = P->fstride;
+  const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
+  const float2* __restrict__ U = (MODE == 1) ? P->hl[ring] : mixed_in(P, s, ring);
+  float gt[6], be[3], gtu[6], wko[3], wup[3], c1, c2, c11;
+  point_setup(U, q, fs, true, P->dx, S.prm.sigma_ko, gt, be, gtu, wko, wup, c1, c2, c11);
+  const GlobalSlots slots{dslot, npts, (long long)blockIdx.x * 128 + t};
+  const int f0 = blockIdx.y * FG;
+#pragma unroll 1
+  for (int f = f0; f < f0 + FG; ++f) {
+    if (f + 1 < f0 + FG) prefetch_field(U + (long long)(f + 1) * fs + q, sy, sz, plan(f + 1).d2 != 0);
+    field_pass_p<true>(GlobalAcc{U + (long long)f * fs + q, sy, sz}, plan(f), f, slots, wko, wup, c1, c2, c11,
+                       gtu);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 3) z4c_algebra_kernel(StageArgs S, const float* __restrict__ dslot,
+                                                             long long npts) {
+  const Tile tl = S.tiles[blockIdx.x];
+  const DevPatch* P = S.patches + tl.patch;
+  const int t = threadIdx.x;
+  const int i = tl.x0 + (t & 31), j = tl.y0 + (t >> 5), k = tl.z0;
+  if (i >= P->n[0] || j >= P->n[1] || k >= P->n[2]) return;
+  const int ring = S.lev->ring, s = S.stage;
+  const long long sy = P->px, sz = P->plane, fs = P->fstride;
+  const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
+  const float2* __restrict__ U = (MODE == 1) ? P->hl[ring] : mixed_in(P, s, ring);
+  if (MODE == 0) {
+    const double* ya = (s == 1) ? P->buf[ring] : P->buf[B_Y];
+#pragma unroll 5
+    for (int f = 0; f < NF; ++f) {
+      prefetch_l2(ya + f * fs + q);
+      if (s < 4) prefetch_l2(P->hl[ring] + f * fs + q);
+    }
+  }
+  float cen[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const float2 v = __ldg(U + (long long)f * fs + q);
+    cen[f] = v.x + v.y;
+  }
+  float gt[6], gtu[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) gt[a] = cen[F_GXX + a];
+  sym_inv_f(gt, gtu);
+  float r[NF];
+  sources<true>(GlobalSlotsIn{dslot, npts, (long long)blockIdx.x * 128 + t}, cen, gt, gtu, S.prm, r);
+  if (MODE == 1) {
+    double* out = P->buf[B_S1];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) out[f * fs + q] = (double)r[f];
+  } else {
+    rk_update_mixed(P, s, ring, S.dt, q, r, S.prm.w_floor, S.err);
+  }
+}
+
 }  // namespace
 
 // tile shape (TY, TZ) of each TMA variant
 static const int kShape[TMA_NVARIANTS][2] = {{4, 1}, {2, 2}, {4, 2}, {8, 1}};
 
 void tma_variant_shape(int v, int* ty, int* tz) {
-  *ty = kShape[v][0];
-  *tz = kShape[v][1];
+  const bool ok = v >= 0 && v < TMA_NVARIANTS;
+  *ty = ok ? kShape[v][0] : 0;
+  *tz = ok ? kShape[v][1] : 0;
 }
 
-int tma_box_bytes(int v) { return 38 * (kShape[v][0] + 6) * (kShape[v][1] + 6) * 8; }
+int tma_box_bytes(int v) {
+  return (v >= 0 && v < TMA_NVARIANTS) ? 38 * (kShape[v][0] + 6) * (kShape[v][1] + 6) * 8 : 0;
+}
 
 int tma_setup_variant(int v) {
   switch (v) {
@@ -632,6 +869,31 @@ void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st) {
     case 1: launch_variant<2, 2>(a, grid, st); break;
     case 2: launch_variant<4, 2>(a, grid, st); break;
     case 3: launch_variant<8, 1>(a, grid, st); break;
+  }
+}
+
+int ldg_setup(int prefetch) { return prefetch ? setup_ldg<true>() : setup_ldg<false>(); }
+
+void launch_stage_ldg(int prefetch, const StageArgs& a, cudaStream_t st) {
+  if (a.ntiles == 0) return;
+  if (prefetch)
+    launch_ldg<true>(a, st);
+  else
+    launch_ldg<false>(a, st);
+}
+
+long long split_slot_floats(long long ntiles) { return (long long)NSLOT_SPLIT * ntiles * 128; }
+
+void launch_stage_split(const StageArgs& a, float* dslot, cudaStream_t st) {
+  if (a.ntiles == 0) return;
+  const long long npts = (long long)a.ntiles * 128;
+  const dim3 gd(a.ntiles, NF / FG);
+  if (a.stage == 0) {
+    z4c_deriv_kernel<1><<<gd, 128, 0, st>>>(a, dslot, npts);
+    z4c_algebra_kernel<1><<<a.ntiles, 128, 0, st>>>(a, dslot, npts);
+  } else {
+    z4c_deriv_kernel<0><<<gd, 128, 0, st>>>(a, dslot, npts);
+    z4c_algebra_kernel<0><<<a.ntiles, 128, 0, st>>>(a, dslot, npts);
   }
 }
 

@@ -24,6 +24,7 @@ from tests.gpu_common import grid_for, rel_err
 skbuild.build()
 
 TMA = [1, 2, 3, 4]
+PAIRS = [5, 6, 7]  # L1 path and split launches, same arithmetic
 TOL = 1e-4          # mixed precision vs the FP64 oracle
 TOL_KERNELS = 2e-5  # TMA kernel vs direct mixed kernel, same data
 
@@ -45,7 +46,7 @@ def _rhs(p, u, kernel, **prm):
     return r
 
 
-@pytest.mark.parametrize("kernel", TMA)
+@pytest.mark.parametrize("kernel", TMA + PAIRS)
 def test_tma_rhs_puncture(kernel):
     p = idd.single_puncture_patch(32, 8.0)
     u = idd.single_puncture_data(p)
@@ -57,12 +58,12 @@ def test_tma_rhs_puncture(kernel):
     assert e0.max() <= TOL_KERNELS, dict(zip(idd.FIELD_NAMES, e0))
 
 
-@pytest.mark.parametrize("kernel", TMA)
+@pytest.mark.parametrize("kernel", TMA + PAIRS)
 @pytest.mark.parametrize("n", [(40, 10, 7), (33, 9, 5), (64, 12, 4)])
 def test_tma_ragged_patch_rhs(kernel, n):
     """Tiles cut by the patch edge in x, y and z: the copies past the array
     are filled with zeros and the points beyond the patch write nothing."""
-    ty, tz = {1: (4, 1), 2: (2, 2), 3: (4, 2), 4: (8, 1)}[kernel]
+    ty, tz = {1: (4, 1), 2: (2, 2), 3: (4, 2), 4: (8, 1), 5: (1, 1), 6: (1, 1), 7: (1, 1)}[kernel]
     if n[1] < ty or n[2] < tz:
         pytest.skip("patch thinner than the tile")
     dx = 0.25
@@ -81,7 +82,7 @@ def test_tma_ragged_patch_rhs(kernel, n):
     assert np.all(r[~inner] == 0.0)
 
 
-@pytest.mark.parametrize("kernel", TMA)
+@pytest.mark.parametrize("kernel", TMA + PAIRS)
 def test_tma_rhs_gauge_wave(kernel):
     p = idd.Patch(n=(32, 4, 4), dx=1 / 32, origin=(-0.5, -2 / 32, -2 / 32))
     if kernel == 4:
@@ -93,7 +94,7 @@ def test_tma_rhs_gauge_wave(kernel):
     assert e.max() <= TOL, dict(zip(idd.FIELD_NAMES, e))
 
 
-@pytest.mark.parametrize("kernel", TMA)
+@pytest.mark.parametrize("kernel", [0] + TMA + PAIRS)
 def test_tma_rk4_step_puncture(kernel):
     p = idd.single_puncture_patch(32, 8.0)
     u = idd.single_puncture_data(p)
@@ -108,7 +109,7 @@ def test_tma_rk4_step_puncture(kernel):
     assert e.max() <= TOL, dict(zip(idd.FIELD_NAMES, e))
 
 
-@pytest.mark.parametrize("kernel", TMA)
+@pytest.mark.parametrize("kernel", [0] + TMA + PAIRS)
 def test_tma_pi_symmetry_bitwise(kernel):
     p = idd.single_puncture_patch(32, 8.0)
     g = grid_for([p], precision=1)
@@ -126,10 +127,13 @@ def _tma_hierarchy():
     return h, idd.hierarchy_data(h, noise=1e-10)
 
 
-def test_tma_level_step_hierarchy_vs_oracle():
+@pytest.mark.parametrize("kernel", [1, 6, 7])
+def test_tma_level_step_hierarchy_vs_oracle(kernel):
     h, states = _tma_hierarchy()
     g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(precision=1), stream=torch.cuda.Stream())
-    assert all(g.stage_kernel(l) == 1 for l in range(len(h.levels)))  # the default where it fits
+    assert all(g.stage_kernel(l) == 6 for l in range(len(h.levels)))  # the mixed-precision default
+    for l in range(len(h.levels)):
+        g.set_stage_kernel(l, kernel)
     for i, u in enumerate(states):
         g.upload_fields(i, u)
     bo = oracle.BOHierarchy(h, states, oracle.Params(), courant=0.5)
@@ -151,7 +155,7 @@ def test_autotune_choice_and_parity():
         a.upload_fields(i, u)
         b.upload_fields(i, u)
     us = a.autotune(reps=2, use_cache=False)
-    assert us.shape == (len(h.levels), 5)
+    assert us.shape == (len(h.levels), len(sk.STAGE_KERNELS))
     for l in range(len(h.levels)):
         k = a.stage_kernel(l)
         assert us[l, k] > 0 and us[l, k] == us[l][us[l] > 0].min()
@@ -174,9 +178,13 @@ def test_autotune_choice_and_parity():
 def test_tma_kernel_rejected_where_it_does_not_fit():
     p = idd.Patch(n=(24, 8, 8), dx=0.25, origin=(-3.0, -1.0, -1.0))
     g = grid_for([p], precision=1)
-    assert g.stage_kernel(0) == 0
+    assert g.stage_kernel(0) == 6
     with pytest.raises(sk.SacrakError):
         g.set_stage_kernel(0, 1)
-    f = grid_for([idd.single_puncture_patch(32, 8.0)])  # FP64: only the direct kernel
     with pytest.raises(sk.SacrakError):
-        f.set_stage_kernel(0, 1)
+        g.set_stage_kernel(0, 8)
+    f = grid_for([idd.single_puncture_patch(32, 8.0)])  # FP64: only the direct kernel
+    assert f.stage_kernel(0) == 0
+    for k in (1, 5):
+        with pytest.raises(sk.SacrakError):
+            f.set_stage_kernel(0, k)
