@@ -189,6 +189,7 @@ def main():
                     help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
                          "mixed-error: the 7-level hierarchy in FP64 and mixed precision side by side")
     ap.add_argument("--coarse-steps", type=int, default=64, help="mixed-error: coarse steps")
+    ap.add_argument("--error-kernels", default="", help="mixed-error: stage kernels to compare, e.g. 6,0")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -270,8 +271,9 @@ def main():
 
 
 # per-zone DRAM traffic of one stage-kernel launch from the ncu captures of the
-# 96^3 case (profiles/): FP64 1.53-1.98 GB, mixed 0.877 GB per 884,736 zones
-NCU_TRAFFIC_PER_ZONE = {0: 1.98e9 / 884736, 1: 0.877e9 / 884736}
+# 96^3 case (profiles/): FP64 1.53-1.98 GB, mixed (stage kernel 6) 0.847 GB
+# per 884,736 zones
+NCU_TRAFFIC_PER_ZONE = {0: 1.98e9 / 884736, 1: 0.847e9 / 884736}
 
 
 def roofline(r, hbm):
@@ -559,14 +561,20 @@ def mixed_error_case(torch, sk, args):
     """Evolve the 7-level binary in FP64 and in mixed precision from the same
     data for --coarse-steps coarse steps; report per level and field the
     max |mixed - FP64| (absolute and over the field's max |FP64|) and both
-    runs' constraint norms."""
+    runs' constraint norms.  --error-kernels lists the mixed stage kernels to
+    compare (one mixed run each, default: the default kernel)."""
     import initial_data as idd
     h = hierarchy()
     grids = {}
-    for name, prec in (("fp64", 0), ("mixed", 1)):
+    kernels = [int(k) for k in args.error_kernels.split(",")] if args.error_kernels else [None]
+    runs = [("fp64", 0, None)] + [("mixed" if k is None else "mixed-k%d" % k, 1, k) for k in kernels]
+    for name, prec, k in runs:
         g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(courant=args.courant, precision=prec),
                     stream=torch.cuda.Stream())
         g.set_initial_data(1, h.masses, h.positions)
+        if k is not None:
+            for l in range(len(h.levels)):
+                g.set_stage_kernel(l, k)
         grids[name] = g
     times = {}
     for name, g in grids.items():
@@ -577,24 +585,28 @@ def mixed_error_case(torch, sk, args):
         times[name] = (time.perf_counter() - t0) / args.coarse_steps
     report = {"case": "mixed-error", "coarse_steps": args.coarse_steps, "courant": args.courant,
               "t_final": grids["fp64"].level_time(0),
-              "s_per_coarse_step": times, "levels": []}
+              "s_per_coarse_step": times, "stage_kernels": {n: sk.STAGE_KERNELS[grids[n].stage_kernel(0)]
+                                                            for n in grids}, "levels": []}
     for l in range(len(h.levels)):
         ids = [i for i, p in enumerate(h.patches) if p.level == l]
-        err = np.zeros(25)
-        rel = np.zeros(25)
-        for i in ids:
-            a = grids["fp64"].download_fields(i)[:, 3:-3, 3:-3, 3:-3]
-            m = grids["mixed"].download_fields(i)[:, 3:-3, 3:-3, 3:-3]
-            d = np.abs(m - a).max(axis=(1, 2, 3))
-            s = np.abs(a).max(axis=(1, 2, 3))
-            err = np.maximum(err, d)
-            rel = np.maximum(rel, np.where(s > 0, d / np.where(s > 0, s, 1), d))
-        report["levels"].append({
-            "level": l,
-            "max_abs_err": {n: float(v) for n, v in zip(idd.FIELD_NAMES, err)},
-            "max_rel_err": {n: float(v) for n, v in zip(idd.FIELD_NAMES, rel)},
-            "constraints_fp64": list(map(float, grids["fp64"].constraints(l))),
-            "constraints_mixed": list(map(float, grids["mixed"].constraints(l)))})
+        row = {"level": l, "constraints_fp64": list(map(float, grids["fp64"].constraints(l)))}
+        for name in grids:
+            if name == "fp64":
+                continue
+            err = np.zeros(25)
+            rel = np.zeros(25)
+            for i in ids:
+                a = grids["fp64"].download_fields(i)[:, 3:-3, 3:-3, 3:-3]
+                m = grids[name].download_fields(i)[:, 3:-3, 3:-3, 3:-3]
+                d = np.abs(m - a).max(axis=(1, 2, 3))
+                sc = np.abs(a).max(axis=(1, 2, 3))
+                err = np.maximum(err, d)
+                rel = np.maximum(rel, np.where(sc > 0, d / np.where(sc > 0, sc, 1), d))
+            sfx = "" if name == "mixed" else "_" + name
+            row["max_abs_err" + sfx] = {n: float(v) for n, v in zip(idd.FIELD_NAMES, err)}
+            row["max_rel_err" + sfx] = {n: float(v) for n, v in zip(idd.FIELD_NAMES, rel)}
+            row["constraints_" + name] = list(map(float, grids[name].constraints(l)))
+        report["levels"].append(row)
     print(json.dumps(report), flush=True)
     for g in grids.values():
         g.close()

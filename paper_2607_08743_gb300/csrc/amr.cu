@@ -111,7 +111,13 @@ __device__ __forceinline__ int floor_half(int i) { return i >= 0 ? i / 2 : -((-i
 // directions.  One CTA takes one field of one brick: it stages the brick's
 // parent cells plus a 3-cell halo in shared memory and applies the 6-point
 // interpolant as three separable passes (x, then y, then z), each child at
-// -1/4 (nodes -3..2) or +1/4 (nodes -2..3) of its parent cell.
+// -1/4 (nodes -3..2) or +1/4 (nodes -2..3) of its parent cell.  The passes
+// run in FP64, or in mixed precision in double-float FP32 pairs from the
+// parent's hi/lo split, stored as the split of the result.  (A plain FP32
+// version on differences from one reference per brick spread its rounding
+// over the brick's variation, up to 14 parent cells; the refinement-boundary
+// ghosts it produced made the Gamma-driver fields of the finest levels drift
+// about five times further from the FP64 run over 64 coarse steps.)
 struct ProlongArgs {
   const DevPatch* patches;
   const int* patch_ids;   // children (one level)
@@ -156,9 +162,35 @@ int prolong_bricks(int n0, int n1, int n2) {
   return tot;
 }
 
+// Arithmetic of the passes: FP64, or (mixed precision) double-float pairs
+// (hi, lo) of FP32 with error-free products and sums, which keep about 44
+// bits at FP32 instruction rates.  The weights are exact in FP32.
+__device__ __forceinline__ void p_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void p_zero(float2& a) { a = make_float2(0.0f, 0.0f); }
+__device__ __forceinline__ void p_fma(double& acc, double w, double x) { acc = fma(w, x, acc); }
+// (explicitly rounded intrinsics: a contraction into an FMA would break the
+// error-free transformations)
+__device__ __forceinline__ void p_fma(float2& acc, double wd, float2 x) {
+  const float w = (float)wd;
+  const float p = __fmul_rn(w, x.x);
+  const float pe = fmaf(w, x.x, -p);  // p + pe = w x.hi exactly
+  const float sh = __fadd_rn(acc.x, p);  // two-sum of acc.hi and p
+  const float bb = __fsub_rn(sh, acc.x);
+  const float e = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(sh, bb)), __fsub_rn(p, bb));
+  acc.y = __fadd_rn(acc.y, fmaf(w, x.y, __fadd_rn(e, pe)));
+  acc.x = sh;
+}
+__device__ __forceinline__ void p_norm(double&) {}
+__device__ __forceinline__ void p_norm(float2& a) {  // two-sum: hi = RN(hi + lo)
+  const float sh = __fadd_rn(a.x, a.y);
+  const float bb = __fsub_rn(sh, a.x);
+  a.y = __fadd_rn(__fsub_rn(a.x, __fsub_rn(sh, bb)), __fsub_rn(a.y, bb));
+  a.x = sh;
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A) {
-  typedef typename std::conditional<MIXED, float, double>::type T;
+  typedef typename std::conditional<MIXED, float2, double>::type T;
   __shared__ T S[PB_S];
   __shared__ T X1[PB_X1];
   __shared__ T X2[PB_X2];
@@ -203,18 +235,6 @@ __global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A
   // the nesting margin) are read: the children that are kept need no others,
   // and cells outside that range (possibly never written) would turn a zero
   // weight into NaN.  They are staged as 0.
-  float h0 = 0.0f, l0 = 0.0f;
-  double u0 = 0.0;
-  if (MIXED) {
-    // reference: the brick's first parent cell; the weights sum to one along
-    // every axis, so interpolating differences from it and adding it back in
-    // FP64 changes only the rounding
-    const long long qr = pq(lo[0], lo[1], lo[2]);
-    const float2 r = P->hl[slot][fo + qr];
-    h0 = r.x;
-    l0 = r.y;
-    u0 = P->buf[slot][fo + qr];
-  }
   // threads as a 16 x 16 sheet (x, y); every pass loops over its third axis
   // (every extent is at most 16)
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -223,15 +243,13 @@ __global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A
     const bool inxy = a >= -2 && a <= m[0] + 1 && bb >= -2 && bb <= m[1] + 1;
     for (int z = 0; z < Sz; ++z) {
       const int c = lo[2] - 3 + z;
-      T v = T(0);
+      T v;
+      p_zero(v);
       if (inxy && c >= -2 && c <= m[2] + 1) {
-        const long long q = fo + pq(a, bb, c);
-        if (MIXED) {
-          const float2 w = __ldg(P->hl[slot] + q);
-          v = (T)((w.x - h0) + (w.y - l0));
-        } else {
-          v = (T)__ldg(P->buf[slot] + q);
-        }
+        if (MIXED)
+          v = *reinterpret_cast<const T*>(P->hl[slot] + fo + pq(a, bb, c));
+        else
+          v = *reinterpret_cast<const T*>(P->buf[slot] + fo + pq(a, bb, c));
       }
       S[(z * Sy + ty) * Sx + tx] = v;
     }
@@ -242,9 +260,11 @@ __global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A
     const int p = tx >> 1, od = tx & 1;
     for (int z = 0; z < Sz; ++z) {
       const T* row = S + (z * Sy + ty) * Sx + p + od;
-      T acc = T(0);
+      T acc;
+      p_zero(acc);
 #pragma unroll
-      for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * row[t];
+      for (int t = 0; t < 6; ++t) p_fma(acc, od ? c_wp[t] : c_wm[t], row[t]);
+      p_norm(acc);
       X1[(z * Sy + ty) * Cx + tx] = acc;
     }
   }
@@ -254,9 +274,11 @@ __global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A
     const int p = ty >> 1, od = ty & 1;
     for (int z = 0; z < Sz; ++z) {
       const T* col = X1 + (z * Sy + p + od) * Cx + tx;
-      T acc = T(0);
+      T acc;
+      p_zero(acc);
 #pragma unroll
-      for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * col[t * Cx];
+      for (int t = 0; t < 6; ++t) p_fma(acc, od ? c_wp[t] : c_wm[t], col[t * Cx]);
+      p_norm(acc);
       X2[(z * Cy + ty) * Cx + tx] = acc;
     }
   }
@@ -275,14 +297,13 @@ __global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A
       if (actxy && k >= 0 && k < C->n[2]) continue;
       const int p = cz >> 1, od = cz & 1;
       const T* col = X2 + ((p + od) * Cy + ty) * Cx + tx;
-      T acc = T(0);
+      T acc;
+      p_zero(acc);
 #pragma unroll
-      for (int t = 0; t < 6; ++t) acc += (T)(od ? c_wp[t] : c_wm[t]) * col[t * Cx * Cy];
+      for (int t = 0; t < 6; ++t) p_fma(acc, od ? c_wp[t] : c_wm[t], col[t * Cx * Cy]);
+      p_norm(acc);  // mixed precision: (RN(v), v - RN(v)), the split of the value
       const long long o = (i + GH) + (long long)(j + GH) * C->px + (long long)(k + GH) * C->plane;
-      if (MIXED)
-        split_to(u0 + (double)acc, g2, o);
-      else
-        g[o] = (double)acc;
+      *reinterpret_cast<T*>(MIXED ? (void*)(g2 + o) : (void*)(g + o)) = acc;
     }
   }
 }
@@ -305,14 +326,17 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
   const long long q = i + (long long)j * C->px + (long long)k * C->plane;
   // this block's five fields (gridDim.z = 5 groups)
   const int f0 = blockIdx.z * (NF / 5);
+  const bool dual = A.dual && A.mode == 0 && A.stage == 2;
   if (!A.mixed) {
     double* __restrict__ dst = C->buf[fill_slot(A.mode, A.stage, ring)];
+    double* __restrict__ dst3 = C->buf[fill_slot(0, 3, ring)];
 #pragma unroll
     for (int f = f0; f < f0 + NF / 5; ++f) {
       const long long o = f * C->fstride + q;
       double v = w1 * g1[o] + w2 * g2[o];
       if (q3) v += w0 * g0[o];
       dst[o] = v;
+      if (dual) dst3[o] = v;
     }
     return;
   }
@@ -322,6 +346,7 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
   // in FP32, so both are formed in FP32 on differences from a nearby hi.
   const bool later = (A.mode == 0 && A.stage > 1);
   float2* __restrict__ in = later ? mixed_in(C, A.stage, ring) : nullptr;
+  float2* __restrict__ in3 = mixed_in(C, 3, ring);
   const float2* __restrict__ h0 = reinterpret_cast<const float2*>(g0);
   const float2* __restrict__ h1 = reinterpret_cast<const float2*>(g1);
   const float2* __restrict__ h2 = reinterpret_cast<const float2*>(g2);
@@ -336,6 +361,7 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
       float lo = w1f * ((a1.x - hi) + a1.y) + w2f * ((a2.x - hi) + a2.y);
       if (q3) lo += w0f * ((a0.x - hi) + a0.y);
       in[o] = make_float2(hi, lo);
+      if (dual) in3[o] = make_float2(hi, lo);
     } else {
       const float r = a1.x;
       float d = w1f * a1.y + w2f * ((a2.x - r) + a2.y);
@@ -481,6 +507,26 @@ __global__ void exchange_kernel(ExchArgs E) {
       split_to(*pb, Pb->hl[slot], ob);
     }
   }
+}
+
+// Copy between a patch buffer (rows of px doubles) and a contiguous patch
+// array (rows of NX doubles): host transfers then move one contiguous block.
+__global__ void repack_kernel(double* __restrict__ dst, const double* __restrict__ src, long long rows, int NX,
+                              int px, int to_pitched) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= NX) return;
+  for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+    if (to_pitched)
+      dst[r * px + x] = src[r * NX + x];
+    else
+      dst[r * NX + x] = src[r * px + x];
+  }
+}
+
+void launch_repack(double* dst, const double* src, long long rows, int NX, int px, int to_pitched,
+                   cudaStream_t st) {
+  const unsigned gy = (unsigned)(rows < 65535 ? rows : 65535);
+  repack_kernel<<<dim3((NX + 127) / 128, gy), 128, 0, st>>>(dst, src, rows, NX, px, to_pitched);
 }
 
 // level bookkeeping after a completed RK4 step: advance the ring, count valid

@@ -402,12 +402,15 @@ FillArgs fill_args(sacrak_grid* g, int l, int mode, int stage, double s0, double
   a.stage = stage;
   ghost_time_weights(s0, ds, mode == 0 ? stage : 0, a.wq, a.wl);
   a.mixed = g->prm.precision == 1;
+  a.dual = 0;
   return a;
 }
 
 // ghost fill of level l for the buffer given by (mode, stage); for levels
 // > 0 the child step starts at fraction s0 of the parent step and lasts ds
-void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double ds) {
+// prolong: 0 skip the time fill (exchange only), 1 fill, 2 fill the stage-2
+// input and the stage-3 input together (stages 2 and 3 share their time)
+void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double ds, int prolong = 1) {
   const int np = (int)g->lvl_ids[l].size();
   if (l == 0) {
     if (g->prm.bc == 1)
@@ -416,7 +419,11 @@ void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double d
       launch_fill(FILL_FROZEN, fill_args(g, l, mode, stage, 0.0), np, g->lvl_max_shell[l], g->stream);
     return;
   }
-  launch_fill(FILL_PROLONG, fill_args(g, l, mode, stage, s0, ds), np, g->lvl_max_shell[l], g->stream);
+  if (prolong) {
+    FillArgs fa = fill_args(g, l, mode, stage, s0, ds);
+    fa.dual = prolong == 2;
+    launch_fill(FILL_PROLONG, fa, np, g->lvl_max_shell[l], g->stream);
+  }
   // same-level exchange between every overlapping pair
   const auto& ids = g->lvl_ids[l];
   for (size_t a = 0; a < ids.size(); ++a)
@@ -473,7 +480,7 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
   const int np = (int)g->lvl_ids[l].size();
   for (int s = 1; s <= 4; ++s) {
     if (!(l == 0 && (g->prm.bc == 0 || (g->prm.bc == 2 && s == 1))))
-      fill_ghosts(g, l, 0, s, frac0, dfrac);
+      fill_ghosts(g, l, 0, s, frac0, dfrac, l > 0 ? (s == 2 ? 2 : (s == 3 ? 0 : 1)) : 1);
     StageArgs a;
     a.tiles = g->d_tiles + g->lvl_tile_off[l];
     a.ntiles = (int)g->lvl_ntiles[l];
@@ -787,6 +794,24 @@ static sacrak_status copy_patch(sacrak_grid* g, int patch, double* dst_dev_slot,
   const DevPatch& P = g->hp[patch];
   size_t width = (size_t)P.NX * sizeof(double);
   size_t rows = (size_t)NF * P.NY * P.NZ;
+  cudaPointerAttributes at;
+  const void* host_side = upload ? (const void*)src : (const void*)dst;
+  const bool is_host = cudaPointerGetAttributes(&at, host_side) != cudaSuccess ||
+                       at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+  cudaGetLastError();
+  if (is_host) {
+    // one contiguous host transfer through a free stage buffer of the patch,
+    // repacked to / from the padded rows on the device
+    double* stage = (dst_dev_slot == P.buf[B_S1]) ? P.buf[B_S0] : P.buf[B_S1];
+    if (upload) {
+      CK(cudaMemcpyAsync(stage, src, width * rows, cudaMemcpyHostToDevice, g->stream));
+      launch_repack(dst_dev_slot, stage, (long long)rows, P.NX, P.px, 1, g->stream);
+    } else {
+      launch_repack(stage, dst_dev_slot, (long long)rows, P.NX, P.px, 0, g->stream);
+      CK(cudaMemcpyAsync(dst, stage, width * rows, cudaMemcpyDeviceToHost, g->stream));
+    }
+    return check_launch(g);
+  }
   if (upload)
     CK(cudaMemcpy2DAsync(dst_dev_slot, P.px * sizeof(double), src, width, width, rows,
                          cudaMemcpyDefault, g->stream));

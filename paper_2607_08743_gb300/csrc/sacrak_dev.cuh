@@ -246,6 +246,7 @@ struct FillArgs {
   // for three valid levels (wq) and for two (wl, oldest weight 0)
   double wq[3], wl[3];
   int mixed;  // also maintain the FP32 split buffers
+  int dual;   // time fill of stage 2: also fill the stage-3 input (same stage time)
 };
 
 struct ExchArgs {
@@ -285,6 +286,9 @@ void launch_sommerfeld_mixed(const GhostArgs& a, int npatches, long long max_she
 void launch_split(const DevPatch* patches, const DevLevel* levels, int patch, long long tot,
                   cudaStream_t st);
 void launch_level_advance(DevLevel* L, double dt, cudaStream_t st);
+// pitched patch buffer <-> contiguous patch array (rows of NX doubles)
+void launch_repack(double* dst, const double* src, long long rows, int NX, int px, int to_pitched,
+                   cudaStream_t st);
 void launch_init(const InitArgs& a, int patch, long long tot, cudaStream_t st);
 void launch_symmetrise(const DevPatch* p, const DevLevel* l, int patch, long long half_tot,
                        cudaStream_t st);
