@@ -102,6 +102,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(ms: float, dist) -> float:
+    """The slowest rank's time (replicas: every rank times its own hierarchy;
+    one all-reduce outside the timed region).  NCCL reduces a CUDA tensor,
+    gloo a CPU one."""
+    if not dist:
+        return ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(zone_updates_per_rank: int, world: int, ms: float) -> float:
+    """Zone updates of all ranks per second of the slowest rank."""
+    return world * zone_updates_per_rank / (ms * 1e-3)
+
+
 def hierarchy():
     import initial_data as idd
     return idd.binary_7_level()
@@ -109,14 +127,16 @@ def hierarchy():
 
 def launches_per_coarse_step(h) -> int:
     """Kernels launched by one coarse step (the recursion is static): per level
-    step 4 x (ghost fill on levels > 0, fused stage kernel, Sommerfeld ghosts
-    on level 0), the level bookkeeping, the spatial prolongation of the new
-    slot for the children; per child level step pair: ghost fill at the new
-    time, restriction and the prolongation of the restricted slot."""
+    step 4 fused stage kernels, 3 ghost time fills on levels > 0 (stages 2 and
+    3 share one), 4 Sommerfeld ghost updates on level 0, the level
+    bookkeeping, the spatial prolongation of the new slot for the children;
+    per child level step pair: ghost fill at the new time, restriction and the
+    prolongation of the restricted slot.  (No same-level overlaps in these
+    hierarchies, so no exchange launches.)"""
     total = 0
     nlev = len(h.levels)
     for l, lv in enumerate(h.levels):
-        per = 4 * (1 + (1 if l > 0 else 0) + (1 if l == 0 else 0)) + 1
+        per = 4 + (3 if l > 0 else 4) + 1
         if l + 1 < nlev:
             per += 1 + 3  # prolong new slot; after the two child steps: fill, restrict, prolong
         total += (2 ** l) * per
@@ -185,7 +205,8 @@ def main():
     ap.add_argument("--gw-steps", type=int, default=1000,
                     help="gauge-wave: RK4 steps on the coarsest grid; robust-stability: steps per grid")
     ap.add_argument("--case", default="amr7",
-                    choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep"],
+                    choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep",
+                             "amr7-zsym"],
                     help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
                          "mixed-error: the 7-level hierarchy in FP64 and mixed precision side by side")
     ap.add_argument("--coarse-steps", type=int, default=64, help="mixed-error: coarse steps")
@@ -215,6 +236,9 @@ def main():
         return
     if args.case == "mixed-error":
         mixed_error_case(torch, sk, args)
+        return
+    if args.case == "amr7-zsym":
+        zsym_case(torch, sk, args)
         return
     if args.case == "sweep":
         sweep_case(torch, sk, args)
@@ -271,9 +295,9 @@ def main():
 
 
 # per-zone DRAM traffic of one stage-kernel launch from the ncu captures of the
-# 96^3 case (profiles/): FP64 1.53-1.98 GB, mixed (stage kernel 6) 0.847 GB
+# 96^3 case (profiles/): FP64 1.53-1.98 GB, mixed (stage kernel 10) 0.854 GB
 # per 884,736 zones
-NCU_TRAFFIC_PER_ZONE = {0: 1.98e9 / 884736, 1: 0.847e9 / 884736}
+NCU_TRAFFIC_PER_ZONE = {0: 1.98e9 / 884736, 1: 0.854e9 / 884736}
 
 
 def roofline(r, hbm):
@@ -324,10 +348,7 @@ def measure(torch, sk, h, precision, args, world, dist):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     norms = list(map(float, g.constraints(0)))  # also checks the state stayed finite
     nprof = max(1, min(args.steps, 2))
     kern = stage_kernel_timing(g, nprof)
@@ -336,12 +357,49 @@ def measure(torch, sk, h, precision, args, world, dist):
     kern["stage_kernels"] = [sk.STAGE_KERNELS[k] for k in kern.pop("kernel_ids")]
     if tune:
         kern["autotune"] = tune
-    out = {"precision": precision, "value": world * zu / (ms * 1e-3), "ms": ms, "kern": kern,
+    out = {"precision": precision, "value": whole_job_value(zu, world, ms), "ms": ms, "kern": kern,
            "constraints_l0": norms,
            "bytes_per_zone_update": BYTES_PER_ZONE_UPDATE_MIXED if precision == "mixed" else BYTES_PER_ZONE_UPDATE}
     if not args.no_e2e:
         out["e2e"] = end_to_end(torch, sk, h, prm, args, world, dist)
     return out
+
+
+def zsym_case(torch, sk, args):
+    """The 7-level binary with equatorial reflection symmetry (Sec. 2.2.2):
+    the z >= 0 half of every patch is evolved (38.9 M zone updates per coarse
+    step instead of 77.8 M).  Reports zone-updates/s of the half domain and
+    the full-domain equivalent (the physical domain covered per second), both
+    precisions."""
+    import initial_data as idd
+    h = idd.upper_half_hierarchy(hierarchy())
+    zu = h.zone_updates_per_coarse_step()
+    out = {"case": "amr7-zsym", "zone_updates_per_step": zu, "courant": args.courant, "runs": {}}
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(courant=args.courant, precision=prec, zsym=1),
+                    stream=torch.cuda.Stream())
+        g.set_initial_data(1, h.masses, h.positions)
+        if prec:
+            g.autotune(reps=3)
+        steps = args.steps if prec else max(1, args.steps // 2)
+        for _ in range(args.warmup):
+            g.level_step(0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(g.stream)
+        for _ in range(steps):
+            g.level_step(0)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out["runs"][name] = {"ms_per_step": ms, "zone_updates_per_s": zu / (ms * 1e-3),
+                             "full_domain_equivalent_per_s": 2 * zu / (ms * 1e-3),
+                             "constraints_l0": list(map(float, g.constraints(0)))}
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
 
 
 def _gw_grid(torch, sk, n, precision, **prm):
@@ -631,7 +689,8 @@ def stage_kernel_timing(g, steps):
         import paper_2607_08743_gb300 as sk
         kn = {0: "z4c_stage_mixed_kernel"}
         kn.update({k: "z4c_stage_tma_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (1, 2, 3, 4)})
-        kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6)})
+        kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6, 8, 9, 10, 11)})
+        kn[7] = "z4c_deriv_kernel + z4c_algebra_kernel"
         names = sorted({kn[k] for k in ids})
         name = " + ".join(names)
     return {"name": name, "kernel_ids": ids,
@@ -676,13 +735,10 @@ def end_to_end(torch, sk, h, prm, args, world, dist):
         step()
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     g.close()
     zu = h.zone_updates_per_coarse_step()
-    return {"value": world * zu / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+    return {"value": whole_job_value(zu, world, ms), "unit": UNIT, "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes, "ms_per_step": ms}
 
 

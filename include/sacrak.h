@@ -71,6 +71,11 @@ typedef struct {
   int bc;                /* coarsest level ghosts: 0 Sommerfeld, 1 periodic, 2 frozen */
   int precision;         /* 0: FP64, 1: mixed (FP32 stencils/sources, FP64 state) */
   int lapse_uses_khat;   /* 0: 1+log source uses K = Khat + 2 Theta, 1: Khat */
+  int zsym;              /* 1: equatorial reflection symmetry (Sec. 2.2.2): only z >= 0 is
+                            evolved; patches whose lower z face is z = 0 get their z < 0
+                            ghosts by reflection (f(-z) = s_z f(z), s_z = -1 for fields with
+                            an odd number of z indices) after every other ghost treatment;
+                            not with bc = 1 */
 } sacrak_params;
 
 /* One patch: refinement level, active cells per axis, lower face of active
@@ -78,7 +83,9 @@ typedef struct {
  * inside one patch of level l-1 with its faces on that parent's cell faces
  * and at least 4 parent cells between its active region and the parent's
  * active edge (the 6-point prolongation stencils of its ghosts then read
- * parent active cells only); n must be even on levels > 0. */
+ * parent active cells only); n must be even on levels > 0.  With zsym, a
+ * patch and its parent may both start at z = 0 (the margin below is then the
+ * parent's reflected ghosts). */
 typedef struct {
   int level;
   int n[3];
@@ -100,7 +107,7 @@ size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* pa
  * least sacrak_arena_bytes(...) bytes of device memory, 256-byte aligned.
  * cuda_stream is a cudaStream_t (NULL = legacy default stream). Fields start
  * as Minkowski.  With the Sommerfeld boundary (bc = 0) every level-0 patch must
- * contain the coordinate origin. */
+ * contain the coordinate origin (with zsym: on its lower z face). */
 sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
                                  const sacrak_patch_desc* patches, const sacrak_params* params,
                                  void* cuda_stream, void* device_arena, size_t arena_bytes,
@@ -194,10 +201,13 @@ sacrak_status sacrak_constraints_noalloc(const double* dev_u, const int n[3], do
  * 3 CTAs per SM; kernel 6 also prefetches the next field's stencil rows
  * into L1 and the RK update's streaming reads into L2; kernel 7 splits the
  * stage into two launches, the derivatives (five fields per thread) into FP32
- * planes in the arena and then the algebra and RK4 update.  All kernels compute the same RHS up to FP32
+ * planes in the arena and then the algebra and RK4 update; kernel 8 is
+ * kernel 6 with 4 CTAs per SM (128 registers), kernels 9, 10 and 11 are
+ * kernel 6 prefetching only the star rows, only the z-arm rows, and only the
+ * RK update's streaming reads.  All kernels compute the same RHS up to FP32
  * rounding order.  A TMA kernel needs at most 8 patches on the level and at
  * least 32 x TY x TZ active cells per patch, else SACRAK_EINVAL.  New grids
- * use kernel 6 in mixed precision and 0 in FP64.  Changing the kernel of a
+ * use kernel 10 in mixed precision and 0 in FP64.  Changing the kernel of a
  * level drops the recorded CUDA graph of the coarse step (it is recorded
  * again at the next sacrak_level_step). */
 sacrak_status sacrak_set_stage_kernel(sacrak_grid* grid, int level, int kernel);
@@ -208,9 +218,10 @@ sacrak_status sacrak_get_stage_kernel(sacrak_grid* grid, int level, int* kernel)
  * first stage buffer, so the state is unchanged) with every kernel usable on
  * that level, `reps` launches each after one warm-up launch (CUDA events on
  * the grid's stream), and selects the fastest.  Results are cached for the
- * process, keyed by device, precision and the level's patch shapes; with
- * use_cache != 0 a cached level is not timed again.  us_per_launch, if not
- * NULL, receives nlevels x 8 timings in microseconds (kernel 0..7 of each
+ * process, keyed by device, precision and the level's patch shapes (levels
+ * of identical shapes share one timing and one choice); with use_cache != 0
+ * a cached level is not timed again.  us_per_launch, if not
+ * NULL, receives nlevels x 12 timings in microseconds (kernel 0..11 of each
  * level; -1 where not timed).  Synchronises the stream; must not be called
  * while the stream is being captured (SACRAK_ESTATE). */
 sacrak_status sacrak_autotune(sacrak_grid* grid, int reps, int use_cache, double* us_per_launch);

@@ -41,6 +41,11 @@ PI_PARITY = np.array([
     1, 1, 1, -1, 1, -1, 1, 1, 1, 1, 1, -1, 1, -1, 1, -1, -1, 1, 1, -1, -1, 1, -1, -1, 1,
 ], dtype=np.float64)
 
+# sign of each field under reflection z -> -z (odd number of z indices: -1)
+Z_PARITY = np.array([
+    1, 1, 1, -1, 1, -1, 1, 1, 1, 1, 1, -1, 1, -1, 1, 1, 1, -1, 1, 1, 1, -1, 1, 1, -1,
+], dtype=np.float64)
+
 GHOST = 3
 
 
@@ -276,6 +281,34 @@ def level_origin(h: Hierarchy, level: int):
     """Origin used for level-global cell indices: the coarsest patch's origin
     refined to this level (every patch of the level is aligned with it)."""
     return tuple(h.levels[0][0].origin)
+
+
+def symmetrise_z(p: Patch, u: np.ndarray) -> np.ndarray:
+    """Make data on a patch centred on z = 0 exactly symmetric under z -> -z:
+    every point with z < 0 takes Z_PARITY times its mirror's value."""
+    nz = u.shape[1]
+    assert nz % 2 == 0 and abs(p.origin[2] + 0.5 * p.n[2] * p.dx) < 1e-12 * p.dx
+    v = np.array(u, copy=True)
+    v[:, : nz // 2] = Z_PARITY[:, None, None, None] * v[:, nz // 2:][:, ::-1]
+    return v
+
+
+def upper_half(p: Patch) -> Patch:
+    """The z >= 0 half of a patch centred on z = 0."""
+    assert p.n[2] % 2 == 0 and abs(p.origin[2] + 0.5 * p.n[2] * p.dx) < 1e-12 * p.dx
+    return Patch(n=(p.n[0], p.n[1], p.n[2] // 2), dx=p.dx, origin=(p.origin[0], p.origin[1], 0.0),
+                 level=p.level, g=p.g)
+
+
+def upper_half_array(p: Patch, u: np.ndarray) -> np.ndarray:
+    """The array of upper_half(p) (ghosts included) cut from the full one."""
+    nz = p.n[2]
+    return np.ascontiguousarray(u[:, nz // 2: nz // 2 + nz // 2 + 2 * p.g])
+
+
+def upper_half_hierarchy(h: Hierarchy) -> Hierarchy:
+    return Hierarchy(dx0=h.dx0, levels=[[upper_half(p) for p in lv] for lv in h.levels],
+                     masses=h.masses, positions=h.positions)
 
 
 def hierarchy_data(h: Hierarchy, noise: float = 0.0, seed: int = PUNCTURE_SEED) -> List[np.ndarray]:

@@ -54,6 +54,7 @@ class _OrcParams(ctypes.Structure):
 
 
 BC_SOMMERFELD, BC_PERIODIC, BC_FROZEN = 0, 1, 2
+BC_ZREFLECT = 8  # or-ed into bc: equatorial reflection symmetry at z = 0 (Sec. 2.2.2)
 
 
 @dataclasses.dataclass
@@ -85,6 +86,9 @@ def lib():
             L.orc_z4c_rhs_terms.argtypes = [P(_OrcPatch), P(_OrcParams), dp, dp, ctypes.c_int]
             L.orc_sommerfeld_rhs.argtypes = [P(_OrcPatch), dp, dp]
             L.orc_fill_periodic.argtypes = [P(_OrcPatch), dp]
+            L.orc_fill_zreflect.argtypes = [P(_OrcPatch), dp]
+            L.orc_fill_zreflect.restype = ctypes.c_int
+            L.orc_prolong_ghosts_ex.argtypes = [P(_OrcPatch), dp, P(_OrcPatch), dp, ctypes.c_int]
             L.orc_enforce.argtypes = [P(_OrcPatch), ctypes.c_double, ctypes.c_int, dp]
             L.orc_rk4_step.argtypes = [P(_OrcPatch), P(_OrcParams), ctypes.c_int, ctypes.c_double, dp]
             L.orc_rk4_stage.argtypes = [P(_OrcPatch), P(_OrcParams), ctypes.c_int, ctypes.c_double,
@@ -140,6 +144,20 @@ def fill_periodic(p, u: np.ndarray) -> np.ndarray:
     return u
 
 
+def fill_zreflect(p, u: np.ndarray) -> np.ndarray:
+    """Equatorial reflection (Sec. 2.2.2): the z < 0 ghost layers mirror z > 0
+    with the sign of each field's z parity.  The patch's lower z face must be
+    z = 0."""
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    if lib().orc_fill_zreflect(ctypes.byref(_cp(p)), _ptr(u)) != 0:
+        raise ValueError("patch does not start at z = 0")
+    return u
+
+
+def touches_equator(p) -> bool:
+    return abs(p.origin[2]) <= 1e-12 * p.dx
+
+
 def enforce(p, u: np.ndarray, w_floor: float = 1e-10, all_points: bool = False) -> np.ndarray:
     u = np.array(u, dtype=np.float64, order="C", copy=True)
     lib().orc_enforce(ctypes.byref(_cp(p)), w_floor, int(all_points), _ptr(u))
@@ -171,10 +189,13 @@ def pi_symmetry(p, u: np.ndarray, include_ghosts: bool = True) -> float:
     return lib().orc_pi_symmetry(ctypes.byref(_cp(p)), _ptr(u), int(include_ghosts))
 
 
-def prolong_ghosts(parent, up: np.ndarray, child, uc: np.ndarray) -> np.ndarray:
+def prolong_ghosts(parent, up: np.ndarray, child, uc: np.ndarray, skip_zlower: bool = False) -> np.ndarray:
+    """Ghosts of the child from the parent (skip_zlower: not the z < 0
+    layers, which the equatorial reflection fills)."""
     up = np.ascontiguousarray(up, dtype=np.float64)
     uc = np.array(uc, dtype=np.float64, order="C", copy=True)
-    rc = lib().orc_prolong_ghosts(ctypes.byref(_cp(parent)), _ptr(up), ctypes.byref(_cp(child)), _ptr(uc))
+    rc = lib().orc_prolong_ghosts_ex(ctypes.byref(_cp(parent)), _ptr(up), ctypes.byref(_cp(child)), _ptr(uc),
+                                     int(skip_zlower))
     if rc != 0:
         raise ValueError("prolongation stencil leaves the parent patch or patches misaligned")
     return uc
@@ -236,15 +257,18 @@ class BOHierarchy:
     then, for level l+1: ghosts prolonged at the parent's new time from the
     unrestricted parent, exchange, and restriction of every child onto l.
     Level 0's ghosts follow the Sommerfeld condition and are evolved with the
-    stage.
+    stage.  With zsym (equatorial reflection symmetry, Sec. 2.2.2) only z >= 0
+    is evolved: the z < 0 ghosts of every patch whose lower face is z = 0 are
+    filled by reflection after the other ghost treatments of every stage.
     """
 
     def __init__(self, hierarchy, states: List[np.ndarray], prm: Params, courant: float = 0.5,
-                 bc0: int = BC_SOMMERFELD, previous: Optional[List[np.ndarray]] = None):
+                 bc0: int = BC_SOMMERFELD, previous: Optional[List[np.ndarray]] = None, zsym: bool = False):
         self.h = hierarchy
         self.prm = prm
         self.courant = courant
         self.bc0 = bc0
+        self.zsym = zsym
         self.patches = [p for lv in hierarchy.levels for p in lv]
         idx = 0
         self.level_ids = []
@@ -266,8 +290,8 @@ class BOHierarchy:
         c = self.patches[pid]
         for qid in self.level_ids[l - 1]:
             q = self.patches[qid]
-            inside = all(q.origin[d] <= c.origin[d] and
-                         c.origin[d] + c.n[d] * c.dx <= q.origin[d] + q.n[d] * q.dx for d in range(3))
+            inside = all(q.origin[d] <= c.origin[d] + 1e-12 and
+                         c.origin[d] + c.n[d] * c.dx <= q.origin[d] + q.n[d] * q.dx + 1e-12 for d in range(3))
             if inside:
                 return qid
         raise ValueError("patch %d has no parent" % pid)
@@ -289,7 +313,14 @@ class BOHierarchy:
         up = np.zeros_like(src[0])
         for wi, si in zip(ws, src):
             up = up + wi * si
-        return prolong_ghosts(self.patches[ppid], up, self.patches[pid], u)
+        skip = self.zsym and touches_equator(self.patches[pid])
+        return prolong_ghosts(self.patches[ppid], up, self.patches[pid], u, skip_zlower=skip)
+
+    def _reflect(self, ids, arrays):
+        if not self.zsym:
+            return arrays
+        return [fill_zreflect(self.patches[pid], a) if touches_equator(self.patches[pid]) else a
+                for pid, a in zip(ids, arrays)]
 
     def _exchange_level(self, l, arrays):
         ids = self.level_ids[l]
@@ -315,12 +346,16 @@ class BOHierarchy:
                     cur[a] = self._fill_child_ghosts(pid, cur[a], frac0 + stage_frac[s - 1] * dfrac)
                 if len(ids) > 1:
                     self._exchange_level(l, cur)
-                if s == 1:  # the stage-1 state, ghosts filled, is the step's u_n
-                    un = [c.copy() for c in cur]
+            cur = self._reflect(ids, cur)
+            if s == 1:  # the stage-1 state, ghosts filled, is the step's u_n
+                un = [c.copy() for c in cur]
             out = [np.empty_like(a) for a in un]
             for a, pid in enumerate(ids):
                 rk4_stage(self.patches[pid], self.prm, s, dt, evolve_ghosts, cur[a], un[a], y[a], out[a])
             cur = out
+        # the new level's z < 0 ghosts mirror its own new values: the
+        # children's prolongation reads those parent cells
+        cur = self._reflect(ids, cur)
         for a, pid in enumerate(ids):
             if l == 0 and self.bc0 == BC_PERIODIC:
                 cur[a] = fill_periodic(self.patches[pid], cur[a])
@@ -342,7 +377,16 @@ class BOHierarchy:
             if len(kids) > 1:
                 cur = [self.tl[pid][-1] for pid in kids]
                 self._exchange_level(l + 1, cur)
+            if self.zsym:
+                cur = self._reflect(kids, [self.tl[pid][-1] for pid in kids])
+                for pid, c in zip(kids, cur):
+                    self.tl[pid][-1] = c
             for pid in kids:
                 ppid = self.parent[pid]
                 self.tl[ppid][-1] = restrict(self.patches[ppid], self.tl[ppid][-1],
                                              self.patches[pid], self.tl[pid][-1])
+            if self.zsym:  # the restricted cells next to z = 0 have mirrors among the ghosts
+                ids = self.level_ids[l]
+                cur = self._reflect(ids, [self.tl[pid][-1] for pid in ids])
+                for pid, c in zip(ids, cur):
+                    self.tl[pid][-1] = c

@@ -556,6 +556,27 @@ void orc_fill_periodic(const orc_patch* p, double* u) {
         }
 }
 
+/* Equatorial reflection symmetry (Sec. 2.2.2): only z >= 0 is evolved; a
+ * field with an odd number of z indices changes sign under z -> -z. */
+static int zparity(int f) {
+  return (f == F_GXZ || f == F_GYZ || f == F_AXZ || f == F_AYZ || f == F_GAMZ || f == F_BETZ || f == F_BZ)
+             ? -1
+             : 1;
+}
+
+int orc_fill_zreflect(const orc_patch* p, double* u) {
+  if (fabs(p->origin[2]) > 1e-12 * p->dx) return -1;
+  layout L = make_layout(p);
+  const int g = p->g;
+  for (int f = 0; f < NF; ++f)
+    for (int k = 0; k < g; ++k) /* ghost layer z-index k - g < 0 mirrors 2g - 1 - k */
+      for (int j = 0; j < L.NY; ++j)
+        for (int i = 0; i < L.NX; ++i)
+          u[f * L.sf + i + j * L.s[1] + k * L.s[2]] =
+              zparity(f) * u[f * L.sf + i + j * L.s[1] + (2 * g - 1 - k) * L.s[2]];
+  return 0;
+}
+
 /* ---------------- algebraic constraints ---------------- */
 
 static void enforce_point(double* u, ptrdiff_t sf, ptrdiff_t q, double w_floor) {
@@ -642,6 +663,9 @@ void orc_rk4_step(const orc_patch* p, const orc_params* prm, int bc, double dt, 
   double* y = (double*)malloc(sizeof(double) * np);
   double* a = (double*)malloc(sizeof(double) * np);
   double* b = (double*)malloc(sizeof(double) * np);
+  const int zsym = (bc & ORC_BC_ZREFLECT) != 0;
+  bc &= ~ORC_BC_ZREFLECT;
+  if (zsym) orc_fill_zreflect(p, u);
   memcpy(un, u, sizeof(double) * np);
   int eg = (bc == ORC_BC_SOMMERFELD);
   const double* cur = un;
@@ -649,10 +673,12 @@ void orc_rk4_step(const orc_patch* p, const orc_params* prm, int bc, double dt, 
   for (int s = 1; s <= 4; ++s) {
     double* out = (s == 4) ? u : bufs[(s - 1) % 2];
     if (bc == ORC_BC_PERIODIC) orc_fill_periodic(p, (double*)cur);
+    if (zsym) orc_fill_zreflect(p, (double*)cur);
     orc_rk4_stage(p, prm, s, dt, eg, cur, un, y, out);
     cur = out;
   }
   if (bc == ORC_BC_PERIODIC) orc_fill_periodic(p, u);
+  if (zsym) orc_fill_zreflect(p, u);
   free(un);
   free(y);
   free(a);
@@ -767,6 +793,11 @@ static int floor_div2(int i) { return i >= 0 ? i / 2 : -((-i + 1) / 2); }
 
 int orc_prolong_ghosts(const orc_patch* parent, const double* up, const orc_patch* child,
                        double* uc) {
+  return orc_prolong_ghosts_ex(parent, up, child, uc, 0);
+}
+
+int orc_prolong_ghosts_ex(const orc_patch* parent, const double* up, const orc_patch* child,
+                          double* uc, int skip_zlower) {
   int off[3];
   if (child_offset(parent, child, off)) return -1;
   layout Lp = make_layout(parent), Lc = make_layout(child);
@@ -781,7 +812,7 @@ int orc_prolong_ghosts(const orc_patch* parent, const double* up, const orc_patc
   int cdim[3] = {Lc.NX, Lc.NY, Lc.NZ};
   /* check that every stencil stays inside the parent array */
   for (int d = 0; d < 3; ++d)
-    for (int ic = -gc; ic < child->n[d] + gc; ++ic) {
+    for (int ic = (d == 2 && skip_zlower) ? 0 : -gc; ic < child->n[d] + gc; ++ic) {
       int P = off[d] + floor_div2(ic);
       int lo = (ic & 1) ? P - 2 : P - 3, hi = (ic & 1) ? P + 3 : P + 2;
       if (lo + gp < 0 || hi + gp >= pdim[d]) return -1;
@@ -790,6 +821,7 @@ int orc_prolong_ghosts(const orc_patch* parent, const double* up, const orc_patc
     for (int jc = 0; jc < cdim[1]; ++jc)
       for (int ic = 0; ic < cdim[0]; ++ic) {
         if (!is_ghost(child, ic, jc, kc)) continue;
+        if (skip_zlower && kc < gc) continue; /* left to the reflection */
         int ci[3] = {ic - gc, jc - gc, kc - gc};
         int base[3];
         const double* w[3];

@@ -18,6 +18,8 @@
  *   orc_sommerfeld_rhs  2nd-order convergence on an exact outgoing wave
  *   orc_rk4_step/stage  gauge wave (closed form in time) at 4th order
  *   orc_fill_periodic   brute force
+ *   orc_fill_zreflect   brute force; a z-symmetric full-domain evolution
+ *                       equals the half-domain one with reflection
  *   orc_enforce         det gt = 1 and gt^ij At_ij = 0 to rounding
  *   orc_pi_symmetry     symmetrised data 0, noisy data > 0; RHS and RK4 keep 0
  *   orc_prolong_ghosts  exact on degree <= 5, not on degree 6
@@ -63,8 +65,10 @@ typedef struct {
   int lapse_uses_khat;    /* 0: lapse source uses K = Khat + 2 Theta; 1: Khat */
 } orc_params;
 
-/* ghost treatment of a uniform patch */
-enum { ORC_BC_SOMMERFELD = 0, ORC_BC_PERIODIC = 1, ORC_BC_FROZEN = 2, ORC_BC_NONE = 3 };
+/* ghost treatment of a uniform patch; ORC_BC_ZREFLECT may be or-ed in:
+ * equatorial reflection symmetry at z = 0 (Sec. 2.2.2) for a patch whose
+ * lower z face is z = 0 -- its z < 0 ghosts mirror z > 0 before every stage */
+enum { ORC_BC_SOMMERFELD = 0, ORC_BC_PERIODIC = 1, ORC_BC_FROZEN = 2, ORC_BC_NONE = 3, ORC_BC_ZREFLECT = 8 };
 
 size_t orc_patch_points(const orc_patch* p);
 
@@ -81,6 +85,12 @@ void orc_sommerfeld_rhs(const orc_patch* p, const double* u, double* rhs);
 
 /* periodic ghost fill */
 void orc_fill_periodic(const orc_patch* p, double* u);
+
+/* equatorial reflection: the z < 0 ghost layers (all x, y) take the mirror
+ * value f(x, y, -z) = s_z f(x, y, z), s_z = -1 for fields with an odd number
+ * of z indices (gt_xz, gt_yz, At_xz, At_yz, Gamt^z, beta^z, B^z).  The patch's
+ * lower z face must be z = 0 (else -1). */
+int orc_fill_zreflect(const orc_patch* p, double* u);
 
 /* algebraic constraints: det gt = 1, At trace-free, W >= w_floor; at active
  * points (all points when all_points != 0) */
@@ -116,6 +126,11 @@ double orc_pi_symmetry(const orc_patch* p, const double* u, int include_ghosts);
  * the parent array or the patches are not aligned. */
 int orc_prolong_ghosts(const orc_patch* parent, const double* up, const orc_patch* child,
                        double* uc);
+/* Same; with skip_zlower the child's z < 0 ghost layers are left alone (they
+ * come from the equatorial reflection) and the parent is only read at z >= -3
+ * cells. */
+int orc_prolong_ghosts_ex(const orc_patch* parent, const double* up, const orc_patch* child,
+                          double* uc, int skip_zlower);
 
 /* 4th-order Lagrange restriction of the child onto every parent cell covered
  * by the child's active region (child ghosts must be valid). */

@@ -34,9 +34,13 @@ EXPORTS = [
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
 # 5..6 L1 path with packed pair arithmetic (without / with prefetching),
-# 7 split into a derivative and an algebra launch
+# 7 split into a derivative and an algebra launch, 8 as 6 with 4 CTAs per SM,
+# 9 as 6 prefetching the star rows only, 10 only the z-arm rows, 11 only the
+# RK update's streaming reads
 STAGE_KERNELS = {0: "direct", 1: "tma 32x4x1", 2: "tma 32x2x2", 3: "tma 32x4x2", 4: "tma 32x8x1",
-                 5: "l1 pairs", 6: "l1 pairs + prefetch", 7: "split deriv + algebra"}
+                 5: "l1 pairs", 6: "l1 pairs + prefetch", 7: "split deriv + algebra",
+                 8: "l1 pairs + prefetch, 4/SM", 9: "l1 pairs + star prefetch",
+                 10: "l1 pairs + z-arm prefetch", 11: "l1 pairs + epilogue prefetch"}
 
 
 class SacrakError(RuntimeError):
@@ -49,7 +53,7 @@ class sacrak_params(ctypes.Structure):
     _fields_ = [("kappa1", ctypes.c_double), ("kappa2", ctypes.c_double), ("eta", ctypes.c_double),
                 ("sigma_ko", ctypes.c_double), ("courant", ctypes.c_double), ("w_floor", ctypes.c_double),
                 ("lapse", ctypes.c_int), ("shift", ctypes.c_int), ("bc", ctypes.c_int),
-                ("precision", ctypes.c_int), ("lapse_uses_khat", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("lapse_uses_khat", ctypes.c_int), ("zsym", ctypes.c_int)]
 
 
 class sacrak_patch_desc(ctypes.Structure):
@@ -118,10 +122,12 @@ class Params:
     bc: int = 0            # 0 Sommerfeld, 1 periodic, 2 frozen
     precision: int = 0     # 0 FP64, 1 mixed
     lapse_uses_khat: int = 0
+    zsym: int = 0          # 1: equatorial reflection symmetry, only z >= 0 evolved
 
     def c(self) -> sacrak_params:
         return sacrak_params(self.kappa1, self.kappa2, self.eta, self.sigma_ko, self.courant, self.w_floor,
-                             self.lapse, self.shift, self.bc, self.precision, self.lapse_uses_khat)
+                             self.lapse, self.shift, self.bc, self.precision, self.lapse_uses_khat,
+                             self.zsym)
 
 
 def _descs(patches) -> ctypes.Array:
@@ -292,7 +298,7 @@ class Grid:
 
     def autotune(self, reps: int = 3, use_cache: bool = True) -> np.ndarray:
         """Time every usable stage kernel on every level and keep the fastest;
-        returns the timings (nlevels x 8, microseconds per launch, -1 = not
+        returns the timings (nlevels x 12, microseconds per launch, -1 = not
         timed) and leaves the choice in place."""
         out = np.full((self.nlevels, len(STAGE_KERNELS)), -1.0)
         self._check(lib().sacrak_autotune(self._h, reps, int(use_cache),

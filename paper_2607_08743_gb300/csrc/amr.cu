@@ -245,7 +245,11 @@ __global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A
       const int c = lo[2] - 3 + z;
       T v;
       p_zero(v);
-      if (inxy && c >= -2 && c <= m[2] + 1) {
+      // (with equatorial symmetry a child on z = 0 has no parent margin
+      // below: parent cells outside the parent array are staged as 0; they
+      // only reach children at z < 0, which the reflection overwrites)
+      const int pk = C->off[2] - 2 + c + GH;
+      if (inxy && c >= -2 && c <= m[2] + 1 && pk >= 0 && pk < P->NZ) {
         if (MIXED)
           v = *reinterpret_cast<const T*>(P->hl[slot] + fo + pq(a, bb, c));
         else
@@ -507,6 +511,56 @@ __global__ void exchange_kernel(ExchArgs E) {
       split_to(*pb, Pb->hl[slot], ob);
     }
   }
+}
+
+// Equatorial reflection symmetry (Sec. 2.2.2): the z < 0 ghost layers of a
+// patch whose lower z face is z = 0 take f(x, y, -z) = s_z f(x, y, z);
+// s_z = -1 for the fields with an odd number of z indices.  Ghost layer k
+// (array index) mirrors active layer 2 GH - 1 - k, over the whole x-y extent.
+__device__ __forceinline__ int zparity(int f) {
+  const unsigned odd = (1u << F_GXZ) | (1u << F_GYZ) | (1u << F_AXZ) | (1u << F_AYZ) | (1u << F_GAMZ) |
+                       (1u << F_BETZ) | (1u << F_BZ);
+  return (odd >> f) & 1u ? -1 : 1;
+}
+
+__global__ void zreflect_kernel(FillArgs A) {
+  const DevPatch* P = A.patches + A.patch_ids[blockIdx.y];
+  if (!P->zrefl) return;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long slab = (long long)GH * P->NY * P->NX;
+  if (id >= slab) return;
+  const int i = (int)(id % P->NX);
+  const int j = (int)((id / P->NX) % P->NY);
+  const int k = (int)(id / ((long long)P->NX * P->NY));
+  const int ring = A.lev->ring;
+  const long long q = i + (long long)j * P->px + (long long)k * P->plane;
+  const long long qm = i + (long long)j * P->px + (long long)(2 * GH - 1 - k) * P->plane;
+  const long long fs = P->fstride;
+  if (A.mixed && A.mode == 0 && A.stage > 1) {
+    float2* in = mixed_in(P, A.stage, ring);  // the split stage state (hi, lo): both change sign
+    for (int f = 0; f < NF; ++f) {
+      const float2 v = in[f * fs + qm];
+      const float sg = (float)zparity(f);
+      in[f * fs + q] = make_float2(sg * v.x, sg * v.y);
+    }
+    return;
+  }
+  const int slot = fill_slot(A.mode, A.stage, ring);
+  double* u = P->buf[slot];
+  for (int f = 0; f < NF; ++f) u[f * fs + q] = zparity(f) * u[f * fs + qm];
+  if (A.mixed && slot < 3) {  // a time level: its split as well
+    float2* hl = P->hl[slot];
+    for (int f = 0; f < NF; ++f) {
+      const float2 v = hl[f * fs + qm];
+      const float sg = (float)zparity(f);
+      hl[f * fs + q] = make_float2(sg * v.x, sg * v.y);
+    }
+  }
+}
+
+void launch_zreflect(const FillArgs& a, int npatches, long long maxpts, cudaStream_t st) {
+  if (npatches == 0 || maxpts == 0) return;
+  zreflect_kernel<<<dim3((unsigned)((maxpts + 127) / 128), npatches), 128, 0, st>>>(a);
 }
 
 // Copy between a patch buffer (rows of px doubles) and a contiguous patch

@@ -125,6 +125,7 @@ struct sacrak_grid {
   std::vector<int> lvl_id_off;             // offset of each level's ids in the device id array
   std::vector<size_t> lvl_tile_off, lvl_ntiles;
   std::vector<long long> lvl_max_shell, lvl_max_restrict, lvl_max_clusters;  // clusters: prolongation bricks
+  std::vector<long long> lvl_max_zslab;  // points of the z < 0 ghost slab
   bool shells_dirty = true;
   bool split_dirty = true;  // mixed precision: hi/lo of the current levels stale
   DevPatch* d_patches;
@@ -249,12 +250,19 @@ bool tma_eligible(const sacrak_grid* g, int v, const std::vector<int>& pids) {
 // kernel ids: 0 direct, 1..TMA_NVARIANTS TMA variant id-1, then the two
 // L1-path kernels with packed pair arithmetic (without and with prefetching)
 constexpr int K_LDG3 = TMA_NVARIANTS + 1, K_LDG4 = TMA_NVARIANTS + 2, K_SPLIT = TMA_NVARIANTS + 3,
-              K_COUNT = TMA_NVARIANTS + 4;
+              K_LDG_PF4 = TMA_NVARIANTS + 4, K_LDG_PFS = TMA_NVARIANTS + 5, K_LDG_PFZ = TMA_NVARIANTS + 6,
+              K_LDG_PFE = TMA_NVARIANTS + 7, K_COUNT = TMA_NVARIANTS + 8;
+
+// L1-path variant of a kernel id (-1 for others)
+int ldg_variant(int k) {
+  return k == K_LDG3 ? 0 : k == K_LDG4 ? 1 : k == K_LDG_PF4 ? 2 : k == K_LDG_PFS ? 3 : k == K_LDG_PFZ ? 4
+         : k == K_LDG_PFE ? 5 : -1;
+}
 
 bool kernel_eligible(const sacrak_grid* g, int k, const std::vector<int>& pids) {
   if (k == 0) return true;
   if (k >= 1 && k <= TMA_NVARIANTS) return tma_eligible(g, k - 1, pids);
-  return (k == K_LDG3 || k == K_LDG4 || k == K_SPLIT) && g->prm.precision == 1;
+  return (ldg_variant(k) >= 0 || k == K_SPLIT) && g->prm.precision == 1;
 }
 
 // tensor maps of variant v for every patch: the five split buffers viewed as
@@ -332,8 +340,8 @@ void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones, const std
     const long long res = (long long)g->nsm * g->tma_blocks[v];
     const int grid = (int)(acc < res ? acc : res);
     if (grid > 0) launch_stage_tma(v, t, grid, g->stream);
-  } else if (g->prm.precision == 1 && (kernel == K_LDG3 || kernel == K_LDG4)) {
-    launch_stage_ldg(kernel == K_LDG4 ? 1 : 0, a, g->stream);
+  } else if (g->prm.precision == 1 && ldg_variant(kernel) >= 0) {
+    launch_stage_ldg(ldg_variant(kernel), a, g->stream);
   } else if (g->prm.precision == 1 && kernel == K_SPLIT) {
     launch_stage_split(a, g->d_dslot, g->stream);
   } else if (g->prm.precision == 1) {
@@ -356,13 +364,14 @@ sacrak_status select_kernel(sacrak_grid* g, int l, int kernel) {
     sacrak_status st = ensure_maps(g, kernel - 1);
     if (st != SACRAK_OK) return st;
   }
-  if (kernel == K_LDG3 || kernel == K_LDG4) {
-    static bool done[64][2] = {};  // shared-memory opt-in, once per device
+  if (ldg_variant(kernel) >= 0) {
+    static bool done[64][6] = {};  // shared-memory opt-in, once per device
+    const int v = ldg_variant(kernel);
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !done[dev][kernel - K_LDG3]) {
-      if (!ldg_setup(kernel == K_LDG4 ? 1 : 0)) return fail(g, SACRAK_ECUDA, "stage kernel %d setup failed", kernel);
-      if (dev >= 0 && dev < 64) done[dev][kernel - K_LDG3] = true;
+    if (dev < 0 || dev >= 64 || !done[dev][v]) {
+      if (!ldg_setup(v)) return fail(g, SACRAK_ECUDA, "stage kernel %d setup failed", kernel);
+      if (dev >= 0 && dev < 64) done[dev][v] = true;
     }
   }
   if (g->lvl_kernel[l] != kernel && g->graph_exec) {  // the captured coarse step used the old kernel
@@ -453,6 +462,12 @@ void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double d
     }
 }
 
+// equatorial reflection of the level's z < 0 ghosts in the (mode, stage) buffer
+void zreflect(sacrak_grid* g, int l, int mode, int stage) {
+  if (!g->prm.zsym) return;
+  launch_zreflect(fill_args(g, l, mode, stage, 0.0), (int)g->lvl_ids[l].size(), g->lvl_max_zslab[l], g->stream);
+}
+
 // spatial prolongation of level l-1's current slot onto level l's shells
 void refresh_shells(sacrak_grid* g, int l) {
   if (l <= 0 || l >= g->nlevels) return;
@@ -464,6 +479,8 @@ void refresh_shells(sacrak_grid* g, int l) {
 // after new data: every child level's cache for its parent's current slot,
 // and (mixed precision) the hi/lo split of every current level
 void refresh_all_shells(sacrak_grid* g) {
+  if (g->prm.zsym && (g->split_dirty || g->shells_dirty))  // new data: mirror it first
+    for (int l = 0; l < g->nlevels; ++l) zreflect(g, l, 1, 0);
   if (g->prm.precision == 1 && g->split_dirty) {
     for (int p = 0; p < g->npatches; ++p) {
       const DevPatch& P = g->hp[p];
@@ -481,6 +498,7 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
   for (int s = 1; s <= 4; ++s) {
     if (!(l == 0 && (g->prm.bc == 0 || (g->prm.bc == 2 && s == 1))))
       fill_ghosts(g, l, 0, s, frac0, dfrac, l > 0 ? (s == 2 ? 2 : (s == 3 ? 0 : 1)) : 1);
+    zreflect(g, l, 0, s);  // equatorial symmetry: after every other ghost treatment
     StageArgs a;
     a.tiles = g->d_tiles + g->lvl_tile_off[l];
     a.ntiles = (int)g->lvl_ntiles[l];
@@ -511,6 +529,9 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
     launch_fill(FILL_PERIODIC, fill_args(g, l, 2, 4, 0.0), np, g->lvl_max_shell[l], g->stream);
   if (l == 0 && g->prm.bc == 2)
     launch_fill(FILL_FROZEN, fill_args(g, l, 2, 4, 0.0), np, g->lvl_max_shell[l], g->stream);
+  // the new level's z < 0 ghosts mirror its new values (the children's
+  // prolongation reads those parent cells)
+  zreflect(g, l, 2, 4);
   launch_level_advance(g->d_levels + l, dt, g->stream);
   refresh_shells(g, l + 1);  // the children's cache of this level's new slot
 }
@@ -522,8 +543,10 @@ void level_step_rec(sacrak_grid* g, int l, double frac0, double dfrac) {
     level_step_rec(g, l + 1, 0.5, 0.5);
     const int nc = (int)g->lvl_ids[l + 1].size();
     fill_ghosts(g, l + 1, 1, 0, 1.0, 0.0);  // prolongation (unrestricted parent) + exchange
+    zreflect(g, l + 1, 1, 0);
     launch_fill(FILL_RESTRICT, fill_args(g, l + 1, 1, 0, 0.0), nc, g->lvl_max_restrict[l + 1],
                 g->stream);
+    zreflect(g, l, 1, 0);      // restricted cells next to z = 0 have mirrors among the ghosts
     refresh_shells(g, l + 1);  // the restricted slot, for the next parent step
   }
 }
@@ -575,7 +598,8 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   if (arena_bytes < L.total || ((uintptr_t)device_arena % 256) != 0) return SACRAK_EINVAL;
   const sacrak_params& p = *params;
   if (p.lapse < 0 || p.lapse > 1 || p.shift < 0 || p.shift > 1 || p.bc < 0 || p.bc > 2 ||
-      p.precision < 0 || p.precision > 1 || !(p.courant > 0.0) || !(p.sigma_ko >= 0.0))
+      p.precision < 0 || p.precision > 1 || !(p.courant > 0.0) || !(p.sigma_ko >= 0.0) || p.zsym < 0 ||
+      p.zsym > 1 || (p.zsym && p.bc == 1))
     return SACRAK_EINVAL;
 
   cudaPointerAttributes attr;
@@ -610,6 +634,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
     P.fstride = L.fstride[i];
     P.level = pd[i].level;
     P.dx = dx0 / std::ldexp(1.0, P.level);
+    P.zrefl = (p.zsym && std::fabs(P.origin[2]) <= 1e-12 * P.dx) ? 1 : 0;
     P.parent = -1;
     for (int b = 0; b < NBUF; ++b)
       P.buf[b] = (double*)(g->arena + L.patch_state[i] + (size_t)b * NF * P.fstride * sizeof(double));
@@ -645,8 +670,11 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
         double r = std::floor(t + 0.5);
         if (std::fabs(t - r) > 1e-9) ok = false;
         off[d] = (int)r;
-        // prolongation stencils need parent cells off-4 .. off+n/2+3 inside the active region
-        if (off[d] - 4 < 0 || off[d] + C.n[d] / 2 + 3 > P.n[d] - 1) ok = false;
+        // prolongation stencils need parent cells off-4 .. off+n/2+3 inside the
+        // active region; with equatorial symmetry a child and its parent may
+        // both start at z = 0 (the parent's reflected ghosts serve below)
+        const bool zlow = d == 2 && C.zrefl && P.zrefl && off[d] == 0;
+        if ((!zlow && off[d] - 4 < 0) || off[d] + C.n[d] / 2 + 3 > P.n[d] - 1) ok = false;
       }
       if (ok) {
         C.parent = j;
@@ -665,7 +693,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
     for (int i : g->lvl_ids[0])
       for (int d = 0; d < 3; ++d) {
         const DevPatch& P = g->hp[i];
-        if (!(P.origin[d] < 0.0 && P.origin[d] + P.n[d] * P.dx > 0.0)) {
+        if (!((P.origin[d] < 0.0 || (d == 2 && P.zrefl)) && P.origin[d] + P.n[d] * P.dx > 0.0)) {
           delete g;
           return SACRAK_EINVAL;
         }
@@ -687,6 +715,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   g->lvl_zones.assign(nlevels, 0);
   g->lvl_max_clusters.assign(nlevels, 0);
   g->lvl_max_restrict.assign(nlevels, 0);
+  g->lvl_max_zslab.assign(nlevels, 0);
   for (int l = 0; l < nlevels; ++l) {
     g->lvl_id_off[l] = (int)ids.size();
     g->lvl_tile_off[l] = tiles.size();
@@ -696,6 +725,8 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
       for (int z = 0; z < P.n[2]; ++z)
         for (int y = 0; y < P.n[1]; y += TILE_Y)
           for (int x = 0; x < P.n[0]; x += TILE_X) tiles.push_back(Tile{pid, x, y, z});
+      const long long zs = (long long)GH * P.NX * P.NY;
+      if (zs > g->lvl_max_zslab[l]) g->lvl_max_zslab[l] = zs;
       long long sh = (long long)P.NX * P.NY * P.NZ - (long long)P.n[0] * P.n[1] * P.n[2];
       if (sh > g->lvl_max_shell[l]) g->lvl_max_shell[l] = sh;
       g->lvl_zones[l] += (long long)P.n[0] * P.n[1] * P.n[2];
@@ -724,10 +755,11 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   }
   if (st == SACRAK_OK) st = sacrak_set_initial_data(g, 0, 0, nullptr, nullptr, 0, 1, 0, 0, 0);
   // default stage kernel (mixed precision): the L1-path kernel with packed
-  // pair arithmetic and prefetching (the fastest on 64^3 and 96^3 patches)
+  // pair arithmetic that prefetches the next field's z arms and the RK
+  // update's streaming reads (the fastest on 48^3 .. 192^3 patches)
   g->lvl_kernel.assign(nlevels, 0);
   for (int l = 0; st == SACRAK_OK && l < nlevels; ++l)
-    if (p.precision == 1) st = select_kernel(g, l, K_LDG4);
+    if (p.precision == 1) st = select_kernel(g, l, K_LDG_PFZ);
   if (st != SACRAK_OK) {
     cudaGetLastError();
     delete g;
@@ -1031,9 +1063,21 @@ sacrak_status sacrak_autotune(sacrak_grid* g, int reps, int use_cache, double* u
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   sacrak_status st = SACRAK_OK;
+  // levels of identical shape in this call share one timing (and so one
+  // choice, as the process-wide cache would give them)
+  std::map<std::vector<int>, std::pair<int, std::vector<double>>> now;
   for (int l = 0; l < g->nlevels && st == SACRAK_OK; ++l) {
     std::vector<int> key = {dev, g->prm.precision};
     for (int pid : g->lvl_ids[l]) key.insert(key.end(), g->hp[pid].n, g->hp[pid].n + 3);
+    {
+      auto it = now.find(key);
+      if (it != now.end()) {
+        if (us_out)
+          for (int k = 0; k < K_COUNT; ++k) us_out[l * K_COUNT + k] = it->second.second[k];
+        st = select_kernel(g, l, it->second.first);
+        continue;
+      }
+    }
     if (use_cache) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune_cache.find(key);
@@ -1084,6 +1128,12 @@ sacrak_status sacrak_autotune(sacrak_grid* g, int reps, int use_cache, double* u
       break;
     }
     st = select_kernel(g, l, best);
+    {
+      std::vector<double> row(K_COUNT, -1.0);
+      if (us_out)
+        for (int k = 0; k < K_COUNT; ++k) row[k] = us_out[l * K_COUNT + k];
+      now[key] = std::make_pair(best, row);
+    }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
   }

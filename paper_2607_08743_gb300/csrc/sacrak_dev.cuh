@@ -32,7 +32,7 @@ struct DevPatch {
   int level;
   int parent;        // parent patch index, -1 on level 0
   int off[3];        // this patch's origin in parent cell units
-  int pad_;
+  int zrefl;         // equatorial symmetry: lower z face at z = 0, ghosts below by reflection
   long long plane;   // px * NY
   long long fstride; // doubles between consecutive fields
   double dx;
@@ -278,6 +278,9 @@ void launch_sommerfeld(const GhostArgs& a, int npatches, long long max_shell, cu
 void launch_constraints(const ConsArgs& a, int ntiles, double* out5, cudaStream_t st);
 void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cudaStream_t st);
 void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st);
+// equatorial reflection of the z < 0 ghost layers of the level's zrefl
+// patches, in the buffer selected by (mode, stage) as for the other fills
+void launch_zreflect(const FillArgs& a, int npatches, long long maxpts, cudaStream_t st);
 // bricks of the spatial prolongation of one child patch (n active cells)
 int prolong_bricks(int n0, int n1, int n2);
 void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,

@@ -34,12 +34,14 @@ int tma_setup_variant(int v);
 void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st);
 
 // The same arithmetic reading every stencil value through the L1 cache, over
-// the 32 x 4 x 1 tile list of StageArgs, 3 CTAs per SM; with prefetch != 0
-// the next field's stencil rows are prefetched into L1 and the epilogue's
-// streaming reads into L2.  ldg_setup opts the kernels in to their shared
-// memory (false on failure).
-int ldg_setup(int prefetch);
-void launch_stage_ldg(int prefetch, const StageArgs& a, cudaStream_t st);
+// the 32 x 4 x 1 tile list of StageArgs.  Variant v: 0 3 CTAs per SM; 1 also
+// prefetches the next field's stencil rows into L1 and the epilogue's
+// streaming reads into L2; 2 as 1 with 4 CTAs per SM (128 registers); 3 as 1
+// with only the star rows prefetched; 4 only the z-arm rows; 5 only the
+// epilogue's reads.  ldg_setup opts the kernels in to their shared memory
+// (false on failure).
+int ldg_setup(int v);
+void launch_stage_ldg(int v, const StageArgs& a, cudaStream_t st);
 
 // The stage split in two launches: derivatives of five fields per thread into
 // FP32 slot planes in global memory (dslot, split_slot_floats(ntiles) floats

@@ -668,6 +668,17 @@ int setup_variant() {
 
 // ------------------------------------------------------------------ L1 path
 
+// Prefetch into L1 the centre row and the z arms of the next field (rows of
+// other planes, which the other warps of the CTA do not load)
+__device__ __forceinline__ void prefetch_zarms(const float2* F, long long sz) {
+  prefetch_l1(F);
+#pragma unroll
+  for (int k = 1; k <= 3; ++k) {
+    prefetch_l1(F + k * sz);
+    prefetch_l1(F - k * sz);
+  }
+}
+
 // Prefetch into L1 the rows of the next field that its stencils read: the
 // centre row, the y and z arms of the star, and (for fields with second
 // derivatives) the 16 rows of the y-z mixed stencil.  x neighbours share the
@@ -694,7 +705,10 @@ __device__ __forceinline__ void prefetch_field(const float2* F, long long sy, lo
 // through the L1 cache (no staging and no barriers, so threads beyond the
 // patch leave at once): one thread per point of the level's 32 x 4 x 1 tile
 // list, MINB CTAs per SM (NSLOT x 128 shared-memory slots each).
-template <int MINB, int MODE, bool PF>
+// PF: 0 no prefetching, 1 the next field's star and mixed-derivative rows,
+// 2 its star rows only, 3 its z-arm rows only, 4 none of its rows (only the
+// epilogue's streaming reads into L2)
+template <int MINB, int MODE, int PF>
 __global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
   extern __shared__ float sd[];
   const Tile tl = S.tiles[blockIdx.x];
@@ -724,7 +738,9 @@ __global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
   // next field's rows are prefetched into L1 while this one is formed
 #pragma unroll 1
   for (int f = 0; f < NF; ++f) {
-    if (PF && f + 1 < NF) prefetch_field(U + (long long)(f + 1) * fs + q, sy, sz, plan(f + 1).d2 != 0);
+    if (PF >= 1 && PF <= 2 && f + 1 < NF)
+      prefetch_field(U + (long long)(f + 1) * fs + q, sy, sz, PF == 1 && plan(f + 1).d2 != 0);
+    if (PF == 3 && f + 1 < NF) prefetch_zarms(U + (long long)(f + 1) * fs + q, sz);
     const GlobalAcc at{U + (long long)f * fs + q, sy, sz};
     field_pass_p<false>(at, plan(f), f, SmemSlots<128>{sd, t}, wko, wup, c1, c2, c11, gtu);
   }
@@ -745,22 +761,22 @@ __global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
   }
 }
 
-template <bool PF>
+template <int MINB, int PF>
 bool setup_ldg() {
   const int smem = NSLOT * 128 * 4;
-  return cudaFuncSetAttribute(z4c_stage_ldg_kernel<3, 0, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(z4c_stage_ldg_kernel<3, 1, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-             cudaSuccess;
+  return cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 0, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem) == cudaSuccess &&
+         cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 1, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem) == cudaSuccess;
 }
 
-template <bool PF>
+template <int MINB, int PF>
 void launch_ldg(const StageArgs& a, cudaStream_t st) {
   const int smem = NSLOT * 128 * 4;
   if (a.stage == 0)
-    z4c_stage_ldg_kernel<3, 1, PF><<<a.ntiles, 128, smem, st>>>(a);
+    z4c_stage_ldg_kernel<MINB, 1, PF><<<a.ntiles, 128, smem, st>>>(a);
   else
-    z4c_stage_ldg_kernel<3, 0, PF><<<a.ntiles, 128, smem, st>>>(a);
+    z4c_stage_ldg_kernel<MINB, 0, PF><<<a.ntiles, 128, smem, st>>>(a);
 }
 
 // ------------------------------------------------------------------ split path
@@ -872,14 +888,31 @@ void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st) {
   }
 }
 
-int ldg_setup(int prefetch) { return prefetch ? setup_ldg<true>() : setup_ldg<false>(); }
+// variant v: 0 (3 CTAs/SM, no prefetch), 1 (3, prefetch), 2 (4, prefetch),
+// 3 (3, prefetch of the star rows only), 4 (3, z-arm rows only), 5 (3, the
+// epilogue's reads only)
+int ldg_setup(int v) {
+  switch (v) {
+    case 0: return setup_ldg<3, 0>();
+    case 1: return setup_ldg<3, 1>();
+    case 2: return setup_ldg<4, 1>();
+    case 3: return setup_ldg<3, 2>();
+    case 4: return setup_ldg<3, 3>();
+    case 5: return setup_ldg<3, 4>();
+  }
+  return 0;
+}
 
-void launch_stage_ldg(int prefetch, const StageArgs& a, cudaStream_t st) {
+void launch_stage_ldg(int v, const StageArgs& a, cudaStream_t st) {
   if (a.ntiles == 0) return;
-  if (prefetch)
-    launch_ldg<true>(a, st);
-  else
-    launch_ldg<false>(a, st);
+  switch (v) {
+    case 0: launch_ldg<3, 0>(a, st); break;
+    case 1: launch_ldg<3, 1>(a, st); break;
+    case 2: launch_ldg<4, 1>(a, st); break;
+    case 3: launch_ldg<3, 2>(a, st); break;
+    case 4: launch_ldg<3, 3>(a, st); break;
+    case 5: launch_ldg<3, 4>(a, st); break;
+  }
 }
 
 long long split_slot_floats(long long ntiles) { return (long long)NSLOT_SPLIT * ntiles * 128; }

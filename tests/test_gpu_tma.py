@@ -24,7 +24,7 @@ from tests.gpu_common import grid_for, rel_err
 skbuild.build()
 
 TMA = [1, 2, 3, 4]
-PAIRS = [5, 6, 7]  # L1 path and split launches, same arithmetic
+PAIRS = [5, 6, 7, 8, 9, 10, 11]  # L1 path and split launches, same arithmetic
 TOL = 1e-4          # mixed precision vs the FP64 oracle
 TOL_KERNELS = 2e-5  # TMA kernel vs direct mixed kernel, same data
 
@@ -63,7 +63,7 @@ def test_tma_rhs_puncture(kernel):
 def test_tma_ragged_patch_rhs(kernel, n):
     """Tiles cut by the patch edge in x, y and z: the copies past the array
     are filled with zeros and the points beyond the patch write nothing."""
-    ty, tz = {1: (4, 1), 2: (2, 2), 3: (4, 2), 4: (8, 1), 5: (1, 1), 6: (1, 1), 7: (1, 1)}[kernel]
+    ty, tz = {1: (4, 1), 2: (2, 2), 3: (4, 2), 4: (8, 1)}.get(kernel, (1, 1))
     if n[1] < ty or n[2] < tz:
         pytest.skip("patch thinner than the tile")
     dx = 0.25
@@ -127,11 +127,11 @@ def _tma_hierarchy():
     return h, idd.hierarchy_data(h, noise=1e-10)
 
 
-@pytest.mark.parametrize("kernel", [1, 6, 7])
+@pytest.mark.parametrize("kernel", [1, 7, 10])
 def test_tma_level_step_hierarchy_vs_oracle(kernel):
     h, states = _tma_hierarchy()
     g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(precision=1), stream=torch.cuda.Stream())
-    assert all(g.stage_kernel(l) == 6 for l in range(len(h.levels)))  # the mixed-precision default
+    assert all(g.stage_kernel(l) == 10 for l in range(len(h.levels)))  # the mixed-precision default
     for l in range(len(h.levels)):
         g.set_stage_kernel(l, kernel)
     for i, u in enumerate(states):
@@ -178,11 +178,11 @@ def test_autotune_choice_and_parity():
 def test_tma_kernel_rejected_where_it_does_not_fit():
     p = idd.Patch(n=(24, 8, 8), dx=0.25, origin=(-3.0, -1.0, -1.0))
     g = grid_for([p], precision=1)
-    assert g.stage_kernel(0) == 6
+    assert g.stage_kernel(0) == 10
     with pytest.raises(sk.SacrakError):
         g.set_stage_kernel(0, 1)
     with pytest.raises(sk.SacrakError):
-        g.set_stage_kernel(0, 8)
+        g.set_stage_kernel(0, len(sk.STAGE_KERNELS))
     f = grid_for([idd.single_puncture_patch(32, 8.0)])  # FP64: only the direct kernel
     assert f.stage_kernel(0) == 0
     for k in (1, 5):
