@@ -102,6 +102,9 @@ def lib():
             L.orc_exchange.restype = ctypes.c_long
             L.orc_lagrange_weights.argtypes = [ctypes.c_int, P(ctypes.c_int), ctypes.c_double, dp]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_adm_integrals.argtypes = [P(_OrcPatch), dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
+            L.orc_adm_integrals.restype = ctypes.c_int
+            L.orc_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
             L.orc_stencils.argtypes = [P(_OrcPatch), dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, dp, dp]
             _lib = L
@@ -227,6 +230,25 @@ def stencils(p, u: np.ndarray, field: int, i: int, j: int, k: int, b=(1.0, 1.0, 
     out = np.empty(15)
     lib().orc_stencils(ctypes.byref(_cp(p)), _ptr(u), field, i, j, k, _ptr(bb), _ptr(out))
     return out
+
+
+def adm_integrals(p, u: np.ndarray, centre, radius: float, ntheta: int = 24, nphi: int = 48):
+    """(M_ADM, J_z) on the coordinate sphere of the given radius (Sec. 2.3)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    c = np.ascontiguousarray(centre, dtype=np.float64)
+    out = np.empty(2)
+    rc = lib().orc_adm_integrals(ctypes.byref(_cp(p)), _ptr(u), _ptr(c), float(radius), int(ntheta), int(nphi),
+                                 _ptr(out))
+    if rc != 0:
+        raise ValueError("sphere leaves the patch (interpolation needs 2 cells more)")
+    return float(out[0]), float(out[1])
+
+
+def gauss_legendre(n: int):
+    x = np.empty(n)
+    w = np.empty(n)
+    lib().orc_gauss_legendre(n, _ptr(x), _ptr(w))
+    return x, w
 
 
 def lagrange_weights(nodes: Sequence[int], x: float) -> np.ndarray:

@@ -577,6 +577,143 @@ int orc_fill_zreflect(const orc_patch* p, double* u) {
   return 0;
 }
 
+/* ---------------- ADM surface integrals (Sec. 2.3) ---------------- */
+
+#define ORC_PI 3.14159265358979323846
+
+/* Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on the
+ * Legendre polynomial P_n (three-term recurrence), Chebyshev-like starting
+ * points. */
+void orc_gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = cos(ORC_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      if (n == 1) {
+        p1 = z;
+        p0 = 1.0;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0); /* P_n'(z) */
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+/* At cell q: the mass integrand vector sqrt(gamma) gamma^ik gamma^jl
+ * (d_j gamma_kl - d_k gamma_jl) (out m[3]) and sqrt(gamma) K_x^j, K_y^j
+ * (out kx[3], ky[3]), from gamma_ij = gt_ij / W^2 and
+ * K_ij = (At_ij + gt_ij K / 3) / W^2, K = Khat + 2 Theta; derivatives by the
+ * 4th-order centred D1. */
+static void adm_cell(const double* u, const layout* L, double h, ptrdiff_t q, double m[3], double kx[3],
+                     double ky[3]) {
+  const double W = u[F_W * L->sf + q];
+  double gt[6], gtu[6], At[6];
+  for (int a = 0; a < 6; ++a) {
+    gt[a] = u[(F_GXX + a) * L->sf + q];
+    At[a] = u[(F_AXX + a) * L->sf + q];
+  }
+  const double det = sym_inverse(gt, gtu);
+  double gamu[6], dgam[3][6];
+  for (int a = 0; a < 6; ++a) gamu[a] = gtu[a] * W * W;
+  for (int d = 0; d < 3; ++d) {
+    const double dW = D1(u + F_W * L->sf, q, L->s[d], h);
+    for (int a = 0; a < 6; ++a) {
+      const double dgt = D1(u + (F_GXX + a) * L->sf, q, L->s[d], h);
+      dgam[d][a] = dgt / (W * W) - 2.0 * gt[a] * dW / (W * W * W);
+    }
+  }
+  const double sg = sqrt(det) / (W * W * W);
+  for (int i = 0; i < 3; ++i) {
+    double v = 0.0;
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l)
+          v += gamu[SYM[i][k]] * gamu[SYM[j][l]] * (dgam[j][SYM[k][l]] - dgam[k][SYM[j][l]]);
+    m[i] = sg * v;
+  }
+  const double K = u[F_KH * L->sf + q] + 2.0 * u[F_TH * L->sf + q];
+  /* K_i^j = gamma^jk K_ik = gt^jk (At_ik + gt_ik K / 3) */
+  for (int j = 0; j < 3; ++j) {
+    double ax = 0.0, ay = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      ax += gtu[SYM[j][k]] * (At[SYM[0][k]] + gt[SYM[0][k]] * K / 3.0);
+      ay += gtu[SYM[j][k]] * (At[SYM[1][k]] + gt[SYM[1][k]] * K / 3.0);
+    }
+    kx[j] = sg * ax;
+    ky[j] = sg * ay;
+  }
+}
+
+int orc_adm_integrals(const orc_patch* p, const double* u, const double c[3], double r, int ntheta, int nphi,
+                      double out[2]) {
+  layout L = make_layout(p);
+  const double h = p->dx;
+  const int g = p->g;
+  const int N[3] = {L.NX, L.NY, L.NZ};
+  double* xg = (double*)malloc(sizeof(double) * ntheta);
+  double* wg = (double*)malloc(sizeof(double) * ntheta);
+  orc_gauss_legendre(ntheta, xg, wg);
+  static const int nodes[4] = {0, 1, 2, 3};
+  double M = 0.0, J = 0.0;
+  int bad = 0;
+  for (int it = 0; it < ntheta && !bad; ++it) {
+    const double ct = xg[it], st = sqrt(1.0 - ct * ct);
+    for (int ip = 0; ip < nphi && !bad; ++ip) {
+      const double ph = 2.0 * ORC_PI * ip / nphi;
+      const double n[3] = {st * cos(ph), st * sin(ph), ct};
+      const double x[3] = {c[0] + r * n[0], c[1] + r * n[1], c[2] + r * n[2]};
+      /* 4 nearest cell centres per axis: array index of cell i is i + g,
+       * its centre origin + (i + 1/2) h */
+      int i0[3];
+      double wl[3][4];
+      for (int d = 0; d < 3; ++d) {
+        const double t = (x[d] - p->origin[d]) / h - 0.5 + g; /* array coordinate */
+        i0[d] = (int)floor(t) - 1;
+        if (i0[d] < 2 || i0[d] + 3 > N[d] - 3) bad = 1;
+        orc_lagrange_weights(4, nodes, t - i0[d], wl[d]);
+      }
+      if (bad) break;
+      double m[3] = {0, 0, 0}, kx[3] = {0, 0, 0}, ky[3] = {0, 0, 0};
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b)
+          for (int e = 0; e < 4; ++e) {
+            const ptrdiff_t q = (i0[0] + a) + (ptrdiff_t)(i0[1] + b) * L.s[1] + (ptrdiff_t)(i0[2] + e) * L.s[2];
+            double mc[3], kxc[3], kyc[3];
+            adm_cell(u, &L, h, q, mc, kxc, kyc);
+            const double w = wl[0][a] * wl[1][b] * wl[2][e];
+            for (int d = 0; d < 3; ++d) {
+              m[d] += w * mc[d];
+              kx[d] += w * kxc[d];
+              ky[d] += w * kyc[d];
+            }
+          }
+      const double dA = wg[it] * (2.0 * ORC_PI / nphi) * r * r; /* n_i dS = n_i r^2 dOmega */
+      double mn = 0.0, jn = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        mn += m[d] * n[d];
+        jn += ((x[0] - c[0]) * ky[d] - (x[1] - c[1]) * kx[d]) * n[d];
+      }
+      M += dA * mn;
+      J += dA * jn;
+    }
+  }
+  free(xg);
+  free(wg);
+  if (bad) return -1;
+  out[0] = M / (16.0 * ORC_PI);
+  out[1] = J / (8.0 * ORC_PI);
+  return 0;
+}
+
 /* ---------------- algebraic constraints ---------------- */
 
 static void enforce_point(double* u, ptrdiff_t sf, ptrdiff_t q, double w_floor) {
