@@ -13,12 +13,12 @@ analytic families stand in for it):
 * Brill-Lindquist punctures (time-symmetric, conformally flat): psi = 1 +
   sum_a m_a / (2 |x - x_a|), W = psi^-2, gt_ij = delta_ij, K = At = Gamt = 0,
   precollapsed lapse alpha = psi^-2, beta = B = 0.
-* Spinning puncture: the Brill-Lindquist conformal factor of one puncture
-  with the Bowen-York extrinsic curvature of spin J (Bowen & York 1980),
-  K_ij = psi^-2 Ahat_ij, Ahat_ij = 3/r^3 (eps_kil J^l n^k n_j + eps_kjl J^l
-  n^k n_i), so At_ij = psi^-6 Ahat_ij; K = 0.  The Hamiltonian constraint is
-  not re-solved for the spin (psi stays 1 + m/(2r)): an input, not a
-  solution.
+* Bowen-York puncture: the Brill-Lindquist conformal factor of one puncture
+  with the Bowen-York extrinsic curvature of spin S and momentum P (Bowen &
+  York 1980), K_ij = psi^-2 Ahat_ij, Ahat_ij = 3/r^3 (eps_kil S^l n^k n_j +
+  eps_kjl S^l n^k n_i) + 3/(2 r^2) (P_i n_j + P_j n_i - (delta_ij - n_i n_j)
+  P.n), so At_ij = psi^-6 Ahat_ij; K = 0.  The Hamiltonian constraint is not
+  re-solved (psi stays 1 + m/(2r)): an input, not a solution.
 * Gauge wave (Alcubierre et al. 2004 test-bed form): H = 1 - A sin(2 pi (x - t)/d),
   ds^2 = -H dt^2 + H dx^2 + dy^2 + dz^2, converted to the W/Z4c variables.
 * Noise: uniform in [-a, a] added to every field at every point; the value at
@@ -116,19 +116,23 @@ def punctures(p: Patch, masses: Sequence[float], positions: Sequence[Sequence[fl
     return u
 
 
-def spinning_puncture(p: Patch, mass: float, spin: Sequence[float], centre=(0.0, 0.0, 0.0)) -> np.ndarray:
-    """One puncture with Bowen-York spin vector `spin` (see module doc)."""
+def bowen_york(p: Patch, mass: float, centre=(0.0, 0.0, 0.0), spin=(0.0, 0.0, 0.0),
+               momentum=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """One puncture with Bowen-York spin and linear momentum (see module doc)."""
     u = punctures(p, [mass], [centre])
     z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
     xs = [x - centre[0], y - centre[1], z - centre[2]]
     r = np.sqrt(xs[0] ** 2 + xs[1] ** 2 + xs[2] ** 2)
     n = [c / r for c in xs]
-    # (J x n)_i = eps_ikl J^k n^l, equal to eps_kil J^l n^k
-    jxn = [spin[1] * n[2] - spin[2] * n[1], spin[2] * n[0] - spin[0] * n[2], spin[0] * n[1] - spin[1] * n[0]]
+    S, P = spin, momentum
+    # (S x n)_i = eps_ikl S^k n^l, equal to eps_kil S^l n^k
+    sxn = [S[1] * n[2] - S[2] * n[1], S[2] * n[0] - S[0] * n[2], S[0] * n[1] - S[1] * n[0]]
+    pn = P[0] * n[0] + P[1] * n[1] + P[2] * n[2]
     psi6 = u[0] ** 3  # W^3 = psi^-6
     sym = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
     for a, (i, j) in enumerate(sym):
-        ahat = 3.0 / r ** 3 * (jxn[i] * n[j] + jxn[j] * n[i])
+        ahat = 3.0 / r ** 3 * (sxn[i] * n[j] + sxn[j] * n[i])
+        ahat = ahat + 1.5 / r ** 2 * (P[i] * n[j] + P[j] * n[i] - ((1.0 if i == j else 0.0) - n[i] * n[j]) * pn)
         u[9 + a] = psi6 * ahat
     return u
 

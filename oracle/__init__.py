@@ -233,15 +233,16 @@ def stencils(p, u: np.ndarray, field: int, i: int, j: int, k: int, b=(1.0, 1.0, 
 
 
 def adm_integrals(p, u: np.ndarray, centre, radius: float, ntheta: int = 24, nphi: int = 48):
-    """(M_ADM, J_z) on the coordinate sphere of the given radius (Sec. 2.3)."""
+    """(M_ADM, J_z, P_x, P_y, P_z) on the coordinate sphere of the given
+    radius (Sec. 2.3, Sec. 3.2)."""
     u = np.ascontiguousarray(u, dtype=np.float64)
     c = np.ascontiguousarray(centre, dtype=np.float64)
-    out = np.empty(2)
+    out = np.empty(5)
     rc = lib().orc_adm_integrals(ctypes.byref(_cp(p)), _ptr(u), _ptr(c), float(radius), int(ntheta), int(nphi),
                                  _ptr(out))
     if rc != 0:
         raise ValueError("sphere leaves the patch (interpolation needs 2 cells more)")
-    return float(out[0]), float(out[1])
+    return tuple(float(v) for v in out)
 
 
 def gauss_legendre(n: int):

@@ -609,12 +609,14 @@ void orc_gauss_legendre(int n, double* x, double* w) {
 }
 
 /* At cell q: the mass integrand vector sqrt(gamma) gamma^ik gamma^jl
- * (d_j gamma_kl - d_k gamma_jl) (out m[3]) and sqrt(gamma) K_x^j, K_y^j
- * (out kx[3], ky[3]), from gamma_ij = gt_ij / W^2 and
- * K_ij = (At_ij + gt_ij K / 3) / W^2, K = Khat + 2 Theta; derivatives by the
- * 4th-order centred D1. */
-static void adm_cell(const double* u, const layout* L, double h, ptrdiff_t q, double m[3], double kx[3],
-                     double ky[3]) {
+ * (d_j gamma_kl - d_k gamma_jl) (out m[3]), the mixed extrinsic curvature
+ * times sqrt(gamma), kk[i][j] = sqrt(gamma) K_i^j, and sqrt(gamma) K (out
+ * sk), from gamma_ij = gt_ij / W^2, K_ij = (At_ij + gt_ij K / 3) / W^2,
+ * K = Khat + 2 Theta; derivatives by the 4th-order centred D1.  The proper
+ * surface element of the coordinate sphere is dS_i = sqrt(gamma) n_i r^2
+ * dOmega (n_i = x_i / r), so these are the integrands per coordinate area. */
+static void adm_cell(const double* u, const layout* L, double h, ptrdiff_t q, double m[3], double kk[3][3],
+                     double* sk) {
   const double W = u[F_W * L->sf + q];
   double gt[6], gtu[6], At[6];
   for (int a = 0; a < 6; ++a) {
@@ -642,19 +644,17 @@ static void adm_cell(const double* u, const layout* L, double h, ptrdiff_t q, do
   }
   const double K = u[F_KH * L->sf + q] + 2.0 * u[F_TH * L->sf + q];
   /* K_i^j = gamma^jk K_ik = gt^jk (At_ik + gt_ik K / 3) */
-  for (int j = 0; j < 3; ++j) {
-    double ax = 0.0, ay = 0.0;
-    for (int k = 0; k < 3; ++k) {
-      ax += gtu[SYM[j][k]] * (At[SYM[0][k]] + gt[SYM[0][k]] * K / 3.0);
-      ay += gtu[SYM[j][k]] * (At[SYM[1][k]] + gt[SYM[1][k]] * K / 3.0);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double a = 0.0;
+      for (int k = 0; k < 3; ++k) a += gtu[SYM[j][k]] * (At[SYM[i][k]] + gt[SYM[i][k]] * K / 3.0);
+      kk[i][j] = sg * a;
     }
-    kx[j] = sg * ax;
-    ky[j] = sg * ay;
-  }
+  *sk = sg * K;
 }
 
 int orc_adm_integrals(const orc_patch* p, const double* u, const double c[3], double r, int ntheta, int nphi,
-                      double out[2]) {
+                      double out[5]) {
   layout L = make_layout(p);
   const double h = p->dx;
   const int g = p->g;
@@ -663,7 +663,7 @@ int orc_adm_integrals(const orc_patch* p, const double* u, const double c[3], do
   double* wg = (double*)malloc(sizeof(double) * ntheta);
   orc_gauss_legendre(ntheta, xg, wg);
   static const int nodes[4] = {0, 1, 2, 3};
-  double M = 0.0, J = 0.0;
+  double M = 0.0, J = 0.0, P[3] = {0.0, 0.0, 0.0};
   int bad = 0;
   for (int it = 0; it < ntheta && !bad; ++it) {
     const double ct = xg[it], st = sqrt(1.0 - ct * ct);
@@ -682,28 +682,34 @@ int orc_adm_integrals(const orc_patch* p, const double* u, const double c[3], do
         orc_lagrange_weights(4, nodes, t - i0[d], wl[d]);
       }
       if (bad) break;
-      double m[3] = {0, 0, 0}, kx[3] = {0, 0, 0}, ky[3] = {0, 0, 0};
+      double m[3] = {0, 0, 0}, kk[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, sk = 0.0;
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b)
           for (int e = 0; e < 4; ++e) {
             const ptrdiff_t q = (i0[0] + a) + (ptrdiff_t)(i0[1] + b) * L.s[1] + (ptrdiff_t)(i0[2] + e) * L.s[2];
-            double mc[3], kxc[3], kyc[3];
-            adm_cell(u, &L, h, q, mc, kxc, kyc);
+            double mc[3], kc[3][3], skc;
+            adm_cell(u, &L, h, q, mc, kc, &skc);
             const double w = wl[0][a] * wl[1][b] * wl[2][e];
             for (int d = 0; d < 3; ++d) {
               m[d] += w * mc[d];
-              kx[d] += w * kxc[d];
-              ky[d] += w * kyc[d];
+              for (int f = 0; f < 3; ++f) kk[d][f] += w * kc[d][f];
             }
+            sk += w * skc;
           }
-      const double dA = wg[it] * (2.0 * ORC_PI / nphi) * r * r; /* n_i dS = n_i r^2 dOmega */
+      const double dA = wg[it] * (2.0 * ORC_PI / nphi) * r * r; /* coordinate area of the node */
       double mn = 0.0, jn = 0.0;
       for (int d = 0; d < 3; ++d) {
         mn += m[d] * n[d];
-        jn += ((x[0] - c[0]) * ky[d] - (x[1] - c[1]) * kx[d]) * n[d];
+        jn += ((x[0] - c[0]) * kk[1][d] - (x[1] - c[1]) * kk[0][d]) * n[d];
       }
       M += dA * mn;
       J += dA * jn;
+      /* (K_i^j - delta_i^j K) n_j */
+      for (int i = 0; i < 3; ++i) {
+        double pn = -sk * n[i];
+        for (int d = 0; d < 3; ++d) pn += kk[i][d] * n[d];
+        P[i] += dA * pn;
+      }
     }
   }
   free(xg);
@@ -711,6 +717,7 @@ int orc_adm_integrals(const orc_patch* p, const double* u, const double c[3], do
   if (bad) return -1;
   out[0] = M / (16.0 * ORC_PI);
   out[1] = J / (8.0 * ORC_PI);
+  for (int i = 0; i < 3; ++i) out[2 + i] = P[i] / (8.0 * ORC_PI);
   return 0;
 }
 

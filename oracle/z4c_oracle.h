@@ -28,8 +28,10 @@
  *   orc_lagrange_weights exact fractions (Fraction arithmetic)
  *   orc_adm_integrals   Schwarzschild in isotropic coordinates: M psi(r)
  *                       (closed form) at 4th order in dx; Bowen-York spin:
- *                       J_z = J for any conformal factor; nodes integrate
- *                       polynomials exactly (orc_gauss_legendre)
+ *                       J_z = J and boost: P = P for any conformal factor;
+ *                       a pure-gauge perturbation of flat space gives a
+ *                       mass of second order; nodes integrate polynomials
+ *                       exactly (orc_gauss_legendre)
  *   Berger-Oliger driver (oracle/__init__.py) gauge wave on 3 nested levels,
  *                       2nd-order convergence with quadratic time interpolation
  * No function is left "parity unpinned".
@@ -154,16 +156,19 @@ long orc_exchange(const orc_patch* a, double* ua, const orc_patch* b, double* ub
 void orc_stencils(const orc_patch* p, const double* u, int field, int i, int j, int k,
                   const double b[3], double out[15]);
 
-/* ADM mass and angular momentum (Sec. 2.3) on the coordinate sphere of
- * radius r around c: M = 1/(16 pi) sum sqrt(g) g^ik g^jl (d_j g_kl - d_k g_jl)
- * n_i r^2 dOmega and J_z = 1/(8 pi) sum sqrt(g) (x K_y^j - y K_x^j) n_j r^2 dOmega
- * (x, y relative to c), the integrands formed at cell centres (4th-order
- * derivatives), interpolated to the sphere with the 4 nearest cell centres
- * per axis (cubic Lagrange), Gauss-Legendre in cos(theta) (ntheta nodes)
- * times the trapezoid rule in phi (nphi points).  out = {M, J_z}; -1 if an
- * interpolation stencil comes within 2 cells of the array edge. */
+/* ADM mass, angular momentum (Sec. 2.3) and linear momentum (Sec. 3.2) on
+ * the coordinate sphere of radius r around c, with the proper surface
+ * element dS_i = sqrt(g) n_i r^2 dOmega:
+ *   M   = 1/(16 pi) int g^ik g^jl (d_j g_kl - d_k g_jl) dS_i
+ *   J_z = 1/(8 pi)  int (x K_y^j - y K_x^j) dS_j      (x, y relative to c)
+ *   P_i = 1/(8 pi)  int (K_i^j - delta_i^j K) dS_j
+ * the integrands formed at cell centres (4th-order derivatives), interpolated
+ * to the sphere with the 4 nearest cell centres per axis (cubic Lagrange),
+ * Gauss-Legendre in cos(theta) (ntheta nodes) times the trapezoid rule in phi
+ * (nphi points).  out = {M, J_z, P_x, P_y, P_z}; -1 if an interpolation
+ * stencil comes within 2 cells of the array edge. */
 int orc_adm_integrals(const orc_patch* p, const double* u, const double c[3], double r, int ntheta, int nphi,
-                      double out[2]);
+                      double out[5]);
 void orc_gauss_legendre(int n, double* x, double* w);
 
 /* Lagrange basis weights of a set of integer nodes at position x. */

@@ -7,9 +7,14 @@
   gamma_ij = psi^4 delta_ij, psi = 1 + M/(2r), so the mass integrand is
   -8 psi d_i psi and M_ADM(r) = M psi(r) = M (1 + M/(2r)) on every sphere
   around the puncture; the error must fall like dx^4.
-* Bowen-York spin: sqrt(gamma) K_i^j = Ahat_ij for any conformal factor and
-  Ahat_ij n^j = 3/r^3 (J x n)_i, so J_z = J . e_z on every sphere around the
-  puncture.
+* Bowen-York spin and boost: sqrt(gamma) K_i^j = Ahat_ij for any conformal
+  factor (K = 0); for spin S, Ahat_ij n^j = 3/r^3 (S x n)_i, so J_z = S_z and
+  P = 0 on every sphere around the puncture; for momentum P, Ahat_ij n^j =
+  3/(2 r^2) (P_i + n_i P.n), whose flux is P (and J_z = 0).
+* The trace term of P^ADM: a pure-trace K_ij = K gamma_ij / 3 with
+  gamma = delta gives (K/3 - K) n_i, so P_i = -(1/12 pi) int K n_i dS; for
+  K = k0 + k1 x this is -(k1 r^3 / 9) e_x (int n_x^2 dOmega = 4 pi / 3; the
+  k0 part cancels).
 * A pure-gauge linear perturbation gamma_ij = delta_ij + eps (d_i xi_j +
   d_j xi_i) of flat space: the linearised mass integrand is the divergence of
   an antisymmetric tensor, whose flux through a closed surface vanishes, so
@@ -37,25 +42,25 @@ def test_gauss_legendre_nodes():
 
 def test_minkowski_zero():
     p = idt.centred_patch(32, 0.5)
-    m, j = oracle.adm_integrals(p, idt.minkowski(p), (0.0, 0.0, 0.0), 5.0, 16, 32)
-    assert m == 0.0 and j == 0.0
+    v = oracle.adm_integrals(p, idt.minkowski(p), (0.0, 0.0, 0.0), 5.0, 16, 32)
+    assert v == (0.0,) * 5
 
 
 def test_schwarzschild_mass_fourth_order():
     mass = 1.0
     for n in (32, 96):
         p = idt.centred_patch(n, 16.0 / n)
-        u = idt.spinning_puncture(p, mass, (0.0, 0.0, 0.0))
+        u = idt.bowen_york(p, mass)
         errs = []
         for r in (4.5, 5.0, 5.5, 6.0):
-            m, j = oracle.adm_integrals(p, u, (0.0, 0.0, 0.0), r, 48, 96)
+            m, j, px, py, pz = oracle.adm_integrals(p, u, (0.0, 0.0, 0.0), r, 48, 96)
             errs.append(abs(m - mass * (1.0 + mass / (2.0 * r))))
-            assert j == 0.0
+            assert j == 0.0 and px == py == pz == 0.0
         # truncation C dx^4 with C measured below 3e-4 for these spheres
         assert max(errs) < 1e-3 * p.dx ** 4, (n, errs)
     # the radius dependence M psi(r) itself, not only its limit
     p = idt.centred_patch(96, 16.0 / 96)
-    u = idt.spinning_puncture(p, 0.5, (0.0, 0.0, 0.0))
+    u = idt.bowen_york(p, 0.5)
     m4 = oracle.adm_integrals(p, u, (0.0, 0.0, 0.0), 4.0, 48, 96)[0]
     m7 = oracle.adm_integrals(p, u, (0.0, 0.0, 0.0), 7.0, 48, 96)[0]
     assert abs((m4 - m7) - 0.5 * 0.5 * (1 / 8.0 - 1 / 14.0)) < 1e-6
@@ -65,10 +70,40 @@ def test_schwarzschild_mass_fourth_order():
 def test_bowen_york_spin(spin):
     p = idt.centred_patch(64, 0.25)
     c = (1.0, -0.5, 0.25)
-    u = idt.spinning_puncture(p, 1.0, spin, c)
-    m, j = oracle.adm_integrals(p, u, c, 5.0, 48, 96)
+    u = idt.bowen_york(p, 1.0, c, spin=spin)
+    m, j, *P = oracle.adm_integrals(p, u, c, 5.0, 48, 96)
     assert abs(j - spin[2]) < 2e-6
     assert abs(m - 1.1) < 1e-6  # the spin does not enter the mass
+    assert max(abs(v) for v in P) < 1e-6
+
+
+@pytest.mark.parametrize("mom", [(0.2, 0.0, 0.0), (0.0, -0.3, 0.1), (0.1, 0.2, 0.3)])
+def test_bowen_york_boost(mom):
+    p = idt.centred_patch(64, 0.25)
+    c = (-0.5, 0.75, 0.25)
+    u = idt.bowen_york(p, 1.0, c, momentum=mom)
+    for r in (4.0, 5.5):
+        m, j, *P = oracle.adm_integrals(p, u, c, r, 48, 96)
+        assert max(abs(a - b) for a, b in zip(P, mom)) < 5e-6, (r, P)
+        assert abs(j) < 2e-6
+        assert abs(m - (1.0 + 1.0 / (2.0 * r))) < 1e-5
+
+
+def test_trace_term_of_momentum():
+    p = idt.centred_patch(48, 0.25)
+    z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
+    k0, k1 = 0.3, 0.05
+    u = idt.minkowski(p)
+    u[7] = k0 + k1 * x  # Khat; Theta = 0
+    for r in (2.0, 4.0):
+        m, j, px, py, pz = oracle.adm_integrals(p, u, (0.0, 0.0, 0.0), r, 24, 48)
+        assert abs(px - (-k1 * r ** 3 / 9.0)) < 1e-12 * r ** 3
+        assert abs(py) < 1e-14 and abs(pz) < 1e-14 and abs(j) < 1e-14 and m == 0.0
+    # Theta enters K twice: the same trace from Theta = Khat / 2
+    u[8] = 0.5 * u[7]
+    u[7] = 0.0
+    px2 = oracle.adm_integrals(p, u, (0.0, 0.0, 0.0), 2.0, 24, 48)[2]
+    assert abs(px2 - (-k1 * 8.0 / 9.0)) < 1e-12 * 8.0
 
 
 def _gauge_flat(p, eps, x0=(0.3, -0.2, 0.1), sig=2.0):
