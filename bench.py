@@ -206,11 +206,12 @@ def main():
                     help="gauge-wave: RK4 steps on the coarsest grid; robust-stability: steps per grid")
     ap.add_argument("--case", default="amr7",
                     choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep",
-                             "amr7-zsym"],
+                             "amr7-zsym", "adm"],
                     help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
                          "mixed-error: the 7-level hierarchy in FP64 and mixed precision side by side")
     ap.add_argument("--coarse-steps", type=int, default=64, help="mixed-error: coarse steps")
     ap.add_argument("--error-kernels", default="", help="mixed-error: stage kernels to compare, e.g. 6,0")
+    ap.add_argument("--adm-steps", type=int, default=2, help="adm: coarse steps evolved before the integrals")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -248,6 +249,9 @@ def main():
         return
     if args.case == "robust-stability":
         robust_stability_case(torch, sk, args)
+        return
+    if args.case == "adm":
+        adm_case(torch, sk, args)
         return
 
     h = hierarchy()
@@ -400,6 +404,55 @@ def zsym_case(torch, sk, args):
         del g
         torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
+
+
+def adm_case(torch, sk, args):
+    """ADM mass, J_z and linear momentum (Sec. 2.3, Sec. 3.2) on coordinate
+    spheres of the 7-level binary (mixed precision) after --adm-steps coarse
+    steps: the GPU's values, the oracle's on the downloaded state, and the
+    time per call of the GPU integral (64 x 128 sphere points; CUDA events on
+    the grid's stream, the call returns its five numbers to the host) next to
+    the oracle's time on the host cores.  Brill-Lindquist data: M -> m1 + m2
+    = 1 as r grows, J_z = P = 0."""
+    import initial_data as idd
+    import oracle
+    h = hierarchy()
+    g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(courant=args.courant, precision=1),
+                stream=torch.cuda.Stream())
+    g.set_initial_data(1, h.masses, h.positions)
+    for _ in range(args.adm_steps):
+        g.level_step(0)
+    torch.cuda.synchronize()
+    nt, nph, reps = 64, 128, 20
+    rows = []
+    for pid, r in ((0, 100.0), (0, 150.0), (1, 40.0), (1, 80.0)):
+        p = h.patches[pid]
+        for _ in range(3):
+            vg = g.adm_integrals(pid, (0.0, 0.0, 0.0), r, nt, nph)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(g.stream)
+        for _ in range(reps):
+            vg = g.adm_integrals(pid, (0.0, 0.0, 0.0), r, nt, nph)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / reps
+        ms = e0.elapsed_time(e1) / reps
+        u = g.download_fields(pid)
+        t0 = time.perf_counter()
+        vo = oracle.adm_integrals(p, u, (0.0, 0.0, 0.0), r, nt, nph)
+        to = time.perf_counter() - t0
+        scale = max(abs(v) for v in vo)
+        rows.append({"patch": pid, "level": p.level, "dx": p.dx, "r": r, "gpu": list(vg), "oracle": list(vo),
+                     "max_abs_diff_over_max": max(abs(a - b) for a, b in zip(vg, vo)) / scale,
+                     "gpu_ms_per_call": ms, "gpu_wall_ms_per_call": wall * 1e3,
+                     "sphere_points_per_s": nt * nph / (ms * 1e-3), "oracle_ms_per_call": to * 1e3,
+                     "oracle_threads": 1})
+    print(json.dumps({"case": "adm", "coarse_steps": args.adm_steps, "time": g.level_time(0),
+                      "ntheta": nt, "nphi": nph, "rows": rows}), flush=True)
+    g.close()
 
 
 def _gw_grid(torch, sk, n, precision, **prm):

@@ -156,6 +156,26 @@ sacrak_status sacrak_level_step(sacrak_grid* grid, int level);
 sacrak_status sacrak_constraints(sacrak_grid* grid, int level, double w_excise,
                                  double out_l2[4]);
 
+/* ADM mass, angular momentum about z (Sec. 2.3) and linear momentum
+ * (Sec. 3.2) on the coordinate sphere |x - centre| = radius of one patch's
+ * current time level (FP64 in both precisions), with the proper surface
+ * element dS_i = sqrt(g) n_i r^2 dOmega:
+ *   out[0]   = M   = 1/(16 pi) int g^ik g^jl (d_j g_kl - d_k g_jl) dS_i
+ *   out[1]   = J_z = 1/(8 pi)  int (x K_y^j - y K_x^j) dS_j
+ *   out[2+i] = P_i = 1/(8 pi)  int (K_i^j - delta_i^j K) dS_j
+ * (x, y relative to centre; g_ij = gt_ij / W^2, K_ij = (At_ij + gt_ij K/3) / W^2,
+ * K = Khat + 2 Theta).  The integrands are formed at cell centres with the
+ * 4th-order centred first derivative, interpolated to the sphere from the
+ * 4 x 4 x 4 nearest cell centres (tricubic Lagrange) and integrated with
+ * ntheta Gauss-Legendre nodes in cos(theta) (1..1024) times nphi equally
+ * spaced phi points (1..2^20).  centre and out are host pointers; the call
+ * returns when out is written.  Ghost cells are read, so a sphere closer than
+ * 5 cells to the active region's edge needs current ghosts.  SACRAK_EINVAL
+ * for bad arguments or when a sphere point's stencil would leave the array
+ * (some cell within 2 cells of its edge); out is then not written. */
+sacrak_status sacrak_adm_integrals(sacrak_grid* grid, int patch, const double centre[3],
+                                   double radius, int ntheta, int nphi, double out[5]);
+
 /* max over all points (ghosts included) and fields of |f(x,y,z) - s_f f(-x,-y,z)|
  * for one patch centred on x = y = 0 (Sec. 3.2). */
 sacrak_status sacrak_pi_symmetry(sacrak_grid* grid, int patch, double* max_abs_diff);

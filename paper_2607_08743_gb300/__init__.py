@@ -29,7 +29,7 @@ EXPORTS = [
     "sacrak_upload_fields", "sacrak_download_fields", "sacrak_rhs", "sacrak_rk4_step",
     "sacrak_level_step", "sacrak_constraints", "sacrak_pi_symmetry", "sacrak_level_time",
     "sacrak_last_error", "sacrak_profile_enable", "sacrak_profile_read", "sacrak_constraints_noalloc",
-    "sacrak_set_stage_kernel", "sacrak_get_stage_kernel", "sacrak_autotune",
+    "sacrak_set_stage_kernel", "sacrak_get_stage_kernel", "sacrak_autotune", "sacrak_adm_integrals",
 ]
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
@@ -264,6 +264,16 @@ class Grid:
         self._check(lib().sacrak_constraints(self._h, level, w_excise,
                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "constraints")
         return out
+
+    def adm_integrals(self, patch: int, centre=(0.0, 0.0, 0.0), radius: float = 1.0, ntheta: int = 24,
+                      nphi: int = 48):
+        """(M_ADM, J_z, P_x, P_y, P_z) on the sphere |x - centre| = radius of
+        the patch."""
+        c = (ctypes.c_double * 3)(*[float(v) for v in centre])
+        out = (ctypes.c_double * 5)()
+        self._check(lib().sacrak_adm_integrals(self._h, patch, c, ctypes.c_double(radius), ntheta, nphi, out),
+                    "adm_integrals")
+        return tuple(float(v) for v in out)
 
     def pi_symmetry(self, patch: int = 0) -> float:
         v = ctypes.c_double()

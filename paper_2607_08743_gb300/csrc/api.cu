@@ -85,6 +85,7 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed,
   L.results = off;
   off = align_up(off + 64 * sizeof(double), 256);
   L.scratch_doubles = maxtiles_level * 5 > maxpts / 256 + 1 ? maxtiles_level * 5 : maxpts / 256 + 1;
+  if (L.scratch_doubles < 6 * (size_t)ADM_MAX_THETA) L.scratch_doubles = 6 * (size_t)ADM_MAX_THETA;
   L.scratch = off;
   off = align_up(off + L.scratch_doubles * sizeof(double), 256);
   // mixed precision: FP32 derivative planes of the split stage kernel, for
@@ -982,6 +983,35 @@ sacrak_status sacrak_constraints(sacrak_grid* g, int level, double w_excise, dou
   st = sync_and_check(g);
   if (st != SACRAK_OK) return st;
   for (int c = 0; c < 4; ++c) out_l2[c] = sums[4] > 0 ? std::sqrt(sums[c] / sums[4]) : 0.0;
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_adm_integrals(sacrak_grid* g, int patch, const double centre[3], double radius,
+                                   int ntheta, int nphi, double out[5]) {
+  if (!g) return SACRAK_EINVAL;
+  if (patch < 0 || patch >= g->npatches || !centre || !out || !(radius > 0.0) || !std::isfinite(radius) ||
+      ntheta < 1 || ntheta > ADM_MAX_THETA || nphi < 1 || nphi > (1 << 20) || !std::isfinite(centre[0]) ||
+      !std::isfinite(centre[1]) || !std::isfinite(centre[2]))
+    return fail(g, SACRAK_EINVAL, "bad arguments");
+  AdmArgs a;
+  a.patches = g->d_patches;
+  a.levels = g->d_levels;
+  a.patch = patch;
+  a.ntheta = ntheta;
+  a.nphi = nphi;
+  for (int d = 0; d < 3; ++d) a.c[d] = centre[d];
+  a.r = radius;
+  a.ring = g->d_scratch;
+  launch_adm(a, g->d_results, g->stream);
+  sacrak_status st = check_launch(g);
+  if (st != SACRAK_OK) return st;
+  double v[6];
+  CK(cudaMemcpyAsync(v, g->d_results, sizeof v, cudaMemcpyDeviceToHost, g->stream));
+  st = sync_and_check(g);
+  if (st != SACRAK_OK) return st;
+  if (v[5] != 0.0)
+    return fail(g, SACRAK_EINVAL, "%.0f sphere points within 2 cells of the edge of patch %d", v[5], patch);
+  for (int c = 0; c < 5; ++c) out[c] = v[c];
   return SACRAK_OK;
 }
 

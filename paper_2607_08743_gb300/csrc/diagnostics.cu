@@ -161,4 +161,198 @@ int launch_pi_symmetry(const DevPatch* p, const DevLevel* l, int patch, long lon
   return nb;
 }
 
+// ---------------------------------------------------------------------------
+// ADM mass, angular momentum (Sec. 2.3) and linear momentum (Sec. 3.2) on the
+// coordinate sphere |x - c| = r, with the proper surface element
+// dS_i = sqrt(g) n_i r^2 dOmega:
+//   M   = 1/(16 pi) int g^ik g^jl (d_j g_kl - d_k g_jl) dS_i
+//   J_z = 1/(8 pi)  int (x K_y^j - y K_x^j) dS_j
+//   P_i = 1/(8 pi)  int (K_i^j - delta_i^j K) dS_j
+// The integrands are formed at cell centres from g_ij = gt_ij / W^2 and
+// K_ij = (At_ij + gt_ij K / 3) / W^2 (K = Khat + 2 Theta) with 4th-order
+// centred derivatives, interpolated to the sphere with the 4 x 4 x 4 nearest
+// cell centres (tricubic Lagrange), and integrated with Gauss-Legendre nodes
+// in cos(theta) times the trapezoid rule in phi.  One block per theta ring;
+// every sum runs in a fixed order.
+
+// Node i (descending in x) and weight of the n-point Gauss-Legendre rule on
+// [-1, 1]: Newton's method on P_n, evaluated with the three-term recurrence
+// (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}, from cos(pi (4i+3)/(4n+2)).
+__device__ void gauss_legendre_node(int n, int i, double& x, double& w) {
+  double z = cospi((4.0 * i + 3.0) / (4.0 * n + 2.0)), dpn = 1.0;
+  for (int it = 0; it < 64; ++it) {
+    double pkm1 = 1.0, pk = z;
+    for (int k = 1; k < n; ++k) {
+      const double pk1 = ((2.0 * k + 1.0) * z * pk - k * pkm1) / (k + 1.0);
+      pkm1 = pk;
+      pk = pk1;
+    }
+    dpn = n * (z * pk - pkm1) / (z * z - 1.0);  // P_n'(z) = n (z P_n - P_{n-1}) / (z^2 - 1)
+    const double step = pk / dpn;
+    z -= step;
+    if (fabs(step) < 1e-16) break;
+  }
+  x = z;
+  w = 2.0 / ((1.0 - z * z) * dpn * dpn);
+}
+
+// Integrands per coordinate area at array offset q: mass flux density m^i,
+// kk[i][j] = sqrt(g) K_i^j and sk = sqrt(g) K.
+__device__ void adm_cell_integrands(const double* __restrict__ u, long long fs, long long q,
+                                   const long long st[3], double ih12, double m[3], double kk[3][3],
+                                   double& sk) {
+  const double W = __ldg(u + F_W * fs + q), W2 = W * W;
+  double gt[6], At[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    gt[a] = __ldg(u + (F_GXX + a) * fs + q);
+    At[a] = __ldg(u + (F_AXX + a) * fs + q);
+  }
+  // conformal inverse from the adjugate
+  const double a0 = gt[3] * gt[5] - gt[4] * gt[4], a1 = gt[2] * gt[4] - gt[1] * gt[5],
+               a2 = gt[1] * gt[4] - gt[2] * gt[3];
+  const double det = gt[0] * a0 + gt[1] * a1 + gt[2] * a2, idet = 1.0 / det;
+  const double gtu[6] = {a0 * idet, a1 * idet, a2 * idet, (gt[0] * gt[5] - gt[2] * gt[2]) * idet,
+                         (gt[1] * gt[2] - gt[0] * gt[4]) * idet, (gt[0] * gt[3] - gt[1] * gt[1]) * idet};
+  constexpr int S[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  // d_k g_ij = (d_k gt_ij - 2 gt_ij d_k W / W) / W^2; physical g^ij = W^2 gt^ij
+  double dg[3][6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double dWW = d1u(u + F_W * fs, q, st[d]) * ih12 / W;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+      dg[d][a] = (d1u(u + (F_GXX + a) * fs, q, st[d]) * ih12 - 2.0 * gt[a] * dWW) / W2;
+  }
+  // m^i = sqrt(g) g^ik (g^jl d_j g_kl - g^jl d_k g_jl)
+  double v[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) s += gtu[S[j][l]] * (dg[j][S[k][l]] - dg[k][S[j][l]]);
+    v[k] = W2 * s;
+  }
+  const double sg = sqrt(det) / (W2 * W);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    m[i] = sg * W2 * (gtu[S[i][0]] * v[0] + gtu[S[i][1]] * v[1] + gtu[S[i][2]] * v[2]);
+  // K_i^j = gt^jk (At_ik + gt_ik K / 3)  (the W^2 factors cancel)
+  const double K = __ldg(u + F_KH * fs + q) + 2.0 * __ldg(u + F_TH * fs + q), K3 = K / 3.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double a = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) a += gtu[S[j][k]] * (At[S[i][k]] + gt[S[i][k]] * K3);
+      kk[i][j] = sg * a;
+    }
+  sk = sg * K;
+}
+
+// cubic Lagrange basis on the nodes 0, 1, 2, 3 at position s
+__device__ __forceinline__ void cubic_weights(double s, double w[4]) {
+  const double s1 = s - 1.0, s2 = s - 2.0, s3 = s - 3.0;
+  w[0] = -s1 * s2 * s3 / 6.0;
+  w[1] = s * s2 * s3 / 2.0;
+  w[2] = -s * s1 * s3 / 2.0;
+  w[3] = s * s1 * s2 / 6.0;
+}
+
+constexpr int ADM_THREADS = 128;
+constexpr int ADM_NQ = 6;  // M, J_z, P_x, P_y, P_z, points outside
+
+__global__ void __launch_bounds__(ADM_THREADS) adm_ring_kernel(AdmArgs A) {
+  __shared__ double node[2];
+  __shared__ double red[ADM_NQ][ADM_THREADS];
+  const int it = blockIdx.x;
+  if (threadIdx.x == 0) {
+    double x, w;
+    gauss_legendre_node(A.ntheta, it, x, w);
+    node[0] = x;
+    node[1] = w;
+  }
+  __syncthreads();
+  const DevPatch* P = A.patches + A.patch;
+  const double* __restrict__ u = P->buf[A.levels[P->level].ring];
+  const long long st[3] = {1, P->px, P->plane};
+  const int N[3] = {P->NX, P->NY, P->NZ};
+  const double ih12 = 1.0 / (12.0 * P->dx);
+  const double ct = node[0], sth = sqrt((1.0 - ct) * (1.0 + ct));
+  double acc[ADM_NQ] = {0, 0, 0, 0, 0, 0};
+  for (int ip = threadIdx.x; ip < A.nphi; ip += ADM_THREADS) {
+    double sp, cp;
+    sincospi(2.0 * ip / A.nphi, &sp, &cp);
+    const double n[3] = {sth * cp, sth * sp, ct};
+    double wl[3][4];
+    int i0[3];
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double x = A.c[d] + A.r * n[d];
+      const double t = (x - P->origin[d]) / P->dx - 0.5 + GH;  // array coordinate
+      ok = ok && t >= 3.0 && t < N[d] - 4.0;  // 4 interpolation cells +- 2 derivative cells inside
+      i0[d] = ok ? (int)floor(t) - 1 : 0;
+      cubic_weights(ok ? t - i0[d] : 0.0, wl[d]);
+    }
+    if (!ok) {
+      acc[5] += 1.0;
+      continue;
+    }
+    double m[3] = {0, 0, 0}, kk[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, sk = 0.0;
+    for (int c = 0; c < 4; ++c)
+      for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+          const long long q = (i0[0] + a) + (i0[1] + b) * st[1] + (i0[2] + c) * st[2];
+          double mc[3], kc[3][3], skc;
+          adm_cell_integrands(u, P->fstride, q, st, ih12, mc, kc, skc);
+          const double w = wl[0][a] * wl[1][b] * wl[2][c];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            m[d] += w * mc[d];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) kk[d][e] += w * kc[d][e];
+          }
+          sk += w * skc;
+        }
+    const double rx = A.r * n[0], ry = A.r * n[1];
+    acc[0] += m[0] * n[0] + m[1] * n[1] + m[2] * n[2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) acc[1] += (rx * kk[1][d] - ry * kk[0][d]) * n[d];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      acc[2 + i] += kk[i][0] * n[0] + kk[i][1] * n[1] + kk[i][2] * n[2] - sk * n[i];
+  }
+#pragma unroll
+  for (int c = 0; c < ADM_NQ; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int o = ADM_THREADS / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int c = 0; c < ADM_NQ; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < ADM_NQ)
+    A.ring[threadIdx.x * A.ntheta + it] = (threadIdx.x < 5 ? node[1] : 1.0) * red[threadIdx.x][0];
+}
+
+// rings in order; dS = r^2 dcos(theta) dphi with dphi = 2 pi / nphi
+__global__ void adm_sum_kernel(const double* ring, int ntheta, int nphi, double r, double* out) {
+  if (threadIdx.x >= ADM_NQ) return;
+  const int c = threadIdx.x;
+  double s = 0.0;
+  for (int i = 0; i < ntheta; ++i) s += ring[c * ntheta + i];
+  // (2 pi / nphi) r^2 / (16 pi) for M, / (8 pi) for J and P
+  const double f = c == 0 ? r * r / (8.0 * nphi) : (c < 5 ? r * r / (4.0 * nphi) : 1.0);
+  out[c] = s * f;
+}
+
+void launch_adm(const AdmArgs& a, double* out3, cudaStream_t st) {
+  adm_ring_kernel<<<a.ntheta, ADM_THREADS, 0, st>>>(a);
+  adm_sum_kernel<<<1, 32, 0, st>>>(a.ring, a.ntheta, a.nphi, a.r, out3);
+}
+
 }  // namespace sacrak

@@ -271,6 +271,18 @@ struct InitArgs {
   double lo[3];  // level-0 origin (origin of level-global cell indices)
 };
 
+// ADM surface integrals on the sphere |x - c| = r of one patch's current time
+// level: ring holds 6 * ntheta doubles (per-ring M, J_z, P_x, P_y, P_z and
+// points whose stencil leaves the array)
+constexpr int ADM_MAX_THETA = 1024;
+struct AdmArgs {
+  const DevPatch* patches;
+  const DevLevel* levels;
+  int patch, ntheta, nphi;
+  double c[3], r;
+  double* ring;
+};
+
 // launchers (host)
 void launch_stage_fp64(const StageArgs& a, cudaStream_t st);
 void launch_stage_mixed(const StageArgs& a, cudaStream_t st);
@@ -293,6 +305,8 @@ void launch_level_advance(DevLevel* L, double dt, cudaStream_t st);
 void launch_repack(double* dst, const double* src, long long rows, int NX, int px, int to_pitched,
                    cudaStream_t st);
 void launch_init(const InitArgs& a, int patch, long long tot, cudaStream_t st);
+// out6 = {M, J_z, P_x, P_y, P_z, points outside}
+void launch_adm(const AdmArgs& a, double* out6, cudaStream_t st);
 void launch_symmetrise(const DevPatch* p, const DevLevel* l, int patch, long long half_tot,
                        cudaStream_t st);
 int launch_pi_symmetry(const DevPatch* p, const DevLevel* l, int patch, long long tot,
