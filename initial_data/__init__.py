@@ -283,6 +283,17 @@ def small_binary(n_fixed: int = 24, n_moving: int = 16, n_levels: int = 4, n_fix
                       [(sep, 0.0, 0.0), (-sep, 0.0, 0.0)])
 
 
+def moving_binary_3_level() -> Hierarchy:
+    """3 levels with room for the moving patches: L0 32^3 (dx 1), L1 two
+    24^3 (dx 1/2) and L2 two 16^3 (dx 1/4) centred on Brill-Lindquist
+    punctures m = 0.5 at (+-3, 0, 0)."""
+    pos = [(3.0, 0.0, 0.0), (-3.0, 0.0, 0.0)]
+    levels = [[centred_patch(32, 1.0, level=0)],
+              [centred_patch(24, 0.5, centre=c, level=1) for c in pos],
+              [centred_patch(16, 0.25, centre=c, level=2) for c in pos]]
+    return Hierarchy(dx0=1.0, levels=levels, masses=[0.5, 0.5], positions=pos)
+
+
 def nesting_ok(h: Hierarchy, margin: int = 4) -> bool:
     """Every patch of level l > 0 lies inside a patch of level l-1, aligned with
     its cell faces, with at least `margin` parent cells around it."""

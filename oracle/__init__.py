@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import math
 import os
 import subprocess
 import threading
@@ -105,6 +106,10 @@ def lib():
             L.orc_adm_integrals.argtypes = [P(_OrcPatch), dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
             L.orc_adm_integrals.restype = ctypes.c_int
             L.orc_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
+            L.orc_move_patch.argtypes = [P(_OrcPatch), dp, P(_OrcPatch), dp, P(_OrcPatch), dp, ctypes.c_int]
+            L.orc_move_patch.restype = ctypes.c_int
+            L.orc_interp_point.argtypes = [P(_OrcPatch), dp, ctypes.c_int, dp, dp]
+            L.orc_interp_point.restype = ctypes.c_int
             L.orc_stencils.argtypes = [P(_OrcPatch), dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, dp, dp]
             _lib = L
@@ -245,6 +250,27 @@ def adm_integrals(p, u: np.ndarray, centre, radius: float, ntheta: int = 24, nph
     return tuple(float(v) for v in out)
 
 
+def move_patch(parent, up: np.ndarray, old, uo: np.ndarray, new, skip_zlower: bool = False) -> np.ndarray:
+    """Data of a patch shifted from geometry `old` to `new` (Sec. 2.2.1)."""
+    up = np.ascontiguousarray(up, dtype=np.float64)
+    uo = np.ascontiguousarray(uo, dtype=np.float64)
+    un = np.zeros(new.shape)
+    rc = lib().orc_move_patch(ctypes.byref(_cp(parent)), _ptr(up), ctypes.byref(_cp(old)), _ptr(uo),
+                              ctypes.byref(_cp(new)), _ptr(un), int(skip_zlower))
+    if rc != 0:
+        raise ValueError("shifted patch misaligned or its prolongation leaves the parent")
+    return un
+
+
+def interp_point(p, u: np.ndarray, f: int, x) -> float:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty(1)
+    if lib().orc_interp_point(ctypes.byref(_cp(p)), _ptr(u), int(f), _ptr(xx), _ptr(out)) != 0:
+        raise ValueError("interpolation stencil leaves the active cells")
+    return float(out[0])
+
+
 def gauss_legendre(n: int):
     x = np.empty(n)
     w = np.empty(n)
@@ -308,6 +334,9 @@ class BOHierarchy:
             for pid, s in enumerate(previous):
                 self.tl[pid].insert(0, np.array(s, dtype=np.float64, copy=True))
         self.nsteps = [0] * len(hierarchy.levels)
+        self.punct = []                          # puncture positions
+        self.follow = [-1] * len(self.patches)   # puncture each patch follows
+        self.track_patch = []                    # the patch that tracks each puncture
 
     def _find_parent(self, pid, l):
         c = self.patches[pid]
@@ -321,6 +350,141 @@ class BOHierarchy:
 
     def dt(self, l):
         return self.courant * self.h.dx0 / (2 ** l)
+
+    # ---- moving boxes (Sec. 2.2.1) ----
+
+    def track(self, positions, follow):
+        """Punctures at `positions`; follow[pid] = the puncture patch pid
+        follows (-1: none).  Puncture p is tracked on the finest patch that
+        follows it: after every step of that patch, dx/dt = -beta(x) is
+        integrated over the step with Heun's method, beta interpolated
+        (tricubic) from the step's old and new time levels."""
+        self.punct = [np.array(x, dtype=np.float64) for x in positions]
+        self.follow = [int(v) for v in follow]
+        self.track_patch = []
+        for p in range(len(self.punct)):
+            best = None
+            for pid, q in enumerate(self.follow):
+                if q == p and (best is None or self.patches[pid].level > self.patches[best].level):
+                    best = pid
+            self.track_patch.append(best)
+
+    def _track(self, l):
+        for p, pid in enumerate(self.track_patch):
+            if pid is None or self.patches[pid].level != l:
+                continue
+            pa, dt = self.patches[pid], self.dt(l)
+            u0, u1 = self.tl[pid][-2], self.tl[pid][-1]
+            x = self.punct[p]
+            b0 = np.array([interp_point(pa, u0, 19 + d, x) for d in range(3)])
+            xs = x - dt * b0
+            b1 = np.array([interp_point(pa, u1, 19 + d, xs) for d in range(3)])
+            self.punct[p] = x - 0.5 * dt * (b0 + b1)
+
+    def synchronised(self) -> bool:
+        return all(self.nsteps[l] == self.nsteps[0] * 2 ** l for l in range(len(self.nsteps)))
+
+    def _children(self, pid):
+        return [q for q, par in enumerate(self.parent) if par == pid]
+
+    def _nest_lo(self, c, par, d, off):
+        """Smallest offset (parent cells) of child c along d inside par."""
+        zlow = self.zsym and d == 2 and touches_equator(c) and touches_equator(par) and off == 0
+        return 0 if zlow else 4
+
+    def _shift_range(self, pid, geoms, kids):
+        """Per axis the shifts (parent cells) that keep patch pid nested in
+        its parent geoms[parent] and the children `kids` (at their geoms)
+        nested in it; under equatorial symmetry no patch moves along z
+        (punctures on the equator stay there)."""
+        c = geoms[pid]
+        par = geoms[self.parent[pid]]
+        lo, hi = [], []
+        for d in range(3):
+            off = int(round((c.origin[d] - par.origin[d]) / par.dx))
+            a = self._nest_lo(c, par, d, off) - off
+            b = par.n[d] - 4 - c.n[d] // 2 - off
+            for kid in kids:
+                k = geoms[kid]
+                koff = int(round((k.origin[d] - c.origin[d]) / c.dx))
+                # the child's offset becomes koff - 2 s
+                a = max(a, -((c.n[d] - 4 - k.n[d] // 2 - koff) // 2))
+                b = min(b, (koff - self._nest_lo(k, c, d, koff)) // 2)
+            if self.zsym and d == 2:
+                a = b = 0
+            lo.append(a)
+            hi.append(b)
+        return lo, hi
+
+    def shift_range(self, pid):
+        return self._shift_range(pid, self.patches, self._children(pid))
+
+    def _shifted(self, c, shift):
+        return dataclasses.replace(c, origin=tuple(c.origin[d] + (2 * int(shift[d])) * c.dx for d in range(3)))
+
+    def _apply_move(self, pid, shift):
+        c = self.patches[pid]
+        new = self._shifted(c, shift)
+        ppid = self.parent[pid]
+        skip = self.zsym and touches_equator(c)
+        un = move_patch(self.patches[ppid], self.tl[ppid][-1], c, self.tl[pid][-1], new, skip_zlower=skip)
+        if skip:
+            un = fill_zreflect(new, un)
+        self.patches[pid] = new
+        for q in self.level_ids[new.level]:
+            self.tl[q] = [self.tl[q][-1]]
+        self.tl[pid] = [un]
+
+    def move_patch(self, pid, shift):
+        """Shift patch pid by shift[d] parent cells (2 shift[d] of its own):
+        cells that were active keep their values, the others are prolonged
+        from the parent's current time level; the time-level history of the
+        patch's level restarts (its older levels no longer cover the patch).
+        The shift must keep the patch and its children nested."""
+        if not self.synchronised():
+            raise ValueError("levels not synchronised")
+        lo, hi = self.shift_range(pid)
+        if any(not (lo[d] <= shift[d] <= hi[d]) for d in range(3)):
+            raise ValueError("shift breaks the nesting")
+        self._apply_move(pid, shift)
+
+    def regrid(self) -> int:
+        """Coarse to fine, every patch that follows a puncture moves by
+        trunc((x_p - centre) / dx_parent) parent cells per axis (the puncture
+        then lies within one parent cell of its centre), clamped so that it
+        stays nested in its parent's new position and keeps its children
+        that follow no puncture nested.  The whole plan is checked before
+        any data moves.  Returns the number of patches moved."""
+        if not self.synchronised():
+            raise ValueError("levels not synchronised")
+        geoms = list(self.patches)
+        plan = []
+        for l in range(1, len(self.level_ids)):
+            for pid in self.level_ids[l]:
+                p = self.follow[pid]
+                if p < 0:
+                    continue
+                c = geoms[pid]
+                dxp = 2.0 * c.dx
+                s = [int(math.trunc((self.punct[p][d] - (c.origin[d] + 0.5 * c.n[d] * c.dx)) / dxp))
+                     for d in range(3)]
+                fixed_kids = [q for q in self._children(pid) if self.follow[q] < 0]
+                lo, hi = self._shift_range(pid, geoms, fixed_kids)
+                if any(lo[d] > hi[d] for d in range(3)):
+                    raise ValueError("patch %d cannot stay nested" % pid)
+                s = [min(max(s[d], lo[d]), hi[d]) for d in range(3)]
+                if any(s):
+                    geoms[pid] = self._shifted(c, s)
+                    plan.append((pid, s))
+        for pid in range(len(geoms)):  # the final configuration nests
+            if self.parent[pid] is None:
+                continue
+            lo, hi = self._shift_range(pid, geoms, self._children(pid))
+            if any(not (lo[d] <= 0 <= hi[d]) for d in range(3)):
+                raise ValueError("regrid would break the nesting of patch %d" % pid)
+        for pid, s in plan:
+            self._apply_move(pid, s)
+        return len(plan)
 
     def current(self, pid) -> np.ndarray:
         return self.tl[pid][-1]
@@ -385,6 +549,7 @@ class BOHierarchy:
             self.tl[pid].append(cur[a])
             if len(self.tl[pid]) > 3:
                 self.tl[pid].pop(0)
+        self._track(l)
         self.nsteps[l] += 1
 
     def level_step(self, l=0, frac0=0.0, dfrac=1.0):

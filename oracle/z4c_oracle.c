@@ -940,8 +940,68 @@ int orc_prolong_ghosts(const orc_patch* parent, const double* up, const orc_patc
   return orc_prolong_ghosts_ex(parent, up, child, uc, 0);
 }
 
+/* 6th-order prolongation of the parent's data onto the child's ghost cells
+ * (all_cells = 0) or onto every cell of the child's array (all_cells = 1). */
+static int prolong_cells(const orc_patch* parent, const double* up, const orc_patch* child, double* uc,
+                         int skip_zlower, int all_cells);
+
 int orc_prolong_ghosts_ex(const orc_patch* parent, const double* up, const orc_patch* child,
                           double* uc, int skip_zlower) {
+  return prolong_cells(parent, up, child, uc, skip_zlower, 0);
+}
+
+int orc_move_patch(const orc_patch* parent, const double* up, const orc_patch* oldc, const double* uo,
+                   const orc_patch* newc, double* un, int skip_zlower) {
+  int sh[3];
+  if (oldc->g != newc->g || fabs(oldc->dx - newc->dx) > 1e-14 * oldc->dx) return -1;
+  for (int d = 0; d < 3; ++d) {
+    if (oldc->n[d] != newc->n[d]) return -1;
+    const double t = (newc->origin[d] - oldc->origin[d]) / newc->dx;
+    const double r = floor(t + 0.5);
+    if (fabs(t - r) > 1e-9) return -1;
+    sh[d] = (int)r; /* new array index + sh = old array index */
+  }
+  if (prolong_cells(parent, up, newc, un, skip_zlower, 1)) return -1;
+  layout L = make_layout(newc);
+  const int g = newc->g;
+  for (int k = 0; k < L.NZ; ++k)
+    for (int j = 0; j < L.NY; ++j)
+      for (int i = 0; i < L.NX; ++i) {
+        const int io = i + sh[0], jo = j + sh[1], ko = k + sh[2];
+        if (io < g || io >= g + oldc->n[0] || jo < g || jo >= g + oldc->n[1] || ko < g ||
+            ko >= g + oldc->n[2])
+          continue; /* not an active cell of the old patch: keep the prolonged value */
+        const ptrdiff_t qn = i + j * L.s[1] + (ptrdiff_t)k * L.s[2];
+        const ptrdiff_t qo = io + jo * L.s[1] + (ptrdiff_t)ko * L.s[2];
+        for (int f = 0; f < NF; ++f) un[f * L.sf + qn] = uo[f * L.sf + qo];
+      }
+  return 0;
+}
+
+int orc_interp_point(const orc_patch* p, const double* u, int f, const double x[3], double* out) {
+  layout L = make_layout(p);
+  const int g = p->g;
+  static const int nodes[4] = {0, 1, 2, 3};
+  int i0[3];
+  double w[3][4];
+  for (int d = 0; d < 3; ++d) {
+    const double t = (x[d] - p->origin[d]) / p->dx - 0.5 + g; /* array coordinate */
+    if (!(t >= g + 1.0 && t < g + p->n[d] - 2.0)) return -1; /* 4 active cells */
+    i0[d] = (int)floor(t) - 1;
+    orc_lagrange_weights(4, nodes, t - i0[d], w[d]);
+  }
+  double v = 0.0;
+  for (int c = 0; c < 4; ++c)
+    for (int b = 0; b < 4; ++b)
+      for (int a = 0; a < 4; ++a)
+        v += w[0][a] * w[1][b] * w[2][c] *
+             u[f * L.sf + (i0[0] + a) + (i0[1] + b) * L.s[1] + (ptrdiff_t)(i0[2] + c) * L.s[2]];
+  *out = v;
+  return 0;
+}
+
+static int prolong_cells(const orc_patch* parent, const double* up, const orc_patch* child, double* uc,
+                         int skip_zlower, int all_cells) {
   int off[3];
   if (child_offset(parent, child, off)) return -1;
   layout Lp = make_layout(parent), Lc = make_layout(child);
@@ -964,7 +1024,7 @@ int orc_prolong_ghosts_ex(const orc_patch* parent, const double* up, const orc_p
   for (int kc = 0; kc < cdim[2]; ++kc)
     for (int jc = 0; jc < cdim[1]; ++jc)
       for (int ic = 0; ic < cdim[0]; ++ic) {
-        if (!is_ghost(child, ic, jc, kc)) continue;
+        if (!all_cells && !is_ghost(child, ic, jc, kc)) continue;
         if (skip_zlower && kc < gc) continue; /* left to the reflection */
         int ci[3] = {ic - gc, jc - gc, kc - gc};
         int base[3];

@@ -26,6 +26,9 @@
  *   orc_restrict        exact on degree <= 3, not on degree 4
  *   orc_exchange        brute force of the three overlap rules
  *   orc_lagrange_weights exact fractions (Fraction arithmetic)
+ *   orc_move_patch      copies equal the old cells, prolonged cells exact
+ *                       on degree-5 polynomials; shift and back restores
+ *   orc_interp_point    exact on tricubic polynomials
  *   orc_adm_integrals   Schwarzschild in isotropic coordinates: M psi(r)
  *                       (closed form) at 4th order in dx; Bowen-York spin:
  *                       J_z = J and boost: P = P for any conformal factor;
@@ -170,6 +173,18 @@ void orc_stencils(const orc_patch* p, const double* u, int field, int i, int j, 
 int orc_adm_integrals(const orc_patch* p, const double* u, const double c[3], double r, int ntheta, int nphi,
                       double out[5]);
 void orc_gauss_legendre(int n, double* x, double* w);
+
+/* Moving boxes (Sec. 2.2.1): the data of a patch shifted from geometry oldc
+ * to newc (same level and size, origins a whole number of cells apart):
+ * every cell of newc's array that is an active cell of oldc takes the old
+ * value, every other cell (ghosts included) the 6th-order prolongation of the
+ * parent data (as for ghosts; with skip_zlower the z < 0 ghost layers are
+ * left to the reflection).  -1 if misaligned or a stencil leaves the parent. */
+int orc_move_patch(const orc_patch* parent, const double* up, const orc_patch* oldc, const double* uo,
+                   const orc_patch* newc, double* un, int skip_zlower);
+/* Field f at point x: tricubic Lagrange interpolation from the 4 nearest
+ * cell centres per axis, all of them active cells; -1 otherwise. */
+int orc_interp_point(const orc_patch* p, const double* u, int f, const double x[3], double* out);
 
 /* Lagrange basis weights of a set of integer nodes at position x. */
 void orc_lagrange_weights(int nnodes, const int* nodes, double x, double* w);
