@@ -392,6 +392,17 @@ class BOHierarchy:
         zlow = self.zsym and d == 2 and touches_equator(c) and touches_equator(par) and off == 0
         return 0 if zlow else 4
 
+    def _active_overlap(self, l) -> bool:
+        """Do two patches of level l share active cells?"""
+        ids = self.level_ids[l]
+        for a in range(len(ids)):
+            for b in range(a + 1, len(ids)):
+                A, B = self.patches[ids[a]], self.patches[ids[b]]
+                off = [int(round((A.origin[d] - B.origin[d]) / A.dx)) for d in range(3)]
+                if all(off[d] < B.n[d] and off[d] + A.n[d] > 0 for d in range(3)):
+                    return True
+        return False
+
     def _shift_range(self, pid, geoms, kids):
         """Per axis the shifts (parent cells) that keep patch pid nested in
         its parent geoms[parent] and the children `kids` (at their geoms)
@@ -434,12 +445,21 @@ class BOHierarchy:
         for q in self.level_ids[new.level]:
             self.tl[q] = [self.tl[q][-1]]
         self.tl[pid] = [un]
+        # where the parent level's patches share active cells, the exchange
+        # at the start of each of its steps averages them in its stored time
+        # levels, and the older levels the moved patch's ghosts would be
+        # interpolated from are no longer those of its last steps: that
+        # level's history restarts too
+        if self._active_overlap(new.level - 1):
+            for q in self.level_ids[new.level - 1]:
+                self.tl[q] = [self.tl[q][-1]]
 
     def move_patch(self, pid, shift):
         """Shift patch pid by shift[d] parent cells (2 shift[d] of its own):
         cells that were active keep their values, the others are prolonged
         from the parent's current time level; the time-level history of the
-        patch's level restarts (its older levels no longer cover the patch).
+        patch's level restarts (its older levels no longer cover the patch),
+        and so does the parent level's where its patches share active cells.
         The shift must keep the patch and its children nested."""
         if not self.synchronised():
             raise ValueError("levels not synchronised")

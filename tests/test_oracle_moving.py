@@ -176,3 +176,19 @@ def test_regrid_recentres_and_nests():
         assert np.array_equal(bo.current(pid)[(slice(None),) + sl_new], before[pid][(slice(None),) + sl_old])
     # a second regrid has nothing to do
     assert bo.regrid() == 0
+
+
+def test_move_restarts_histories():
+    """The moved patch's level always restarts its time-level history; the
+    parent level only where its patches share active cells (the two level-1
+    patches of this hierarchy overlap by 12 cells)."""
+    h = idd.moving_binary_3_level()
+    bo = oracle.BOHierarchy(h, idd.hierarchy_data(h), oracle.Params(), courant=0.5)
+    bo.level_step(0)
+    assert [len(bo.tl[i]) for i in range(5)] == [2, 3, 3, 3, 3]
+    assert bo._active_overlap(1) and not bo._active_overlap(2)
+    bo.move_patch(3, (1, 0, 0))
+    assert [len(bo.tl[i]) for i in range(5)] == [2, 1, 1, 1, 1]
+    bo.level_step(0)
+    bo.move_patch(1, (-1, 0, 0))  # level 0 (one patch) keeps its history
+    assert [len(bo.tl[i]) for i in range(5)] == [3, 1, 1, 3, 3]
