@@ -156,6 +156,53 @@ sacrak_status sacrak_level_step(sacrak_grid* grid, int level);
 sacrak_status sacrak_constraints(sacrak_grid* grid, int level, double w_excise,
                                  double out_l2[4]);
 
+/* ---- Moving boxes (Sec. 2.2.1) ----
+ * Punctures are tracked by integrating dx/dt = -beta^i(x); the patches that
+ * follow them are shifted in steps of two of their cells (one parent cell),
+ * which keeps parent and child cell faces aligned, and the region a shifted
+ * patch newly covers is prolonged from its parent. */
+
+/* Up to 8 punctures at pos[3 p .. 3 p + 2] (host array); follow[patch] (host
+ * array of npatches entries) is the puncture that patch follows, -1 for
+ * none (level-0 patches cannot follow).  Each puncture must be followed by
+ * some patch; it is tracked on the finest of them (the first of equal
+ * level): after every step of that patch's level, inside the captured
+ * coarse step, x <- x - dt/2 (beta_n(x) + beta_{n+1}(x - dt beta_n(x)))
+ * (Heun's method), beta interpolated tricubically from the 4 x 4 x 4 nearest
+ * active cell centres of the old and new time levels.  A puncture whose
+ * stencil would leave the active cells keeps its position and the next
+ * synchronising call returns SACRAK_EINVAL once.  npunct = 0 stops tracking.
+ * Synchronises the stream. */
+sacrak_status sacrak_track_punctures(sacrak_grid* grid, int npunct, const double* pos, const int* follow);
+
+/* Current puncture positions into pos[3 * npunct] (host); synchronises. */
+sacrak_status sacrak_get_punctures(sacrak_grid* grid, double* pos);
+
+/* Shift patch (level > 0) by shift[d] cells of its parent (2 shift[d] of its
+ * own) while all levels are at the same time (between coarse steps): cells
+ * that were active keep their values, every other cell of the patch's
+ * current time level (ghosts included) is the 6th-order prolongation of the
+ * parent's current time level; the parent offsets of its children follow.
+ * The time-level history of the patch's level restarts (the ghosts of its
+ * children are interpolated linearly in time during its next step, as at
+ * the start of a run) and the captured coarse step is rebuilt at the next
+ * sacrak_level_step.  SACRAK_EINVAL unless the patch and its children stay
+ * nested (4 parent cells of margin; under equatorial symmetry no shift along
+ * z).  Synchronises. */
+sacrak_status sacrak_move_patch(sacrak_grid* grid, int patch, const int shift[3]);
+
+/* Lower face of active cell 0 of a patch (host array of 3), as moved. */
+sacrak_status sacrak_patch_origin(sacrak_grid* grid, int patch, double origin[3]);
+
+/* Regrid between coarse steps: coarse to fine, every patch that follows a
+ * puncture is shifted by trunc((x_p - centre) / dx_parent) parent cells per
+ * axis (the puncture then lies within one parent cell of the patch centre),
+ * clamped so that it nests in its parent's new position and keeps its
+ * children that follow no puncture nested; the whole plan is checked before
+ * any data moves (SACRAK_EINVAL and nothing moved if the result would not
+ * nest).  *moved = patches shifted.  Synchronises. */
+sacrak_status sacrak_regrid(sacrak_grid* grid, int* moved);
+
 /* ADM mass, angular momentum about z (Sec. 2.3) and linear momentum
  * (Sec. 3.2) on the coordinate sphere |x - centre| = radius of one patch's
  * current time level (FP64 in both precisions), with the proper surface

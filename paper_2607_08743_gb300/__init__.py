@@ -30,6 +30,8 @@ EXPORTS = [
     "sacrak_level_step", "sacrak_constraints", "sacrak_pi_symmetry", "sacrak_level_time",
     "sacrak_last_error", "sacrak_profile_enable", "sacrak_profile_read", "sacrak_constraints_noalloc",
     "sacrak_set_stage_kernel", "sacrak_get_stage_kernel", "sacrak_autotune", "sacrak_adm_integrals",
+    "sacrak_track_punctures", "sacrak_get_punctures", "sacrak_move_patch", "sacrak_regrid",
+    "sacrak_patch_origin",
 ]
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
@@ -264,6 +266,37 @@ class Grid:
         self._check(lib().sacrak_constraints(self._h, level, w_excise,
                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "constraints")
         return out
+
+    def track_punctures(self, positions, follow):
+        """Track punctures at `positions` (N x 3); follow[patch] = puncture
+        the patch follows (-1: none)."""
+        pos = np.ascontiguousarray(np.asarray(positions, dtype=np.float64).reshape(-1))
+        n = pos.size // 3
+        fl = (ctypes.c_int * max(1, len(follow)))(*[int(v) for v in follow])
+        pp = pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._check(lib().sacrak_track_punctures(self._h, n, pp, fl), "track_punctures")
+        self._npunct = n
+
+    def punctures(self) -> np.ndarray:
+        n = getattr(self, "_npunct", 0)
+        out = np.zeros(3 * max(1, n))
+        self._check(lib().sacrak_get_punctures(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "get_punctures")
+        return out[:3 * n].reshape(n, 3)
+
+    def move_patch(self, patch: int, shift):
+        sh = (ctypes.c_int * 3)(*[int(v) for v in shift])
+        self._check(lib().sacrak_move_patch(self._h, patch, sh), "move_patch")
+
+    def patch_origin(self, patch: int):
+        o = (ctypes.c_double * 3)()
+        self._check(lib().sacrak_patch_origin(self._h, patch, o), "patch_origin")
+        return tuple(o)
+
+    def regrid(self) -> int:
+        m = ctypes.c_int()
+        self._check(lib().sacrak_regrid(self._h, ctypes.byref(m)), "regrid")
+        return m.value
 
     def adm_integrals(self, patch: int, centre=(0.0, 0.0, 0.0), radius: float = 1.0, ntheta: int = 24,
                       nphi: int = 48):

@@ -121,7 +121,8 @@ __device__ __forceinline__ int floor_half(int i) { return i >= 0 ? i / 2 : -((-i
 struct ProlongArgs {
   const DevPatch* patches;
   const int* patch_ids;   // children (one level)
-  const DevLevel* plev;   // parent level: slot = its current ring slot
+  const DevLevel* plev;   // parent level: slot = its current ring slot - back
+  int back;
 };
 
 constexpr int PB = 8;          // brick edge along a slab's long directions
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(PB_THREADS) prolong_brick_kernel(ProlongArgs A
   const int Sx = B[0] + 6, Sy = B[1] + 6, Sz = B[2] + 6;
   const int Cx = 2 * B[0], Cy = 2 * B[1], Cz = 2 * B[2];
   const DevPatch* P = A.patches + C->parent;
-  const int slot = A.plev->ring;
+  const int slot = (A.plev->ring + 3 - A.back) % 3;
   const long long fo = (long long)f * P->fstride;
   // parent array index of shell cell a along d: off[d] - 2 + a + GH
   auto pq = [&](int a, int bb, int c) {
@@ -592,6 +593,109 @@ __global__ void level_advance_kernel(DevLevel* L, double dt) {
   L->t += dt;
 }
 
+__global__ void set_nvalid_kernel(DevLevel* L, int nvalid) { L->nvalid = nvalid; }
+
+// ---------------------------------------------------------------------------
+// Moving boxes (Sec. 2.2.1)
+
+// beta^i at x: tricubic Lagrange from the 4 nearest cell centres per axis,
+// all of them active cells (false otherwise)
+__device__ bool interp_shift(const DevPatch* P, const double* __restrict__ u, const double x[3],
+                             double b[3]) {
+  int i0[3];
+  double w[3][4];
+  const int n[3] = {P->n[0], P->n[1], P->n[2]};
+  for (int d = 0; d < 3; ++d) {
+    const double t = (x[d] - P->origin[d]) / P->dx - 0.5 + GH;  // array coordinate
+    if (!(t >= GH + 1.0 && t < GH + n[d] - 2.0)) return false;
+    i0[d] = (int)floor(t) - 1;
+    const double s = t - i0[d], s1 = s - 1.0, s2 = s - 2.0, s3 = s - 3.0;
+    w[d][0] = -s1 * s2 * s3 / 6.0;
+    w[d][1] = s * s2 * s3 / 2.0;
+    w[d][2] = -s * s1 * s3 / 2.0;
+    w[d][3] = s * s1 * s2 / 6.0;
+  }
+  for (int c = 0; c < 3; ++c) {
+    const double* f = u + (long long)(F_BETX + c) * P->fstride;
+    double v = 0.0;
+    for (int k = 0; k < 4; ++k)
+      for (int j = 0; j < 4; ++j)
+        for (int i = 0; i < 4; ++i)
+          v += w[0][i] * w[1][j] * w[2][k] *
+               f[(i0[0] + i) + (long long)(i0[1] + j) * P->px + (long long)(i0[2] + k) * P->plane];
+    b[c] = v;
+  }
+  return true;
+}
+
+// one thread per puncture: x <- x - dt/2 (beta_old(x) + beta_new(x - dt beta_old(x)))
+__global__ void track_kernel(TrackArgs A) {
+  const int p = threadIdx.x;
+  if (p >= A.np) return;
+  DevPunct* q = A.punct + p;
+  if (q->level != A.level) return;
+  const DevPatch* P = A.patches + q->patch;
+  const int ring = A.levels[A.level].ring;
+  double x[3], b0[3], b1[3], xs[3];
+  for (int d = 0; d < 3; ++d) x[d] = q->x[d];
+  if (!interp_shift(P, P->buf[ring], x, b0)) {
+    atomicOr(A.err, ERR_TRACK);
+    return;
+  }
+  for (int d = 0; d < 3; ++d) xs[d] = __dsub_rn(x[d], __dmul_rn(A.dt, b0[d]));
+  if (!interp_shift(P, P->buf[(ring + 1) % 3], xs, b1)) {
+    atomicOr(A.err, ERR_TRACK);
+    return;
+  }
+  const double h = __dmul_rn(0.5, A.dt);
+  for (int d = 0; d < 3; ++d) q->x[d] = __dsub_rn(x[d], __dmul_rn(h, __dadd_rn(b0[d], b1[d])));
+}
+
+__global__ void move_patch_kernel(MoveArgs A) {
+  const DevPatch* C = A.patches + A.patch;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = (long long)C->NX * C->NY * C->NZ;
+  if (id >= tot) return;
+  const int i = (int)(id % C->NX), j = (int)((id / C->NX) % C->NY), k = (int)(id / ((long long)C->NX * C->NY));
+  const long long q = i + (long long)j * C->px + (long long)k * C->plane;
+  const int io = i + A.sh[0], jo = j + A.sh[1], ko = k + A.sh[2];
+  const double* __restrict__ src = C->buf[A.levels[C->level].ring];
+  if (io >= GH && io < GH + C->n[0] && jo >= GH && jo < GH + C->n[1] && ko >= GH && ko < GH + C->n[2]) {
+    const long long qo = io + (long long)jo * C->px + (long long)ko * C->plane;
+    for (int f = 0; f < NF; ++f) A.dst[f * C->fstride + q] = src[f * C->fstride + qo];
+    return;
+  }
+  if (A.skip_zlower && k < GH) return;  // the reflection fills these
+  const DevPatch* P = A.patches + C->parent;
+  const double* __restrict__ up = P->buf[A.levels[P->level].ring];
+  // parent array index of the first stencil point and the weights along each
+  // axis: child cell c (active index) lies at parent cell off + floor(c/2)
+  // +- 1/4; odd c: nodes -2..3 (c_wp), even c: nodes -3..2 (c_wm)
+  const int ci[3] = {i - GH, j - GH, k - GH};
+  const int Pd[3] = {P->NX, P->NY, P->NZ};
+  int lo[3];
+  const double* w[3];
+  for (int d = 0; d < 3; ++d) {
+    const int odd = ci[d] & 1;
+    lo[d] = A.noff[d] + floor_half(ci[d]) + GH - (odd ? 2 : 3);
+    w[d] = odd ? c_wp : c_wm;
+    if (lo[d] < 0 || lo[d] + 5 >= Pd[d]) {
+      atomicOr(A.err, ERR_BOUNDS);
+      return;
+    }
+  }
+  for (int f = 0; f < NF; ++f) {
+    const double* fp = up + (long long)f * P->fstride;
+    double v = 0.0;
+    for (int c = 0; c < 6; ++c)
+      for (int b = 0; b < 6; ++b)
+        for (int a = 0; a < 6; ++a)
+          v += w[0][a] * w[1][b] * w[2][c] *
+               fp[(lo[0] + a) + (long long)(lo[1] + b) * P->px + (long long)(lo[2] + c) * P->plane];
+    A.dst[f * C->fstride + q] = v;
+  }
+}
+
 // ----------------------------------------------------------------------------
 
 void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cudaStream_t st) {
@@ -606,12 +710,13 @@ void launch_fill(int kind, const FillArgs& a, int npatches, long long maxpts, cu
 }
 
 void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,
-                          long long max_bricks, int mixed, cudaStream_t st) {
+                          long long max_bricks, int mixed, cudaStream_t st, int back) {
   if (nchildren == 0 || max_bricks == 0) return;
   ProlongArgs a;
   a.patches = patches;
   a.patch_ids = ids;
   a.plev = plev;
+  a.back = back;
   dim3 grid((unsigned)max_bricks, NF, nchildren);
   if (mixed)
     prolong_brick_kernel<true><<<grid, PB_THREADS, 0, st>>>(a);
@@ -621,6 +726,14 @@ void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLeve
 
 void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st) {
   exchange_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(e);
+}
+
+void launch_set_nvalid(DevLevel* L, int nvalid, cudaStream_t st) { set_nvalid_kernel<<<1, 1, 0, st>>>(L, nvalid); }
+
+void launch_track(const TrackArgs& a, cudaStream_t st) { track_kernel<<<1, 32, 0, st>>>(a); }
+
+void launch_move(const MoveArgs& a, long long tot, cudaStream_t st) {
+  move_patch_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(a);
 }
 
 void launch_level_advance(DevLevel* L, double dt, cudaStream_t st) {

@@ -28,7 +28,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
   // byte offsets inside the arena
-  size_t patches, levels, ids, tiles, err, results, scratch, dslot, states, total;
+  size_t patches, levels, ids, tiles, err, results, punct, scratch, dslot, states, total;
   std::vector<size_t> patch_state;  // offset of each patch's first buffer
   std::vector<long long> fstride;
   std::vector<int> px;
@@ -84,6 +84,8 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed,
   off = align_up(off + 16, 256);
   L.results = off;
   off = align_up(off + 64 * sizeof(double), 256);
+  L.punct = off;
+  off = align_up(off + MAX_PUNCT * sizeof(DevPunct), 256);
   L.scratch_doubles = maxtiles_level * 5 > maxpts / 256 + 1 ? maxtiles_level * 5 : maxpts / 256 + 1;
   if (L.scratch_doubles < 6 * (size_t)ADM_MAX_THETA) L.scratch_doubles = 6 * (size_t)ADM_MAX_THETA;
   L.scratch = off;
@@ -137,6 +139,12 @@ struct sacrak_grid {
   double* d_results;
   double* d_scratch;
   float* d_dslot;  // mixed precision: derivative planes of the split stage kernel
+  // moving boxes: tracked punctures (positions on the device), the puncture
+  // each patch follows (-1: none), the levels a tracker runs on
+  DevPunct* d_punct;
+  int npunct = 0;
+  std::vector<int> follow;
+  std::vector<DevPunct> hpunct;  // tracking patch and level of each puncture
   bool invalid = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -209,6 +217,11 @@ sacrak_status sync_and_check(sacrak_grid* g) {
   if (flag & ERR_NONFINITE) return fail(g, SACRAK_ENONFINITE, "non-finite value in a stage update");
   if (flag & ERR_TIMEOUT) return fail(g, SACRAK_ETIMEOUT, "bounded device wait ran out");
   if (flag & ERR_BOUNDS) return fail(g, SACRAK_ECUDA, "device bounds check failed");
+  if (flag & ERR_TRACK) {  // reported once; the grid stays usable
+    const unsigned rest = flag & ~(unsigned)ERR_TRACK;
+    CK(cudaMemcpy(g->d_err, &rest, sizeof rest, cudaMemcpyHostToDevice));
+    return fail(g, SACRAK_EINVAL, "a puncture's interpolation stencil left its tracking patch (regrid)");
+  }
   return SACRAK_OK;
 }
 
@@ -358,6 +371,15 @@ void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones, const std
 }
 
 // select the stage kernel of a level (0 direct, 1.. TMA variant + 1)
+// forget the captured coarse step (its launches no longer match the grid)
+void drop_graph(sacrak_grid* g) {
+  if (!g->graph_exec) return;
+  cudaGraphExecDestroy(g->graph_exec);
+  cudaGraphDestroy(g->graph);
+  g->graph_exec = nullptr;
+  g->graph = nullptr;
+}
+
 sacrak_status select_kernel(sacrak_grid* g, int l, int kernel) {
   if (!kernel_eligible(g, kernel, g->lvl_ids[l]))
     return fail(g, SACRAK_EINVAL, "kernel %d not usable on level %d", kernel, l);
@@ -375,12 +397,7 @@ sacrak_status select_kernel(sacrak_grid* g, int l, int kernel) {
       if (dev >= 0 && dev < 64) done[dev][v] = true;
     }
   }
-  if (g->lvl_kernel[l] != kernel && g->graph_exec) {  // the captured coarse step used the old kernel
-    cudaGraphExecDestroy(g->graph_exec);
-    cudaGraphDestroy(g->graph);
-    g->graph_exec = nullptr;
-    g->graph = nullptr;
-  }
+  if (g->lvl_kernel[l] != kernel) drop_graph(g);  // the captured coarse step used the old kernel
   g->lvl_kernel[l] = kernel;
   return SACRAK_OK;
 }
@@ -533,8 +550,39 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
   // the new level's z < 0 ghosts mirror its new values (the children's
   // prolongation reads those parent cells)
   zreflect(g, l, 2, 4);
+  for (int p = 0; p < g->npunct; ++p)
+    if (g->hpunct[p].level == l) {  // the punctures tracked on this level
+      TrackArgs ta;
+      ta.patches = g->d_patches;
+      ta.levels = g->d_levels;
+      ta.punct = g->d_punct;
+      ta.np = g->npunct;
+      ta.level = l;
+      ta.dt = dt;
+      ta.err = g->d_err;
+      launch_track(ta, g->stream);
+      break;
+    }
   launch_level_advance(g->d_levels + l, dt, g->stream);
   refresh_shells(g, l + 1);  // the children's cache of this level's new slot
+}
+
+// do two patches of level l share active cells (the exchange then averages
+// them, changing active data that the next level's prolongation reads)?
+bool active_overlap(const sacrak_grid* g, int l) {
+  const auto& ids = g->lvl_ids[l];
+  for (size_t a = 0; a < ids.size(); ++a)
+    for (size_t b = a + 1; b < ids.size(); ++b) {
+      const DevPatch& A = g->hp[ids[a]];
+      const DevPatch& B = g->hp[ids[b]];
+      bool ov = true;
+      for (int d = 0; d < 3; ++d) {
+        const int off = (int)std::llround((A.origin[d] - B.origin[d]) / A.dx);
+        if (!(off < B.n[d] && off + A.n[d] > 0)) ov = false;
+      }
+      if (ov) return true;
+    }
+  return false;
 }
 
 void level_step_rec(sacrak_grid* g, int l, double frac0, double dfrac) {
@@ -545,11 +593,123 @@ void level_step_rec(sacrak_grid* g, int l, double frac0, double dfrac) {
     const int nc = (int)g->lvl_ids[l + 1].size();
     fill_ghosts(g, l + 1, 1, 0, 1.0, 0.0);  // prolongation (unrestricted parent) + exchange
     zreflect(g, l + 1, 1, 0);
+    // the exchange averaged shared active cells of level l+1: its children
+    // cache that slot again
+    if (l + 2 < g->nlevels && active_overlap(g, l + 1)) refresh_shells(g, l + 2);
     launch_fill(FILL_RESTRICT, fill_args(g, l + 1, 1, 0, 0.0), nc, g->lvl_max_restrict[l + 1],
                 g->stream);
     zreflect(g, l, 1, 0);      // restricted cells next to z = 0 have mirrors among the ghosts
     refresh_shells(g, l + 1);  // the restricted slot, for the next parent step
   }
+}
+
+// ---- moving boxes (Sec. 2.2.1) ----
+
+int floor_div2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
+
+// smallest offset (parent cells) of child c along d inside par: 4, or 0 for
+// a child that starts on the equator with its parent under equatorial symmetry
+int nest_lo(const sacrak_grid* g, const DevPatch& c, const DevPatch& par, int d, int off) {
+  return (g->prm.zsym && d == 2 && c.zrefl && par.zrefl && off == 0) ? 0 : 4;
+}
+
+std::vector<int> children_of(const sacrak_grid* g, int pid, bool only_fixed) {
+  std::vector<int> k;
+  for (int q = 0; q < g->npatches; ++q)
+    if (g->hp[q].parent == pid && (!only_fixed || g->follow[q] < 0)) k.push_back(q);
+  return k;
+}
+
+// the shifts (parent cells) per axis that keep patch pid (geometry geo[pid])
+// nested in geo[parent] and the children kids nested in it; no z shifts
+// under equatorial symmetry (punctures on the equator stay there)
+void shift_range(const sacrak_grid* g, int pid, const std::vector<DevPatch>& geo, const std::vector<int>& kids,
+                 int lo[3], int hi[3]) {
+  const DevPatch& c = geo[pid];
+  const DevPatch& par = geo[c.parent];
+  for (int d = 0; d < 3; ++d) {
+    const int off = (int)std::llround((c.origin[d] - par.origin[d]) / par.dx);
+    int a = nest_lo(g, c, par, d, off) - off;
+    int b = par.n[d] - 4 - c.n[d] / 2 - off;
+    for (int kid : kids) {
+      const DevPatch& k = geo[kid];
+      const int koff = (int)std::llround((k.origin[d] - c.origin[d]) / c.dx);
+      // the child's offset becomes koff - 2 s
+      a = std::max(a, -floor_div2(c.n[d] - 4 - k.n[d] / 2 - koff));
+      b = std::min(b, floor_div2(koff - nest_lo(g, k, c, d, koff)));
+    }
+    if (g->prm.zsym && d == 2) a = b = 0;
+    lo[d] = a;
+    hi[d] = b;
+  }
+}
+
+// all levels at the same time (after whole coarse steps); lv gets the levels
+sacrak_status synchronised(sacrak_grid* g, std::vector<DevLevel>& lv) {
+  lv.resize(g->nlevels);
+  CK(cudaMemcpyAsync(lv.data(), g->d_levels, sizeof(DevLevel) * g->nlevels, cudaMemcpyDeviceToHost, g->stream));
+  CK(cudaStreamSynchronize(g->stream));
+  for (int l = 1; l < g->nlevels; ++l)
+    if ((long long)lv[l].steps != ((long long)lv[0].steps << l))
+      return fail(g, SACRAK_EINVAL, "levels not synchronised (move patches between coarse steps)");
+  return SACRAK_OK;
+}
+
+// shift patch pid by s parent cells: its current time level into the stage
+// buffer (old active cells copied, the rest prolonged from the parent), back
+// into the ring slot, then the geometry; the level's time-level history
+// restarts
+void apply_move(sacrak_grid* g, int pid, const int s[3], const std::vector<DevLevel>& lv) {
+  DevPatch& C = g->hp[pid];
+  MoveArgs a;
+  a.patches = g->d_patches;
+  a.levels = g->d_levels;
+  a.patch = pid;
+  for (int d = 0; d < 3; ++d) {
+    a.sh[d] = 2 * s[d];
+    a.noff[d] = C.off[d] + s[d];
+  }
+  a.skip_zlower = g->prm.zsym && C.zrefl;
+  a.dst = C.buf[B_S0];
+  a.err = g->d_err;
+  launch_move(a, (long long)C.NX * C.NY * C.NZ, g->stream);
+  cudaMemcpyAsync(C.buf[lv[C.level].ring], C.buf[B_S0], sizeof(double) * NF * C.fstride,
+                  cudaMemcpyDeviceToDevice, g->stream);
+  for (int d = 0; d < 3; ++d) {
+    C.origin[d] = C.origin[d] + (2 * s[d]) * C.dx;
+    C.off[d] += s[d];
+  }
+  for (int k : children_of(g, pid, false))
+    for (int d = 0; d < 3; ++d) g->hp[k].off[d] -= 2 * s[d];
+  cudaMemcpyAsync(g->d_patches, g->hp.data(), sizeof(DevPatch) * g->npatches, cudaMemcpyHostToDevice,
+                  g->stream);
+  launch_set_nvalid(g->d_levels + C.level, 1, g->stream);
+  // where the parent level's patches share active cells, the exchange at the
+  // start of each of its steps averaged them in place in its stored time
+  // levels: caches of its older slots rebuilt now would differ from those
+  // its children used, so its history restarts too
+  if (active_overlap(g, C.level - 1)) launch_set_nvalid(g->d_levels + C.level - 1, 1, g->stream);
+  zreflect(g, C.level, 1, 0);
+  if (g->prm.precision == 1)
+    launch_split(g->d_patches, g->d_levels, pid, (long long)C.NX * C.NY * C.NZ, g->stream);
+}
+
+// after moves: every child level's cache of all three parent slots, and no
+// captured coarse step
+void refresh_after_move(sacrak_grid* g) {
+  for (int l = 1; l < g->nlevels; ++l)
+    for (int back = 0; back < 3; ++back)
+      launch_prolong_space(g->d_patches, g->d_ids + g->lvl_id_off[l], g->d_levels + (l - 1),
+                           (int)g->lvl_ids[l].size(), g->lvl_max_clusters[l], g->prm.precision == 1,
+                           g->stream, back);
+  drop_graph(g);
+}
+
+sacrak_status not_capturing(sacrak_grid* g) {
+  cudaStreamCaptureStatus cs;
+  CK(cudaStreamIsCapturing(g->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(g, SACRAK_ESTATE, "stream is being captured");
+  return SACRAK_OK;
 }
 
 sacrak_status reset_levels(sacrak_grid* g) {
@@ -707,6 +867,8 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   g->d_results = (double*)(g->arena + L.results);
   g->d_scratch = (double*)(g->arena + L.scratch);
   g->d_dslot = (float*)(g->arena + L.dslot);
+  g->d_punct = (DevPunct*)(g->arena + L.punct);
+  g->follow.assign(npatches, -1);
   std::vector<int> ids;
   std::vector<Tile> tiles;
   g->lvl_id_off.resize(nlevels);
@@ -1013,6 +1175,143 @@ sacrak_status sacrak_adm_integrals(sacrak_grid* g, int patch, const double centr
     return fail(g, SACRAK_EINVAL, "%.0f sphere points within 2 cells of the edge of patch %d", v[5], patch);
   for (int c = 0; c < 5; ++c) out[c] = v[c];
   return SACRAK_OK;
+}
+
+sacrak_status sacrak_track_punctures(sacrak_grid* g, int npunct, const double* pos, const int* follow) {
+  if (!g) return SACRAK_EINVAL;
+  if (npunct < 0 || npunct > MAX_PUNCT || (npunct > 0 && (!pos || !follow)))
+    return fail(g, SACRAK_EINVAL, "bad arguments");
+  std::vector<DevPunct> hp(npunct);
+  for (int p = 0; p < npunct; ++p) {
+    for (int d = 0; d < 3; ++d) {
+      if (!std::isfinite(pos[3 * p + d])) return fail(g, SACRAK_EINVAL, "puncture position not finite");
+      hp[p].x[d] = pos[3 * p + d];
+    }
+    hp[p].patch = -1;
+    hp[p].level = -1;
+  }
+  std::vector<int> fl(g->npatches, -1);
+  if (npunct > 0)
+    for (int q = 0; q < g->npatches; ++q) {
+      if (follow[q] < -1 || follow[q] >= npunct) return fail(g, SACRAK_EINVAL, "follow[%d] out of range", q);
+      if (follow[q] >= 0 && g->hp[q].level == 0)
+        return fail(g, SACRAK_EINVAL, "level-0 patch %d cannot move", q);
+      fl[q] = follow[q];
+      if (fl[q] >= 0 && g->hp[q].level > hp[fl[q]].level) {  // the finest patch tracks
+        hp[fl[q]].patch = q;
+        hp[fl[q]].level = g->hp[q].level;
+      }
+    }
+  for (int p = 0; p < npunct; ++p)
+    if (hp[p].patch < 0) return fail(g, SACRAK_EINVAL, "puncture %d is followed by no patch", p);
+  sacrak_status st = not_capturing(g);
+  if (st != SACRAK_OK) return st;
+  if (npunct > 0)
+    CK(cudaMemcpyAsync(g->d_punct, hp.data(), sizeof(DevPunct) * npunct, cudaMemcpyHostToDevice, g->stream));
+  st = sync_and_check(g);  // (also keeps hp alive until the copy is done)
+  if (st != SACRAK_OK) return st;
+  g->npunct = npunct;
+  g->hpunct = hp;
+  g->follow = fl;
+  drop_graph(g);  // the captured coarse step has no (or other) trackers
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_get_punctures(sacrak_grid* g, double* pos) {
+  if (!g) return SACRAK_EINVAL;
+  if (g->npunct > 0 && !pos) return fail(g, SACRAK_EINVAL, "bad arguments");
+  std::vector<DevPunct> hp(g->npunct);
+  if (g->npunct > 0)
+    CK(cudaMemcpyAsync(hp.data(), g->d_punct, sizeof(DevPunct) * g->npunct, cudaMemcpyDeviceToHost, g->stream));
+  sacrak_status st = sync_and_check(g);
+  if (st != SACRAK_OK) return st;
+  for (int p = 0; p < g->npunct; ++p)
+    for (int d = 0; d < 3; ++d) pos[3 * p + d] = hp[p].x[d];
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_move_patch(sacrak_grid* g, int patch, const int shift[3]) {
+  if (!g) return SACRAK_EINVAL;
+  if (patch < 0 || patch >= g->npatches || !shift) return fail(g, SACRAK_EINVAL, "bad arguments");
+  if (g->hp[patch].level == 0) return fail(g, SACRAK_EINVAL, "level-0 patches do not move");
+  if (g->invalid) return fail(g, SACRAK_ESTATE, "grid holds invalid data");
+  sacrak_status st = not_capturing(g);
+  if (st != SACRAK_OK) return st;
+  std::vector<DevLevel> lv;
+  st = synchronised(g, lv);
+  if (st != SACRAK_OK) return st;
+  int lo[3], hi[3];
+  shift_range(g, patch, g->hp, children_of(g, patch, false), lo, hi);
+  for (int d = 0; d < 3; ++d)
+    if (shift[d] < lo[d] || shift[d] > hi[d])
+      return fail(g, SACRAK_EINVAL, "shift %d along axis %d outside %d..%d (nesting)", shift[d], d, lo[d], hi[d]);
+  if (shift[0] == 0 && shift[1] == 0 && shift[2] == 0) return SACRAK_OK;
+  apply_move(g, patch, shift, lv);
+  refresh_after_move(g);
+  st = check_launch(g);
+  if (st != SACRAK_OK) return st;
+  return sync_and_check(g);
+}
+
+sacrak_status sacrak_patch_origin(sacrak_grid* g, int patch, double origin[3]) {
+  if (!g) return SACRAK_EINVAL;
+  if (patch < 0 || patch >= g->npatches || !origin) return fail(g, SACRAK_EINVAL, "bad arguments");
+  for (int d = 0; d < 3; ++d) origin[d] = g->hp[patch].origin[d];
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_regrid(sacrak_grid* g, int* moved) {
+  if (!g) return SACRAK_EINVAL;
+  if (!moved) return fail(g, SACRAK_EINVAL, "bad arguments");
+  *moved = 0;
+  if (g->npunct == 0) return SACRAK_OK;
+  if (g->invalid) return fail(g, SACRAK_ESTATE, "grid holds invalid data");
+  sacrak_status st = not_capturing(g);
+  if (st != SACRAK_OK) return st;
+  std::vector<DevLevel> lv;
+  st = synchronised(g, lv);
+  if (st != SACRAK_OK) return st;
+  std::vector<DevPunct> hx(g->npunct);
+  CK(cudaMemcpyAsync(hx.data(), g->d_punct, sizeof(DevPunct) * g->npunct, cudaMemcpyDeviceToHost, g->stream));
+  st = sync_and_check(g);
+  if (st != SACRAK_OK) return st;
+  // plan coarse to fine on copies of the geometry, check it, then move
+  std::vector<DevPatch> geo = g->hp;
+  std::vector<std::pair<int, std::array<int, 3>>> plan;
+  for (int l = 1; l < g->nlevels; ++l)
+    for (int pid : g->lvl_ids[l]) {
+      const int p = g->follow[pid];
+      if (p < 0) continue;
+      DevPatch& c = geo[pid];
+      const double dxp = 2.0 * c.dx;
+      std::array<int, 3> s;
+      for (int d = 0; d < 3; ++d)
+        s[d] = (int)std::trunc((hx[p].x[d] - (c.origin[d] + 0.5 * c.n[d] * c.dx)) / dxp);
+      int lo[3], hi[3];
+      shift_range(g, pid, geo, children_of(g, pid, true), lo, hi);
+      for (int d = 0; d < 3; ++d) {
+        if (lo[d] > hi[d]) return fail(g, SACRAK_EINVAL, "patch %d cannot stay nested", pid);
+        s[d] = std::min(std::max(s[d], lo[d]), hi[d]);
+      }
+      if (s[0] || s[1] || s[2]) {
+        for (int d = 0; d < 3; ++d) c.origin[d] = c.origin[d] + (2 * s[d]) * c.dx;
+        plan.push_back({pid, s});
+      }
+    }
+  for (int pid = 0; pid < g->npatches; ++pid) {
+    if (geo[pid].parent < 0) continue;
+    int lo[3], hi[3];
+    shift_range(g, pid, geo, children_of(g, pid, false), lo, hi);
+    for (int d = 0; d < 3; ++d)
+      if (lo[d] > 0 || hi[d] < 0) return fail(g, SACRAK_EINVAL, "regrid would break the nesting of patch %d", pid);
+  }
+  if (plan.empty()) return SACRAK_OK;
+  for (auto& m : plan) apply_move(g, m.first, m.second.data(), lv);
+  refresh_after_move(g);
+  st = check_launch(g);
+  if (st != SACRAK_OK) return st;
+  *moved = (int)plan.size();
+  return sync_and_check(g);
 }
 
 sacrak_status sacrak_pi_symmetry(sacrak_grid* g, int patch, double* out) {

@@ -70,7 +70,7 @@ struct DevParams {
 };
 
 // error flags written by kernels (bitmask), read by the host after a sync
-enum { ERR_NONFINITE = 1, ERR_BOUNDS = 2, ERR_TIMEOUT = 4 };
+enum { ERR_NONFINITE = 1, ERR_BOUNDS = 2, ERR_TIMEOUT = 4, ERR_TRACK = 8 };
 
 // pi-rotation parity of each field (x,y -> -x,-y)
 __host__ __device__ inline int pi_parity(int f) {
@@ -283,6 +283,40 @@ struct AdmArgs {
   double* ring;
 };
 
+// Moving boxes (Sec. 2.2.1).  A tracked puncture: position, the patch it is
+// tracked on (the finest patch that follows it) and that patch's level.
+constexpr int MAX_PUNCT = 8;
+struct DevPunct {
+  double x[3];
+  int patch, level;
+};
+// the punctures tracked on `level`, after the stage 4 of its step (old time
+// level in the ring slot, new one in the next slot): Heun's method for
+// dx/dt = -beta(x) over dt
+struct TrackArgs {
+  const DevPatch* patches;
+  const DevLevel* levels;
+  DevPunct* punct;
+  int np, level;
+  double dt;
+  unsigned* err;
+};
+// data of patch `patch` shifted by sh own cells (new array index + sh = old
+// array index) with its new offset noff in parent cells, written to dst (a
+// full patch buffer): old active cells copied from the current slot, the
+// rest prolonged from the parent's current slot; with skip_zlower the z < 0
+// ghost layers are left to the reflection.  The device table still holds the
+// old geometry.
+struct MoveArgs {
+  const DevPatch* patches;
+  const DevLevel* levels;
+  int patch;
+  int sh[3], noff[3];
+  int skip_zlower;
+  double* dst;
+  unsigned* err;
+};
+
 // launchers (host)
 void launch_stage_fp64(const StageArgs& a, cudaStream_t st);
 void launch_stage_mixed(const StageArgs& a, cudaStream_t st);
@@ -295,8 +329,13 @@ void launch_exchange(const ExchArgs& e, long long tot, cudaStream_t st);
 void launch_zreflect(const FillArgs& a, int npatches, long long maxpts, cudaStream_t st);
 // bricks of the spatial prolongation of one child patch (n active cells)
 int prolong_bricks(int n0, int n1, int n2);
+// back = 0: the parent's current slot; 1, 2: the one and two time levels
+// before it (after a patch moved, every cached slot is recomputed)
 void launch_prolong_space(const DevPatch* patches, const int* ids, const DevLevel* plev, int nchildren,
-                          long long max_bricks, int mixed, cudaStream_t st);
+                          long long max_bricks, int mixed, cudaStream_t st, int back = 0);
+void launch_track(const TrackArgs& a, cudaStream_t st);
+void launch_move(const MoveArgs& a, long long tot, cudaStream_t st);
+void launch_set_nvalid(DevLevel* L, int nvalid, cudaStream_t st);
 void launch_sommerfeld_mixed(const GhostArgs& a, int npatches, long long max_shell, cudaStream_t st);
 void launch_split(const DevPatch* patches, const DevLevel* levels, int patch, long long tot,
                   cudaStream_t st);
