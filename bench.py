@@ -206,7 +206,7 @@ def main():
                     help="gauge-wave: RK4 steps on the coarsest grid; robust-stability: steps per grid")
     ap.add_argument("--case", default="amr7",
                     choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep",
-                             "amr7-zsym", "adm"],
+                             "amr7-zsym", "adm", "amr7-moving"],
                     help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
                          "mixed-error: the 7-level hierarchy in FP64 and mixed precision side by side")
     ap.add_argument("--coarse-steps", type=int, default=64, help="mixed-error: coarse steps")
@@ -252,6 +252,9 @@ def main():
         return
     if args.case == "adm":
         adm_case(torch, sk, args)
+        return
+    if args.case == "amr7-moving":
+        moving_case(torch, sk, args)
         return
 
     h = hierarchy()
@@ -400,6 +403,61 @@ def zsym_case(torch, sk, args):
         out["runs"][name] = {"ms_per_step": ms, "zone_updates_per_s": zu / (ms * 1e-3),
                              "full_domain_equivalent_per_s": 2 * zu / (ms * 1e-3),
                              "constraints_l0": list(map(float, g.constraints(0)))}
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
+def moving_case(torch, sk, args):
+    """Moving boxes (Sec. 2.2.1) on the 7-level binary in mixed precision:
+    the L5/L6 patches follow their punctures, tracked after every L6 step
+    inside the captured coarse step, and sacrak_regrid runs after every coarse
+    step (a host synchronisation; a patch move rebuilds the graph).  Three
+    runs of --steps coarse steps each: static boxes, moving boxes with the
+    data at rest (Brill-Lindquist, the punctures barely move), and moving
+    boxes with a uniform shift of 0.05 added (the punctures drift by -0.05
+    per unit time and the boxes follow).  CUDA events around the whole loop,
+    regrids included."""
+    h = hierarchy()
+    zu = h.zone_updates_per_coarse_step()
+    follow = [-1 if p.level < 5 else (0 if p.origin[0] + 0.5 * p.n[0] * p.dx > 0 else 1) for p in h.patches]
+    out = {"case": "amr7-moving", "zone_updates_per_step": zu, "courant": args.courant, "follow": follow,
+           "runs": {}}
+    for name, moving, drift in (("static", False, 0.0), ("moving", True, 0.0), ("moving-drift", True, 0.05)):
+        g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(courant=args.courant, precision=1),
+                    stream=torch.cuda.Stream())
+        g.set_initial_data(1, h.masses, h.positions)
+        if drift:
+            for i in range(len(h.patches)):
+                u = g.download_fields(i)
+                u[19] += drift
+                g.upload_fields(i, u)
+        g.autotune(reps=3)
+        if moving:
+            g.track_punctures(h.positions, follow)
+        for _ in range(args.warmup):
+            g.level_step(0)
+            if moving:
+                g.regrid()
+        moved = 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(g.stream)
+        for _ in range(args.steps):
+            g.level_step(0)
+            if moving:
+                moved += g.regrid()
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        run = {"ms_per_step": ms, "zone_updates_per_s": zu / (ms * 1e-3), "patches_moved": moved,
+               "constraints_l0": list(map(float, g.constraints(0)))}
+        if moving:
+            run["punctures"] = g.punctures().tolist()
+            run["origins_l6"] = [g.patch_origin(i) for i in range(len(h.patches)) if h.patches[i].level == 6]
+        out["runs"][name] = run
         g.close()
         del g
         torch.cuda.empty_cache()
