@@ -19,6 +19,12 @@ analytic families stand in for it):
   eps_kjl S^l n^k n_i) + 3/(2 r^2) (P_i n_j + P_j n_i - (delta_ij - n_i n_j)
   P.n), so At_ij = psi^-6 Ahat_ij; K = 0.  The Hamiltonian constraint is not
   re-solved (psi stays 1 + m/(2r)): an input, not a solution.
+* Linearised plane gravitational wave along the unit vector k: in TT gauge
+  g_ij = delta_ij + h_+(u) (e1 e1 - e2 e2)_ij + h_x(u) (e1 e2 + e2 e1)_ij,
+  u = t - k.x, h_+ = A sin(w u), h_x = B cos(w u), (e1, e2) the theta and phi
+  unit vectors of the direction k; K_ij = -d_t g_ij / 2, alpha = 1, beta = 0,
+  split into W, gt, Khat = K, At; Gamt = 0 (its exact value is second order
+  in the amplitude).
 * Gauge wave (Alcubierre et al. 2004 test-bed form): H = 1 - A sin(2 pi (x - t)/d),
   ds^2 = -H dt^2 + H dx^2 + dy^2 + dz^2, converted to the W/Z4c variables.
 * Noise: uniform in [-a, a] added to every field at every point; the value at
@@ -134,6 +140,41 @@ def bowen_york(p: Patch, mass: float, centre=(0.0, 0.0, 0.0), spin=(0.0, 0.0, 0.
         ahat = 3.0 / r ** 3 * (sxn[i] * n[j] + sxn[j] * n[i])
         ahat = ahat + 1.5 / r ** 2 * (P[i] * n[j] + P[j] * n[i] - ((1.0 if i == j else 0.0) - n[i] * n[j]) * pn)
         u[9 + a] = psi6 * ahat
+    return u
+
+
+def plane_wave_basis(theta: float, phi: float):
+    """Direction k and the polarisation vectors e1 (theta), e2 (phi)."""
+    st, ct, sp, cp = math.sin(theta), math.cos(theta), math.sin(phi), math.cos(phi)
+    return (np.array([st * cp, st * sp, ct]), np.array([ct * cp, ct * sp, -st]), np.array([-sp, cp, 0.0]))
+
+
+def plane_wave(p: Patch, amp_plus: float, amp_cross: float, omega: float, theta: float, phi: float,
+               t: float = 0.0) -> np.ndarray:
+    """Linearised plane wave along the direction (theta, phi) (module doc)."""
+    k, e1, e2 = plane_wave_basis(theta, phi)
+    z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
+    uu = t - (k[0] * x + k[1] * y + k[2] * z)
+    hp, hx = amp_plus * np.sin(omega * uu), amp_cross * np.cos(omega * uu)
+    dhp, dhx = amp_plus * omega * np.cos(omega * uu), -amp_cross * omega * np.sin(omega * uu)
+    g = np.zeros((3, 3) + x.shape)
+    kk = np.zeros((3, 3) + x.shape)
+    for i in range(3):
+        for j in range(3):
+            ep = e1[i] * e1[j] - e2[i] * e2[j]
+            ex = e1[i] * e2[j] + e2[i] * e1[j]
+            g[i, j] = (1.0 if i == j else 0.0) + hp * ep + hx * ex
+            kk[i, j] = -0.5 * (dhp * ep + dhx * ex)
+    gm = np.moveaxis(g, (0, 1), (-2, -1))
+    W = np.linalg.det(gm) ** (-1.0 / 6.0)
+    gu = np.moveaxis(np.linalg.inv(gm), (-2, -1), (0, 1))
+    K = np.einsum("ij...,ij...->...", gu, kk)
+    u = minkowski(p)
+    u[0] = W
+    u[7] = K
+    for a, (i, j) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
+        u[1 + a] = W * W * g[i, j]
+        u[9 + a] = W * W * (kk[i, j] - g[i, j] * K / 3.0)
     return u
 
 

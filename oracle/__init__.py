@@ -110,6 +110,12 @@ def lib():
             L.orc_move_patch.restype = ctypes.c_int
             L.orc_interp_point.argtypes = [P(_OrcPatch), dp, ctypes.c_int, dp, dp]
             L.orc_interp_point.restype = ctypes.c_int
+            L.orc_psi4_point.argtypes = [P(_OrcPatch), dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            L.orc_psi4_point.restype = ctypes.c_int
+            L.orc_psi4_modes.argtypes = [P(_OrcPatch), dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, dp]
+            L.orc_psi4_modes.restype = ctypes.c_int
+            L.orc_swsh.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
             L.orc_stencils.argtypes = [P(_OrcPatch), dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, dp, dp]
             _lib = L
@@ -269,6 +275,41 @@ def interp_point(p, u: np.ndarray, f: int, x) -> float:
     if lib().orc_interp_point(ctypes.byref(_cp(p)), _ptr(u), int(f), _ptr(xx), _ptr(out)) != 0:
         raise ValueError("interpolation stencil leaves the active cells")
     return float(out[0])
+
+
+def psi4_point(p, u: np.ndarray, centre, r: float, theta: float, phi: float) -> complex:
+    """Psi4 at the point of angles (theta, phi) on the sphere |x - centre| = r."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    c = np.ascontiguousarray(centre, dtype=np.float64)
+    out = np.empty(2)
+    if lib().orc_psi4_point(ctypes.byref(_cp(p)), _ptr(u), _ptr(c), float(r), float(theta), float(phi),
+                            _ptr(out)) != 0:
+        raise ValueError("stencil leaves the patch")
+    return complex(out[0], out[1])
+
+
+def psi4_modes(p, u: np.ndarray, centre, r: float, ntheta: int = 24, nphi: int = 48, lmax: int = 4):
+    """{(l, m): Psi4^lm} for l = 2..lmax on the sphere |x - centre| = r."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    c = np.ascontiguousarray(centre, dtype=np.float64)
+    nm = (lmax + 1) ** 2 - 4
+    out = np.empty(2 * nm)
+    if lib().orc_psi4_modes(ctypes.byref(_cp(p)), _ptr(u), _ptr(c), float(r), int(ntheta), int(nphi), int(lmax),
+                            _ptr(out)) != 0:
+        raise ValueError("sphere leaves the patch")
+    modes = {}
+    k = 0
+    for l in range(2, lmax + 1):
+        for m in range(-l, l + 1):
+            modes[(l, m)] = complex(out[2 * k], out[2 * k + 1])
+            k += 1
+    return modes
+
+
+def swsh(l: int, m: int, theta: float, phi: float) -> complex:
+    out = np.empty(2)
+    lib().orc_swsh(int(l), int(m), float(theta), float(phi), _ptr(out))
+    return complex(out[0], out[1])
 
 
 def gauss_legendre(n: int):

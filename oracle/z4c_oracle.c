@@ -721,6 +721,222 @@ int orc_adm_integrals(const orc_patch* p, const double* u, const double c[3], do
   return 0;
 }
 
+/* ---------------- Psi4 extraction (Sec. 2.3) ---------------- */
+
+/* Electric and magnetic parts of the Weyl tensor (vacuum, physical,
+ * covariant) and the physical metric at cell q:
+ *   E_ij = R_ij - K_ik K^k_j + K K_ij
+ *   B_ij = 1/2 (eps_i^kl D_k K_lj + eps_j^kl D_k K_li),  eps_ikl = sqrt(g) [ikl]
+ * with g_ij = gt_ij / W^2, K_ij = (At_ij + gt_ij K / 3) / W^2, K = Khat + 2
+ * Theta, R_ij the physical Ricci tensor of the RHS (conformal part plus W
+ * part), Gamma^i_jk = Gt^i_jk - (delta^i_j d_k W + delta^i_k d_j W - gt_jk
+ * gt^il d_l W) / W. */
+static void weyl_cell(const double* u, const layout* L, double h, ptrdiff_t q, double E[6], double B[6],
+                      double gam[6]) {
+  pointgeo G;
+  point_geometry(u, L, h, q, &G);
+  const double W = G.W, W2 = W * W;
+  double Kl[6], gu[6], Kud[3][3]; /* K_ij, g^ij, K^i_j */
+  for (int a = 0; a < 6; ++a) {
+    gam[a] = G.gt[a] / W2;
+    Kl[a] = (G.At[a] + G.gt[a] * G.K / 3.0) / W2;
+    gu[a] = W2 * G.gtu[a];
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += gu[SYM[i][k]] * Kl[SYM[k][j]];
+      Kud[i][j] = s;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      double kk = 0.0;
+      for (int k = 0; k < 3; ++k) kk += Kl[SYM[i][k]] * Kud[k][j];
+      E[SYM[i][j]] = G.Ric[SYM[i][j]] - kk + G.K * Kl[SYM[i][j]];
+    }
+  /* d_k K_ij from the derivatives of At, gt, W, Khat, Theta */
+  double dK[3][6];
+  for (int k = 0; k < 3; ++k) {
+    const double dKt = G.dKh[k] + 2.0 * G.dTh[k];
+    for (int a = 0; a < 6; ++a) {
+      const double dA = D1(u + (F_AXX + a) * L->sf, q, L->s[k], h);
+      dK[k][a] = (dA + G.dgt[k][a] * G.K / 3.0 + G.gt[a] * dKt / 3.0) / W2 - 2.0 * Kl[a] * G.dW[k] / W;
+    }
+  }
+  /* physical Christoffels Gamma^m_kl */
+  double Gp[3][6];
+  for (int m = 0; m < 3; ++m)
+    for (int k = 0; k < 3; ++k)
+      for (int l = k; l < 3; ++l) {
+        double gw = 0.0; /* gt^mn d_n W */
+        for (int n = 0; n < 3; ++n) gw += G.gtu[SYM[m][n]] * G.dW[n];
+        const double c = ((m == k) ? G.dW[l] : 0.0) + ((m == l) ? G.dW[k] : 0.0) - G.gt[SYM[k][l]] * gw;
+        Gp[m][SYM[k][l]] = G.Gu[m][SYM[k][l]] - c / W;
+      }
+  /* DK[k][l][j] = D_k K_lj */
+  double DK[3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l)
+      for (int j = 0; j < 3; ++j) {
+        double v = dK[k][SYM[l][j]];
+        for (int m = 0; m < 3; ++m)
+          v -= Gp[m][SYM[k][l]] * Kl[SYM[m][j]] + Gp[m][SYM[k][j]] * Kl[SYM[l][m]];
+        DK[k][l][j] = v;
+      }
+  /* eps_i^kl = g^ka g^lb sqrt(g) [iab]; sqrt(g) = sqrt(det gt) / W^3 */
+  const double gtdet = G.gt[0] * (G.gt[3] * G.gt[5] - G.gt[4] * G.gt[4]) -
+                       G.gt[1] * (G.gt[1] * G.gt[5] - G.gt[4] * G.gt[2]) +
+                       G.gt[2] * (G.gt[1] * G.gt[4] - G.gt[3] * G.gt[2]);
+  const double sg = sqrt(gtdet) / (W2 * W);
+  double C[3][3]; /* C_ij = eps_i^kl D_k K_lj */
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          const int lc = (a == (i + 1) % 3 && b == (i + 2) % 3) ? 1 : ((b == (i + 1) % 3 && a == (i + 2) % 3) ? -1 : 0);
+          if (!lc) continue;
+          for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) v += lc * gu[SYM[k][a]] * gu[SYM[l][b]] * DK[k][l][j];
+        }
+      C[i][j] = sg * v;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) B[SYM[i][j]] = 0.5 * (C[i][j] + C[j][i]);
+}
+
+/* spin-weight -2 spherical harmonic: sqrt((2l+1)/(4 pi)) d^l_{m,2}(theta)
+ * e^{i m phi}, with the Wigner d-function
+ * d^l_{m,2} = sum_k (-1)^k sqrt((l+m)!(l-m)!(l+2)!(l-2)!) / ((l+m-k)! (l-2-k)!
+ *             k! (k+2-m)!) cos(theta/2)^(2l+m-2-2k) sin(theta/2)^(2k+2-m),
+ * k from max(0, m-2) to min(l+m, l-2) */
+static double fact(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+void orc_swsh(int l, int m, double theta, double phi, double out[2]) {
+  const double c = cos(0.5 * theta), s = sin(0.5 * theta);
+  const double pre = sqrt(fact(l + m) * fact(l - m) * fact(l + 2) * fact(l - 2));
+  double d = 0.0;
+  const int k1 = m - 2 > 0 ? m - 2 : 0, k2 = (l + m < l - 2) ? l + m : l - 2;
+  for (int k = k1; k <= k2; ++k) {
+    const double t = pre / (fact(l + m - k) * fact(l - 2 - k) * fact(k) * fact(k + 2 - m));
+    d += ((k & 1) ? -t : t) * pow(c, 2 * l + m - 2 - 2 * k) * pow(s, 2 * k + 2 - m);
+  }
+  const double a = sqrt((2.0 * l + 1.0) / (4.0 * ORC_PI)) * d;
+  out[0] = a * cos(m * phi);
+  out[1] = a * sin(m * phi);
+}
+
+/* Psi4 at the sphere point with angles (theta, phi) about c at radius r:
+ * E, B, g interpolated tricubically from the 4 nearest cell centres per axis;
+ * orthonormal triad (Gram-Schmidt with g) from the coordinate radial, theta
+ * and phi directions; mbar = (e_theta - i e_phi)/sqrt(2);
+ * Psi4 = (E_ij - i B_ij) mbar^i mbar^j.  -1 if the stencils leave the array. */
+static int psi4_at(const orc_patch* p, const double* u, const double c[3], double r, double ct, double st,
+                   double cp, double sp, double out[2]) {
+  layout L = make_layout(p);
+  const int g = p->g;
+  const int N[3] = {L.NX, L.NY, L.NZ};
+  static const int nodes[4] = {0, 1, 2, 3};
+  const double n[3] = {st * cp, st * sp, ct};
+  int i0[3];
+  double wl[3][4];
+  for (int d = 0; d < 3; ++d) {
+    const double x = c[d] + r * n[d];
+    const double t = (x - p->origin[d]) / p->dx - 0.5 + g;
+    i0[d] = (int)floor(t) - 1;
+    if (!(t >= 3.0 && t < N[d] - 4.0)) return -1;
+    orc_lagrange_weights(4, nodes, t - i0[d], wl[d]);
+  }
+  double E[6] = {0}, B[6] = {0}, gam[6] = {0};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int e = 0; e < 4; ++e) {
+        const ptrdiff_t q = (i0[0] + a) + (ptrdiff_t)(i0[1] + b) * L.s[1] + (ptrdiff_t)(i0[2] + e) * L.s[2];
+        double Ec[6], Bc[6], gc[6];
+        weyl_cell(u, &L, p->dx, q, Ec, Bc, gc);
+        const double w = wl[0][a] * wl[1][b] * wl[2][e];
+        for (int k = 0; k < 6; ++k) {
+          E[k] += w * Ec[k];
+          B[k] += w * Bc[k];
+          gam[k] += w * gc[k];
+        }
+      }
+  /* Gram-Schmidt: e_r, e_theta, e_phi orthonormal in g */
+  double v[3][3] = {{n[0], n[1], n[2]}, {ct * cp, ct * sp, -st}, {-sp, cp, 0.0}};
+  double e[3][3];
+  for (int a = 0; a < 3; ++a) {
+    double w[3] = {v[a][0], v[a][1], v[a][2]};
+    for (int b = 0; b < a; ++b) {
+      double dot = 0.0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) dot += gam[SYM[i][j]] * w[i] * e[b][j];
+      for (int i = 0; i < 3; ++i) w[i] -= dot * e[b][i];
+    }
+    double nn = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) nn += gam[SYM[i][j]] * w[i] * w[j];
+    nn = sqrt(nn);
+    for (int i = 0; i < 3; ++i) e[a][i] = w[i] / nn;
+  }
+  /* mbar mbar = P - i Q, P = (e_th e_th - e_ph e_ph)/2, Q = (e_th e_ph + e_ph e_th)/2 */
+  double EP = 0.0, EQ = 0.0, BP = 0.0, BQ = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double P = 0.5 * (e[1][i] * e[1][j] - e[2][i] * e[2][j]);
+      const double Q = 0.5 * (e[1][i] * e[2][j] + e[2][i] * e[1][j]);
+      EP += E[SYM[i][j]] * P;
+      EQ += E[SYM[i][j]] * Q;
+      BP += B[SYM[i][j]] * P;
+      BQ += B[SYM[i][j]] * Q;
+    }
+  out[0] = EP - BQ;
+  out[1] = -(EQ + BP);
+  return 0;
+}
+
+int orc_psi4_point(const orc_patch* p, const double* u, const double c[3], double r, double theta, double phi,
+                   double out[2]) {
+  return psi4_at(p, u, c, r, cos(theta), sin(theta), cos(phi), sin(phi), out);
+}
+
+int orc_psi4_modes(const orc_patch* p, const double* u, const double c[3], double r, int ntheta, int nphi,
+                   int lmax, double* out) {
+  const int nm = (lmax + 1) * (lmax + 1) - 4;
+  double* xg = (double*)malloc(sizeof(double) * ntheta);
+  double* wg = (double*)malloc(sizeof(double) * ntheta);
+  orc_gauss_legendre(ntheta, xg, wg);
+  for (int k = 0; k < 2 * nm; ++k) out[k] = 0.0;
+  int bad = 0;
+  for (int it = 0; it < ntheta && !bad; ++it) {
+    const double ct = xg[it], st = sqrt(1.0 - ct * ct), th = acos(ct);
+    for (int ip = 0; ip < nphi && !bad; ++ip) {
+      const double ph = 2.0 * ORC_PI * ip / nphi;
+      double psi[2];
+      if (psi4_at(p, u, c, r, ct, st, cos(ph), sin(ph), psi)) {
+        bad = 1;
+        break;
+      }
+      const double w = wg[it] * 2.0 * ORC_PI / nphi;
+      int k = 0;
+      for (int l = 2; l <= lmax; ++l)
+        for (int m = -l; m <= l; ++m, ++k) {
+          double y[2];
+          orc_swsh(l, m, th, ph, y);
+          /* Psi4 conj(Y) */
+          out[2 * k] += w * (psi[0] * y[0] + psi[1] * y[1]);
+          out[2 * k + 1] += w * (psi[1] * y[0] - psi[0] * y[1]);
+        }
+    }
+  }
+  free(xg);
+  free(wg);
+  return bad ? -1 : 0;
+}
+
 /* ---------------- algebraic constraints ---------------- */
 
 static void enforce_point(double* u, ptrdiff_t sf, ptrdiff_t q, double w_floor) {

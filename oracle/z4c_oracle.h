@@ -29,6 +29,12 @@
  *   orc_move_patch      copies equal the old cells, prolonged cells exact
  *                       on degree-5 polynomials; shift and back restores
  *   orc_interp_point    exact on tricubic polynomials
+ *   orc_swsh            closed forms of l = 2, orthonormality to l = 8
+ *   orc_psi4_point      linearised plane waves along several directions:
+ *                       -d_t^2 (h_+ - i h_x) at 4th order; Schwarzschild:
+ *                       0 at 4th order
+ *   orc_psi4_modes      modes of a plane wave against a fine quadrature of
+ *                       its closed-form Psi4 on the sphere
  *   orc_adm_integrals   Schwarzschild in isotropic coordinates: M psi(r)
  *                       (closed form) at 4th order in dx; Bowen-York spin:
  *                       J_z = J and boost: P = P for any conformal factor;
@@ -173,6 +179,23 @@ void orc_stencils(const orc_patch* p, const double* u, int field, int i, int j, 
 int orc_adm_integrals(const orc_patch* p, const double* u, const double c[3], double r, int ntheta, int nphi,
                       double out[5]);
 void orc_gauss_legendre(int n, double* x, double* w);
+
+/* Psi4 extraction (Sec. 2.3).  Psi4 = (E_ij - i B_ij) mbar^i mbar^j with the
+ * vacuum electric and magnetic Weyl parts E_ij = R_ij - K_ik K^k_j + K K_ij,
+ * B_ij = sym(eps_i^kl D_k K_lj), interpolated (tricubic, cell centres) to the
+ * point, and mbar = (e_theta - i e_phi)/sqrt(2) from the orthonormal triad
+ * Gram-Schmidt-built (metric g) on the coordinate radial, theta and phi
+ * directions about c; for an outgoing wave h = h_+ - i h_x this gives
+ * Psi4 = -d_t^2 h.  orc_psi4_point: at angles (theta, phi), radius r.
+ * orc_psi4_modes: Psi4^lm = int Psi4 conj(_{-2}Y_lm) dOmega for l = 2..lmax,
+ * m = -l..l (out: Re, Im pairs in that order), Gauss-Legendre in cos(theta)
+ * times the trapezoid rule in phi.  -1 if a stencil leaves the array. */
+int orc_psi4_point(const orc_patch* p, const double* u, const double c[3], double r, double theta, double phi,
+                   double out[2]);
+int orc_psi4_modes(const orc_patch* p, const double* u, const double c[3], double r, int ntheta, int nphi,
+                   int lmax, double* out);
+/* spin-weight -2 spherical harmonic _{-2}Y_lm(theta, phi) (Re, Im) */
+void orc_swsh(int l, int m, double theta, double phi, double out[2]);
 
 /* Moving boxes (Sec. 2.2.1): the data of a patch shifted from geometry oldc
  * to newc (same level and size, origins a whole number of cells apart):
