@@ -223,6 +223,26 @@ sacrak_status sacrak_regrid(sacrak_grid* grid, int* moved);
 sacrak_status sacrak_adm_integrals(sacrak_grid* grid, int patch, const double centre[3],
                                    double radius, int ntheta, int nphi, double out[5]);
 
+/* Psi4 modes (Sec. 2.3) on the coordinate sphere |x - centre| = radius of
+ * one patch's current FP64 time level.  Psi4 = (E_ij - i B_ij) mbar^i mbar^j
+ * with the vacuum electric and magnetic Weyl parts E_ij = R_ij - K_ik K^k_j
+ * + K K_ij and B_ij = sym(eps_i^kl D_k K_lj) (R_ij the physical Ricci tensor
+ * of the right-hand side, D the physical covariant derivative), formed at
+ * cell centres and interpolated tricubically to the sphere points, and
+ * mbar = (e_theta - i e_phi)/sqrt(2) from the triad orthonormalised
+ * (Gram-Schmidt with g_ij) from the coordinate radial, theta and phi
+ * directions about centre; an outgoing wave h = h_+ - i h_x gives
+ * Psi4 = -d_t^2 h.  out[2k], out[2k+1] = Re, Im of
+ * Psi4^lm = int Psi4 conj(_{-2}Y_lm) dOmega for l = 2..lmax (lmax 2..8),
+ * m = -l..l, k counting in that order ((lmax+1)^2 - 4 modes), with ntheta
+ * Gauss-Legendre nodes in cos(theta) (1..1024) and nphi equally spaced phi
+ * points; 2 ntheta nphi must not exceed the doubles of one state copy of the
+ * patch, whose first RK stage buffer (dead between steps) holds the sphere
+ * values.  Host pointers; returns when out is written.  SACRAK_EINVAL for
+ * bad arguments or a sphere point within 2 cells of the array's edge. */
+sacrak_status sacrak_psi4_modes(sacrak_grid* grid, int patch, const double centre[3], double radius,
+                                int ntheta, int nphi, int lmax, double* out);
+
 /* max over all points (ghosts included) and fields of |f(x,y,z) - s_f f(-x,-y,z)|
  * for one patch centred on x = y = 0 (Sec. 3.2). */
 sacrak_status sacrak_pi_symmetry(sacrak_grid* grid, int patch, double* max_abs_diff);

@@ -31,7 +31,7 @@ EXPORTS = [
     "sacrak_last_error", "sacrak_profile_enable", "sacrak_profile_read", "sacrak_constraints_noalloc",
     "sacrak_set_stage_kernel", "sacrak_get_stage_kernel", "sacrak_autotune", "sacrak_adm_integrals",
     "sacrak_track_punctures", "sacrak_get_punctures", "sacrak_move_patch", "sacrak_regrid",
-    "sacrak_patch_origin",
+    "sacrak_patch_origin", "sacrak_psi4_modes",
 ]
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
@@ -307,6 +307,21 @@ class Grid:
         self._check(lib().sacrak_adm_integrals(self._h, patch, c, ctypes.c_double(radius), ntheta, nphi, out),
                     "adm_integrals")
         return tuple(float(v) for v in out)
+
+    def psi4_modes(self, patch: int, centre=(0.0, 0.0, 0.0), radius: float = 1.0, ntheta: int = 24,
+                   nphi: int = 48, lmax: int = 4):
+        """{(l, m): Psi4^lm} on the sphere |x - centre| = radius of the patch."""
+        c = (ctypes.c_double * 3)(*[float(v) for v in centre])
+        nm = (lmax + 1) ** 2 - 4
+        out = (ctypes.c_double * (2 * max(nm, 1)))()
+        self._check(lib().sacrak_psi4_modes(self._h, patch, c, ctypes.c_double(radius), ntheta, nphi, lmax, out),
+                    "psi4_modes")
+        modes, k = {}, 0
+        for l in range(2, lmax + 1):
+            for m in range(-l, l + 1):
+                modes[(l, m)] = complex(out[2 * k], out[2 * k + 1])
+                k += 1
+        return modes
 
     def pi_symmetry(self, patch: int = 0) -> float:
         v = ctypes.c_double()

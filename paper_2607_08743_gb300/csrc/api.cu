@@ -1314,6 +1314,46 @@ sacrak_status sacrak_regrid(sacrak_grid* g, int* moved) {
   return sync_and_check(g);
 }
 
+sacrak_status sacrak_psi4_modes(sacrak_grid* g, int patch, const double centre[3], double radius, int ntheta,
+                                int nphi, int lmax, double* out) {
+  if (!g) return SACRAK_EINVAL;
+  if (patch < 0 || patch >= g->npatches || !centre || !out || !(radius > 0.0) || !std::isfinite(radius) ||
+      ntheta < 1 || ntheta > ADM_MAX_THETA || nphi < 1 || nphi > (1 << 20) || lmax < 2 || lmax > PSI4_MAX_L ||
+      !std::isfinite(centre[0]) || !std::isfinite(centre[1]) || !std::isfinite(centre[2]))
+    return fail(g, SACRAK_EINVAL, "bad arguments");
+  const DevPatch& P = g->hp[patch];
+  const int nm = (lmax + 1) * (lmax + 1) - 4;
+  // the sphere values go to the patch's first stage buffer (dead between steps)
+  if (2.0 * ntheta * (double)nphi > (double)NF * P.fstride)
+    return fail(g, SACRAK_EINVAL, "ntheta x nphi too large for the patch's stage buffer");
+  if ((size_t)(3 * ntheta + 2 * nm) > g->L.scratch_doubles) return fail(g, SACRAK_EINVAL, "ntheta too large");
+  Psi4Args a;
+  a.patches = g->d_patches;
+  a.levels = g->d_levels;
+  a.patch = patch;
+  a.ntheta = ntheta;
+  a.nphi = nphi;
+  a.lmax = lmax;
+  for (int d = 0; d < 3; ++d) a.c[d] = centre[d];
+  a.r = radius;
+  a.psi = P.buf[B_S0];
+  a.ring = g->d_scratch;
+  a.out = g->d_scratch + 3 * ntheta;
+  launch_psi4(a, g->stream);
+  sacrak_status st = check_launch(g);
+  if (st != SACRAK_OK) return st;
+  std::vector<double> v(3 * ntheta + 2 * nm);
+  CK(cudaMemcpyAsync(v.data(), g->d_scratch, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, g->stream));
+  st = sync_and_check(g);
+  if (st != SACRAK_OK) return st;
+  double bad = 0.0;
+  for (int i = 0; i < ntheta; ++i) bad += v[2 * ntheta + i];
+  if (bad != 0.0)
+    return fail(g, SACRAK_EINVAL, "%.0f sphere points within 2 cells of the edge of patch %d", bad, patch);
+  for (int k = 0; k < 2 * nm; ++k) out[k] = v[3 * ntheta + k];
+  return SACRAK_OK;
+}
+
 sacrak_status sacrak_pi_symmetry(sacrak_grid* g, int patch, double* out) {
   if (!g) return SACRAK_EINVAL;
   if (patch < 0 || patch >= g->npatches || !out) return fail(g, SACRAK_EINVAL, "bad arguments");

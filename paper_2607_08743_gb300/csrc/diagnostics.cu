@@ -175,27 +175,6 @@ int launch_pi_symmetry(const DevPatch* p, const DevLevel* l, int patch, long lon
 // in cos(theta) times the trapezoid rule in phi.  One block per theta ring;
 // every sum runs in a fixed order.
 
-// Node i (descending in x) and weight of the n-point Gauss-Legendre rule on
-// [-1, 1]: Newton's method on P_n, evaluated with the three-term recurrence
-// (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}, from cos(pi (4i+3)/(4n+2)).
-__device__ void gauss_legendre_node(int n, int i, double& x, double& w) {
-  double z = cospi((4.0 * i + 3.0) / (4.0 * n + 2.0)), dpn = 1.0;
-  for (int it = 0; it < 64; ++it) {
-    double pkm1 = 1.0, pk = z;
-    for (int k = 1; k < n; ++k) {
-      const double pk1 = ((2.0 * k + 1.0) * z * pk - k * pkm1) / (k + 1.0);
-      pkm1 = pk;
-      pk = pk1;
-    }
-    dpn = n * (z * pk - pkm1) / (z * z - 1.0);  // P_n'(z) = n (z P_n - P_{n-1}) / (z^2 - 1)
-    const double step = pk / dpn;
-    z -= step;
-    if (fabs(step) < 1e-16) break;
-  }
-  x = z;
-  w = 2.0 / ((1.0 - z * z) * dpn * dpn);
-}
-
 // Integrands per coordinate area at array offset q: mass flux density m^i,
 // kk[i][j] = sqrt(g) K_i^j and sk = sqrt(g) K.
 __device__ void adm_cell_integrands(const double* __restrict__ u, long long fs, long long q,
@@ -251,15 +230,6 @@ __device__ void adm_cell_integrands(const double* __restrict__ u, long long fs, 
       kk[i][j] = sg * a;
     }
   sk = sg * K;
-}
-
-// cubic Lagrange basis on the nodes 0, 1, 2, 3 at position s
-__device__ __forceinline__ void cubic_weights(double s, double w[4]) {
-  const double s1 = s - 1.0, s2 = s - 2.0, s3 = s - 3.0;
-  w[0] = -s1 * s2 * s3 / 6.0;
-  w[1] = s * s2 * s3 / 2.0;
-  w[2] = -s * s1 * s3 / 2.0;
-  w[3] = s * s1 * s2 / 6.0;
 }
 
 constexpr int ADM_THREADS = 128;

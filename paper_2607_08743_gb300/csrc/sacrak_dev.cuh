@@ -163,6 +163,38 @@ __device__ __forceinline__ double delta6(const double* __restrict__ f, long long
   return (a - 6.0 * b) + 15.0 * c;
 }
 
+// Sphere quadrature and interpolation shared by the surface diagnostics
+
+// Node i (descending in x) and weight of the n-point Gauss-Legendre rule on
+// [-1, 1]: Newton's method on P_n, evaluated with the three-term recurrence
+// (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}, from cos(pi (4i+3)/(4n+2)).
+__device__ inline void gauss_legendre_node(int n, int i, double& x, double& w) {
+  double z = cospi((4.0 * i + 3.0) / (4.0 * n + 2.0)), dpn = 1.0;
+  for (int it = 0; it < 64; ++it) {
+    double pkm1 = 1.0, pk = z;
+    for (int k = 1; k < n; ++k) {
+      const double pk1 = ((2.0 * k + 1.0) * z * pk - k * pkm1) / (k + 1.0);
+      pkm1 = pk;
+      pk = pk1;
+    }
+    dpn = n * (z * pk - pkm1) / (z * z - 1.0);  // P_n'(z) = n (z P_n - P_{n-1}) / (z^2 - 1)
+    const double step = pk / dpn;
+    z -= step;
+    if (fabs(step) < 1e-16) break;
+  }
+  x = z;
+  w = 2.0 / ((1.0 - z * z) * dpn * dpn);
+}
+
+// cubic Lagrange basis on the nodes 0, 1, 2, 3 at position s
+__device__ __forceinline__ void cubic_weights(double s, double w[4]) {
+  const double s1 = s - 1.0, s2 = s - 2.0, s3 = s - 3.0;
+  w[0] = -s1 * s2 * s3 / 6.0;
+  w[1] = s * s2 * s3 / 2.0;
+  w[2] = -s * s1 * s3 / 2.0;
+  w[3] = s * s1 * s2 / 6.0;
+}
+
 // Kernel argument bundles ----------------------------------------------------
 
 // linear ghost-shell index -> (i,j,k) array indices (ghosts included): two z
@@ -317,6 +349,22 @@ struct MoveArgs {
   unsigned* err;
 };
 
+// Psi4 extraction (Sec. 2.3) on the sphere |x - c| = r of one patch's current
+// time level: Psi4 at the ntheta x nphi sphere points into psi (2 doubles
+// each), per ring the node, its weight and the points whose stencil leaves
+// the array into ring (3 * ntheta); then the modes l = 2..lmax, m = -l..l
+// into out (2 doubles each)
+constexpr int PSI4_MAX_L = 8;
+struct Psi4Args {
+  const DevPatch* patches;
+  const DevLevel* levels;
+  int patch, ntheta, nphi, lmax;
+  double c[3], r;
+  double* psi;
+  double* ring;
+  double* out;
+};
+
 // launchers (host)
 void launch_stage_fp64(const StageArgs& a, cudaStream_t st);
 void launch_stage_mixed(const StageArgs& a, cudaStream_t st);
@@ -344,6 +392,7 @@ void launch_level_advance(DevLevel* L, double dt, cudaStream_t st);
 void launch_repack(double* dst, const double* src, long long rows, int NX, int px, int to_pitched,
                    cudaStream_t st);
 void launch_init(const InitArgs& a, int patch, long long tot, cudaStream_t st);
+void launch_psi4(const Psi4Args& a, cudaStream_t st);
 // out6 = {M, J_z, P_x, P_y, P_z, points outside}
 void launch_adm(const AdmArgs& a, double* out6, cudaStream_t st);
 void launch_symmetrise(const DevPatch* p, const DevLevel* l, int patch, long long half_tot,

@@ -470,6 +470,278 @@ __global__ void __launch_bounds__(128) sommerfeld_stage_kernel(GhostArgs A) {
 // partial sums of H^2, (M^x)^2, (M^y)^2, (M^z)^2 and the count over active
 // points with W >= w_excise.
 
+// ---------------------------------------------------------------------------
+// Psi4 extraction (Sec. 2.3).  At cell q the vacuum electric and magnetic
+// parts of the Weyl tensor (physical, covariant) and the physical metric:
+//   E_ij = R_ij - K_ik K^k_j + K K_ij
+//   B_ij = 1/2 (eps_i^kl D_k K_lj + eps_j^kl D_k K_li),  eps_ikl = sqrt(g) [ikl]
+// with g_ij = gt_ij / W^2, K_ij = (At_ij + gt_ij K / 3) / W^2, K = Khat + 2
+// Theta, R_ij the RHS's physical Ricci tensor and Gamma^i_jk = Gt^i_jk -
+// (delta^i_j d_k W + delta^i_k d_j W - gt_jk gt^il d_l W) / W.
+__device__ __noinline__ void weyl_cell(const double* __restrict__ u, long long q, const long long st[3],
+                                       long long fs, double h, double E[6], double B[6], double gam[6]) {
+  const double c1 = 1.0 / (12.0 * h), c2 = c1 / h, c11 = c1 * c1;
+  PointState c;
+  load_centre(u, q, fs, c);
+  Geo G;
+  double dGam[3][3], dbe[3][3];
+  geometry(u, q, st, fs, c1, c2, c11, c, G, dGam, dbe);
+  const double W = c.W, W2 = W * W, iW = 1.0 / W;
+  const double K = c.Kh + 2.0 * c.Th;
+  double Kl[6], gu[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    gam[a] = c.gt[a] / W2;
+    Kl[a] = (c.At[a] + c.gt[a] * K / 3.0) / W2;
+    gu[a] = W2 * G.gtu[a];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      double kk = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double kup = gu[S2(k, 0)] * Kl[S2(0, j)] + gu[S2(k, 1)] * Kl[S2(1, j)] + gu[S2(k, 2)] * Kl[S2(2, j)];
+        kk += Kl[S2(i, k)] * kup;
+      }
+      E[S2(i, j)] = G.Ric[S2(i, j)] - kk + K * Kl[S2(i, j)];
+    }
+  // d_k K_ij from the derivatives of At, gt, W, Khat, Theta
+  double dK[3][6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double dKt = (d1u(u + F_KH * fs, q, st[d]) + 2.0 * d1u(u + F_TH * fs, q, st[d])) * c1;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const double dA = d1u(u + (F_AXX + a) * fs, q, st[d]) * c1;
+      const double dg = d1u(u + (F_GXX + a) * fs, q, st[d]) * c1;
+      dK[d][a] = (dA + dg * K / 3.0 + c.gt[a] * dKt / 3.0) / W2 - 2.0 * Kl[a] * G.dW[d] * iW;
+    }
+  }
+  double gw[3];  // gt^mn d_n W
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+    gw[m] = G.gtu[S2(m, 0)] * G.dW[0] + G.gtu[S2(m, 1)] * G.dW[1] + G.gtu[S2(m, 2)] * G.dW[2];
+  double Gp[3][6];  // physical Gamma^m_kl
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = k; l < 3; ++l) {
+        const double cw = (m == k ? G.dW[l] : 0.0) + (m == l ? G.dW[k] : 0.0) - c.gt[S2(k, l)] * gw[m];
+        Gp[m][S2(k, l)] = G.Gu[m][S2(k, l)] - cw * iW;
+      }
+  const double a0 = c.gt[3] * c.gt[5] - c.gt[4] * c.gt[4], a1 = c.gt[2] * c.gt[4] - c.gt[1] * c.gt[5],
+               a2 = c.gt[1] * c.gt[4] - c.gt[2] * c.gt[3];
+  const double sg = sqrt(c.gt[0] * a0 + c.gt[1] * a1 + c.gt[2] * a2) / (W2 * W);
+  // C_ij = eps_i^kl D_k K_lj, D_k K_lj = d_k K_lj - Gamma^m_kl K_mj - Gamma^m_kj K_lm
+  double C[3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    double DK[3][3];  // DK[k][l] = D_k K_lj
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        double v = dK[k][S2(l, j)];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) v -= Gp[m][S2(k, l)] * Kl[S2(m, j)] + Gp[m][S2(k, j)] * Kl[S2(l, m)];
+        DK[k][l] = v;
+      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int a = (i + 1) % 3, b = (i + 2) % 3;  // [iab] = +1, [iba] = -1
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+          v += (gu[S2(k, a)] * gu[S2(l, b)] - gu[S2(k, b)] * gu[S2(l, a)]) * DK[k][l];
+      C[i][j] = sg * v;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) B[S2(i, j)] = 0.5 * (C[i][j] + C[j][i]);
+}
+
+constexpr int PSI4_THREADS = 128;
+
+// One block per theta ring: Psi4 = (E_ij - i B_ij) mbar^i mbar^j at each of
+// its phi points, with E, B and g interpolated tricubically from the 4 x 4 x 4
+// nearest cell centres and mbar = (e_theta - i e_phi)/sqrt(2) from the triad
+// Gram-Schmidt-built (metric g) on the coordinate radial, theta and phi
+// directions.
+__global__ void __launch_bounds__(PSI4_THREADS) psi4_sphere_kernel(Psi4Args A) {
+  __shared__ double node[2];
+  __shared__ double red[PSI4_THREADS];
+  const int it = blockIdx.x;
+  if (threadIdx.x == 0) {
+    double x, w;
+    gauss_legendre_node(A.ntheta, it, x, w);
+    node[0] = x;
+    node[1] = w;
+    A.ring[it] = x;
+    A.ring[A.ntheta + it] = w;
+  }
+  __syncthreads();
+  const DevPatch* P = A.patches + A.patch;
+  const double* __restrict__ u = P->buf[A.levels[P->level].ring];
+  const long long st[3] = {1, P->px, P->plane};
+  const int N[3] = {P->NX, P->NY, P->NZ};
+  const double ct = node[0], sth = sqrt((1.0 - ct) * (1.0 + ct));
+  double bad = 0.0;
+  for (int ip = threadIdx.x; ip < A.nphi; ip += PSI4_THREADS) {
+    double sp, cp;
+    sincospi(2.0 * ip / A.nphi, &sp, &cp);
+    const double n[3] = {sth * cp, sth * sp, ct};
+    double wl[3][4];
+    int i0[3];
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double t = (A.c[d] + A.r * n[d] - P->origin[d]) / P->dx - 0.5 + GH;
+      ok = ok && t >= 3.0 && t < N[d] - 4.0;
+      i0[d] = ok ? (int)floor(t) - 1 : 0;
+      cubic_weights(ok ? t - i0[d] : 0.0, wl[d]);
+    }
+    double* out = A.psi + 2 * ((long long)it * A.nphi + ip);
+    if (!ok) {
+      bad += 1.0;
+      out[0] = out[1] = 0.0;
+      continue;
+    }
+    double E[6] = {0, 0, 0, 0, 0, 0}, B[6] = {0, 0, 0, 0, 0, 0}, g[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < 4; ++c)
+      for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+          const long long q = (i0[0] + a) + (i0[1] + b) * st[1] + (i0[2] + c) * st[2];
+          double Ec[6], Bc[6], gc[6];
+          weyl_cell(u, q, st, P->fstride, P->dx, Ec, Bc, gc);
+          const double w = wl[0][a] * wl[1][b] * wl[2][c];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            E[k] += w * Ec[k];
+            B[k] += w * Bc[k];
+            g[k] += w * gc[k];
+          }
+        }
+    double e[3][3];
+    const double v[3][3] = {{n[0], n[1], n[2]}, {ct * cp, ct * sp, -sth}, {-sp, cp, 0.0}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double w[3] = {v[a][0], v[a][1], v[a][2]};
+#pragma unroll
+      for (int b = 0; b < a; ++b) {
+        double dot = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) dot += g[S2(i, j)] * w[i] * e[b][j];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[i] -= dot * e[b][i];
+      }
+      double nn = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) nn += g[S2(i, j)] * w[i] * w[j];
+      nn = 1.0 / sqrt(nn);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) e[a][i] = w[i] * nn;
+    }
+    // mbar mbar = P - i Q; Psi4 = (E:P - B:Q) - i (E:Q + B:P)
+    double EP = 0.0, EQ = 0.0, BP = 0.0, BQ = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double Pm = 0.5 * (e[1][i] * e[1][j] - e[2][i] * e[2][j]);
+        const double Qm = 0.5 * (e[1][i] * e[2][j] + e[2][i] * e[1][j]);
+        EP += E[S2(i, j)] * Pm;
+        EQ += E[S2(i, j)] * Qm;
+        BP += B[S2(i, j)] * Pm;
+        BQ += B[S2(i, j)] * Qm;
+      }
+    out[0] = EP - BQ;
+    out[1] = -(EQ + BP);
+  }
+  red[threadIdx.x] = bad;
+  __syncthreads();
+  for (int o = PSI4_THREADS / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) A.ring[2 * A.ntheta + it] = red[0];
+}
+
+// _{-2}Y_lm amplitude sqrt((2l+1)/(4 pi)) d^l_{m,2}(theta) from the half-angle
+// cosine c and sine s (Wigner d-function as a finite sum)
+__device__ double swsh_amp(int l, int m, double c, double s) {
+  double f[2 * PSI4_MAX_L + 1];
+  f[0] = 1.0;
+  for (int i = 1; i <= 2 * l; ++i) f[i] = f[i - 1] * i;
+  const double pre = sqrt(f[l + m] * f[l - m] * f[l + 2] * f[l - 2]);
+  const int k1 = m - 2 > 0 ? m - 2 : 0, k2 = l + m < l - 2 ? l + m : l - 2;
+  double d = 0.0;
+  for (int k = k1; k <= k2; ++k) {
+    double t = pre / (f[l + m - k] * f[l - 2 - k] * f[k] * f[k + 2 - m]);
+    const int pc = 2 * l + m - 2 - 2 * k, ps = 2 * k + 2 - m;
+    for (int i = 0; i < pc; ++i) t *= c;
+    for (int i = 0; i < ps; ++i) t *= s;
+    d += (k & 1) ? -t : t;
+  }
+  return sqrt((2.0 * l + 1.0) / (4.0 * 3.141592653589793)) * d;
+}
+
+// One block per mode (l, m): Psi4^lm = sum over rings (in order) of the ring
+// weight times sum over phi (in order) of Psi4 conj(_{-2}Y_lm) 2 pi / nphi
+__global__ void __launch_bounds__(PSI4_THREADS) psi4_modes_kernel(Psi4Args A) {
+  __shared__ double red[2][PSI4_THREADS];
+  const int k = blockIdx.x;
+  int l = 2;
+  while ((l + 1) * (l + 1) - 4 <= k) ++l;
+  const int m = k - (l * l - 4) - l;
+  double ar = 0.0, ai = 0.0;
+  for (int it = threadIdx.x; it < A.ntheta; it += PSI4_THREADS) {
+    const double ct = A.ring[it], w = A.ring[A.ntheta + it];
+    const double amp = swsh_amp(l, m, sqrt(0.5 * (1.0 + ct)), sqrt(0.5 * (1.0 - ct)));
+    const double* ps = A.psi + 2 * (long long)it * A.nphi;
+    double sr = 0.0, si = 0.0;
+    for (int ip = 0; ip < A.nphi; ++ip) {
+      double sn, cs;
+      sincospi(2.0 * m * ip / A.nphi, &sn, &cs);
+      sr += ps[2 * ip] * cs + ps[2 * ip + 1] * sn;
+      si += ps[2 * ip + 1] * cs - ps[2 * ip] * sn;
+    }
+    ar += w * amp * sr;
+    ai += w * amp * si;
+  }
+  red[0][threadIdx.x] = ar;
+  red[1][threadIdx.x] = ai;
+  __syncthreads();
+  for (int o = PSI4_THREADS / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double dphi = 2.0 * 3.141592653589793 / A.nphi;
+    A.out[2 * k] = red[0][0] * dphi;
+    A.out[2 * k + 1] = red[1][0] * dphi;
+  }
+}
+
+void launch_psi4(const Psi4Args& a, cudaStream_t st) {
+  psi4_sphere_kernel<<<a.ntheta, PSI4_THREADS, 0, st>>>(a);
+  psi4_modes_kernel<<<(a.lmax + 1) * (a.lmax + 1) - 4, PSI4_THREADS, 0, st>>>(a);
+}
+
 __global__ void __launch_bounds__(128) constraints_kernel(ConsArgs A) {
   __shared__ double red[5][4];
   const Tile tl = A.tiles[blockIdx.x];
