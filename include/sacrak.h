@@ -243,6 +243,36 @@ sacrak_status sacrak_adm_integrals(sacrak_grid* grid, int patch, const double ce
 sacrak_status sacrak_psi4_modes(sacrak_grid* grid, int patch, const double centre[3], double radius,
                                 int ntheta, int nphi, int lmax, double* out);
 
+/* ---- Waveform post-processing (Sec. 2.3) ----
+ * Stream-ordered on cuda_stream (a cudaStream_t, NULL = legacy default), on
+ * device arrays owned by the caller; no grid needed. */
+
+/* Nakano extrapolation of one Psi4 mode's time series: n samples at times
+ * t[n], psi[2n] (Re, Im interleaved), mode index l >= 2, extraction radius
+ * r0 > 0 and total mass m0 > 0 with D0 / (2 m0) > 1, D0 = r0 (1 + m0/(2 r0))^2.
+ * Writes t_ret[n] = t - [D0 + 2 m0 ln(D0/(2 m0) - 1)] and out[2n] =
+ * D0 Psi4^{l,m,inf} = C [D0 psi - (l-1)(l+2)/2 int_{t_0}^t psi dt'] with
+ * C = 1 - 2 m0 / D0, the integral by the trapezoid rule from the first
+ * sample (a fixed-order chunked scan).  out must not alias psi.
+ * SACRAK_EINVAL for bad arguments. */
+sacrak_status sacrak_nakano(const double* t, const double* psi, int n, int l, double r0, double m0,
+                            double* t_ret, double* out, void* cuda_stream);
+
+/* Device work-area bytes sacrak_ffi_strain needs for n samples (0 if cuFFT
+ * cannot be loaded or n < 1). */
+size_t sacrak_ffi_work_bytes(int n);
+
+/* Fixed frequency integration of a uniformly sampled Psi4 mode psi[2n]
+ * (spacing dt) to the strain h[2n] (Re, Im; h = h_+ - i h_x):
+ * h = IFFT[ FFT(psi) / (2 pi max(|f|, f_cut))^2 ] over the DFT frequencies.
+ * cuFFT (libcufft.so, loaded at the first call) runs the transforms on the
+ * caller's work area (>= sacrak_ffi_work_bytes(n) bytes); its plan keeps its
+ * own small tables for the duration of the call.  Synchronises the stream.
+ * SACRAK_EINVAL for bad arguments or a short work area, SACRAK_ECUDA if
+ * cuFFT is missing or fails. */
+sacrak_status sacrak_ffi_strain(const double* psi, int n, double dt, double f_cut, double* h, void* work,
+                                size_t work_bytes, void* cuda_stream);
+
 /* max over all points (ghosts included) and fields of |f(x,y,z) - s_f f(-x,-y,z)|
  * for one patch centred on x = y = 0 (Sec. 3.2). */
 sacrak_status sacrak_pi_symmetry(sacrak_grid* grid, int patch, double* max_abs_diff);

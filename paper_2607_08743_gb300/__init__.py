@@ -31,7 +31,7 @@ EXPORTS = [
     "sacrak_last_error", "sacrak_profile_enable", "sacrak_profile_read", "sacrak_constraints_noalloc",
     "sacrak_set_stage_kernel", "sacrak_get_stage_kernel", "sacrak_autotune", "sacrak_adm_integrals",
     "sacrak_track_punctures", "sacrak_get_punctures", "sacrak_move_patch", "sacrak_regrid",
-    "sacrak_patch_origin", "sacrak_psi4_modes",
+    "sacrak_patch_origin", "sacrak_psi4_modes", "sacrak_nakano", "sacrak_ffi_work_bytes", "sacrak_ffi_strain",
 ]
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
@@ -104,8 +104,10 @@ def lib() -> ctypes.CDLL:
             L.sacrak_last_error.argtypes = [vp]
             L.sacrak_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
-                if name != "sacrak_arena_bytes" and name != "sacrak_last_error":
+                if name not in ("sacrak_arena_bytes", "sacrak_last_error", "sacrak_ffi_work_bytes"):
                     getattr(L, name).restype = ctypes.c_int
+            L.sacrak_ffi_work_bytes.argtypes = [ctypes.c_int]
+            L.sacrak_ffi_work_bytes.restype = ctypes.c_size_t
             _lib = L
     return _lib
 
@@ -155,6 +157,46 @@ def _ptr(a) -> int:
         return a.ctypes.data
     assert a.dtype.itemsize == 8 and a.is_contiguous()
     return a.data_ptr()
+
+
+def nakano_extrapolate(t, psi, l: int, r0: float, m0: float, stream=None):
+    """(t_ret, D0 Psi4^{l,m,inf}) of one mode's time series (Sec. 2.3), on
+    the GPU (numpy in, numpy out)."""
+    import torch
+    tt = torch.as_tensor(np.ascontiguousarray(t, dtype=np.float64), device="cuda")
+    pc = np.ascontiguousarray(np.asarray(psi, dtype=np.complex128))
+    pp = torch.as_tensor(pc.view(np.float64).copy(), device="cuda")
+    tr = torch.empty_like(tt)
+    out = torch.empty_like(pp)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().sacrak_nakano(ctypes.c_void_p(tt.data_ptr()), ctypes.c_void_p(pp.data_ptr()), len(tt), int(l),
+                             ctypes.c_double(r0), ctypes.c_double(m0), ctypes.c_void_p(tr.data_ptr()),
+                             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise SacrakError(st, "sacrak_nakano failed")
+    s.synchronize()
+    return tr.cpu().numpy(), out.cpu().numpy().view(np.complex128)
+
+
+def ffi_strain(psi, dt: float, f_cut: float, stream=None):
+    """Strain h = h_+ - i h_x of a uniformly sampled Psi4 mode by fixed
+    frequency integration (Sec. 2.3), on the GPU."""
+    import torch
+    pc = np.ascontiguousarray(np.asarray(psi, dtype=np.complex128))
+    pp = torch.as_tensor(pc.view(np.float64).copy(), device="cuda")
+    h = torch.empty_like(pp)
+    n = len(pc)
+    wb = lib().sacrak_ffi_work_bytes(n)
+    if wb == 0:
+        raise SacrakError(3, "cuFFT not available")
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().sacrak_ffi_strain(ctypes.c_void_p(pp.data_ptr()), n, ctypes.c_double(dt), ctypes.c_double(f_cut),
+                                 ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                                 ctypes.c_size_t(wb), ctypes.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise SacrakError(st, "sacrak_ffi_strain failed")
+    return h.cpu().numpy().view(np.complex128)
 
 
 def constraints_noalloc(dev_u, n, dx: float, w_excise: float = 0.0, stream=None) -> np.ndarray:
