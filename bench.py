@@ -206,7 +206,7 @@ def main():
                     help="gauge-wave: RK4 steps on the coarsest grid; robust-stability: steps per grid")
     ap.add_argument("--case", default="amr7",
                     choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep",
-                             "amr7-zsym", "adm", "amr7-moving"],
+                             "amr7-zsym", "adm", "amr7-moving", "psi4"],
                     help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
                          "mixed-error: the 7-level hierarchy in FP64 and mixed precision side by side")
     ap.add_argument("--coarse-steps", type=int, default=64, help="mixed-error: coarse steps")
@@ -255,6 +255,9 @@ def main():
         return
     if args.case == "amr7-moving":
         moving_case(torch, sk, args)
+        return
+    if args.case == "psi4":
+        psi4_case(torch, sk, args)
         return
 
     h = hierarchy()
@@ -462,6 +465,67 @@ def moving_case(torch, sk, args):
         del g
         torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
+
+
+def psi4_case(torch, sk, args):
+    """Psi4 extraction (Sec. 2.3) on the 7-level binary (mixed precision)
+    after --adm-steps coarse steps: the modes l = 2..8 on spheres of levels 0
+    and 1 (64 x 128 points), the GPU's time per call (CUDA events, the call
+    returns the modes to the host) and the oracle's on the downloaded state
+    (one host thread), their largest difference relative to the largest
+    mode, and the waveform post-processing (Nakano, FFI) of a 65536-sample
+    series on the GPU."""
+    import initial_data as idd
+    import oracle
+    from oracle import waveform
+    h = hierarchy()
+    g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(courant=args.courant, precision=1),
+                stream=torch.cuda.Stream())
+    g.set_initial_data(1, h.masses, h.positions)
+    for _ in range(args.adm_steps):
+        g.level_step(0)
+    torch.cuda.synchronize()
+    nt, nph, lmax, reps = 64, 128, 8, 10
+    rows = []
+    for pid, r in ((0, 100.0), (1, 40.0)):
+        p = h.patches[pid]
+        for _ in range(2):
+            mg = g.psi4_modes(pid, (0.0, 0.0, 0.0), r, nt, nph, lmax)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(g.stream)
+        for _ in range(reps):
+            mg = g.psi4_modes(pid, (0.0, 0.0, 0.0), r, nt, nph, lmax)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        u = g.download_fields(pid)
+        t0 = time.perf_counter()
+        mo = oracle.psi4_modes(p, u, (0.0, 0.0, 0.0), r, nt, nph, lmax)
+        to = time.perf_counter() - t0
+        scale = max(abs(v) for v in mo.values())
+        rows.append({"patch": pid, "r": r, "gpu_ms_per_call": ms, "oracle_ms_per_call": to * 1e3,
+                     "sphere_points_per_s": nt * nph / (ms * 1e-3),
+                     "max_mode": scale, "psi4_22": [mg[(2, 2)].real, mg[(2, 2)].imag],
+                     "max_diff_over_max_mode": max(abs(mg[k] - mo[k]) for k in mo) / scale})
+    g.close()
+    n = 65536
+    t = np.linspace(0.0, 2000.0, n)
+    psi = 1e-3 * np.exp(-1j * (0.05 * t + 1e-5 * t * t))
+    wt = {}
+    for name, fn in (("nakano", lambda: sk.nakano_extrapolate(t, psi, 2, 100.0, 1.0)),
+                     ("ffi", lambda: sk.ffi_strain(psi, t[1] - t[0], 0.005))):
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            fn()
+        wt[name + "_ms_per_call_incl_transfers"] = (time.perf_counter() - t0) / 5 * 1e3
+    t0 = time.perf_counter()
+    waveform.nakano_extrapolate(t, psi, 2, 100.0, 1.0)
+    wt["nakano_oracle_ms"] = (time.perf_counter() - t0) * 1e3
+    print(json.dumps({"case": "psi4", "coarse_steps": args.adm_steps, "ntheta": nt, "nphi": nph, "lmax": lmax,
+                      "rows": rows, "waveform_65536": wt}), flush=True)
 
 
 def adm_case(torch, sk, args):
