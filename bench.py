@@ -305,9 +305,10 @@ def main():
 
 
 # per-zone DRAM traffic of one stage-kernel launch from the ncu captures of the
-# 96^3 case (profiles/): FP64 1.53-1.98 GB, mixed (stage kernel 10) 0.854 GB
-# per 884,736 zones
-NCU_TRAFFIC_PER_ZONE = {0: 1.98e9 / 884736, 1: 0.854e9 / 884736}
+# 96^3 case (profiles/), by (precision, stage kernel id): FP64 1.98 GB, mixed
+# stage kernel 10 0.854 GB per 884,736 zones.  A kernel without a capture
+# reports no traffic.
+NCU_TRAFFIC_PER_ZONE = {(0, 0): 1.98e9 / 884736, (1, 10): 0.854e9 / 884736}
 
 
 def roofline(r, hbm):
@@ -325,7 +326,13 @@ def roofline(r, hbm):
     out["stage_kernels"] = k.get("stage_kernels")
     if k.get("autotune"):
         out["autotune"] = k["autotune"]
-    out.update({"traffic": NCU_TRAFFIC_PER_ZONE[0 if r["precision"] == "fp64" else 1] * k["zones_per_launch"],
+    prec = 0 if r["precision"] == "fp64" else 1
+    ids = k.get("kernel_ids_used") or []
+    per_zone = {NCU_TRAFFIC_PER_ZONE.get((prec, i)) for i in ids}
+    traffic = None
+    if len(per_zone) == 1 and None not in per_zone:  # every level on one captured kernel
+        traffic = per_zone.pop() * k["zones_per_launch"]
+    out.update({"traffic": traffic,
                 "kernel": k["name"], "launch_ms": k["ms"], "launches_per_step": k["launches"] / k["steps"],
                 "share_of_step": k["ms"] * k["launches"] / k["steps"] / r["ms"],
                 "algorithmic_bytes_per_launch": k["bytes_per_launch"],
@@ -364,6 +371,7 @@ def measure(torch, sk, h, precision, args, world, dist):
     kern = stage_kernel_timing(g, nprof)
     kern["steps"] = nprof
     g.close()
+    kern["kernel_ids_used"] = sorted(set(kern["kernel_ids"]))
     kern["stage_kernels"] = [sk.STAGE_KERNELS[k] for k in kern.pop("kernel_ids")]
     if tune:
         kern["autotune"] = tune
@@ -864,7 +872,7 @@ def stage_kernel_timing(g, steps):
         import paper_2607_08743_gb300 as sk
         kn = {0: "z4c_stage_mixed_kernel"}
         kn.update({k: "z4c_stage_tma_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (1, 2, 3, 4)})
-        kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6, 8, 9, 10, 11)})
+        kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6, 8, 9, 10, 11, 12, 13)})
         kn[7] = "z4c_deriv_kernel + z4c_algebra_kernel"
         names = sorted({kn[k] for k in ids})
         name = " + ".join(names)

@@ -38,7 +38,9 @@ void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st);
 // prefetches the next field's stencil rows into L1 and the epilogue's
 // streaming reads into L2; 2 as 1 with 4 CTAs per SM (128 registers); 3 as 1
 // with only the star rows prefetched; 4 only the z-arm rows; 5 only the
-// epilogue's reads.  ldg_setup opts the kernels in to their shared memory
+// epilogue's reads; 6 as 4 with the x-neighbour inner differences of the
+// mixed derivatives D_x D_y, D_x D_z exchanged by warp shuffles; 7 as 6 with
+// 4 CTAs per SM.  ldg_setup opts the kernels in to their shared memory
 // (false on failure).
 int ldg_setup(int v);
 void launch_stage_ldg(int v, const StageArgs& a, cudaStream_t st);

@@ -225,14 +225,32 @@ struct GlobalAcc {
 // One field, values from `at`: forms the plan's derivatives into the slots
 // (NT columns), the advection + dissipation sum into S_AK + F, and returns
 // the centre value.
-template <bool SPLIT, class Acc, class Slots>
+// The unscaled first difference 8 (f_1 - f_-1) - (f_2 - f_-2) along B at the
+// point `at` + k e_A, summed from its hi/lo pair (the inner derivative of the
+// nested mixed derivative D_A (D_B f)).
+template <class Acc>
+__device__ __forceinline__ float inner_d1(const Acc& at, int A, int B, int k) {
+  auto pt = [&](int kb) {
+    return at((A == 0 ? k : 0) + (B == 0 ? kb : 0), (A == 1 ? k : 0) + (B == 1 ? kb : 0),
+              (A == 2 ? k : 0) + (B == 2 ? kb : 0));
+  };
+  return hsum(fma2s(sub2(pt(1), pt(-1)), 8.0f, sub2(pt(-2), pt(2))));
+}
+
+// D_A (D_B f) * 144 h^2 from the inner differences at A-offsets +1, -1, +2, -2
+__device__ __forceinline__ float outer_d1(float gp1, float gm1, float gp2, float gm2) {
+  return __fmaf_rn(__fsub_rn(gp1, gm1), 8.0f, __fsub_rn(gm2, gp2));
+}
+
+template <bool SPLIT, class Acc, class Slots, bool SHF = false>
 __device__ __forceinline__ float field_pass_p(const Acc& at, const FieldPlan P, const int F, const Slots& SD,
                                               const float wko[3], const float wup[3], float c1, float c2,
-                                              float c11, const float gtu[6]) {
+                                              float c11, const float gtu[6], bool full = false) {
 #define AT(d, k) at((d) == 0 ? (k) : 0, (d) == 1 ? (k) : 0, (d) == 2 ? (k) : 0)
   const float2 c0 = at(0, 0, 0);
   float2 acc = make_float2(0.0f, 0.0f);
   float dd[6];  // second derivatives, symmetric index
+  float g1[3];  // unscaled first differences at the point (the inner ones of D_x D_y, D_x D_z)
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const float2 m3 = AT(d, -3), m2 = AT(d, -2), m1 = AT(d, -1);
@@ -247,14 +265,49 @@ __device__ __forceinline__ float field_pass_p(const Acc& at, const FieldPlan P, 
     const float2 as = fma2s(e1, 21.0f, fma2s(e2n, 6.0f, e3));
     acc = fma2s(ko, wko[d], acc);
     acc = fma2s(as, wup[d], acc);
-    if (P.d1 >= 0) SD(P.d1 + P.d1s * d) = hsum(fma2s(e1, 8.0f, e2n)) * c1;
+    g1[d] = hsum(fma2s(e1, 8.0f, e2n));
+    if (P.d1 >= 0) SD(P.d1 + P.d1s * d) = g1[d] * c1;
     if (P.d2 != 0) dd[d == 0 ? 0 : (d == 1 ? 3 : 5)] = hsum(fma2s(cc, 16.0f, neg2(b))) * c2;
   }
   if (P.d2 != 0) {
     // nested D_a (D_b f) from pair differences, (a, b) = (x, y), (x, z), (y, z)
     constexpr int PA[3] = {0, 0, 1}, PB[3] = {1, 2, 2}, PS[3] = {1, 2, 4};
+    int m0 = 0;
+    if (SHF) {
+      // (x, y) and (x, z): the inner differences at the x neighbours are the
+      // lanes' own g1 (a warp is 32 consecutive x); the four outside the warp
+      // (x0 - 2, x0 - 1, x0 + 32, x0 + 33) come from lanes 0..3.  A warp that
+      // does not fill its 32 x loads them all, in the same arithmetic.
+      const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
+      for (int m = 0; m < 2; ++m) {
+        const int B = PB[m];
+        float gp1, gm1, gp2, gm2;
+        if (full) {
+          float hg = 0.0f;
+          if (lane < 4) hg = inner_d1(at, 0, B, lane < 2 ? -2 : 30);
+          auto nb = [&](int k) {
+            const int src = lane + k;
+            const float v = __shfl_sync(0xffffffffu, g1[B], src & 31);
+            const float hv = __shfl_sync(0xffffffffu, hg, (src < 0 ? src + 2 : src - 30) & 3);
+            return (src >= 0 && src < 32) ? v : hv;
+          };
+          gp1 = nb(1);
+          gm1 = nb(-1);
+          gp2 = nb(2);
+          gm2 = nb(-2);
+        } else {
+          gp1 = inner_d1(at, 0, B, 1);
+          gm1 = inner_d1(at, 0, B, -1);
+          gp2 = inner_d1(at, 0, B, 2);
+          gm2 = inner_d1(at, 0, B, -2);
+        }
+        dd[PS[m]] = outer_d1(gp1, gm1, gp2, gm2) * c11;
+      }
+      m0 = 2;
+    }
+#pragma unroll
+    for (int m = m0; m < 3; ++m) {
       const int A = PA[m], B = PB[m];
       float2 inner[4];
       constexpr int KA[4] = {1, -1, 2, -2};
@@ -708,7 +761,7 @@ __device__ __forceinline__ void prefetch_field(const float2* F, long long sy, lo
 // PF: 0 no prefetching, 1 the next field's star and mixed-derivative rows,
 // 2 its star rows only, 3 its z-arm rows only, 4 none of its rows (only the
 // epilogue's streaming reads into L2)
-template <int MINB, int MODE, int PF>
+template <int MINB, int MODE, int PF, bool SHF = false>
 __global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
   extern __shared__ float sd[];
   const Tile tl = S.tiles[blockIdx.x];
@@ -716,6 +769,9 @@ __global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
   const int t = threadIdx.x;
   const int i = tl.x0 + (t & 31), j = tl.y0 + (t >> 5), k = tl.z0;
   if (i >= P->n[0] || j >= P->n[1] || k >= P->n[2]) return;
+  // every lane of the warp is alive (its row is inside the patch, and so are
+  // all 32 x of the tile): the x-neighbour exchange by shuffles is allowed
+  const bool full = tl.x0 + 32 <= P->n[0];
   const int ring = S.lev->ring, s = S.stage;
   const long long sy = P->px, sz = P->plane, fs = P->fstride;
   const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
@@ -742,7 +798,8 @@ __global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
       prefetch_field(U + (long long)(f + 1) * fs + q, sy, sz, PF == 1 && plan(f + 1).d2 != 0);
     if (PF == 3 && f + 1 < NF) prefetch_zarms(U + (long long)(f + 1) * fs + q, sz);
     const GlobalAcc at{U + (long long)f * fs + q, sy, sz};
-    field_pass_p<false>(at, plan(f), f, SmemSlots<128>{sd, t}, wko, wup, c1, c2, c11, gtu);
+    field_pass_p<false, GlobalAcc, SmemSlots<128>, SHF>(at, plan(f), f, SmemSlots<128>{sd, t}, wko, wup, c1, c2,
+                                                         c11, gtu, full);
   }
   float cen[NF];
 #pragma unroll
@@ -761,22 +818,22 @@ __global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
   }
 }
 
-template <int MINB, int PF>
+template <int MINB, int PF, bool SHF = false>
 bool setup_ldg() {
   const int smem = NSLOT * 128 * 4;
-  return cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 0, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem) == cudaSuccess &&
-         cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 1, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem) == cudaSuccess;
+  return cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 0, PF, SHF>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+         cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 1, PF, SHF>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
 }
 
-template <int MINB, int PF>
+template <int MINB, int PF, bool SHF = false>
 void launch_ldg(const StageArgs& a, cudaStream_t st) {
   const int smem = NSLOT * 128 * 4;
   if (a.stage == 0)
-    z4c_stage_ldg_kernel<MINB, 1, PF><<<a.ntiles, 128, smem, st>>>(a);
+    z4c_stage_ldg_kernel<MINB, 1, PF, SHF><<<a.ntiles, 128, smem, st>>>(a);
   else
-    z4c_stage_ldg_kernel<MINB, 0, PF><<<a.ntiles, 128, smem, st>>>(a);
+    z4c_stage_ldg_kernel<MINB, 0, PF, SHF><<<a.ntiles, 128, smem, st>>>(a);
 }
 
 // ------------------------------------------------------------------ split path
@@ -890,7 +947,8 @@ void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st) {
 
 // variant v: 0 (3 CTAs/SM, no prefetch), 1 (3, prefetch), 2 (4, prefetch),
 // 3 (3, prefetch of the star rows only), 4 (3, z-arm rows only), 5 (3, the
-// epilogue's reads only)
+// epilogue's reads only), 6 (as 4, the x-neighbour inner differences of the
+// mixed derivatives exchanged by warp shuffles), 7 (as 6 with 4 CTAs/SM)
 int ldg_setup(int v) {
   switch (v) {
     case 0: return setup_ldg<3, 0>();
@@ -899,6 +957,8 @@ int ldg_setup(int v) {
     case 3: return setup_ldg<3, 2>();
     case 4: return setup_ldg<3, 3>();
     case 5: return setup_ldg<3, 4>();
+    case 6: return setup_ldg<3, 3, true>();
+    case 7: return setup_ldg<4, 3, true>();
   }
   return 0;
 }
@@ -912,6 +972,8 @@ void launch_stage_ldg(int v, const StageArgs& a, cudaStream_t st) {
     case 3: launch_ldg<3, 2>(a, st); break;
     case 4: launch_ldg<3, 3>(a, st); break;
     case 5: launch_ldg<3, 4>(a, st); break;
+    case 6: launch_ldg<3, 3, true>(a, st); break;
+    case 7: launch_ldg<4, 3, true>(a, st); break;
   }
 }
 
