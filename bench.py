@@ -305,10 +305,12 @@ def main():
 
 
 # per-zone DRAM traffic of one stage-kernel launch from the ncu captures of the
-# 96^3 case (profiles/), by (precision, stage kernel id): FP64 1.98 GB, mixed
-# stage kernel 10 0.854 GB per 884,736 zones.  A kernel without a capture
-# reports no traffic.
-NCU_TRAFFIC_PER_ZONE = {(0, 0): 1.98e9 / 884736, (1, 10): 0.854e9 / 884736}
+# 96^3 case (profiles/), by (precision, stage kernel id): FP64 1.98 GB; mixed
+# stage kernel 10 0.8531 GB, kernel 11 0.8518 GB, kernel 13 0.9256 GB per
+# 884,736 zones.  A kernel without a capture reports no traffic; levels on
+# different captured kernels report the largest.
+NCU_TRAFFIC_PER_ZONE = {(0, 0): 1.98e9 / 884736, (1, 10): 0.8531e9 / 884736, (1, 11): 0.8518e9 / 884736,
+                        (1, 13): 0.9256e9 / 884736}
 
 
 def roofline(r, hbm):
@@ -328,10 +330,10 @@ def roofline(r, hbm):
         out["autotune"] = k["autotune"]
     prec = 0 if r["precision"] == "fp64" else 1
     ids = k.get("kernel_ids_used") or []
-    per_zone = {NCU_TRAFFIC_PER_ZONE.get((prec, i)) for i in ids}
+    per_zone = [NCU_TRAFFIC_PER_ZONE.get((prec, i)) for i in ids]
     traffic = None
-    if len(per_zone) == 1 and None not in per_zone:  # every level on one captured kernel
-        traffic = per_zone.pop() * k["zones_per_launch"]
+    if per_zone and None not in per_zone:  # every level on a captured kernel
+        traffic = max(per_zone) * k["zones_per_launch"]
     out.update({"traffic": traffic,
                 "kernel": k["name"], "launch_ms": k["ms"], "launches_per_step": k["launches"] / k["steps"],
                 "share_of_step": k["ms"] * k["launches"] / k["steps"] / r["ms"],
