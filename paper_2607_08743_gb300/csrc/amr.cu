@@ -324,6 +324,9 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
   const int pr = A.plev->ring;
   const bool q3 = A.plev->nvalid >= 3;
   const double w0 = q3 ? A.wq[0] : 0.0, w1 = q3 ? A.wq[1] : A.wl[1], w2 = q3 ? A.wq[2] : A.wl[2];
+  // at a parent time level (the start of the first child step, the end of
+  // the second) only one weight is non-zero: the other slots are not read
+  const bool u0 = q3 && w0 != 0.0, u1 = w1 != 0.0, u2 = w2 != 0.0;
   const double* __restrict__ g0 = C->gsh[(pr + 1) % 3];
   const double* __restrict__ g1 = C->gsh[(pr + 2) % 3];
   const double* __restrict__ g2 = C->gsh[pr];
@@ -338,8 +341,9 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
 #pragma unroll
     for (int f = f0; f < f0 + NF / 5; ++f) {
       const long long o = f * C->fstride + q;
-      double v = w1 * g1[o] + w2 * g2[o];
-      if (q3) v += w0 * g0[o];
+      // (a zero weight times a finite cached value adds exactly nothing)
+      double v = (u1 && u2) ? w1 * g1[o] + w2 * g2[o] : (u1 ? w1 * g1[o] : w2 * g2[o]);
+      if (u0) v += w0 * g0[o];
       dst[o] = v;
       if (dual) dst3[o] = v;
     }
@@ -359,18 +363,20 @@ __global__ void ghost_time_fill_kernel(FillArgs A) {
 #pragma unroll
   for (int f = f0; f < f0 + NF / 5; ++f) {
     const long long o = f * C->fstride + q;
-    const float2 a1 = h1[o], a2 = h2[o];
-    const float2 a0 = q3 ? h0[o] : make_float2(0.0f, 0.0f);
+    const float2 z = make_float2(0.0f, 0.0f);
+    const float2 a1 = u1 ? h1[o] : z, a2 = u2 ? h2[o] : z;
+    const float2 a0 = u0 ? h0[o] : z;
     if (later) {
       const float hi = C->hl[ring][o].x;
       float lo = w1f * ((a1.x - hi) + a1.y) + w2f * ((a2.x - hi) + a2.y);
-      if (q3) lo += w0f * ((a0.x - hi) + a0.y);
+      if (u0) lo += w0f * ((a0.x - hi) + a0.y);
       in[o] = make_float2(hi, lo);
       if (dual) in3[o] = make_float2(hi, lo);
     } else {
-      const float r = a1.x;
-      float d = w1f * a1.y + w2f * ((a2.x - r) + a2.y);
-      if (q3) d += w0f * ((a0.x - r) + a0.y);
+      // differences from the hi part of the first slot read
+      const float r = u1 ? a1.x : a2.x;
+      float d = u1 ? w1f * a1.y + w2f * ((a2.x - r) + a2.y) : w2f * a2.y;
+      if (u0) d += w0f * ((a0.x - r) + a0.y);
       const double v = (double)r + (double)d;
       C->buf[ring][o] = v;
       split_to(v, C->hl[ring], o);
