@@ -238,7 +238,8 @@ sacrak_status sacrak_adm_integrals(sacrak_grid* grid, int patch, const double ce
  * Gauss-Legendre nodes in cos(theta) (1..1024) and nphi equally spaced phi
  * points; 2 ntheta nphi must not exceed the doubles of one state copy of the
  * patch, whose first RK stage buffer (dead between steps) holds the sphere
- * values.  Host pointers; returns when out is written.  SACRAK_EINVAL for
+ * values (its second holds E, B and g of the cells near the sphere, formed
+ * once each).  Host pointers; returns when out is written.  SACRAK_EINVAL for
  * bad arguments or a sphere point within 2 cells of the array's edge. */
 sacrak_status sacrak_psi4_modes(sacrak_grid* grid, int patch, const double centre[3], double radius,
                                 int ntheta, int nphi, int lmax, double* out);

@@ -1324,7 +1324,8 @@ sacrak_status sacrak_psi4_modes(sacrak_grid* g, int patch, const double centre[3
     return fail(g, SACRAK_EINVAL, "bad arguments");
   const DevPatch& P = g->hp[patch];
   const int nm = (lmax + 1) * (lmax + 1) - 4;
-  // the sphere values go to the patch's first stage buffer (dead between steps)
+  // the sphere values go to the patch's first RK stage buffer, the per-cell
+  // Weyl parts to its second (both dead between steps)
   if (2.0 * ntheta * (double)nphi > (double)NF * P.fstride)
     return fail(g, SACRAK_EINVAL, "ntheta x nphi too large for the patch's stage buffer");
   if ((size_t)(3 * ntheta + 2 * nm) > g->L.scratch_doubles) return fail(g, SACRAK_EINVAL, "ntheta too large");
@@ -1338,9 +1339,10 @@ sacrak_status sacrak_psi4_modes(sacrak_grid* g, int patch, const double centre[3
   for (int d = 0; d < 3; ++d) a.c[d] = centre[d];
   a.r = radius;
   a.psi = P.buf[B_S0];
+  a.cells = P.buf[B_S1];
   a.ring = g->d_scratch;
   a.out = g->d_scratch + 3 * ntheta;
-  launch_psi4(a, g->stream);
+  launch_psi4(a, (long long)P.NX * P.NY * P.NZ, g->stream);
   sacrak_status st = check_launch(g);
   if (st != SACRAK_OK) return st;
   std::vector<double> v(3 * ntheta + 2 * nm);

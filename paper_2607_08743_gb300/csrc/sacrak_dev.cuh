@@ -363,6 +363,7 @@ struct Psi4Args {
   double* psi;
   double* ring;
   double* out;
+  double* cells;  // E_ij, B_ij, g_ij (18 fields, patch layout) of the cells near the sphere
 };
 
 // launchers (host)
@@ -392,7 +393,7 @@ void launch_level_advance(DevLevel* L, double dt, cudaStream_t st);
 void launch_repack(double* dst, const double* src, long long rows, int NX, int px, int to_pitched,
                    cudaStream_t st);
 void launch_init(const InitArgs& a, int patch, long long tot, cudaStream_t st);
-void launch_psi4(const Psi4Args& a, cudaStream_t st);
+void launch_psi4(const Psi4Args& a, long long patch_points, cudaStream_t st);
 // out6 = {M, J_z, P_x, P_y, P_z, points outside}
 void launch_adm(const AdmArgs& a, double* out6, cudaStream_t st);
 void launch_symmetrise(const DevPatch* p, const DevLevel* l, int patch, long long half_tot,

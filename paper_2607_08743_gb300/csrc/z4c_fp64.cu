@@ -570,9 +570,35 @@ __device__ __noinline__ void weyl_cell(const double* __restrict__ u, long long q
 
 constexpr int PSI4_THREADS = 128;
 
-// One block per theta ring: Psi4 = (E_ij - i B_ij) mbar^i mbar^j at each of
-// its phi points, with E, B and g interpolated tricubically from the 4 x 4 x 4
-// nearest cell centres and mbar = (e_theta - i e_phi)/sqrt(2) from the triad
+// Pass 1: E_ij, B_ij and g_ij of every cell whose centre lies within 3.6 dx
+// of the sphere (the interpolation cells of any sphere point are within
+// 2 sqrt(3) dx of it) and whose derivative stencils stay in the array, into
+// 18 fields of `cells`.
+__global__ void __launch_bounds__(128) psi4_cells_kernel(Psi4Args A) {
+  const DevPatch* P = A.patches + A.patch;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)P->NX * P->NY * P->NZ) return;
+  const int i = (int)(id % P->NX), j = (int)((id / P->NX) % P->NY), k = (int)(id / ((long long)P->NX * P->NY));
+  if (i < 2 || j < 2 || k < 2 || i > P->NX - 3 || j > P->NY - 3 || k > P->NZ - 3) return;
+  const double dx = P->origin[0] + (i - GH + 0.5) * P->dx - A.c[0];
+  const double dy = P->origin[1] + (j - GH + 0.5) * P->dx - A.c[1];
+  const double dz = P->origin[2] + (k - GH + 0.5) * P->dx - A.c[2];
+  if (fabs(sqrt(dx * dx + dy * dy + dz * dz) - A.r) > 3.6 * P->dx) return;
+  const long long st[3] = {1, P->px, P->plane};
+  const long long q = i + (long long)j * P->px + (long long)k * P->plane;
+  double E[6], B[6], g[6];
+  weyl_cell(P->buf[A.levels[P->level].ring], q, st, P->fstride, P->dx, E, B, g);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    A.cells[a * P->fstride + q] = E[a];
+    A.cells[(6 + a) * P->fstride + q] = B[a];
+    A.cells[(12 + a) * P->fstride + q] = g[a];
+  }
+}
+
+// Pass 2, one block per theta ring: Psi4 = (E_ij - i B_ij) mbar^i mbar^j at
+// each of its phi points, with E, B and g interpolated tricubically from the
+// pass-1 values of the 4 x 4 x 4 nearest cell centres and mbar = (e_theta - i e_phi)/sqrt(2) from the triad
 // Gram-Schmidt-built (metric g) on the coordinate radial, theta and phi
 // directions.
 __global__ void __launch_bounds__(PSI4_THREADS) psi4_sphere_kernel(Psi4Args A) {
@@ -619,14 +645,13 @@ __global__ void __launch_bounds__(PSI4_THREADS) psi4_sphere_kernel(Psi4Args A) {
       for (int b = 0; b < 4; ++b)
         for (int a = 0; a < 4; ++a) {
           const long long q = (i0[0] + a) + (i0[1] + b) * st[1] + (i0[2] + c) * st[2];
-          double Ec[6], Bc[6], gc[6];
-          weyl_cell(u, q, st, P->fstride, P->dx, Ec, Bc, gc);
+          const double* cq = A.cells + q;
           const double w = wl[0][a] * wl[1][b] * wl[2][c];
 #pragma unroll
           for (int k = 0; k < 6; ++k) {
-            E[k] += w * Ec[k];
-            B[k] += w * Bc[k];
-            g[k] += w * gc[k];
+            E[k] += w * cq[k * P->fstride];
+            B[k] += w * cq[(6 + k) * P->fstride];
+            g[k] += w * cq[(12 + k) * P->fstride];
           }
         }
     double e[3][3];
@@ -737,7 +762,8 @@ __global__ void __launch_bounds__(PSI4_THREADS) psi4_modes_kernel(Psi4Args A) {
   }
 }
 
-void launch_psi4(const Psi4Args& a, cudaStream_t st) {
+void launch_psi4(const Psi4Args& a, long long patch_points, cudaStream_t st) {
+  psi4_cells_kernel<<<(unsigned)((patch_points + 127) / 128), 128, 0, st>>>(a);
   psi4_sphere_kernel<<<a.ntheta, PSI4_THREADS, 0, st>>>(a);
   psi4_modes_kernel<<<(a.lmax + 1) * (a.lmax + 1) - 4, PSI4_THREADS, 0, st>>>(a);
 }
