@@ -198,39 +198,44 @@ __device__ __forceinline__ void cubic_weights(double s, double w[4]) {
 // Kernel argument bundles ----------------------------------------------------
 
 // linear ghost-shell index -> (i,j,k) array indices (ghosts included): two z
-// slabs, then two y slabs over the middle z range, then two x slabs
-__device__ __forceinline__ void shell_ijk(long long id, int NX, int NY, int NZ, int& i, int& j,
-                                          int& k) {
-  const long long zslab = (long long)GH * NY * NX;
+// slabs, then two y slabs over the middle z range, then two x slabs.  32-bit
+// arithmetic: a shell has fewer than 2^31 points for patches of up to 4096
+// cells per axis, and 64-bit division would dominate the cost of the fills.
+__device__ __forceinline__ void shell_ijk(long long id64, int NX, int NY, int NZ, int& i, int& j, int& k) {
+  int id = (int)id64;
+  const int zslab = GH * NY * NX;
   const int nz = NZ - 2 * GH, ny = NY - 2 * GH;
-  const long long yslab = (long long)GH * NX * nz;
+  const int yslab = GH * NX * nz;
   if (id < 2 * zslab) {
-    int side = id >= zslab;
-    long long r = id - side * zslab;
-    i = (int)(r % NX);
-    r /= NX;
-    j = (int)(r % NY);
-    k = (int)(r / NY) + (side ? NZ - GH : 0);
+    const int side = id >= zslab;
+    int r = id - side * zslab;
+    const int rr = r / NX;
+    i = r - rr * NX;
+    k = rr / NY;
+    j = rr - k * NY;
+    k += side ? NZ - GH : 0;
     return;
   }
   id -= 2 * zslab;
   if (id < 2 * yslab) {
-    int side = id >= yslab;
-    long long r = id - side * yslab;
-    i = (int)(r % NX);
-    r /= NX;
-    j = (int)(r % GH) + (side ? NY - GH : 0);
-    k = (int)(r / GH) + GH;
+    const int side = id >= yslab;
+    const int r = id - side * yslab;
+    const int rr = r / NX;
+    i = r - rr * NX;
+    k = rr / GH;
+    j = rr - k * GH + (side ? NY - GH : 0);
+    k += GH;
     return;
   }
   id -= 2 * yslab;
-  const long long xslab = (long long)GH * ny * nz;
-  int side = id >= xslab;
-  long long r = id - side * xslab;
-  i = (int)(r % GH) + (side ? NX - GH : 0);
-  r /= GH;
-  j = (int)(r % ny) + GH;
-  k = (int)(r / ny) + GH;
+  const int xslab = GH * ny * nz;
+  const int side = id >= xslab;
+  const int r = id - side * xslab;
+  const int rr = r / GH;
+  i = r - rr * GH + (side ? NX - GH : 0);
+  k = rr / ny;
+  j = rr - k * ny + GH;
+  k += GH;
 }
 
 __host__ __device__ inline long long shell_count(int NX, int NY, int NZ) {
