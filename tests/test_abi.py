@@ -64,3 +64,30 @@ def test_invalid_arguments_rejected_before_device_work(L):
     assert L.sacrak_level_step(None, 0) == sk.EINVAL
     assert L.sacrak_grid_destroy(None) == sk.EINVAL
     assert L.sacrak_last_error(None) == b"null grid"
+
+
+def test_diagnostics_and_moving_boxes_reject_before_device_work(L):
+    """The newer entry points validate their handles and arguments on the
+    host: null grids, null arrays and impossible parameters return
+    SACRAK_EINVAL without touching a device."""
+    d = ctypes.c_double
+    c3 = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    out = (ctypes.c_double * 160)()
+    assert L.sacrak_adm_integrals(None, 0, c3, d(1.0), 8, 16, out) == sk.EINVAL
+    assert L.sacrak_psi4_modes(None, 0, c3, d(1.0), 8, 16, 2, out) == sk.EINVAL
+    assert L.sacrak_track_punctures(None, 0, None, None) == sk.EINVAL
+    assert L.sacrak_get_punctures(None, out) == sk.EINVAL
+    assert L.sacrak_move_patch(None, 0, (ctypes.c_int * 3)(1, 0, 0)) == sk.EINVAL
+    assert L.sacrak_regrid(None, ctypes.byref(ctypes.c_int())) == sk.EINVAL
+    assert L.sacrak_patch_origin(None, 0, c3) == sk.EINVAL
+    # waveform post-processing: null arrays, n < 1, l < 2, r0 = m0 / 2
+    # (D0 / (2 m0) = 1), non-positive spacing or cut
+    p = ctypes.c_void_p(256)
+    assert L.sacrak_nakano(None, p, 8, 2, d(100.0), d(1.0), p, p, None) == sk.EINVAL
+    assert L.sacrak_nakano(p, p, 0, 2, d(100.0), d(1.0), p, p, None) == sk.EINVAL
+    assert L.sacrak_nakano(p, p, 8, 1, d(100.0), d(1.0), p, p, None) == sk.EINVAL
+    assert L.sacrak_nakano(p, p, 8, 2, d(1.0), d(2.0), p, p, None) == sk.EINVAL
+    assert L.sacrak_ffi_strain(None, 8, d(0.1), d(0.5), p, p, ctypes.c_size_t(1 << 20), None) == sk.EINVAL
+    assert L.sacrak_ffi_strain(p, 8, d(0.0), d(0.5), p, p, ctypes.c_size_t(1 << 20), None) == sk.EINVAL
+    assert L.sacrak_ffi_strain(p, 8, d(0.1), d(-1.0), p, p, ctypes.c_size_t(1 << 20), None) == sk.EINVAL
+    assert L.sacrak_ffi_work_bytes(0) == 0
