@@ -164,3 +164,28 @@ def test_errors():
     g.track_punctures(h.positions, FOLLOW)
     g.level_step(0)
     assert np.all(np.isfinite(g.punctures()))
+
+
+def test_half_domain_shift_parity():
+    """Equatorial symmetry with patch shifts: the GPU's half-domain grid
+    against the oracle's half-domain hierarchy doing the same shifts."""
+    h = idd.moving_binary_3_level()
+    states = idd.hierarchy_data(h, noise=0.0)
+    for u in states:
+        u[19] += 0.2
+        u[20] -= 0.1
+    hh = idd.upper_half_hierarchy(h)
+    half = [idd.upper_half_array(p, u) for p, u in zip(h.patches, states)]
+    g = sk.Grid(len(hh.levels), hh.dx0, hh.patches, sk.Params(courant=0.5, zsym=1), stream=torch.cuda.Stream())
+    for i, u in enumerate(half):
+        g.upload_fields(i, u)
+    bo = oracle.BOHierarchy(hh, half, oracle.Params(), courant=0.5, zsym=True)
+    for x in (g, bo):
+        x.level_step(0)
+        x.move_patch(1, (-1, 1, 0))
+        x.move_patch(4, (1, 0, 0))
+        x.level_step(0)
+    with pytest.raises(sk.SacrakError):
+        g.move_patch(3, (0, 0, 1))
+    for i in range(len(hh.patches)):
+        assert rel_err(g.download_fields(i), bo.current(i), active_only=True).max() <= 1e-10, i

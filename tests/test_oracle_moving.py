@@ -192,3 +192,31 @@ def test_move_restarts_histories():
     bo.level_step(0)
     bo.move_patch(1, (-1, 0, 0))  # level 0 (one patch) keeps its history
     assert [len(bo.tl[i]) for i in range(5)] == [3, 1, 1, 3, 3]
+
+
+def test_half_domain_shift_equals_full_domain():
+    """Equatorial symmetry (Sec. 2.2.2) through a patch shift: the half-domain
+    hierarchy that shifts a level-1 patch in x and y equals the upper half of
+    the full-domain hierarchy doing the same on z-symmetric data."""
+    h = idd.moving_binary_3_level()
+    states = idd.hierarchy_data(h, noise=0.0)  # punctures on z = 0: symmetric
+    for u in states:
+        u[19] += 0.2   # a shift along x and y keeps the z symmetry
+        u[20] -= 0.1
+    hh = idd.upper_half_hierarchy(h)
+    half = [idd.upper_half_array(p, u) for p, u in zip(h.patches, states)]
+    full = oracle.BOHierarchy(h, states, oracle.Params(), courant=0.5)
+    half_bo = oracle.BOHierarchy(hh, half, oracle.Params(), courant=0.5, zsym=True)
+    for bo in (full, half_bo):
+        bo.level_step(0)
+        bo.move_patch(1, (-1, 1, 0))
+        bo.move_patch(4, (1, 0, 0))
+        bo.level_step(0)
+    with pytest.raises(ValueError):  # no z shifts under the symmetry
+        half_bo.move_patch(3, (0, 0, 1))
+    g = 3
+    for i, p in enumerate(full.patches):
+        a = idd.upper_half_array(p, full.current(i))[:, g:-g, g:-g, g:-g]
+        b = half_bo.current(i)[:, g:-g, g:-g, g:-g]
+        scale = np.maximum(np.abs(a).max(axis=(1, 2, 3)), 1e-300)
+        assert (np.abs(a - b).max(axis=(1, 2, 3)) / scale).max() <= 1e-12, i
