@@ -338,7 +338,9 @@ sacrak_status sacrak_get_stage_kernel(sacrak_grid* grid, int level, int* kernel)
  * reads the current time level and writes only the RK accumulator and the
  * first stage buffer, so the state is unchanged) with every kernel usable on
  * that level, `reps` launches each after one warm-up launch (CUDA events on
- * the grid's stream), and selects the fastest.  Results are cached for the
+ * the grid's stream), and selects the fastest; the level's current kernel
+ * stays unless the fastest beats it by more than 2% (stage 1 stands in for
+ * all four stages).  Results are cached for the
  * process, keyed by device, precision and the level's patch shapes (levels
  * of identical shapes share one timing and one choice); with use_cache != 0
  * a cached level is not timed again.  us_per_launch, if not

@@ -145,8 +145,9 @@ def test_tma_level_step_hierarchy_vs_oracle(kernel):
 
 
 def test_autotune_choice_and_parity():
-    """The autotuner times every usable kernel per level, keeps the fastest,
-    leaves the state untouched, and the tuned coarse step agrees with the
+    """The autotuner times every usable kernel per level, keeps the fastest
+    (the current kernel unless another is more than 2% faster), leaves the
+    state untouched, and the tuned coarse step agrees with the
     direct kernel's to FP32 rounding."""
     h, states = _tma_hierarchy()
     a = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(precision=1), stream=torch.cuda.Stream())
@@ -158,7 +159,9 @@ def test_autotune_choice_and_parity():
     assert us.shape == (len(h.levels), len(sk.STAGE_KERNELS))
     for l in range(len(h.levels)):
         k = a.stage_kernel(l)
-        assert us[l, k] > 0 and us[l, k] == us[l][us[l] > 0].min()
+        m = us[l][us[l] > 0].min()
+        # the fastest, or the level's previous kernel (10) within 2% of it
+        assert us[l, k] > 0 and (us[l, k] == m or (k == 10 and m >= 0.98 * us[l, k])), (l, k, us[l])
         b.set_stage_kernel(l, 0)
     for i, u in enumerate(states):  # tuning did not touch the current level
         assert np.array_equal(a.download_fields(i), u)
