@@ -91,3 +91,11 @@ def test_diagnostics_and_moving_boxes_reject_before_device_work(L):
     assert L.sacrak_ffi_strain(p, 8, d(0.0), d(0.5), p, p, ctypes.c_size_t(1 << 20), None) == sk.EINVAL
     assert L.sacrak_ffi_strain(p, 8, d(0.1), d(-1.0), p, p, ctypes.c_size_t(1 << 20), None) == sk.EINVAL
     assert L.sacrak_ffi_work_bytes(0) == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without libsacrak.so the binding raises: there is no fallback path."""
+    monkeypatch.setattr(sk, "_lib", None)
+    monkeypatch.setattr(sk, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libsacrak.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        sk.lib()
