@@ -874,7 +874,7 @@ def stage_kernel_timing(g, steps):
         import paper_2607_08743_gb300 as sk
         kn = {0: "z4c_stage_mixed_kernel"}
         kn.update({k: "z4c_stage_tma_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (1, 2, 3, 4)})
-        kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6, 8, 9, 10, 11, 12, 13)})
+        kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6, 8, 9, 10, 11, 12, 13, 14)})
         kn[7] = "z4c_deriv_kernel + z4c_algebra_kernel"
         names = sorted({kn[k] for k in ids})
         name = " + ".join(names)

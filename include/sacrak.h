@@ -325,7 +325,8 @@ sacrak_status sacrak_constraints_noalloc(const double* dev_u, const int n[3], do
  * RK update's streaming reads; kernel 12 is kernel 10 with the inner
  * differences of D_x D_y f and D_x D_z f at the x neighbours taken from the
  * neighbouring lanes of the warp by shuffles (loads where a tile does not
- * fill its 32 x), kernel 13 is kernel 12 with 4 CTAs per SM.  All kernels
+ * fill its 32 x), kernel 13 is kernel 12 with 4 CTAs per SM, kernel 14 is
+ * kernel 10 with 4 CTAs per SM (128 registers).  All kernels
  * compute the same RHS up to FP32 rounding order.  A TMA kernel needs at most 8 patches on the level and at
  * least 32 x TY x TZ active cells per patch, else SACRAK_EINVAL.  New grids
  * use kernel 10 in mixed precision and 0 in FP64.  Changing the kernel of a
@@ -344,7 +345,7 @@ sacrak_status sacrak_get_stage_kernel(sacrak_grid* grid, int level, int* kernel)
  * process, keyed by device, precision and the level's patch shapes (levels
  * of identical shapes share one timing and one choice); with use_cache != 0
  * a cached level is not timed again.  us_per_launch, if not
- * NULL, receives nlevels x 14 timings in microseconds (kernel 0..13 of each
+ * NULL, receives nlevels x 15 timings in microseconds (kernel 0..14 of each
  * level; -1 where not timed).  Synchronises the stream; must not be called
  * while the stream is being captured (SACRAK_ESTATE). */
 sacrak_status sacrak_autotune(sacrak_grid* grid, int reps, int use_cache, double* us_per_launch);

@@ -39,12 +39,14 @@ EXPORTS = [
 # 7 split into a derivative and an algebra launch, 8 as 6 with 4 CTAs per SM,
 # 9 as 6 prefetching the star rows only, 10 only the z-arm rows, 11 only the
 # RK update's streaming reads, 12 as 10 with the x-neighbour inner differences
-# of the mixed derivatives exchanged by warp shuffles, 13 as 12 with 4 CTAs per SM
+# of the mixed derivatives exchanged by warp shuffles, 13 as 12 with 4 CTAs per SM,
+# 14 as 10 with 4 CTAs per SM
 STAGE_KERNELS = {0: "direct", 1: "tma 32x4x1", 2: "tma 32x2x2", 3: "tma 32x4x2", 4: "tma 32x8x1",
                  5: "l1 pairs", 6: "l1 pairs + prefetch", 7: "split deriv + algebra",
                  8: "l1 pairs + prefetch, 4/SM", 9: "l1 pairs + star prefetch",
                  10: "l1 pairs + z-arm prefetch", 11: "l1 pairs + epilogue prefetch",
-                 12: "l1 pairs + z-arm prefetch + x shuffles", 13: "l1 pairs + z-arm prefetch + x shuffles, 4/SM"}
+                 12: "l1 pairs + z-arm prefetch + x shuffles", 13: "l1 pairs + z-arm prefetch + x shuffles, 4/SM",
+                 14: "l1 pairs + z-arm prefetch, 4/SM"}
 
 
 class SacrakError(RuntimeError):
@@ -400,7 +402,7 @@ class Grid:
 
     def autotune(self, reps: int = 3, use_cache: bool = True) -> np.ndarray:
         """Time every usable stage kernel on every level and keep the fastest;
-        returns the timings (nlevels x 14, microseconds per launch, -1 = not
+        returns the timings (nlevels x 15, microseconds per launch, -1 = not
         timed) and leaves the choice in place."""
         out = np.full((self.nlevels, len(STAGE_KERNELS)), -1.0)
         self._check(lib().sacrak_autotune(self._h, reps, int(use_cache),

@@ -40,7 +40,7 @@ void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st);
 // with only the star rows prefetched; 4 only the z-arm rows; 5 only the
 // epilogue's reads; 6 as 4 with the x-neighbour inner differences of the
 // mixed derivatives D_x D_y, D_x D_z exchanged by warp shuffles; 7 as 6 with
-// 4 CTAs per SM.  ldg_setup opts the kernels in to their shared memory
+// 4 CTAs per SM; 8 as 4 with 4 CTAs per SM.  ldg_setup opts the kernels in to their shared memory
 // (false on failure).
 int ldg_setup(int v);
 void launch_stage_ldg(int v, const StageArgs& a, cudaStream_t st);

@@ -948,7 +948,8 @@ void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st) {
 // variant v: 0 (3 CTAs/SM, no prefetch), 1 (3, prefetch), 2 (4, prefetch),
 // 3 (3, prefetch of the star rows only), 4 (3, z-arm rows only), 5 (3, the
 // epilogue's reads only), 6 (as 4, the x-neighbour inner differences of the
-// mixed derivatives exchanged by warp shuffles), 7 (as 6 with 4 CTAs/SM)
+// mixed derivatives exchanged by warp shuffles), 7 (as 6 with 4 CTAs/SM),
+// 8 (as 4 with 4 CTAs/SM, 128 registers)
 int ldg_setup(int v) {
   switch (v) {
     case 0: return setup_ldg<3, 0>();
@@ -959,6 +960,7 @@ int ldg_setup(int v) {
     case 5: return setup_ldg<3, 4>();
     case 6: return setup_ldg<3, 3, true>();
     case 7: return setup_ldg<4, 3, true>();
+    case 8: return setup_ldg<4, 3>();
   }
   return 0;
 }
@@ -974,6 +976,7 @@ void launch_stage_ldg(int v, const StageArgs& a, cudaStream_t st) {
     case 5: launch_ldg<3, 4>(a, st); break;
     case 6: launch_ldg<3, 3, true>(a, st); break;
     case 7: launch_ldg<4, 3, true>(a, st); break;
+    case 8: launch_ldg<4, 3>(a, st); break;
   }
 }
 

@@ -24,7 +24,7 @@ from tests.gpu_common import grid_for, rel_err
 skbuild.build()
 
 TMA = [1, 2, 3, 4]
-PAIRS = [5, 6, 7, 8, 9, 10, 11, 12, 13]  # L1 path and split launches, same arithmetic
+PAIRS = [5, 6, 7, 8, 9, 10, 11, 12, 13, 14]  # L1 path and split launches, same arithmetic
 TOL = 1e-4          # mixed precision vs the FP64 oracle
 TOL_KERNELS = 2e-5  # TMA kernel vs direct mixed kernel, same data
 
