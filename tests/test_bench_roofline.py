@@ -29,3 +29,25 @@ def test_fraction_is_achieved_over_peak():
     r = bench.roofline(_run("mixed", [10]), 6657.6)
     assert abs(r["achieved"] - 884736.0 * 900 / 0.5e-3 / 1e9) < 1e-6
     assert abs(r["frac"] - r["achieved"] / 6657.6) < 1e-12
+
+
+def test_launches_per_coarse_step_by_recursion():
+    """The launch count the bench reports for one coarse step, counted by
+    walking the Berger-Oliger recursion: per level step 4 stage kernels, the
+    ghost work (4 Sommerfeld updates on level 0; on finer levels fills for
+    stage 1, stages 2-3 together and stage 4), the level bookkeeping and,
+    with children, the prolongation of the new slot; per child level step
+    pair the fill at the new time, the restriction and the prolongation of
+    the restricted slot.  1269 launches for the 7-level binary (the ncu
+    launch list of the step has exactly these)."""
+    import initial_data as idd
+    h = idd.binary_7_level()
+    nlev = len(h.levels)
+
+    def level_step(l):
+        n = 4 + (4 if l == 0 else 3) + 1
+        if l + 1 < nlev:
+            n += 1 + level_step(l + 1) + level_step(l + 1) + 3
+        return n
+
+    assert level_step(0) == bench.launches_per_coarse_step(h) == 1269
