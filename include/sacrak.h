@@ -7,8 +7,12 @@
  * (Sec. 2.2), on static box-in-box Berger-Oliger patches with subcycling,
  * 6th-order Lagrange prolongation, time interpolation between parent time
  * levels and 4th-order Lagrange restriction (Sec. 2.2.1), with the Sommerfeld
- * outgoing-wave condition on the coarsest level (Sec. 2.2.2) and the
- * Hamiltonian/momentum constraint monitor (Sec. 2.3).
+ * outgoing-wave condition on the coarsest level and optional equatorial
+ * reflection symmetry (Sec. 2.2.2), puncture tracking with moving patches
+ * (Sec. 2.2.1), and the diagnostics of Sec. 2.3 and 3.2: constraint norms,
+ * pi symmetry, ADM mass / angular / linear momentum, Psi4 modes and the
+ * waveform post-processing (Nakano extrapolation, fixed frequency
+ * integration).
  *
  * Conventions shared by every call
  *  - Field order: 0 W; 1-6 gt_xx,xy,xz,yy,yz,zz; 7 Khat; 8 Theta;
@@ -22,10 +26,12 @@
  *    device memory; the library asks CUDA which it is.
  *  - Ownership: the caller owns every buffer it passes, including the device
  *    arena given to sacrak_grid_create, which the library never frees and
- *    never reallocates.  The library allocates no device memory on any call.
+ *    never reallocates.  The library allocates no device memory on any call
+ *    (except the tables cuFFT keeps for the duration of sacrak_ffi_strain).
  *  - Ordering: all device work is issued on the grid's CUDA stream, in call
  *    order.  Calls that return values computed on the device (constraints,
- *    pi symmetry, downloads to host memory) synchronise that stream.
+ *    pi symmetry, surface integrals, puncture positions, downloads to host
+ *    memory) and the regrid calls synchronise that stream.
  *  - Errors: no call aborts or throws across the ABI.  Invalid arguments
  *    return SACRAK_EINVAL before any device work is issued; a CUDA error
  *    returns SACRAK_ECUDA; a non-finite value detected by a stage returns
