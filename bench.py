@@ -778,7 +778,8 @@ def uniform_case(torch, sk, args):
     g.set_initial_data(1, h.masses, h.positions)
     tune = None
     if prm.precision == 1:
-        tune = [round(float(x), 1) for x in g.autotune(reps=3, use_cache=False)[0]]
+        if not args.no_autotune:
+            tune = [round(float(x), 1) for x in g.autotune(reps=3, use_cache=False)[0]]
         if args.kernel is not None:
             g.set_stage_kernel(0, args.kernel)
     for _ in range(args.warmup):

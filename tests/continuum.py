@@ -265,3 +265,39 @@ def on_points(fn, pts):
     for s in range(0, P.shape[0], 2048):
         out.append(vmap(fn)(P[s:s + 2048]).detach().numpy())
     return np.concatenate(out, axis=0)
+
+
+# ------------------------------------------------------------- Theta and Z data
+
+def theta(x):
+    """A smooth, generic Theta(x) (O(0.05)) for the damping-term pins."""
+    X, Y, Z = x[0], x[1], x[2]
+    return 0.05 * torch.sin(PI * X + 0.4) * torch.cos(0.5 * PI * Z - 0.2) + 0.03 * torch.cos(PI * Y + 0.1)
+
+
+def gam_offset(x):
+    """A smooth vector added to the evolved Gamt^i, so that Gamt^i - Gamd^i
+    (twice the conformal Z4 vector, gt^ij Z_j) is non-zero."""
+    X, Y, Z = x[0], x[1], x[2]
+    return torch.stack([0.04 * torch.cos(PI * Y - 0.3), -0.03 * torch.sin(PI * (X + Z) + 0.2),
+                        0.05 * torch.cos(PI * X) * torch.sin(0.5 * PI * Y + 0.7)])
+
+
+_PATCH_CACHE = {}
+
+
+def patch_state(n):
+    """The n^3 patch on [-1/2, 1/2]^3 (ghosts included) with the generic data
+    of z4c_state at every cell centre, as a (25, n+6, n+6, n+6) array; cached
+    per n for the test session."""
+    import numpy as np
+
+    import initial_data as idd
+
+    if n not in _PATCH_CACHE:
+        p = idd.Patch(n=(n, n, n), dx=1.0 / n, origin=(-0.5, -0.5, -0.5))
+        z, y, xx = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
+        pts = np.stack([xx.ravel(), y.ravel(), z.ravel()], axis=1)
+        u = np.ascontiguousarray(on_points(z4c_state, pts).T.reshape(p.shape))
+        _PATCH_CACHE[n] = (p, pts, u)
+    return _PATCH_CACHE[n]
