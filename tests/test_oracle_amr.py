@@ -202,3 +202,51 @@ def test_bo_driver_gauge_wave():
     assert math.log2(max(e16) / max(e32)) > 1.5, (e16, e32)
     e_lin, _ = _gw_amr_errors(16, 2, history=False)
     assert max(e_lin) < 5e-4, e_lin
+
+
+# ------------------------------------------------------------------ two patches on a level
+
+def _split_merged(split):
+    """3 levels: L0 32^3 (dx 1), L1 one 32x16x16 patch on [-8,8]x[-4,4]^2 or the
+    same region as two abutting 16^3 patches (split at x = 0), L2 8^3 (dx 1/4)
+    inside the right half."""
+    l0 = [idd.Patch(n=(32, 32, 32), dx=1.0, origin=(-16.0, -16.0, -16.0), level=0)]
+    if split:
+        l1 = [idd.Patch(n=(16, 16, 16), dx=0.5, origin=(-8.0, -4.0, -4.0), level=1),
+              idd.Patch(n=(16, 16, 16), dx=0.5, origin=(0.0, -4.0, -4.0), level=1)]
+    else:
+        l1 = [idd.Patch(n=(32, 16, 16), dx=0.5, origin=(-8.0, -4.0, -4.0), level=1)]
+    l2 = [idd.Patch(n=(8, 8, 8), dx=0.25, origin=(3.0, -1.0, -1.0), level=2)]
+    h = idd.Hierarchy(dx0=1.0, levels=[l0, l1, l2], masses=[0.3], positions=[(4.05, 0.1, -0.15)])
+    return h, idd.hierarchy_data(h, noise=1e-6, seed=7)
+
+
+def test_bo_split_level_equals_merged_level():
+    """A level made of two abutting patches evolves exactly like the single
+    patch covering the same cells (Sec. 2.2.1): at every stage each patch's
+    ghosts over the neighbour's active cells take the neighbour's values
+    (exchange after the prolongation), and after the two child steps the
+    ghosts are refilled at the parent's new time, exchanged and only then
+    restricted.  Any other order leaves prolonged values where the merged
+    patch has evolved ones, and the two runs part at O(1e-6) (the noise)."""
+    hs, us = _split_merged(True)
+    hm, um = _split_merged(False)
+    prm = oracle.Params()
+    bs = oracle.BOHierarchy(hs, us, prm, courant=0.25)
+    bm = oracle.BOHierarchy(hm, um, prm, courant=0.25)
+    for _ in range(2):
+        bs.level_step(0)
+        bm.level_step(0)
+    g = 3
+    act = (slice(None), slice(g, -g), slice(g, -g), slice(g, -g))
+    scale = np.abs(bm.current(0)[act]).max()
+    for a, b in ((0, 0), (3, 2)):  # L0 and L2 patches
+        d = np.abs(bs.current(a)[act] - bm.current(b)[act]).max()
+        assert d <= 1e-14 * scale, (a, d)
+    merged = bm.current(1)
+    for pid, x0 in ((1, 0), (2, 16)):  # the halves inside the merged patch
+        part = merged[:, g:-g, g:-g, g + x0:g + x0 + 16]
+        d = np.abs(bs.current(pid)[act] - part).max()
+        assert d <= 1e-14 * scale, (pid, d)
+    # the runs did evolve the noise (the pin is not vacuous)
+    assert np.abs(bm.current(1)[act] - um[1][act]).max() > 1e-4
