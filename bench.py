@@ -279,8 +279,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2: %.2f GB per state copy" % (
                            sum(25 * 8 * (p.n[0] + 6) * (p.n[1] + 6) * (p.n[2] + 6) for p in h.patches) / 1e9),
-                       "hbm_roofline_zone_updates_per_s": hbm * 1e9 / head["bytes_per_zone_update"],
-                       "hbm_frac_of_measured": head["value"] / world / (hbm * 1e9 / head["bytes_per_zone_update"])},
+                       "hbm_roofline_zone_updates_per_s": hbm * 1e9 / BYTES_PER_ZONE_UPDATE,
+                       "step_hbm_frac_of_measured": head["value"] / world / (hbm * 1e9 / BYTES_PER_ZONE_UPDATE)},
             "roofline": roofline(head, hbm),
             "gpu_launches": launches_per_coarse_step(h) * args.steps * len(precisions),
             "clocks": clk.summary(),
@@ -304,27 +304,37 @@ def main():
         dist.destroy_process_group()
 
 
-# per-zone DRAM traffic of one stage-kernel launch from the ncu captures of the
-# 96^3 case (profiles/), by (precision, stage kernel id): FP64 1.98 GB; mixed
-# stage kernel 10 0.8531 GB, kernel 11 0.8518 GB, kernel 13 0.9256 GB per
-# 884,736 zones.  A kernel without a capture reports no traffic; levels on
-# different captured kernels report the largest.
-NCU_TRAFFIC_PER_ZONE = {(0, 0): 1.98e9 / 884736, (1, 10): 0.8531e9 / 884736, (1, 11): 0.8518e9 / 884736,
-                        (1, 13): 0.9256e9 / 884736}
+# per-zone DRAM traffic of the stage kernel (ncu dram__bytes_read + write of
+# the four RK4 stage launches of one step on the 96^3 patch, averaged over
+# the stages, divided by its 884,736 zones), by (precision, stage kernel id);
+# the captures are in profiles/.  A kernel without a capture reports no
+# traffic; levels on different captured kernels report the largest.
+NCU_TRAFFIC_PER_ZONE = {(0, 0): 1961.2, (1, 10): 1064.6}
+# the metric's roofline: the algorithmic bytes of one RK4 step (16 FP64
+# field passes of 25 fields) per zone update, the same in both precisions
+# (the hi/lo split copies of mixed precision are an implementation choice)
+ALG_BYTES_PER_ZONE_STAGE = BYTES_PER_ZONE_UPDATE / 4.0
 
 
 def roofline(r, hbm):
+    """The dominant kernel (the fused RHS + RK4 stage) against the HBM
+    roofline of the algorithmic bytes; FP64 adds its FP64-pipe use, the
+    resource that limits it."""
     k = r["kern"]
+    alg = k["zones_per_launch"] * ALG_BYTES_PER_ZONE_STAGE
+    ach = alg / (k["ms"] * 1e-3) / 1e9
+    out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+           "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)",
+           "algorithmic_bytes_per_zone_stage": ALG_BYTES_PER_ZONE_STAGE}
     if r["precision"] == "fp64":
-        ach = k["flops_per_launch"] / (k["ms"] * 1e-3) / 1e12 if k["flops_per_launch"] else None
-        out = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "frac": ach / FP64_PEAK_TFLOPS if ach else None,
-               "peak_note": "FP64 pipe, nominal 1.25 TFLOP/s (the recipe's unit rate); a DFMA probe "
-                            "measured 1.0 TFLOP/s on this GPU"}
+        fl = k["flops_per_launch"] / (k["ms"] * 1e-3) / 1e12 if k["flops_per_launch"] else None
+        out["limited_by"] = "FP64 pipe"
+        out["alu"] = {"achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                      "frac": fl / FP64_PEAK_TFLOPS if fl else None,
+                      "peak_note": "FP64 pipe, nominal 1.25 TFLOP/s (the recipe's unit rate); flops are the "
+                                   "kernel's executed FP64 operations (ncu, DFMA = 2)"}
     else:
-        ach = k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9
-        out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-               "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+        out["implementation_bytes_per_zone_stage"] = BYTES_PER_ZONE_UPDATE_MIXED / 4.0
     out["stage_kernels"] = k.get("stage_kernels")
     if k.get("autotune"):
         out["autotune"] = k["autotune"]
@@ -335,10 +345,11 @@ def roofline(r, hbm):
     if per_zone and None not in per_zone:  # every level on a captured kernel
         traffic = max(per_zone) * k["zones_per_launch"]
     out.update({"traffic": traffic,
+                "traffic_note": "ncu DRAM bytes averaged over the four RK4 stage launches of the 96^3 patch, "
+                                "per zone, times the zones of the average launch",
                 "kernel": k["name"], "launch_ms": k["ms"], "launches_per_step": k["launches"] / k["steps"],
                 "share_of_step": k["ms"] * k["launches"] / k["steps"] / r["ms"],
-                "algorithmic_bytes_per_launch": k["bytes_per_launch"],
-                "hbm_frac_of_measured": k["bytes_per_launch"] / (k["ms"] * 1e-3) / 1e9 / hbm})
+                "algorithmic_bytes_per_launch": alg})
     return out
 
 
@@ -378,8 +389,7 @@ def measure(torch, sk, h, precision, args, world, dist):
     if tune:
         kern["autotune"] = tune
     out = {"precision": precision, "value": whole_job_value(zu, world, ms), "ms": ms, "kern": kern,
-           "constraints_l0": norms,
-           "bytes_per_zone_update": BYTES_PER_ZONE_UPDATE_MIXED if precision == "mixed" else BYTES_PER_ZONE_UPDATE}
+           "constraints_l0": norms}
     if not args.no_e2e:
         out["e2e"] = end_to_end(torch, sk, h, prm, args, world, dist)
     return out
@@ -711,7 +721,7 @@ def sweep_case(torch, sk, args):
                 row["kernel"] = sk.STAGE_KERNELS[g.stage_kernel(0)]
             ms = _time_rk4(torch, g, 0, 5 if prec else 2)
             zu = p.active_points / (ms * 1e-3)
-            bpz = BYTES_PER_ZONE_UPDATE_MIXED if prec else BYTES_PER_ZONE_UPDATE
+            bpz = BYTES_PER_ZONE_UPDATE
             row[key] = {"ms_per_rk4_step": ms, "zone_updates_per_s": zu, "hbm_frac": zu * bpz / (hbm * 1e9)}
             g.close()
             del g
@@ -736,7 +746,7 @@ def sweep_case(torch, sk, args):
             act = sum(p.active_points for p in lv)
             ms = _time_rk4(torch, g, l, 2)
             zu = act / (ms * 1e-3)
-            bpz = BYTES_PER_ZONE_UPDATE_MIXED if prec else BYTES_PER_ZONE_UPDATE
+            bpz = BYTES_PER_ZONE_UPDATE
             res["per_level"].append({"level": l, "patches": [list(p.n) for p in lv],
                                      "kernel": sk.STAGE_KERNELS[g.stage_kernel(l)],
                                      "ms_per_rk4_step": ms, "zone_updates_per_s": zu,
@@ -756,7 +766,7 @@ def sweep_case(torch, sk, args):
             ms = e0.elapsed_time(e1)
             zu = h.zone_updates_per_coarse_step()
             res["coarse_step"] = {"ms": ms, "zone_updates": zu, "zone_updates_per_s": zu / (ms * 1e-3),
-                                  "hbm_frac": zu / (ms * 1e-3) * BYTES_PER_ZONE_UPDATE_MIXED / (hbm * 1e9),
+                                  "hbm_frac": zu / (ms * 1e-3) * BYTES_PER_ZONE_UPDATE / (hbm * 1e9),
                                   "constraints_l0": list(map(float, g.constraints(0)))}
         out["levels"].append(res)
         print(json.dumps(res), flush=True)
@@ -881,8 +891,7 @@ def stage_kernel_timing(g, steps):
         name = " + ".join(names)
     return {"name": name, "kernel_ids": ids,
             "ms": per, "launches": n, "share_of_step": None,
-            "bytes_per_launch": zones_per_launch * (BYTES_PER_ZONE_UPDATE_MIXED if g.params.precision == 1
-                                                    else BYTES_PER_ZONE_UPDATE) / 4.0,
+            "bytes_per_launch": zones_per_launch * ALG_BYTES_PER_ZONE_STAGE,
             "flops_per_launch": zones_per_launch * fz if fz else None,
             "traffic": None, "zones_per_launch": zones_per_launch}
 

@@ -98,7 +98,9 @@ typedef struct {
   double origin[3];
 } sacrak_patch_desc;
 
-/* Bytes of device memory a grid of this shape needs: per patch 6 FP64 state
+/* Bytes of device memory a grid of this shape needs.  Sec. 2.4 keeps every
+ * evolved field in device memory for the whole evolution; this is that
+ * resident state, held in one caller-owned arena: per patch 6 FP64 state
  * copies (3 time levels, the RK accumulator, 2 stage buffers), 3 more on
  * levels > 0 (the parent's time levels prolonged onto the ghost shell), and
  * with params->precision == 1 five copies of FP32 hi/lo pairs (the split of
@@ -109,7 +111,9 @@ typedef struct {
 size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* patches,
                           const sacrak_params* params);
 
-/* Create a grid on the current CUDA device.  device_arena must point to at
+/* Create a grid on the current CUDA device: the box-in-box refinement levels
+ * of Sec. 2.2.1 (factor-2 spacing per level, dx_level = dx0 / 2^level) over
+ * the caller's arena.  device_arena must point to at
  * least sacrak_arena_bytes(...) bytes of device memory, 256-byte aligned.
  * cuda_stream is a cudaStream_t (NULL = legacy default stream). Fields start
  * as Minkowski.  With the Sommerfeld boundary (bc = 0) every level-0 patch must
@@ -136,17 +140,31 @@ sacrak_status sacrak_set_initial_data(sacrak_grid* grid, int kind, int npunct, c
                                       double noise_amp, uint64_t seed, int symmetrise_pi);
 
 /* Copy a whole patch array (ghosts included) into / out of the current time
- * level.  Upload resets the time levels like sacrak_set_initial_data. */
+ * level: the transfers of Sec. 2.4 (initial data copied to the device at the
+ * start; fields copied back only for diagnostics and snapshots).  Host
+ * memory goes through one contiguous copy and a repacking kernel; device
+ * memory through a device copy.  Upload resets the time levels like
+ * sacrak_set_initial_data.  SACRAK_EINVAL for a bad patch or a null pointer. */
 sacrak_status sacrak_upload_fields(sacrak_grid* grid, int patch, const double* host_or_dev);
 sacrak_status sacrak_download_fields(sacrak_grid* grid, int patch, double* host_or_dev);
 
 /* Z4c right-hand side (sources + upwind advection + Kreiss-Oliger) of the
- * current state of one patch at its active points, ghosts used as they are.
- * Output is a patch array whose ghost entries are 0. */
+ * current state of one patch at its active points, ghosts used as they are:
+ * the Z4c equations with the 1+log / harmonic slicing and the Gamma-driver
+ * shift of Sec. 2.1.1, discretised as Sec. 2.2 states (4th-order centred
+ * derivatives, 4th-order lopsided upwind advection following the sign of the
+ * shift, 6th-order Kreiss-Oliger dissipation with sigma_ko), evaluated by
+ * the level's stage kernel (FP64, or with precision = 1 in FP32 on
+ * centre-referenced hi/lo differences).  Output is a patch array whose ghost entries are
+ * 0; the call returns when it is written.  SACRAK_EINVAL for a bad patch or
+ * a null pointer. */
 sacrak_status sacrak_rhs(sacrak_grid* grid, int patch, double* host_or_dev_rhs);
 
-/* One classical RK4 step of every patch of one level with dt (dt <= 0: use
- * courant * dx_level).  Level 0's ghosts follow params.bc; ghosts of finer
+/* One classical RK4 step (Sec. 2.2: method of lines, classical fourth-order
+ * Runge-Kutta, dt = Courant factor x spacing) of every patch of one level
+ * with dt (dt <= 0: use courant * dx_level), each stage fused with the
+ * right-hand side and the algebraic constraints (det gt = 1, trace-free At,
+ * W floor).  Level 0's ghosts follow params.bc; ghosts of finer
  * levels are prolonged from the parent at every stage time.  Does not recurse
  * into finer levels and does not restrict. */
 sacrak_status sacrak_rk4_step(sacrak_grid* grid, int level, double dt);
@@ -309,7 +327,11 @@ sacrak_status sacrak_profile_read(sacrak_grid* grid, double* stage_ms, long long
  * overlap on the GPU share the array and race; serialise them (one stream,
  * or one call at a time).  Runs on cuda_stream (a cudaStream_t, NULL = legacy
  * default) and synchronises it to return out_l2 (host memory).  Sizes beyond
- * the limits and non-device dev_u return SACRAK_EINVAL. */
+ * the limits return SACRAK_EINVAL, and so does a dev_u that is not device
+ * memory of the current device or whose allocation (as the driver reports
+ * it) does not hold the whole patch array; all before any launch.  The
+ * cached address of the array is dropped when a call finds the device's
+ * context destroyed (after a device reset), and looked up again. */
 sacrak_status sacrak_constraints_noalloc(const double* dev_u, const int n[3], double dx,
                                          double w_excise, void* cuda_stream, double out_l2[4]);
 
@@ -355,6 +377,16 @@ sacrak_status sacrak_get_stage_kernel(sacrak_grid* grid, int level, int* kernel)
  * level; -1 where not timed).  Synchronises the stream; must not be called
  * while the stream is being captured (SACRAK_ESTATE). */
 sacrak_status sacrak_autotune(sacrak_grid* grid, int reps, int use_cache, double* us_per_launch);
+
+/* Bound of the TMA stage kernels' (kernels 1..4) wait for each field's copy,
+ * in SM clock cycles: 0 restores the default (4e9, about 2 s); cycles < 0
+ * makes every such wait count as run out at once, a test hook for the
+ * time-out path (no paper counterpart).  A wait that runs out sets the
+ * device error flag (SACRAK_ETIMEOUT at the next synchronising call, the
+ * grid then invalid until new data); the CTA issues no further copy, waits
+ * with the default bound for the copies it has in flight, and returns
+ * without writing results.  Drops the recorded coarse-step graph. */
+sacrak_status sacrak_set_wait_limit(sacrak_grid* grid, long long cycles);
 
 /* Current time of a level. */
 sacrak_status sacrak_level_time(sacrak_grid* grid, int level, double* t);

@@ -32,6 +32,7 @@ EXPORTS = [
     "sacrak_set_stage_kernel", "sacrak_get_stage_kernel", "sacrak_autotune", "sacrak_adm_integrals",
     "sacrak_track_punctures", "sacrak_get_punctures", "sacrak_move_patch", "sacrak_regrid",
     "sacrak_patch_origin", "sacrak_psi4_modes", "sacrak_nakano", "sacrak_ffi_work_bytes", "sacrak_ffi_strain",
+    "sacrak_set_wait_limit",
 ]
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
@@ -40,13 +41,17 @@ EXPORTS = [
 # 9 as 6 prefetching the star rows only, 10 only the z-arm rows, 11 only the
 # RK update's streaming reads, 12 as 10 with the x-neighbour inner differences
 # of the mixed derivatives exchanged by warp shuffles, 13 as 12 with 4 CTAs per SM,
-# 14 as 10 with 4 CTAs per SM
+# 14 as 10 with 4 CTAs per SM, 15 two x-adjacent points per thread with 128-bit
+# loads of the hi/lo pairs, 16 as 15 prefetching the next field's z-arm rows,
+# 17 as 16 with 3 CTAs per SM (more of the SM's memory left to L1)
 STAGE_KERNELS = {0: "direct", 1: "tma 32x4x1", 2: "tma 32x2x2", 3: "tma 32x4x2", 4: "tma 32x8x1",
                  5: "l1 pairs", 6: "l1 pairs + prefetch", 7: "split deriv + algebra",
                  8: "l1 pairs + prefetch, 4/SM", 9: "l1 pairs + star prefetch",
                  10: "l1 pairs + z-arm prefetch", 11: "l1 pairs + epilogue prefetch",
                  12: "l1 pairs + z-arm prefetch + x shuffles", 13: "l1 pairs + z-arm prefetch + x shuffles, 4/SM",
-                 14: "l1 pairs + z-arm prefetch, 4/SM"}
+                 14: "l1 pairs + z-arm prefetch, 4/SM", 15: "two points/thread, 128-bit loads",
+                 16: "two points/thread, 128-bit loads + z-arm prefetch",
+                 17: "two points/thread, 128-bit loads + z-arm prefetch, 3/SM"}
 
 
 class SacrakError(RuntimeError):
@@ -103,6 +108,7 @@ def lib() -> ctypes.CDLL:
             L.sacrak_constraints_noalloc.argtypes = [vp, P(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                                      vp, dp]
             L.sacrak_set_stage_kernel.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            L.sacrak_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
             L.sacrak_get_stage_kernel.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
             L.sacrak_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
             L.sacrak_last_error.argtypes = [vp]
@@ -157,9 +163,12 @@ def arena_bytes(nlevels: int, patches, params: Optional["Params"] = None) -> int
 def _ptr(a) -> int:
     """Address of a numpy array or torch tensor (host or device)."""
     if isinstance(a, np.ndarray):
-        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise SacrakError(EINVAL, "expected a C-contiguous float64 array")
         return a.ctypes.data
-    assert a.dtype.itemsize == 8 and a.is_contiguous()
+    import torch
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise SacrakError(EINVAL, "expected a contiguous float64 tensor")
     return a.data_ptr()
 
 
@@ -207,11 +216,23 @@ def constraints_noalloc(dev_u, n, dx: float, w_excise: float = 0.0, stream=None)
     """Constraint norms of one patch array held in caller-owned device memory
     (a CUDA tensor in the unpadded patch-array layout), without a grid and
     without any device allocation (sacrak_constraints_noalloc)."""
-    nn = (ctypes.c_int * 3)(*[int(v) for v in n])
+    import torch
+    nn = [int(v) for v in n]
+    if len(nn) != 3:
+        raise SacrakError(EINVAL, "n must hold 3 sizes")
+    if not isinstance(dev_u, torch.Tensor) or not dev_u.is_cuda:
+        raise SacrakError(EINVAL, "dev_u must be a CUDA tensor")
+    if dev_u.dtype != torch.float64 or not dev_u.is_contiguous():
+        raise SacrakError(EINVAL, "dev_u must be a contiguous float64 tensor")
+    if dev_u.device.index != torch.cuda.current_device():
+        raise SacrakError(EINVAL, "dev_u is not on the current CUDA device")
+    need = NF * (nn[0] + 6) * (nn[1] + 6) * (nn[2] + 6)
+    if min(nn) < 1 or dev_u.numel() < need:
+        raise SacrakError(EINVAL, "dev_u holds %d values, the patch array needs %d" % (dev_u.numel(), need))
     out = np.empty(4)
     sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
-    st = lib().sacrak_constraints_noalloc(ctypes.c_void_p(_ptr(dev_u)), nn, dx, w_excise, sp,
-                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    st = lib().sacrak_constraints_noalloc(ctypes.c_void_p(dev_u.data_ptr()), (ctypes.c_int * 3)(*nn), dx,
+                                          w_excise, sp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if st != OK:
         raise SacrakError(st, "sacrak_constraints_noalloc failed")
     return out
@@ -395,6 +416,11 @@ class Grid:
         """Stage kernel of a level (see STAGE_KERNELS)."""
         self._check(lib().sacrak_set_stage_kernel(self._h, level, kernel), "set_stage_kernel")
 
+    def set_wait_limit(self, cycles: int):
+        """Bound (SM cycles) of the TMA stage kernels' copy waits; 0 = default,
+        < 0 = run out at once (tests of the time-out path)."""
+        self._check(lib().sacrak_set_wait_limit(self._h, int(cycles)), "set_wait_limit")
+
     def stage_kernel(self, level: int) -> int:
         v = ctypes.c_int()
         self._check(lib().sacrak_get_stage_kernel(self._h, level, ctypes.byref(v)), "get_stage_kernel")
@@ -402,7 +428,7 @@ class Grid:
 
     def autotune(self, reps: int = 3, use_cache: bool = True) -> np.ndarray:
         """Time every usable stage kernel on every level and keep the fastest;
-        returns the timings (nlevels x 15, microseconds per launch, -1 = not
+        returns the timings (nlevels x len(STAGE_KERNELS), microseconds per launch, -1 = not
         timed) and leaves the choice in place."""
         out = np.full((self.nlevels, len(STAGE_KERNELS)), -1.0)
         self._check(lib().sacrak_autotune(self._h, reps, int(use_cache),

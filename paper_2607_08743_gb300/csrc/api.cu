@@ -100,7 +100,10 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed,
   L.px.resize(npatches);
   for (int p = 0; p < npatches; ++p) {
     int NX = pd[p].n[0] + 2 * GH, NY = pd[p].n[1] + 2 * GH, NZ = pd[p].n[2] + 2 * GH;
-    int px = (int)align_up(NX, 8);
+    // row pitch: at least one spare element per row, rounded to 8 (the
+    // buffers start one element past their 256-byte boundary, so that cells
+    // 2m, 2m+1 of a row share a 16-byte line; see the patch table below)
+    int px = (int)align_up(NX + 1, 8);
     long long fs = (long long)px * NY * NZ;
     L.px[p] = px;
     L.fstride[p] = fs;
@@ -109,7 +112,9 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed,
     off = align_up(off + (size_t)nbuf * NF * fs * sizeof(double), 256);
     if (mixed) off = align_up(off + (size_t)5 * NF * fs * sizeof(float2), 256);  // hl[3] sa sb
   }
-  L.total = off;
+  // whole-buffer copies and fills from the shifted bases reach one element
+  // past the last buffer
+  L.total = off + 256;
   return true;
 }
 
@@ -151,6 +156,7 @@ struct sacrak_grid {
   std::string last_error;
   // profiling of the fused stage kernel
   bool prof = false;
+  long long tma_wait_cycles = 0;  // 0: TMA_WAIT_CYCLES (sacrak_set_wait_limit)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   size_t ev_used = 0;
   long long prof_zones = 0;
@@ -266,7 +272,11 @@ bool tma_eligible(const sacrak_grid* g, int v, const std::vector<int>& pids) {
 constexpr int K_LDG3 = TMA_NVARIANTS + 1, K_LDG4 = TMA_NVARIANTS + 2, K_SPLIT = TMA_NVARIANTS + 3,
               K_LDG_PF4 = TMA_NVARIANTS + 4, K_LDG_PFS = TMA_NVARIANTS + 5, K_LDG_PFZ = TMA_NVARIANTS + 6,
               K_LDG_PFE = TMA_NVARIANTS + 7, K_LDG_SHF = TMA_NVARIANTS + 8, K_LDG_SHF4 = TMA_NVARIANTS + 9,
-              K_LDG_PFZ4 = TMA_NVARIANTS + 10, K_COUNT = TMA_NVARIANTS + 11;
+              K_LDG_PFZ4 = TMA_NVARIANTS + 10, K_PAIR = TMA_NVARIANTS + 11, K_PAIR_PFZ = TMA_NVARIANTS + 12,
+              K_PAIR_PFZ3 = TMA_NVARIANTS + 13, K_COUNT = TMA_NVARIANTS + 14;
+
+// pair-kernel variant of a kernel id (-1 for others)
+int pair_variant(int k) { return k == K_PAIR ? 0 : k == K_PAIR_PFZ ? 1 : k == K_PAIR_PFZ3 ? 2 : -1; }
 
 // L1-path variant of a kernel id (-1 for others)
 int ldg_variant(int k) {
@@ -277,12 +287,20 @@ int ldg_variant(int k) {
 bool kernel_eligible(const sacrak_grid* g, int k, const std::vector<int>& pids) {
   if (k == 0) return true;
   if (k >= 1 && k <= TMA_NVARIANTS) return tma_eligible(g, k - 1, pids);
+  if (pair_variant(k) >= 0) {
+    if (g->prm.precision != 1) return false;
+    for (int pid : pids)  // 32-bit element offsets
+      if ((long long)NF * g->hp[pid].fstride >= (1LL << 31)) return false;
+    return true;
+  }
   return (ldg_variant(k) >= 0 || k == K_SPLIT) && g->prm.precision == 1;
 }
 
 // tensor maps of variant v for every patch: the five split buffers viewed as
-// 3D arrays of floats [NF*NZ][NY][2*NX] (row pitch px pairs), box
-// 76 x (TY+6) x (TZ+6) floats
+// 3D arrays of floats [NF*NZ][NY][2*(NX+1)] from their 256-byte aligned slot
+// (element 0 of a row is the spare element before ghost cell -3; row pitch
+// px pairs), box 80 x (TY+6) x (TZ+6) floats: 40 pairs from cell x0 - 4, so
+// that the box's x coordinate 2*x0 floats is a multiple of 16 bytes
 sacrak_status ensure_maps(sacrak_grid* g, int v) {
   if (!g->maps[v].empty() && g->tma_blocks[v] > 0) return SACRAK_OK;
   EncodeTiledFn enc = encode_tiled();
@@ -293,12 +311,12 @@ sacrak_status ensure_maps(sacrak_grid* g, int v) {
   for (int p = 0; p < g->npatches; ++p) {
     const DevPatch& P = g->hp[p];
     float2* bufs[5] = {P.hl[0], P.hl[1], P.hl[2], P.sa, P.sb};
-    const cuuint64_t dims[3] = {(cuuint64_t)2 * P.NX, (cuuint64_t)P.NY, (cuuint64_t)NF * P.NZ};
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * (P.NX + 1), (cuuint64_t)P.NY, (cuuint64_t)NF * P.NZ};
     const cuuint64_t strides[2] = {(cuuint64_t)P.px * 8, (cuuint64_t)P.plane * 8};
-    const cuuint32_t box[3] = {76, (cuuint32_t)(ty + 6), (cuuint32_t)(tz + 6)};
+    const cuuint32_t box[3] = {80, (cuuint32_t)(ty + 6), (cuuint32_t)(tz + 6)};
     const cuuint32_t es[3] = {1, 1, 1};
     for (int b = 0; b < 5; ++b) {
-      CUresult r = enc(&maps[p][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)bufs[b], dims, strides, box, es,
+      CUresult r = enc(&maps[p][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)(bufs[b] - 1), dims, strides, box, es,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return fail(g, SACRAK_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -352,11 +370,14 @@ void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones, const std
     }
     t.tstart[t.np] = acc;
     t.ntiles = acc;
+    t.wait_cycles = g->tma_wait_cycles != 0 ? g->tma_wait_cycles : TMA_WAIT_CYCLES;
     const long long res = (long long)g->nsm * g->tma_blocks[v];
     const int grid = (int)(acc < res ? acc : res);
     if (grid > 0) launch_stage_tma(v, t, grid, g->stream);
   } else if (g->prm.precision == 1 && ldg_variant(kernel) >= 0) {
     launch_stage_ldg(ldg_variant(kernel), a, g->stream);
+  } else if (g->prm.precision == 1 && pair_variant(kernel) >= 0) {
+    launch_stage_pair(pair_variant(kernel), a, g->stream);
   } else if (g->prm.precision == 1 && kernel == K_SPLIT) {
     launch_stage_split(a, g->d_dslot, g->stream);
   } else if (g->prm.precision == 1) {
@@ -395,6 +416,16 @@ sacrak_status select_kernel(sacrak_grid* g, int l, int kernel) {
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !done[dev][v]) {
       if (!ldg_setup(v)) return fail(g, SACRAK_ECUDA, "stage kernel %d setup failed", kernel);
+      if (dev >= 0 && dev < 64) done[dev][v] = true;
+    }
+  }
+  if (pair_variant(kernel) >= 0) {
+    static bool done[64][3] = {};  // shared-memory opt-in, once per device
+    const int v = pair_variant(kernel);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done[dev][v]) {
+      if (!pair_setup(v)) return fail(g, SACRAK_ECUDA, "stage kernel %d setup failed", kernel);
       if (dev >= 0 && dev < 64) done[dev][v] = true;
     }
   }
@@ -798,19 +829,24 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
     P.dx = dx0 / std::ldexp(1.0, P.level);
     P.zrefl = (p.zsym && std::fabs(P.origin[2]) <= 1e-12 * P.dx) ? 1 : 0;
     P.parent = -1;
+    // Every state buffer starts one element (8 bytes) past its 256-byte
+    // aligned slot: active cell i of a row is then at element i + 4 of the
+    // slot, so the pair of cells (2m, 2m+1) is one aligned 16-byte vector
+    // (the pair stage kernels load them with 128-bit loads).  The row pitch
+    // keeps a spare element, so every row stays inside its own pitch.
     for (int b = 0; b < NBUF; ++b)
-      P.buf[b] = (double*)(g->arena + L.patch_state[i] + (size_t)b * NF * P.fstride * sizeof(double));
+      P.buf[b] = (double*)(g->arena + L.patch_state[i] + (size_t)b * NF * P.fstride * sizeof(double)) + 1;
     for (int b = 0; b < 3; ++b)
       P.gsh[b] = P.level > 0 ? (double*)(g->arena + L.patch_state[i] +
-                                        (size_t)(NBUF + b) * NF * P.fstride * sizeof(double))
+                                        (size_t)(NBUF + b) * NF * P.fstride * sizeof(double)) + 1
                              : nullptr;
     if (p.precision == 1) {
       const size_t nb = (size_t)(NBUF + (P.level > 0 ? 3 : 0)) * NF * P.fstride * sizeof(double);
       float2* m0 = (float2*)(g->arena + align_up(L.patch_state[i] + nb, 256));
       const size_t fl = (size_t)NF * P.fstride;
-      for (int b = 0; b < 3; ++b) P.hl[b] = m0 + (size_t)b * fl;
-      P.sa = m0 + 3 * fl;
-      P.sb = m0 + 4 * fl;
+      for (int b = 0; b < 3; ++b) P.hl[b] = m0 + (size_t)b * fl + 1;
+      P.sa = m0 + 3 * fl + 1;
+      P.sb = m0 + 4 * fl + 1;
     }
     g->lvl_ids[P.level].push_back(i);
   }
@@ -1405,6 +1441,13 @@ sacrak_status sacrak_set_stage_kernel(sacrak_grid* g, int level, int kernel) {
       !kernel_eligible(g, kernel, g->lvl_ids[level]))
     return fail(g, SACRAK_EINVAL, "stage kernel %d not usable on level %d", kernel, level);
   return select_kernel(g, level, kernel);
+}
+
+sacrak_status sacrak_set_wait_limit(sacrak_grid* g, long long cycles) {
+  if (!g) return SACRAK_EINVAL;
+  if (g->tma_wait_cycles != cycles) drop_graph(g);  // the captured launches hold the old bound
+  g->tma_wait_cycles = cycles;
+  return SACRAK_OK;
 }
 
 sacrak_status sacrak_get_stage_kernel(sacrak_grid* g, int level, int* kernel) {

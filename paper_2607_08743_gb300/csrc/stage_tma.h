@@ -11,6 +11,8 @@
 namespace sacrak {
 
 constexpr int TMA_MAXP = 8;       // patches of one level in one launch
+// bound of a TMA stage kernel's wait for one copy: about 2 s of SM clock
+constexpr long long TMA_WAIT_CYCLES = 4000000000LL;
 constexpr int TMA_NVARIANTS = 4;  // tile shapes 32x4x1, 32x2x2, 32x4x2, 32x8x1
 
 struct TmaStageArgs {
@@ -22,11 +24,13 @@ struct TmaStageArgs {
   int tstart[TMA_MAXP + 1];      // first tile of each slot
   int ntx[TMA_MAXP], nty[TMA_MAXP];  // tiles along x and y of each slot
   int nz[TMA_MAXP];              // NZ (z extent incl. ghosts) of each slot
+  long long wait_cycles;         // bound of the wait for a field's copy (SM clock cycles);
+                                 // < 0: every such wait counts as run out at once (tests)
 };
 
 // tile shape (TY, TZ) of variant v; tiles are 32 x TY x TZ points
 void tma_variant_shape(int v, int* ty, int* tz);
-// bytes of one field box (38 x (TY+6) x (TZ+6) hi/lo pairs)
+// bytes of one field box (40 x (TY+6) x (TZ+6) hi/lo pairs)
 int tma_box_bytes(int v);
 // opt the kernels of variant v in to their shared memory; returns the
 // resident CTAs per SM (0 on failure)
@@ -50,5 +54,14 @@ void launch_stage_ldg(int v, const StageArgs& a, cudaStream_t st);
 // for a launch over ntiles tiles), then the algebra and the RK4 update.
 long long split_slot_floats(long long ntiles);
 void launch_stage_split(const StageArgs& a, float* dslot, cudaStream_t st);
+
+// Two x-adjacent points per thread with 128-bit loads of the hi/lo pairs
+// (z4c_mixed_pair.cu), one 64-thread CTA per 32 x 4 x 1 tile of StageArgs;
+// element offsets are 32-bit, so every patch needs 25 * fstride < 2^31.
+// Variant v: 0 prefetches the epilogue's streaming reads into L2; 1 also the
+// next field's z-arm rows into L1; 2 as 1 with 3 CTAs per SM.  pair_setup opts the kernels in to their
+// shared memory (false on failure).
+int pair_setup(int v);
+void launch_stage_pair(int v, const StageArgs& a, cudaStream_t st);
 
 }  // namespace sacrak

@@ -923,23 +923,49 @@ static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * 5
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 
-// device address of the scratch array on the current device (looked up once
-// per device, with that device current; the host-side symbol is only a
-// stand-in and must never be handed to a kernel)
-cudaError_t noalloc_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// device address of the scratch array on device `dev` (the current device):
+// looked up once per device, with that device current; the host-side symbol
+// is only a stand-in and must never be handed to a kernel.  A context that
+// was destroyed and created again (a device reset) reloads the module at a
+// new address, so the cached address is dropped whenever a call on that
+// device reports a destroyed context (noalloc_forget).
+cudaError_t noalloc_scratch(int dev, double** out) {
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_noalloc_addr[dev] = p;
   }
   *out = (double*)g_noalloc_addr[dev];
   return cudaSuccess;
+}
+
+void noalloc_forget(int dev, cudaError_t e) {
+  if (e != cudaErrorContextIsDestroyed && e != cudaErrorDeviceUninitialized) return;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  g_noalloc_addr[dev] = nullptr;
+}
+
+// cuMemGetAddressRange from the driver (base and size of the allocation that
+// holds a device address), looked up once through the runtime
+typedef int (*AddressRangeFn)(unsigned long long*, size_t*, unsigned long long);
+AddressRangeFn address_range_fn() {
+  static AddressRangeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (AddressRangeFn)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
 }
 
 // one block per group of 32x4 points of a z-plane, grid-striding over the
@@ -1040,24 +1066,53 @@ extern "C" sacrak_status sacrak_constraints_noalloc(const double* dev_u, const i
   if (!dev_u || !n || !out_l2 || !(dx > 0.0)) return SACRAK_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (n[d] < 4 || n[d] > NOALLOC_MAX_N) return SACRAK_EINVAL;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SACRAK_ECUDA;
+  }
+  // dev_u must be device memory of the current device (a peer GPU's memory
+  // would be read across the link, or fault without peer access) ...
   cudaPointerAttributes attr;
-  if (cudaPointerGetAttributes(&attr, dev_u) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+  if (cudaPointerGetAttributes(&attr, dev_u) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
+      attr.device != dev) {
     cudaGetLastError();
     return SACRAK_EINVAL;
   }
+  // ... and its allocation must hold the whole patch array
+  const size_t need = sizeof(double) * NF * (size_t)(n[0] + 2 * GH) * (n[1] + 2 * GH) * (n[2] + 2 * GH);
+  AddressRangeFn range = address_range_fn();
+  if (!range) return SACRAK_ECUDA;
+  unsigned long long base = 0;
+  size_t size = 0;
+  const unsigned long long a = (unsigned long long)(uintptr_t)dev_u;
+  if (range(&base, &size, a) != 0) {
+    cudaGetLastError();
+    return SACRAK_EINVAL;
+  }
+  if (a < base || a - base + need > size) return SACRAK_EINVAL;
   double* scratch = nullptr;
-  if (noalloc_scratch(&scratch) != cudaSuccess) return SACRAK_ECUDA;
+  e = noalloc_scratch(dev, &scratch);
+  if (e != cudaSuccess) {
+    noalloc_forget(dev, e);
+    cudaGetLastError();
+    return SACRAK_ECUDA;
+  }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const long long ntiles = (long long)((n[0] + 31) / 32) * ((n[1] + 3) / 4) * n[2];
   const int nblocks = (int)(ntiles < NOALLOC_MAX_BLOCKS ? ntiles : NOALLOC_MAX_BLOCKS);
   constraints_noalloc_kernel<<<nblocks, 128, 0, st>>>(dev_u, n[0], n[1], n[2], dx, w_excise, scratch);
   double* sums_dev = scratch + (size_t)NOALLOC_MAX_BLOCKS * 5;
   sum_partials_kernel<<<1, 256, 0, st>>>(scratch, nblocks, 5, sums_dev);
-  if (cudaGetLastError() != cudaSuccess) return SACRAK_ECUDA;
+  e = cudaGetLastError();
   double sums[5];
-  if (cudaMemcpyAsync(sums, sums_dev, sizeof sums, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sums, sums_dev, sizeof sums, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    noalloc_forget(dev, e);
     return SACRAK_ECUDA;
+  }
   for (int c = 0; c < 4; ++c) out_l2[c] = sums[4] > 0 ? sqrt(sums[c] / sums[4]) : 0.0;
   return SACRAK_OK;
 }

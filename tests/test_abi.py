@@ -36,11 +36,12 @@ def test_arena_bytes_host_side(L):
     import initial_data as idd
     h = idd.binary_7_level()
     def copies(mixed):
-        # 6 FP64 state copies per patch, 3 prolongation caches on levels > 0,
+        # 6 FP64 state copies per patch (rows padded to a multiple of 8 with at
+        # least one spare element), 3 prolongation caches on levels > 0,
         # mixed precision: 5 copies of FP32 hi/lo pairs (= 5 FP64 copies) and
         # 103 FP32 derivative planes over the largest level's 32 x 4 x 1 tiles
         st = sum((6 + (3 if p.level > 0 else 0) + (5 if mixed else 0)) * 25 * 8 *
-                 (p.n[0] + 6 + (-(p.n[0] + 6)) % 8) * (p.n[1] + 6) * (p.n[2] + 6) for p in h.patches)
+                 (p.n[0] + 7 + (-(p.n[0] + 7)) % 8) * (p.n[1] + 6) * (p.n[2] + 6) for p in h.patches)
         tiles = max(sum(-(-p.n[0] // 32) * -(-p.n[1] // 4) * p.n[2] for p in lv) for lv in h.levels)
         return st + (103 * 128 * 4 * tiles if mixed else 0)
     n = sk.arena_bytes(len(h.levels), h.patches)

@@ -1,34 +1,47 @@
-"""Host logic of the benchmark's roofline object (no GPU): the traffic of
-the dominant kernel comes from the ncu captures of the stage kernels the
-levels use, and is null when a level uses a kernel without a capture."""
+"""Host logic of the benchmark's roofline object (no GPU): the fraction is
+the algorithmic bytes of the method (16 FP64 field passes of 25 fields per
+RK4 step, 800 B per zone and stage on average) over the stage kernel's
+launch time, against the measured HBM peak, in both precisions; FP64 adds
+its FP64-pipe use; the traffic comes from the ncu captures of the stage
+kernels the levels use and is null when a level uses a kernel without one."""
 import bench
 
 
 def _run(precision, ids):
     kern = {"name": "k", "ms": 0.5, "launches": 508, "steps": 1, "zones_per_launch": 884736.0,
-            "bytes_per_launch": 884736.0 * 900, "flops_per_launch": 884736.0 * 5355 if precision == "fp64" else None,
+            "bytes_per_launch": 884736.0 * 800, "flops_per_launch": 884736.0 * 5355 if precision == "fp64" else None,
             "kernel_ids_used": ids, "stage_kernels": ["x"] * 7}
     return {"precision": precision, "kern": kern, "ms": 280.0}
 
 
-def test_traffic_from_captured_kernels():
+def test_traffic_from_captured_kernels(monkeypatch):
+    monkeypatch.setattr(bench, "NCU_TRAFFIC_PER_ZONE", {(1, 10): 1000.0, (1, 11): 1100.0, (0, 0): 2000.0})
     r = bench.roofline(_run("mixed", [10]), 6657.6)
-    assert r["bound"] == "hbm" and abs(r["traffic"] - 0.8531e9) < 1.0
+    assert r["bound"] == "hbm" and abs(r["traffic"] - 1000.0 * 884736) < 1.0
     r = bench.roofline(_run("mixed", [10, 11]), 6657.6)  # the larger of the two captures
-    assert abs(r["traffic"] - 0.8531e9) < 1.0
+    assert abs(r["traffic"] - 1100.0 * 884736) < 1.0
     r = bench.roofline(_run("fp64", [0]), 6657.6)
-    assert r["bound"] == "alu" and abs(r["traffic"] - 1.98e9) < 1.0
+    assert r["bound"] == "hbm" and r["limited_by"] == "FP64 pipe" and abs(r["traffic"] - 2000.0 * 884736) < 1.0
 
 
-def test_no_traffic_for_uncaptured_kernel():
+def test_no_traffic_for_uncaptured_kernel(monkeypatch):
+    monkeypatch.setattr(bench, "NCU_TRAFFIC_PER_ZONE", {(1, 10): 1000.0})
     assert bench.roofline(_run("mixed", [10, 12]), 6657.6)["traffic"] is None
     assert bench.roofline(_run("mixed", []), 6657.6)["traffic"] is None
 
 
-def test_fraction_is_achieved_over_peak():
-    r = bench.roofline(_run("mixed", [10]), 6657.6)
-    assert abs(r["achieved"] - 884736.0 * 900 / 0.5e-3 / 1e9) < 1e-6
-    assert abs(r["frac"] - r["achieved"] / 6657.6) < 1e-12
+def test_fraction_is_algorithmic_bytes_over_peak():
+    """3200 B per zone update (one RK4 step) = 800 B per zone per stage, the
+    same for both precisions; the mixed path's own hi/lo copies are reported
+    beside it, not in the fraction."""
+    assert bench.BYTES_PER_ZONE_UPDATE == 3200 and bench.ALG_BYTES_PER_ZONE_STAGE == 800
+    for prec in ("mixed", "fp64"):
+        r = bench.roofline(_run(prec, [10 if prec == "mixed" else 0]), 6657.6)
+        assert abs(r["achieved"] - 884736.0 * 800 / 0.5e-3 / 1e9) < 1e-6
+        assert abs(r["frac"] - r["achieved"] / 6657.6) < 1e-12
+    r = bench.roofline(_run("fp64", [0]), 6657.6)
+    assert abs(r["alu"]["achieved"] - 884736.0 * 5355 / 0.5e-3 / 1e12) < 1e-9
+    assert abs(r["alu"]["frac"] - r["alu"]["achieved"] / 1.25) < 1e-12
 
 
 def test_launches_per_coarse_step_by_recursion():

@@ -1,5 +1,6 @@
 """TMA-staged mixed-precision stage kernels (tile shapes 32x4x1, 32x2x2,
-32x4x2, 32x8x1) and the autotuner, through the C ABI.
+32x4x2, 32x8x1), the L1-path, split and two-points-per-thread kernels, and
+the autotuner, through the C ABI.
 
 Every kernel is held to the mixed path's tolerances against the FP64 oracle
 (1e-4 of each field's RHS scale, 1e-4 of the change an RK4 step makes), and
@@ -24,7 +25,9 @@ from tests.gpu_common import grid_for, rel_err
 skbuild.build()
 
 TMA = [1, 2, 3, 4]
-PAIRS = [5, 6, 7, 8, 9, 10, 11, 12, 13, 14]  # L1 path and split launches, same arithmetic
+# L1 path, split launches and two points per thread with 128-bit loads: the
+# same arithmetic
+PAIRS = [5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17]
 TOL = 1e-4          # mixed precision vs the FP64 oracle
 TOL_KERNELS = 2e-5  # TMA kernel vs direct mixed kernel, same data
 
@@ -127,7 +130,7 @@ def _tma_hierarchy():
     return h, idd.hierarchy_data(h, noise=1e-10)
 
 
-@pytest.mark.parametrize("kernel", [1, 7, 10])
+@pytest.mark.parametrize("kernel", [1, 7, 10, 15, 16])
 def test_tma_level_step_hierarchy_vs_oracle(kernel):
     h, states = _tma_hierarchy()
     g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(precision=1), stream=torch.cuda.Stream())
@@ -188,6 +191,6 @@ def test_tma_kernel_rejected_where_it_does_not_fit():
         g.set_stage_kernel(0, len(sk.STAGE_KERNELS))
     f = grid_for([idd.single_puncture_patch(32, 8.0)])  # FP64: only the direct kernel
     assert f.stage_kernel(0) == 0
-    for k in (1, 5):
+    for k in (1, 5, 15):
         with pytest.raises(sk.SacrakError):
             f.set_stage_kernel(0, k)
