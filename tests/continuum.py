@@ -163,8 +163,49 @@ def dt_gamma(x):
     return -2.0 * alpha(x) * Kij(x) + lie_cov(gamma, x)
 
 
-def dt_K(x):
-    """d_t K_ij (vacuum ADM)."""
+# ------------------------------------------------------------- perfect fluid
+
+FLUID_EOS = {"K": 100.0, "Gamma": 2.0, "Gamma_th": 1.8}
+
+
+def fluid(x):
+    """Generic smooth primitives (rho, eps, u_i) of a perfect fluid, eps above
+    the cold curve of FLUID_EOS (a positive thermal part)."""
+    X, Y, Z = x[0], x[1], x[2]
+    rho = 3e-3 * (1.0 + 0.3 * torch.sin(PI * X + 0.2) * torch.cos(0.5 * PI * Z) + 0.2 * torch.cos(PI * Y - 0.4))
+    K, G = FLUID_EOS["K"], FLUID_EOS["Gamma"]
+    eps = K * rho ** (G - 1.0) / (G - 1.0) * (1.3 + 0.2 * torch.sin(PI * (X - Y) + 0.3))
+    ul = torch.stack([0.35 * torch.sin(PI * Y + 0.5), -0.3 * torch.cos(PI * (X + Z)),
+                      0.3 * torch.sin(PI * Z - 0.3) * torch.cos(0.5 * PI * X) + 0.1])
+    return rho, eps, ul
+
+
+def fluid_pressure(rho, eps):
+    """Polytropic cold part plus thermal part, P = K rho^G + (G_th - 1) rho (eps - eps_cold)."""
+    K, G, Gt = FLUID_EOS["K"], FLUID_EOS["Gamma"], FLUID_EOS["Gamma_th"]
+    ec = K * rho ** (G - 1.0) / (G - 1.0)
+    return K * rho ** G + (Gt - 1.0) * rho * (eps - ec)
+
+
+def tmunu_31(x):
+    """rho_ADM = n n T, S_i = -gamma_i^mu n^nu T_{mu nu}, S_ij = gamma gamma T of
+    T_{mu nu} = rho h u_mu u_nu + P g_{mu nu}, from the 4-velocity's spatial
+    covariant components u_i and n_mu u^mu = -W_L (W_L the Lorentz factor)."""
+    rho, eps, ul = fluid(x)
+    P = fluid_pressure(rho, eps)
+    h = 1.0 + eps + P / rho
+    g = gamma(x)
+    gu = inv3(g)
+    WL = torch.sqrt(1.0 + ul @ gu @ ul)
+    E = rho * h * WL ** 2 - P
+    S = rho * h * WL * ul
+    Sij = rho * h * torch.outer(ul, ul) + P * g
+    return E, S, Sij
+
+
+def dt_K(x, matter=False):
+    """d_t K_ij (ADM; with matter the -8 pi alpha (S_ij - gamma_ij (S - rho)/2)
+    source)."""
     G = christoffel(x)
     da = jacfwd(alpha)(x)
     dda = jacfwd(jacfwd(alpha))(x)
@@ -173,12 +214,18 @@ def dt_K(x):
     gu = inv3(gamma(x))
     Kmix = torch.einsum("kl,lj->kj", gu, K)  # K^k_j
     trK = torch.einsum("kk->", Kmix)
-    return (-DDa + alpha(x) * (ricci(x) - 2.0 * torch.einsum("ik,kj->ij", K, Kmix) + trK * K)
-            + lie_cov(Kij, x))
+    out = (-DDa + alpha(x) * (ricci(x) - 2.0 * torch.einsum("ik,kj->ij", K, Kmix) + trK * K)
+           + lie_cov(Kij, x))
+    if matter:
+        E, _, Sij = tmunu_31(x)
+        Str = torch.einsum("ij,ij->", gu, Sij)
+        out = out - 8.0 * PI * alpha(x) * (Sij - 0.5 * gamma(x) * (Str - E))
+    return out
 
 
-def constraints_adm(x):
-    """Hamiltonian H and covariant momentum constraint M_j."""
+def constraints_adm(x, matter=False):
+    """Hamiltonian H and covariant momentum constraint M_j (with matter:
+    -16 pi rho_ADM and -8 pi S_j)."""
     g = gamma(x)
     gu = inv3(g)
     K = Kij(x)
@@ -193,6 +240,10 @@ def constraints_adm(x):
           - torch.einsum("lij,kl->ikj", G, K))
     dtrK = jacfwd(Ktr_of)(x)
     M = torch.einsum("ik,ikj->j", gu, DK) - dtrK
+    if matter:
+        E, Sl, _ = tmunu_31(x)
+        H = H - 16.0 * PI * E
+        M = M - 8.0 * PI * Sl
     return H, M
 
 
@@ -205,17 +256,17 @@ def dt_gt(x):
     return 2.0 * W_of(x) * dt_W(x) * gamma(x) + W_of(x) ** 2 * dt_gamma(x)
 
 
-def dt_Ktr(x):
+def dt_Ktr(x, matter=False):
     gu = inv3(gamma(x))
     dgu = -gu @ dt_gamma(x) @ gu
-    return torch.einsum("ij,ij->", dgu, Kij(x)) + torch.einsum("ij,ij->", gu, dt_K(x))
+    return torch.einsum("ij,ij->", dgu, Kij(x)) + torch.einsum("ij,ij->", gu, dt_K(x, matter))
 
 
-def dt_At(x):
+def dt_At(x, matter=False):
     W = W_of(x)
     K = Ktr_of(x)
     return (2.0 * W * dt_W(x) * (Kij(x) - gamma(x) * K / 3.0)
-            + W ** 2 * (dt_K(x) - dt_gamma(x) * K / 3.0 - gamma(x) * dt_Ktr(x) / 3.0))
+            + W ** 2 * (dt_K(x, matter) - dt_gamma(x) * K / 3.0 - gamma(x) * dt_Ktr(x, matter) / 3.0))
 
 
 def dt_gtu(x):
@@ -228,17 +279,18 @@ def dt_Gamt_kinematic(x):
     return -torch.einsum("ijj->i", d)
 
 
-def z4c_rhs_continuum(x, eta=0.36):
-    """Expected Z4c RHS (no dissipation) for this data, 25 fields."""
-    H, M = constraints_adm(x)
+def z4c_rhs_continuum(x, eta=0.36, matter=False):
+    """Expected Z4c RHS (no dissipation) for this data, 25 fields (with the
+    fluid of tmunu_31 as matter when `matter`)."""
+    H, M = constraints_adm(x, matter)
     a = alpha(x)
     b = beta(x)
     gtu = gtu_of(x)
     rW = dt_W(x)
     rgt = _six(dt_gt(x))
     rTh = 0.5 * a * H
-    rKh = dt_Ktr(x) - a * H
-    rAt = _six(dt_At(x))
+    rKh = dt_Ktr(x, matter) - a * H
+    rAt = _six(dt_At(x, matter))
     rG = dt_Gamt_kinematic(x) + 2.0 * a * (gtu @ M)
     K = Ktr_of(x)
     ra = -2.0 * a * K + b @ jacfwd(alpha)(x)
@@ -250,9 +302,9 @@ def z4c_rhs_continuum(x, eta=0.36):
     return torch.cat([rW[None], rgt, rKh[None], rTh[None], rAt, rG, ra[None], rb, rB])
 
 
-def constraints_continuum(x):
+def constraints_continuum(x, matter=False):
     """H and M^i (index raised with the physical metric)."""
-    H, M = constraints_adm(x)
+    H, M = constraints_adm(x, matter)
     gu = inv3(gamma(x))
     return torch.cat([H[None], gu @ M])
 
@@ -301,3 +353,9 @@ def patch_state(n):
         u = np.ascontiguousarray(on_points(z4c_state, pts).T.reshape(p.shape))
         _PATCH_CACHE[n] = (p, pts, u)
     return _PATCH_CACHE[n]
+
+
+def fluid_prims(x):
+    """(rho, eps, u_x, u_y, u_z) at one point, for the grid arrays."""
+    rho, eps, ul = fluid(x)
+    return torch.cat([rho[None], eps[None], ul])
