@@ -82,6 +82,8 @@ typedef struct {
                             ghosts by reflection (f(-z) = s_z f(z), s_z = -1 for fields with
                             an odd number of z indices) after every other ghost treatment;
                             not with bc = 1 */
+  int matter;            /* 1: a perfect fluid evolved with the spacetime (Sec. 2.1.2, 2.2):
+                            one level, FP64, no zsym; see the matter calls below */
 } sacrak_params;
 
 /* One patch: refinement level, active cells per axis, lower face of active
@@ -387,6 +389,56 @@ sacrak_status sacrak_autotune(sacrak_grid* grid, int reps, int use_cache, double
  * with the default bound for the copies it has in flight, and returns
  * without writing results.  Drops the recorded coarse-step graph. */
 sacrak_status sacrak_set_wait_limit(sacrak_grid* grid, long long cycles);
+
+/* ---- Matter: a perfect fluid on the evolving spacetime (Sec. 2.1.2, 2.2) ----
+ * Grids created with params.matter = 1 (one level, FP64) carry a perfect
+ * fluid: primitives (rho, eps, u_x, u_y, u_z) -- rest-mass density, specific
+ * internal energy, spatial covariant components of the four-velocity -- and
+ * the densitised conserved variables sqrt(gamma) (D, J_i, rho_H), D = rho w,
+ * J_i = rho h w u_i, rho_H = rho h w^2 - P, w = sqrt(1 + gamma^ij u_i u_j),
+ * h = 1 + eps + P/rho.  Every RK4 stage recovers the primitives from the
+ * stage's conserved variables (Newton-Raphson on w, the previous w as the
+ * guess; a negative thermal part is repaired to the cold value; a cell below
+ * the floor or without a root is reset to rest at the floor density on the
+ * cold curve), adds the fluid's terms to the Z4c right-hand side (Khat
+ * 4 pi alpha (S + rho_H), Theta -8 pi alpha rho_H, At_ij -8 pi alpha W^2
+ * [S_ij]^TF, Gamt^i and B^i -16 pi alpha gt^ij J_j), and advances the
+ * conserved variables with PPM face states (steep minmod b = 3), HLLE fluxes
+ * with the relativistic characteristic speeds, the metric at faces by
+ * 4th-order interpolation and the geometric sources (4th-order metric
+ * derivatives).  Ghost cells of the fluid: zero gradient (outflow), periodic
+ * with bc = 1.  A "matter array" exchanged with the caller is
+ * double[5][NZ][NY][NX] in the patch-array layout above.  The stepping calls
+ * return SACRAK_ESTATE until sacrak_upload_matter has run. */
+
+/* Hybrid EOS (Sec. 2.1.2): P = P_cold(rho) + (gamma_th - 1) rho (eps -
+ * eps_cold(rho)), cold part a piecewise polytrope P = K_i rho^gammas[i] on
+ * [rho_bounds[i-1], rho_bounds[i]) (npieces 1..4, npieces - 1 increasing
+ * boundaries, K_0 = K0 >= 0, the other K_i and the eps offsets fixed by
+ * continuity of P and eps).  K0 = 0 gives the ideal gas P = (gamma_th - 1)
+ * rho eps.  SACRAK_EINVAL for bad values or a grid without a fluid. */
+sacrak_status sacrak_set_eos(sacrak_grid* grid, int npieces, double K0, const double* gammas,
+                             const double* rho_bounds, double gamma_th);
+
+/* Density floor of the atmosphere (Sec. 2.2): rho_atm within the coordinate
+ * radius r_atm, falling as r^-3 outside (the paper: 1e-12 of the maximum
+ * density within eight times the finest domain). */
+sacrak_status sacrak_set_atmosphere(sacrak_grid* grid, double rho_atm, double r_atm);
+
+/* Primitives of one patch (a matter array, ghosts included, host or device
+ * memory) into the current time level; the conserved variables are formed
+ * with the patch's current metric, so upload the spacetime first.  Needs the
+ * EOS and the atmosphere (SACRAK_ESTATE otherwise).  Synchronises. */
+sacrak_status sacrak_upload_matter(sacrak_grid* grid, int patch, const double* host_or_dev_prim);
+
+/* The primitives of the last recovery (after a step: of the new time level)
+ * into a matter array (host or device memory).  Synchronises. */
+sacrak_status sacrak_download_matter(sacrak_grid* grid, int patch, double* host_or_dev_prim);
+
+/* d_t of the conserved variables of the current state of one patch (flux
+ * divergence + sources, active cells; ghost entries 0) after recovering its
+ * primitives (which may repair cells as a stage does).  Synchronises. */
+sacrak_status sacrak_matter_rhs(sacrak_grid* grid, int patch, double* host_or_dev_rhs);
 
 /* Current time of a level. */
 sacrak_status sacrak_level_time(sacrak_grid* grid, int level, double* t);

@@ -94,6 +94,8 @@ def lib():
             L.orc_rk4_step.argtypes = [P(_OrcPatch), P(_OrcParams), ctypes.c_int, ctypes.c_double, dp]
             L.orc_rk4_stage.argtypes = [P(_OrcPatch), P(_OrcParams), ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, dp, dp, dp, dp]
+            L.orc_rk4_stage_src.argtypes = [P(_OrcPatch), P(_OrcParams), ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_int, dp, dp, dp, dp, dp]
             L.orc_constraints.argtypes = [P(_OrcPatch), dp, ctypes.c_double, dp, dp]
             L.orc_pi_symmetry.argtypes = [P(_OrcPatch), dp, ctypes.c_int]
             L.orc_pi_symmetry.restype = ctypes.c_double
@@ -184,9 +186,16 @@ def rk4_step(p, u: np.ndarray, dt: float, prm: Params = Params(), bc: int = BC_S
     return u
 
 
-def rk4_stage(p, prm: Params, s: int, dt: float, evolve_ghosts: bool, us, un, y, out):
-    lib().orc_rk4_stage(ctypes.byref(_cp(p)), ctypes.byref(prm.c()), s, dt, int(evolve_ghosts),
-                        _ptr(us), _ptr(un), _ptr(y), _ptr(out))
+def rk4_stage(p, prm: Params, s: int, dt: float, evolve_ghosts: bool, us, un, y, out, src=None):
+    """RK4 stage s of the Z4c state; src (a patch array or None) is added to
+    the right-hand side at the active points (the matter terms)."""
+    if src is None:
+        lib().orc_rk4_stage(ctypes.byref(_cp(p)), ctypes.byref(prm.c()), s, dt, int(evolve_ghosts),
+                            _ptr(us), _ptr(un), _ptr(y), _ptr(out))
+    else:
+        src = np.ascontiguousarray(src, dtype=np.float64)
+        lib().orc_rk4_stage_src(ctypes.byref(_cp(p)), ctypes.byref(prm.c()), s, dt, int(evolve_ghosts),
+                                _ptr(us), _ptr(un), _ptr(y), _ptr(out), _ptr(src))
 
 
 def constraints(p, u: np.ndarray, w_excise: float = 0.0):

@@ -425,12 +425,12 @@ def tmunu(prim, u, eos):
     return E, J, Sll
 
 
-def z4c_matter_rhs(prim, u, eos):
+def z4c_matter_rhs(prim, u, eos, frozen_shift=False):
     """Matter terms of the Z4c right-hand side (25 fields, every cell):
     Khat += 4 pi alpha (S + rho), Theta -= 8 pi alpha rho,
     At_ij -= 8 pi alpha W^2 (S_ij - gamma_ij S / 3), Gamt^i -= 16 pi alpha
     gt^ij S_j, and the same Gamt term in B^i (the Gamma driver carries
-    d_t Gamt)."""
+    d_t Gamt; not with a frozen shift)."""
     E, J, Sll = tmunu(prim, u, eos)
     m = metric(u)
     al, W = u[ALP], u[W_]
@@ -444,7 +444,8 @@ def z4c_matter_rhs(prim, u, eos):
     for i in range(3):
         gi = -16.0 * math.pi * al * sum(gtu[SYM[i][j]] * J[j] for j in range(3))
         out[GAMX + i] = gi
-        out[BX + i] = gi
+        if not frozen_shift:
+            out[BX + i] = gi
     return out
 
 
@@ -512,3 +513,53 @@ def rk4_step_cowling(p, cons, u, dt, eos, floor, b=3.0, bc="outflow"):
     out[a] = new[a]
     pr, out = prims(out)
     return out, pr
+
+
+def rk4_step_coupled(p, u, cons, dt, eos, floor, prm, bc="sommerfeld", b=3.0):
+    """One classical RK4 step of the Z4c spacetime and the matter together
+    (method of lines, Sec. 2.2): at every stage the primitives are recovered
+    from the stage's conserved variables (atmosphere applied, outflow or
+    periodic ghosts), the Z4c stage runs with the matter terms of those
+    primitives added to its right-hand side, and the matter stage uses the
+    stage's metric.  Spacetime ghosts: bc "sommerfeld" (evolved with the
+    stage), "frozen" (held fixed) or "periodic" (filled before every stage
+    and after the step).  Returns (u, cons, prim) of the new level (prim
+    recovered from it)."""
+    import oracle as z4c
+    fillm = periodic_ghosts if bc == "periodic" else outflow_ghosts
+    a = (slice(None),) + _act(p)
+    un = np.array(u, dtype=np.float64, copy=True)
+    if bc == "periodic":
+        un = z4c.fill_periodic(p, un)
+    y = np.zeros_like(un)
+    cur = un
+    pr, c0, _ = recover(cons, un, eos, floor)
+    pr = fillm(p, pr)
+    cs = c0
+    ym = np.zeros_like(c0)
+    cw = [0.5, 0.5, 1.0, None]
+    bw = [1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0]
+    for s in range(1, 5):
+        if s > 1:
+            if bc == "periodic":
+                cur = z4c.fill_periodic(p, cur)
+            pr, cs, _ = recover(cs, cur, eos, floor)
+            pr = fillm(p, pr)
+        src = z4c_matter_rhs(pr, cur, eos, frozen_shift=prm.shift == 1)
+        out = np.empty_like(un)
+        z4c.rk4_stage(p, prm, s, dt, bc == "sommerfeld", cur, un, y, out, src)
+        km = matter_rhs(p, pr, cur, eos, b)
+        nxt = cs.copy()
+        if s == 1:
+            ym[a] = c0[a] + bw[0] * dt * km[a]
+        elif s < 4:
+            ym[a] = ym[a] + bw[s - 1] * dt * km[a]
+        if s < 4:
+            nxt[a] = c0[a] + cw[s - 1] * dt * km[a]
+        else:
+            nxt[a] = ym[a] + bw[3] * dt * km[a]
+        cur, cs = out, nxt
+    if bc == "periodic":
+        cur = z4c.fill_periodic(p, cur)
+    pr, cs, _ = recover(cs, cur, eos, floor)
+    return cur, cs, fillm(p, pr)

@@ -970,13 +970,24 @@ void orc_enforce(const orc_patch* p, double w_floor, int all_points, double* u) 
 
 /* ---------------- classical RK4 (Sec. 2.2) ---------------- */
 
-void orc_rk4_stage(const orc_patch* p, const orc_params* prm, int s, double dt,
-                   int evolve_ghosts, const double* us, const double* un, double* y,
-                   double* out) {
+/* src (may be NULL): a term added to the right-hand side at the active
+ * points, e.g. the matter terms of the Z4c equations (Sec. 2.1.2) */
+void orc_rk4_stage_src(const orc_patch* p, const orc_params* prm, int s, double dt,
+                       int evolve_ghosts, const double* us, const double* un, double* y,
+                       double* out, const double* src) {
   layout L = make_layout(p);
   size_t np = (size_t)L.sf * NF;
   double* k = (double*)malloc(sizeof(double) * np);
   orc_z4c_rhs(p, prm, us, k);
+  if (src)
+    for (int kk = 0; kk < L.NZ; ++kk)
+      for (int j = 0; j < L.NY; ++j)
+        for (int i = 0; i < L.NX; ++i)
+          if (!is_ghost(p, i, j, kk))
+            for (int f = 0; f < NF; ++f) {
+              ptrdiff_t q = f * L.sf + i + j * L.s[1] + kk * L.s[2];
+              k[q] += src[q];
+            }
   if (evolve_ghosts) {
     double* kg = (double*)malloc(sizeof(double) * np);
     orc_sommerfeld_rhs(p, us, kg);
@@ -1014,6 +1025,12 @@ void orc_rk4_stage(const orc_patch* p, const orc_params* prm, int s, double dt,
         enforce_point(out, L.sf, q0, prm->w_floor);
       }
   free(k);
+}
+
+void orc_rk4_stage(const orc_patch* p, const orc_params* prm, int s, double dt,
+                   int evolve_ghosts, const double* us, const double* un, double* y,
+                   double* out) {
+  orc_rk4_stage_src(p, prm, s, dt, evolve_ghosts, us, un, y, out, NULL);
 }
 
 void orc_rk4_step(const orc_patch* p, const orc_params* prm, int bc, double dt, double* u) {

@@ -122,6 +122,11 @@ void orc_rk4_step(const orc_patch* p, const orc_params* prm, int bc, double dt, 
  *   s<4: out = un + c_s dt k (c = 1/2, 1/2, 1)
  * then enforcement on the written points.  Points that are not updated keep
  * the values of un in out. */
+/* orc_rk4_stage with src (NULL or a patch array) added to the right-hand
+ * side at the active points (the matter terms of the Z4c equations). */
+void orc_rk4_stage_src(const orc_patch* p, const orc_params* prm, int s, double dt,
+                       int evolve_ghosts, const double* us, const double* un, double* y,
+                       double* out, const double* src);
 void orc_rk4_stage(const orc_patch* p, const orc_params* prm, int s, double dt,
                    int evolve_ghosts, const double* us, const double* un, double* y,
                    double* out);

@@ -32,7 +32,8 @@ EXPORTS = [
     "sacrak_set_stage_kernel", "sacrak_get_stage_kernel", "sacrak_autotune", "sacrak_adm_integrals",
     "sacrak_track_punctures", "sacrak_get_punctures", "sacrak_move_patch", "sacrak_regrid",
     "sacrak_patch_origin", "sacrak_psi4_modes", "sacrak_nakano", "sacrak_ffi_work_bytes", "sacrak_ffi_strain",
-    "sacrak_set_wait_limit",
+    "sacrak_set_wait_limit", "sacrak_set_eos", "sacrak_set_atmosphere", "sacrak_upload_matter",
+    "sacrak_download_matter", "sacrak_matter_rhs",
 ]
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
@@ -64,7 +65,8 @@ class sacrak_params(ctypes.Structure):
     _fields_ = [("kappa1", ctypes.c_double), ("kappa2", ctypes.c_double), ("eta", ctypes.c_double),
                 ("sigma_ko", ctypes.c_double), ("courant", ctypes.c_double), ("w_floor", ctypes.c_double),
                 ("lapse", ctypes.c_int), ("shift", ctypes.c_int), ("bc", ctypes.c_int),
-                ("precision", ctypes.c_int), ("lapse_uses_khat", ctypes.c_int), ("zsym", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("lapse_uses_khat", ctypes.c_int), ("zsym", ctypes.c_int),
+                ("matter", ctypes.c_int)]
 
 
 class sacrak_patch_desc(ctypes.Structure):
@@ -109,6 +111,11 @@ def lib() -> ctypes.CDLL:
                                                      vp, dp]
             L.sacrak_set_stage_kernel.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             L.sacrak_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+            L.sacrak_set_eos.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_double]
+            L.sacrak_set_atmosphere.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+            L.sacrak_upload_matter.argtypes = [vp, ctypes.c_int, vp]
+            L.sacrak_download_matter.argtypes = [vp, ctypes.c_int, vp]
+            L.sacrak_matter_rhs.argtypes = [vp, ctypes.c_int, vp]
             L.sacrak_get_stage_kernel.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
             L.sacrak_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
             L.sacrak_last_error.argtypes = [vp]
@@ -137,11 +144,12 @@ class Params:
     precision: int = 0     # 0 FP64, 1 mixed
     lapse_uses_khat: int = 0
     zsym: int = 0          # 1: equatorial reflection symmetry, only z >= 0 evolved
+    matter: int = 0        # 1: a perfect fluid evolved with the spacetime (one level, FP64)
 
     def c(self) -> sacrak_params:
         return sacrak_params(self.kappa1, self.kappa2, self.eta, self.sigma_ko, self.courant, self.w_floor,
                              self.lapse, self.shift, self.bc, self.precision, self.lapse_uses_khat,
-                             self.zsym)
+                             self.zsym, self.matter)
 
 
 def _descs(patches) -> ctypes.Array:
@@ -320,6 +328,40 @@ class Grid:
         if out is None:
             out = np.empty(self.shape(patch))
         self._check(lib().sacrak_rhs(self._h, patch, ctypes.c_void_p(_ptr(out))), "rhs")
+        return out
+
+    # ---- matter (Sec. 2.1.2, 2.2) ----
+
+    def matter_shape(self, patch: int):
+        sh = self.shape(patch)
+        return (5,) + tuple(sh[1:])
+
+    def set_eos(self, K0: float, gammas, rho_bounds=(), gamma_th: float = 1.8):
+        """Hybrid EOS: piecewise polytrope (K0, gammas, rho_bounds) + thermal part."""
+        g = (ctypes.c_double * len(gammas))(*[float(v) for v in gammas])
+        b = (ctypes.c_double * max(1, len(rho_bounds)))(*[float(v) for v in rho_bounds])
+        self._check(lib().sacrak_set_eos(self._h, len(gammas), float(K0), g, b, float(gamma_th)), "set_eos")
+
+    def set_atmosphere(self, rho_atm: float, r_atm: float):
+        self._check(lib().sacrak_set_atmosphere(self._h, float(rho_atm), float(r_atm)), "set_atmosphere")
+
+    def upload_matter(self, patch: int, prim):
+        if isinstance(prim, np.ndarray):
+            prim = np.ascontiguousarray(prim, dtype=np.float64)
+            if prim.shape != self.matter_shape(patch):
+                raise SacrakError(EINVAL, "matter array of shape %s, expected %s" % (prim.shape, self.matter_shape(patch)))
+        self._check(lib().sacrak_upload_matter(self._h, patch, ctypes.c_void_p(_ptr(prim))), "upload_matter")
+
+    def download_matter(self, patch: int, out=None):
+        if out is None:
+            out = np.empty(self.matter_shape(patch))
+        self._check(lib().sacrak_download_matter(self._h, patch, ctypes.c_void_p(_ptr(out))), "download_matter")
+        return out
+
+    def matter_rhs(self, patch: int, out=None):
+        if out is None:
+            out = np.empty(self.matter_shape(patch))
+        self._check(lib().sacrak_matter_rhs(self._h, patch, ctypes.c_void_p(_ptr(out))), "matter_rhs")
         return out
 
     def rk4_step(self, level: int = 0, dt: float = 0.0):

@@ -15,6 +15,7 @@
 
 #include "../../include/sacrak.h"
 #include "sacrak_dev.cuh"
+#include "grhd.h"
 #include "stage_tma.h"
 
 using namespace sacrak;
@@ -30,13 +31,22 @@ struct Layout {
   // byte offsets inside the arena
   size_t patches, levels, ids, tiles, err, results, punct, scratch, dslot, states, total;
   std::vector<size_t> patch_state;  // offset of each patch's first buffer
+  std::vector<size_t> matter_state; // offset of each patch's matter arrays (fluid grids)
   std::vector<long long> fstride;
   std::vector<int> px;
   size_t ntiles = 0, scratch_doubles = 0;
 };
 
-bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed, Layout& L,
+// fields of the matter arrays of a patch: conserved variables in the six
+// state slots, primitives + Lorentz factor, face fluxes, Z4c matter terms
+constexpr int MATTER_FIELDS = NBUF * NM + NMP + 3 * NM + NZSRC;
+
+bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed, int matter, Layout& L,
               std::string& why) {
+  if (matter && (nlevels != 1 || mixed)) {
+    why = "a fluid needs one level and FP64";
+    return false;
+  }
   if (nlevels < 1 || npatches < 1 || !pd) {
     why = "need at least one level and one patch";
     return false;
@@ -96,6 +106,7 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed,
   if (mixed) off = align_up(off + (size_t)split_slot_floats((long long)maxtiles_level) * sizeof(float), 256);
   L.states = off;
   L.patch_state.resize(npatches);
+  L.matter_state.assign(npatches, 0);
   L.fstride.resize(npatches);
   L.px.resize(npatches);
   for (int p = 0; p < npatches; ++p) {
@@ -111,6 +122,10 @@ bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed,
     const int nbuf = NBUF + (pd[p].level > 0 ? 3 : 0);  // + cached prolongation slots
     off = align_up(off + (size_t)nbuf * NF * fs * sizeof(double), 256);
     if (mixed) off = align_up(off + (size_t)5 * NF * fs * sizeof(float2), 256);  // hl[3] sa sb
+    if (matter) {
+      L.matter_state[p] = off;
+      off = align_up(off + (size_t)MATTER_FIELDS * fs * sizeof(double), 256);
+    }
   }
   // whole-buffer copies and fills from the shifted bases reach one element
   // past the last buffer
@@ -157,6 +172,11 @@ struct sacrak_grid {
   // profiling of the fused stage kernel
   bool prof = false;
   long long tma_wait_cycles = 0;  // 0: TMA_WAIT_CYCLES (sacrak_set_wait_limit)
+  // fluid (params.matter): EOS and atmosphere
+  DevEOS eos = {};
+  bool eos_set = false;
+  bool matter_ready = false;  // primitives uploaded
+  double rho_atm = 0.0, r_atm = 0.0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   size_t ev_used = 0;
   long long prof_zones = 0;
@@ -203,7 +223,7 @@ DevParams dev_params(const sacrak_params& p) {
   d.lapse = p.lapse;
   d.shift = p.shift;
   d.lapse_uses_khat = p.lapse_uses_khat;
-  d.pad_ = 0;
+  d.matter = p.matter;
   return d;
 }
 
@@ -543,12 +563,63 @@ void refresh_all_shells(sacrak_grid* g) {
   g->shells_dirty = false;
 }
 
+MatterArgs matter_args(const sacrak_grid* g, int pid, int stage, double dt) {
+  const DevPatch& P = g->hp[pid];
+  MatterArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.P = g->d_patches + pid;
+  a.lev = g->d_levels + P.level;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = P.n[d];
+    a.origin[d] = P.origin[d];
+  }
+  a.NX = P.NX;
+  a.NY = P.NY;
+  a.NZ = P.NZ;
+  a.sy = P.px;
+  a.sz = P.plane;
+  a.fs = P.fstride;
+  a.dx = P.dx;
+  a.eos = g->eos;
+  a.rho_atm = g->rho_atm;
+  a.r_atm = g->r_atm;
+  a.periodic = g->prm.bc == 1;
+  a.stage = stage;
+  a.coupled = 1;
+  a.dt = dt;
+  a.out = nullptr;
+  a.err = g->d_err;
+  return a;
+}
+
+// fluid of level l at RK stage s (0: the current level, 5: the new level):
+// recovery (atmosphere, Z4c matter terms) and the primitives' ghost cells
+void matter_recover(sacrak_grid* g, int l, int s, double dt) {
+  for (int pid : g->lvl_ids[l]) {
+    const MatterArgs a = matter_args(g, pid, s, dt);
+    launch_matter_prep(a, g->stream);
+    launch_matter_ghosts(a, g->stream);
+  }
+}
+
+// face fluxes and the stage update of the fluid (s = 0: d_t into out)
+void matter_advance(sacrak_grid* g, int l, int s, double dt, double* out = nullptr) {
+  for (int pid : g->lvl_ids[l]) {
+    MatterArgs a = matter_args(g, pid, s, dt);
+    a.out = out;
+    for (int d = 0; d < 3; ++d) launch_matter_flux(a, d, g->stream);
+    launch_matter_update(a, g->stream);
+  }
+}
+
 void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
   const int np = (int)g->lvl_ids[l].size();
   for (int s = 1; s <= 4; ++s) {
     if (!(l == 0 && (g->prm.bc == 0 || (g->prm.bc == 2 && s == 1))))
       fill_ghosts(g, l, 0, s, frac0, dfrac, l > 0 ? (s == 2 ? 2 : (s == 3 ? 0 : 1)) : 1);
     zreflect(g, l, 0, s);  // equatorial symmetry: after every other ghost treatment
+    // the fluid of this stage: primitives and the Z4c matter terms first
+    if (g->prm.matter) matter_recover(g, l, s, dt);
     StageArgs a;
     a.tiles = g->d_tiles + g->lvl_tile_off[l];
     a.ntiles = (int)g->lvl_ntiles[l];
@@ -573,7 +644,9 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
       else
         launch_sommerfeld(ga, np, g->lvl_max_shell[l], g->stream);
     }
+    if (g->prm.matter) matter_advance(g, l, s, dt);  // on this stage's metric
   }
+  if (g->prm.matter) matter_recover(g, l, 5, dt);  // primitives of the new level
   // ghosts of the new time level for periodic / frozen outer boundaries
   if (l == 0 && g->prm.bc == 1)
     launch_fill(FILL_PERIODIC, fill_args(g, l, 2, 4, 0.0), np, g->lvl_max_shell[l], g->stream);
@@ -775,7 +848,8 @@ size_t sacrak_arena_bytes(int nlevels, int npatches, const sacrak_patch_desc* pa
   Layout L;
   std::string why;
   const int mixed = params ? (params->precision == 1) : 0;
-  if (!describe(nlevels, npatches, patches, mixed, L, why)) return 0;
+  const int matter = params ? (params->matter != 0) : 0;
+  if (!describe(nlevels, npatches, patches, mixed, matter, L, why)) return 0;
   return L.total;
 }
 
@@ -787,7 +861,8 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   *out = nullptr;
   Layout L;
   std::string why;
-  if (!describe(nlevels, npatches, pd, params->precision == 1, L, why)) return SACRAK_EINVAL;
+  if (params->matter < 0 || params->matter > 1 || (params->matter && params->zsym)) return SACRAK_EINVAL;
+  if (!describe(nlevels, npatches, pd, params->precision == 1, params->matter, L, why)) return SACRAK_EINVAL;
   if (arena_bytes < L.total || ((uintptr_t)device_arena % 256) != 0) return SACRAK_EINVAL;
   const sacrak_params& p = *params;
   if (p.lapse < 0 || p.lapse > 1 || p.shift < 0 || p.shift > 1 || p.bc < 0 || p.bc > 2 ||
@@ -847,6 +922,14 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
       for (int b = 0; b < 3; ++b) P.hl[b] = m0 + (size_t)b * fl + 1;
       P.sa = m0 + 3 * fl + 1;
       P.sb = m0 + 4 * fl + 1;
+    }
+    if (p.matter) {
+      double* m0 = (double*)(g->arena + L.matter_state[i]);
+      const size_t fl = (size_t)P.fstride;
+      for (int b = 0; b < NBUF; ++b) P.mcons[b] = m0 + (size_t)b * NM * fl;
+      P.mprim = m0 + (size_t)NBUF * NM * fl;
+      P.mflux = P.mprim + (size_t)NMP * fl;
+      P.mzsrc = P.mflux + (size_t)3 * NM * fl;
     }
     g->lvl_ids[P.level].push_back(i);
   }
@@ -1022,10 +1105,10 @@ sacrak_status sacrak_set_initial_data(sacrak_grid* g, int kind, int npunct, cons
 }
 
 static sacrak_status copy_patch(sacrak_grid* g, int patch, double* dst_dev_slot, const double* src,
-                                double* dst, bool upload) {
+                                double* dst, bool upload, int nfields = NF) {
   const DevPatch& P = g->hp[patch];
   size_t width = (size_t)P.NX * sizeof(double);
-  size_t rows = (size_t)NF * P.NY * P.NZ;
+  size_t rows = (size_t)nfields * P.NY * P.NZ;
   cudaPointerAttributes at;
   const void* host_side = upload ? (const void*)src : (const void*)dst;
   const bool is_host = cudaPointerGetAttributes(&at, host_side) != cudaSuccess ||
@@ -1116,6 +1199,10 @@ sacrak_status sacrak_rhs(sacrak_grid* g, int patch, double* dst) {
   a.dt = 0.0;
   a.prm = dev_params(g->prm);
   a.err = g->d_err;
+  if (g->prm.matter) {
+    if (!g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
+    matter_recover(g, l, 0, 0.0);
+  }
   launch_stage(g, a, (long long)P.n[0] * P.n[1] * P.n[2], std::vector<int>{patch}, g->lvl_kernel[l]);
   sacrak_status st = check_launch(g);
   if (st != SACRAK_OK) return st;
@@ -1128,6 +1215,7 @@ sacrak_status sacrak_rk4_step(sacrak_grid* g, int level, double dt) {
   if (!g) return SACRAK_EINVAL;
   if (level < 0 || level >= g->nlevels) return fail(g, SACRAK_EINVAL, "bad level");
   if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
+  if (g->prm.matter && !g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
   refresh_all_shells(g);
   rk4_level(g, level, dt > 0.0 ? dt : level_dt(g, level), 0.0, 0.5);
   return check_launch(g);
@@ -1137,6 +1225,7 @@ sacrak_status sacrak_level_step(sacrak_grid* g, int level) {
   if (!g) return SACRAK_EINVAL;
   if (level < 0 || level >= g->nlevels) return fail(g, SACRAK_EINVAL, "bad level");
   if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
+  if (g->prm.matter && !g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
   refresh_all_shells(g);  // eager, outside any graph
   if (level > 0 || g->stream == nullptr || g->prof) {
     level_step_rec(g, level, 0.0, 0.5);
@@ -1163,6 +1252,97 @@ sacrak_status sacrak_level_step(sacrak_grid* g, int level) {
   }
   CK(cudaGraphLaunch(g->graph_exec, g->stream));
   return SACRAK_OK;
+}
+
+// ---- matter (Sec. 2.1.2, 2.2) ----
+
+sacrak_status sacrak_set_eos(sacrak_grid* g, int npieces, double K0, const double* gammas, const double* rho_bounds,
+                             double gamma_th) {
+  if (!g) return SACRAK_EINVAL;
+  if (!g->prm.matter) return fail(g, SACRAK_EINVAL, "grid created without a fluid (params.matter = 0)");
+  if (npieces < 1 || npieces > MAX_PIECES || !gammas || (npieces > 1 && !rho_bounds) || !(K0 >= 0.0) ||
+      !(gamma_th > 1.0) || !std::isfinite(K0) || !std::isfinite(gamma_th))
+    return fail(g, SACRAK_EINVAL, "bad EOS parameters");
+  DevEOS e;
+  std::memset(&e, 0, sizeof e);
+  e.n = npieces;
+  e.gth = gamma_th;
+  for (int i = 0; i < npieces; ++i) {
+    if (!(gammas[i] > 1.0) || !std::isfinite(gammas[i])) return fail(g, SACRAK_EINVAL, "polytrope index <= 1");
+    e.G[i] = gammas[i];
+  }
+  for (int i = 0; i + 1 < npieces; ++i) {
+    if (!(rho_bounds[i] > 0.0) || (i > 0 && !(rho_bounds[i] > rho_bounds[i - 1])))
+      return fail(g, SACRAK_EINVAL, "piece boundaries must be positive and increasing");
+    e.rb[i] = rho_bounds[i];
+  }
+  // continuity of P and eps_cold at the boundaries fixes K_i and a_i
+  e.K[0] = K0;
+  e.a[0] = 0.0;
+  for (int i = 1; i < npieces; ++i) {
+    const double rb = e.rb[i - 1], g0 = e.G[i - 1], g1 = e.G[i];
+    e.K[i] = e.K[i - 1] * std::pow(rb, g0 - g1);
+    const double eprev = e.a[i - 1] + e.K[i - 1] * std::pow(rb, g0 - 1.0) / (g0 - 1.0);
+    e.a[i] = eprev - e.K[i] * std::pow(rb, g1 - 1.0) / (g1 - 1.0);
+  }
+  g->eos = e;
+  g->eos_set = true;
+  drop_graph(g);  // the captured launches hold the old EOS
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_set_atmosphere(sacrak_grid* g, double rho_atm, double r_atm) {
+  if (!g) return SACRAK_EINVAL;
+  if (!g->prm.matter) return fail(g, SACRAK_EINVAL, "grid created without a fluid (params.matter = 0)");
+  if (!(rho_atm > 0.0) || !(r_atm > 0.0) || !std::isfinite(rho_atm) || !std::isfinite(r_atm))
+    return fail(g, SACRAK_EINVAL, "atmosphere density and radius must be positive");
+  g->rho_atm = rho_atm;
+  g->r_atm = r_atm;
+  drop_graph(g);
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_upload_matter(sacrak_grid* g, int patch, const double* prim) {
+  if (!g) return SACRAK_EINVAL;
+  if (!g->prm.matter) return fail(g, SACRAK_EINVAL, "grid created without a fluid (params.matter = 0)");
+  if (patch < 0 || patch >= g->npatches || !prim) return fail(g, SACRAK_EINVAL, "bad patch or pointer");
+  if (!g->eos_set || !(g->rho_atm > 0.0)) return fail(g, SACRAK_ESTATE, "set the EOS and the atmosphere first");
+  const DevPatch& P = g->hp[patch];
+  sacrak_status st = copy_patch(g, patch, P.mprim, prim, nullptr, true, NM);
+  if (st != SACRAK_OK) return st;
+  launch_matter_prim2con(matter_args(g, patch, 0, 0.0), g->stream);
+  st = check_launch(g);
+  if (st != SACRAK_OK) return st;
+  g->matter_ready = true;
+  return sync_and_check(g);
+}
+
+sacrak_status sacrak_download_matter(sacrak_grid* g, int patch, double* prim) {
+  if (!g) return SACRAK_EINVAL;
+  if (!g->prm.matter) return fail(g, SACRAK_EINVAL, "grid created without a fluid (params.matter = 0)");
+  if (patch < 0 || patch >= g->npatches || !prim) return fail(g, SACRAK_EINVAL, "bad patch or pointer");
+  if (!g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
+  const DevPatch& P = g->hp[patch];
+  sacrak_status st = copy_patch(g, patch, P.mprim, nullptr, prim, false, NM);
+  if (st != SACRAK_OK) return st;
+  return sync_and_check(g);
+}
+
+sacrak_status sacrak_matter_rhs(sacrak_grid* g, int patch, double* rhs) {
+  if (!g) return SACRAK_EINVAL;
+  if (!g->prm.matter) return fail(g, SACRAK_EINVAL, "grid created without a fluid (params.matter = 0)");
+  if (patch < 0 || patch >= g->npatches || !rhs) return fail(g, SACRAK_EINVAL, "bad patch or pointer");
+  if (!g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
+  if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
+  const DevPatch& P = g->hp[patch];
+  CK(cudaMemsetAsync(P.buf[B_S1], 0, (size_t)NM * P.fstride * sizeof(double), g->stream));
+  matter_recover(g, P.level, 0, 0.0);
+  matter_advance(g, P.level, 0, 0.0, P.buf[B_S1]);
+  sacrak_status st = check_launch(g);
+  if (st != SACRAK_OK) return st;
+  st = copy_patch(g, patch, P.buf[B_S1], nullptr, rhs, false, NM);
+  if (st != SACRAK_OK) return st;
+  return sync_and_check(g);
 }
 
 sacrak_status sacrak_constraints(sacrak_grid* g, int level, double w_excise, double out_l2[4]) {

@@ -1,0 +1,602 @@
+// GR hydrodynamics of a perfect fluid on the evolving spacetime (Sec. 2.1.2,
+// 2.2 of the SACRA-K paper), FP64.
+//
+//  - Variables: primitives (rho, eps, u_i) with u_i the spatial covariant
+//    components of the four-velocity, w = alpha u^t = sqrt(1 + gamma^ij u_i
+//    u_j); densitised conserved variables sqrt(gamma) (D, J_i, rho_H) with
+//    D = rho w, J_i = rho h w u_i, rho_H = rho h w^2 - P, h = 1 + eps + P/rho.
+//  - Hybrid EOS: P = P_cold(rho) + (Gamma_th - 1) rho (eps - eps_cold(rho)),
+//    the cold part a piecewise polytrope.
+//  - Fluxes along j with V^j = alpha gamma^jk u_k / w - beta^j:
+//    D^ V^j, J^_i V^j + alpha sqrt(gamma) P delta^j_i, E^ V^j + sqrt(gamma)
+//    P (V^j + beta^j); sources sqrt(gamma) (-rho_H d_i alpha + J_k d_i beta^k
+//    + alpha/2 S^jk d_i gamma_jk) and sqrt(gamma) (alpha S^jk K_jk - J^j
+//    d_j alpha), S^jk = rho h u^j u^k + P gamma^jk.
+//  - Faces: PPM (Colella & Woodward) edge values with slopes limited by the
+//    steep minmod of parameter b = 3, metric by the 4th-order Lagrange
+//    interpolation (-1, 9, 9, -1)/16, HLLE flux with the relativistic
+//    characteristic speeds; metric derivatives of the sources by the
+//    4th-order centred differences.
+//  - Recovery: Newton-Raphson on w with the hybrid EOS solved for P(w) in
+//    closed form, f(w) = w - (rho_H + P) / sqrt((rho_H + P)^2 - S^2), the
+//    previous recovery's w as the guess and a bisection bracket; a negative
+//    thermal part is repaired to the cold value; a cell below the floor or
+//    without a root is reset to rest at the floor density (atmosphere).
+//
+// Kernels: one thread per active cell (recovery, update) or per face
+// (fluxes, one launch per direction into a face-flux array), grid-striding.
+#include <math.h>
+
+#include "grhd.h"
+#include "sacrak_dev.cuh"
+
+namespace sacrak {
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double PPM_B = 3.0;
+
+struct Met {
+  double al, be[3], g[6], gu[6], sg;
+};
+
+__device__ __forceinline__ double inv_sym(const double g[6], double gu[6]) {
+  const double c0 = g[3] * g[5] - g[4] * g[4];
+  const double c1 = g[2] * g[4] - g[1] * g[5];
+  const double c2 = g[1] * g[4] - g[2] * g[3];
+  const double det = g[0] * c0 + g[1] * c1 + g[2] * c2;
+  const double id = 1.0 / det;
+  gu[0] = c0 * id;
+  gu[1] = c1 * id;
+  gu[2] = c2 * id;
+  gu[3] = (g[0] * g[5] - g[2] * g[2]) * id;
+  gu[4] = (g[1] * g[2] - g[0] * g[4]) * id;
+  gu[5] = (g[0] * g[3] - g[1] * g[1]) * id;
+  return det;
+}
+
+// 3+1 metric at cell q of the Z4c state u (optionally K_ij)
+__device__ __forceinline__ void metric_at(const double* __restrict__ u, long long q, long long fs, Met& m,
+                                          double* K_ll) {
+  const double W = __ldg(u + F_W * fs + q);
+  double gt[6], gtu[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) gt[a] = __ldg(u + (F_GXX + a) * fs + q);
+  const double det = inv_sym(gt, gtu);
+  const double iW2 = 1.0 / (W * W);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    m.g[a] = gt[a] * iW2;
+    m.gu[a] = gtu[a] * (W * W);
+  }
+  m.sg = sqrt(det) / (W * W * W);
+  m.al = __ldg(u + F_ALP * fs + q);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) m.be[d] = __ldg(u + (F_BETX + d) * fs + q);
+  if (K_ll) {
+    const double K = __ldg(u + F_KH * fs + q) + 2.0 * __ldg(u + F_TH * fs + q);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) K_ll[a] = (__ldg(u + (F_AXX + a) * fs + q) + gt[a] * K / 3.0) * iW2;
+  }
+}
+
+__device__ __forceinline__ void raise3(const double gu[6], const double v[3], double r[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) r[i] = gu[S2(i, 0)] * v[0] + gu[S2(i, 1)] * v[1] + gu[S2(i, 2)] * v[2];
+}
+
+// ------------------------------------------------------------------ EOS
+
+__device__ __forceinline__ void eos_cold(const DevEOS& e, double rho, double& P, double& eps, double& dP) {
+  int i = 0;
+  for (int b = 0; b < e.n - 1; ++b) i += rho >= e.rb[b] ? 1 : 0;
+  const double K = e.K[i], G = e.G[i];
+  const double rg = pow(rho, G - 1.0);
+  P = K * rg * rho;
+  eps = e.a[i] + K * rg / (G - 1.0);
+  dP = G * K * rg;
+}
+
+__device__ __forceinline__ double eos_pressure(const DevEOS& e, double rho, double eps) {
+  double Pc, ec, dP;
+  eos_cold(e, rho, Pc, ec, dP);
+  return Pc + (e.gth - 1.0) * rho * (eps - ec);
+}
+
+__device__ __forceinline__ double eos_cs2(const DevEOS& e, double rho, double eps) {
+  double Pc, ec, dPc;
+  eos_cold(e, rho, Pc, ec, dPc);
+  const double g = e.gth - 1.0;
+  const double P = Pc + g * rho * (eps - ec);
+  const double chi = dPc + g * (eps - ec) - g * Pc / rho;
+  const double kap = g * rho;
+  const double h = 1.0 + eps + P / rho;
+  return (chi + P / (rho * rho) * kap) / h;
+}
+
+// ------------------------------------------------------------------ prim <-> con
+
+__device__ __forceinline__ void prim2con(const DevEOS& e, const Met& m, const double pr[NM], double c[NM],
+                                         double& w, double& h, double& P) {
+  const double ul[3] = {pr[2], pr[3], pr[4]};
+  double uu[3];
+  raise3(m.gu, ul, uu);
+  w = sqrt(1.0 + ul[0] * uu[0] + ul[1] * uu[1] + ul[2] * uu[2]);
+  P = eos_pressure(e, pr[0], pr[1]);
+  h = 1.0 + pr[1] + P / pr[0];
+  c[0] = m.sg * pr[0] * w;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) c[1 + i] = m.sg * pr[0] * h * w * ul[i];
+  c[4] = m.sg * (pr[0] * h * w * w - P);
+}
+
+// P(w) of the hybrid EOS at fixed D, rho_H (closed form) and dP/dw
+__device__ __forceinline__ void pressure_of_w(const DevEOS& e, double w, double D, double E, double& P,
+                                              double& dPdw) {
+  const double rho = D / w;
+  double Pc, ec, dPc;
+  eos_cold(e, rho, Pc, ec, dPc);
+  const double g = e.gth - 1.0;
+  const double iw = 1.0 / w, iw2 = iw * iw;
+  const double N = Pc + g * (E * iw2 - D * iw * (1.0 + ec));
+  const double Q = 1.0 + g * (1.0 - iw2);
+  // d eps_cold / d rho = P_cold / rho^2, d rho / d w = -D / w^2
+  const double dN = -D * iw2 * dPc + g * (-2.0 * E * iw2 * iw + D * iw2 * (1.0 + ec) + Pc * iw);
+  const double dQ = 2.0 * g * iw2 * iw;
+  P = N / Q;
+  dPdw = (dN * Q - N * dQ) / (Q * Q);
+}
+
+// Newton-Raphson on w within the bracket [lo, hi] (bisection where a step
+// leaves it); returns true for a physical root
+__device__ bool con2prim(const DevEOS& e, const Met& m, const double c[NM], double wg, double pr[NM],
+                         double& wout) {
+  const double D = c[0] / m.sg, E = c[4] / m.sg;
+  const double J[3] = {c[1] / m.sg, c[2] / m.sg, c[3] / m.sg};
+  double Ju[3];
+  raise3(m.gu, J, Ju);
+  const double S2 = J[0] * Ju[0] + J[1] * Ju[1] + J[2] * Ju[2];
+  if (!(D > 0.0) || !(E > 0.0) || !isfinite(D) || !isfinite(E)) return false;
+  double w = fmin(fmax(wg, 1.0), 1e4), lo = 1.0, hi = 1e4;
+  double P = 0.0, dP = 0.0;
+#pragma unroll 1
+  for (int it = 0; it < 60; ++it) {
+    pressure_of_w(e, w, D, E, P, dP);
+    const double X = E + P;
+    const double q = X * X - S2;
+    const double R = sqrt(fmax(q, 1e-300));
+    const double f = w - X / R;
+    if (f < 0.0) lo = fmax(lo, w);
+    if (f > 0.0) hi = fmin(hi, w);
+    const double fp = 1.0 + dP * S2 / (R * R * R);
+    double wn = w - f / (fp != 0.0 ? fp : 1.0);
+    if (!(wn > lo && wn < hi)) wn = 0.5 * (lo + hi);
+    const bool done = fabs(wn - w) <= 1e-15 * wn;
+    w = wn;
+    if (done) break;
+  }
+  pressure_of_w(e, w, D, E, P, dP);
+  const double X = E + P;
+  const double q = X * X - S2;
+  const double f = w - X / sqrt(fmax(q, 1e-300));
+  const double rho = D / w;
+  const double h = X / (D * w);
+  pr[0] = rho;
+  pr[1] = h - 1.0 - P / rho;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) pr[2 + i] = J[i] / (rho * h * w);
+  wout = w;
+  return isfinite(w) && q > 0.0 && rho > 0.0 && fabs(f) <= 1e-10 * w;
+}
+
+__device__ __forceinline__ double floor_at(const MatterArgs& A, int i, int j, int k) {
+  const double x = A.origin[0] + (i + 0.5) * A.dx, y = A.origin[1] + (j + 0.5) * A.dx,
+               z = A.origin[2] + (k + 0.5) * A.dx;
+  const double r = sqrt(x * x + y * y + z * z);
+  if (r <= A.r_atm) return A.rho_atm;
+  const double s = A.r_atm / fmax(r, 1e-300);
+  return A.rho_atm * s * s * s;
+}
+
+__device__ __forceinline__ const double* z4c_stage_state(const MatterArgs& A, int ring) {
+  const int s = A.stage;
+  return A.P->buf[s == 0 ? ring : (s == 5 ? stage_out_slot(4, ring) : stage_in_slot(s, ring))];
+}
+__device__ __forceinline__ double* matter_stage_state(const MatterArgs& A, int ring) {
+  const int s = A.stage;
+  return A.P->mcons[s == 0 ? ring : (s == 5 ? stage_out_slot(4, ring) : stage_in_slot(s, ring))];
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void __launch_bounds__(128) matter_prep_kernel(MatterArgs A) {
+  const long long nact = (long long)A.n[0] * A.n[1] * A.n[2];
+  const int ring = A.lev->ring;
+  const double* __restrict__ u = z4c_stage_state(A, ring);
+  double* __restrict__ cons = matter_stage_state(A, ring);
+  double* __restrict__ prim = A.P->mprim;
+  double* __restrict__ zs = A.P->mzsrc;
+  const long long fs = A.fs;
+  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < nact;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % A.n[0]);
+    const int j = (int)((id / A.n[0]) % A.n[1]);
+    const int k = (int)(id / ((long long)A.n[0] * A.n[1]));
+    const long long q = (i + GH) + (j + GH) * A.sy + (k + GH) * A.sz;
+    Met m;
+    metric_at(u, q, fs, m, nullptr);
+    double c[NM], pr[NM], w;
+#pragma unroll
+    for (int f = 0; f < NM; ++f) c[f] = cons[f * fs + q];
+    bool ok = con2prim(A.eos, m, c, prim[NM * fs + q], pr, w);
+    double Pc, ec, dP;
+    eos_cold(A.eos, ok ? pr[0] : 1.0, Pc, ec, dP);
+    bool fix = false;
+    if (ok && pr[1] < ec) {
+      pr[1] = ec;
+      fix = true;
+    }
+    const double fl = floor_at(A, i, j, k);
+    if (!ok || pr[0] < fl) {
+      double Pf, ef, dPf;
+      eos_cold(A.eos, fl, Pf, ef, dPf);
+      pr[0] = fl;
+      pr[1] = ef;
+      pr[2] = pr[3] = pr[4] = 0.0;
+      fix = true;
+    }
+    double h, P;
+    if (fix) {
+      prim2con(A.eos, m, pr, c, w, h, P);
+#pragma unroll
+      for (int f = 0; f < NM; ++f) cons[f * fs + q] = c[f];
+    } else {
+      P = eos_pressure(A.eos, pr[0], pr[1]);
+      h = 1.0 + pr[1] + P / pr[0];
+    }
+#pragma unroll
+    for (int f = 0; f < NM; ++f) prim[f * fs + q] = pr[f];
+    prim[NM * fs + q] = w;
+    if (A.coupled) {
+      // rho_ADM = rho_H, S_i = J_i, S_ij = rho h u_i u_j + P gamma_ij and the
+      // Z4c matter terms (Khat, Theta, At_ij, Gamt^i)
+      const double rho = pr[0];
+      const double ul[3] = {pr[2], pr[3], pr[4]};
+      const double E = rho * h * w * w - P;
+      double Sl[3], Sll[6], Str = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Sl[a] = rho * h * w * ul[a];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b) Sll[S2(a, b)] = rho * h * ul[a] * ul[b] + P * m.g[S2(a, b)];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Str += m.gu[S2(a, b)] * Sll[S2(a, b)];
+      const double W = u[F_W * fs + q];
+      const double al = m.al;
+      zs[0 * fs + q] = 4.0 * PI * al * (Str + E);
+      zs[1 * fs + q] = -8.0 * PI * al * E;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) zs[(2 + a) * fs + q] = -8.0 * PI * al * W * W * (Sll[a] - m.g[a] * Str / 3.0);
+      // gt^ij = gamma^ij / W^2
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        zs[(8 + a) * fs + q] = -16.0 * PI * al *
+                               (m.gu[S2(a, 0)] * Sl[0] + m.gu[S2(a, 1)] * Sl[1] + m.gu[S2(a, 2)] * Sl[2]) / (W * W);
+    }
+  }
+}
+
+// ghost cells of the NMP primitive arrays: nearest active cell (outflow) or
+// the periodic image
+__global__ void __launch_bounds__(128) matter_ghost_kernel(MatterArgs A) {
+  const long long ntot = (long long)A.NX * A.NY * A.NZ;
+  double* __restrict__ prim = A.P->mprim;
+  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < ntot;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(id % A.NX), J = (int)((id / A.NX) % A.NY), K = (int)(id / ((long long)A.NX * A.NY));
+    const int c[3] = {I, J, K}, N[3] = {A.n[0], A.n[1], A.n[2]};
+    bool ghost = false;
+    int s[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int a = c[d] - GH;  // active index
+      ghost |= (a < 0 || a >= N[d]);
+      s[d] = A.periodic ? ((a % N[d]) + N[d]) % N[d] : (a < 0 ? 0 : (a >= N[d] ? N[d] - 1 : a));
+    }
+    if (!ghost) continue;
+    const long long q = I + J * A.sy + K * A.sz;
+    const long long qs = (s[0] + GH) + (s[1] + GH) * A.sy + (s[2] + GH) * A.sz;
+#pragma unroll
+    for (int f = 0; f < NMP; ++f) prim[f * A.fs + q] = prim[f * A.fs + qs];
+  }
+}
+
+__device__ __forceinline__ double minmod3(double a, double b, double c) {
+  const bool pos = a > 0.0 && b > 0.0 && c > 0.0, neg = a < 0.0 && b < 0.0 && c < 0.0;
+  if (!(pos || neg)) return 0.0;
+  const double m = fmin(fmin(fabs(a), fabs(b)), fabs(c));
+  return pos ? m : -m;
+}
+
+// PPM states at the face between cells 2 and 3 of v[0..5] (cells m-2 .. m+3)
+__device__ __forceinline__ void ppm_face(const double v[6], double& left, double& right) {
+  double sl[4];  // limited slopes at cells 1..4
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double a0 = v[i], a1 = v[i + 1], a2 = v[i + 2];
+    sl[i] = minmod3(0.5 * (a2 - a0), PPM_B * (a2 - a1), PPM_B * (a1 - a0));
+  }
+  // face values between cells (1,2), (2,3), (3,4)
+  double af[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) af[i] = 0.5 * (v[i + 1] + v[i + 2]) - (sl[i + 1] - sl[i]) / 6.0;
+  // cell 2 (aL = af[0], aR = af[1]) and cell 3 (aL = af[1], aR = af[2]), monotonised
+#pragma unroll
+  for (int cidx = 0; cidx < 2; ++cidx) {
+    const double c = v[2 + cidx];
+    double aL = af[cidx], aR = af[cidx + 1];
+    if ((aR - c) * (c - aL) <= 0.0) {
+      aL = c;
+      aR = c;
+    }
+    const double d = aR - aL, mid = c - 0.5 * (aL + aR);
+    const bool ol = d * mid > d * d / 6.0;
+    if (ol) aL = 3.0 * c - 2.0 * aR;
+    if (!ol && -d * d / 6.0 > d * mid) aR = 3.0 * c - 2.0 * aL;
+    if (cidx == 0)
+      left = aR;
+    else
+      right = aL;
+  }
+}
+
+// conserved variables, flux along d and characteristic speeds of a state
+template <int d>
+__device__ __forceinline__ void phys_flux(const DevEOS& e, const Met& m, const double pr[NM], double U[NM],
+                                          double F[NM], double& lp, double& lm) {
+  double w, h, P;
+  prim2con(e, m, pr, U, w, h, P);
+  const double ul[3] = {pr[2], pr[3], pr[4]};
+  double uu[3];
+  raise3(m.gu, ul, uu);
+  const double V = m.al * uu[d] / w - m.be[d];
+#pragma unroll
+  for (int f = 0; f < NM; ++f) F[f] = U[f] * V;
+  F[1 + d] += m.al * m.sg * P;
+  F[4] += m.sg * P * (V + m.be[d]);
+  const double vd = uu[d] / w;
+  const double v2 = 1.0 - 1.0 / (w * w);
+  const double cs2 = eos_cs2(e, pr[0], pr[1]);
+  const double gdd = m.gu[S2(d, d)];
+  const double root = sqrt(fmax(cs2 * (1.0 - v2) * (gdd * (1.0 - v2 * cs2) - vd * vd * (1.0 - cs2)), 0.0));
+  const double pre = m.al / (1.0 - v2 * cs2);
+  lp = pre * (vd * (1.0 - cs2) + root) - m.be[d];
+  lm = pre * (vd * (1.0 - cs2) - root) - m.be[d];
+}
+
+// one thread per face: faces m+1/2 along dir for m = 2 .. n+2 (array index),
+// the other axes over active cells; flux stored at cell m
+template <int dir>
+__global__ void __launch_bounds__(128) matter_flux_kernel(MatterArgs A) {
+  constexpr int a1 = (dir + 1) % 3, a2 = (dir + 2) % 3;
+  const long long nf = (long long)(A.n[dir] + 1) * A.n[a1] * A.n[a2];
+  const int ring = A.lev->ring;
+  const double* __restrict__ u = z4c_stage_state(A, ring);
+  const double* __restrict__ prim = A.P->mprim;
+  double* __restrict__ flux = A.P->mflux + (long long)dir * NM * A.fs;
+  const long long sd = dir == 0 ? 1 : (dir == 1 ? A.sy : A.sz);
+  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < nf;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(id % (A.n[dir] + 1)) + 2;  // array index of the cell left of the face
+    const long long r = id / (A.n[dir] + 1);
+    const int c1 = (int)(r % A.n[a1]) + GH, c2 = (int)(r / A.n[a1]) + GH;
+    const int cx = dir == 0 ? m : (a1 == 0 ? c1 : c2);
+    const int cy = dir == 1 ? m : (a1 == 1 ? c1 : c2);
+    const int cz = dir == 2 ? m : (a1 == 2 ? c1 : c2);
+    const long long q = cx + cy * A.sy + cz * A.sz;
+    // face metric: (-1, 9, 9, -1)/16 of alpha, beta, gamma_ij from cells m-1 .. m+2
+    Met mf;
+    {
+      double vals[10];
+      for (int t = 0; t < 10; ++t) vals[t] = 0.0;
+      const double wts[4] = {-1.0 / 16.0, 9.0 / 16.0, 9.0 / 16.0, -1.0 / 16.0};
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        Met mc;
+        metric_at(u, q + (o - 1) * sd, A.fs, mc, nullptr);
+        vals[0] += wts[o] * mc.al;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) vals[1 + b] += wts[o] * mc.be[b];
+#pragma unroll
+        for (int b = 0; b < 6; ++b) vals[4 + b] += wts[o] * mc.g[b];
+      }
+      mf.al = vals[0];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) mf.be[b] = vals[1 + b];
+#pragma unroll
+      for (int b = 0; b < 6; ++b) mf.g[b] = vals[4 + b];
+      mf.sg = sqrt(inv_sym(mf.g, mf.gu));
+    }
+    double pl[NM], pr[NM];
+#pragma unroll
+    for (int f = 0; f < NM; ++f) {
+      double v[6];
+#pragma unroll
+      for (int o = 0; o < 6; ++o) v[o] = prim[f * A.fs + q + (o - 2) * sd];
+      ppm_face(v, pl[f], pr[f]);
+    }
+    double UL[NM], FL[NM], UR[NM], FR[NM], lpl, lml, lpr, lmr;
+    phys_flux<dir>(A.eos, mf, pl, UL, FL, lpl, lml);
+    phys_flux<dir>(A.eos, mf, pr, UR, FR, lpr, lmr);
+    const double ap = fmax(0.0, fmax(lpl, lpr)), am = fmin(0.0, fmin(lml, lmr));
+    const double den = (ap - am > 0.0) ? ap - am : 1.0;
+#pragma unroll
+    for (int f = 0; f < NM; ++f) flux[f * A.fs + q] = (ap * FL[f] - am * FR[f] + ap * am * (UR[f] - UL[f])) / den;
+  }
+}
+
+// 4th-order centred first derivative of a metric quantity computed by `get`
+// at the cells q + k st (k = -2..2)
+template <class G>
+__device__ __forceinline__ double d1c(const G& get, long long q, long long st, double ih12) {
+  return (8.0 * (get(q + st) - get(q - st)) - (get(q + 2 * st) - get(q - 2 * st))) * ih12;
+}
+
+__global__ void __launch_bounds__(128) matter_update_kernel(MatterArgs A) {
+  const long long nact = (long long)A.n[0] * A.n[1] * A.n[2];
+  const int ring = A.lev->ring;
+  const int s = A.stage;
+  const double* __restrict__ u = z4c_stage_state(A, ring);
+  const double* __restrict__ prim = A.P->mprim;
+  const double* __restrict__ flux = A.P->mflux;
+  const long long fs = A.fs;
+  const long long st[3] = {1, A.sy, A.sz};
+  const double ih = 1.0 / A.dx, ih12 = 1.0 / (12.0 * A.dx);
+  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < nact;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % A.n[0]);
+    const int j = (int)((id / A.n[0]) % A.n[1]);
+    const int k = (int)(id / ((long long)A.n[0] * A.n[1]));
+    const long long q = (i + GH) + (j + GH) * A.sy + (k + GH) * A.sz;
+    double rhs[NM];
+#pragma unroll
+    for (int f = 0; f < NM; ++f) rhs[f] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double* Fd = flux + (long long)d * NM * fs;
+#pragma unroll
+      for (int f = 0; f < NM; ++f) rhs[f] -= (Fd[f * fs + q] - Fd[f * fs + q - st[d]]) * ih;
+    }
+    // sources at the cell
+    Met m;
+    double K_ll[6];
+    metric_at(u, q, fs, m, K_ll);
+    double pr[NM];
+#pragma unroll
+    for (int f = 0; f < NM; ++f) pr[f] = prim[f * fs + q];
+    double U[NM], w, h, P;
+    prim2con(A.eos, m, pr, U, w, h, P);
+    const double rho = pr[0];
+    const double ul[3] = {pr[2], pr[3], pr[4]};
+    double uu[3];
+    raise3(m.gu, ul, uu);
+    const double E = rho * h * w * w - P;
+    double J[3], Ju[3], Suu[6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) J[a] = rho * h * w * ul[a];
+    raise3(m.gu, J, Ju);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b) Suu[S2(a, b)] = rho * h * uu[a] * uu[b] + P * m.gu[S2(a, b)];
+    double dal[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      dal[d] = d1c([&](long long p) { return __ldg(u + F_ALP * fs + p); }, q, st[d], ih12);
+      double sgd = 0.0;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const double dg = d1c(
+            [&](long long p) {
+              const double Wp = __ldg(u + F_W * fs + p);
+              return __ldg(u + (F_GXX + a) * fs + p) / (Wp * Wp);
+            },
+            q, st[d], ih12);
+        sgd += ((a == 0 || a == 3 || a == 5) ? 1.0 : 2.0) * Suu[a] * dg;
+      }
+      double jdb = 0.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        jdb += J[b] * d1c([&](long long p) { return __ldg(u + (F_BETX + b) * fs + p); }, q, st[d], ih12);
+      rhs[1 + d] += m.sg * (-E * dal[d] + jdb + 0.5 * m.al * sgd);
+    }
+    double SK = 0.0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) SK += ((a == 0 || a == 3 || a == 5) ? 1.0 : 2.0) * Suu[a] * K_ll[a];
+    rhs[4] += m.sg * (m.al * SK - (Ju[0] * dal[0] + Ju[1] * dal[1] + Ju[2] * dal[2]));
+    if (s == 0) {
+#pragma unroll
+      for (int f = 0; f < NM; ++f) A.out[f * fs + q] = rhs[f];
+      continue;
+    }
+    // RK4 stage update (the spacetime's weights)
+    double* __restrict__ un = A.P->mcons[ring];
+    double* __restrict__ y = A.P->mcons[B_Y];
+    double* __restrict__ out = A.P->mcons[stage_out_slot(s, ring)];
+    const double bw = (s == 1 || s == 4) ? (1.0 / 6.0) : (1.0 / 3.0);
+    const double cw = (s == 3) ? 1.0 : 0.5;
+    bool bad = false;
+#pragma unroll
+    for (int f = 0; f < NM; ++f) {
+      const long long o = f * fs + q;
+      double v;
+      if (s == 4) {
+        v = y[o] + bw * A.dt * rhs[f];
+      } else {
+        const double a = un[o];
+        y[o] = (s == 1 ? a : y[o]) + bw * A.dt * rhs[f];
+        v = a + cw * A.dt * rhs[f];
+      }
+      out[o] = v;
+      bad |= !isfinite(v);
+    }
+    if (bad) atomicOr(A.err, (unsigned)ERR_NONFINITE);
+  }
+}
+
+__global__ void __launch_bounds__(128) matter_prim2con_kernel(MatterArgs A) {
+  const long long ntot = (long long)A.NX * A.NY * A.NZ;
+  const int ring = A.lev->ring;
+  const double* __restrict__ u = A.P->buf[ring];
+  double* __restrict__ cons = A.P->mcons[ring];
+  double* __restrict__ prim = A.P->mprim;
+  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < ntot;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(id % A.NX), J = (int)((id / A.NX) % A.NY), K = (int)(id / ((long long)A.NX * A.NY));
+    const long long q = I + J * A.sy + K * A.sz;
+    Met m;
+    metric_at(u, q, A.fs, m, nullptr);
+    double pr[NM], c[NM], w, h, P;
+#pragma unroll
+    for (int f = 0; f < NM; ++f) pr[f] = prim[f * A.fs + q];
+    prim2con(A.eos, m, pr, c, w, h, P);
+#pragma unroll
+    for (int f = 0; f < NM; ++f) cons[f * A.fs + q] = c[f];
+    prim[NM * A.fs + q] = w;
+  }
+}
+
+int blocks_for(long long n) {
+  long long b = (n + 127) / 128;
+  return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+}  // namespace
+
+void launch_matter_prep(const MatterArgs& a, cudaStream_t st) {
+  matter_prep_kernel<<<blocks_for((long long)a.n[0] * a.n[1] * a.n[2]), 128, 0, st>>>(a);
+}
+void launch_matter_ghosts(const MatterArgs& a, cudaStream_t st) {
+  matter_ghost_kernel<<<blocks_for((long long)a.NX * a.NY * a.NZ), 128, 0, st>>>(a);
+}
+void launch_matter_flux(const MatterArgs& a, int dir, cudaStream_t st) {
+  const int a1 = (dir + 1) % 3, a2 = (dir + 2) % 3;
+  const int nb = blocks_for((long long)(a.n[dir] + 1) * a.n[a1] * a.n[a2]);
+  if (dir == 0)
+    matter_flux_kernel<0><<<nb, 128, 0, st>>>(a);
+  else if (dir == 1)
+    matter_flux_kernel<1><<<nb, 128, 0, st>>>(a);
+  else
+    matter_flux_kernel<2><<<nb, 128, 0, st>>>(a);
+}
+void launch_matter_update(const MatterArgs& a, cudaStream_t st) {
+  matter_update_kernel<<<blocks_for((long long)a.n[0] * a.n[1] * a.n[2]), 128, 0, st>>>(a);
+}
+void launch_matter_prim2con(const MatterArgs& a, cudaStream_t st) {
+  matter_prim2con_kernel<<<blocks_for((long long)a.NX * a.NY * a.NZ), 128, 0, st>>>(a);
+}
+
+}  // namespace sacrak

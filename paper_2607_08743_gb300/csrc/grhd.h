@@ -1,0 +1,55 @@
+// Launch interface of the GR hydrodynamics (matter) kernels (grhd.cu).
+//
+// The fluid of Sec. 2.1.2 of the SACRA-K paper: primitives (rho, eps, u_i)
+// and the densitised conserved variables sqrt(gamma) (D, J_i, rho_H), with
+// the hybrid EOS (piecewise polytrope + thermal part), evolved with the
+// spacetime by the same RK4 stages (Sec. 2.2): PPM (steep minmod b = 3) +
+// HLLE face fluxes, geometric sources, Newton-Raphson recovery on the
+// Lorentz factor w, atmosphere floor.  FP64 throughout.
+#pragma once
+#include "sacrak_dev.cuh"
+
+namespace sacrak {
+
+constexpr int NM = 5;        // rho, eps, u_x, u_y, u_z  /  D^, J^_x, J^_y, J^_z, E^
+constexpr int NMP = 6;       // primitive arrays: the five plus the Lorentz factor w
+constexpr int NZSRC = 11;    // matter terms of the Z4c RHS: Khat, Theta, At (6), Gamt (3)
+constexpr int MAX_PIECES = 4;
+
+struct DevEOS {
+  int n;                      // pieces of the cold polytrope
+  double K[MAX_PIECES], G[MAX_PIECES], a[MAX_PIECES];
+  double rb[MAX_PIECES - 1];  // density boundaries between pieces
+  double gth;                 // Gamma_th
+};
+
+struct MatterArgs {
+  const DevPatch* P;          // device pointer to the patch
+  const DevLevel* lev;        // its level (ring slot on the device)
+  int n[3], NX, NY, NZ;
+  long long sy, sz, fs;
+  double dx, origin[3];
+  DevEOS eos;
+  double rho_atm, r_atm;      // floor f_atm rho_max inside r_atm, r^-3 outside
+  int periodic;               // ghost cells: 0 outflow (zero gradient), 1 periodic
+  int stage;                  // 1..4 RK stage; 5: the new level after stage 4; 0: current level
+  int coupled;                // write the Z4c matter terms (spacetime evolved with the fluid)
+  double dt;
+  double* out;                // update kernel with stage 0: d_t of the conserved variables
+  unsigned* err;
+};
+
+// Primitive recovery of the stage's conserved state (active cells) with the
+// atmosphere, the Lorentz factor of the previous recovery as the Newton
+// guess, and (coupled) the Z4c matter terms of the recovered fluid.
+void launch_matter_prep(const MatterArgs& a, cudaStream_t st);
+// ghost cells of the primitive arrays
+void launch_matter_ghosts(const MatterArgs& a, cudaStream_t st);
+// HLLE face fluxes along dir (0, 1, 2) from the PPM states
+void launch_matter_flux(const MatterArgs& a, int dir, cudaStream_t st);
+// flux divergence + sources: RK4 stage update (stage 1..4) or d_t (stage 0)
+void launch_matter_update(const MatterArgs& a, cudaStream_t st);
+// conserved variables of the primitives (after an upload of primitives)
+void launch_matter_prim2con(const MatterArgs& a, cudaStream_t st);
+
+}  // namespace sacrak

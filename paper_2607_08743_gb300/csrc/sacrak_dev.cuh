@@ -3,9 +3,11 @@
 //
 // Memory layout (HBM): every patch owns six state copies (three time levels,
 // the RK4 accumulator y and two stage buffers).  A state copy is
-// double[25][NZ][NY][px]: x fastest, the row pitch px rounded up to 8 doubles
-// (64 B) so that every row starts on a 64-byte boundary, and every field
-// padded to a multiple of 32 doubles (256 B).  Ghost width is 3 on every side.
+// double[25][NZ][NY][px]: x fastest, the row pitch px = NX + 1 rounded up to
+// 8 doubles (64 B), every copy starting one element past a 256-byte
+// boundary, so that active cell i of a row sits at element i + 4 of its
+// 64-byte aligned row and the cells (2m, 2m+1) form one 16-byte vector.
+// Ghost width is 3 on every side.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -49,6 +51,14 @@ struct DevPatch {
   float2* hl[3];
   float2* sa;
   float2* sb;
+  // matter (FP64 one-level grids with a fluid): the densitised conserved
+  // variables in the same slots as buf (5 fields each), the primitives and
+  // the Lorentz factor (6 fields), the face fluxes along x, y, z (15) and the
+  // matter terms of the Z4c right-hand side (11); null without a fluid
+  double* mcons[NBUF];
+  double* mprim;
+  double* mflux;
+  double* mzsrc;
 };
 
 struct DevLevel {
@@ -66,7 +76,8 @@ struct Tile {
 
 struct DevParams {
   double kappa1, kappa2, eta, sigma_ko, w_floor;
-  int lapse, shift, lapse_uses_khat, pad_;
+  int lapse, shift, lapse_uses_khat;
+  int matter;  // 1: add the fluid's terms (DevPatch::mzsrc) to the Z4c right-hand side
 };
 
 // error flags written by kernels (bitmask), read by the host after a sync

@@ -410,6 +410,21 @@ __global__ void __launch_bounds__(128) z4c_stage_fp64_kernel(StageArgs A) {
   const double* __restrict__ u = P->buf[MODE ? ring : stage_in_slot(s, ring)];
   double r[NF];
   z4c_rhs_point(u, q, sy, sz, fs, P->dx, A.prm, r);
+  if (A.prm.matter) {
+    // the fluid's terms (Sec. 2.1.2), formed by the matter recovery kernel from
+    // this stage's state: Khat, Theta, At_ij, Gamt^i (and B^i through Gamt^i)
+    const double* __restrict__ zs = P->mzsrc;
+    r[F_KH] += zs[q];
+    r[F_TH] += zs[fs + q];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) r[F_AXX + a] += zs[(2 + a) * fs + q];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double g = zs[(8 + a) * fs + q];
+      r[F_GAMX + a] += g;
+      if (A.prm.shift == 0) r[F_BX + a] += g;
+    }
+  }
   if (MODE == 1) {
     double* out = P->buf[B_S1];
 #pragma unroll
