@@ -205,13 +205,14 @@ def main():
     ap.add_argument("--gw-steps", type=int, default=1000,
                     help="gauge-wave: RK4 steps on the coarsest grid; robust-stability: steps per grid")
     ap.add_argument("--case", default="amr7",
-                    choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep",
+                    choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep", "tov",
                              "amr7-zsym", "adm", "amr7-moving", "psi4"],
                     help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
                          "mixed-error: the 7-level hierarchy in FP64 and mixed precision side by side")
     ap.add_argument("--coarse-steps", type=int, default=64, help="mixed-error: coarse steps")
     ap.add_argument("--error-kernels", default="", help="mixed-error: stage kernels to compare, e.g. 6,0")
     ap.add_argument("--adm-steps", type=int, default=2, help="adm: coarse steps evolved before the integrals")
+    ap.add_argument("--tov-n", type=int, default=128, help="tov: cells per axis of the patch on [-16, 16]^3")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -258,6 +259,9 @@ def main():
         return
     if args.case == "psi4":
         psi4_case(torch, sk, args)
+        return
+    if args.case == "tov":
+        tov_case(torch, sk, args)
         return
 
     h = hierarchy()
@@ -773,6 +777,59 @@ def sweep_case(torch, sk, args):
         g.close()
         del g
         torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
+def tov_case(torch, sk, args):
+    """The coupled RK4 step of spacetime and fluid (Sec. 2.1.2, 2.2) for a TOV
+    star (cold Gamma = 2 polytrope, K = 100, rho_c = 1.28e-3, M = 1.40,
+    Gamma_th = 1.8) on one FP64 patch of n^3 cells over [-16, 16]^3: 1+log
+    slicing and Gamma driver, Sommerfeld ghosts for the spacetime, outflow
+    ghosts for the fluid, atmosphere 1e-12 rho_c.  Each step is one captured
+    graph replay (the RK4 step and the level bookkeeping).  Reported: zone
+    updates/s of the coupled step and of the spacetime alone on the same
+    patch, and the drift of the central density over the timed steps."""
+    import initial_data as idd
+    from initial_data.tov import TOV, tov_patch_data
+    n = args.tov_n
+    p = idd.centred_patch(n, 32.0 / n)
+    star = TOV()
+    rho_atm, r_atm = 1e-12 * 1.28e-3, 8 * 32.0
+    u, prim = tov_patch_data(p, star, rho_atm)
+    c = p.g + n // 2
+    out = {"case": "tov", "n": n, "dx": p.dx, "courant": args.courant, "zones": p.active_points,
+           "star": {"M": star.M, "R_areal": star.R, "R_isotropic": star.Rbar}, "runs": {}}
+    for name, matter in (("spacetime+fluid", 1), ("spacetime", 0)):
+        g = sk.Grid(1, p.dx, [p], sk.Params(courant=args.courant, matter=matter), stream=torch.cuda.Stream())
+        if matter:
+            g.set_eos(star.K, [star.G], (), 1.8)
+            g.set_atmosphere(rho_atm, r_atm)
+        g.upload_fields(0, u)
+        if matter:
+            g.upload_matter(0, prim)
+        for _ in range(args.warmup):
+            g.level_step(0)
+        rho0 = float(g.download_matter(0)[0, c, c, c]) if matter else None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(g.stream)
+        for _ in range(args.steps):
+            g.level_step(0)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        run = {"ms_per_rk4_step": ms, "zone_updates_per_s": p.active_points / (ms * 1e-3),
+               "constraints": list(map(float, g.constraints(0)))}
+        if matter:
+            rho1 = float(g.download_matter(0)[0, c, c, c])
+            run["central_density_drift"] = (rho1 - rho0) / rho0
+        out["runs"][name] = run
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    r = out["runs"]
+    out["fluid_ms_per_step"] = r["spacetime+fluid"]["ms_per_rk4_step"] - r["spacetime"]["ms_per_rk4_step"]
     print(json.dumps(out), flush=True)
 
 

@@ -1,6 +1,6 @@
-"""Static spherical star (Tolman-Oppenheimer-Volkoff) for the matter pins,
-computed independently of the oracle with scipy: the TOV equations in the
-areal radius r for a cold polytrope P = K rho^Gamma, eps = K rho^(Gamma-1) /
+"""Static spherical star (Tolman-Oppenheimer-Volkoff): initial data for the
+fluid tests and the benchmark, computed with scipy (it holds none of the
+evolution's arithmetic): the TOV equations in the areal radius r for a cold polytrope P = K rho^Gamma, eps = K rho^(Gamma-1) /
 (Gamma-1), together with d ln rbar / dr = 1 / (r sqrt(1 - 2m/r)) for the
 isotropic radius rbar, matched at the surface R to the exterior
 Schwarzschild solution in isotropic coordinates (rbar(R) = (sqrt(R^2 - 2MR)
@@ -63,3 +63,21 @@ class TOV:
         ha = self.M / (2.0 * np.maximum(rbar, 1e-12))
         alpha = np.where(inside, np.exp(self._nu(rc)), (1.0 - ha) / (1.0 + ha))
         return rho, psi, alpha
+
+
+def tov_patch_data(p, star=None, rho_floor=None):
+    """Z4c fields (isotropic coordinates: W = psi^-2, conformally flat, the
+    static lapse, zero shift and extrinsic curvature) and fluid primitives
+    (rho, eps on the cold polytrope, at rest) of the star on patch p; rho is
+    at least rho_floor (an array or number) outside the star."""
+    import initial_data as idd
+    star = star or TOV()
+    z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
+    rho, psi, al = star.fields(np.sqrt(x * x + y * y + z * z))
+    u = idd.minkowski(p)
+    u[0] = psi ** -2
+    u[18] = al
+    prim = np.zeros((5,) + p.shape[1:])
+    prim[0] = np.maximum(rho, rho_floor if rho_floor is not None else 0.0)
+    prim[1] = star.K * prim[0] ** (star.G - 1.0) / (star.G - 1.0)
+    return u, prim

@@ -212,7 +212,8 @@ def con2prim(cons, m, eos, w_guess=None, tol=1e-15, maxit=60):
         lo = np.where(f < 0, np.maximum(lo, w), lo)
         hi = np.where(f > 0, np.minimum(hi, w), hi)
         wn = w - f / np.where(fp != 0, fp, 1.0)
-        out = ~((wn > lo) & (wn < hi)) | ~np.isfinite(wn)
+        # the bracket is closed: w = 1 (a fluid at rest) is a root
+        out = ~((wn >= lo) & (wn <= hi)) | ~np.isfinite(wn)
         wn = np.where(out, 0.5 * (lo + hi), wn)
         done = np.abs(wn - w) <= tol * wn
         w = wn

@@ -55,6 +55,17 @@ __device__ __forceinline__ double inv_sym(const double g[6], double gu[6]) {
   return det;
 }
 
+// alpha, beta^i, gamma_ij at cell q (what the face interpolation needs)
+__device__ __forceinline__ void metric_ll_at(const double* __restrict__ u, long long q, long long fs, double v[10]) {
+  const double W = __ldg(u + F_W * fs + q);
+  const double iW2 = 1.0 / (W * W);
+  v[0] = __ldg(u + F_ALP * fs + q);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) v[1 + d] = __ldg(u + (F_BETX + d) * fs + q);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) v[4 + a] = __ldg(u + (F_GXX + a) * fs + q) * iW2;
+}
+
 // 3+1 metric at cell q of the Z4c state u (optionally K_ij)
 __device__ __forceinline__ void metric_at(const double* __restrict__ u, long long q, long long fs, Met& m,
                                           double* K_ll) {
@@ -87,11 +98,21 @@ __device__ __forceinline__ void raise3(const double gu[6], const double v[3], do
 
 // ------------------------------------------------------------------ EOS
 
+// rho^x for the polytrope exponent x = Gamma - 1: the exponents 1, 1/2, 3/2
+// and 2 without pow (the same values to rounding)
+__device__ __forceinline__ double pow_gm1(double rho, double x) {
+  if (x == 1.0) return rho;
+  if (x == 0.5) return sqrt(rho);
+  if (x == 1.5) return rho * sqrt(rho);
+  if (x == 2.0) return rho * rho;
+  return pow(rho, x);
+}
+
 __device__ __forceinline__ void eos_cold(const DevEOS& e, double rho, double& P, double& eps, double& dP) {
   int i = 0;
   for (int b = 0; b < e.n - 1; ++b) i += rho >= e.rb[b] ? 1 : 0;
   const double K = e.K[i], G = e.G[i];
-  const double rg = pow(rho, G - 1.0);
+  const double rg = pow_gm1(rho, G - 1.0);
   P = K * rg * rho;
   eps = e.a[i] + K * rg / (G - 1.0);
   dP = G * K * rg;
@@ -101,17 +122,6 @@ __device__ __forceinline__ double eos_pressure(const DevEOS& e, double rho, doub
   double Pc, ec, dP;
   eos_cold(e, rho, Pc, ec, dP);
   return Pc + (e.gth - 1.0) * rho * (eps - ec);
-}
-
-__device__ __forceinline__ double eos_cs2(const DevEOS& e, double rho, double eps) {
-  double Pc, ec, dPc;
-  eos_cold(e, rho, Pc, ec, dPc);
-  const double g = e.gth - 1.0;
-  const double P = Pc + g * rho * (eps - ec);
-  const double chi = dPc + g * (eps - ec) - g * Pc / rho;
-  const double kap = g * rho;
-  const double h = 1.0 + eps + P / rho;
-  return (chi + P / (rho * rho) * kap) / h;
 }
 
 // ------------------------------------------------------------------ prim <-> con
@@ -143,8 +153,9 @@ __device__ __forceinline__ void pressure_of_w(const DevEOS& e, double w, double 
   // d eps_cold / d rho = P_cold / rho^2, d rho / d w = -D / w^2
   const double dN = -D * iw2 * dPc + g * (-2.0 * E * iw2 * iw + D * iw2 * (1.0 + ec) + Pc * iw);
   const double dQ = 2.0 * g * iw2 * iw;
-  P = N / Q;
-  dPdw = (dN * Q - N * dQ) / (Q * Q);
+  const double iQ = 1.0 / Q;
+  P = N * iQ;
+  dPdw = (dN - P * dQ) * iQ;
 }
 
 // Newton-Raphson on w within the bracket [lo, hi] (bisection where a step
@@ -164,14 +175,17 @@ __device__ bool con2prim(const DevEOS& e, const Met& m, const double c[NM], doub
     pressure_of_w(e, w, D, E, P, dP);
     const double X = E + P;
     const double q = X * X - S2;
-    const double R = sqrt(fmax(q, 1e-300));
-    const double f = w - X / R;
+    const double iR = 1.0 / sqrt(fmax(q, 1e-300));
+    const double f = w - X * iR;
     if (f < 0.0) lo = fmax(lo, w);
     if (f > 0.0) hi = fmin(hi, w);
-    const double fp = 1.0 + dP * S2 / (R * R * R);
+    const double fp = 1.0 + dP * S2 * (iR * iR * iR);
     double wn = w - f / (fp != 0.0 ? fp : 1.0);
-    if (!(wn > lo && wn < hi)) wn = 0.5 * (lo + hi);
-    const bool done = fabs(wn - w) <= 1e-15 * wn;
+    const bool newton = wn >= lo && wn <= hi;  // closed: w = 1 (at rest) is a root
+    if (!newton) wn = 0.5 * (lo + hi);
+    // quadratic convergence: a Newton step below 1e-10 w leaves an iterate
+    // accurate to rounding (a bisection step never ends the iteration)
+    const bool done = newton && fabs(wn - w) <= 1e-10 * wn;
     w = wn;
     if (done) break;
   }
@@ -332,7 +346,7 @@ __device__ __forceinline__ void ppm_face(const double v[6], double& left, double
   // face values between cells (1,2), (2,3), (3,4)
   double af[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) af[i] = 0.5 * (v[i + 1] + v[i + 2]) - (sl[i + 1] - sl[i]) / 6.0;
+  for (int i = 0; i < 3; ++i) af[i] = 0.5 * (v[i + 1] + v[i + 2]) - (sl[i + 1] - sl[i]) * (1.0 / 6.0);
   // cell 2 (aL = af[0], aR = af[1]) and cell 3 (aL = af[1], aR = af[2]), monotonised
 #pragma unroll
   for (int cidx = 0; cidx < 2; ++cidx) {
@@ -343,9 +357,10 @@ __device__ __forceinline__ void ppm_face(const double v[6], double& left, double
       aR = c;
     }
     const double d = aR - aL, mid = c - 0.5 * (aL + aR);
-    const bool ol = d * mid > d * d / 6.0;
+    const double d6 = d * d * (1.0 / 6.0);
+    const bool ol = d * mid > d6;
     if (ol) aL = 3.0 * c - 2.0 * aR;
-    if (!ol && -d * d / 6.0 > d * mid) aR = 3.0 * c - 2.0 * aL;
+    if (!ol && -d6 > d * mid) aR = 3.0 * c - 2.0 * aL;
     if (cidx == 0)
       left = aR;
     else
@@ -357,8 +372,23 @@ __device__ __forceinline__ void ppm_face(const double v[6], double& left, double
 template <int d>
 __device__ __forceinline__ void phys_flux(const DevEOS& e, const Met& m, const double pr[NM], double U[NM],
                                           double F[NM], double& lp, double& lm) {
-  double w, h, P;
-  prim2con(e, m, pr, U, w, h, P);
+  // one cold-EOS evaluation for the pressure and the sound speed
+  double Pc, ec, dPc;
+  eos_cold(e, pr[0], Pc, ec, dPc);
+  const double P = Pc + (e.gth - 1.0) * pr[0] * (pr[1] - ec);
+  const double irho = 1.0 / pr[0];
+  const double h = 1.0 + pr[1] + P * irho;
+  double w;
+  {
+    const double ul[3] = {pr[2], pr[3], pr[4]};
+    double uu[3];
+    raise3(m.gu, ul, uu);
+    w = sqrt(1.0 + ul[0] * uu[0] + ul[1] * uu[1] + ul[2] * uu[2]);
+    U[0] = m.sg * pr[0] * w;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) U[1 + i] = m.sg * pr[0] * h * w * ul[i];
+    U[4] = m.sg * (pr[0] * h * w * w - P);
+  }
   const double ul[3] = {pr[2], pr[3], pr[4]};
   double uu[3];
   raise3(m.gu, ul, uu);
@@ -369,7 +399,9 @@ __device__ __forceinline__ void phys_flux(const DevEOS& e, const Met& m, const d
   F[4] += m.sg * P * (V + m.be[d]);
   const double vd = uu[d] / w;
   const double v2 = 1.0 - 1.0 / (w * w);
-  const double cs2 = eos_cs2(e, pr[0], pr[1]);
+  // sound speed: (dP/drho|_eps + P/rho^2 dP/deps|_rho) / h
+  const double g1 = e.gth - 1.0;
+  const double cs2 = (dPc + g1 * (pr[1] - ec) - g1 * Pc * irho + P * irho * g1) / h;
   const double gdd = m.gu[S2(d, d)];
   const double root = sqrt(fmax(cs2 * (1.0 - v2) * (gdd * (1.0 - v2 * cs2) - vd * vd * (1.0 - cs2)), 0.0));
   const double pre = m.al / (1.0 - v2 * cs2);
@@ -388,14 +420,15 @@ __global__ void __launch_bounds__(128) matter_flux_kernel(MatterArgs A) {
   const double* __restrict__ prim = A.P->mprim;
   double* __restrict__ flux = A.P->mflux + (long long)dir * NM * A.fs;
   const long long sd = dir == 0 ? 1 : (dir == 1 ? A.sy : A.sz);
+  // faces m+1/2 along dir for array index m = 2 .. n+2, active cells along
+  // the other axes; x varies fastest over the threads (coalesced rows)
+  const int ex = A.n[0] + (dir == 0 ? 1 : 0), ey = A.n[1] + (dir == 1 ? 1 : 0);
   for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < nf;
        id += (long long)gridDim.x * blockDim.x) {
-    const int m = (int)(id % (A.n[dir] + 1)) + 2;  // array index of the cell left of the face
-    const long long r = id / (A.n[dir] + 1);
-    const int c1 = (int)(r % A.n[a1]) + GH, c2 = (int)(r / A.n[a1]) + GH;
-    const int cx = dir == 0 ? m : (a1 == 0 ? c1 : c2);
-    const int cy = dir == 1 ? m : (a1 == 1 ? c1 : c2);
-    const int cz = dir == 2 ? m : (a1 == 2 ? c1 : c2);
+    const int ix = (int)(id % ex);
+    const int iy = (int)((id / ex) % ey);
+    const int iz = (int)(id / ((long long)ex * ey));
+    const int cx = ix + (dir == 0 ? 2 : GH), cy = iy + (dir == 1 ? 2 : GH), cz = iz + (dir == 2 ? 2 : GH);
     const long long q = cx + cy * A.sy + cz * A.sz;
     // face metric: (-1, 9, 9, -1)/16 of alpha, beta, gamma_ij from cells m-1 .. m+2
     Met mf;
@@ -405,13 +438,10 @@ __global__ void __launch_bounds__(128) matter_flux_kernel(MatterArgs A) {
       const double wts[4] = {-1.0 / 16.0, 9.0 / 16.0, 9.0 / 16.0, -1.0 / 16.0};
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
-        Met mc;
-        metric_at(u, q + (o - 1) * sd, A.fs, mc, nullptr);
-        vals[0] += wts[o] * mc.al;
+        double vc[10];
+        metric_ll_at(u, q + (o - 1) * sd, A.fs, vc);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) vals[1 + b] += wts[o] * mc.be[b];
-#pragma unroll
-        for (int b = 0; b < 6; ++b) vals[4 + b] += wts[o] * mc.g[b];
+        for (int b = 0; b < 10; ++b) vals[b] += wts[o] * vc[b];
       }
       mf.al = vals[0];
 #pragma unroll
@@ -496,15 +526,21 @@ __global__ void __launch_bounds__(128) matter_update_kernel(MatterArgs A) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       dal[d] = d1c([&](long long p) { return __ldg(u + F_ALP * fs + p); }, q, st[d], ih12);
+      // gamma_jk = gt_jk / W^2 at the four neighbours (one reciprocal each)
+      double iw2[4];
+      const int off[4] = {1, -1, 2, -2};
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const double Wp = __ldg(u + F_W * fs + q + off[o] * st[d]);
+        iw2[o] = 1.0 / (Wp * Wp);
+      }
       double sgd = 0.0;
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
-        const double dg = d1c(
-            [&](long long p) {
-              const double Wp = __ldg(u + F_W * fs + p);
-              return __ldg(u + (F_GXX + a) * fs + p) / (Wp * Wp);
-            },
-            q, st[d], ih12);
+        const double* ga = u + (F_GXX + a) * fs + q;
+        const double gp1 = __ldg(ga + st[d]) * iw2[0], gm1 = __ldg(ga - st[d]) * iw2[1];
+        const double gp2 = __ldg(ga + 2 * st[d]) * iw2[2], gm2 = __ldg(ga - 2 * st[d]) * iw2[3];
+        const double dg = (8.0 * (gp1 - gm1) - (gp2 - gm2)) * ih12;
         sgd += ((a == 0 || a == 3 || a == 5) ? 1.0 : 2.0) * Suu[a] * dg;
       }
       double jdb = 0.0;

@@ -69,7 +69,7 @@ def _generic(n):
 
 
 def _tov(n, half=12.0):
-    from tests.tov import TOV
+    from initial_data.tov import TOV
     star = TOV()
     p = idd.centred_patch(n, 2 * half / n)
     z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")

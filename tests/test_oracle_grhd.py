@@ -263,7 +263,7 @@ def test_density_wave_advection_converges():
 
 @pytest.fixture(scope="module")
 def tov_runs():
-    from tests.tov import TOV
+    from initial_data.tov import TOV
     star = TOV()
     eos = grhd.EOS(K0=star.K, gammas=[star.G], gamma_th=1.8)
     out = {"star": star}
