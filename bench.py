@@ -143,23 +143,59 @@ def launches_per_coarse_step(h) -> int:
     return total
 
 
-def cpu_sample(steps: int = 1):
+def cpu_sample(steps: int = 1, n: int = 96, threads: int = 0):
     """The oracle (as it stands) on a bounded sample of the workload: RK4
-    steps of the level-0 96^3 patch with its Sommerfeld ghosts, all host cores."""
+    steps of the level-0 patch (96^3, or its central n^3) with its Sommerfeld
+    ghosts, on all host cores or on `threads` of them."""
     import initial_data as idd
     import oracle
     h = hierarchy()
-    p = h.levels[0][0]
+    p0 = h.levels[0][0]
+    p = p0 if n == p0.n[0] else idd.centred_patch(n, p0.dx)
     u = idd.punctures(p, h.masses, h.positions)
     prm = oracle.Params()
-    oracle.rk4_step(p, u, 0.25 * p.dx, prm)  # warm (builds the oracle)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        u = oracle.rk4_step(p, u, 0.25 * p.dx, prm)
-    dt = time.perf_counter() - t0
+    all_threads = oracle.num_threads()
+    if threads:
+        oracle.set_num_threads(threads)
+    try:
+        oracle.rk4_step(p, u, 0.25 * p.dx, prm)  # warm (builds the oracle)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            u = oracle.rk4_step(p, u, 0.25 * p.dx, prm)
+        dt = time.perf_counter() - t0
+        used = oracle.num_threads()
+    finally:
+        if threads:
+            oracle.set_num_threads(all_threads)
     zu = steps * p.active_points
-    return zu / dt, oracle.num_threads(), "%d RK4 step(s) of the level-0 96^3 patch (%d zone updates)" % (
-        steps, zu)
+    return zu / dt, used, "%d RK4 step(s) of the level-0 patch%s (%d zone updates)" % (
+        steps, "" if n == p0.n[0] else ", its central %d^3" % n, zu)
+
+
+def cpu_baseline(line_unit):
+    """cpu_baseline of the bench line: the oracle on all host cores (one RK4
+    step of the level-0 96^3 patch) and on one core (its central 48^3)."""
+    v, cores, sample = cpu_sample(1)
+    v1, _, sample1 = cpu_sample(1, n=48, threads=1)
+    return {"value": v, "unit": line_unit, "cores": cores, "kind": "oracle", "sample": sample,
+            "one_core": {"value": v1, "unit": line_unit, "cores": 1, "sample": sample1}}
+
+
+def cpu_coarse_step_case(args):
+    """The oracle's time for one full coarse step of the 7-level binary
+    (BOHierarchy, all host cores, 77.76 M zone updates): long, not part of
+    the default run."""
+    import initial_data as idd
+    import oracle
+    h = hierarchy()
+    states = idd.hierarchy_data(h)
+    bo = oracle.BOHierarchy(h, states, oracle.Params(), courant=args.courant)
+    t0 = time.perf_counter()
+    bo.level_step(0)
+    dt = time.perf_counter() - t0
+    zu = h.zone_updates_per_coarse_step()
+    print(json.dumps({"case": "cpu-coarse-step", "seconds": dt, "zone_updates": zu,
+                      "zone_updates_per_s": zu / dt, "cores": oracle.num_threads()}), flush=True)
 
 
 def run_reference(args, rank, world):
@@ -206,11 +242,14 @@ def main():
                     help="gauge-wave: RK4 steps on the coarsest grid; robust-stability: steps per grid")
     ap.add_argument("--case", default="amr7",
                     choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep", "tov",
+                             "cpu-coarse-step",
                              "amr7-zsym", "adm", "amr7-moving", "psi4"],
                     help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
                          "mixed-error: the 7-level hierarchy in FP64 and mixed precision side by side")
     ap.add_argument("--coarse-steps", type=int, default=64, help="mixed-error: coarse steps")
     ap.add_argument("--error-kernels", default="", help="mixed-error: stage kernels to compare, e.g. 6,0")
+    ap.add_argument("--fp64-twin", action="store_true",
+                    help="mixed-error: also an FP64 run from data perturbed at 1e-7 (FP32 rounding size)")
     ap.add_argument("--adm-steps", type=int, default=2, help="adm: coarse steps evolved before the integrals")
     ap.add_argument("--tov-n", type=int, default=128, help="tov: cells per axis of the patch on [-16, 16]^3")
     args = ap.parse_args()
@@ -219,6 +258,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.case == "cpu-coarse-step":
+        if rank == 0:
+            cpu_coarse_step_case(args)
         return
 
     import torch
@@ -300,8 +343,7 @@ def main():
     if len(precisions) > 1:
         line["speedup_mixed_over_fp64"] = runs["mixed"]["value"] / runs["fp64"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_sample(1)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = cpu_baseline(UNIT)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -873,16 +915,28 @@ def mixed_error_case(torch, sk, args):
     data for --coarse-steps coarse steps; report per level and field the
     max |mixed - FP64| (absolute and over the field's max |FP64|) and both
     runs' constraint norms.  --error-kernels lists the mixed stage kernels to
-    compare (one mixed run each, default: the default kernel)."""
+    compare (one mixed run each, default: the default kernel).  --fp64-twin
+    adds an FP64 run from the same data perturbed by 1e-7 relative, the size
+    of FP32 rounding: how far two FP64 evolutions part from differences of
+    that size, beside how far mixed and FP64 part."""
     import initial_data as idd
     h = hierarchy()
     grids = {}
     kernels = [int(k) for k in args.error_kernels.split(",")] if args.error_kernels else [None]
     runs = [("fp64", 0, None)] + [("mixed" if k is None else "mixed-k%d" % k, 1, k) for k in kernels]
+    if args.fp64_twin:
+        runs.append(("fp64-perturbed", 0, None))
     for name, prec, k in runs:
         g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(courant=args.courant, precision=prec),
                     stream=torch.cuda.Stream())
         g.set_initial_data(1, h.masses, h.positions)
+        if name == "fp64-perturbed":
+            # every value times (1 + 1e-7 r), r uniform in [-1, 1): the size of
+            # the FP32 rounding of the mixed path's arithmetic, in FP64
+            for i, p in enumerate(h.patches):
+                u = g.download_fields(i)
+                r = idd.add_noise(p, np.zeros_like(u), 1.0, 987654321, idd.level_origin(h, p.level))
+                g.upload_fields(i, u * (1.0 + 1e-7 * r))
         if k is not None:
             for l in range(len(h.levels)):
                 g.set_stage_kernel(l, k)

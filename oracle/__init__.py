@@ -105,6 +105,7 @@ def lib():
             L.orc_exchange.restype = ctypes.c_long
             L.orc_lagrange_weights.argtypes = [ctypes.c_int, P(ctypes.c_int), ctypes.c_double, dp]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             L.orc_adm_integrals.argtypes = [P(_OrcPatch), dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
             L.orc_adm_integrals.restype = ctypes.c_int
             L.orc_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
@@ -136,6 +137,11 @@ def _ptr(a: np.ndarray):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (for timing on a core count)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def rhs(p, u: np.ndarray, prm: Params = Params(), terms: int = 7) -> np.ndarray:

@@ -99,6 +99,15 @@ size_t orc_patch_points(const orc_patch* p) {
   return (size_t)L.sf;
 }
 
+/* threads of the OpenMP loops (timing of the oracle on a given core count) */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

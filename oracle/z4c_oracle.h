@@ -218,6 +218,7 @@ int orc_interp_point(const orc_patch* p, const double* u, int f, const double x[
 void orc_lagrange_weights(int nnodes, const int* nodes, double x, double* w);
 
 /* number of threads the OpenMP loops use (1 without OpenMP) */
+void orc_set_num_threads(int n);
 int orc_num_threads(void);
 
 #ifdef __cplusplus
