@@ -27,6 +27,40 @@ _lib = None
 NF = 25
 
 
+_COUNT_PATH = os.path.join(_BUILD, "flop_count")
+
+
+def build_flop_count(force: bool = False) -> str:
+    """Compile the counting-scalar build of the oracle (flop_count.cpp: the
+    oracle's C source with a scalar type that counts its operations)."""
+    srcs = [os.path.join(_HERE, f) for f in ("flop_count.cpp", "z4c_oracle.c", "z4c_oracle.h")]
+    if not force and os.path.exists(_COUNT_PATH) and os.path.getmtime(_COUNT_PATH) >= max(map(os.path.getmtime, srcs)):
+        return _COUNT_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _COUNT_PATH + ".tmp%d" % os.getpid()
+    subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-I" + _HERE, "-o", tmp,
+                    srcs[0]], check=True)
+    os.replace(tmp, _COUNT_PATH)
+    return _COUNT_PATH
+
+
+def flop_counts(p, u: np.ndarray):
+    """FP64 operations per active point of the oracle's evaluation of patch
+    array u (centred patch of spacing p.dx): the right-hand side, its
+    sources / advection / dissipation parts and one 5-pass RK4 stage; and
+    the right-hand side the counting build computed (the oracle's to the bit)."""
+    import json
+    import tempfile
+    exe = build_flop_count()
+    with tempfile.TemporaryDirectory() as d:
+        fi, fo = os.path.join(d, "in.bin"), os.path.join(d, "out.bin")
+        np.ascontiguousarray(u, dtype=np.float64).tofile(fi)
+        r = subprocess.run([exe, str(p.n[0]), str(p.n[1]), str(p.n[2]), repr(float(p.dx)), fi, fo],
+                           capture_output=True, text=True, check=True)
+        rhs = np.fromfile(fo).reshape(u.shape)
+    return json.loads(r.stdout), rhs
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no GPU involved)."""
     src = os.path.join(_HERE, "z4c_oracle.c")
