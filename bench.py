@@ -233,6 +233,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", type=int, default=None,
                     help="uniform96: force this stage kernel (0 direct, 1-4 TMA tiles) after autotuning")
+    ap.add_argument("--serial-ghosts", action="store_true",
+                    help="refined levels' ghost fills and prolongation on the grid's stream, in order "
+                         "(default: beside the stage kernels on a second stream)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default stage kernels instead of timing them first")
     ap.add_argument("--sizes", default="32,64,128", help="gauge-wave / robust-stability grid sizes")
@@ -323,6 +326,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "levels": len(h.levels), "patches": len(h.patches),
                        "zone_updates_per_step": zu, "courant": args.courant, "precision": precisions[0],
+                       "ghost_schedule": "serial" if args.serial_ghosts else "overlapped",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2: %.2f GB per state copy" % (
                            sum(25 * 8 * (p.n[0] + 6) * (p.n[1] + 6) * (p.n[2] + 6) for p in h.patches) / 1e9),
@@ -404,6 +408,7 @@ def measure(torch, sk, h, precision, args, world, dist):
     prm = sk.Params(courant=args.courant, precision=1 if precision == "mixed" else 0)
     stream = torch.cuda.Stream()
     g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=stream)
+    g.set_overlap(not args.serial_ghosts)
     g.set_initial_data(1, h.masses, h.positions)
     tune = None
     if precision == "mixed" and not args.no_autotune:
@@ -1018,6 +1023,7 @@ def end_to_end(torch, sk, h, prm, args, world, dist):
     downloads every patch."""
     stream = torch.cuda.Stream()
     g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=stream)
+    g.set_overlap(not args.serial_ghosts)
     g.set_initial_data(1, h.masses, h.positions)
     host = [torch.empty(g.shape(i), dtype=torch.float64).pin_memory() for i in range(len(h.patches))]
     for i in range(len(h.patches)):

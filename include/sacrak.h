@@ -390,6 +390,18 @@ sacrak_status sacrak_autotune(sacrak_grid* grid, int reps, int use_cache, double
  * without writing results.  Drops the recorded coarse-step graph. */
 sacrak_status sacrak_set_wait_limit(sacrak_grid* grid, long long cycles);
 
+/* Schedule of the refined levels' ghost work (Sec. 2.2.1).  on = 1 (the
+ * default): within each RK4 step of a level > 0, the time fill of the
+ * stage-2 and stage-3 inputs runs on a second stream of the library's
+ * concurrently with the stage-1 kernel, the fill of the stage-4 input with
+ * the stage-3 kernel, and the spatial prolongation of a parent's new time
+ * level with the children's first stage; every call that launches them
+ * makes the caller's stream wait for that stream before it returns (under
+ * capture these are graph edges).  on = 0: every launch on the caller's
+ * stream, one after another.  Results are the same bit for bit.  Drops the
+ * recorded coarse-step graph; SACRAK_EINVAL for other values. */
+sacrak_status sacrak_set_overlap(sacrak_grid* grid, int on);
+
 /* ---- Matter: a perfect fluid on the evolving spacetime (Sec. 2.1.2, 2.2) ----
  * Grids created with params.matter = 1 (one level, FP64) carry a perfect
  * fluid: primitives (rho, eps, u_x, u_y, u_z) -- rest-mass density, specific

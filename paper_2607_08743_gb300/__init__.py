@@ -33,7 +33,7 @@ EXPORTS = [
     "sacrak_track_punctures", "sacrak_get_punctures", "sacrak_move_patch", "sacrak_regrid",
     "sacrak_patch_origin", "sacrak_psi4_modes", "sacrak_nakano", "sacrak_ffi_work_bytes", "sacrak_ffi_strain",
     "sacrak_set_wait_limit", "sacrak_set_eos", "sacrak_set_atmosphere", "sacrak_upload_matter",
-    "sacrak_download_matter", "sacrak_matter_rhs",
+    "sacrak_download_matter", "sacrak_matter_rhs", "sacrak_set_overlap",
 ]
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
                                                      vp, dp]
             L.sacrak_set_stage_kernel.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             L.sacrak_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+            L.sacrak_set_overlap.argtypes = [vp, ctypes.c_int]
             L.sacrak_set_eos.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_double]
             L.sacrak_set_atmosphere.argtypes = [vp, ctypes.c_double, ctypes.c_double]
             L.sacrak_upload_matter.argtypes = [vp, ctypes.c_int, vp]
@@ -462,6 +463,11 @@ class Grid:
         """Bound (SM cycles) of the TMA stage kernels' copy waits; 0 = default,
         < 0 = run out at once (tests of the time-out path)."""
         self._check(lib().sacrak_set_wait_limit(self._h, int(cycles)), "set_wait_limit")
+
+    def set_overlap(self, on: bool):
+        """Refined levels' ghost fills and prolongation beside the stage
+        kernels on a second stream (default) or all on the grid's stream."""
+        self._check(lib().sacrak_set_overlap(self._h, 1 if on else 0), "set_overlap")
 
     def stage_kernel(self, level: int) -> int:
         v = ctypes.c_int()

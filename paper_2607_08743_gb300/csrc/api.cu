@@ -168,6 +168,13 @@ struct sacrak_grid {
   bool invalid = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  // second stream for the refinement-boundary time fills and the parent's
+  // prolongation, which run beside the stage kernels (sacrak_set_overlap);
+  // side_live: work on it that the main stream has not waited for yet
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool side_live = false;
+  bool overlap = true;
   std::string last_error;
   // profiling of the fused stage kernel
   bool prof = false;
@@ -485,25 +492,41 @@ FillArgs fill_args(sacrak_grid* g, int l, int mode, int stage, double s0, double
   return a;
 }
 
-// ghost fill of level l for the buffer given by (mode, stage); for levels
-// > 0 the child step starts at fraction s0 of the parent step and lasts ds
-// prolong: 0 skip the time fill (exchange only), 1 fill, 2 fill the stage-2
-// input and the stage-3 input together (stages 2 and 3 share their time)
-void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double ds, int prolong = 1) {
-  const int np = (int)g->lvl_ids[l].size();
-  if (l == 0) {
-    if (g->prm.bc == 1)
-      launch_fill(FILL_PERIODIC, fill_args(g, l, mode, stage, 0.0), np, g->lvl_max_shell[l], g->stream);
-    else if (g->prm.bc == 2)
-      launch_fill(FILL_FROZEN, fill_args(g, l, mode, stage, 0.0), np, g->lvl_max_shell[l], g->stream);
-    return;
-  }
-  if (prolong) {
-    FillArgs fa = fill_args(g, l, mode, stage, s0, ds);
-    fa.dual = prolong == 2;
-    launch_fill(FILL_PROLONG, fa, np, g->lvl_max_shell[l], g->stream);
-  }
-  // same-level exchange between every overlapping pair
+void release_side(sacrak_grid* g) {
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
+  if (g->side) cudaStreamDestroy(g->side);
+  g->ev_fork = g->ev_join = nullptr;
+  g->side = nullptr;
+}
+
+// The main stream hands work to the side stream (fork) and waits for all of
+// it (join).  Both are stream-ordered event operations, so they become graph
+// edges under capture.
+void fork_side(sacrak_grid* g) {
+  cudaEventRecord(g->ev_fork, g->stream);
+  cudaStreamWaitEvent(g->side, g->ev_fork, 0);
+  g->side_live = true;
+}
+void join_side(sacrak_grid* g) {
+  if (!g->side_live) return;
+  cudaEventRecord(g->ev_join, g->side);
+  cudaStreamWaitEvent(g->stream, g->ev_join, 0);
+  g->side_live = false;
+}
+
+// time fill of a refined level's ghosts from the cached prolongations, for
+// the buffer given by (mode, stage); the child step starts at fraction s0 of
+// the parent step and lasts ds; dual: the stage-2 input and the stage-3
+// input together (stages 2 and 3 share their time)
+void time_fill(sacrak_grid* g, int l, int mode, int stage, double s0, double ds, bool dual, cudaStream_t st) {
+  FillArgs fa = fill_args(g, l, mode, stage, s0, ds);
+  fa.dual = dual;
+  launch_fill(FILL_PROLONG, fa, (int)g->lvl_ids[l].size(), g->lvl_max_shell[l], st);
+}
+
+// same-level exchange between every overlapping pair of level l
+void exchange_level(sacrak_grid* g, int l, int mode, int stage) {
   const auto& ids = g->lvl_ids[l];
   for (size_t a = 0; a < ids.size(); ++a)
     for (size_t b = a + 1; b < ids.size(); ++b) {
@@ -532,6 +555,23 @@ void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double d
     }
 }
 
+// ghost fill of level l for the buffer given by (mode, stage); for levels
+// > 0 the child step starts at fraction s0 of the parent step and lasts ds
+// prolong: 0 skip the time fill (exchange only), 1 fill, 2 fill the stage-2
+// input and the stage-3 input together (stages 2 and 3 share their time)
+void fill_ghosts(sacrak_grid* g, int l, int mode, int stage, double s0, double ds, int prolong = 1) {
+  const int np = (int)g->lvl_ids[l].size();
+  if (l == 0) {
+    if (g->prm.bc == 1)
+      launch_fill(FILL_PERIODIC, fill_args(g, l, mode, stage, 0.0), np, g->lvl_max_shell[l], g->stream);
+    else if (g->prm.bc == 2)
+      launch_fill(FILL_FROZEN, fill_args(g, l, mode, stage, 0.0), np, g->lvl_max_shell[l], g->stream);
+    return;
+  }
+  if (prolong) time_fill(g, l, mode, stage, s0, ds, prolong == 2, g->stream);
+  exchange_level(g, l, mode, stage);
+}
+
 // equatorial reflection of the level's z < 0 ghosts in the (mode, stage) buffer
 void zreflect(sacrak_grid* g, int l, int mode, int stage) {
   if (!g->prm.zsym) return;
@@ -539,11 +579,14 @@ void zreflect(sacrak_grid* g, int l, int mode, int stage) {
 }
 
 // spatial prolongation of level l-1's current slot onto level l's shells
-void refresh_shells(sacrak_grid* g, int l) {
+// (on the side stream with overlap: the children's first stage-2 fill, also
+// on the side stream, is the first reader of the new slot's cache)
+void refresh_shells(sacrak_grid* g, int l, bool side = false) {
   if (l <= 0 || l >= g->nlevels) return;
+  if (side) fork_side(g);
   launch_prolong_space(g->d_patches, g->d_ids + g->lvl_id_off[l], g->d_levels + (l - 1),
                        (int)g->lvl_ids[l].size(), g->lvl_max_clusters[l], g->prm.precision == 1,
-                       g->stream);
+                       side ? g->side : g->stream);
 }
 
 // after new data: every child level's cache for its parent's current slot,
@@ -614,9 +657,22 @@ void matter_advance(sacrak_grid* g, int l, int s, double dt, double* out = nullp
 
 void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
   const int np = (int)g->lvl_ids[l].size();
+  // refined levels with overlap: the time fill of stage 2 (with stage 3's)
+  // runs on the side stream beside the stage-1 kernel, the one of stage 4
+  // beside the stage-3 kernel.  Each writes only ghost cells, of buffers that
+  // the concurrent kernel neither reads nor writes (stage kernels write
+  // active cells only); the same-level exchange, which reads active cells of
+  // the stage input, follows the join on the main stream.
+  const bool ov = g->overlap && l > 0;
   for (int s = 1; s <= 4; ++s) {
-    if (!(l == 0 && (g->prm.bc == 0 || (g->prm.bc == 2 && s == 1))))
-      fill_ghosts(g, l, 0, s, frac0, dfrac, l > 0 ? (s == 2 ? 2 : (s == 3 ? 0 : 1)) : 1);
+    if (!(l == 0 && (g->prm.bc == 0 || (g->prm.bc == 2 && s == 1)))) {
+      if (ov && (s == 2 || s == 4)) {
+        join_side(g);
+        exchange_level(g, l, 0, s);
+      } else {
+        fill_ghosts(g, l, 0, s, frac0, dfrac, l > 0 ? (s == 2 ? 2 : (s == 3 ? 0 : 1)) : 1);
+      }
+    }
     zreflect(g, l, 0, s);  // equatorial symmetry: after every other ghost treatment
     // the fluid of this stage: primitives and the Z4c matter terms first
     if (g->prm.matter) matter_recover(g, l, s, dt);
@@ -629,7 +685,10 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
     a.dt = dt;
     a.prm = dev_params(g->prm);
     a.err = g->d_err;
+    const bool fill_next = ov && (s == 1 || s == 3);
+    if (fill_next) fork_side(g);  // recorded before the stage kernel: the fill does not wait for it
     launch_stage(g, a, g->lvl_zones[l], g->lvl_ids[l], g->lvl_kernel[l]);
+    if (fill_next) time_fill(g, l, 0, s + 1, frac0, dfrac, s == 1, g->side);
     if (l == 0 && g->prm.bc == 0) {
       GhostArgs ga;
       ga.patches = g->d_patches;
@@ -669,7 +728,7 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
       break;
     }
   launch_level_advance(g->d_levels + l, dt, g->stream);
-  refresh_shells(g, l + 1);  // the children's cache of this level's new slot
+  refresh_shells(g, l + 1, g->overlap);  // the children's cache of this level's new slot
 }
 
 // do two patches of level l share active cells (the exchange then averages
@@ -879,6 +938,14 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   sacrak_grid* g = new sacrak_grid();
   g->prm = p;
   g->stream = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    release_side(g);
+    delete g;
+    return SACRAK_ECUDA;
+  }
   g->arena = (char*)device_arena;
   g->arena_bytes = arena_bytes;
   g->nlevels = nlevels;
@@ -1045,6 +1112,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
     if (p.precision == 1) st = select_kernel(g, l, K_LDG_PFZ);
   if (st != SACRAK_OK) {
     cudaGetLastError();
+    release_side(g);
     delete g;
     return st;
   }
@@ -1054,6 +1122,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
 
 sacrak_status sacrak_grid_destroy(sacrak_grid* g) {
   if (!g) return SACRAK_EINVAL;
+  release_side(g);
   for (auto& p : g->ev) {
     cudaEventDestroy(p.first);
     cudaEventDestroy(p.second);
@@ -1218,6 +1287,7 @@ sacrak_status sacrak_rk4_step(sacrak_grid* g, int level, double dt) {
   if (g->prm.matter && !g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
   refresh_all_shells(g);
   rk4_level(g, level, dt > 0.0 ? dt : level_dt(g, level), 0.0, 0.5);
+  join_side(g);
   return check_launch(g);
 }
 
@@ -1229,6 +1299,7 @@ sacrak_status sacrak_level_step(sacrak_grid* g, int level) {
   refresh_all_shells(g);  // eager, outside any graph
   if (level > 0 || g->stream == nullptr || g->prof) {
     level_step_rec(g, level, 0.0, 0.5);
+    join_side(g);
     return check_launch(g);
   }
   if (!g->graph_exec) {
@@ -1236,10 +1307,12 @@ sacrak_status sacrak_level_step(sacrak_grid* g, int level) {
     CK(cudaStreamIsCapturing(g->stream, &cs));
     if (cs != cudaStreamCaptureStatusNone) {  // caller is capturing: just record launches
       level_step_rec(g, 0, 0.0, 1.0);
+      join_side(g);
       return check_launch(g);
     }
     CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
     level_step_rec(g, 0, 0.0, 1.0);
+    join_side(g);
     cudaGraph_t graph;
     cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
     if (e != cudaSuccess) return fail(g, SACRAK_ECUDA, "graph capture: %s", cudaGetErrorString(e));
@@ -1627,6 +1700,14 @@ sacrak_status sacrak_set_wait_limit(sacrak_grid* g, long long cycles) {
   if (!g) return SACRAK_EINVAL;
   if (g->tma_wait_cycles != cycles) drop_graph(g);  // the captured launches hold the old bound
   g->tma_wait_cycles = cycles;
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_set_overlap(sacrak_grid* g, int on) {
+  if (!g) return SACRAK_EINVAL;
+  if (on != 0 && on != 1) return fail(g, SACRAK_EINVAL, "overlap must be 0 or 1");
+  if (g->overlap != (on == 1)) drop_graph(g);  // the captured coarse step has the other schedule
+  g->overlap = on == 1;
   return SACRAK_OK;
 }
 
