@@ -28,18 +28,23 @@
  *    arena given to sacrak_grid_create, which the library never frees and
  *    never reallocates.  The library allocates no device memory on any call
  *    (except the tables cuFFT keeps for the duration of sacrak_ffi_strain).
- *  - Ordering: all device work is issued on the grid's CUDA stream, in call
- *    order.  Calls that return values computed on the device (constraints,
- *    pi symmetry, surface integrals, puncture positions, downloads to host
- *    memory) and the regrid calls synchronise that stream.
+ *  - Ordering: all device work is ordered on the grid's CUDA stream, in call
+ *    order.  (Refined levels' ghost work may run on a second stream owned by
+ *    the grid, forked from and joined back into the grid's stream within the
+ *    same call: sacrak_set_overlap.)  Calls that return values computed on
+ *    the device (constraints, pi symmetry, surface integrals, puncture
+ *    positions, downloads to host memory) and the regrid calls synchronise
+ *    that stream.
  *  - Errors: no call aborts or throws across the ABI.  Invalid arguments
  *    return SACRAK_EINVAL before any device work is issued; a CUDA error
  *    returns SACRAK_ECUDA; a non-finite value detected by a stage returns
  *    SACRAK_ENONFINITE at the next call that synchronises; a bounded device
- *    wait that runs out returns SACRAK_ETIMEOUT.  After ECUDA, ENONFINITE or
- *    ETIMEOUT the grid is marked invalid and every stepping call returns
- *    SACRAK_ESTATE until new data is uploaded or set.  sacrak_last_error
- *    gives a one-line description.
+ *    wait that runs out returns SACRAK_ETIMEOUT (reported ahead of a
+ *    non-finite value seen in the same interval: the stage that gave up left
+ *    its outputs unwritten).  After ECUDA, ENONFINITE or ETIMEOUT the grid
+ *    is marked invalid and every stepping call returns SACRAK_ESTATE until
+ *    new data is uploaded or set.  sacrak_last_error gives a one-line
+ *    description.
  *  - Thread safety: one grid per host thread.
  */
 #ifndef SACRAK_H

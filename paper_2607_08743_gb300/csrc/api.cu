@@ -247,9 +247,11 @@ sacrak_status sync_and_check(sacrak_grid* g) {
   unsigned flag = 0;
   CK(cudaMemcpyAsync(&flag, g->d_err, sizeof flag, cudaMemcpyDeviceToHost, g->stream));
   CK(cudaStreamSynchronize(g->stream));
-  if (flag & ERR_NONFINITE) return fail(g, SACRAK_ENONFINITE, "non-finite value in a stage update");
+  // a wait that ran out or a failed bounds check skipped writes, so later
+  // non-finite values may be their consequence: they are reported first
   if (flag & ERR_TIMEOUT) return fail(g, SACRAK_ETIMEOUT, "bounded device wait ran out");
   if (flag & ERR_BOUNDS) return fail(g, SACRAK_ECUDA, "device bounds check failed");
+  if (flag & ERR_NONFINITE) return fail(g, SACRAK_ENONFINITE, "non-finite value in a stage update");
   if (flag & ERR_TRACK) {  // reported once; the grid stays usable
     const unsigned rest = flag & ~(unsigned)ERR_TRACK;
     CK(cudaMemcpy(g->d_err, &rest, sizeof rest, cudaMemcpyHostToDevice));

@@ -70,27 +70,18 @@ struct Geo {
   double Rsc;         // R
 };
 
-__device__ __forceinline__ void geometry(const double* __restrict__ u, long long q,
-                                         const long long st[3], long long fs, double c1,
-                                         double c2, double c11, const PointState& c, Geo& G,
-                                         double dGam[3][3], double dbe[3][3]) {
+// G.dW, G.dal and dgt (first derivatives, scaled) are given; d2(g, d) is the
+// scaled second derivative along axis d of W (g = 0), gt_a (g = 1 + a) and
+// alpha (g = 7); the mixed second derivatives are formed here.
+template <class D2>
+__device__ __forceinline__ void geometry_t(const double* __restrict__ u, long long q,
+                                           const long long st[3], long long fs, double c11,
+                                           const PointState& c, Geo& G, const double dgt[3][6],
+                                           const double dGam[3][3], const D2& d2) {
   sym_inv(c.gt, G.gtu);
   const double* gtu = G.gtu;
 
-  // first derivatives of gt -> Christoffel symbols of the first kind
-  double dgt[3][6];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-#pragma unroll
-    for (int a = 0; a < 6; ++a) dgt[d][a] = d1u(u + (F_GXX + a) * fs, q, st[d]) * c1;
-    G.dW[d] = d1u(u + F_W * fs, q, st[d]) * c1;
-    G.dal[d] = d1u(u + F_ALP * fs, q, st[d]) * c1;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      dGam[d][i] = d1u(u + (F_GAMX + i) * fs, q, st[d]) * c1;
-      dbe[d][i] = d1u(u + (F_BETX + i) * fs, q, st[d]) * c1;
-    }
-  }
+  // Christoffel symbols of the first kind from the first derivatives of gt
   double Gl[3][6];  // Gt_ijk = 1/2 (d_j gt_ik + d_k gt_ij - d_i gt_jk)
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -127,11 +118,10 @@ __device__ __forceinline__ void geometry(const double* __restrict__ u, long long
       const int ij = S2(i, j);
       // -1/2 gt^lm d_l d_m gt_ij
       const double* f = u + (F_GXX + ij) * fs;
-      double f0 = c.gt[ij];
       double dd[6];
-      dd[0] = d2u(f, q, st[0], f0) * c2;
-      dd[3] = d2u(f, q, st[1], f0) * c2;
-      dd[5] = d2u(f, q, st[2], f0) * c2;
+      dd[0] = d2(1 + ij, 0);
+      dd[3] = d2(1 + ij, 1);
+      dd[5] = d2(1 + ij, 2);
       dd[1] = d11u(f, q, st[0], st[1]) * c11;
       dd[2] = d11u(f, q, st[0], st[2]) * c11;
       dd[4] = d11u(f, q, st[1], st[2]) * c11;
@@ -165,15 +155,15 @@ __device__ __forceinline__ void geometry(const double* __restrict__ u, long long
     const double* fW = u + F_W * fs;
     const double* fa = u + F_ALP * fs;
     double ddW[6], dda[6];
-    ddW[0] = d2u(fW, q, st[0], W) * c2;
-    ddW[3] = d2u(fW, q, st[1], W) * c2;
-    ddW[5] = d2u(fW, q, st[2], W) * c2;
+    ddW[0] = d2(0, 0);
+    ddW[3] = d2(0, 1);
+    ddW[5] = d2(0, 2);
     ddW[1] = d11u(fW, q, st[0], st[1]) * c11;
     ddW[2] = d11u(fW, q, st[0], st[2]) * c11;
     ddW[4] = d11u(fW, q, st[1], st[2]) * c11;
-    dda[0] = d2u(fa, q, st[0], c.al) * c2;
-    dda[3] = d2u(fa, q, st[1], c.al) * c2;
-    dda[5] = d2u(fa, q, st[2], c.al) * c2;
+    dda[0] = d2(7, 0);
+    dda[3] = d2(7, 1);
+    dda[5] = d2(7, 2);
     dda[1] = d11u(fa, q, st[0], st[1]) * c11;
     dda[2] = d11u(fa, q, st[0], st[2]) * c11;
     dda[4] = d11u(fa, q, st[1], st[2]) * c11;
@@ -204,9 +194,92 @@ __device__ __forceinline__ void geometry(const double* __restrict__ u, long long
   G.Lapa = W * W * trDDa - W * dWda;
 }
 
+// second derivatives along the axes formed on demand (constraint monitor,
+// surface diagnostics)
+struct D2Direct {
+  const double* u;
+  long long q, fs;
+  const long long* st;
+  double c2;
+  const PointState* c;
+  __device__ __forceinline__ double operator()(int g, int d) const {
+    const int f = g == 0 ? F_W : (g == 7 ? F_ALP : F_GXX + g - 1);
+    const double f0 = g == 0 ? c->W : (g == 7 ? c->al : c->gt[g - 1]);
+    return d2u(u + f * fs, q, st[d], f0) * c2;
+  }
+};
+
+__device__ __forceinline__ void geometry(const double* __restrict__ u, long long q,
+                                         const long long st[3], long long fs, double c1,
+                                         double c2, double c11, const PointState& c, Geo& G,
+                                         double dGam[3][3], double dbe[3][3]) {
+  double dgt[3][6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) dgt[d][a] = d1u(u + (F_GXX + a) * fs, q, st[d]) * c1;
+    G.dW[d] = d1u(u + F_W * fs, q, st[d]) * c1;
+    G.dal[d] = d1u(u + F_ALP * fs, q, st[d]) * c1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dGam[d][i] = d1u(u + (F_GAMX + i) * fs, q, st[d]) * c1;
+      dbe[d][i] = d1u(u + (F_BETX + i) * fs, q, st[d]) * c1;
+    }
+  }
+  geometry_t(u, q, st, fs, c11, c, G, dgt, dGam, D2Direct{u, q, fs, st, c2, &c});
+}
+
+// Per-thread stash of the fused stencil pass in shared memory, one column per
+// thread ([slot][thread]): each field's advection + dissipation, and the
+// second derivatives along the axes of W, gt (6), alpha and beta (3).
+constexpr int STAGE_THREADS = 128;
+constexpr int ST_ADV = 0;        // NF slots
+constexpr int ST_D2 = NF;        // 11 groups x 3 axes: 0 W, 1..6 gt, 7 alpha, 8..10 beta
+constexpr int ST_N = NF + 33;
+constexpr size_t STAGE_SMEM = (size_t)ST_N * STAGE_THREADS * sizeof(double);
+
+struct Stash {
+  double* p;  // this thread's column
+  __device__ __forceinline__ double& operator[](int slot) const { return p[slot * STAGE_THREADS]; }
+};
+struct D2Stash {
+  Stash S;
+  __device__ __forceinline__ double operator()(int g, int d) const { return S[ST_D2 + 3 * g + d]; }
+};
+
+// One field's stencils along the three axes from one read of f_-3 .. f_3:
+// with d_k = f_k - f_-k and e_k = (f_k - f0) + (f_-k - f0), D1 = 8 d1 - d2 (the
+// first derivative times 12h), D2 = 16 e1 - e2 (the second times 12h^2), and
+// the return value, the field's advection along the shift plus dissipation,
+//   sum_d [ b_d (21 d1 - 6 d2 + d3) + a_d (e3 - 6 e2 + 15 e1) ],
+// b_d = beta^d / (24h), a_d = |beta^d| / (24h) + sigma_KO / (64h).  The lopsided
+// upwind derivative (one point behind, three ahead along the shift) equals
+// its antisymmetric part, (21 d1 - 6 d2 + d3) / (24h), plus |beta|/2 times the
+// sixth difference e3 - 6 e2 + 15 e1 over 12h, for either sign of beta; the
+// sixth difference is also the Kreiss-Oliger stencil.
+template <bool WANT_D1, bool WANT_D2>
+__device__ __forceinline__ double field_axes(const double* __restrict__ f, long long q, const long long st[3],
+                                             double f0, const double b[3], const double a[3], double D1[3],
+                                             double D2[3]) {
+  double adk = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const long long o = st[d];
+    const double p1 = __ldg(f + q + o), m1 = __ldg(f + q - o);
+    const double p2 = __ldg(f + q + 2 * o), m2 = __ldg(f + q - 2 * o);
+    const double p3 = __ldg(f + q + 3 * o), m3 = __ldg(f + q - 3 * o);
+    const double d1 = p1 - m1, d2 = p2 - m2, d3 = p3 - m3;
+    const double e1 = (p1 - f0) + (m1 - f0), e2 = (p2 - f0) + (m2 - f0), e3 = (p3 - f0) + (m3 - f0);
+    if (WANT_D1) D1[d] = 8.0 * d1 - d2;
+    if (WANT_D2) D2[d] = 16.0 * e1 - e2;
+    adk += b[d] * ((21.0 * d1 - 6.0 * d2) + d3) + a[d] * ((e3 - 6.0 * e2) + 15.0 * e1);
+  }
+  return adk;
+}
+
 __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ u, long long q,
                                               long long sy, long long sz, long long fs,
-                                              double h, const DevParams& prm, double r[NF]) {
+                                              double h, const DevParams& prm, Stash S, double r[NF]) {
   const long long st[3] = {1, sy, sz};
   const double c1 = 1.0 / (12.0 * h);
   const double c2 = c1 / h;
@@ -214,8 +287,63 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ u, long
   PointState c;
   load_centre(u, q, fs, c);
   Geo G;
-  double dGam[3][3], dbe[3][3];
-  geometry(u, q, st, fs, c1, c2, c11, c, G, dGam, dbe);
+  double dgt[3][6], dGam[3][3], dbe[3][3], dKh[3], dTh[3];
+  {
+    const double hb = 0.5 * c1, cko = prm.sigma_ko / (64.0 * h);
+    double wb[3], wa[3], t1[3], t2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      wb[d] = c.be[d] * hb;
+      wa[d] = fabs(c.be[d]) * hb + cko;
+    }
+    S[ST_ADV + F_W] = field_axes<true, true>(u + F_W * fs, q, st, c.W, wb, wa, t1, t2);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      G.dW[d] = t1[d] * c1;
+      S[ST_D2 + d] = t2[d] * c2;
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      S[ST_ADV + F_GXX + a] = field_axes<true, true>(u + (F_GXX + a) * fs, q, st, c.gt[a], wb, wa, t1, t2);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        dgt[d][a] = t1[d] * c1;
+        S[ST_D2 + 3 * (1 + a) + d] = t2[d] * c2;
+      }
+    }
+    S[ST_ADV + F_KH] = field_axes<true, false>(u + F_KH * fs, q, st, c.Kh, wb, wa, t1, t2);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dKh[d] = t1[d] * c1;
+    S[ST_ADV + F_TH] = field_axes<true, false>(u + F_TH * fs, q, st, c.Th, wb, wa, t1, t2);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dTh[d] = t1[d] * c1;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+      S[ST_ADV + F_AXX + a] = field_axes<false, false>(u + (F_AXX + a) * fs, q, st, c.At[a], wb, wa, t1, t2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      S[ST_ADV + F_GAMX + i] = field_axes<true, false>(u + (F_GAMX + i) * fs, q, st, c.Gam[i], wb, wa, t1, t2);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) dGam[d][i] = t1[d] * c1;
+    }
+    S[ST_ADV + F_ALP] = field_axes<true, true>(u + F_ALP * fs, q, st, c.al, wb, wa, t1, t2);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      G.dal[d] = t1[d] * c1;
+      S[ST_D2 + 21 + d] = t2[d] * c2;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      S[ST_ADV + F_BETX + i] = field_axes<true, true>(u + (F_BETX + i) * fs, q, st, c.be[i], wb, wa, t1, t2);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        dbe[d][i] = t1[d] * c1;
+        S[ST_D2 + 3 * (8 + i) + d] = t2[d] * c2;
+      }
+      S[ST_ADV + F_BX + i] = field_axes<false, false>(u + (F_BX + i) * fs, q, st, c.Bv[i], wb, wa, t1, t2);
+    }
+  }
+  geometry_t(u, q, st, fs, c11, c, G, dgt, dGam, D2Stash{S});
   const double* gtu = G.gtu;
   const double W = c.W, al = c.al;
   const double K = c.Kh + 2.0 * c.Th;
@@ -278,9 +406,9 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ u, long
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const double* f = u + (F_BETX + i) * fs;
-      ddb[i][0] = d2u(f, q, st[0], c.be[i]) * c2;
-      ddb[i][3] = d2u(f, q, st[1], c.be[i]) * c2;
-      ddb[i][5] = d2u(f, q, st[2], c.be[i]) * c2;
+      ddb[i][0] = S[ST_D2 + 3 * (8 + i) + 0];
+      ddb[i][3] = S[ST_D2 + 3 * (8 + i) + 1];
+      ddb[i][5] = S[ST_D2 + 3 * (8 + i) + 2];
       ddb[i][1] = d11u(f, q, st[0], st[1]) * c11;
       ddb[i][2] = d11u(f, q, st[0], st[2]) * c11;
       ddb[i][4] = d11u(f, q, st[1], st[2]) * c11;
@@ -288,12 +416,6 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ u, long
     double ddivb[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) ddivb[j] = ddb[0][S2(j, 0)] + ddb[1][S2(j, 1)] + ddb[2][S2(j, 2)];
-    double dKh[3], dTh[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      dKh[d] = d1u(u + F_KH * fs, q, st[d]) * c1;
-      dTh[d] = d1u(u + F_TH * fs, q, st[d]) * c1;
-    }
     const double iW = 1.0 / W;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -327,16 +449,8 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ u, long
   }
 
   // advection along the shift (upwind) and Kreiss-Oliger dissipation
-  const double cko = prm.sigma_ko / (64.0 * h);
-#pragma unroll 1
-  for (int f = 0; f < NF; ++f) {
-    const double* fp = u + f * fs;
-    const double f0 = __ldg(fp + q);
-    double adv = c.be[0] * dupu(fp, q, st[0], c.be[0], f0) + c.be[1] * dupu(fp, q, st[1], c.be[1], f0) +
-                 c.be[2] * dupu(fp, q, st[2], c.be[2], f0);
-    double ko = delta6(fp, q, st[0], f0) + delta6(fp, q, st[1], f0) + delta6(fp, q, st[2], f0);
-    r[f] += adv * c1 + ko * cko;
-  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) r[f] += S[ST_ADV + f];
   if (prm.shift == 1) {
 #pragma unroll
     for (int f = F_BETX; f < NF; ++f) r[f] = 0.0;
@@ -396,7 +510,8 @@ __device__ __forceinline__ void rk_update(int s, double dt, long long q, long lo
 }
 
 template <int MODE>  // 0: RK stage, 1: RHS only
-__global__ void __launch_bounds__(128) z4c_stage_fp64_kernel(StageArgs A) {
+__global__ void __launch_bounds__(STAGE_THREADS) z4c_stage_fp64_kernel(StageArgs A) {
+  extern __shared__ double stash[];
   const Tile tl = A.tiles[blockIdx.x];
   const DevPatch* P = A.patches + tl.patch;
   const int i = tl.x0 + (threadIdx.x & 31);
@@ -409,7 +524,7 @@ __global__ void __launch_bounds__(128) z4c_stage_fp64_kernel(StageArgs A) {
   const long long q = (i + GH) + (long long)(j + GH) * sy + (long long)(k + GH) * sz;
   const double* __restrict__ u = P->buf[MODE ? ring : stage_in_slot(s, ring)];
   double r[NF];
-  z4c_rhs_point(u, q, sy, sz, fs, P->dx, A.prm, r);
+  z4c_rhs_point(u, q, sy, sz, fs, P->dx, A.prm, Stash{stash + threadIdx.x}, r);
   if (A.prm.matter) {
     // the fluid's terms (Sec. 2.1.2), formed by the matter recovery kernel from
     // this stage's state: Khat, Theta, At_ij, Gamt^i (and B^i through Gamt^i)
@@ -891,10 +1006,18 @@ __global__ void sum_partials_kernel(const double* partial, int nblocks, int widt
 
 void launch_stage_fp64(const StageArgs& a, cudaStream_t st) {
   if (a.ntiles == 0) return;
+  static bool ready[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !ready[dev]) {  // the stash is above the 48 KB default
+    cudaFuncSetAttribute(z4c_stage_fp64_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGE_SMEM);
+    cudaFuncSetAttribute(z4c_stage_fp64_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STAGE_SMEM);
+    ready[dev] = true;
+  }
   if (a.stage == 0)
-    z4c_stage_fp64_kernel<1><<<a.ntiles, 128, 0, st>>>(a);
+    z4c_stage_fp64_kernel<1><<<a.ntiles, STAGE_THREADS, STAGE_SMEM, st>>>(a);
   else
-    z4c_stage_fp64_kernel<0><<<a.ntiles, 128, 0, st>>>(a);
+    z4c_stage_fp64_kernel<0><<<a.ntiles, STAGE_THREADS, STAGE_SMEM, st>>>(a);
 }
 
 void launch_sommerfeld(const GhostArgs& a, int npatches, long long max_shell, cudaStream_t st) {
