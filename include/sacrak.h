@@ -420,10 +420,10 @@ sacrak_status sacrak_set_overlap(sacrak_grid* grid, int on);
  * cold curve), adds the fluid's terms to the Z4c right-hand side (Khat
  * 4 pi alpha (S + rho_H), Theta -8 pi alpha rho_H, At_ij -8 pi alpha W^2
  * [S_ij]^TF, Gamt^i and B^i -16 pi alpha gt^ij J_j), and advances the
- * conserved variables with PPM face states (steep minmod b = 3), HLLE fluxes
- * with the relativistic characteristic speeds, the metric at faces by
- * 4th-order interpolation and the geometric sources (4th-order metric
- * derivatives).  Ghost cells of the fluid: zero gradient (outflow), periodic
+ * conserved variables with PPM face states (steep minmod b = 3), face fluxes
+ * (sacrak_set_riemann: HLLC in the face tetrad by default, or HLLE), the
+ * metric at faces by 4th-order interpolation and the geometric sources
+ * (4th-order metric derivatives).  Ghost cells of the fluid: zero gradient (outflow), periodic
  * with bc = 1.  A "matter array" exchanged with the caller is
  * double[5][NZ][NY][NX] in the patch-array layout above.  The stepping calls
  * return SACRAK_ESTATE until sacrak_upload_matter has run. */
@@ -441,6 +441,18 @@ sacrak_status sacrak_set_eos(sacrak_grid* grid, int npieces, double K0, const do
  * radius r_atm, falling as r^-3 outside (the paper: 1e-12 of the maximum
  * density within eight times the finest domain). */
 sacrak_status sacrak_set_atmosphere(sacrak_grid* grid, double rho_atm, double r_atm);
+
+/* Face flux of the fluid (Sec. 2.2).  solver = 0 (the default): the HLLC
+ * flux of special relativity (Mignone & Bodo 2005) solved in an orthonormal
+ * tetrad in which the face is at rest (e1 along the gradient of the face
+ * coordinate, e0 the Eulerian observer projected onto the face), with the
+ * HLLE flux there where the intermediate state is unphysical (no real
+ * contact speed, a contact speed outside the outer waves or not below light
+ * speed, a non-positive intermediate pressure), transformed back to the
+ * coordinate frame.  solver = 1: the HLLE flux in the coordinate frame with
+ * the relativistic characteristic speeds.  SACRAK_EINVAL for other values or
+ * a grid without a fluid.  Drops the recorded coarse-step graph. */
+sacrak_status sacrak_set_riemann(sacrak_grid* grid, int solver);
 
 /* Primitives of one patch (a matter array, ghosts included, host or device
  * memory) into the current time level; the conserved variables are formed

@@ -24,11 +24,14 @@ vectorised over the grid, one operation of the method after the other:
   with S^{jk} = rho h u^j u^k + P gamma^{jk}, u^j = gamma^{jk} u_k.
 * Finite volume (Sec. 2.2): the primitives are reconstructed at the cell
   faces with PPM (Colella & Woodward 1984) whose slopes are limited by the
-  steep minmod with b = 3; the face flux is the HLLE flux with the
-  relativistic characteristic speeds of the face states; the metric at a
-  face is the 4th-order Lagrange interpolation (-1, 9, 9, -1)/16 of the
-  cell values; the metric derivatives of the sources are the 4th-order
-  centred differences of the spacetime.
+  steep minmod with b = 3; the face flux is the HLLC flux of special
+  relativity (Mignone & Bodo 2005) solved in an orthonormal tetrad in which
+  the face is at rest, with the HLLE flux there where the intermediate state
+  is unphysical, transformed back to the coordinate frame (an HLLE flux in
+  the coordinate frame is kept as an option); the metric at a face is the
+  4th-order Lagrange interpolation (-1, 9, 9, -1)/16 of the cell values; the
+  metric derivatives of the sources are the 4th-order centred differences
+  of the spacetime.
 * Primitive recovery (Sec. 2.2): Newton-Raphson on w.  With rho = D/w and
   h = (rho_H + P)/(D w), the hybrid EOS gives P as an explicit function of
   w, P(w) = [P_cold + (G-1)(rho_H/w^2 - (D/w)(1 + eps_cold))] /
@@ -44,9 +47,11 @@ vectorised over the grid, one operation of the method after the other:
   d_t Gamt^i -= 16 pi alpha gt^ij S_j (and B^i through Gamt^i), and the
   constraints H -= 16 pi rho_ADM, M_i -= 8 pi S_i.
 
-Readings where the paper is silent are listed in the design notes: the HLLE
-flux in the coordinate frame (the paper solves an HLLC problem in a tetrad
-frame and falls back to HLLE), no PPM contact steepening or flattening, the
+Readings where the paper is silent are listed in the design notes: the
+tetrad (e1 along the gradient of the face coordinate, e0 the Eulerian
+observer projected onto the face), the HLLE fallback also where the contact
+speed has no real root or leaves the outer waves, no PPM contact steepening
+or flattening, the
 repair eps -> eps_cold when the recovered thermal energy is negative,
 outflow (zero-gradient) ghost cells on the outer boundary.
 """
@@ -353,6 +358,150 @@ def hlle_flux(pl, pr, m, eos, d):
     return (ap[None] * fl - am[None] * fr + (ap * am)[None] * (ur - ul)) / den[None]
 
 
+# ------------------------------------------------------------------ HLLC in a tetrad frame
+
+def _dot4(m, a, b):
+    """g_{mu nu} a^mu b^nu of contravariant 4-vectors (4, ...)."""
+    al, be, g = m["alpha"], m["beta"], m["g_ll"]
+    bl = np.array([sum(g[SYM[i][j]] * be[j] for j in range(3)) for i in range(3)])
+    g00 = -al * al + (bl * be).sum(axis=0)
+    out = g00 * a[0] * b[0]
+    for i in range(3):
+        out = out + bl[i] * (a[0] * b[1 + i] + a[1 + i] * b[0])
+        for j in range(3):
+            out = out + g[SYM[i][j]] * a[1 + i] * b[1 + j]
+    return out
+
+
+def face_tetrad(m, d):
+    """Orthonormal tetrad at faces normal to x^d (Sec. 2.2: the Riemann
+    problem is solved in a local Minkowski frame).  e1 is the unit vector
+    along the spacetime gradient of x^d, g^{mu d} / sqrt(g^{dd}); e0 is the
+    Eulerian observer n projected onto the face's world-sheet x^d = const and
+    normalised; e2, e3 are the two coordinate directions along the face made
+    orthonormal to e0 (and e2) by Gram-Schmidt.  e0, e2, e3 are tangent to
+    the world-sheet, so the face is at rest in this frame.  Returns
+    (e (4 vectors, each (4, ...)), sqrt(g^dd))."""
+    al, be, gu = m["alpha"], m["beta"], m["g_uu"]
+    one, zero = np.ones_like(al), np.zeros_like(al)
+    gdd = gu[SYM[d][d]] - be[d] ** 2 / al ** 2
+    s1 = np.sqrt(gdd)
+    xi = np.array([be[d] / al ** 2] + [gu[SYM[i][d]] - be[i] * be[d] / al ** 2 for i in range(3)])
+    e1 = xi / s1
+    n = np.array([1.0 / al] + [-be[i] / al for i in range(3)])
+    c = -be[d] / al / s1  # n . e1
+    e0 = (n - c * e1) / np.sqrt(1.0 + c * c)
+    es = []
+    for k, a in enumerate(((d + 1) % 3, (d + 2) % 3)):
+        v = np.array([zero] + [one if i == a else zero for i in range(3)])
+        v = v + _dot4(m, v, e0) * e0
+        for q in es:
+            v = v - _dot4(m, v, q) * q
+        es.append(v / np.sqrt(_dot4(m, v, v)))
+    return [e0, e1, es[0], es[1]], s1
+
+
+def _sr_state(prim, m, eos, e):
+    """Special-relativistic state in the tetrad frame: conserved (D, S_1,
+    S_2, S_3, E) with E = rho h W^2 - P, the flux along 1, the speeds along
+    1 and (v_1, P)."""
+    rho, eps, ul = prim[0], prim[1], prim[2:5]
+    al, be = m["alpha"], m["beta"]
+    uu = _raise(m["g_uu"], ul)
+    w = np.sqrt(1.0 + (ul * uu).sum(axis=0))
+    u_low = np.array([-al * w + (be * ul).sum(axis=0)] + [ul[i] for i in range(3)])  # u_mu
+    comp = [(e[a] * u_low).sum(axis=0) for a in range(4)]
+    Wt = -comp[0]
+    v = [comp[a] / Wt for a in (1, 2, 3)]
+    P = eos.pressure(rho, eps)
+    h = 1.0 + eps + P / rho
+    U = np.array([rho * Wt, rho * h * Wt * Wt * v[0], rho * h * Wt * Wt * v[1], rho * h * Wt * Wt * v[2],
+                  rho * h * Wt * Wt - P])
+    F = U * v[0]
+    F[1] = F[1] + P
+    F[4] = U[1]
+    v2 = v[0] ** 2 + v[1] ** 2 + v[2] ** 2
+    cs2 = eos.cs2(rho, eps)
+    root = np.sqrt(np.maximum(cs2 * (1.0 - v2) * (1.0 - v2 * cs2 - v[0] ** 2 * (1.0 - cs2)), 0.0))
+    lp = (v[0] * (1.0 - cs2) + root) / (1.0 - v2 * cs2)
+    lm = (v[0] * (1.0 - cs2) - root) / (1.0 - v2 * cs2)
+    return U, F, lp, lm, v[0], P
+
+
+def sr_hllc(UL, FL, lpl, lml, vL, PL, UR, FR, lpr, lmr, vR, PR):
+    """HLLC flux of special-relativistic hydrodynamics across an interface at
+    rest (Mignone & Bodo 2005), with the HLLE flux where the intermediate
+    state is unphysical (Sec. 2.2: a negative intermediate pressure or a
+    superluminal contact speed; also no real contact speed or one outside the
+    outer waves).  Variables (D, S_1, S_2, S_3, E), E the total energy
+    density.  Returns (flux, hllc_used)."""
+    lL = np.minimum(lml, lmr)
+    lR = np.maximum(lpl, lpr)
+    den = lR - lL
+    Uh = (lR * UR - lL * UL + FL - FR) / den
+    Fh = (lR * FL - lL * FR + lL * lR * (UR - UL)) / den
+    # contact speed: F_E^hll l^2 - (E^hll + F_S1^hll) l + S1^hll = 0, the root
+    # that stays finite as F_E^hll -> 0
+    b = Uh[4] + Fh[1]
+    disc = b * b - 4.0 * Fh[4] * Uh[1]
+    ls = 2.0 * Uh[1] / (b + np.sqrt(np.maximum(disc, 0.0)))
+    ps = Fh[1] - ls * Fh[4]
+    ok = (disc >= 0.0) & (ps > 0.0) & (np.abs(ls) < 1.0) & (ls > lL) & (ls < lR)
+
+    def star(U, F, lK, vK, PK):
+        r = 1.0 / (lK - ls)
+        Us = np.array([U[0] * (lK - vK) * r, (U[1] * (lK - vK) + ps - PK) * r, U[2] * (lK - vK) * r,
+                       U[3] * (lK - vK) * r, (U[4] * (lK - vK) + ps * ls - PK * vK) * r])
+        return F + lK * (Us - U)
+
+    FsL = star(UL, FL, lL, vL, PL)
+    FsR = star(UR, FR, lR, vR, PR)
+    hllc = np.where(lL >= 0.0, FL, np.where(ls >= 0.0, FsL, np.where(lR > 0.0, FsR, FR)))
+    hlle = np.where(lL >= 0.0, FL, np.where(lR <= 0.0, FR, Fh))
+    return np.where(ok, hllc, hlle), ok
+
+
+def hllc_tetrad_flux(pl, pr, m, eos, d):
+    """Face flux of the densitised conserved variables (Sec. 2.2): the
+    left and right states in the face tetrad, the special-relativistic HLLC
+    flux there, back to the coordinate frame.  With xi = dx^d and
+    xi . e_a = 0 for a != 1, the coordinate flux needs only the flux row
+    along e1: rho u^d = sqrt(g^dd) F_D and T^d_nu = sqrt(g^dd) [F_E (e0)_nu +
+    sum_j F_Sj (e_j)_nu] ((e)_nu lowered), so with sqrt(-g) = alpha
+    sqrt(gamma):
+        D^   flux: alpha sqrt(gamma) sqrt(g^dd) F_D
+        J^_i flux: alpha sqrt(gamma) sqrt(g^dd) [F_E (e0)_i + sum_j F_Sj (e_j)_i]
+        E^   flux: alpha sqrt(gamma) (-T^d_nu n^nu)
+               = alpha^2 sqrt(gamma) sqrt(g^dd) [F_E e0^t + sum_j F_Sj e_j^t]."""
+    e, s1 = face_tetrad(m, d)
+    UL, FL, lpl, lml, vL, PL = _sr_state(pl, m, eos, e)
+    UR, FR, lpr, lmr, vR, PR = _sr_state(pr, m, eos, e)
+    Ft, _ = sr_hllc(UL, FL, lpl, lml, vL, PL, UR, FR, lpr, lmr, vR, PR)
+    al, be, g = m["alpha"], m["beta"], m["g_ll"]
+    bl = np.array([sum(g[SYM[i][j]] * be[j] for j in range(3)) for i in range(3)])
+    pre = al * m["sqrtg"] * s1
+    rows = [Ft[4], Ft[1], Ft[2], Ft[3]]  # weights of e0, e1, e2, e3
+    out = np.empty_like(Ft)
+    out[0] = pre * Ft[0]
+    for i in range(3):
+        acc = 0.0
+        for a in range(4):
+            low = bl[i] * e[a][0] + sum(g[SYM[i][j]] * e[a][1 + j] for j in range(3))  # (e_a)_i
+            acc = acc + rows[a] * low
+        out[1 + i] = pre * acc
+    out[4] = pre * al * sum(rows[a] * e[a][0] for a in range(4))
+    return out
+
+
+def face_flux(pl, pr, m, eos, d, solver="hllc"):
+    """The face flux of the scheme: "hllc" (Sec. 2.2: HLLC in the face
+    tetrad, HLLE there where the intermediate state is unphysical) or
+    "hlle" (HLLE in the coordinate frame)."""
+    if solver == "hllc":
+        return hllc_tetrad_flux(pl, pr, m, eos, d)
+    return hlle_flux(pl, pr, m, eos, d)
+
+
 # ------------------------------------------------------------------ right-hand sides
 
 def _d1(f, axis, h):
@@ -368,10 +517,10 @@ def _act(p):
     return (slice(g, -g), slice(g, -g), slice(g, -g))
 
 
-def matter_rhs(p, prim, u, eos, b=3.0):
+def matter_rhs(p, prim, u, eos, b=3.0, solver="hllc"):
     """d_t of the densitised conserved variables at the active cells (ghost
-    entries 0): minus the divergence of the HLLE face fluxes plus the
-    geometric sources.  prim (ghosts included) and the Z4c state u give the
+    entries 0): minus the divergence of the face fluxes (`face_flux`) plus
+    the geometric sources.  prim (ghosts included) and the Z4c state u give the
     fluid and the metric."""
     out = np.zeros_like(prim)
     a = _act(p)
@@ -383,7 +532,7 @@ def matter_rhs(p, prim, u, eos, b=3.0):
         pr = np.empty_like(prim)
         for v in range(NP):
             pl[v], pr[v] = ppm_faces(prim[v], ax)
-        F = hlle_flux(pl, pr, mf, eos, d)  # F[..., m] at face m+1/2
+        F = face_flux(pl, pr, mf, eos, d, solver)  # F[..., m] at face m+1/2
         Fm = np.roll(F, 1, axis=ax + 1)    # face m-1/2 at cell m
         div = (F - Fm) / h
         out[(slice(None),) + a] -= div[(slice(None),) + a]
@@ -484,7 +633,7 @@ def periodic_ghosts(p, prim):
     return out
 
 
-def rk4_step_cowling(p, cons, u, dt, eos, floor, b=3.0, bc="outflow"):
+def rk4_step_cowling(p, cons, u, dt, eos, floor, b=3.0, bc="outflow", solver="hllc"):
     """One classical RK4 step of the matter on the fixed spacetime u
     (Cowling approximation), primitives recovered after every stage update
     (Sec. 2.2) and outflow (or periodic) ghosts.  Returns (cons, prim) of
@@ -497,12 +646,12 @@ def rk4_step_cowling(p, cons, u, dt, eos, floor, b=3.0, bc="outflow"):
 
     a = (slice(None),) + _act(p)
     pr, c0 = prims(cons)
-    k = matter_rhs(p, pr, u, eos, b)
+    k = matter_rhs(p, pr, u, eos, b, solver)
     y = c0 + dt / 6.0 * k
     cs = c0 + 0.5 * dt * k
     for s, (cw, bw) in enumerate([(0.5, 1.0 / 3.0), (1.0, 1.0 / 3.0), (None, 1.0 / 6.0)]):
         pr, cs = prims(cs)
-        k = matter_rhs(p, pr, u, eos, b)
+        k = matter_rhs(p, pr, u, eos, b, solver)
         if cw is None:
             new = y + bw * dt * k
         else:
@@ -516,7 +665,7 @@ def rk4_step_cowling(p, cons, u, dt, eos, floor, b=3.0, bc="outflow"):
     return out, pr
 
 
-def rk4_step_coupled(p, u, cons, dt, eos, floor, prm, bc="sommerfeld", b=3.0):
+def rk4_step_coupled(p, u, cons, dt, eos, floor, prm, bc="sommerfeld", b=3.0, solver="hllc"):
     """One classical RK4 step of the Z4c spacetime and the matter together
     (method of lines, Sec. 2.2): at every stage the primitives are recovered
     from the stage's conserved variables (atmosphere applied, outflow or
@@ -549,7 +698,7 @@ def rk4_step_coupled(p, u, cons, dt, eos, floor, prm, bc="sommerfeld", b=3.0):
         src = z4c_matter_rhs(pr, cur, eos, frozen_shift=prm.shift == 1)
         out = np.empty_like(un)
         z4c.rk4_stage(p, prm, s, dt, bc == "sommerfeld", cur, un, y, out, src)
-        km = matter_rhs(p, pr, cur, eos, b)
+        km = matter_rhs(p, pr, cur, eos, b, solver)
         nxt = cs.copy()
         if s == 1:
             ym[a] = c0[a] + bw[0] * dt * km[a]

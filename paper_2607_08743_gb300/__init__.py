@@ -33,7 +33,7 @@ EXPORTS = [
     "sacrak_track_punctures", "sacrak_get_punctures", "sacrak_move_patch", "sacrak_regrid",
     "sacrak_patch_origin", "sacrak_psi4_modes", "sacrak_nakano", "sacrak_ffi_work_bytes", "sacrak_ffi_strain",
     "sacrak_set_wait_limit", "sacrak_set_eos", "sacrak_set_atmosphere", "sacrak_upload_matter",
-    "sacrak_download_matter", "sacrak_matter_rhs", "sacrak_set_overlap",
+    "sacrak_download_matter", "sacrak_matter_rhs", "sacrak_set_overlap", "sacrak_set_riemann",
 ]
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
             L.sacrak_set_stage_kernel.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             L.sacrak_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
             L.sacrak_set_overlap.argtypes = [vp, ctypes.c_int]
+            L.sacrak_set_riemann.argtypes = [vp, ctypes.c_int]
             L.sacrak_set_eos.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_double]
             L.sacrak_set_atmosphere.argtypes = [vp, ctypes.c_double, ctypes.c_double]
             L.sacrak_upload_matter.argtypes = [vp, ctypes.c_int, vp]
@@ -342,6 +343,15 @@ class Grid:
         g = (ctypes.c_double * len(gammas))(*[float(v) for v in gammas])
         b = (ctypes.c_double * max(1, len(rho_bounds)))(*[float(v) for v in rho_bounds])
         self._check(lib().sacrak_set_eos(self._h, len(gammas), float(K0), g, b, float(gamma_th)), "set_eos")
+
+    def set_riemann(self, solver: str = "hllc"):
+        """Face flux of the fluid: "hllc" (HLLC in the face tetrad, HLLE
+        where its intermediate state is unphysical; the default) or "hlle"
+        (HLLE in the coordinate frame)."""
+        code = {"hllc": 0, "hlle": 1}.get(solver)
+        if code is None:
+            raise SacrakError(EINVAL, "solver must be 'hllc' or 'hlle'")
+        self._check(lib().sacrak_set_riemann(self._h, code), "set_riemann")
 
     def set_atmosphere(self, rho_atm: float, r_atm: float):
         self._check(lib().sacrak_set_atmosphere(self._h, float(rho_atm), float(r_atm)), "set_atmosphere")

@@ -184,6 +184,7 @@ struct sacrak_grid {
   bool eos_set = false;
   bool matter_ready = false;  // primitives uploaded
   double rho_atm = 0.0, r_atm = 0.0;
+  int riemann = 0;  // face flux of the fluid: 0 HLLC in the face tetrad, 1 HLLE (sacrak_set_riemann)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   size_t ev_used = 0;
   long long prof_zones = 0;
@@ -631,6 +632,7 @@ MatterArgs matter_args(const sacrak_grid* g, int pid, int stage, double dt) {
   a.periodic = g->prm.bc == 1;
   a.stage = stage;
   a.coupled = 1;
+  a.riemann = g->riemann;
   a.dt = dt;
   a.out = nullptr;
   a.err = g->d_err;
@@ -1373,6 +1375,15 @@ sacrak_status sacrak_set_atmosphere(sacrak_grid* g, double rho_atm, double r_atm
     return fail(g, SACRAK_EINVAL, "atmosphere density and radius must be positive");
   g->rho_atm = rho_atm;
   g->r_atm = r_atm;
+  drop_graph(g);
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_set_riemann(sacrak_grid* g, int solver) {
+  if (!g) return SACRAK_EINVAL;
+  if (!g->prm.matter) return fail(g, SACRAK_EINVAL, "grid created without a fluid (params.matter = 0)");
+  if (solver != 0 && solver != 1) return fail(g, SACRAK_EINVAL, "Riemann solver must be 0 (HLLC) or 1 (HLLE)");
+  g->riemann = solver;
   drop_graph(g);
   return SACRAK_OK;
 }

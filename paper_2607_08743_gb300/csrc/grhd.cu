@@ -14,9 +14,13 @@
 //    d_j alpha), S^jk = rho h u^j u^k + P gamma^jk.
 //  - Faces: PPM (Colella & Woodward) edge values with slopes limited by the
 //    steep minmod of parameter b = 3, metric by the 4th-order Lagrange
-//    interpolation (-1, 9, 9, -1)/16, HLLE flux with the relativistic
-//    characteristic speeds; metric derivatives of the sources by the
-//    4th-order centred differences.
+//    interpolation (-1, 9, 9, -1)/16; the face flux is the HLLC flux of
+//    special relativity (Mignone & Bodo 2005) in an orthonormal tetrad in
+//    which the face is at rest, with the HLLE flux there where the
+//    intermediate state is unphysical, or (MatterArgs::riemann = 1) the
+//    HLLE flux in the coordinate frame with the relativistic characteristic
+//    speeds; metric derivatives of the sources by the 4th-order centred
+//    differences.
 //  - Recovery: Newton-Raphson on w with the hybrid EOS solved for P(w) in
 //    closed form, f(w) = w - (rho_H + P) / sqrt((rho_H + P)^2 - S^2), the
 //    previous recovery's w as the guess and a bisection bracket; a negative
@@ -409,6 +413,167 @@ __device__ __forceinline__ void phys_flux(const DevEOS& e, const Met& m, const d
   lm = pre * (vd * (1.0 - cs2) - root) - m.be[d];
 }
 
+// ------------------------------------------------------------------ HLLC in the face tetrad
+
+// Orthonormal tetrad at a face normal to x^d: e1 along the spacetime gradient
+// of x^d (g^{mu d} / sqrt(g^dd)), e0 the Eulerian observer n projected onto
+// the face's world-sheet x^d = const and normalised, e2 and e3 the two
+// coordinate directions along the face made orthonormal to e0 (and e2).
+// e0, e2, e3 are tangent to the world-sheet: the face is at rest in the frame.
+struct Tetrad {
+  double e[4][4];  // e[a][mu], contravariant
+  double lo[4][3]; // (e_a)_i, the spatial components lowered with the 4-metric
+  double s1;       // sqrt(g^dd)
+};
+
+// The Gram-Schmidt steps in closed form: with p0 = (e0)_a and q0 = (e0)_b
+// (a, b the face's directions), e2 = (d_a + p0 e0) / N2 with N2^2 = g_aa +
+// p0^2 (e0 . e0 = -1), e3 = (d_b + q0 e0 - p2 e2) / N3 with p2 = (g_ab + p0
+// q0) / N2 and N3^2 = g_bb + q0^2 - p2^2.  Lowered: (e1)_i = delta^d_i / s1
+// and (e0)_i = -c / (s1 sqrt(1 + c^2)) delta^d_i (n_i = 0), so p0 = q0 = 0.
+template <int d>
+__device__ __forceinline__ void face_tetrad(const Met& m, Tetrad& T) {
+  constexpr int a = (d + 1) % 3, b = (d + 2) % 3;
+  const double ia2 = 1.0 / (m.al * m.al);
+  T.s1 = sqrt(m.gu[S2(d, d)] - m.be[d] * m.be[d] * ia2);
+  const double is1 = 1.0 / T.s1;
+  double* e0 = T.e[0];
+  double* e1 = T.e[1];
+  e1[0] = m.be[d] * ia2 * is1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) e1[1 + i] = (m.gu[S2(i, d)] - m.be[i] * m.be[d] * ia2) * is1;
+  const double c = -m.be[d] / m.al * is1;  // n . e1
+  const double ic = 1.0 / sqrt(1.0 + c * c);
+  e0[0] = (1.0 / m.al - c * e1[0]) * ic;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) e0[1 + i] = (-m.be[i] / m.al - c * e1[1 + i]) * ic;
+  const double e0d = -c * is1 * ic;  // (e0)_d, the only spatial lowered component
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T.lo[0][i] = (i == d) ? e0d : 0.0;
+    T.lo[1][i] = (i == d) ? is1 : 0.0;
+  }
+  const double iN2 = 1.0 / sqrt(m.g[S2(a, a)]);
+  const double p2 = m.g[S2(a, b)] * iN2;
+  const double iN3 = 1.0 / sqrt(m.g[S2(b, b)] - p2 * p2);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const double e2 = (mu == 1 + a ? 1.0 : 0.0) * iN2;
+    T.e[2][mu] = e2;
+    T.e[3][mu] = ((mu == 1 + b ? 1.0 : 0.0) - p2 * e2) * iN3;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double l2 = m.g[S2(a, i)] * iN2;
+    T.lo[2][i] = l2;
+    T.lo[3][i] = (m.g[S2(b, i)] - p2 * l2) * iN3;
+  }
+}
+
+// special-relativistic state in the tetrad frame: conserved (D, S_1, S_2,
+// S_3, E = rho h W^2 - P), flux along 1, speeds along 1, v_1 and P
+__device__ __forceinline__ void sr_state(const DevEOS& e, const Met& m, const Tetrad& T, const double pr[NM],
+                                         double U[5], double F[5], double& lp, double& lm, double& v1,
+                                         double& P) {
+  double Pc, ec, dPc;
+  eos_cold(e, pr[0], Pc, ec, dPc);
+  P = Pc + (e.gth - 1.0) * pr[0] * (pr[1] - ec);
+  const double irho = 1.0 / pr[0];
+  const double h = 1.0 + pr[1] + P * irho;
+  const double ul[3] = {pr[2], pr[3], pr[4]};
+  double uu[3];
+  raise3(m.gu, ul, uu);
+  const double w = sqrt(1.0 + ul[0] * uu[0] + ul[1] * uu[1] + ul[2] * uu[2]);
+  const double u0 = -m.al * w + m.be[0] * ul[0] + m.be[1] * ul[1] + m.be[2] * ul[2];  // u_t
+  double comp[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+    comp[a] = T.e[a][0] * u0 + T.e[a][1] * ul[0] + T.e[a][2] * ul[1] + T.e[a][3] * ul[2];
+  const double Wt = -comp[0], iW = 1.0 / Wt;
+  const double v[3] = {comp[1] * iW, comp[2] * iW, comp[3] * iW};
+  const double rhw2 = pr[0] * h * Wt * Wt;
+  U[0] = pr[0] * Wt;
+  U[1] = rhw2 * v[0];
+  U[2] = rhw2 * v[1];
+  U[3] = rhw2 * v[2];
+  U[4] = rhw2 - P;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) F[f] = U[f] * v[0];
+  F[1] += P;
+  F[4] = U[1];
+  const double g1 = e.gth - 1.0;
+  const double cs2 = (dPc + g1 * (pr[1] - ec) - g1 * Pc * irho + P * irho * g1) / h;
+  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const double root = sqrt(fmax(cs2 * (1.0 - v2) * (1.0 - v2 * cs2 - v[0] * v[0] * (1.0 - cs2)), 0.0));
+  const double id = 1.0 / (1.0 - v2 * cs2);
+  lp = (v[0] * (1.0 - cs2) + root) * id;
+  lm = (v[0] * (1.0 - cs2) - root) * id;
+  v1 = v[0];
+}
+
+// HLLC flux across an interface at rest (Mignone & Bodo 2005), the HLLE flux
+// where the intermediate state is unphysical: no real contact speed, a
+// contact speed outside the outer waves or not below light speed, or a
+// non-positive intermediate pressure
+__device__ __forceinline__ void sr_hllc(const double UL[5], const double FL[5], double lpl, double lml, double vL,
+                                        double PL, const double UR[5], const double FR[5], double lpr, double lmr,
+                                        double vR, double PR, double out[5]) {
+  const double lL = fmin(lml, lmr), lR = fmax(lpl, lpr);
+  if (lL >= 0.0) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) out[f] = FL[f];
+    return;
+  }
+  if (lR <= 0.0) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) out[f] = FR[f];
+    return;
+  }
+  const double iden = 1.0 / (lR - lL);
+  double Uh[5], Fh[5];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    Uh[f] = (lR * UR[f] - lL * UL[f] + FL[f] - FR[f]) * iden;
+    Fh[f] = (lR * FL[f] - lL * FR[f] + lL * lR * (UR[f] - UL[f])) * iden;
+  }
+  const double b = Uh[4] + Fh[1];
+  const double disc = b * b - 4.0 * Fh[4] * Uh[1];
+  const double ls = 2.0 * Uh[1] / (b + sqrt(fmax(disc, 0.0)));
+  const double ps = Fh[1] - ls * Fh[4];
+  if (!(disc >= 0.0 && ps > 0.0 && fabs(ls) < 1.0 && ls > lL && ls < lR)) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) out[f] = Fh[f];
+    return;
+  }
+  const bool left = ls >= 0.0;
+  const double* U = left ? UL : UR;
+  const double* F = left ? FL : FR;
+  const double lK = left ? lL : lR, vK = left ? vL : vR, PK = left ? PL : PR;
+  const double r = 1.0 / (lK - ls), a = lK - vK;
+  const double Us[5] = {U[0] * a * r, (U[1] * a + ps - PK) * r, U[2] * a * r, U[3] * a * r,
+                        (U[4] * a + ps * ls - PK * vK) * r};
+#pragma unroll
+  for (int f = 0; f < 5; ++f) out[f] = F[f] + lK * (Us[f] - U[f]);
+}
+
+// Coordinate-frame flux of the densitised conserved variables from the
+// tetrad-frame flux row Ft = (F_D, F_S1, F_S2, F_S3, F_E): with xi = dx^d and
+// xi . e_a = 0 for a != 1, rho u^d = sqrt(g^dd) F_D and T^d_nu = sqrt(g^dd)
+// [F_E (e0)_nu + sum_j F_Sj (e_j)_nu], so (sqrt(-g) = alpha sqrt(gamma))
+// D^: alpha sqrt(gamma) sqrt(g^dd) F_D; J^_i: alpha sqrt(gamma) sqrt(g^dd)
+// [F_E (e0)_i + sum_j F_Sj (e_j)_i]; E^ (alpha sqrt(gamma) times -T^d_nu n^nu):
+// alpha^2 sqrt(gamma) sqrt(g^dd) [F_E e0^t + sum_j F_Sj e_j^t].
+__device__ __forceinline__ void tetrad_to_coordinate(const Met& m, const Tetrad& T, const double Ft[5],
+                                                     double out[NM]) {
+  const double pre = m.al * m.sg * T.s1;
+  const double rows[4] = {Ft[4], Ft[1], Ft[2], Ft[3]};
+  out[0] = pre * Ft[0];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    out[1 + i] = pre * (rows[0] * T.lo[0][i] + rows[1] * T.lo[1][i] + rows[2] * T.lo[2][i] + rows[3] * T.lo[3][i]);
+  out[4] = pre * m.al * (rows[0] * T.e[0][0] + rows[1] * T.e[1][0] + rows[2] * T.e[2][0] + rows[3] * T.e[3][0]);
+}
+
 // one thread per face: faces m+1/2 along dir for m = 2 .. n+2 (array index),
 // the other axes over active cells; flux stored at cell m
 template <int dir>
@@ -459,6 +624,18 @@ __global__ void __launch_bounds__(128) matter_flux_kernel(MatterArgs A) {
       ppm_face(v, pl[f], pr[f]);
     }
     double UL[NM], FL[NM], UR[NM], FR[NM], lpl, lml, lpr, lmr;
+    if (A.riemann == 0) {
+      Tetrad T;
+      face_tetrad<dir>(mf, T);
+      double vL, PL, vR, PR, Ft[5], out[NM];
+      sr_state(A.eos, mf, T, pl, UL, FL, lpl, lml, vL, PL);
+      sr_state(A.eos, mf, T, pr, UR, FR, lpr, lmr, vR, PR);
+      sr_hllc(UL, FL, lpl, lml, vL, PL, UR, FR, lpr, lmr, vR, PR, Ft);
+      tetrad_to_coordinate(mf, T, Ft, out);
+#pragma unroll
+      for (int f = 0; f < NM; ++f) flux[f * A.fs + q] = out[f];
+      continue;
+    }
     phys_flux<dir>(A.eos, mf, pl, UL, FL, lpl, lml);
     phys_flux<dir>(A.eos, mf, pr, UR, FR, lpr, lmr);
     const double ap = fmax(0.0, fmax(lpl, lpr)), am = fmin(0.0, fmin(lml, lmr));

@@ -5,7 +5,10 @@
 // the hybrid EOS (piecewise polytrope + thermal part), evolved with the
 // spacetime by the same RK4 stages (Sec. 2.2): PPM (steep minmod b = 3) +
 // HLLE face fluxes, geometric sources, Newton-Raphson recovery on the
-// Lorentz factor w, atmosphere floor.  FP64 throughout.
+// Lorentz factor w, atmosphere floor.  FP64 throughout.  (Face fluxes:
+// HLLC of special relativity in an orthonormal tetrad in which the face is
+// at rest, HLLE there where the intermediate state is unphysical; or HLLE
+// in the coordinate frame.)
 #pragma once
 #include "sacrak_dev.cuh"
 
@@ -34,6 +37,7 @@ struct MatterArgs {
   int periodic;               // ghost cells: 0 outflow (zero gradient), 1 periodic
   int stage;                  // 1..4 RK stage; 5: the new level after stage 4; 0: current level
   int coupled;                // write the Z4c matter terms (spacetime evolved with the fluid)
+  int riemann;                // face flux: 0 HLLC in the face tetrad (HLLE fallback), 1 HLLE in the coordinate frame
   double dt;
   double* out;                // update kernel with stage 0: d_t of the conserved variables
   unsigned* err;
@@ -45,7 +49,7 @@ struct MatterArgs {
 void launch_matter_prep(const MatterArgs& a, cudaStream_t st);
 // ghost cells of the primitive arrays
 void launch_matter_ghosts(const MatterArgs& a, cudaStream_t st);
-// HLLE face fluxes along dir (0, 1, 2) from the PPM states
+// face fluxes along dir (0, 1, 2) from the PPM states (MatterArgs::riemann)
 void launch_matter_flux(const MatterArgs& a, int dir, cudaStream_t st);
 // flux divergence + sources: RK4 stage update (stage 1..4) or d_t (stage 0)
 void launch_matter_update(const MatterArgs& a, cudaStream_t st);

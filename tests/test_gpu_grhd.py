@@ -1,9 +1,11 @@
 """GPU parity of the matter sector (Sec. 2.1.2, 2.2) with the oracle
 (oracle/grhd.py), through the C ABI, FP64:
 
-* the conserved-variable right-hand side (PPM + HLLE face fluxes, geometric
+* the conserved-variable right-hand side (PPM + face fluxes, geometric
   sources) on generic curved metric and fluid data and on a TOV star,
-  ragged patch sizes included;
+  ragged patch sizes included, with both face fluxes: HLLC in the face
+  tetrad (the default) and HLLE in the coordinate frame;
+* a contact discontinuity at rest, which HLLC keeps exactly;
 * the recovery of the primitives with the atmosphere (cells below the floor
   reset to rest);
 * the Z4c right-hand side with the fluid's terms;
@@ -98,8 +100,9 @@ def _upload(g, u, prim, rho_atm, r_atm):
     g.upload_matter(0, prim)
 
 
+@pytest.mark.parametrize("solver", ["hllc", "hlle"])
 @pytest.mark.parametrize("n", [(16, 16, 16), (18, 12, 10)])
-def test_matter_rhs_generic(n):
+def test_matter_rhs_generic(n, solver):
     p0, u0, prim0 = _generic(32)  # the ragged patch is cut from the 32^3 data
     p = idd.Patch(n=n, dx=p0.dx, origin=p0.origin)
     sl = (slice(None), slice(0, n[2] + 6), slice(0, n[1] + 6), slice(0, n[0] + 6))
@@ -107,10 +110,11 @@ def test_matter_rhs_generic(n):
     prim = np.ascontiguousarray(prim0[sl])
     floor = np.full(p.shape[1:], 1e-12 * 3e-3)
     g = _grid(p, bc=2)
+    g.set_riemann(solver)
     _upload(g, u, prim, 1e-12 * 3e-3, 1e3)
     r = g.matter_rhs(0)
     cons, pr = _oracle_state(p, u, prim, floor)
-    ro = grhd.matter_rhs(p, pr, u, _eos())
+    ro = grhd.matter_rhs(p, pr, u, _eos(), solver=solver)
     e = _rel(r, ro)
     assert e.max() <= 1e-11, e
     assert np.all(r[:, :3] == 0.0) and np.all(r[:, :, :, -3:] == 0.0)
@@ -120,13 +124,15 @@ def test_matter_rhs_generic(n):
     g.close()
 
 
-def test_matter_rhs_tov():
+@pytest.mark.parametrize("solver", ["hllc", "hlle"])
+def test_matter_rhs_tov(solver):
     p, u, prim, floor = _tov(32)
     g = _grid(p, bc=0)
+    g.set_riemann(solver)
     _upload(g, u, prim, 1e-12 * 1.28e-3, 8 * 24.0)
     r = g.matter_rhs(0)
     cons, pr = _oracle_state(p, u, prim, floor)
-    ro = grhd.matter_rhs(p, pr, u, _eos())
+    ro = grhd.matter_rhs(p, pr, u, _eos(), solver=solver)
     # at rest D and E fluxes are numerical dissipation only: scale per field
     e = _rel(r, ro)
     assert e.max() <= 1e-10, e
@@ -231,6 +237,30 @@ def test_coupled_steps_density_wave_periodic():
     assert em[0] <= 1e-9 and em[2] <= 1e-9, em
 
 
+def test_contact_at_rest_is_stationary_with_hllc():
+    """A density step at rest with uniform pressure on flat space: HLLC in the
+    face tetrad resolves the contact, so the fluid's right-hand side is zero
+    to rounding; with HLLE the density diffuses."""
+    n = 16
+    p = idd.centred_patch(n, 1.0 / n)
+    u = idd.minkowski(p)
+    gas = dict(K0=0.0, gammas=[2.0], gamma_th=5.0 / 3.0)
+    prim = np.zeros((5,) + p.shape[1:])
+    prim[0] = np.where(np.abs(p.axis(0)) < 0.25, 2.0, 1.0)[None, None, :]
+    prim[1] = 1.0 / ((5.0 / 3.0 - 1.0) * prim[0])
+    out = {}
+    for solver in ("hllc", "hlle"):
+        g = sk.Grid(1, p.dx, [p], sk.Params(matter=1, bc=1))
+        g.set_eos(gas["K0"], gas["gammas"], (), gas["gamma_th"])
+        g.set_riemann(solver)
+        _upload(g, u, prim, 1e-12, 1e3)
+        out[solver] = g.matter_rhs(0)
+        g.close()
+    assert np.abs(out["hllc"][[0, 2, 3, 4]]).max() <= 1e-13
+    assert np.abs(out["hllc"][1]).max() <= 1e-12
+    assert np.abs(out["hlle"][0]).max() > 1e-2
+
+
 def test_matter_arguments_rejected():
     p = idd.centred_patch(8, 1.0)
     g = sk.Grid(1, p.dx, [p], sk.Params())
@@ -244,6 +274,8 @@ def test_matter_arguments_rejected():
         m.set_eos(100.0, [0.9])          # index <= 1
     with pytest.raises(sk.SacrakError):
         m.set_atmosphere(-1.0, 1.0)
+    with pytest.raises(sk.SacrakError):
+        m._check(sk.lib().sacrak_set_riemann(m._h, 2), "set_riemann")
     with pytest.raises(sk.SacrakError):
         m.upload_matter(0, np.zeros((5, 3, 3, 3)))
     m.close()
