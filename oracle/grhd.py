@@ -517,10 +517,11 @@ def _act(p):
     return (slice(g, -g), slice(g, -g), slice(g, -g))
 
 
-def matter_rhs(p, prim, u, eos, b=3.0, solver="hllc"):
+def matter_rhs(p, prim, u, eos, b=3.0, solver="hllc", fluxes_out=None):
     """d_t of the densitised conserved variables at the active cells (ghost
     entries 0): minus the divergence of the face fluxes (`face_flux`) plus
-    the geometric sources.  prim (ghosts included) and the Z4c state u give the
+    the geometric sources.  fluxes_out (a list) receives the face fluxes of
+    every direction, F[..., m] at face m+1/2 along that direction.  prim (ghosts included) and the Z4c state u give the
     fluid and the metric."""
     out = np.zeros_like(prim)
     a = _act(p)
@@ -533,6 +534,8 @@ def matter_rhs(p, prim, u, eos, b=3.0, solver="hllc"):
         for v in range(NP):
             pl[v], pr[v] = ppm_faces(prim[v], ax)
         F = face_flux(pl, pr, mf, eos, d, solver)  # F[..., m] at face m+1/2
+        if fluxes_out is not None:
+            fluxes_out.append(F)
         Fm = np.roll(F, 1, axis=ax + 1)    # face m-1/2 at cell m
         div = (F - Fm) / h
         out[(slice(None),) + a] -= div[(slice(None),) + a]

@@ -1,0 +1,409 @@
+"""CPU FP64 oracle of the matter sector on the Berger-Oliger hierarchy --
+test infrastructure only (the tests use it; the product library never
+does).
+
+Written from the paper's description of its mesh refinement for the fluid
+(Sec. 2.2.1), with the hierarchy, the time levels and the spacetime's
+prolongation, restriction and time interpolation of the oracle's
+BOHierarchy (oracle/__init__.py):
+
+* Prolongation of the fluid onto a child's ghost cells (the 3-cell
+  refinement boundary): the conserved rest-mass density, densitised
+  D^ = sqrt(gamma) rho w, by a conservative fifth-order WENO interpolation
+  (Jiang & Shu smoothness indicators on the three 3-cell stencils, applied
+  along x, then y, then z; the two children of a parent cell average to
+  it); eps and u_i by the spacetime's 6th-order Lagrange interpolation.
+  Where the WENO value is unphysical (D^ <= 0) it falls back to the parent
+  cell's value, and eps there, or wherever its interpolant is <= 0, falls
+  back to trilinear interpolation.  The child's rho is D^ / (sqrt(gamma) w)
+  with the child's own metric.
+* Time: every parent time level is prolonged, and the child's ghost values
+  at a stage time are the time interpolant of those (quadratic through three
+  levels, linear through two, as for the spacetime).
+* Restriction: a parent cell under a child's active cells takes the volume
+  average of its 8 children's densitised conserved variables.
+* Reflux: for a parent cell outside a child that shares a face with the
+  child's active region, the parent step's flux through that face (the
+  RK4-weighted sum of its stage fluxes) is replaced by the children's: the
+  RK4-weighted fluxes through the 4 fine faces, averaged over the face and
+  over the child's two steps.  With periodic or no-flux outer boundaries the
+  total rest mass (sum of D^ dV over the cells not covered by a finer level)
+  is then conserved to rounding.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Optional
+
+import numpy as np
+
+import oracle as z4c
+from oracle import grhd
+
+GAMMA = (3.0 / 16.0, 5.0 / 8.0, 3.0 / 16.0)  # linear weights: the 5-cell quartic's left-half average
+RK_B = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
+
+
+# ------------------------------------------------------------------ 1D operators on cell averages
+
+def weno5_children(q, axis):
+    """Averages over the two halves of every parent cell along `axis` from
+    the parent cell averages q.  For parent cell I with neighbours
+    a..e = q_{I-2} .. q_{I+2} the left-half averages of the three quadratic
+    interpolants are (-a + 4b + 5c)/8, (b + 8c - d)/8, (11c - 4d + e)/8;
+    their combination with weights (3/16, 5/8, 3/16) is the left-half
+    average of the 5-cell quartic.  The nonlinear weights are
+    gamma_k / (eps + beta_k)^2, normalised, with the Jiang-Shu indicators
+    beta_k and eps = 1e-6 times the mean square of a..e.  The right half is
+    2c - left (the two halves average to the parent).  Output: 2N cells
+    along axis (children 2I, 2I+1 of parent I), NaN for the parent cells
+    without two neighbours on each side."""
+    q = np.moveaxis(np.asarray(q, dtype=np.float64), axis, 0)
+    N = q.shape[0]
+    out = np.full((2 * N,) + q.shape[1:], np.nan)
+    a, b, c, d, e = q[0:N - 4], q[1:N - 3], q[2:N - 2], q[3:N - 1], q[4:N]
+    L = [(-a + 4.0 * b + 5.0 * c) / 8.0, (b + 8.0 * c - d) / 8.0, (11.0 * c - 4.0 * d + e) / 8.0]
+    B = [13.0 / 12.0 * (a - 2.0 * b + c) ** 2 + 0.25 * (a - 4.0 * b + 3.0 * c) ** 2,
+         13.0 / 12.0 * (b - 2.0 * c + d) ** 2 + 0.25 * (b - d) ** 2,
+         13.0 / 12.0 * (c - 2.0 * d + e) ** 2 + 0.25 * (3.0 * c - 4.0 * d + e) ** 2]
+    eps = 1e-6 * (a * a + b * b + c * c + d * d + e * e) / 5.0 + 1e-300
+    al = [GAMMA[k] / (eps + B[k]) ** 2 for k in range(3)]
+    s = al[0] + al[1] + al[2]
+    left = (al[0] * L[0] + al[1] * L[1] + al[2] * L[2]) / s
+    out[4:2 * N - 4:2] = left
+    out[5:2 * N - 3:2] = 2.0 * c - left
+    return np.moveaxis(out, 0, axis)
+
+
+def linear_children(q, axis):
+    """Linear interpolation at the two child centres (-1/4 and +1/4 of a
+    parent cell): 3/4 of the cell plus 1/4 of the neighbour on that side."""
+    q = np.moveaxis(np.asarray(q, dtype=np.float64), axis, 0)
+    N = q.shape[0]
+    out = np.full((2 * N,) + q.shape[1:], np.nan)
+    out[2:2 * N - 2:2] = 0.75 * q[1:N - 1] + 0.25 * q[0:N - 2]
+    out[3:2 * N - 1:2] = 0.75 * q[1:N - 1] + 0.25 * q[2:N]
+    return np.moveaxis(out, 0, axis)
+
+
+# ------------------------------------------------------------------ geometry of a child in its parent
+
+def child_offset(parent, child):
+    return [int(round((child.origin[d] - parent.origin[d]) / parent.dx)) for d in range(3)]
+
+
+def _parent_box(parent, child, arr, margin):
+    """Parent array block covering the child's array (ghosts included) plus
+    `margin` parent cells on each side; arr is (..., z, y, x) with ghosts."""
+    off = child_offset(parent, child)
+    g = parent.g
+    sl = []
+    for d in (2, 1, 0):
+        lo = off[d] - 2 - margin + g        # parent cell of child cell -3 is off - 2
+        hi = off[d] + child.n[d] // 2 + 1 + margin + g
+        if lo < 0 or hi >= arr.shape[-1 - d]:
+            raise ValueError("child too close to its parent's edge for the fluid's prolongation")
+        sl.append(slice(lo, hi + 1))
+    return arr[(Ellipsis,) + tuple(sl)]
+
+
+def _child_cells(box_children, child, margin):
+    """Crop the child-resolution block (children of parent cells off-2-margin
+    .. off+n/2+1+margin) to the child's array: child cells -3 .. n+2."""
+    k = 2 * margin + 1  # child cell -4 - 2 margin is first; -3 is one later
+    sl = tuple(slice(k, k + child.n[d] + 2 * child.g) for d in (2, 1, 0))
+    return box_children[(Ellipsis,) + sl]
+
+
+def weno5_prolong(parent, child, q):
+    """The child's array (ghosts included) of a parent cell-average field q
+    (parent array with ghosts) by the conservative WENO5, x then y then z."""
+    box = _parent_box(parent, child, q, 2)
+    for ax in (-1, -2, -3):
+        box = weno5_children(box, ax)
+    return _child_cells(box, child, 2)
+
+
+def linear_prolong(parent, child, q):
+    box = _parent_box(parent, child, q, 1)
+    for ax in (-1, -2, -3):
+        box = linear_children(box, ax)
+    return _child_cells(box, child, 1)
+
+
+def parent_cell_values(parent, child, q):
+    """The value of the parent cell containing each child cell."""
+    box = _parent_box(parent, child, q, 0)
+    for ax in (-1, -2, -3):
+        box = np.repeat(box, 2, axis=ax)
+    return _child_cells(box, child, 0)
+
+
+def lagrange_prolong(parent, child, fields):
+    """6th-order Lagrange prolongation of a few fields onto the child's ghost
+    cells (the spacetime's operator, oracle.prolong_ghosts)."""
+    nf = len(fields)
+    up = np.zeros((z4c.NF,) + fields[0].shape)
+    up[:nf] = fields
+    uc = np.zeros((z4c.NF,) + tuple(child.n[d] + 2 * child.g for d in (2, 1, 0)))
+    uc = z4c.prolong_ghosts(parent, up, child, uc)
+    return uc[:nf]
+
+
+def ghost_mask(child):
+    g = child.g
+    m = np.ones(tuple(child.n[d] + 2 * g for d in (2, 1, 0)), dtype=bool)
+    m[g:-g, g:-g, g:-g] = False
+    return m
+
+
+def prolong_fluid(parent, cons_p, prim_p, child):
+    """Child ghost values (D^, eps, u_x, u_y, u_z) from one parent time
+    level (densitised conserved variables and primitives, arrays with
+    ghosts); entries outside the ghost shell are NaN."""
+    D = weno5_prolong(parent, child, cons_p[0])
+    bad = ~(D > 0.0)
+    D = np.where(bad, parent_cell_values(parent, child, cons_p[0]), D)
+    lag = lagrange_prolong(parent, child, [prim_p[1], prim_p[2], prim_p[3], prim_p[4]])
+    eps_lin = linear_prolong(parent, child, prim_p[1])
+    eps = np.where(bad | ~(lag[0] > 0.0), eps_lin, lag[0])
+    out = np.array([D, eps, lag[1], lag[2], lag[3]])
+    out[:, ~ghost_mask(child)] = np.nan
+    return out
+
+
+def ghost_primitives(vals, child, u, eos):
+    """Primitives (rho, eps, u_i) at the child's ghost cells from the
+    time-interpolated (D^, eps, u_i) and the child's metric u."""
+    m = grhd.metric(u)
+    ul = vals[2:5]
+    uu = grhd._raise(m["g_uu"], ul)
+    w = np.sqrt(1.0 + (ul * uu).sum(axis=0))
+    rho = vals[0] / (m["sqrtg"] * w)
+    return np.array([rho, vals[1], ul[0], ul[1], ul[2]])
+
+
+# ------------------------------------------------------------------ restriction and reflux
+
+def restrict_fluid(parent, cons_p, child, cons_c):
+    """Parent cells under the child's active cells <- mean of their 8
+    children (densitised conserved variables)."""
+    off = child_offset(parent, child)
+    g, gc = parent.g, child.g
+    out = np.array(cons_p, copy=True)
+    c = cons_c[:, gc:-gc, gc:-gc, gc:-gc]
+    avg = 0.125 * (c[:, 0::2, 0::2, 0::2] + c[:, 0::2, 0::2, 1::2] + c[:, 0::2, 1::2, 0::2] +
+                   c[:, 0::2, 1::2, 1::2] + c[:, 1::2, 0::2, 0::2] + c[:, 1::2, 0::2, 1::2] +
+                   c[:, 1::2, 1::2, 0::2] + c[:, 1::2, 1::2, 1::2])
+    nz, ny, nx = child.n[2] // 2, child.n[1] // 2, child.n[0] // 2
+    out[:, off[2] + g:off[2] + g + nz, off[1] + g:off[1] + g + ny, off[0] + g:off[0] + g + nx] = avg
+    return out
+
+
+def reflux(parent, cons_p, fbar_p, child, fbar_c, dt_p):
+    """Correct the parent cells outside the child next to its boundary:
+    the parent's RK4-weighted face fluxes (fbar_p[d][..., m] at face m+1/2
+    of array index m along axis d) through the child's boundary faces are
+    replaced by the child's, fbar_c averaged over the 4 fine faces (fbar_c
+    already averaged over the child's two steps)."""
+    off = child_offset(parent, child)
+    g, gc = parent.g, child.g
+    out = np.array(cons_p, copy=True)
+    h = parent.dx
+    for d in range(3):
+        ax = 3 - d  # array axis of direction d (fields, z, y, x)
+        t = [e for e in range(3) if e != d]
+        for side in (0, 1):
+            # parent face array index along d and the parent cell outside
+            if side == 0:
+                mp, cell = off[d] - 1 + g, off[d] - 1 + g
+                mc = gc - 1
+            else:
+                mp, cell = off[d] + child.n[d] // 2 - 1 + g, off[d] + child.n[d] // 2 + g
+                mc = child.n[d] - 1 + gc
+            fp = np.take(fbar_p[d], mp, axis=ax)   # (5, ..) over the two tangential axes
+            fc = np.take(fbar_c[d], mc, axis=ax)
+            # tangential ranges (array order: the remaining axes are z/y/x minus d)
+            sl_p, sl_c = [], []
+            for e in sorted(t, reverse=True):  # array order: higher direction first
+                sl_p.append(slice(off[e] + g, off[e] + g + child.n[e] // 2))
+                sl_c.append(slice(gc, gc + child.n[e]))
+            fp = fp[(slice(None),) + tuple(sl_p)]
+            fc = fc[(slice(None),) + tuple(sl_c)]
+            fine = 0.25 * (fc[:, 0::2, 0::2] + fc[:, 0::2, 1::2] + fc[:, 1::2, 0::2] + fc[:, 1::2, 1::2])
+            corr = (dt_p / h) * (fine - fp) * (-1.0 if side == 0 else 1.0)
+            idx = [slice(None)] * 4
+            idx[ax] = cell
+            te = sorted(t, reverse=True)
+            for k, e in enumerate(te):
+                idx[3 - e] = sl_p[k]
+            out[tuple(idx)] = out[tuple(idx)] + corr
+    return out
+
+
+def rest_mass(hierarchy_patches, cons, levels_children):
+    """Sum of D^ dV over the cells not covered by a finer level's active
+    cells (the composite grid)."""
+    total = 0.0
+    for pid, p in enumerate(hierarchy_patches):
+        g = p.g
+        D = np.array(cons[pid][0, g:-g, g:-g, g:-g], copy=True)
+        for cid in levels_children[pid]:
+            c = hierarchy_patches[cid]
+            off = child_offset(p, c)
+            D[off[2]:off[2] + c.n[2] // 2, off[1]:off[1] + c.n[1] // 2, off[0]:off[0] + c.n[0] // 2] = 0.0
+        total += D.sum() * p.dx ** 3
+    return total
+
+
+# ------------------------------------------------------------------ the coupled hierarchy
+
+class MatterHierarchy(z4c.BOHierarchy):
+    """The spacetime hierarchy of BOHierarchy with a perfect fluid evolved on
+    every level in the same RK4 stages (Sec. 2.2, 2.2.1): per stage and level,
+    the primitives recovered from the stage's conserved variables (the
+    atmosphere applied), their ghosts filled (level 0: periodic or outflow;
+    finer levels: from the parent, above), the Z4c stage with the fluid's
+    terms, the fluid's stage with the stage's metric.  After a level's two
+    child steps: the spacetime as in BOHierarchy, then the fluid's
+    restriction and reflux and the parent's primitives recovered again.
+    Patches of one level must not overlap."""
+
+    def __init__(self, hierarchy, states, prims, eos, floors, prm, courant=0.25, bc0=z4c.BC_PERIODIC,
+                 solver="hllc", reflux=True):
+        super().__init__(hierarchy, states, prm, courant=courant, bc0=bc0)
+        self.eos, self.floors, self.solver, self.do_reflux = eos, floors, solver, reflux
+        self.mbc = "periodic" if bc0 == z4c.BC_PERIODIC else "outflow"
+        self.ctl = []  # time levels of (cons, prim) per patch, oldest first
+        for pid, (u, pr) in enumerate(zip(states, prims)):
+            cons, _, _, _ = grhd.prim2con(pr, grhd.metric(u), eos)
+            prn, cons, _ = grhd.recover(cons, u, eos, floors[pid])
+            self.ctl.append([(cons, self._fill_level0(pid, prn) if self.patches[pid].level == 0 else prn)])
+        self.fstep = [None] * len(self.patches)  # the last step's RK4-weighted face fluxes
+        self.favg = [None] * len(self.patches)   # a child's, averaged over its two steps
+        self.children = [[c for c in range(len(self.patches)) if self.parent[c] == pid]
+                         for pid in range(len(self.patches))]
+
+    def _fill_level0(self, pid, prim):
+        fill = grhd.periodic_ghosts if self.mbc == "periodic" else grhd.outflow_ghosts
+        return fill(self.patches[pid], prim)
+
+    def _fluid_ghosts(self, pid, prim, u, frac):
+        """Child ghost primitives at fraction frac of the parent's last step."""
+        ppid = self.parent[pid]
+        levels = self.ctl[ppid]
+        w = z4c.time_weights(len(levels), frac)
+        src = levels[-3:] if len(levels) >= 3 else [levels[-2], levels[-1]]
+        ws = w if len(levels) >= 3 else w[1:]
+        vals = None
+        for wi, (cp, pp) in zip(ws, src):
+            v = prolong_fluid(self.patches[ppid], cp, pp, self.patches[pid])
+            vals = wi * v if vals is None else vals + wi * v
+        gp = ghost_primitives(vals, self.patches[pid], u, self.eos)
+        mask = ghost_mask(self.patches[pid])
+        out = np.array(prim, copy=True)
+        out[:, mask] = gp[:, mask]
+        return out
+
+    def _prims(self, pid, cons, u, frac):
+        pr, cons, _ = grhd.recover(cons, u, self.eos, self.floors[pid])
+        if self.patches[pid].level == 0:
+            return self._fill_level0(pid, pr), cons
+        return self._fluid_ghosts(pid, pr, u, frac), cons
+
+    def _rk4_level(self, l, frac0, dfrac):
+        ids = self.level_ids[l]
+        dt = self.dt(l)
+        un = [self.tl[pid][-1] for pid in ids]
+        y = [np.zeros_like(a) for a in un]
+        cur = [a.copy() for a in un]
+        c0 = [self.ctl[pid][-1][0] for pid in ids]
+        cs = [c.copy() for c in c0]
+        ym = [np.zeros_like(c) for c in c0]
+        fb = [[0.0, 0.0, 0.0] for _ in ids]
+        stage_frac = [0.0, 0.5, 0.5, 1.0]
+        cw = [0.5, 0.5, 1.0, None]
+        evolve_ghosts = (l == 0 and self.bc0 == z4c.BC_SOMMERFELD)
+        for s in range(1, 5):
+            if l == 0 and self.bc0 == z4c.BC_PERIODIC:
+                cur = [z4c.fill_periodic(self.patches[pid], c) for pid, c in zip(ids, cur)]
+            if l > 0:
+                for a, pid in enumerate(ids):
+                    cur[a] = self._fill_child_ghosts(pid, cur[a], frac0 + stage_frac[s - 1] * dfrac)
+            if s == 1:
+                un = [c.copy() for c in cur]
+            out = [np.empty_like(a) for a in un]
+            for a, pid in enumerate(ids):
+                p = self.patches[pid]
+                pr, cs[a] = self._prims(pid, cs[a], cur[a], frac0 + stage_frac[s - 1] * dfrac)
+                if s == 1:
+                    c0[a] = cs[a]
+                src = grhd.z4c_matter_rhs(pr, cur[a], self.eos, frozen_shift=self.prm.shift == 1)
+                z4c.rk4_stage(p, self.prm, s, dt, evolve_ghosts, cur[a], un[a], y[a], out[a], src)
+                fl = []
+                km = grhd.matter_rhs(p, pr, cur[a], self.eos, solver=self.solver, fluxes_out=fl)
+                for d in range(3):
+                    fb[a][d] = fb[a][d] + RK_B[s - 1] * fl[d]
+                act = (slice(None),) + grhd._act(p)
+                nxt = cs[a].copy()
+                if s == 1:
+                    ym[a][act] = c0[a][act] + RK_B[0] * dt * km[act]
+                elif s < 4:
+                    ym[a][act] = ym[a][act] + RK_B[s - 1] * dt * km[act]
+                if s < 4:
+                    nxt[act] = c0[a][act] + cw[s - 1] * dt * km[act]
+                else:
+                    nxt[act] = ym[a][act] + RK_B[3] * dt * km[act]
+                cs[a] = nxt
+            cur = out
+        for a, pid in enumerate(ids):
+            if l == 0 and self.bc0 == z4c.BC_PERIODIC:
+                cur[a] = z4c.fill_periodic(self.patches[pid], cur[a])
+            self.tl[pid].append(cur[a])
+            if len(self.tl[pid]) > 3:
+                self.tl[pid].pop(0)
+            pr, cn = self._prims(pid, cs[a], cur[a], frac0 + dfrac)
+            self.ctl[pid].append((cn, pr))
+            if len(self.ctl[pid]) > 3:
+                self.ctl[pid].pop(0)
+            # RK4-weighted face fluxes of this step; a child's two steps averaged
+            self.fstep[pid] = fb[a]
+            if l > 0:
+                self.favg[pid] = fb[a] if frac0 == 0.0 else [0.5 * (self.favg[pid][d] + fb[a][d]) for d in range(3)]
+        self.nsteps[l] += 1
+
+    def level_step(self, l=0, frac0=0.0, dfrac=1.0):
+        self._rk4_level(l, frac0, dfrac)
+        if l + 1 < len(self.h.levels):
+            self.level_step(l + 1, 0.0, 0.5)
+            self.level_step(l + 1, 0.5, 0.5)
+            kids = self.level_ids[l + 1]
+            for pid in kids:
+                self.tl[pid][-1] = self._fill_child_ghosts(pid, self.tl[pid][-1], 1.0)
+            for pid in kids:
+                ppid = self.parent[pid]
+                self.tl[ppid][-1] = z4c.restrict(self.patches[ppid], self.tl[ppid][-1],
+                                                 self.patches[pid], self.tl[pid][-1])
+            # the fluid: restriction, reflux, the parent's primitives again
+            for pid in kids:
+                ppid = self.parent[pid]
+                cp, _ = self.ctl[ppid][-1]
+                cp = restrict_fluid(self.patches[ppid], cp, self.patches[pid], self.ctl[pid][-1][0])
+                if self.do_reflux:
+                    cp = reflux(self.patches[ppid], cp, self.fstep[ppid], self.patches[pid], self.favg[pid],
+                                self.dt(l))
+                self.ctl[ppid][-1] = (cp, None)
+            for ppid in self.level_ids[l]:
+                cp, pr = self.ctl[ppid][-1]
+                if pr is None:
+                    pr, cp = self._prims(ppid, cp, self.tl[ppid][-1], frac0 + dfrac)
+                    self.ctl[ppid][-1] = (cp, pr)
+
+    def cons(self, pid):
+        return self.ctl[pid][-1][0]
+
+    def prim(self, pid):
+        return self.ctl[pid][-1][1]
+
+    def rest_mass(self):
+        return rest_mass(self.patches, [self.cons(pid) for pid in range(len(self.patches))], self.children)
