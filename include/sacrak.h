@@ -88,7 +88,8 @@ typedef struct {
                             an odd number of z indices) after every other ghost treatment;
                             not with bc = 1 */
   int matter;            /* 1: a perfect fluid evolved with the spacetime (Sec. 2.1.2, 2.2):
-                            one level, FP64, no zsym; see the matter calls below */
+                            FP64, no zsym, no overlapping patches on a level, no
+                            moving patches; see the matter calls below */
 } sacrak_params;
 
 /* One patch: refinement level, active cells per axis, lower face of active
@@ -408,7 +409,7 @@ sacrak_status sacrak_set_wait_limit(sacrak_grid* grid, long long cycles);
 sacrak_status sacrak_set_overlap(sacrak_grid* grid, int on);
 
 /* ---- Matter: a perfect fluid on the evolving spacetime (Sec. 2.1.2, 2.2) ----
- * Grids created with params.matter = 1 (one level, FP64) carry a perfect
+ * Grids created with params.matter = 1 (FP64) carry a perfect
  * fluid: primitives (rho, eps, u_x, u_y, u_z) -- rest-mass density, specific
  * internal energy, spatial covariant components of the four-velocity -- and
  * the densitised conserved variables sqrt(gamma) (D, J_i, rho_H), D = rho w,
@@ -423,8 +424,20 @@ sacrak_status sacrak_set_overlap(sacrak_grid* grid, int on);
  * conserved variables with PPM face states (steep minmod b = 3), face fluxes
  * (sacrak_set_riemann: HLLC in the face tetrad by default, or HLLE), the
  * metric at faces by 4th-order interpolation and the geometric sources
- * (4th-order metric derivatives).  Ghost cells of the fluid: zero gradient (outflow), periodic
- * with bc = 1.  A "matter array" exchanged with the caller is
+ * (4th-order metric derivatives).  Ghost cells of the fluid: on level 0 zero
+ * gradient (outflow), periodic with bc = 1; on finer levels from the parent
+ * (Sec. 2.2.1): every parent time level is prolonged onto the child's ghost
+ * shell -- D^ by a conservative fifth-order WENO interpolation (applied along
+ * x, y, z; the parent cell's value where it is not positive), eps and u_i by
+ * the 6th-order Lagrange interpolation of the spacetime (eps trilinear where
+ * D^ fell back or eps is not positive) -- and interpolated in time like the
+ * spacetime's ghosts, rho = D^ / (sqrt(gamma) w) with the child's metric.
+ * After a level's two child steps the parent cells under a child take the
+ * mean of their 8 children's conserved variables, and the parent cells next
+ * to a child have their boundary-face fluxes of the parent's step (RK4-
+ * weighted) replaced by the children's (averaged over the 4 fine faces and
+ * the 2 child steps): the reflux, which conserves the total rest mass.  A
+ * "matter array" exchanged with the caller is
  * double[5][NZ][NY][NX] in the patch-array layout above.  The stepping calls
  * return SACRAK_ESTATE until sacrak_upload_matter has run. */
 

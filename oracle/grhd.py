@@ -437,6 +437,11 @@ def sr_hllc(UL, FL, lpl, lml, vL, PL, UR, FR, lpr, lmr, vR, PR):
     density.  Returns (flux, hllc_used)."""
     lL = np.minimum(lml, lmr)
     lR = np.maximum(lpl, lpr)
+    with np.errstate(divide="ignore", invalid="ignore"):  # branches not taken are computed too
+        return _sr_hllc(UL, FL, vL, PL, UR, FR, vR, PR, lL, lR)
+
+
+def _sr_hllc(UL, FL, vL, PL, UR, FR, vR, PR, lL, lR):
     den = lR - lL
     Uh = (lR * UR - lL * UL + FL - FR) / den
     Fh = (lR * FL - lL * FR + lL * lR * (UR - UL)) / den

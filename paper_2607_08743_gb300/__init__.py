@@ -146,7 +146,7 @@ class Params:
     precision: int = 0     # 0 FP64, 1 mixed
     lapse_uses_khat: int = 0
     zsym: int = 0          # 1: equatorial reflection symmetry, only z >= 0 evolved
-    matter: int = 0        # 1: a perfect fluid evolved with the spacetime (one level, FP64)
+    matter: int = 0        # 1: a perfect fluid evolved with the spacetime (FP64)
 
     def c(self) -> sacrak_params:
         return sacrak_params(self.kappa1, self.kappa2, self.eta, self.sigma_ko, self.courant, self.w_floor,

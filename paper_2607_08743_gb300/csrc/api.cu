@@ -38,13 +38,15 @@ struct Layout {
 };
 
 // fields of the matter arrays of a patch: conserved variables in the six
-// state slots, primitives + Lorentz factor, face fluxes, Z4c matter terms
-constexpr int MATTER_FIELDS = NBUF * NM + NMP + 3 * NM + NZSRC;
+// state slots, primitives + Lorentz factor, face fluxes, Z4c matter terms,
+// the cached prolongations of the parent's three time levels, and the
+// RK4-weighted face fluxes of the last step and of the last two steps
+constexpr int MATTER_FIELDS = NBUF * NM + NMP + 3 * NM + NZSRC + 3 * NM + 3 * NM + 3 * NM;
 
 bool describe(int nlevels, int npatches, const sacrak_patch_desc* pd, int mixed, int matter, Layout& L,
               std::string& why) {
-  if (matter && (nlevels != 1 || mixed)) {
-    why = "a fluid needs one level and FP64";
+  if (matter && mixed) {
+    why = "a fluid needs FP64";
     return false;
   }
   if (nlevels < 1 || npatches < 1 || !pd) {
@@ -183,6 +185,7 @@ struct sacrak_grid {
   DevEOS eos = {};
   bool eos_set = false;
   bool matter_ready = false;  // primitives uploaded
+  bool matter_shells_dirty = true;  // the children's fluid caches predate the last upload
   double rho_atm = 0.0, r_atm = 0.0;
   int riemann = 0;  // face flux of the fluid: 0 HLLC in the face tetrad, 1 HLLE (sacrak_set_riemann)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -581,6 +584,22 @@ void zreflect(sacrak_grid* g, int l, int mode, int stage) {
   launch_zreflect(fill_args(g, l, mode, stage, 0.0), (int)g->lvl_ids[l].size(), g->lvl_max_zslab[l], g->stream);
 }
 
+MatterAmrArgs matter_amr_args(const sacrak_grid* g, int l) {
+  MatterAmrArgs a;
+  a.patches = g->d_patches;
+  a.child_ids = g->d_ids + g->lvl_id_off[l];
+  a.plev = g->d_levels + (l - 1);
+  a.clev = g->d_levels + l;
+  a.dt_parent = level_dt(g, l - 1);
+  return a;
+}
+
+// the fluid of level l-1's current slot prolonged onto level l's ghost shells
+void refresh_matter_shells(sacrak_grid* g, int l) {
+  if (!g->prm.matter || l <= 0 || l >= g->nlevels) return;
+  launch_matter_prolong(matter_amr_args(g, l), (int)g->lvl_ids[l].size(), g->lvl_max_shell[l], g->stream);
+}
+
 // spatial prolongation of level l-1's current slot onto level l's shells
 // (on the side stream with overlap: the children's first stage-2 fill, also
 // on the side stream, is the first reader of the new slot's cache)
@@ -604,17 +623,29 @@ void refresh_all_shells(sacrak_grid* g) {
     }
     g->split_dirty = false;
   }
+  if (g->prm.matter && g->matter_ready && g->matter_shells_dirty) {
+    for (int l = 1; l < g->nlevels; ++l) refresh_matter_shells(g, l);
+    g->matter_shells_dirty = false;
+  }
   if (!g->shells_dirty) return;
   for (int l = 1; l < g->nlevels; ++l) refresh_shells(g, l);
   g->shells_dirty = false;
 }
 
-MatterArgs matter_args(const sacrak_grid* g, int pid, int stage, double dt) {
+// the fluid of patch pid at RK stage `stage`; levels > 0 take their ghost
+// cells from the parent at the time s0 + c ds (c = 0, 1/2, 1/2, 1 for the
+// stage `wstage` = 1..4; 0 for wstage 0), s0 and ds locating the call in the
+// parent's last step
+MatterArgs matter_args(const sacrak_grid* g, int pid, int stage, double dt, double s0 = 1.0, double ds = 0.0,
+                       int wstage = 0) {
   const DevPatch& P = g->hp[pid];
   MatterArgs a;
   std::memset(&a, 0, sizeof a);
   a.P = g->d_patches + pid;
   a.lev = g->d_levels + P.level;
+  a.plev = P.level > 0 ? g->d_levels + (P.level - 1) : nullptr;
+  ghost_time_weights(s0, ds, wstage, a.wq, a.wl);
+  a.first_substep = s0 == 0.0;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = P.n[d];
     a.origin[d] = P.origin[d];
@@ -641,18 +672,22 @@ MatterArgs matter_args(const sacrak_grid* g, int pid, int stage, double dt) {
 
 // fluid of level l at RK stage s (0: the current level, 5: the new level):
 // recovery (atmosphere, Z4c matter terms) and the primitives' ghost cells
-void matter_recover(sacrak_grid* g, int l, int s, double dt) {
+// (levels > 0: from the parent at time s0 + c(wstage) ds of its last step)
+void matter_recover(sacrak_grid* g, int l, int s, double dt, double s0 = 1.0, double ds = 0.0, int wstage = 0) {
   for (int pid : g->lvl_ids[l]) {
-    const MatterArgs a = matter_args(g, pid, s, dt);
+    const MatterArgs a = matter_args(g, pid, s, dt, s0, ds, wstage);
     launch_matter_prep(a, g->stream);
-    launch_matter_ghosts(a, g->stream);
+    if (l == 0)
+      launch_matter_ghosts(a, g->stream);
+    else
+      launch_matter_child_ghosts(a, g->stream);
   }
 }
 
 // face fluxes and the stage update of the fluid (s = 0: d_t into out)
-void matter_advance(sacrak_grid* g, int l, int s, double dt, double* out = nullptr) {
+void matter_advance(sacrak_grid* g, int l, int s, double dt, double* out = nullptr, double s0 = 1.0) {
   for (int pid : g->lvl_ids[l]) {
-    MatterArgs a = matter_args(g, pid, s, dt);
+    MatterArgs a = matter_args(g, pid, s, dt, s0);
     a.out = out;
     for (int d = 0; d < 3; ++d) launch_matter_flux(a, d, g->stream);
     launch_matter_update(a, g->stream);
@@ -679,7 +714,7 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
     }
     zreflect(g, l, 0, s);  // equatorial symmetry: after every other ghost treatment
     // the fluid of this stage: primitives and the Z4c matter terms first
-    if (g->prm.matter) matter_recover(g, l, s, dt);
+    if (g->prm.matter) matter_recover(g, l, s, dt, frac0, dfrac, s);
     StageArgs a;
     a.tiles = g->d_tiles + g->lvl_tile_off[l];
     a.ntiles = (int)g->lvl_ntiles[l];
@@ -707,9 +742,9 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
       else
         launch_sommerfeld(ga, np, g->lvl_max_shell[l], g->stream);
     }
-    if (g->prm.matter) matter_advance(g, l, s, dt);  // on this stage's metric
+    if (g->prm.matter) matter_advance(g, l, s, dt, nullptr, frac0);  // on this stage's metric
   }
-  if (g->prm.matter) matter_recover(g, l, 5, dt);  // primitives of the new level
+  if (g->prm.matter) matter_recover(g, l, 5, dt, frac0, dfrac, 4);  // primitives of the new level
   // ghosts of the new time level for periodic / frozen outer boundaries
   if (l == 0 && g->prm.bc == 1)
     launch_fill(FILL_PERIODIC, fill_args(g, l, 2, 4, 0.0), np, g->lvl_max_shell[l], g->stream);
@@ -733,6 +768,7 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
     }
   launch_level_advance(g->d_levels + l, dt, g->stream);
   refresh_shells(g, l + 1, g->overlap);  // the children's cache of this level's new slot
+  refresh_matter_shells(g, l + 1);
 }
 
 // do two patches of level l share active cells (the exchange then averages
@@ -766,6 +802,23 @@ void level_step_rec(sacrak_grid* g, int l, double frac0, double dfrac) {
     if (l + 2 < g->nlevels && active_overlap(g, l + 1)) refresh_shells(g, l + 2);
     launch_fill(FILL_RESTRICT, fill_args(g, l + 1, 1, 0, 0.0), nc, g->lvl_max_restrict[l + 1],
                 g->stream);
+    if (g->prm.matter) {
+      // the fluid (Sec. 2.2.1): volume-averaged restriction, reflux (one child
+      // at a time), the parent's primitives of the corrected level, and the
+      // children's cache of it
+      const MatterAmrArgs ma = matter_amr_args(g, l + 1);
+      launch_matter_restrict(ma, nc, g->lvl_max_restrict[l + 1], g->stream);
+      for (int c = 0; c < nc; ++c) {
+        MatterAmrArgs one = ma;
+        one.child_ids = ma.child_ids + c;
+        const DevPatch& C = g->hp[g->lvl_ids[l + 1][c]];
+        const long long nf = 2LL * ((long long)(C.n[1] / 2) * (C.n[2] / 2) + (long long)(C.n[0] / 2) * (C.n[2] / 2) +
+                                    (long long)(C.n[0] / 2) * (C.n[1] / 2));
+        launch_matter_reflux(one, 1, nf, g->stream);
+      }
+      matter_recover(g, l, 0, 0.0, frac0, dfrac, 4);
+      refresh_matter_shells(g, l + 1);
+    }
     zreflect(g, l, 1, 0);      // restricted cells next to z = 0 have mirrors among the ghosts
     refresh_shells(g, l + 1);  // the restricted slot, for the next parent step
   }
@@ -1001,6 +1054,9 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
       P.mprim = m0 + (size_t)NBUF * NM * fl;
       P.mflux = P.mprim + (size_t)NMP * fl;
       P.mzsrc = P.mflux + (size_t)3 * NM * fl;
+      for (int b = 0; b < 3; ++b) P.mgsh[b] = P.mzsrc + (size_t)(NZSRC + b * NM) * fl;
+      P.mfs = P.mzsrc + (size_t)(NZSRC + 3 * NM) * fl;
+      P.mfa = P.mfs + (size_t)3 * NM * fl;
     }
     g->lvl_ids[P.level].push_back(i);
   }
@@ -1010,6 +1066,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
     if (C.level == 0) continue;
     for (int d = 0; d < 3; ++d)
       if (C.n[d] % 2) {
+        release_side(g);
         delete g;
         return SACRAK_EINVAL;
       }
@@ -1035,6 +1092,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
       }
     }
     if (C.parent < 0) {
+      release_side(g);
       delete g;
       return SACRAK_EINVAL;
     }
@@ -1046,9 +1104,19 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
       for (int d = 0; d < 3; ++d) {
         const DevPatch& P = g->hp[i];
         if (!((P.origin[d] < 0.0 || (d == 2 && P.zrefl)) && P.origin[d] + P.n[d] * P.dx > 0.0)) {
+          release_side(g);
           delete g;
           return SACRAK_EINVAL;
         }
+      }
+  // a fluid on several levels: the patches of a level share no cells (each
+  // parent cell is restricted from one child and refluxed once per face)
+  if (p.matter)
+    for (int l = 1; l < nlevels; ++l)
+      if (active_overlap(g, l)) {
+        release_side(g);
+        delete g;
+        return SACRAK_EINVAL;
       }
   g->d_patches = (DevPatch*)(g->arena + L.patches);
   g->d_levels = (DevLevel*)(g->arena + L.levels);
@@ -1400,6 +1468,8 @@ sacrak_status sacrak_upload_matter(sacrak_grid* g, int patch, const double* prim
   st = check_launch(g);
   if (st != SACRAK_OK) return st;
   g->matter_ready = true;
+  g->matter_shells_dirty = true;
+  drop_graph(g);
   return sync_and_check(g);
 }
 
@@ -1421,6 +1491,7 @@ sacrak_status sacrak_matter_rhs(sacrak_grid* g, int patch, double* rhs) {
   if (!g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
   if (g->invalid) return fail(g, SACRAK_ESTATE, "grid state invalid after an earlier error");
   const DevPatch& P = g->hp[patch];
+  refresh_all_shells(g);  // (levels > 0: the fluid's ghost cells come from the parent's cache)
   CK(cudaMemsetAsync(P.buf[B_S1], 0, (size_t)NM * P.fstride * sizeof(double), g->stream));
   matter_recover(g, P.level, 0, 0.0);
   matter_advance(g, P.level, 0, 0.0, P.buf[B_S1]);
@@ -1482,6 +1553,7 @@ sacrak_status sacrak_adm_integrals(sacrak_grid* g, int patch, const double centr
 
 sacrak_status sacrak_track_punctures(sacrak_grid* g, int npunct, const double* pos, const int* follow) {
   if (!g) return SACRAK_EINVAL;
+  if (g->prm.matter) return fail(g, SACRAK_EINVAL, "moving patches are not supported with a fluid");
   if (npunct < 0 || npunct > MAX_PUNCT || (npunct > 0 && (!pos || !follow)))
     return fail(g, SACRAK_EINVAL, "bad arguments");
   std::vector<DevPunct> hp(npunct);
@@ -1535,6 +1607,7 @@ sacrak_status sacrak_get_punctures(sacrak_grid* g, double* pos) {
 
 sacrak_status sacrak_move_patch(sacrak_grid* g, int patch, const int shift[3]) {
   if (!g) return SACRAK_EINVAL;
+  if (g->prm.matter) return fail(g, SACRAK_EINVAL, "moving patches are not supported with a fluid");
   if (patch < 0 || patch >= g->npatches || !shift) return fail(g, SACRAK_EINVAL, "bad arguments");
   if (g->hp[patch].level == 0) return fail(g, SACRAK_EINVAL, "level-0 patches do not move");
   if (g->invalid) return fail(g, SACRAK_ESTATE, "grid holds invalid data");

@@ -574,6 +574,23 @@ __device__ __forceinline__ void tetrad_to_coordinate(const Met& m, const Tetrad&
   out[4] = pre * m.al * (rows[0] * T.e[0][0] + rows[1] * T.e[1][0] + rows[2] * T.e[2][0] + rows[3] * T.e[3][0]);
 }
 
+// RK4-weighted sum of a face's fluxes over the step's stages (the reflux of
+// Sec. 2.2.1): mfs = sum_s b_s F_s; on levels > 0 after stage 4 also mfa, the
+// sum of the level's first step, then the mean of its two steps
+__device__ __forceinline__ void accumulate_flux(const MatterArgs& A, int dir, long long q, const double F[NM]) {
+  if (A.stage < 1 || A.stage > 4 || !A.P->mfs) return;
+  const double bw = (A.stage == 1 || A.stage == 4) ? 1.0 / 6.0 : 1.0 / 3.0;
+  double* __restrict__ fsum = A.P->mfs + (long long)dir * NM * A.fs;
+  double* __restrict__ favg = A.P->mfa + (long long)dir * NM * A.fs;
+#pragma unroll
+  for (int f = 0; f < NM; ++f) {
+    const long long o = f * A.fs + q;
+    const double v = (A.stage == 1 ? 0.0 : fsum[o]) + bw * F[f];
+    fsum[o] = v;
+    if (A.stage == 4 && A.plev) favg[o] = A.first_substep ? v : 0.5 * (favg[o] + v);
+  }
+}
+
 // one thread per face: faces m+1/2 along dir for m = 2 .. n+2 (array index),
 // the other axes over active cells; flux stored at cell m
 template <int dir>
@@ -634,14 +651,20 @@ __global__ void __launch_bounds__(128) matter_flux_kernel(MatterArgs A) {
       tetrad_to_coordinate(mf, T, Ft, out);
 #pragma unroll
       for (int f = 0; f < NM; ++f) flux[f * A.fs + q] = out[f];
+      accumulate_flux(A, dir, q, out);
       continue;
     }
     phys_flux<dir>(A.eos, mf, pl, UL, FL, lpl, lml);
     phys_flux<dir>(A.eos, mf, pr, UR, FR, lpr, lmr);
     const double ap = fmax(0.0, fmax(lpl, lpr)), am = fmin(0.0, fmin(lml, lmr));
     const double den = (ap - am > 0.0) ? ap - am : 1.0;
+    double out[NM];
 #pragma unroll
-    for (int f = 0; f < NM; ++f) flux[f * A.fs + q] = (ap * FL[f] - am * FR[f] + ap * am * (UR[f] - UL[f])) / den;
+    for (int f = 0; f < NM; ++f) {
+      out[f] = (ap * FL[f] - am * FR[f] + ap * am * (UR[f] - UL[f])) / den;
+      flux[f * A.fs + q] = out[f];
+    }
+    accumulate_flux(A, dir, q, out);
   }
 }
 
@@ -782,6 +805,215 @@ __global__ void __launch_bounds__(128) matter_prim2con_kernel(MatterArgs A) {
   }
 }
 
+// ------------------------------------------------------------------ refinement boundary (Sec. 2.2.1)
+
+__device__ __forceinline__ int fdiv2(int i) { return i >= 0 ? i / 2 : -((-i + 1) / 2); }
+
+__device__ __forceinline__ long long shell_count(const DevPatch* P) {
+  return (long long)P->NX * P->NY * P->NZ - (long long)(P->NX - 2 * GH) * (P->NY - 2 * GH) * (P->NZ - 2 * GH);
+}
+
+// Average over the left (right: the right) half of cell c from the cell
+// averages a..e of cells -2..2: the left-half averages of the three
+// quadratic interpolants, (-a + 4b + 5c)/8, (b + 8c - d)/8, (11c - 4d + e)/8,
+// weighted gamma_k / (eps + beta_k)^2 (gamma = 3/16, 5/8, 3/16, the 5-cell
+// quartic; beta_k the Jiang-Shu indicators; eps = 1e-6 times the mean square
+// of a..e), normalised; the right half is 2c - left (conservative).
+__device__ __forceinline__ double weno_half(double a, double b, double c, double d, double e, bool right) {
+  const double L0 = (-a + 4.0 * b + 5.0 * c) / 8.0, L1 = (b + 8.0 * c - d) / 8.0, L2 = (11.0 * c - 4.0 * d + e) / 8.0;
+  const double t0 = a - 2.0 * b + c, t1 = b - 2.0 * c + d, t2 = c - 2.0 * d + e;
+  const double v0 = a - 4.0 * b + 3.0 * c, v1 = b - d, v2 = 3.0 * c - 4.0 * d + e;
+  const double B0 = 13.0 / 12.0 * t0 * t0 + 0.25 * v0 * v0;
+  const double B1 = 13.0 / 12.0 * t1 * t1 + 0.25 * v1 * v1;
+  const double B2 = 13.0 / 12.0 * t2 * t2 + 0.25 * v2 * v2;
+  const double eps = 1e-6 * (a * a + b * b + c * c + d * d + e * e) / 5.0 + 1e-300;
+  const double r0 = eps + B0, r1 = eps + B1, r2 = eps + B2;
+  const double a0 = (3.0 / 16.0) / (r0 * r0), a1 = (5.0 / 8.0) / (r1 * r1), a2 = (3.0 / 16.0) / (r2 * r2);
+  const double left = (a0 * L0 + a1 * L1 + a2 * L2) / (a0 + a1 + a2);
+  return right ? 2.0 * c - left : left;
+}
+
+// 6-point Lagrange weights at +1/4 (nodes -2..3) and -1/4 (nodes -3..2)
+__constant__ double c_lp[6] = {77.0 / 8192, -693.0 / 8192, 6930.0 / 8192, 2310.0 / 8192, -495.0 / 8192, 63.0 / 8192};
+__constant__ double c_lm[6] = {63.0 / 8192, -495.0 / 8192, 2310.0 / 8192, 6930.0 / 8192, -693.0 / 8192, 77.0 / 8192};
+
+// one thread per ghost-shell cell of a child: the parent's current fluid
+// prolonged, cached in the child's slot of the parent's current ring slot
+__global__ void __launch_bounds__(128) matter_prolong_kernel(MatterAmrArgs A) {
+  const DevPatch* C = A.patches + A.child_ids[blockIdx.y];
+  const DevPatch* P = A.patches + C->parent;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= shell_count(C)) return;
+  int i, j, k;
+  shell_ijk(id, C->NX, C->NY, C->NZ, i, j, k);
+  const int pr = A.plev->ring;
+  const long long sy = P->px, sz = P->plane, fs = P->fstride;
+  const double* __restrict__ D = P->mcons[pr];
+  const double* __restrict__ prim = P->mprim;
+  const int ci[3] = {i - GH, j - GH, k - GH};
+  int pc[3];
+  bool odd[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    pc[d] = C->off[d] + fdiv2(ci[d]) + GH;
+    odd[d] = (ci[d] & 1) != 0;
+  }
+  auto at = [&](const double* f, int x, int y, int z) { return f[x + y * sy + (long long)z * sz]; };
+  // D^: WENO along x (5 x 5 rows), then y (5 rows), then z
+  double vz[5];
+  for (int c = 0; c < 5; ++c) {
+    double vy[5];
+    const int z = pc[2] - 2 + c;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const int y = pc[1] - 2 + b;
+      vy[b] = weno_half(at(D, pc[0] - 2, y, z), at(D, pc[0] - 1, y, z), at(D, pc[0], y, z), at(D, pc[0] + 1, y, z),
+                        at(D, pc[0] + 2, y, z), odd[0]);
+    }
+    vz[c] = weno_half(vy[0], vy[1], vy[2], vy[3], vy[4], odd[1]);
+  }
+  double Dv = weno_half(vz[0], vz[1], vz[2], vz[3], vz[4], odd[2]);
+  const bool bad = !(Dv > 0.0);
+  if (bad) Dv = at(D, pc[0], pc[1], pc[2]);
+  // eps, u_i: 6th-order Lagrange (nodes -3..2 for even child indices, -2..3 for odd)
+  double lag[4] = {0.0, 0.0, 0.0, 0.0};
+  const int n0[3] = {odd[0] ? -2 : -3, odd[1] ? -2 : -3, odd[2] ? -2 : -3};
+  for (int c = 0; c < 6; ++c)
+    for (int b = 0; b < 6; ++b)
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const double w = (odd[0] ? c_lp[a] : c_lm[a]) * (odd[1] ? c_lp[b] : c_lm[b]) * (odd[2] ? c_lp[c] : c_lm[c]);
+        const long long q = (pc[0] + n0[0] + a) + (pc[1] + n0[1] + b) * sy + (long long)(pc[2] + n0[2] + c) * sz;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) lag[f] += w * prim[(1 + f) * fs + q];
+      }
+  double eps = lag[0];
+  if (bad || !(eps > 0.0)) {  // trilinear: 3/4 of the cell, 1/4 of the neighbour on the child's side
+    const int o[3] = {odd[0] ? 1 : -1, odd[1] ? 1 : -1, odd[2] ? 1 : -1};
+    double vzl[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      double vyl[2];
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int y = pc[1] + b * o[1], z = pc[2] + c * o[2];
+        vyl[b] = 0.75 * at(prim + fs, pc[0], y, z) + 0.25 * at(prim + fs, pc[0] + o[0], y, z);
+      }
+      vzl[c] = 0.75 * vyl[0] + 0.25 * vyl[1];
+    }
+    eps = 0.75 * vzl[0] + 0.25 * vzl[1];
+  }
+  double* __restrict__ cache = C->mgsh[pr];
+  const long long fc = C->fstride;
+  const long long qc = i + (long long)j * C->px + (long long)k * C->plane;
+  cache[qc] = Dv;
+  cache[fc + qc] = eps;
+  cache[2 * fc + qc] = lag[1];
+  cache[3 * fc + qc] = lag[2];
+  cache[4 * fc + qc] = lag[3];
+}
+
+// ghost cells of a level > 0 fluid: the time interpolant of the cached
+// prolongations, rho = D^ / (sqrt(gamma) w) with this patch's stage metric
+__global__ void __launch_bounds__(128) matter_child_ghost_kernel(MatterArgs A) {
+  const DevPatch* C = A.P;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= shell_count(C)) return;
+  int i, j, k;
+  shell_ijk(id, C->NX, C->NY, C->NZ, i, j, k);
+  const int pr = A.plev->ring;
+  const bool q3 = A.plev->nvalid >= 3;
+  const double w0 = q3 ? A.wq[0] : 0.0, w1 = q3 ? A.wq[1] : A.wl[1], w2 = q3 ? A.wq[2] : A.wl[2];
+  const double* __restrict__ g0 = C->mgsh[(pr + 1) % 3];
+  const double* __restrict__ g1 = C->mgsh[(pr + 2) % 3];
+  const double* __restrict__ g2 = C->mgsh[pr];
+  const long long fs = A.fs;
+  const long long q = i + (long long)j * A.sy + (long long)k * A.sz;
+  double v[NM];
+#pragma unroll
+  for (int f = 0; f < NM; ++f) {
+    const long long o = f * fs + q;
+    // (slots of zero weight are not read: they may hold no data yet)
+    double t = (w1 != 0.0 ? w1 * g1[o] : 0.0);
+    if (q3 && w0 != 0.0) t = w0 * g0[o] + t;
+    v[f] = t + (w2 != 0.0 ? w2 * g2[o] : 0.0);
+  }
+  Met m;
+  metric_at(z4c_stage_state(A, A.lev->ring), q, fs, m, nullptr);
+  const double ul[3] = {v[2], v[3], v[4]};
+  double uu[3];
+  raise3(m.gu, ul, uu);
+  const double w = sqrt(1.0 + ul[0] * uu[0] + ul[1] * uu[1] + ul[2] * uu[2]);
+  double* __restrict__ prim = C->mprim;
+  prim[q] = v[0] / (m.sg * w);
+  prim[fs + q] = v[1];
+  prim[2 * fs + q] = v[2];
+  prim[3 * fs + q] = v[3];
+  prim[4 * fs + q] = v[4];
+  prim[NM * fs + q] = w;
+}
+
+// parent cells under a child's active cells <- mean of their 8 children
+__global__ void __launch_bounds__(128) matter_restrict_kernel(MatterAmrArgs A) {
+  const DevPatch* C = A.patches + A.child_ids[blockIdx.y];
+  const DevPatch* P = A.patches + C->parent;
+  const int mx = C->n[0] / 2, my = C->n[1] / 2, mz = C->n[2] / 2;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)mx * my * mz) return;
+  const int I = (int)(id % mx), J = (int)((id / mx) % my), K = (int)(id / ((long long)mx * my));
+  const double* __restrict__ cc = C->mcons[A.clev->ring];
+  double* __restrict__ cp = P->mcons[A.plev->ring];
+  const long long sy = C->px, sz = C->plane, fc = C->fstride;
+  const long long q0 = (2 * I + GH) + (2 * J + GH) * sy + (long long)(2 * K + GH) * sz;
+  const long long qp = (I + C->off[0] + GH) + (J + C->off[1] + GH) * P->px + (long long)(K + C->off[2] + GH) * P->plane;
+#pragma unroll
+  for (int f = 0; f < NM; ++f) {
+    const double* x = cc + f * fc + q0;
+    const double s = x[0] + x[1] + x[sy] + x[sy + 1] + x[sz] + x[sz + 1] + x[sz + sy] + x[sz + sy + 1];
+    cp[f * P->fstride + qp] = 0.125 * s;
+  }
+}
+
+// parent cells outside a child next to its boundary: the parent step's
+// boundary-face flux replaced by the child's (4 fine faces, 2 steps averaged)
+__global__ void __launch_bounds__(128) matter_reflux_kernel(MatterAmrArgs A) {
+  const DevPatch* C = A.patches + A.child_ids[blockIdx.y];
+  const DevPatch* P = A.patches + C->parent;
+  const int m[3] = {C->n[0] / 2, C->n[1] / 2, C->n[2] / 2};
+  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int d = 0, side = 0;
+  for (; d < 3; ++d) {
+    const long long nfd = 2LL * m[(d + 1) % 3] * m[(d + 2) % 3];
+    if (id < nfd) break;
+    id -= nfd;
+  }
+  if (d == 3) return;
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;  // tangential directions, t1 < t2
+  const long long per = (long long)m[t1] * m[t2];
+  side = (int)(id / per);
+  id -= side * per;
+  const int T1 = (int)(id % m[t1]), T2 = (int)(id / m[t1]);
+  const long long sp[3] = {1, P->px, P->plane}, sc[3] = {1, C->px, C->plane};
+  // parent face (array index along d), the parent cell outside, the child face
+  const int mp = side ? C->off[d] + m[d] - 1 + GH : C->off[d] - 1 + GH;
+  const int cell = side ? C->off[d] + m[d] + GH : C->off[d] - 1 + GH;
+  const int mc = side ? C->n[d] - 1 + GH : GH - 1;
+  const long long pt = (C->off[t1] + T1 + GH) * sp[t1] + (long long)(C->off[t2] + T2 + GH) * sp[t2];
+  const long long qf = mp * sp[d] + pt, qcell = cell * sp[d] + pt;
+  const long long qc = mc * sc[d] + (2 * T1 + GH) * sc[t1] + (long long)(2 * T2 + GH) * sc[t2];
+  const double* __restrict__ fp = P->mfs + (long long)d * NM * P->fstride;
+  const double* __restrict__ fcs = C->mfa + (long long)d * NM * C->fstride;
+  double* __restrict__ cp = P->mcons[A.plev->ring];
+  const double h = P->dx, sgn = side ? 1.0 : -1.0;
+#pragma unroll
+  for (int f = 0; f < NM; ++f) {
+    const double* x = fcs + f * C->fstride + qc;
+    // the fine faces in array order: (t2, t1) = (0,0), (0,1), (1,0), (1,1)
+    const double fine = 0.25 * (x[0] + x[sc[t1]] + x[sc[t2]] + x[sc[t2] + sc[t1]]);
+    cp[f * P->fstride + qcell] += (A.dt_parent / h) * (fine - fp[f * P->fstride + qf]) * sgn;
+  }
+}
+
 int blocks_for(long long n) {
   long long b = (n + 127) / 128;
   return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
@@ -810,6 +1042,22 @@ void launch_matter_update(const MatterArgs& a, cudaStream_t st) {
 }
 void launch_matter_prim2con(const MatterArgs& a, cudaStream_t st) {
   matter_prim2con_kernel<<<blocks_for((long long)a.NX * a.NY * a.NZ), 128, 0, st>>>(a);
+}
+void launch_matter_child_ghosts(const MatterArgs& a, cudaStream_t st) {
+  const long long sh = (long long)a.NX * a.NY * a.NZ - (long long)a.n[0] * a.n[1] * a.n[2];
+  matter_child_ghost_kernel<<<(unsigned)((sh + 127) / 128), 128, 0, st>>>(a);
+}
+void launch_matter_prolong(const MatterAmrArgs& a, int nchildren, long long max_shell, cudaStream_t st) {
+  if (nchildren == 0 || max_shell == 0) return;
+  matter_prolong_kernel<<<dim3((unsigned)((max_shell + 127) / 128), nchildren), 128, 0, st>>>(a);
+}
+void launch_matter_restrict(const MatterAmrArgs& a, int nchildren, long long max_cells, cudaStream_t st) {
+  if (nchildren == 0 || max_cells == 0) return;
+  matter_restrict_kernel<<<dim3((unsigned)((max_cells + 127) / 128), nchildren), 128, 0, st>>>(a);
+}
+void launch_matter_reflux(const MatterAmrArgs& a, int nchildren, long long max_faces, cudaStream_t st) {
+  if (nchildren == 0 || max_faces == 0) return;
+  matter_reflux_kernel<<<dim3((unsigned)((max_faces + 127) / 128), nchildren), 128, 0, st>>>(a);
 }
 
 }  // namespace sacrak

@@ -41,6 +41,22 @@ struct MatterArgs {
   double dt;
   double* out;                // update kernel with stage 0: d_t of the conserved variables
   unsigned* err;
+  // levels > 0: ghost cells from the parent (Sec. 2.2.1) -- the parent level,
+  // the time weights of its (oldest, middle, newest) time levels at this
+  // call's time (three valid levels / two), and whether the flux sums of the
+  // two-step average start with this step
+  const DevLevel* plev;
+  double wq[3], wl[3];
+  int first_substep;
+};
+
+// One child level's fluid operators at the refinement boundary (Sec. 2.2.1)
+struct MatterAmrArgs {
+  const DevPatch* patches;
+  const int* child_ids;       // the children (one level)
+  const DevLevel* plev;       // their parent level
+  const DevLevel* clev;       // their level
+  double dt_parent;           // reflux: the parent's step
 };
 
 // Primitive recovery of the stage's conserved state (active cells) with the
@@ -55,5 +71,17 @@ void launch_matter_flux(const MatterArgs& a, int dir, cudaStream_t st);
 void launch_matter_update(const MatterArgs& a, cudaStream_t st);
 // conserved variables of the primitives (after an upload of primitives)
 void launch_matter_prim2con(const MatterArgs& a, cudaStream_t st);
+// ghost cells of a level > 0 fluid from the cached prolongations of the
+// parent's time levels (instead of launch_matter_ghosts)
+void launch_matter_child_ghosts(const MatterArgs& a, cudaStream_t st);
+// prolongation of the parent's current fluid onto every child's ghost shell,
+// cached in the child's slot of the parent's current ring slot: conservative
+// WENO5 of D^ (x, y, z), 6th-order Lagrange of eps and u_i, fallbacks
+void launch_matter_prolong(const MatterAmrArgs& a, int nchildren, long long max_shell, cudaStream_t st);
+// parent cells under the children's active cells <- the mean of the 8 children
+void launch_matter_restrict(const MatterAmrArgs& a, int nchildren, long long max_cells, cudaStream_t st);
+// parent cells next to the children: the parent's boundary-face fluxes of its
+// last step replaced by the children's (averaged over 4 faces and 2 steps)
+void launch_matter_reflux(const MatterAmrArgs& a, int nchildren, long long max_faces, cudaStream_t st);
 
 }  // namespace sacrak

@@ -51,7 +51,7 @@ struct DevPatch {
   float2* hl[3];
   float2* sa;
   float2* sb;
-  // matter (FP64 one-level grids with a fluid): the densitised conserved
+  // matter (FP64 grids with a fluid): the densitised conserved
   // variables in the same slots as buf (5 fields each), the primitives and
   // the Lorentz factor (6 fields), the face fluxes along x, y, z (15) and the
   // matter terms of the Z4c right-hand side (11); null without a fluid
@@ -59,6 +59,13 @@ struct DevPatch {
   double* mprim;
   double* mflux;
   double* mzsrc;
+  // levels > 0 of a fluid grid: the parent's fluid in each ring slot prolonged
+  // onto this patch's ghost shell (D^, eps, u_i; 5 fields per slot), and the
+  // RK4-weighted face fluxes of the patch's last step (mfs) and of its last
+  // two steps averaged (mfa), 3 directions x 5 fields each, for the reflux
+  double* mgsh[3];
+  double* mfs;
+  double* mfa;
 };
 
 struct DevLevel {
