@@ -244,7 +244,7 @@ def main():
     ap.add_argument("--gw-steps", type=int, default=1000,
                     help="gauge-wave: RK4 steps on the coarsest grid; robust-stability: steps per grid")
     ap.add_argument("--case", default="amr7",
-                    choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep", "tov",
+                    choices=["amr7", "uniform96", "mixed-error", "gauge-wave", "robust-stability", "sweep", "tov", "tov-amr",
                              "cpu-coarse-step",
                              "amr7-zsym", "adm", "amr7-moving", "psi4"],
                     help="uniform96: RK4 steps of one 96^3 puncture patch only (for ncu captures); "
@@ -306,6 +306,8 @@ def main():
     if args.case == "psi4":
         psi4_case(torch, sk, args)
         return
+    if args.case == "tov-amr":
+        return tov_amr_case(torch, sk, args)
     if args.case == "tov":
         tov_case(torch, sk, args)
         return
@@ -877,6 +879,92 @@ def tov_case(torch, sk, args):
         torch.cuda.empty_cache()
     r = out["runs"]
     out["fluid_ms_per_step"] = r["spacetime+fluid"]["ms_per_rk4_step"] - r["spacetime"]["ms_per_rk4_step"]
+    print(json.dumps(out), flush=True)
+
+
+def _rest_mass(patches, fields, prims, children):
+    """Total rest mass of the composite grid, sum of sqrt(gamma) rho w dV over
+    the active cells not covered by a child (sqrt(gamma) = sqrt(det gt) / W^3,
+    w = sqrt(1 + gamma^ij u_i u_j), gamma^ij = W^2 gt^ij)."""
+    total = 0.0
+    for pid, (p, u, pr) in enumerate(zip(patches, fields, prims)):
+        g = p.g
+        a = (slice(g, -g),) * 3
+        W = u[0][a]
+        gt = [u[1 + c][a] for c in range(6)]
+        gxx, gxy, gxz, gyy, gyz, gzz = gt
+        det = gxx * (gyy * gzz - gyz * gyz) - gxy * (gxy * gzz - gyz * gxz) + gxz * (gxy * gyz - gyy * gxz)
+        inv = [(gyy * gzz - gyz * gyz), (gxz * gyz - gxy * gzz), (gxy * gyz - gxz * gyy),
+               (gxx * gzz - gxz * gxz), (gxy * gxz - gxx * gyz), (gxx * gyy - gxy * gxy)]
+        ul = [pr[2 + d][a] for d in range(3)]
+        pairs = [(0, 0, 0), (0, 1, 1), (0, 2, 2), (1, 1, 3), (1, 2, 4), (2, 2, 5)]
+        uu = sum((1.0 if i == j else 2.0) * inv[c] * ul[i] * ul[j] for i, j, c in pairs) / det * W * W
+        D = np.sqrt(det) / W ** 3 * pr[0][a] * np.sqrt(1.0 + uu)
+        for cid in children[pid]:
+            c = patches[cid]
+            off = [int(round((c.origin[d] - p.origin[d]) / p.dx)) for d in range(3)]
+            D[off[2]:off[2] + c.n[2] // 2, off[1]:off[1] + c.n[1] // 2, off[0]:off[0] + c.n[0] // 2] = 0.0
+        total += float(D.sum()) * p.dx ** 3
+    return total
+
+
+def tov_amr_case(torch, sk, args):
+    """The coupled coarse step of spacetime and fluid (Sec. 2.1.2, 2.2,
+    2.2.1) for the TOV star of the `tov` case on two levels: a 96^3 patch at
+    dx = 1/2 over [-24, 24]^3 and a 96^3 child at dx = 1/4 over [-12, 12]^3
+    around the star (R = 8.1 isotropic), the fluid's ghosts at the refinement
+    boundary by WENO5 / Lagrange prolongation, restriction and reflux after
+    the child's two steps.  Each step is one captured graph replay.
+    Reported: zone updates/s of the coupled coarse step (3 x 96^3 zone
+    updates) and of the spacetime alone on the same hierarchy, and the
+    relative change of the total rest mass over the timed steps (outflow
+    through the atmosphere at the outer boundary and atmosphere resets only:
+    the refinement boundary conserves it)."""
+    import initial_data as idd
+    from initial_data.tov import TOV, tov_patch_data
+    star = TOV()
+    P0 = idd.Patch(n=(96, 96, 96), dx=0.5, origin=(-24.0, -24.0, -24.0), level=0)
+    C1 = idd.Patch(n=(96, 96, 96), dx=0.25, origin=(-12.0, -12.0, -12.0), level=1)
+    ps = [P0, C1]
+    rho_atm, r_atm = 1e-12 * 1.28e-3, 8 * 24.0
+    data = [tov_patch_data(p, star, rho_atm) for p in ps]
+    zu = P0.active_points + 2 * C1.active_points
+    out = {"case": "tov-amr", "levels": [{"n": p.n[0], "dx": p.dx} for p in ps], "courant": args.courant,
+           "zone_updates_per_step": zu, "star": {"M": star.M, "R_isotropic": star.Rbar}, "runs": {}}
+    for name, matter in (("spacetime+fluid", 1), ("spacetime", 0)):
+        g = sk.Grid(2, P0.dx, ps, sk.Params(courant=args.courant, matter=matter), stream=torch.cuda.Stream())
+        if matter:
+            g.set_eos(star.K, [star.G], (), 1.8)
+            g.set_atmosphere(rho_atm, r_atm)
+        for i, (u, prim) in enumerate(data):
+            g.upload_fields(i, u)
+            if matter:
+                g.upload_matter(i, prim)
+        for _ in range(args.warmup):
+            g.level_step(0)
+        if matter:
+            m0 = _rest_mass(ps, [g.download_fields(i) for i in range(2)], [g.download_matter(i) for i in range(2)],
+                            [[1], []])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(g.stream)
+        for _ in range(args.steps):
+            g.level_step(0)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        run = {"ms_per_coarse_step": ms, "zone_updates_per_s": zu / (ms * 1e-3)}
+        if matter:
+            m1 = _rest_mass(ps, [g.download_fields(i) for i in range(2)], [g.download_matter(i) for i in range(2)],
+                            [[1], []])
+            run["rest_mass_change"] = (m1 - m0) / m0
+        out["runs"][name] = run
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    r = out["runs"]
+    out["fluid_ms_per_step"] = r["spacetime+fluid"]["ms_per_coarse_step"] - r["spacetime"]["ms_per_coarse_step"]
     print(json.dumps(out), flush=True)
 
 
