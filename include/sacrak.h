@@ -400,8 +400,9 @@ sacrak_status sacrak_set_wait_limit(sacrak_grid* grid, long long cycles);
  * default): within each RK4 step of a level > 0, the time fill of the
  * stage-2 and stage-3 inputs runs on a second stream of the library's
  * concurrently with the stage-1 kernel, the fill of the stage-4 input with
- * the stage-3 kernel, and the spatial prolongation of a parent's new time
- * level with the children's first stage; every call that launches them
+ * the stage-3 kernel, the spatial prolongation of a parent's new time level
+ * with the children's first stage, and (without zsym) that of its restricted
+ * level with the parent's next step; every call that launches them
  * makes the caller's stream wait for that stream before it returns (under
  * capture these are graph edges).  on = 0: every launch on the caller's
  * stream, one after another.  Results are the same bit for bit.  Drops the

@@ -766,6 +766,9 @@ void rk4_level(sacrak_grid* g, int l, double dt, double frac0, double dfrac) {
       launch_track(ta, g->stream);
       break;
     }
+  // work on the side stream reads this level's ring index (the prolongation
+  // of its restricted slot): it ends before the ring advances
+  join_side(g);
   launch_level_advance(g->d_levels + l, dt, g->stream);
   refresh_shells(g, l + 1, g->overlap);  // the children's cache of this level's new slot
   refresh_matter_shells(g, l + 1);
@@ -820,7 +823,14 @@ void level_step_rec(sacrak_grid* g, int l, double frac0, double dfrac) {
       refresh_matter_shells(g, l + 1);
     }
     zreflect(g, l, 1, 0);      // restricted cells next to z = 0 have mirrors among the ghosts
-    refresh_shells(g, l + 1);  // the restricted slot, for the next parent step
+    // the restricted slot, for the next parent step: with overlap on the side
+    // stream, beside the parent's next step, joined before that step
+    // advances the parent's ring (the kernel reads the ring); it reads only
+    // the parent's active cells, which that step does not change, and its
+    // readers, the children's time fills, come later.  Not under equatorial
+    // symmetry: there it also reads the parent's reflected z < 0 ghosts,
+    // which the parent's next stage-1 time fill rewrites before reflecting.
+    refresh_shells(g, l + 1, g->overlap && !g->prm.zsym);
   }
 }
 
