@@ -232,7 +232,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", type=int, default=None,
-                    help="uniform96: force this stage kernel (0 direct, 1-4 TMA tiles) after autotuning")
+                    help="force this stage kernel (ids of STAGE_KERNELS) on every level, no autotuning")
     ap.add_argument("--serial-ghosts", action="store_true",
                     help="refined levels' ghost fills and prolongation on the grid's stream, in order "
                          "(default: beside the stage kernels on a second stream)")
@@ -412,8 +412,11 @@ def measure(torch, sk, h, precision, args, world, dist):
     g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=stream)
     g.set_overlap(not args.serial_ghosts)
     g.set_initial_data(1, h.masses, h.positions)
+    if args.kernel is not None and precision == "mixed":
+        for l in range(len(h.levels)):
+            g.set_stage_kernel(l, args.kernel)
     tune = None
-    if precision == "mixed" and not args.no_autotune:
+    if precision == "mixed" and not args.no_autotune and args.kernel is None:
         us = g.autotune(reps=3)
         tune = {"kernels": [sk.STAGE_KERNELS[g.stage_kernel(l)] for l in range(len(h.levels))],
                 "us_per_launch": [[round(float(x), 1) for x in row] for row in us]}
@@ -1093,7 +1096,8 @@ def stage_kernel_timing(g, steps, overlap=True):
         import paper_2607_08743_gb300 as sk
         kn = {0: "z4c_stage_mixed_kernel"}
         kn.update({k: "z4c_stage_tma_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (1, 2, 3, 4)})
-        kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6, 8, 9, 10, 11, 12, 13, 14)})
+        kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6, 8, 9, 10, 11, 12, 13, 14, 18)})
+        kn.update({k: "z4c_stage_pair_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (15, 16, 17)})
         kn[7] = "z4c_deriv_kernel + z4c_algebra_kernel"
         names = sorted({kn[k] for k in ids})
         name = " + ".join(names)

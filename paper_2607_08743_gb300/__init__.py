@@ -44,7 +44,8 @@ EXPORTS = [
 # of the mixed derivatives exchanged by warp shuffles, 13 as 12 with 4 CTAs per SM,
 # 14 as 10 with 4 CTAs per SM, 15 two x-adjacent points per thread with 128-bit
 # loads of the hi/lo pairs, 16 as 15 prefetching the next field's z-arm rows,
-# 17 as 16 with 3 CTAs per SM (more of the SM's memory left to L1)
+# 17 as 16 with 3 CTAs per SM (more of the SM's memory left to L1), 18 as 10
+# with a persistent grid (resident CTAs walk the level's tiles)
 STAGE_KERNELS = {0: "direct", 1: "tma 32x4x1", 2: "tma 32x2x2", 3: "tma 32x4x2", 4: "tma 32x8x1",
                  5: "l1 pairs", 6: "l1 pairs + prefetch", 7: "split deriv + algebra",
                  8: "l1 pairs + prefetch, 4/SM", 9: "l1 pairs + star prefetch",
@@ -52,7 +53,8 @@ STAGE_KERNELS = {0: "direct", 1: "tma 32x4x1", 2: "tma 32x2x2", 3: "tma 32x4x2",
                  12: "l1 pairs + z-arm prefetch + x shuffles", 13: "l1 pairs + z-arm prefetch + x shuffles, 4/SM",
                  14: "l1 pairs + z-arm prefetch, 4/SM", 15: "two points/thread, 128-bit loads",
                  16: "two points/thread, 128-bit loads + z-arm prefetch",
-                 17: "two points/thread, 128-bit loads + z-arm prefetch, 3/SM"}
+                 17: "two points/thread, 128-bit loads + z-arm prefetch, 3/SM",
+                 18: "l1 pairs + z-arm prefetch, persistent"}
 
 
 class SacrakError(RuntimeError):

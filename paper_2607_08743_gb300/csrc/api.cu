@@ -306,7 +306,8 @@ constexpr int K_LDG3 = TMA_NVARIANTS + 1, K_LDG4 = TMA_NVARIANTS + 2, K_SPLIT = 
               K_LDG_PF4 = TMA_NVARIANTS + 4, K_LDG_PFS = TMA_NVARIANTS + 5, K_LDG_PFZ = TMA_NVARIANTS + 6,
               K_LDG_PFE = TMA_NVARIANTS + 7, K_LDG_SHF = TMA_NVARIANTS + 8, K_LDG_SHF4 = TMA_NVARIANTS + 9,
               K_LDG_PFZ4 = TMA_NVARIANTS + 10, K_PAIR = TMA_NVARIANTS + 11, K_PAIR_PFZ = TMA_NVARIANTS + 12,
-              K_PAIR_PFZ3 = TMA_NVARIANTS + 13, K_COUNT = TMA_NVARIANTS + 14;
+              K_PAIR_PFZ3 = TMA_NVARIANTS + 13, K_LDG_PFZ_PERS = TMA_NVARIANTS + 14,
+              K_COUNT = TMA_NVARIANTS + 15;
 
 // pair-kernel variant of a kernel id (-1 for others)
 int pair_variant(int k) { return k == K_PAIR ? 0 : k == K_PAIR_PFZ ? 1 : k == K_PAIR_PFZ3 ? 2 : -1; }
@@ -314,7 +315,8 @@ int pair_variant(int k) { return k == K_PAIR ? 0 : k == K_PAIR_PFZ ? 1 : k == K_
 // L1-path variant of a kernel id (-1 for others)
 int ldg_variant(int k) {
   return k == K_LDG3 ? 0 : k == K_LDG4 ? 1 : k == K_LDG_PF4 ? 2 : k == K_LDG_PFS ? 3 : k == K_LDG_PFZ ? 4
-         : k == K_LDG_PFE ? 5 : k == K_LDG_SHF ? 6 : k == K_LDG_SHF4 ? 7 : k == K_LDG_PFZ4 ? 8 : -1;
+         : k == K_LDG_PFE ? 5 : k == K_LDG_SHF ? 6 : k == K_LDG_SHF4 ? 7 : k == K_LDG_PFZ4 ? 8
+         : k == K_LDG_PFZ_PERS ? 9 : -1;
 }
 
 bool kernel_eligible(const sacrak_grid* g, int k, const std::vector<int>& pids) {
@@ -443,7 +445,7 @@ sacrak_status select_kernel(sacrak_grid* g, int l, int kernel) {
     if (st != SACRAK_OK) return st;
   }
   if (ldg_variant(kernel) >= 0) {
-    static bool done[64][9] = {};  // shared-memory opt-in, once per device
+    static bool done[64][10] = {};  // shared-memory opt-in (and resident grid), once per device
     const int v = ldg_variant(kernel);
     int dev = 0;
     cudaGetDevice(&dev);

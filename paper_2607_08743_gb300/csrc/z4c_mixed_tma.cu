@@ -321,9 +321,8 @@ __device__ __forceinline__ void prefetch_field(const float2* F, long long sy, lo
 // 2 its star rows only, 3 its z-arm rows only, 4 none of its rows (only the
 // epilogue's streaming reads into L2)
 template <int MINB, int MODE, int PF, bool SHF = false>
-__global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
-  extern __shared__ float sd[];
-  const Tile tl = S.tiles[blockIdx.x];
+__device__ __forceinline__ void ldg_tile(const StageArgs& S, int tile, float* sd) {
+  const Tile tl = S.tiles[tile];
   const DevPatch* P = S.patches + tl.patch;
   const int t = threadIdx.x;
   const int i = tl.x0 + (t & 31), j = tl.y0 + (t >> 5), k = tl.z0;
@@ -377,22 +376,54 @@ __global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
   }
 }
 
-template <int MINB, int PF, bool SHF = false>
-bool setup_ldg() {
-  const int smem = NSLOT * 128 * 4;
-  return cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 0, PF, SHF>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
-         cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 1, PF, SHF>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+// one CTA per tile, or (PERS) a grid of resident CTAs that walks the level's
+// tiles with a static stride (one persistent launch per level)
+template <int MINB, int MODE, int PF, bool SHF, bool PERS>
+__global__ void __launch_bounds__(128, MINB) z4c_stage_ldg_kernel(StageArgs S) {
+  extern __shared__ float sd[];
+  if (!PERS) {
+    ldg_tile<MINB, MODE, PF, SHF>(S, blockIdx.x, sd);
+    return;
+  }
+  for (int tile = blockIdx.x; tile < S.ntiles; tile += gridDim.x) ldg_tile<MINB, MODE, PF, SHF>(S, tile, sd);
 }
 
-template <int MINB, int PF, bool SHF = false>
+// resident CTAs of the persistent variant per device (0: not set up)
+int g_pers_grid[64] = {};
+
+template <int MINB, int PF, bool SHF = false, bool PERS = false>
+bool setup_ldg() {
+  const int smem = NSLOT * 128 * 4;
+  bool ok = cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 0, PF, SHF, PERS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+            cudaFuncSetAttribute(z4c_stage_ldg_kernel<MINB, 1, PF, SHF, PERS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+  if (ok && PERS) {
+    int dev = 0, nsm = 0, nb = 0;
+    ok = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 &&
+         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, z4c_stage_ldg_kernel<MINB, 0, PF, SHF, PERS>, 128,
+                                                       smem) == cudaSuccess &&
+         nb > 0;
+    if (ok) g_pers_grid[dev] = nsm * nb;
+  }
+  return ok;
+}
+
+template <int MINB, int PF, bool SHF = false, bool PERS = false>
 void launch_ldg(const StageArgs& a, cudaStream_t st) {
   const int smem = NSLOT * 128 * 4;
+  int grid = a.ntiles;
+  if (PERS) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int res = (dev >= 0 && dev < 64) ? g_pers_grid[dev] : 0;
+    if (res > 0 && res < grid) grid = res;
+  }
   if (a.stage == 0)
-    z4c_stage_ldg_kernel<MINB, 1, PF, SHF><<<a.ntiles, 128, smem, st>>>(a);
+    z4c_stage_ldg_kernel<MINB, 1, PF, SHF, PERS><<<grid, 128, smem, st>>>(a);
   else
-    z4c_stage_ldg_kernel<MINB, 0, PF, SHF><<<a.ntiles, 128, smem, st>>>(a);
+    z4c_stage_ldg_kernel<MINB, 0, PF, SHF, PERS><<<grid, 128, smem, st>>>(a);
 }
 
 // ------------------------------------------------------------------ split path
@@ -508,7 +539,8 @@ void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st) {
 // 3 (3, prefetch of the star rows only), 4 (3, z-arm rows only), 5 (3, the
 // epilogue's reads only), 6 (as 4, the x-neighbour inner differences of the
 // mixed derivatives exchanged by warp shuffles), 7 (as 6 with 4 CTAs/SM),
-// 8 (as 4 with 4 CTAs/SM, 128 registers)
+// 8 (as 4 with 4 CTAs/SM, 128 registers), 9 (as 4, persistent: resident
+// CTAs walk the level's tiles)
 int ldg_setup(int v) {
   switch (v) {
     case 0: return setup_ldg<3, 0>();
@@ -520,6 +552,7 @@ int ldg_setup(int v) {
     case 6: return setup_ldg<3, 3, true>();
     case 7: return setup_ldg<4, 3, true>();
     case 8: return setup_ldg<4, 3>();
+    case 9: return setup_ldg<3, 3, false, true>();
   }
   return 0;
 }
@@ -536,6 +569,7 @@ void launch_stage_ldg(int v, const StageArgs& a, cudaStream_t st) {
     case 6: launch_ldg<3, 3, true>(a, st); break;
     case 7: launch_ldg<4, 3, true>(a, st); break;
     case 8: launch_ldg<4, 3>(a, st); break;
+    case 9: launch_ldg<3, 3, false, true>(a, st); break;
   }
 }
 

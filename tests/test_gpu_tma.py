@@ -27,7 +27,7 @@ skbuild.build()
 TMA = [1, 2, 3, 4]
 # L1 path, split launches and two points per thread with 128-bit loads: the
 # same arithmetic
-PAIRS = [5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17]
+PAIRS = [5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18]
 TOL = 1e-4          # mixed precision vs the FP64 oracle
 TOL_KERNELS = 2e-5  # TMA kernel vs direct mixed kernel, same data
 
@@ -130,7 +130,7 @@ def _tma_hierarchy():
     return h, idd.hierarchy_data(h, noise=1e-10)
 
 
-@pytest.mark.parametrize("kernel", [1, 7, 10, 15, 16])
+@pytest.mark.parametrize("kernel", [1, 7, 10, 15, 16, 18])
 def test_tma_level_step_hierarchy_vs_oracle(kernel):
     h, states = _tma_hierarchy()
     g = sk.Grid(len(h.levels), h.dx0, h.patches, sk.Params(precision=1), stream=torch.cuda.Stream())
