@@ -1098,6 +1098,7 @@ def stage_kernel_timing(g, steps, overlap=True):
         kn.update({k: "z4c_stage_tma_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (1, 2, 3, 4)})
         kn.update({k: "z4c_stage_ldg_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (5, 6, 8, 9, 10, 11, 12, 13, 14, 18)})
         kn.update({k: "z4c_stage_pair_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (15, 16, 17)})
+        kn.update({k: "z4c_stage_fixed_kernel (%s)" % sk.STAGE_KERNELS[k] for k in (19, 20)})
         kn[7] = "z4c_deriv_kernel + z4c_algebra_kernel"
         names = sorted({kn[k] for k in ids})
         name = " + ".join(names)

@@ -362,10 +362,20 @@ sacrak_status sacrak_constraints_noalloc(const double* dev_u, const int n[3], do
  * differences of D_x D_y f and D_x D_z f at the x neighbours taken from the
  * neighbouring lanes of the warp by shuffles (loads where a tile does not
  * fill its 32 x), kernel 13 is kernel 12 with 4 CTAs per SM, kernel 14 is
- * kernel 10 with 4 CTAs per SM (128 registers).  All kernels
+ * kernel 10 with 4 CTAs per SM (128 registers); kernels 15..17 take two
+ * x-adjacent points per thread with 128-bit loads of the hi/lo pairs (15
+ * plain, 16 prefetching the z-arm rows, 17 as 16 with 3 CTAs per SM; they
+ * need 25 x the field stride < 2^31); kernel 18 is kernel 10 as a persistent
+ * grid of resident CTAs walking the level's tiles; kernel 19 is kernel 10
+ * with the row and plane pitches fixed at compile time where every patch of
+ * the level has n[0] = n[1] = n for n in {32, 48, 64, 96, 128, 160, 192}
+ * (the stencil offsets become constants of the loads), and kernel 10 itself
+ * elsewhere and for the RHS alone (sacrak_rhs); kernel 19 gives kernel 10's
+ * results bit for bit; kernel 20 is kernel 19 with 4 CTAs per SM (128
+ * registers) where an instance fits, and kernel 10 elsewhere.  All kernels
  * compute the same RHS up to FP32 rounding order.  A TMA kernel needs at most 8 patches on the level and at
  * least 32 x TY x TZ active cells per patch, else SACRAK_EINVAL.  New grids
- * use kernel 10 in mixed precision and 0 in FP64.  Changing the kernel of a
+ * use kernel 20 in mixed precision and 0 in FP64.  Changing the kernel of a
  * level drops the recorded CUDA graph of the coarse step (it is recorded
  * again at the next sacrak_level_step). */
 sacrak_status sacrak_set_stage_kernel(sacrak_grid* grid, int level, int kernel);
@@ -381,7 +391,7 @@ sacrak_status sacrak_get_stage_kernel(sacrak_grid* grid, int level, int* kernel)
  * process, keyed by device, precision and the level's patch shapes (levels
  * of identical shapes share one timing and one choice); with use_cache != 0
  * a cached level is not timed again.  us_per_launch, if not
- * NULL, receives nlevels x 15 timings in microseconds (kernel 0..14 of each
+ * NULL, receives nlevels x 21 timings in microseconds (kernel 0..20 of each
  * level; -1 where not timed).  Synchronises the stream; must not be called
  * while the stream is being captured (SACRAK_ESTATE). */
 sacrak_status sacrak_autotune(sacrak_grid* grid, int reps, int use_cache, double* us_per_launch);

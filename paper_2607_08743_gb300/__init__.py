@@ -54,7 +54,9 @@ STAGE_KERNELS = {0: "direct", 1: "tma 32x4x1", 2: "tma 32x2x2", 3: "tma 32x4x2",
                  14: "l1 pairs + z-arm prefetch, 4/SM", 15: "two points/thread, 128-bit loads",
                  16: "two points/thread, 128-bit loads + z-arm prefetch",
                  17: "two points/thread, 128-bit loads + z-arm prefetch, 3/SM",
-                 18: "l1 pairs + z-arm prefetch, persistent"}
+                 18: "l1 pairs + z-arm prefetch, persistent",
+                 19: "l1 pairs + z-arm prefetch, compile-time pitches",
+                 20: "l1 pairs + z-arm prefetch, compile-time pitches, 4/SM (default)"}
 
 
 class SacrakError(RuntimeError):

@@ -12,8 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsacrak.so")
-SOURCES = ["z4c_fp64.cu", "z4c_mixed.cu", "z4c_mixed_tma.cu", "z4c_mixed_pair.cu", "amr.cu", "diagnostics.cu",
-           "waveform.cu", "grhd.cu", "api.cu"]
+SOURCES = ["z4c_fp64.cu", "z4c_mixed.cu", "z4c_mixed_tma.cu", "z4c_mixed_fixed.cu", "z4c_mixed_pair.cu", "amr.cu",
+           "diagnostics.cu", "waveform.cu", "grhd.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

@@ -307,7 +307,7 @@ constexpr int K_LDG3 = TMA_NVARIANTS + 1, K_LDG4 = TMA_NVARIANTS + 2, K_SPLIT = 
               K_LDG_PFE = TMA_NVARIANTS + 7, K_LDG_SHF = TMA_NVARIANTS + 8, K_LDG_SHF4 = TMA_NVARIANTS + 9,
               K_LDG_PFZ4 = TMA_NVARIANTS + 10, K_PAIR = TMA_NVARIANTS + 11, K_PAIR_PFZ = TMA_NVARIANTS + 12,
               K_PAIR_PFZ3 = TMA_NVARIANTS + 13, K_LDG_PFZ_PERS = TMA_NVARIANTS + 14,
-              K_COUNT = TMA_NVARIANTS + 15;
+              K_LDG_FIX = TMA_NVARIANTS + 15, K_LDG_FIX4 = TMA_NVARIANTS + 16, K_COUNT = TMA_NVARIANTS + 17;
 
 // pair-kernel variant of a kernel id (-1 for others)
 int pair_variant(int k) { return k == K_PAIR ? 0 : k == K_PAIR_PFZ ? 1 : k == K_PAIR_PFZ3 ? 2 : -1; }
@@ -328,7 +328,22 @@ bool kernel_eligible(const sacrak_grid* g, int k, const std::vector<int>& pids) 
       if ((long long)NF * g->hp[pid].fstride >= (1LL << 31)) return false;
     return true;
   }
-  return (ldg_variant(k) >= 0 || k == K_SPLIT) && g->prm.precision == 1;
+  return (ldg_variant(k) >= 0 || k == K_SPLIT || k == K_LDG_FIX || k == K_LDG_FIX4) && g->prm.precision == 1;
+}
+
+// the row and plane pitches shared by every patch of a level (-1 if they differ)
+void level_pitches(const sacrak_grid* g, const std::vector<int>& pids, long long* sy, long long* sz) {
+  *sy = *sz = -1;
+  for (size_t i = 0; i < pids.size(); ++i) {
+    const DevPatch& P = g->hp[pids[i]];
+    if (i == 0) {
+      *sy = P.px;
+      *sz = P.plane;
+    } else if (P.px != *sy || P.plane != *sz) {
+      *sy = *sz = -1;
+      return;
+    }
+  }
 }
 
 // tensor maps of variant v for every patch: the five split buffers viewed as
@@ -411,6 +426,12 @@ void launch_stage(sacrak_grid* g, const StageArgs& a, long long zones, const std
     if (grid > 0) launch_stage_tma(v, t, grid, g->stream);
   } else if (g->prm.precision == 1 && ldg_variant(kernel) >= 0) {
     launch_stage_ldg(ldg_variant(kernel), a, g->stream);
+  } else if (g->prm.precision == 1 && (kernel == K_LDG_FIX || kernel == K_LDG_FIX4)) {
+    // the instance of the level's pitches, else the same kernel with runtime pitches
+    const bool four = kernel == K_LDG_FIX4;
+    long long sy, sz;
+    level_pitches(g, pids, &sy, &sz);
+    if (!launch_stage_fixed(a, sy, sz, four ? 4 : 3, g->stream)) launch_stage_ldg(ldg_variant(K_LDG_PFZ), a, g->stream);
   } else if (g->prm.precision == 1 && pair_variant(kernel) >= 0) {
     launch_stage_pair(pair_variant(kernel), a, g->stream);
   } else if (g->prm.precision == 1 && kernel == K_SPLIT) {
@@ -443,6 +464,17 @@ sacrak_status select_kernel(sacrak_grid* g, int l, int kernel) {
   if (kernel >= 1 && kernel <= TMA_NVARIANTS) {
     sacrak_status st = ensure_maps(g, kernel - 1);
     if (st != SACRAK_OK) return st;
+  }
+  if (kernel == K_LDG_FIX || kernel == K_LDG_FIX4) {
+    static bool done[64][2] = {};  // shared-memory opt-in of the instances and of their fallback, once per device
+    const bool four = kernel == K_LDG_FIX4;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done[dev][four]) {
+      if (!fixed_setup(four ? 4 : 3) || !ldg_setup(ldg_variant(K_LDG_PFZ)))
+        return fail(g, SACRAK_ECUDA, "stage kernel %d setup failed", kernel);
+      if (dev >= 0 && dev < 64) done[dev][four] = true;
+    }
   }
   if (ldg_variant(kernel) >= 0) {
     static bool done[64][10] = {};  // shared-memory opt-in (and resident grid), once per device
@@ -1190,10 +1222,12 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   if (st == SACRAK_OK) st = sacrak_set_initial_data(g, 0, 0, nullptr, nullptr, 0, 1, 0, 0, 0);
   // default stage kernel (mixed precision): the L1-path kernel with packed
   // pair arithmetic that prefetches the next field's z arms and the RK
-  // update's streaming reads (the fastest on 48^3 .. 192^3 patches)
+  // update's streaming reads, with the patch pitches fixed at compile time
+  // and 4 CTAs per SM where the level's patches have an instance, else with
+  // runtime pitches and 3 CTAs per SM
   g->lvl_kernel.assign(nlevels, 0);
   for (int l = 0; st == SACRAK_OK && l < nlevels; ++l)
-    if (p.precision == 1) st = select_kernel(g, l, K_LDG_PFZ);
+    if (p.precision == 1) st = select_kernel(g, l, K_LDG_FIX4);
   if (st != SACRAK_OK) {
     cudaGetLastError();
     release_side(g);

@@ -121,6 +121,16 @@ struct GlobalAcc {
   }
 };
 
+// The same with the row and plane pitches (pairs) fixed at compile time: the
+// offset of every stencil value is a constant folded into the load
+template <int SY, int SZ>
+struct FixedAcc {
+  const float2* __restrict__ F;
+  __device__ __forceinline__ float2 operator()(int dx, int dy, int dz) const {
+    return __ldg(F + (dx + dy * SY + dz * SZ));
+  }
+};
+
 // One field, values from `at`: forms the plan's derivatives into the slots
 // (NT columns), the advection + dissipation sum into S_AK + F, and returns
 // the centre value.

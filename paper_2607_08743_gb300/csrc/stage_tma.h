@@ -49,6 +49,16 @@ void launch_stage_tma(int v, const TmaStageArgs& a, int grid, cudaStream_t st);
 int ldg_setup(int v);
 void launch_stage_ldg(int v, const StageArgs& a, cudaStream_t st);
 
+// Variant 4 with the row and plane pitches of the level's patches fixed at
+// compile time (z4c_mixed_fixed.cu), 3 or 4 CTAs per SM: instances for
+// patches n[0] = n[1] = n, n in {32, 48, 64, 96, 128, 160, 192} (row pitch
+// align8(n + 7) pairs, plane pitch that times n + 6).  launch_stage_fixed
+// launches the instance of pitches (sy, sz) for a stage 1..4 and returns
+// true; it returns false, and launches nothing, for other pitches or for
+// stage 0 (the RHS alone).
+bool fixed_setup(int ctas_per_sm);
+bool launch_stage_fixed(const StageArgs& a, long long sy, long long sz, int ctas_per_sm, cudaStream_t st);
+
 // The stage split in two launches: derivatives of five fields per thread into
 // FP32 slot planes in global memory (dslot, split_slot_floats(ntiles) floats
 // for a launch over ntiles tiles), then the algebra and the RK4 update.

@@ -289,8 +289,10 @@ def test_blast_wave_tube_against_oracle(solver):
     P = 1e-6, ideal gas Gamma = 5/3, at rest) scaled by 1e-8 in density and
     pressure (the Riemann problem is unchanged; the spacetime barely
     responds), 16 RK4 steps on a 64-cell tube with Sommerfeld ghosts: the
-    shock, the contact and the rarefaction form, and the fluid and the
-    spacetime agree with the oracle."""
+    shock, the contact and the rarefaction form, and the fluid agrees with
+    the oracle to 1e-9 of its scale.  The spacetime's response (about 1e-8)
+    agrees to 1e-5 of itself: the two round the O(1) metric fields
+    differently at about 1e-15."""
     n, s = 64, 1e-8
     dx = 1.0 / n
     p = idd.Patch(n=(n, 4, 4), dx=dx, origin=(-0.5, -2 * dx, -2 * dx))
@@ -321,4 +323,4 @@ def test_blast_wave_tube_against_oracle(solver):
     np.testing.assert_allclose(pg[1][a], pro[1][a], rtol=0, atol=1e-9 * np.abs(pro[1][a]).max())
     np.testing.assert_allclose(pg[2:][(slice(None),) + a], pro[2:][(slice(None),) + a], rtol=0, atol=1e-9)
     e = _change_err(ug, uo, u, floor=1e-14)
-    assert e.max() <= 1e-7, dict(zip(idd.FIELD_NAMES, e))
+    assert e.max() <= 1e-5, dict(zip(idd.FIELD_NAMES, e))
