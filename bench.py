@@ -361,7 +361,7 @@ def main():
 # the stages, divided by its 884,736 zones), by (precision, stage kernel id);
 # the captures are in profiles/.  A kernel without a capture reports no
 # traffic; levels on different captured kernels report the largest.
-NCU_TRAFFIC_PER_ZONE = {(0, 0): 1183.6, (1, 10): 1064.6}
+NCU_TRAFFIC_PER_ZONE = {(0, 0): 1183.6, (1, 10): 1064.6, (1, 20): 1103.5}
 # the metric's roofline: the algorithmic bytes of one RK4 step (16 FP64
 # field passes of 25 fields) per zone update, the same in both precisions
 # (the hi/lo split copies of mixed precision are an implementation choice)
