@@ -29,9 +29,16 @@ BOHierarchy (oracle/__init__.py):
   over the child's two steps.  With periodic or no-flux outer boundaries the
   total rest mass (sum of D^ dV over the cells not covered by a finer level)
   is then conserved to rounding.
+* Equatorial reflection symmetry (Sec. 2.2.2: only z >= 0 evolved): the
+  fluid's z < 0 ghost layers of a patch on z = 0 mirror the layers above,
+  rho, eps, u_x, u_y, D^, J^_x, J^_y, E^ even and u_z, J^_z odd in z, after
+  every other ghost treatment; a child on z = 0 is prolonged from its
+  parent extended below z = 0 by the same mirror image (the values the
+  full domain holds there), and its own z < 0 ghosts are then reflected.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from typing import List, Optional
 
@@ -84,6 +91,40 @@ def linear_children(q, axis):
     out[2:2 * N - 2:2] = 0.75 * q[1:N - 1] + 0.25 * q[0:N - 2]
     out[3:2 * N - 1:2] = 0.75 * q[1:N - 1] + 0.25 * q[2:N]
     return np.moveaxis(out, 0, axis)
+
+
+# ------------------------------------------------------------------ equatorial symmetry
+
+PRIM_Z_PARITY = np.array([1.0, 1.0, 1.0, 1.0, -1.0])  # rho, eps, u_x, u_y, u_z
+CONS_Z_PARITY = np.array([1.0, 1.0, 1.0, -1.0, 1.0])  # D^, J^_x, J^_y, J^_z, E^
+
+
+def fill_zreflect_fluid(p, arr, parity):
+    """z -> -z mirror of the z < 0 ghost layers of a patch whose lower face
+    is z = 0: layer k (k < g, at z = (k - g + 1/2) dx) takes parity times
+    layer 2g - 1 - k (at -z)."""
+    if not z4c.touches_equator(p):
+        raise ValueError("the patch's lower z face is not z = 0")
+    g = p.g
+    out = np.array(arr, dtype=np.float64, copy=True)
+    for k in range(g):
+        out[:, k] = parity[:, None, None] * arr[:, 2 * g - 1 - k]
+    return out
+
+
+def mirror_extend(p, arr, parity, rows):
+    """A patch on z = 0 and its array extended by `rows` layers below its
+    z < 0 ghosts, each the mirror image (layer -m takes parity times layer
+    2g - 1 + m): the patch that describes the extended array has its origin
+    `rows` cells lower and `rows` more active cells along z."""
+    if not z4c.touches_equator(p):
+        raise ValueError("the patch's lower z face is not z = 0")
+    g = p.g
+    below = [parity[:, None, None] * arr[:, 2 * g - 1 + m] for m in range(rows, 0, -1)]
+    ext = np.concatenate([np.stack(below, axis=1), arr], axis=1)
+    q = dataclasses.replace(p, n=(p.n[0], p.n[1], p.n[2] + rows),
+                            origin=(p.origin[0], p.origin[1], p.origin[2] - rows * p.dx))
+    return q, ext
 
 
 # ------------------------------------------------------------------ geometry of a child in its parent
@@ -267,22 +308,31 @@ class MatterHierarchy(z4c.BOHierarchy):
     terms, the fluid's stage with the stage's metric.  After a level's two
     child steps: the spacetime as in BOHierarchy, then the fluid's
     restriction and reflux and the parent's primitives recovered again.
-    Patches of one level must not overlap."""
+    Patches of one level must not overlap.  With zsym only z >= 0 is
+    evolved: spacetime and fluid ghosts below z = 0 by reflection."""
 
     def __init__(self, hierarchy, states, prims, eos, floors, prm, courant=0.25, bc0=z4c.BC_PERIODIC,
-                 solver="hllc", reflux=True):
-        super().__init__(hierarchy, states, prm, courant=courant, bc0=bc0)
+                 solver="hllc", reflux=True, zsym=False):
+        super().__init__(hierarchy, states, prm, courant=courant, bc0=bc0, zsym=zsym)
         self.eos, self.floors, self.solver, self.do_reflux = eos, floors, solver, reflux
         self.mbc = "periodic" if bc0 == z4c.BC_PERIODIC else "outflow"
         self.ctl = []  # time levels of (cons, prim) per patch, oldest first
         for pid, (u, pr) in enumerate(zip(states, prims)):
             cons, _, _, _ = grhd.prim2con(pr, grhd.metric(u), eos)
             prn, cons, _ = grhd.recover(cons, u, eos, floors[pid])
-            self.ctl.append([(cons, self._fill_level0(pid, prn) if self.patches[pid].level == 0 else prn)])
+            prn = self._fill_level0(pid, prn) if self.patches[pid].level == 0 else prn
+            self.ctl.append([self._reflect_fluid(pid, cons, prn)])
         self.fstep = [None] * len(self.patches)  # the last step's RK4-weighted face fluxes
         self.favg = [None] * len(self.patches)   # a child's, averaged over its two steps
         self.children = [[c for c in range(len(self.patches)) if self.parent[c] == pid]
                          for pid in range(len(self.patches))]
+
+    def _reflect_fluid(self, pid, cons, prim):
+        """(cons, prim) with the z < 0 ghosts mirrored (zsym, patches on z = 0)."""
+        if not (self.zsym and z4c.touches_equator(self.patches[pid])):
+            return cons, prim
+        p = self.patches[pid]
+        return fill_zreflect_fluid(p, cons, CONS_Z_PARITY), fill_zreflect_fluid(p, prim, PRIM_Z_PARITY)
 
     def _fill_level0(self, pid, prim):
         fill = grhd.periodic_ghosts if self.mbc == "periodic" else grhd.outflow_ghosts
@@ -296,8 +346,13 @@ class MatterHierarchy(z4c.BOHierarchy):
         src = levels[-3:] if len(levels) >= 3 else [levels[-2], levels[-1]]
         ws = w if len(levels) >= 3 else w[1:]
         vals = None
+        on_equator = self.zsym and z4c.touches_equator(self.patches[pid])
         for wi, (cp, pp) in zip(ws, src):
-            v = prolong_fluid(self.patches[ppid], cp, pp, self.patches[pid])
+            par = self.patches[ppid]
+            if on_equator:  # the stencils reach below z = 0: the parent's mirror image
+                _, cp = mirror_extend(par, cp, CONS_Z_PARITY, 2)
+                par, pp = mirror_extend(par, pp, PRIM_Z_PARITY, 2)
+            v = prolong_fluid(par, cp, pp, self.patches[pid])
             vals = wi * v if vals is None else vals + wi * v
         gp = ghost_primitives(vals, self.patches[pid], u, self.eos)
         mask = ghost_mask(self.patches[pid])
@@ -308,8 +363,11 @@ class MatterHierarchy(z4c.BOHierarchy):
     def _prims(self, pid, cons, u, frac):
         pr, cons, _ = grhd.recover(cons, u, self.eos, self.floors[pid])
         if self.patches[pid].level == 0:
-            return self._fill_level0(pid, pr), cons
-        return self._fluid_ghosts(pid, pr, u, frac), cons
+            pr = self._fill_level0(pid, pr)
+        else:
+            pr = self._fluid_ghosts(pid, pr, u, frac)
+        cons, pr = self._reflect_fluid(pid, cons, pr)
+        return pr, cons
 
     def _rk4_level(self, l, frac0, dfrac):
         ids = self.level_ids[l]
@@ -330,6 +388,7 @@ class MatterHierarchy(z4c.BOHierarchy):
             if l > 0:
                 for a, pid in enumerate(ids):
                     cur[a] = self._fill_child_ghosts(pid, cur[a], frac0 + stage_frac[s - 1] * dfrac)
+            cur = self._reflect(ids, cur)
             if s == 1:
                 un = [c.copy() for c in cur]
             out = [np.empty_like(a) for a in un]
@@ -356,6 +415,7 @@ class MatterHierarchy(z4c.BOHierarchy):
                     nxt[act] = ym[a][act] + RK_B[3] * dt * km[act]
                 cs[a] = nxt
             cur = out
+        cur = self._reflect(ids, cur)  # the children's prolongation reads these ghosts
         for a, pid in enumerate(ids):
             if l == 0 and self.bc0 == z4c.BC_PERIODIC:
                 cur[a] = z4c.fill_periodic(self.patches[pid], cur[a])
@@ -380,10 +440,15 @@ class MatterHierarchy(z4c.BOHierarchy):
             kids = self.level_ids[l + 1]
             for pid in kids:
                 self.tl[pid][-1] = self._fill_child_ghosts(pid, self.tl[pid][-1], 1.0)
+            for pid, c in zip(kids, self._reflect(kids, [self.tl[pid][-1] for pid in kids])):
+                self.tl[pid][-1] = c
             for pid in kids:
                 ppid = self.parent[pid]
                 self.tl[ppid][-1] = z4c.restrict(self.patches[ppid], self.tl[ppid][-1],
                                                  self.patches[pid], self.tl[pid][-1])
+            ids = self.level_ids[l]  # restricted cells next to z = 0 have mirrors among the ghosts
+            for pid, c in zip(ids, self._reflect(ids, [self.tl[pid][-1] for pid in ids])):
+                self.tl[pid][-1] = c
             # the fluid: restriction, reflux, the parent's primitives again
             for pid in kids:
                 ppid = self.parent[pid]
