@@ -88,8 +88,10 @@ typedef struct {
                             an odd number of z indices) after every other ghost treatment;
                             not with bc = 1 */
   int matter;            /* 1: a perfect fluid evolved with the spacetime (Sec. 2.1.2, 2.2):
-                            FP64, no zsym, no overlapping patches on a level, no
-                            moving patches; see the matter calls below */
+                            FP64, no overlapping patches on a level, no moving
+                            patches; with zsym the fluid's z < 0 ghosts are
+                            reflected too (u_z and J_z odd, the rest even); see the
+                            matter calls below */
 } sacrak_params;
 
 /* One patch: refinement level, active cells per axis, lower face of active

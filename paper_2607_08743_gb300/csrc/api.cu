@@ -645,6 +645,8 @@ void refresh_shells(sacrak_grid* g, int l, bool side = false) {
                        side ? g->side : g->stream);
 }
 
+MatterArgs matter_args(const sacrak_grid* g, int pid, int stage, double dt, double s0, double ds, int wstage);
+
 // after new data: every child level's cache for its parent's current slot,
 // and (mixed precision) the hi/lo split of every current level
 void refresh_all_shells(sacrak_grid* g) {
@@ -658,6 +660,8 @@ void refresh_all_shells(sacrak_grid* g) {
     g->split_dirty = false;
   }
   if (g->prm.matter && g->matter_ready && g->matter_shells_dirty) {
+    if (g->prm.zsym)  // new fluid data: mirror it first
+      for (int p = 0; p < g->npatches; ++p) launch_matter_zreflect(matter_args(g, p, 0, 0.0, 1.0, 0.0, 0), g->stream);
     for (int l = 1; l < g->nlevels; ++l) refresh_matter_shells(g, l);
     g->matter_shells_dirty = false;
   }
@@ -715,6 +719,8 @@ void matter_recover(sacrak_grid* g, int l, int s, double dt, double s0 = 1.0, do
       launch_matter_ghosts(a, g->stream);
     else
       launch_matter_child_ghosts(a, g->stream);
+    // equatorial symmetry: after the other ghost treatments (patches on z = 0)
+    if (g->prm.zsym) launch_matter_zreflect(a, g->stream);
   }
 }
 
@@ -1021,7 +1027,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   *out = nullptr;
   Layout L;
   std::string why;
-  if (params->matter < 0 || params->matter > 1 || (params->matter && params->zsym)) return SACRAK_EINVAL;
+  if (params->matter < 0 || params->matter > 1) return SACRAK_EINVAL;
   if (!describe(nlevels, npatches, pd, params->precision == 1, params->matter, L, why)) return SACRAK_EINVAL;
   if (arena_bytes < L.total || ((uintptr_t)device_arena % 256) != 0) return SACRAK_EINVAL;
   const sacrak_params& p = *params;

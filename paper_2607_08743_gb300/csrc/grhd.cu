@@ -332,6 +332,29 @@ __global__ void __launch_bounds__(128) matter_ghost_kernel(MatterArgs A) {
   }
 }
 
+// equatorial symmetry (Sec. 2.2.2): the z < 0 ghost layers of a patch on
+// z = 0 mirror the layers above (layer k < GH takes layer 2 GH - 1 - k), the
+// primitives and the stage's conserved variables; u_z and J^_z are odd in z,
+// the rest even
+__global__ void __launch_bounds__(128) matter_zreflect_kernel(MatterArgs A) {
+  if (!A.P->zrefl) return;
+  const long long nlay = (long long)A.NX * A.NY;
+  double* __restrict__ prim = A.P->mprim;
+  double* __restrict__ cons = matter_stage_state(A, A.lev->ring);
+  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < GH * nlay;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(id / nlay);
+    const long long r = id - k * nlay;
+    const int I = (int)(r % A.NX), J = (int)(r / A.NX);
+    const long long q = I + J * A.sy + k * A.sz;
+    const long long qm = I + J * A.sy + (2 * GH - 1 - k) * A.sz;
+#pragma unroll
+    for (int f = 0; f < NMP; ++f) prim[f * A.fs + q] = (f == 4 ? -1.0 : 1.0) * prim[f * A.fs + qm];
+#pragma unroll
+    for (int f = 0; f < NM; ++f) cons[f * A.fs + q] = (f == 3 ? -1.0 : 1.0) * cons[f * A.fs + qm];
+  }
+}
+
 __device__ __forceinline__ double minmod3(double a, double b, double c) {
   const bool pos = a > 0.0 && b > 0.0 && c > 0.0, neg = a < 0.0 && b < 0.0 && c < 0.0;
   if (!(pos || neg)) return 0.0;
@@ -846,6 +869,9 @@ __global__ void __launch_bounds__(128) matter_prolong_kernel(MatterAmrArgs A) {
   if (id >= shell_count(C)) return;
   int i, j, k;
   shell_ijk(id, C->NX, C->NY, C->NZ, i, j, k);
+  // a child on z = 0 (equatorial symmetry): its z < 0 ghosts are reflected,
+  // and their stencils would reach below the parent's array
+  if (C->zrefl && k < GH) return;
   const int pr = A.plev->ring;
   const long long sy = P->px, sz = P->plane, fs = P->fstride;
   const double* __restrict__ D = P->mcons[pr];
@@ -921,6 +947,7 @@ __global__ void __launch_bounds__(128) matter_child_ghost_kernel(MatterArgs A) {
   if (id >= shell_count(C)) return;
   int i, j, k;
   shell_ijk(id, C->NX, C->NY, C->NZ, i, j, k);
+  if (C->zrefl && k < GH) return;  // reflected afterwards (not prolonged)
   const int pr = A.plev->ring;
   const bool q3 = A.plev->nvalid >= 3;
   const double w0 = q3 ? A.wq[0] : 0.0, w1 = q3 ? A.wq[1] : A.wl[1], w2 = q3 ? A.wq[2] : A.wl[2];
@@ -1039,6 +1066,9 @@ void launch_matter_flux(const MatterArgs& a, int dir, cudaStream_t st) {
 }
 void launch_matter_update(const MatterArgs& a, cudaStream_t st) {
   matter_update_kernel<<<blocks_for((long long)a.n[0] * a.n[1] * a.n[2]), 128, 0, st>>>(a);
+}
+void launch_matter_zreflect(const MatterArgs& a, cudaStream_t st) {
+  matter_zreflect_kernel<<<blocks_for((long long)GH * a.NX * a.NY), 128, 0, st>>>(a);
 }
 void launch_matter_prim2con(const MatterArgs& a, cudaStream_t st) {
   matter_prim2con_kernel<<<blocks_for((long long)a.NX * a.NY * a.NZ), 128, 0, st>>>(a);

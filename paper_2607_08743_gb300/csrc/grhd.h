@@ -65,6 +65,9 @@ struct MatterAmrArgs {
 void launch_matter_prep(const MatterArgs& a, cudaStream_t st);
 // ghost cells of the primitive arrays
 void launch_matter_ghosts(const MatterArgs& a, cudaStream_t st);
+// equatorial symmetry: the z < 0 ghost layers of the primitives and of the
+// stage's conserved variables mirror those above z = 0 (patches on z = 0)
+void launch_matter_zreflect(const MatterArgs& a, cudaStream_t st);
 // face fluxes along dir (0, 1, 2) from the PPM states (MatterArgs::riemann)
 void launch_matter_flux(const MatterArgs& a, int dir, cudaStream_t st);
 // flux divergence + sources: RK4 stage update (stage 1..4) or d_t (stage 0)

@@ -142,3 +142,85 @@ def test_two_level_tov_star_matches_the_oracle():
     g.close()
     for i, (es, ed, ev) in errs.items():
         assert es <= 1e-9 and ed <= 1e-10 and ev <= 1e-9, errs
+
+
+def _tov_hierarchy_data(patches):
+    """TOV star (R = 8.1 isotropic) data on the given patches: metric,
+    primitives at rest on the cold curve, atmosphere floors."""
+    from initial_data.tov import TOV
+    star = TOV()
+    eos = grhd.EOS(K0=star.K, gammas=[star.G], gamma_th=1.8)
+    us, prims, floors = [], [], []
+    for p in patches:
+        z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
+        rho, psi, al = star.fields(np.sqrt(x * x + y * y + z * z))
+        u = idd.minkowski(p)
+        u[0] = psi ** -2
+        u[18] = al
+        fl = grhd.atmosphere_floor(p, 1.28e-3, 1e-12, 64.0)
+        pr = np.zeros((5,) + p.shape[1:])
+        pr[0] = np.maximum(rho, fl)
+        pr[1] = eos.cold(pr[0])[1]
+        us.append(u)
+        prims.append(pr)
+        floors.append(fl)
+    return star, eos, us, prims, floors
+
+
+def _gpu_tov(patches, us, prims, star, zsym, steps):
+    g = sk.Grid(len(patches), patches[0].dx, list(patches), sk.Params(matter=1, courant=0.25, zsym=int(zsym)),
+                stream=torch.cuda.Stream())
+    g.set_eos(star.K, [star.G], (), 1.8)
+    g.set_atmosphere(1e-12 * 1.28e-3, 64.0)
+    for i in range(len(patches)):
+        g.upload_fields(i, us[i])
+        g.upload_matter(i, prims[i])
+    for _ in range(steps):
+        g.level_step(0)
+    out = [(g.download_fields(i), g.download_matter(i)) for i in range(len(patches))]
+    g.close()
+    return out
+
+
+def test_two_level_tov_star_equatorial_symmetry():
+    """The two-level TOV star evolved on z >= 0 (equatorial symmetry, Sec.
+    2.2.2; the fluid's and the spacetime's z < 0 ghosts reflected, the child
+    on z = 0 prolonged from its parent's mirror image): two coarse steps
+    against the oracle's half-domain hierarchy (same bounds as the full
+    domain's test), and against the GPU's own full-domain evolution, whose
+    upper half it reproduces to rounding."""
+    P0 = idd.Patch(n=(32, 32, 32), dx=1.0, origin=(-16.0, -16.0, -16.0), level=0)
+    C1 = idd.Patch(n=(32, 32, 32), dx=0.5, origin=(-8.0, -8.0, -8.0), level=1)
+    h = idd.Hierarchy(dx0=1.0, levels=[[P0], [C1]], masses=[], positions=[])
+    star, eos, us, prims, floors = _tov_hierarchy_data([P0, C1])
+    hh = idd.upper_half_hierarchy(h)
+    ph = hh.patches
+    uh = [idd.upper_half_array(p, u) for p, u in zip((P0, C1), us)]
+    prh = [idd.upper_half_array(p, a) for p, a in zip((P0, C1), prims)]
+    flh = [idd.upper_half_array(p, f[None])[0] for p, f in zip((P0, C1), floors)]
+    half = _gpu_tov(ph, uh, prh, star, True, 2)
+    full = _gpu_tov((P0, C1), us, prims, star, False, 2)
+    H = A.MatterHierarchy(hh, uh, prh, eos, flh, oracle.Params(), courant=0.25, bc0=oracle.BC_SOMMERFELD,
+                          zsym=True)
+    for _ in range(2):
+        H.level_step(0)
+    a = (slice(None),) + (slice(3, -3),) * 3
+    errs = {}
+    for i, p in enumerate((P0, C1)):
+        (ug, pg), (uf, pf) = half[i], full[i]
+        ug, pg = ug[a], pg[a]
+        # the GPU's own full domain, upper half
+        assert np.abs(ug - idd.upper_half_array(p, uf)[a]).max() <= 1e-13
+        pfu = idd.upper_half_array(p, pf)[a]
+        assert np.abs(pg[0] - pfu[0]).max() <= 1e-12 * 1.28e-3
+        wf = pfu[0][None] / 1.28e-3  # eps and u_i weighted by the density, as below
+        assert np.abs(wf * (pg[1:] - pfu[1:])).max() <= 1e-11 * np.abs(wf * pfu[1:]).max()
+        # the oracle's half domain
+        uo, po = H.current(i)[a], H.prim(i)[a]
+        d = np.abs(ug - uo).max(axis=(1, 2, 3))
+        s = np.maximum(np.abs(uo - uh[i][a]).max(axis=(1, 2, 3)), 1e-5 * np.abs(uo).max(axis=(1, 2, 3)) + 1e-12)
+        wt = po[0][None] / 1.28e-3
+        errs[i] = ((d / s).max(), np.abs(pg[0] - po[0]).max() / 1.28e-3,
+                   np.abs(wt * (pg[2:] - po[2:])).max() / max(np.abs(wt * po[2:]).max(), 1e-30))
+    for i, (es, ed, ev) in errs.items():
+        assert es <= 1e-9 and ed <= 1e-10 and ev <= 1e-9, errs
