@@ -558,6 +558,10 @@ class BOHierarchy:
             raise ValueError("shift breaks the nesting")
         self._apply_move(pid, shift)
 
+    def _targets(self):
+        """The position each moving patch follows: its puncture's."""
+        return {pid: self.punct[p] for pid, p in enumerate(self.follow) if p >= 0}
+
     def regrid(self) -> int:
         """Coarse to fine, every patch that follows a puncture moves by
         trunc((x_p - centre) / dx_parent) parent cells per axis (the puncture
@@ -569,16 +573,16 @@ class BOHierarchy:
             raise ValueError("levels not synchronised")
         geoms = list(self.patches)
         plan = []
+        targets = self._targets()
         for l in range(1, len(self.level_ids)):
             for pid in self.level_ids[l]:
-                p = self.follow[pid]
-                if p < 0:
+                if pid not in targets:
                     continue
+                x = targets[pid]
                 c = geoms[pid]
                 dxp = 2.0 * c.dx
-                s = [int(math.trunc((self.punct[p][d] - (c.origin[d] + 0.5 * c.n[d] * c.dx)) / dxp))
-                     for d in range(3)]
-                fixed_kids = [q for q in self._children(pid) if self.follow[q] < 0]
+                s = [int(math.trunc((x[d] - (c.origin[d] + 0.5 * c.n[d] * c.dx)) / dxp)) for d in range(3)]
+                fixed_kids = [q for q in self._children(pid) if q not in targets]
                 lo, hi = self._shift_range(pid, geoms, fixed_kids)
                 if any(lo[d] > hi[d] for d in range(3)):
                     raise ValueError("patch %d cannot stay nested" % pid)

@@ -93,6 +93,26 @@ def linear_children(q, axis):
     return np.moveaxis(out, 0, axis)
 
 
+# 6-point Lagrange weights of the child centres at +1/4 (nodes -2..3) and
+# -1/4 (nodes -3..2) of a parent cell (the spacetime's prolongation)
+LAG_P = np.array([77.0, -693.0, 6930.0, 2310.0, -495.0, 63.0]) / 8192.0
+LAG_M = LAG_P[::-1]
+
+
+def lagrange_children(q, axis):
+    """Values at the two child centres of every parent cell along `axis`
+    by 6th-order Lagrange interpolation of the parent values q (exact for
+    quintics); NaN for parent cells without three neighbours on each side."""
+    q = np.moveaxis(np.asarray(q, dtype=np.float64), axis, 0)
+    N = q.shape[0]
+    out = np.full((2 * N,) + q.shape[1:], np.nan)
+    left = sum(LAG_M[m] * q[m:N - 6 + m] for m in range(6))       # nodes I-3 .. I+2, I = 3 .. N-4
+    right = sum(LAG_P[m] * q[1 + m:N - 5 + m] for m in range(6))  # nodes I-2 .. I+3
+    out[6:2 * N - 6:2] = left[:N - 6]
+    out[7:2 * N - 5:2] = right[:N - 6]
+    return np.moveaxis(out, 0, axis)
+
+
 # ------------------------------------------------------------------ equatorial symmetry
 
 PRIM_Z_PARITY = np.array([1.0, 1.0, 1.0, 1.0, -1.0])  # rho, eps, u_x, u_y, u_z
@@ -191,6 +211,15 @@ def lagrange_prolong(parent, child, fields):
     return uc[:nf]
 
 
+def lagrange_prolong_cells(parent, child, q):
+    """The child's whole array of a parent field q by the tensor-product
+    6th-order Lagrange interpolation (x, then y, then z)."""
+    box = _parent_box(parent, child, q, 3)
+    for ax in (-1, -2, -3):
+        box = lagrange_children(box, ax)
+    return _child_cells(box, child, 3)
+
+
 def ghost_mask(child):
     g = child.g
     m = np.ones(tuple(child.n[d] + 2 * g for d in (2, 1, 0)), dtype=bool)
@@ -198,18 +227,23 @@ def ghost_mask(child):
     return m
 
 
-def prolong_fluid(parent, cons_p, prim_p, child):
+def prolong_fluid(parent, cons_p, prim_p, child, ghosts_only=True):
     """Child ghost values (D^, eps, u_x, u_y, u_z) from one parent time
     level (densitised conserved variables and primitives, arrays with
-    ghosts); entries outside the ghost shell are NaN."""
+    ghosts); entries outside the ghost shell are NaN (ghosts_only=False:
+    every cell of the child's array)."""
     D = weno5_prolong(parent, child, cons_p[0])
     bad = ~(D > 0.0)
     D = np.where(bad, parent_cell_values(parent, child, cons_p[0]), D)
-    lag = lagrange_prolong(parent, child, [prim_p[1], prim_p[2], prim_p[3], prim_p[4]])
+    if ghosts_only:
+        lag = lagrange_prolong(parent, child, [prim_p[1], prim_p[2], prim_p[3], prim_p[4]])
+    else:
+        lag = [lagrange_prolong_cells(parent, child, prim_p[f]) for f in (1, 2, 3, 4)]
     eps_lin = linear_prolong(parent, child, prim_p[1])
     eps = np.where(bad | ~(lag[0] > 0.0), eps_lin, lag[0])
     out = np.array([D, eps, lag[1], lag[2], lag[3]])
-    out[:, ~ghost_mask(child)] = np.nan
+    if ghosts_only:
+        out[:, ~ghost_mask(child)] = np.nan
     return out
 
 
@@ -297,6 +331,43 @@ def rest_mass(hierarchy_patches, cons, levels_children):
     return total
 
 
+# ------------------------------------------------------------------ moving patches (Sec. 2.2.1)
+
+def density_maximum(p, prim):
+    """(rho_max, x, y, z): the largest rest-mass density over the patch's
+    active cells and that cell's centre (the first in z, y, x order where
+    several are equal).  A neutron star is located there."""
+    g = p.g
+    rho = prim[0, g:-g, g:-g, g:-g]
+    k, j, i = np.unravel_index(int(np.argmax(rho)), rho.shape)
+    return (float(rho[k, j, i]), p.origin[0] + (i + 0.5) * p.dx, p.origin[1] + (j + 0.5) * p.dx,
+            p.origin[2] + (k + 0.5) * p.dx)
+
+
+def move_fluid(parent, cons_p, prim_p, old, cons_o, prim_o, new, u_new, eos):
+    """The fluid of a patch shifted from geometry `old` to `new` (Sec.
+    2.2.1): cells active in both keep their conserved variables and
+    primitives; every other cell (ghosts included) takes the parent's
+    prolongation (D^ conservative WENO5, eps and u_i 6th-order Lagrange,
+    with the fallbacks), rho = D^ / (sqrt(gamma) w) with the new metric, and
+    the conserved variables of those primitives."""
+    vals = prolong_fluid(parent, cons_p, prim_p, new, ghosts_only=False)
+    prim = ghost_primitives(vals, new, u_new, eos)
+    cons, _, _, _ = grhd.prim2con(prim, grhd.metric(u_new), eos)
+    g = new.g
+    sh = [int(round((new.origin[d] - old.origin[d]) / new.dx)) for d in range(3)]
+    dst, src = [slice(None)], [slice(None)]
+    for d in (2, 1, 0):  # new active cell i is old active cell i + sh
+        lo, hi = max(0, -sh[d]), min(new.n[d], old.n[d] - sh[d])
+        if lo >= hi:
+            return cons, prim
+        dst.append(slice(g + lo, g + hi))
+        src.append(slice(g + lo + sh[d], g + hi + sh[d]))
+    cons[tuple(dst)] = cons_o[tuple(src)]
+    prim[tuple(dst)] = prim_o[tuple(src)]
+    return cons, prim
+
+
 # ------------------------------------------------------------------ the coupled hierarchy
 
 class MatterHierarchy(z4c.BOHierarchy):
@@ -326,6 +397,7 @@ class MatterHierarchy(z4c.BOHierarchy):
         self.favg = [None] * len(self.patches)   # a child's, averaged over its two steps
         self.children = [[c for c in range(len(self.patches)) if self.parent[c] == pid]
                          for pid in range(len(self.patches))]
+        self.follow_star = [-1] * len(self.patches)  # star each patch follows
 
     def _reflect_fluid(self, pid, cons, prim):
         """(cons, prim) with the z < 0 ghosts mirrored (zsym, patches on z = 0)."""
@@ -463,6 +535,59 @@ class MatterHierarchy(z4c.BOHierarchy):
                 if pr is None:
                     pr, cp = self._prims(ppid, cp, self.tl[ppid][-1], frac0 + dfrac)
                     self.ctl[ppid][-1] = (cp, pr)
+
+    def track_stars(self, follow_star):
+        """follow_star[pid] = the star patch pid follows (-1: none).  A star
+        is located by the maximum of the rest-mass density on the finest
+        patch that follows it (Sec. 2.2.1); regrid() moves its followers."""
+        if len(follow_star) != len(self.patches):
+            raise ValueError("one entry per patch")
+        for pid, s in enumerate(follow_star):
+            if s >= 0 and (self.patches[pid].level == 0 or self.follow[pid] >= 0):
+                raise ValueError("patch %d cannot follow a star" % pid)
+        self.follow_star = [int(v) for v in follow_star]
+
+    def star_positions(self):
+        out = {}
+        for s in sorted({v for v in self.follow_star if v >= 0}):
+            pid = max((q for q, v in enumerate(self.follow_star) if v == s),
+                      key=lambda q: (self.patches[q].level, -q))
+            out[s] = density_maximum(self.patches[pid], self.prim(pid))[1:]
+        return out
+
+    def _targets(self):
+        t = super()._targets()
+        stars = self.star_positions()
+        for pid, s in enumerate(self.follow_star):
+            if s >= 0:
+                t[pid] = stars[s]
+        return t
+
+    def _apply_move(self, pid, shift):
+        """The spacetime's move, then the fluid's (move_fluid); the moved
+        level's fluid history and, as the parent's cached prolongations of
+        its older time levels would need their primitives, the parent
+        level's whole history (spacetime and fluid) restart at the current
+        time level."""
+        old = self.patches[pid]
+        oc, op = self.ctl[pid][-1]
+        super()._apply_move(pid, shift)
+        un = self.tl[pid][-1]
+        new = self.patches[pid]
+        ppid = self.parent[pid]
+        par = self.patches[ppid]
+        cp, pp = self.ctl[ppid][-1]
+        if self.zsym and z4c.touches_equator(new):
+            _, cp = mirror_extend(par, cp, CONS_Z_PARITY, 2)
+            par, pp = mirror_extend(par, pp, PRIM_Z_PARITY, 2)
+        cons, prim = move_fluid(par, cp, pp, old, oc, op, new, un, self.eos)
+        for q in self.level_ids[new.level]:
+            self.ctl[q] = [self.ctl[q][-1]]
+        self.ctl[pid] = [self._reflect_fluid(pid, cons, prim)]
+        for q in self.level_ids[new.level - 1]:
+            self.tl[q] = [self.tl[q][-1]]
+            self.ctl[q] = [self.ctl[q][-1]]
+        return un
 
     def cons(self, pid):
         return self.ctl[pid][-1][0]
