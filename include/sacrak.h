@@ -88,10 +88,9 @@ typedef struct {
                             an odd number of z indices) after every other ghost treatment;
                             not with bc = 1 */
   int matter;            /* 1: a perfect fluid evolved with the spacetime (Sec. 2.1.2, 2.2):
-                            FP64, no overlapping patches on a level, no moving
-                            patches; with zsym the fluid's z < 0 ghosts are
-                            reflected too (u_z and J_z odd, the rest even); see the
-                            matter calls below */
+                            FP64, no overlapping patches on a level; with zsym the
+                            fluid's z < 0 ghosts are reflected too (u_z and J_z odd,
+                            the rest even); see the matter calls below */
 } sacrak_params;
 
 /* One patch: refinement level, active cells per axis, lower face of active
@@ -222,20 +221,43 @@ sacrak_status sacrak_get_punctures(sacrak_grid* grid, double* pos);
  * the start of a run) and the captured coarse step is rebuilt at the next
  * sacrak_level_step.  SACRAK_EINVAL unless the patch and its children stay
  * nested (4 parent cells of margin; under equatorial symmetry no shift along
- * z).  Synchronises. */
+ * z).  With a fluid (Sec. 2.2.1) the same holds for its conserved variables
+ * and primitives: cells active before and after keep them, every other
+ * cell takes the parent's fluid prolongation (D^ by the conservative WENO5,
+ * eps and u_i by the 6th-order Lagrange interpolation, with the fallbacks of
+ * the refinement-boundary ghosts) with rho = D^ / (sqrt(gamma) w) on the
+ * moved metric; the parent level's time-level history restarts too (the
+ * fluid's primitives exist for the current time level only); SACRAK_ESTATE
+ * before sacrak_upload_matter.  Synchronises. */
 sacrak_status sacrak_move_patch(sacrak_grid* grid, int patch, const int shift[3]);
 
 /* Lower face of active cell 0 of a patch (host array of 3), as moved. */
 sacrak_status sacrak_patch_origin(sacrak_grid* grid, int patch, double origin[3]);
 
 /* Regrid between coarse steps: coarse to fine, every patch that follows a
- * puncture is shifted by trunc((x_p - centre) / dx_parent) parent cells per
- * axis (the puncture then lies within one parent cell of the patch centre),
- * clamped so that it nests in its parent's new position and keeps its
- * children that follow no puncture nested; the whole plan is checked before
+ * puncture or a star is shifted by trunc((x_p - centre) / dx_parent) parent
+ * cells per axis (the object then lies within one parent cell of the patch
+ * centre), clamped so that it nests in its parent's new position and keeps
+ * its children that follow nothing nested; the whole plan is checked before
  * any data moves (SACRAK_EINVAL and nothing moved if the result would not
- * nest).  *moved = patches shifted.  Synchronises. */
+ * nest).  A star's position is the density maximum (sacrak_density_maximum)
+ * of the finest patch that follows it, taken before any patch moves.
+ * *moved = patches shifted.  Synchronises. */
 sacrak_status sacrak_regrid(sacrak_grid* grid, int* moved);
+
+/* Fluid grids: the largest rest-mass density rho over the active cells of a
+ * patch's current time level, out[0], and the centre of that cell,
+ * out[1..3] (the first in z, y, x order where several are equal).  A
+ * neutron star is located there (Sec. 2.2.1).  SACRAK_ENONFINITE when no
+ * cell holds a finite density.  Synchronises. */
+sacrak_status sacrak_density_maximum(sacrak_grid* grid, int patch, double out[4]);
+
+/* Fluid grids: follow[q] (host array of npatches entries) is the star patch
+ * q follows, -1 for none (level-0 patches cannot follow, nor can a patch
+ * that follows a puncture); every star 0..nstars-1 must be followed by some
+ * patch.  sacrak_regrid moves the followers; nstars = 0 stops following.
+ * Host only. */
+sacrak_status sacrak_track_stars(sacrak_grid* grid, int nstars, const int* follow);
 
 /* ADM mass, angular momentum about z (Sec. 2.3) and linear momentum
  * (Sec. 3.2) on the coordinate sphere |x - centre| = radius of one patch's

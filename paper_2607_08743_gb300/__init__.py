@@ -34,6 +34,7 @@ EXPORTS = [
     "sacrak_patch_origin", "sacrak_psi4_modes", "sacrak_nakano", "sacrak_ffi_work_bytes", "sacrak_ffi_strain",
     "sacrak_set_wait_limit", "sacrak_set_eos", "sacrak_set_atmosphere", "sacrak_upload_matter",
     "sacrak_download_matter", "sacrak_matter_rhs", "sacrak_set_overlap", "sacrak_set_riemann",
+    "sacrak_density_maximum", "sacrak_track_stars",
 ]
 
 # stage kernels (sacrak_set_stage_kernel): 0 direct, 1..4 TMA-staged tiles,
@@ -122,6 +123,8 @@ def lib() -> ctypes.CDLL:
             L.sacrak_upload_matter.argtypes = [vp, ctypes.c_int, vp]
             L.sacrak_download_matter.argtypes = [vp, ctypes.c_int, vp]
             L.sacrak_matter_rhs.argtypes = [vp, ctypes.c_int, vp]
+            L.sacrak_density_maximum.argtypes = [vp, ctypes.c_int, dp]
+            L.sacrak_track_stars.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
             L.sacrak_get_stage_kernel.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
             L.sacrak_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
             L.sacrak_last_error.argtypes = [vp]
@@ -416,6 +419,19 @@ class Grid:
         o = (ctypes.c_double * 3)()
         self._check(lib().sacrak_patch_origin(self._h, patch, o), "patch_origin")
         return tuple(o)
+
+    def density_maximum(self, patch: int):
+        """(rho_max, x, y, z) over the patch's active cells (fluid grids)."""
+        out = (ctypes.c_double * 4)()
+        self._check(lib().sacrak_density_maximum(self._h, patch, out), "density_maximum")
+        return tuple(out)
+
+    def track_stars(self, follow):
+        """follow[patch] = the star the patch follows (-1: none); regrid()
+        moves the followers toward each star's density maximum."""
+        n = max([int(v) for v in follow] + [-1]) + 1
+        fl = (ctypes.c_int * max(1, len(follow)))(*[int(v) for v in follow])
+        self._check(lib().sacrak_track_stars(self._h, n, fl), "track_stars")
 
     def regrid(self) -> int:
         m = ctypes.c_int()

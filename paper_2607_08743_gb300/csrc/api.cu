@@ -166,6 +166,10 @@ struct sacrak_grid {
   DevPunct* d_punct;
   int npunct = 0;
   std::vector<int> follow;
+  // fluid grids: the star each patch follows (-1: none), located by the
+  // density maximum of the finest patch that follows it
+  std::vector<int> follow_star;
+  int nstars = 0;
   std::vector<DevPunct> hpunct;  // tracking patch and level of each puncture
   bool invalid = false;
   cudaGraph_t graph = nullptr;
@@ -887,7 +891,7 @@ int nest_lo(const sacrak_grid* g, const DevPatch& c, const DevPatch& par, int d,
 std::vector<int> children_of(const sacrak_grid* g, int pid, bool only_fixed) {
   std::vector<int> k;
   for (int q = 0; q < g->npatches; ++q)
-    if (g->hp[q].parent == pid && (!only_fixed || g->follow[q] < 0)) k.push_back(q);
+    if (g->hp[q].parent == pid && (!only_fixed || (g->follow[q] < 0 && g->follow_star[q] < 0))) k.push_back(q);
   return k;
 }
 
@@ -958,21 +962,44 @@ void apply_move(sacrak_grid* g, int pid, const int s[3], const std::vector<DevLe
   // where the parent level's patches share active cells, the exchange at the
   // start of each of its steps averaged them in place in its stored time
   // levels: caches of its older slots rebuilt now would differ from those
-  // its children used, so its history restarts too
-  if (active_overlap(g, C.level - 1)) launch_set_nvalid(g->d_levels + C.level - 1, 1, g->stream);
+  // its children used, so its history restarts too.  With a fluid it
+  // restarts as well: the fluid's primitives exist for the current time
+  // level only, so the moved patch's cached prolongations of the parent's
+  // older levels cannot be rebuilt
+  if (active_overlap(g, C.level - 1) || g->prm.matter) launch_set_nvalid(g->d_levels + C.level - 1, 1, g->stream);
   zreflect(g, C.level, 1, 0);
+  if (g->prm.matter) {
+    // the fluid (Sec. 2.2.1): kept where active before and after, the
+    // parent's prolongation elsewhere, into the face-flux arrays, then back
+    MatterMoveArgs m;
+    m.patches = g->d_patches;
+    m.patch = pid;
+    m.ring = lv[C.level].ring;
+    m.pring = lv[C.level - 1].ring;
+    for (int d = 0; d < 3; ++d) m.sh[d] = 2 * s[d];
+    m.eos = g->eos;
+    m.err = g->d_err;
+    launch_matter_move(m, (long long)C.NX * C.NY * C.NZ, g->stream);
+    cudaMemcpyAsync(C.mcons[m.ring], C.mflux, sizeof(double) * NM * C.fstride, cudaMemcpyDeviceToDevice, g->stream);
+    cudaMemcpyAsync(C.mprim, C.mflux + NM * C.fstride, sizeof(double) * NMP * C.fstride, cudaMemcpyDeviceToDevice,
+                    g->stream);
+    if (g->prm.zsym) launch_matter_zreflect(matter_args(g, pid, 0, 0.0, 1.0, 0.0, 0), g->stream);
+  }
   if (g->prm.precision == 1)
     launch_split(g->d_patches, g->d_levels, pid, (long long)C.NX * C.NY * C.NZ, g->stream);
 }
 
-// after moves: every child level's cache of all three parent slots, and no
-// captured coarse step
+// after moves: every child level's cache of all three parent slots (the
+// fluid's: of the parent's current slot, the only valid one after a move),
+// and no captured coarse step
 void refresh_after_move(sacrak_grid* g) {
   for (int l = 1; l < g->nlevels; ++l)
     for (int back = 0; back < 3; ++back)
       launch_prolong_space(g->d_patches, g->d_ids + g->lvl_id_off[l], g->d_levels + (l - 1),
                            (int)g->lvl_ids[l].size(), g->lvl_max_clusters[l], g->prm.precision == 1,
                            g->stream, back);
+  if (g->prm.matter)
+    for (int l = 1; l < g->nlevels; ++l) refresh_matter_shells(g, l);
   drop_graph(g);
 }
 
@@ -1178,6 +1205,7 @@ sacrak_status sacrak_grid_create(int nlevels, double dx0, int npatches,
   g->d_dslot = (float*)(g->arena + L.dslot);
   g->d_punct = (DevPunct*)(g->arena + L.punct);
   g->follow.assign(npatches, -1);
+  g->follow_star.assign(npatches, -1);
   std::vector<int> ids;
   std::vector<Tile> tiles;
   g->lvl_id_off.resize(nlevels);
@@ -1605,7 +1633,6 @@ sacrak_status sacrak_adm_integrals(sacrak_grid* g, int patch, const double centr
 
 sacrak_status sacrak_track_punctures(sacrak_grid* g, int npunct, const double* pos, const int* follow) {
   if (!g) return SACRAK_EINVAL;
-  if (g->prm.matter) return fail(g, SACRAK_EINVAL, "moving patches are not supported with a fluid");
   if (npunct < 0 || npunct > MAX_PUNCT || (npunct > 0 && (!pos || !follow)))
     return fail(g, SACRAK_EINVAL, "bad arguments");
   std::vector<DevPunct> hp(npunct);
@@ -1623,6 +1650,8 @@ sacrak_status sacrak_track_punctures(sacrak_grid* g, int npunct, const double* p
       if (follow[q] < -1 || follow[q] >= npunct) return fail(g, SACRAK_EINVAL, "follow[%d] out of range", q);
       if (follow[q] >= 0 && g->hp[q].level == 0)
         return fail(g, SACRAK_EINVAL, "level-0 patch %d cannot move", q);
+      if (follow[q] >= 0 && g->follow_star[q] >= 0)
+        return fail(g, SACRAK_EINVAL, "patch %d follows a star", q);
       fl[q] = follow[q];
       if (fl[q] >= 0 && g->hp[q].level > hp[fl[q]].level) {  // the finest patch tracks
         hp[fl[q]].patch = q;
@@ -1657,9 +1686,60 @@ sacrak_status sacrak_get_punctures(sacrak_grid* g, double* pos) {
   return SACRAK_OK;
 }
 
+// the largest rest-mass density over the patch's active cells and the centre
+// of the first cell (z, y, x order) that holds it
+sacrak_status density_maximum(sacrak_grid* g, int patch, double out[4]) {
+  const DevPatch& P = g->hp[patch];
+  const int maxb = (int)std::min<size_t>(g->L.scratch_doubles / 2, 152 * 16);
+  launch_density_max(g->d_patches, patch, (long long)P.n[0] * P.n[1] * P.n[2], g->d_scratch, maxb, g->stream);
+  double r[2];
+  CK(cudaMemcpyAsync(r, g->d_scratch, sizeof r, cudaMemcpyDeviceToHost, g->stream));
+  sacrak_status st = sync_and_check(g);
+  if (st != SACRAK_OK) return st;
+  const long long id = (long long)r[1];
+  if (id < 0) return fail(g, SACRAK_ENONFINITE, "no finite density on patch %d", patch);
+  const long long i = id % P.n[0], j = (id / P.n[0]) % P.n[1], k = id / ((long long)P.n[0] * P.n[1]);
+  out[0] = r[0];
+  out[1] = P.origin[0] + (i + 0.5) * P.dx;
+  out[2] = P.origin[1] + (j + 0.5) * P.dx;
+  out[3] = P.origin[2] + (k + 0.5) * P.dx;
+  return SACRAK_OK;
+}
+
+sacrak_status sacrak_density_maximum(sacrak_grid* g, int patch, double out[4]) {
+  if (!g) return SACRAK_EINVAL;
+  if (!g->prm.matter) return fail(g, SACRAK_EINVAL, "grid created without a fluid (params.matter = 0)");
+  if (patch < 0 || patch >= g->npatches || !out) return fail(g, SACRAK_EINVAL, "bad arguments");
+  if (!g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
+  sacrak_status st = not_capturing(g);
+  if (st != SACRAK_OK) return st;
+  return density_maximum(g, patch, out);
+}
+
+sacrak_status sacrak_track_stars(sacrak_grid* g, int nstars, const int* follow) {
+  if (!g) return SACRAK_EINVAL;
+  if (!g->prm.matter) return fail(g, SACRAK_EINVAL, "grid created without a fluid (params.matter = 0)");
+  if (nstars < 0 || nstars > g->npatches || (nstars > 0 && !follow)) return fail(g, SACRAK_EINVAL, "bad arguments");
+  std::vector<int> fl(g->npatches, -1), count(nstars, 0);
+  if (nstars > 0)
+    for (int q = 0; q < g->npatches; ++q) {
+      if (follow[q] < -1 || follow[q] >= nstars) return fail(g, SACRAK_EINVAL, "follow[%d] out of range", q);
+      if (follow[q] >= 0 && g->hp[q].level == 0)
+        return fail(g, SACRAK_EINVAL, "level-0 patch %d cannot move", q);
+      if (follow[q] >= 0 && g->follow[q] >= 0) return fail(g, SACRAK_EINVAL, "patch %d follows a puncture", q);
+      fl[q] = follow[q];
+      if (fl[q] >= 0) count[fl[q]]++;
+    }
+  for (int sidx = 0; sidx < nstars; ++sidx)
+    if (count[sidx] == 0) return fail(g, SACRAK_EINVAL, "star %d is followed by no patch", sidx);
+  g->follow_star = fl;
+  g->nstars = nstars;
+  return SACRAK_OK;
+}
+
 sacrak_status sacrak_move_patch(sacrak_grid* g, int patch, const int shift[3]) {
   if (!g) return SACRAK_EINVAL;
-  if (g->prm.matter) return fail(g, SACRAK_EINVAL, "moving patches are not supported with a fluid");
+  if (g->prm.matter && !g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
   if (patch < 0 || patch >= g->npatches || !shift) return fail(g, SACRAK_EINVAL, "bad arguments");
   if (g->hp[patch].level == 0) return fail(g, SACRAK_EINVAL, "level-0 patches do not move");
   if (g->invalid) return fail(g, SACRAK_ESTATE, "grid holds invalid data");
@@ -1692,7 +1772,8 @@ sacrak_status sacrak_regrid(sacrak_grid* g, int* moved) {
   if (!g) return SACRAK_EINVAL;
   if (!moved) return fail(g, SACRAK_EINVAL, "bad arguments");
   *moved = 0;
-  if (g->npunct == 0) return SACRAK_OK;
+  if (g->npunct == 0 && g->nstars == 0) return SACRAK_OK;
+  if (g->prm.matter && !g->matter_ready) return fail(g, SACRAK_ESTATE, "no fluid uploaded (sacrak_upload_matter)");
   if (g->invalid) return fail(g, SACRAK_ESTATE, "grid holds invalid data");
   sacrak_status st = not_capturing(g);
   if (st != SACRAK_OK) return st;
@@ -1700,21 +1781,34 @@ sacrak_status sacrak_regrid(sacrak_grid* g, int* moved) {
   st = synchronised(g, lv);
   if (st != SACRAK_OK) return st;
   std::vector<DevPunct> hx(g->npunct);
-  CK(cudaMemcpyAsync(hx.data(), g->d_punct, sizeof(DevPunct) * g->npunct, cudaMemcpyDeviceToHost, g->stream));
+  if (g->npunct > 0)
+    CK(cudaMemcpyAsync(hx.data(), g->d_punct, sizeof(DevPunct) * g->npunct, cudaMemcpyDeviceToHost, g->stream));
   st = sync_and_check(g);
   if (st != SACRAK_OK) return st;
+  // the stars: the density maximum of the finest patch that follows each
+  std::vector<std::array<double, 3>> xs(g->nstars);
+  for (int sidx = 0; sidx < g->nstars; ++sidx) {
+    int best = -1;
+    for (int q = 0; q < g->npatches; ++q)
+      if (g->follow_star[q] == sidx && (best < 0 || g->hp[q].level > g->hp[best].level)) best = q;
+    double r[4];
+    st = density_maximum(g, best, r);
+    if (st != SACRAK_OK) return st;
+    xs[sidx] = {r[1], r[2], r[3]};
+  }
   // plan coarse to fine on copies of the geometry, check it, then move
   std::vector<DevPatch> geo = g->hp;
   std::vector<std::pair<int, std::array<int, 3>>> plan;
   for (int l = 1; l < g->nlevels; ++l)
     for (int pid : g->lvl_ids[l]) {
-      const int p = g->follow[pid];
-      if (p < 0) continue;
+      const int p = g->follow[pid], sp = g->follow_star[pid];
+      if (p < 0 && sp < 0) continue;
+      const double* target = p >= 0 ? hx[p].x : xs[sp].data();
       DevPatch& c = geo[pid];
       const double dxp = 2.0 * c.dx;
       std::array<int, 3> s;
       for (int d = 0; d < 3; ++d)
-        s[d] = (int)std::trunc((hx[p].x[d] - (c.origin[d] + 0.5 * c.n[d] * c.dx)) / dxp);
+        s[d] = (int)std::trunc((target[d] - (c.origin[d] + 0.5 * c.n[d] * c.dx)) / dxp);
       int lo[3], hi[3];
       shift_range(g, pid, geo, children_of(g, pid, true), lo, hi);
       for (int d = 0; d < 3; ++d) {

@@ -860,23 +860,16 @@ __device__ __forceinline__ double weno_half(double a, double b, double c, double
 __constant__ double c_lp[6] = {77.0 / 8192, -693.0 / 8192, 6930.0 / 8192, 2310.0 / 8192, -495.0 / 8192, 63.0 / 8192};
 __constant__ double c_lm[6] = {63.0 / 8192, -495.0 / 8192, 2310.0 / 8192, 6930.0 / 8192, -693.0 / 8192, 77.0 / 8192};
 
-// one thread per ghost-shell cell of a child: the parent's current fluid
-// prolonged, cached in the child's slot of the parent's current ring slot
-__global__ void __launch_bounds__(128) matter_prolong_kernel(MatterAmrArgs A) {
-  const DevPatch* C = A.patches + A.child_ids[blockIdx.y];
-  const DevPatch* P = A.patches + C->parent;
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= shell_count(C)) return;
-  int i, j, k;
-  shell_ijk(id, C->NX, C->NY, C->NZ, i, j, k);
-  // a child on z = 0 (equatorial symmetry): its z < 0 ghosts are reflected,
-  // and their stencils would reach below the parent's array
-  if (C->zrefl && k < GH) return;
-  const int pr = A.plev->ring;
+// The parent's fluid at cell ci (active index, ghosts negative) of child C,
+// from the parent's ring slot pr: D^ by the conservative WENO5 (x, y, z),
+// eps and u_i by the tensor-product 6th-order Lagrange interpolation, the
+// parent cell's D^ where the WENO value is not positive, trilinear eps where
+// that or the Lagrange eps is not positive.  v = (D^, eps, u_x, u_y, u_z).
+__device__ __forceinline__ void prolong_fluid_cell(const DevPatch* C, const DevPatch* P, int pr, const int ci[3],
+                                                   double v[NM]) {
   const long long sy = P->px, sz = P->plane, fs = P->fstride;
   const double* __restrict__ D = P->mcons[pr];
   const double* __restrict__ prim = P->mprim;
-  const int ci[3] = {i - GH, j - GH, k - GH};
   int pc[3];
   bool odd[3];
 #pragma unroll
@@ -929,14 +922,163 @@ __global__ void __launch_bounds__(128) matter_prolong_kernel(MatterAmrArgs A) {
     }
     eps = 0.75 * vzl[0] + 0.25 * vzl[1];
   }
+  v[0] = Dv;
+  v[1] = eps;
+  v[2] = lag[1];
+  v[3] = lag[2];
+  v[4] = lag[3];
+}
+
+// one thread per ghost-shell cell of a child: the parent's current fluid
+// prolonged, cached in the child's slot of the parent's current ring slot
+__global__ void __launch_bounds__(128) matter_prolong_kernel(MatterAmrArgs A) {
+  const DevPatch* C = A.patches + A.child_ids[blockIdx.y];
+  const DevPatch* P = A.patches + C->parent;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= shell_count(C)) return;
+  int i, j, k;
+  shell_ijk(id, C->NX, C->NY, C->NZ, i, j, k);
+  // a child on z = 0 (equatorial symmetry): its z < 0 ghosts are reflected,
+  // and their stencils would reach below the parent's array
+  if (C->zrefl && k < GH) return;
+  const int pr = A.plev->ring;
+  const int ci[3] = {i - GH, j - GH, k - GH};
+  double v[NM];
+  prolong_fluid_cell(C, P, pr, ci, v);
   double* __restrict__ cache = C->mgsh[pr];
   const long long fc = C->fstride;
   const long long qc = i + (long long)j * C->px + (long long)k * C->plane;
-  cache[qc] = Dv;
-  cache[fc + qc] = eps;
-  cache[2 * fc + qc] = lag[1];
-  cache[3 * fc + qc] = lag[2];
-  cache[4 * fc + qc] = lag[3];
+#pragma unroll
+  for (int f = 0; f < NM; ++f) cache[f * fc + qc] = v[f];
+}
+
+// The fluid of a patch shifted by sh child cells (its geometry already the
+// new one, the spacetime already moved): every cell of its array that was
+// active before and is active now keeps (conserved, primitives, w); every
+// other cell takes the parent's prolongation (prolong_fluid_cell) with
+// rho = D^ / (sqrt(gamma) w) on the new metric and its conserved variables.
+// Output to the patch's face-flux arrays (dead between steps): fields 0..4
+// the conserved variables, 5..10 the primitives and w.
+__global__ void __launch_bounds__(128) matter_move_kernel(MatterMoveArgs A) {
+  const DevPatch* C = A.patches + A.patch;
+  const DevPatch* P = A.patches + C->parent;
+  const long long ntot = (long long)C->NX * C->NY * C->NZ;
+  const long long sy = C->px, sz = C->plane, fs = C->fstride;
+  const double* __restrict__ cons = C->mcons[A.ring];
+  const double* __restrict__ prim = C->mprim;
+  const double* __restrict__ u = C->buf[A.ring];
+  double* __restrict__ out = C->mflux;
+  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < ntot;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(id % C->NX), J = (int)((id / C->NX) % C->NY), K = (int)(id / ((long long)C->NX * C->NY));
+    const long long q = I + J * sy + K * sz;
+    const int ci[3] = {I - GH, J - GH, K - GH};
+    bool copy = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      copy = copy && ci[d] >= 0 && ci[d] < C->n[d] && ci[d] + A.sh[d] >= 0 && ci[d] + A.sh[d] < C->n[d];
+    if (copy) {
+      const long long qo = q + A.sh[0] + A.sh[1] * sy + A.sh[2] * sz;
+#pragma unroll
+      for (int f = 0; f < NM; ++f) out[f * fs + q] = cons[f * fs + qo];
+#pragma unroll
+      for (int f = 0; f < NMP; ++f) out[(NM + f) * fs + q] = prim[f * fs + qo];
+      continue;
+    }
+    if (C->zrefl && K < GH) {  // reflected afterwards
+#pragma unroll
+      for (int f = 0; f < NM + NMP; ++f) out[f * fs + q] = 0.0;
+      continue;
+    }
+    double v[NM];
+    prolong_fluid_cell(C, P, A.pring, ci, v);
+    Met m;
+    metric_at(u, q, fs, m, nullptr);
+    const double ul[3] = {v[2], v[3], v[4]};
+    double uu[3];
+    raise3(m.gu, ul, uu);
+    const double w = sqrt(1.0 + ul[0] * uu[0] + ul[1] * uu[1] + ul[2] * uu[2]);
+    double pr[NM] = {v[0] / (m.sg * w), v[1], v[2], v[3], v[4]}, c[NM], w2, h, Pp;
+    prim2con(A.eos, m, pr, c, w2, h, Pp);
+    bool finite = true;
+#pragma unroll
+    for (int f = 0; f < NM; ++f) {
+      out[f * fs + q] = c[f];
+      out[(NM + f) * fs + q] = pr[f];
+      finite = finite && isfinite(c[f]);
+    }
+    out[(NM + NM) * fs + q] = w2;
+    if (!finite) atomicOr(A.err, (unsigned)ERR_NONFINITE);
+  }
+}
+
+// Density maximum (a neutron star is located there, Sec. 2.2.1): per block
+// the largest rest-mass density over the patch's active cells and the first
+// active index (z, y, x order) that holds it; NaN cells never win.
+__device__ __forceinline__ void argmax_merge(double& v, long long& i, double v2, long long i2) {
+  if (i2 >= 0 && (i < 0 || v2 > v || (v2 == v && i2 < i))) {
+    v = v2;
+    i = i2;
+  }
+}
+
+__global__ void __launch_bounds__(256) density_max_kernel(const DevPatch* patches, int patch, double* part) {
+  const DevPatch* P = patches + patch;
+  const long long nact = (long long)P->n[0] * P->n[1] * P->n[2];
+  double best = 0.0;
+  long long bi = -1;
+  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < nact;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % P->n[0]), j = (int)((id / P->n[0]) % P->n[1]);
+    const int k = (int)(id / ((long long)P->n[0] * P->n[1]));
+    const double r = P->mprim[(i + GH) + (long long)(j + GH) * P->px + (long long)(k + GH) * P->plane];
+    if (r == r) argmax_merge(best, bi, r, id);
+  }
+  __shared__ double sv[256];
+  __shared__ long long si[256];
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      double v = sv[threadIdx.x];
+      long long ix = si[threadIdx.x];
+      argmax_merge(v, ix, sv[threadIdx.x + h], si[threadIdx.x + h]);
+      sv[threadIdx.x] = v;
+      si[threadIdx.x] = ix;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sv[0];
+    part[2 * blockIdx.x + 1] = (double)si[0];
+  }
+}
+
+// the blocks' pairs reduced the same way; the result in part[0], part[1]
+__global__ void __launch_bounds__(256) density_max_final_kernel(double* part, int nblocks) {
+  double best = 0.0;
+  long long bi = -1;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) argmax_merge(best, bi, part[2 * b], (long long)part[2 * b + 1]);
+  __shared__ double sv[256];
+  __shared__ long long si[256];
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      double v = sv[threadIdx.x];
+      long long ix = si[threadIdx.x];
+      argmax_merge(v, ix, sv[threadIdx.x + h], si[threadIdx.x + h]);
+      sv[threadIdx.x] = v;
+      si[threadIdx.x] = ix;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[0] = sv[0];
+    part[1] = (double)si[0];
+  }
 }
 
 // ghost cells of a level > 0 fluid: the time interpolant of the cached
@@ -1080,6 +1222,17 @@ void launch_matter_child_ghosts(const MatterArgs& a, cudaStream_t st) {
 void launch_matter_prolong(const MatterAmrArgs& a, int nchildren, long long max_shell, cudaStream_t st) {
   if (nchildren == 0 || max_shell == 0) return;
   matter_prolong_kernel<<<dim3((unsigned)((max_shell + 127) / 128), nchildren), 128, 0, st>>>(a);
+}
+void launch_matter_move(const MatterMoveArgs& a, long long ncells, cudaStream_t st) {
+  matter_move_kernel<<<blocks_for(ncells), 128, 0, st>>>(a);
+}
+void launch_density_max(const DevPatch* patches, int patch, long long nact, double* part, int max_blocks,
+                        cudaStream_t st) {
+  long long b = (nact + 255) / 256;
+  if (b > max_blocks) b = max_blocks;
+  if (b < 1) b = 1;
+  density_max_kernel<<<(unsigned)b, 256, 0, st>>>(patches, patch, part);
+  density_max_final_kernel<<<1, 256, 0, st>>>(part, (int)b);
 }
 void launch_matter_restrict(const MatterAmrArgs& a, int nchildren, long long max_cells, cudaStream_t st) {
   if (nchildren == 0 || max_cells == 0) return;

@@ -50,6 +50,17 @@ struct MatterArgs {
   int first_substep;
 };
 
+// The fluid of one patch just shifted (Sec. 2.2.1): its level's ring slot,
+// its parent's, the shift in its own cells
+struct MatterMoveArgs {
+  const DevPatch* patches;
+  int patch;
+  int ring, pring;
+  int sh[3];
+  DevEOS eos;
+  unsigned* err;
+};
+
 // One child level's fluid operators at the refinement boundary (Sec. 2.2.1)
 struct MatterAmrArgs {
   const DevPatch* patches;
@@ -65,6 +76,14 @@ struct MatterAmrArgs {
 void launch_matter_prep(const MatterArgs& a, cudaStream_t st);
 // ghost cells of the primitive arrays
 void launch_matter_ghosts(const MatterArgs& a, cudaStream_t st);
+// the fluid of a shifted patch into its face-flux arrays (copy where active
+// before and after, the parent's prolongation elsewhere; see grhd.cu)
+void launch_matter_move(const MatterMoveArgs& a, long long ncells, cudaStream_t st);
+// the largest rest-mass density over a patch's active cells and its first
+// active index: part[0], part[1] (index -1: no finite density); part holds
+// 2 x max_blocks doubles
+void launch_density_max(const DevPatch* patches, int patch, long long nact, double* part, int max_blocks,
+                        cudaStream_t st);
 // equatorial symmetry: the z < 0 ghost layers of the primitives and of the
 // stage's conserved variables mirror those above z = 0 (patches on z = 0)
 void launch_matter_zreflect(const MatterArgs& a, cudaStream_t st);

@@ -81,6 +81,8 @@ def test_diagnostics_and_moving_boxes_reject_before_device_work(L):
     assert L.sacrak_move_patch(None, 0, (ctypes.c_int * 3)(1, 0, 0)) == sk.EINVAL
     assert L.sacrak_regrid(None, ctypes.byref(ctypes.c_int())) == sk.EINVAL
     assert L.sacrak_patch_origin(None, 0, c3) == sk.EINVAL
+    assert L.sacrak_density_maximum(None, 0, out) == sk.EINVAL
+    assert L.sacrak_track_stars(None, 0, None) == sk.EINVAL
     # waveform post-processing: null arrays, n < 1, l < 2, r0 = m0 / 2
     # (D0 / (2 m0) = 1), non-positive spacing or cut
     p = ctypes.c_void_p(256)

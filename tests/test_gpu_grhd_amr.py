@@ -82,12 +82,22 @@ def test_two_level_fluid_matches_the_oracle_and_conserves_mass():
     g.close()
 
 
-def test_fluid_grids_reject_moving_patches():
+def test_fluid_moves_need_an_uploaded_fluid_and_valid_followers():
     h, ps, fluid = _setup()
     g = sk.Grid(2, h.dx0, list(ps), sk.Params(matter=1, bc=1))
     with pytest.raises(sk.SacrakError):
-        g.move_patch(1, (1, 0, 0))
+        g.move_patch(1, (1, 0, 0))       # no fluid uploaded yet
+    with pytest.raises(sk.SacrakError):
+        g.density_maximum(0)
+    with pytest.raises(sk.SacrakError):
+        g.track_stars([0, -1])           # level 0 does not move
+    with pytest.raises(sk.SacrakError):
+        g.track_stars([-1, 1])           # star 0 followed by no patch
     g.close()
+    s = sk.Grid(2, h.dx0, list(ps), sk.Params(bc=1))
+    with pytest.raises(sk.SacrakError):
+        s.track_stars([-1, 0])           # no fluid
+    s.close()
 
 
 def test_two_level_tov_star_matches_the_oracle():
@@ -222,5 +232,118 @@ def test_two_level_tov_star_equatorial_symmetry():
         wt = po[0][None] / 1.28e-3
         errs[i] = ((d / s).max(), np.abs(pg[0] - po[0]).max() / 1.28e-3,
                    np.abs(wt * (pg[2:] - po[2:])).max() / max(np.abs(wt * po[2:]).max(), 1e-30))
+    for i, (es, ed, ev) in errs.items():
+        assert es <= 1e-9 and ed <= 1e-10 and ev <= 1e-9, errs
+
+
+def _bump(p):
+    z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
+    pr = np.zeros((5,) + p.shape[1:])
+    pr[0] = 1e-6 * (1.0 + 0.5 * np.exp(-((x - 0.05) ** 2 + y * y + z * z) / 0.02))
+    pr[1] = 1e-7 / ((5.0 / 3.0 - 1.0) * pr[0])
+    pr[2] = 0.1
+    return pr
+
+
+def test_moved_fluid_patch_matches_the_oracle_and_conserves_mass():
+    """A smooth fluid bump on a periodic two-level box: a coarse step, the
+    child shifted by (2, -1, 1) parent cells, another coarse step; both
+    levels against the oracle's, and the composite rest mass from the GPU's
+    state unchanged by the move."""
+    h, ps, _ = _setup()
+    us = [idd.minkowski(p) for p in ps]
+    prims = [_bump(p) for p in ps]
+    g = sk.Grid(2, h.dx0, list(ps), sk.Params(matter=1, bc=1, lapse=1, shift=1, courant=0.25),
+                stream=torch.cuda.Stream())
+    g.set_eos(0.0, [2.0], (), 5.0 / 3.0)
+    g.set_atmosphere(1e-18, 1e3)
+    for i in range(2):
+        g.upload_fields(i, us[i])
+        g.upload_matter(i, prims[i])
+    H = A.MatterHierarchy(h, us, prims, GAS, [np.full(p.shape[1:], 1e-18) for p in ps],
+                          oracle.Params(lapse=1, shift=1), courant=0.25, bc0=oracle.BC_PERIODIC)
+    g.level_step(0)
+    H.level_step(0)
+
+    def mass():
+        gp = [g.download_matter(i) for i in range(2)]
+        gu = [g.download_fields(i) for i in range(2)]
+        geo = [ps[0], H.patches[1]]
+        cons = [grhd.prim2con(pr, grhd.metric(u), GAS)[0] for u, pr in zip(gu, gp)]
+        return A.rest_mass(geo, cons, [[1], []])
+    g.move_patch(1, (2, -1, 1))
+    H.move_patch(1, (2, -1, 1))
+    assert g.patch_origin(1) == H.patches[1].origin
+    m0 = H.rest_mass()
+    assert abs(mass() - m0) <= 1e-13 * m0
+    for stage in ("moved", "stepped"):
+        for i in range(2):
+            a = (slice(None),) + (slice(3, -3),) * 3
+            want, got = H.prim(i)[a], g.download_matter(i)[a]
+            scale = np.abs(want).max(axis=(1, 2, 3))
+            err = np.abs(got - want).max(axis=(1, 2, 3)) / scale
+            assert err.max() <= 1e-9, (stage, i, err)
+        if stage == "moved":
+            g.level_step(0)
+            H.level_step(0)
+    g.close()
+
+
+def test_density_maximum_and_star_following_regrid():
+    """A TOV star centred at x = 2.2 with the child centred on the origin:
+    the density maximum against numpy on the GPU's own primitives, the
+    star-following regrid's shift (2 parent cells, as the oracle's) and a
+    coarse step after it against the oracle (the bounds of the unmoved
+    TOV test)."""
+    P0 = idd.Patch(n=(32, 32, 32), dx=1.0, origin=(-16.0, -16.0, -16.0), level=0)
+    C1 = idd.Patch(n=(32, 32, 32), dx=0.5, origin=(-8.0, -8.0, -8.0), level=1)
+    h = idd.Hierarchy(dx0=1.0, levels=[[P0], [C1]], masses=[], positions=[])
+    from initial_data.tov import TOV
+    star = TOV()
+    eos = grhd.EOS(K0=star.K, gammas=[star.G], gamma_th=1.8)
+    us, prims, floors = [], [], []
+    for p in (P0, C1):
+        z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
+        rho, psi, al = star.fields(np.sqrt((x - 2.2) ** 2 + y * y + z * z))
+        u = idd.minkowski(p)
+        u[0] = psi ** -2
+        u[18] = al
+        fl = grhd.atmosphere_floor(p, 1.28e-3, 1e-12, 64.0)
+        pr = np.zeros((5,) + p.shape[1:])
+        pr[0] = np.maximum(rho, fl)
+        pr[1] = eos.cold(pr[0])[1]
+        us.append(u)
+        prims.append(pr)
+        floors.append(fl)
+    g = sk.Grid(2, 1.0, [P0, C1], sk.Params(matter=1, courant=0.25), stream=torch.cuda.Stream())
+    g.set_eos(star.K, [star.G], (), 1.8)
+    g.set_atmosphere(1e-12 * 1.28e-3, 64.0)
+    for i in range(2):
+        g.upload_fields(i, us[i])
+        g.upload_matter(i, prims[i])
+    H = A.MatterHierarchy(h, us, prims, eos, floors, oracle.Params(), courant=0.25, bc0=oracle.BC_SOMMERFELD)
+    g.track_stars([-1, 0])
+    H.track_stars([-1, 0])
+    g.level_step(0)
+    H.level_step(0)
+    for i, p in enumerate((P0, C1)):
+        assert g.density_maximum(i) == A.density_maximum(p, g.download_matter(i))
+    assert g.density_maximum(1)[1:] == H.star_positions()[0] == (2.25, -0.25, -0.25)
+    assert g.regrid() == 1 and H.regrid() == 1
+    assert g.patch_origin(1) == H.patches[1].origin == (-6.0, -8.0, -8.0)
+    assert g.regrid() == 0
+    g.level_step(0)
+    H.level_step(0)
+    a = (slice(None),) + (slice(3, -3),) * 3
+    errs = {}
+    for i in range(2):
+        ug, uo = g.download_fields(i)[a], H.current(i)[a]
+        d = np.abs(ug - uo).max(axis=(1, 2, 3))
+        s = np.maximum(np.abs(uo - us[i][a]).max(axis=(1, 2, 3)), 1e-5 * np.abs(uo).max(axis=(1, 2, 3)) + 1e-12)
+        pg, po = g.download_matter(i)[a], H.prim(i)[a]
+        wt = po[0][None] / 1.28e-3
+        errs[i] = ((d / s).max(), np.abs(pg[0] - po[0]).max() / 1.28e-3,
+                   np.abs(wt * (pg[2:] - po[2:])).max() / max(np.abs(wt * po[2:]).max(), 1e-30))
+    g.close()
     for i, (es, ed, ev) in errs.items():
         assert es <= 1e-9 and ed <= 1e-10 and ev <= 1e-9, errs
