@@ -65,14 +65,15 @@ class TOV:
         return rho, psi, alpha
 
 
-def tov_patch_data(p, star=None, rho_floor=None):
+def tov_patch_data(p, star=None, rho_floor=None, centre=(0.0, 0.0, 0.0)):
     """Z4c fields (isotropic coordinates: W = psi^-2, conformally flat, the
     static lapse, zero shift and extrinsic curvature) and fluid primitives
-    (rho, eps on the cold polytrope, at rest) of the star on patch p; rho is
-    at least rho_floor (an array or number) outside the star."""
+    (rho, eps on the cold polytrope, at rest) of the star centred at `centre`
+    on patch p; rho is at least rho_floor (an array or number) outside the
+    star."""
     import initial_data as idd
     star = star or TOV()
-    z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
+    z, y, x = np.meshgrid(p.axis(2) - centre[2], p.axis(1) - centre[1], p.axis(0) - centre[0], indexing="ij")
     rho, psi, al = star.fields(np.sqrt(x * x + y * y + z * z))
     u = idd.minkowski(p)
     u[0] = psi ** -2
