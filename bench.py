@@ -1185,6 +1185,23 @@ def stage_kernel_timing(g, steps, overlap=True):
 FLOPS_PER_ZONE_STAGE = {0: 4812}
 
 
+def _gpu_local_cpus(torch):
+    """The host CPUs (of those this process may use) attached to the
+    current GPU's NUMA node, from sysfs; None where that is unknown."""
+    try:
+        pr = torch.cuda.get_device_properties(torch.cuda.current_device())
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        text = open("/sys/bus/pci/devices/%s/local_cpulist" % bus).read().strip()
+        cpus = set()
+        for part in text.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        local = cpus & os.sched_getaffinity(0)
+        return local or None
+    except Exception:
+        return None
+
+
 def end_to_end(torch, sk, h, prm, args, world, dist):
     """Same metric through the public API with host buffers: every step
     uploads every patch from pinned host memory, runs the coarse step and
@@ -1193,23 +1210,41 @@ def end_to_end(torch, sk, h, prm, args, world, dist):
     g = sk.Grid(len(h.levels), h.dx0, h.patches, prm, stream=stream)
     g.set_overlap(not args.serial_ghosts)
     g.set_initial_data(1, h.masses, h.positions)
+    # the pinned host buffers on the GPU's own NUMA node (the host thread
+    # runs there while it allocates and drives them), as a caller would place
+    # them; the affinity is restored afterwards
+    saved = os.sched_getaffinity(0)
+    local = _gpu_local_cpus(torch)
+    if local and local != saved:
+        os.sched_setaffinity(0, local)
     host = [torch.empty(g.shape(i), dtype=torch.float64).pin_memory() for i in range(len(h.patches))]
     for i in range(len(h.patches)):
         g.download_fields(i, host[i])
     nbytes = sum(x.numel() * 8 for x in host)
 
+    phase = [0.0, 0.0, 0.0]  # upload, coarse step, download (host clock)
+
     def step():
+        t = time.perf_counter()
         for i in range(len(h.patches)):
-            g.upload_fields(i, host[i])
+            g.upload_fields(i, host[i])  # (each call synchronises)
+        t1 = time.perf_counter()
         g.level_step(0)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
         for i in range(len(h.patches)):
             g.download_fields(i, host[i])
+        t3 = time.perf_counter()
+        phase[0] += t1 - t
+        phase[1] += t2 - t1
+        phase[2] += t3 - t2
 
     for _ in range(max(1, args.warmup)):
         step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    phase[:] = [0.0, 0.0, 0.0]
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
@@ -1217,9 +1252,15 @@ def end_to_end(torch, sk, h, prm, args, world, dist):
     ms = (time.perf_counter() - t0) * 1e3 / args.steps
     ms = max_over_ranks(ms, dist)
     g.close()
+    del host
+    os.sched_setaffinity(0, saved)
     zu = h.zone_updates_per_coarse_step()
     return {"value": whole_job_value(zu, world, ms), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "ms_per_step": ms}
+            "host_buffers": ("pinned, allocated and driven from the %d CPUs local to the GPU" % len(local)
+                             if local and local != saved else "pinned (GPU-local CPUs unknown or all local)"),
+            "d2h_bytes_per_step": nbytes, "ms_per_step": ms,
+            "phases_ms": {"upload": 1e3 * phase[0] / args.steps, "coarse_step": 1e3 * phase[1] / args.steps,
+                          "download": 1e3 * phase[2] / args.steps}}
 
 
 if __name__ == "__main__":
