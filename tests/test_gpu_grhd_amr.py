@@ -154,16 +154,17 @@ def test_two_level_tov_star_matches_the_oracle():
         assert es <= 1e-9 and ed <= 1e-10 and ev <= 1e-9, errs
 
 
-def _tov_hierarchy_data(patches):
-    """TOV star (R = 8.1 isotropic) data on the given patches: metric,
-    primitives at rest on the cold curve, atmosphere floors."""
+def _tov_hierarchy_data(patches, xc=0.0):
+    """TOV star (R = 8.1 isotropic, centred at (xc, 0, 0)) data on the given
+    patches: metric, primitives at rest on the cold curve, atmosphere
+    floors."""
     from initial_data.tov import TOV
     star = TOV()
     eos = grhd.EOS(K0=star.K, gammas=[star.G], gamma_th=1.8)
     us, prims, floors = [], [], []
     for p in patches:
         z, y, x = np.meshgrid(p.axis(2), p.axis(1), p.axis(0), indexing="ij")
-        rho, psi, al = star.fields(np.sqrt(x * x + y * y + z * z))
+        rho, psi, al = star.fields(np.sqrt((x - xc) ** 2 + y * y + z * z))
         u = idd.minkowski(p)
         u[0] = psi ** -2
         u[18] = al
@@ -332,6 +333,46 @@ def test_density_maximum_and_star_following_regrid():
     assert g.regrid() == 1 and H.regrid() == 1
     assert g.patch_origin(1) == H.patches[1].origin == (-6.0, -8.0, -8.0)
     assert g.regrid() == 0
+    g.level_step(0)
+    H.level_step(0)
+    a = (slice(None),) + (slice(3, -3),) * 3
+    errs = {}
+    for i in range(2):
+        ug, uo = g.download_fields(i)[a], H.current(i)[a]
+        d = np.abs(ug - uo).max(axis=(1, 2, 3))
+        s = np.maximum(np.abs(uo - us[i][a]).max(axis=(1, 2, 3)), 1e-5 * np.abs(uo).max(axis=(1, 2, 3)) + 1e-12)
+        pg, po = g.download_matter(i)[a], H.prim(i)[a]
+        wt = po[0][None] / 1.28e-3
+        errs[i] = ((d / s).max(), np.abs(pg[0] - po[0]).max() / 1.28e-3,
+                   np.abs(wt * (pg[2:] - po[2:])).max() / max(np.abs(wt * po[2:]).max(), 1e-30))
+    g.close()
+    for i, (es, ed, ev) in errs.items():
+        assert es <= 1e-9 and ed <= 1e-10 and ev <= 1e-9, errs
+
+
+def test_star_following_under_equatorial_symmetry():
+    """A TOV star at x = 2.2 on the upper half of the 32^3 two-level box
+    (equatorial symmetry), the child following its density maximum: a coarse
+    step, the regrid (2 parent cells along x), a coarse step, against the
+    oracle's half-domain hierarchy (the unmoved TOV test's bounds)."""
+    P0 = idd.Patch(n=(32, 32, 16), dx=1.0, origin=(-16.0, -16.0, 0.0), level=0)
+    C1 = idd.Patch(n=(32, 32, 16), dx=0.5, origin=(-8.0, -8.0, 0.0), level=1)
+    h = idd.Hierarchy(dx0=1.0, levels=[[P0], [C1]], masses=[], positions=[])
+    star, eos, us, prims, floors = _tov_hierarchy_data([P0, C1], xc=2.2)
+    g = sk.Grid(2, 1.0, [P0, C1], sk.Params(matter=1, courant=0.25, zsym=1), stream=torch.cuda.Stream())
+    g.set_eos(star.K, [star.G], (), 1.8)
+    g.set_atmosphere(1e-12 * 1.28e-3, 64.0)
+    for i in range(2):
+        g.upload_fields(i, us[i])
+        g.upload_matter(i, prims[i])
+    H = A.MatterHierarchy(h, us, prims, eos, floors, oracle.Params(), courant=0.25, bc0=oracle.BC_SOMMERFELD,
+                          zsym=True)
+    g.track_stars([-1, 0])
+    H.track_stars([-1, 0])
+    g.level_step(0)
+    H.level_step(0)
+    assert g.regrid() == 1 and H.regrid() == 1
+    assert g.patch_origin(1) == H.patches[1].origin == (-6.0, -8.0, 0.0)
     g.level_step(0)
     H.level_step(0)
     a = (slice(None),) + (slice(3, -3),) * 3
