@@ -16,7 +16,9 @@ The exact solver is pinned first:
   rho*_L = 0.42632, rho*_R = 0.26557 (pressures scaled by eps, velocities
   by sqrt(eps));
 * two equal states colliding head-on give v* = 0, and a contact (equal
-  pressures and velocities) is left as it is.
+  pressures and velocities) is left as it is;
+* the integrated rarefaction follows the closed-form Riemann invariant of
+  the ideal gas, and a vanishing shock moves at the characteristic speed.
 
 Then the scheme: on a tube along x (a patch one zone thick across, flat
 space, outflow boundaries) the L1 error of the density falls with
@@ -62,6 +64,36 @@ def test_exact_solver_symmetric_collision_and_contact():
     assert abs(ps - 1.0) < 1e-10 and abs(vs - 0.3) < 1e-10
     assert at(0.3 - 1e-6) == pytest.approx((1.0, 1.0, 0.3), rel=1e-10)
     assert at(0.3 + 1e-6) == pytest.approx((0.1, 1.0, 0.3), rel=1e-10)
+
+
+@pytest.mark.parametrize("G", [5.0 / 3.0, 1.4])
+def test_rarefaction_follows_the_closed_form_riemann_invariant(G):
+    """Across an ideal-gas rarefaction the rapidity atanh(v) changes by
+    -/+ the integral of c_s d rho / rho along the isentrope, whose closed
+    form is (2 / sqrt(G - 1)) atanh(c_s / sqrt(G - 1)): the solver's
+    integrated simple wave agrees to 1e-11 down to P / P0 = 1e-4."""
+    gas = R.Gas(G)
+    rho0, P0, v0 = 10.0, 13.33, 0.1
+    K = P0 / rho0 ** G
+    F = lambda c: 2.0 / math.sqrt(G - 1.0) * math.atanh(c / math.sqrt(G - 1.0))
+    for P in (1e-3, 0.5, 5.0):
+        rho = (P / K) ** (1.0 / G)
+        for sign in (-1.0, 1.0):
+            v = R._rarefaction_v(gas, rho0, P0, v0, P, sign)
+            want = sign * (F(gas.cs(rho, P)) - F(gas.cs(rho0, P0)))
+            assert abs(math.atanh(v) - math.atanh(v0) - want) <= 1e-11
+
+
+def test_weak_shock_limit():
+    """A shock of vanishing strength moves at the upstream characteristic
+    speed (v0 +/- c) / (1 +/- v0 c) and leaves the upstream state."""
+    gas = R.Gas(G)
+    rho0, P0, v0 = 1.0, 0.1, 0.3
+    c = gas.cs(rho0, P0)
+    for sign in (-1.0, 1.0):
+        rho, v, V = R._shock(gas, rho0, P0, v0, P0 * (1.0 + 1e-7), sign)
+        lam = (v0 + sign * c) / (1.0 + sign * v0 * c)
+        assert abs(V - lam) < 1e-6 and abs(v - v0) < 1e-7 and abs(rho / rho0 - 1.0) < 1e-7
 
 
 def _tube(n, left, right, T=0.2, courant=0.25):
